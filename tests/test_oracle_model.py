@@ -1,0 +1,231 @@
+"""Pins for the oracle's full conditionals, perturbation and exact solves (CPU only).
+
+Each pin compares the oracle against something other than itself: a brute-force
+evaluation of the log posterior from the raw time series, numpy's least squares, dense
+inversion / eigendecomposition, the algebraic covariance of the perturbation, or Monte
+Carlo moments.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle import gibbs, linalg, model, philox
+from oracle.lattice import Lattice
+from paper_1606_00980_gb300 import synth
+
+
+def tiny(dims=(3, 3, 1), K=3, P=1, T=30, nb=4, seed=0, mask=None):
+    nx, ny, nz = dims
+    if mask is None:
+        mask = np.ones((nz, ny, nx), np.uint8)
+    w = synth.make_workload("tiny", dims, mask, T=T, K=K, P=P, neighbourhood=nb, seed=seed,
+                            ar_mean=(0.3, 0.1, 0.05)[:max(P, 1)], drift=(K >= 4), n_blobs=1)
+    return w, Lattice(w.mask, nb)
+
+
+def random_state(w, rng):
+    N, K, P = w.N, w.K, w.P
+    return dict(W=w.W_true + 0.1 * rng.standard_normal((K, N)),
+                A=w.A_true + 0.02 * rng.standard_normal((P, N)),
+                lam=rng.uniform(0.5, 2.0, N), alpha=rng.uniform(0.1, 3.0, K),
+                beta=rng.uniform(1.0, 20.0, P))
+
+
+@pytest.mark.parametrize("P", [0, 1, 3])
+def test_stats_expansion_equals_direct_whitening(P):
+    """The sufficient-statistics expansion of Appendix A equals the direct whitened
+    products of the time series (W block, A block, RSS)."""
+    w, lat = tiny(dims=(4, 3, 2), K=4, P=P, T=50, nb=6)
+    rng = np.random.default_rng(1)
+    s = random_state(w, rng)
+    st = model.sufficient_stats(w.Y, w.X, P)
+    Bd1, b1 = model.w_blocks_direct(w.Y, w.X, s["A"], s["lam"], 1e-3)
+    Bd2, b2 = model.w_blocks_from_stats(st, s["A"], s["lam"], 1e-3)
+    assert np.max(np.abs(Bd1 - Bd2)) <= 1e-12 * np.max(np.abs(Bd1))
+    assert np.max(np.abs(b1 - b2)) <= 1e-12 * np.max(np.abs(b1))
+    r1 = model.rss_direct(w.Y, w.X, s["W"], s["A"])
+    r2 = model.rss_from_stats(st, s["W"], s["A"])
+    yy = np.max(st["Syy"][:, 0, 0])
+    assert np.max(np.abs(r1 - r2)) <= 1e-13 * yy
+    if P > 0:
+        J1, a1 = model.a_blocks_direct(w.Y, w.X, s["W"], s["lam"], P)
+        J2, a2 = model.a_blocks_from_stats(st, s["W"], s["lam"])
+        assert np.max(np.abs(J1 - J2)) <= 1e-13 * yy
+        assert np.max(np.abs(a1 - a2)) <= 1e-13 * yy
+
+
+def test_P0_reduces_to_iid_model():
+    """P = 0: block lambda X'X and right-hand side lambda X'y over the full time range
+    (Eq. fullcondiidW), RSS = ||y - X w||^2 (Eq. fullcondiidlambda), shape T/2 + u2."""
+    w, lat = tiny(K=3, P=0, T=25)
+    rng = np.random.default_rng(2)
+    lam = rng.uniform(0.5, 2, w.N)
+    Bd, bw = model.w_blocks_direct(w.Y, w.X, np.zeros((0, w.N)), lam)
+    for n in range(w.N):
+        assert np.allclose(Bd[n], lam[n] * w.X.T @ w.X, rtol=1e-14, atol=0)
+        assert np.allclose(bw[n], lam[n] * w.X.T @ w.Y[:, n], rtol=1e-14, atol=0)
+    W = rng.standard_normal((3, w.N))
+    rss = model.rss_direct(w.Y, w.X, W, np.zeros((0, w.N)))
+    assert np.allclose(rss, ((w.Y - w.X @ W) ** 2).sum(axis=0), rtol=1e-13)
+    scale, shape = model.lambda_params(rss, w.T, 0, 10.0, 0.1)
+    assert shape == w.T / 2 + 0.1
+
+
+@pytest.mark.parametrize("dims,nb,K,P", [((3, 3, 1), 4, 3, 1), ((4, 4, 4), 6, 6, 3)])
+def test_precision_is_hessian_of_log_posterior(dims, nb, K, P):
+    """B~ and b_w are the Hessian and linear term of minus the log full conditional of W,
+    evaluated by brute force from the time series and the edge differences:
+        f(w) = 1/2 sum_n lambda_n ||y~_n - X~_n w_n||^2 + 1/2 sum_k alpha_k sum_edges (dw)^2
+             = f(0) - b_w'w + 1/2 w'B~w           (Eq. full cond W temporal, Eq. Wk prior)."""
+    w, lat = tiny(dims=dims, K=K, P=P, T=40, nb=nb)
+    rng = np.random.default_rng(3)
+    s = random_state(w, rng)
+    Bd, bw = model.w_blocks_direct(w.Y, w.X, s["A"], s["lam"])
+    B = model.precision(lat, Bd, s["alpha"])
+    b = model.kmajor(bw)
+    E = lat.edges()
+
+    def f(vec):
+        Wm = vec.reshape(K, w.N)
+        tot = 0.0
+        for n in range(w.N):
+            yt, Xt = model.whiten(w.Y[:, n], w.X, s["A"][:, n])
+            r = yt - Xt @ Wm[:, n]
+            tot += 0.5 * s["lam"][n] * r @ r
+        d = Wm[:, E[:, 0]] - Wm[:, E[:, 1]]
+        return tot + 0.5 * np.sum(s["alpha"][:, None] * d * d)
+
+    f0 = f(np.zeros(K * w.N))
+    for _ in range(3):
+        v = rng.standard_normal(K * w.N)
+        lhs = f(v) - f0
+        rhs = -b @ v + 0.5 * v @ (B @ v)
+        assert abs(lhs - rhs) <= 1e-10 * max(1.0, abs(lhs))
+    # symmetric, positive definite
+    Bdn = B.toarray()
+    assert np.array_equal(Bdn, Bdn.T)
+    assert np.linalg.eigvalsh(Bdn).min() > 0
+
+
+@pytest.mark.parametrize("dims,nb,K", [((3, 3, 1), 4, 3), ((4, 4, 4), 6, 6)])
+def test_exact_solve_matches_dense_inverse(dims, nb, K):
+    """Sparse-LU mean and draw vs the dense inverse on a 3x3 slice and a 4x4x4 cube."""
+    w, lat = tiny(dims=dims, K=K, P=1, T=40, nb=nb)
+    s = random_state(w, np.random.default_rng(4))
+    Bd, bw = model.w_blocks_direct(w.Y, w.X, s["A"], s["lam"], 1e-6)
+    x, mu = gibbs.draw_gmrf(lat, Bd, bw, s["alpha"], seed=11, counter=5, tag=philox.TAG_W)
+    B = model.precision(lat, Bd, s["alpha"]).toarray()
+    Binv = np.linalg.inv(B)
+    pert, _, _ = model.perturbation(lat, Bd, s["alpha"], 11, 5, philox.TAG_W)
+    mu_d = Binv @ model.kmajor(bw)
+    x_d = Binv @ (model.kmajor(bw) + pert)
+    assert np.linalg.norm(mu.ravel() - mu_d) <= 1e-12 * np.linalg.norm(mu_d)
+    assert np.linalg.norm(x.ravel() - x_d) <= 1e-12 * np.linalg.norm(x_d)
+
+
+@pytest.mark.parametrize("dims,nb,K", [((3, 3, 1), 4, 2), ((4, 3, 2), 6, 3)])
+def test_perturbation_covariance_is_precision(dims, nb, K):
+    """Algorithm 2 is exact because the perturbation M z has covariance M M' = B~:
+    sum_k alpha_k G'G (= alpha (x) D_w) plus H' L_data L_data' H (= the data blocks)."""
+    w, lat = tiny(dims=dims, K=K, P=1, T=30, nb=nb)
+    s = random_state(w, np.random.default_rng(5))
+    Bd, _ = model.w_blocks_direct(w.Y, w.X, s["A"], s["lam"])
+    M = model.perturbation_matrix(lat, Bd, s["alpha"]).toarray()
+    B = model.precision(lat, Bd, s["alpha"]).toarray()
+    assert np.max(np.abs(M @ M.T - B)) <= 1e-12 * np.max(np.abs(B))
+    # and perturbation() is that map applied to its own normals
+    pert, z1, z2 = model.perturbation(lat, Bd, s["alpha"], 3, 9, philox.TAG_W, 2)
+    z = np.concatenate([model.kmajor(z1), model.kmajor(z2)])
+    assert np.allclose(M @ z, pert, rtol=0, atol=1e-12 * np.abs(pert).max())
+
+
+def test_isolated_voxels_reduce_to_least_squares():
+    """Voxels with no neighbours decouple: the conditional mean is per-voxel GLS, i.e. the
+    least-squares fit of the whitened series (numpy lstsq), whatever alpha is."""
+    mask = (np.indices((3, 3, 3)).sum(axis=0) % 2).astype(np.uint8)
+    w, lat = tiny(dims=(3, 3, 3), K=3, P=2, T=40, nb=6, mask=mask)
+    s = random_state(w, np.random.default_rng(6))
+    Bd, bw = model.w_blocks_direct(w.Y, w.X, s["A"], s["lam"])
+    _, mu = gibbs.draw_gmrf(lat, Bd, bw, np.array([5.0, 0.1, 100.0]), 1, 1, philox.TAG_W)
+    for n in range(w.N):
+        yt, Xt = model.whiten(w.Y[:, n], w.X, s["A"][:, n])
+        ref = np.linalg.lstsq(Xt, yt, rcond=None)[0]
+        assert np.allclose(mu[:, n], ref, rtol=1e-10, atol=1e-12)
+
+
+def test_large_alpha_makes_coefficients_constant():
+    """alpha -> infinity: W_k is constant over the connected mask (the UGL penalises any
+    difference between neighbours), and equals the pooled GLS estimate."""
+    w, lat = tiny(dims=(4, 4, 1), K=2, P=0, T=30, nb=4)
+    lam = np.ones(w.N)
+    Bd, bw = model.w_blocks_direct(w.Y, w.X, np.zeros((0, w.N)), lam)
+    _, mu = gibbs.draw_gmrf(lat, Bd, bw, np.array([1e9, 1e9]), 1, 1, philox.TAG_W)
+    pooled = np.linalg.solve(Bd.sum(axis=0), bw.sum(axis=0))
+    assert np.allclose(mu, pooled[:, None], rtol=1e-5, atol=1e-6)
+
+
+def test_monte_carlo_moments_of_draws():
+    """Draws w = B~^-1 (b_w + M z) with Philox normals: sample mean -> B~^-1 b_w and sample
+    covariance -> B~^-1 within 5 standard errors (3x3 slice, K = 2)."""
+    w, lat = tiny(dims=(3, 3, 1), K=2, P=0, T=30, nb=4)
+    lam = np.full(w.N, 0.01)
+    Bd, bw = model.w_blocks_direct(w.Y, w.X, np.zeros((0, w.N)), lam)
+    alpha = np.array([0.7, 2.0])
+    B = model.precision(lat, Bd, alpha).toarray()
+    Binv = np.linalg.inv(B)
+    M = model.perturbation_matrix(lat, Bd, alpha).toarray()
+    n_draw = 20000
+    E = lat.edges()
+    sites_e = lat.lin[E[:, 0]] * 4 + E[:, 2]
+    # normals for many draw counters at once: draw r uses counter r
+    cnt = np.arange(n_draw)[None, :]
+    def lanes(sites):
+        out = []
+        for j in range(1):
+            z0, z1 = philox.normal_pair(philox.philox4x32_10(
+                np.asarray(sites, np.uint64)[:, None], j, cnt, philox.c3_of(philox.TAG_W, 0), 17, 0))
+            out += [z0, z1]
+        return out                  # lane k -> (n_sites, n_draw)
+    z1 = lanes(sites_e)
+    z2 = lanes(lat.lin * 4 + 3)
+    Z = np.concatenate([z1[0], z1[1], z2[0], z2[1]], axis=0)   # regressor-major blocks
+    X = Binv @ (model.kmajor(bw)[:, None] + M @ Z)
+    mean = X.mean(axis=1)
+    mu = Binv @ model.kmajor(bw)
+    sd = np.sqrt(np.diag(Binv))
+    assert np.all(np.abs(mean - mu) < 5 * sd / np.sqrt(n_draw))
+    C = np.cov(X)
+    se = np.sqrt((Binv ** 2 + np.outer(np.diag(Binv), np.diag(Binv))) / n_draw)
+    assert np.all(np.abs(C - Binv) < 5 * se + 1e-15)
+
+
+def test_quad_forms_edges_equal_laplacian():
+    w, lat = tiny(dims=(5, 4, 3), K=3, P=0, T=10, nb=6)
+    V = np.random.default_rng(7).standard_normal((3, w.N))
+    q1 = model.quad_forms_edges(lat, V)
+    q2 = model.quad_forms_laplacian(lat, V)
+    assert np.allclose(q1, q2, rtol=1e-13)
+
+
+def test_logdet_and_slq():
+    """log det from LU = dense Cholesky = sum of log eigenvalues; Lanczos quadrature of
+    z' log(B) z is exact at m = n; Hutchinson mean within 4 sigma of the exact log det."""
+    w, lat = tiny(dims=(4, 3, 2), K=2, P=1, T=30, nb=6)
+    s = random_state(w, np.random.default_rng(8))
+    Bd, _ = model.w_blocks_direct(w.Y, w.X, s["A"], s["lam"])
+    B = model.precision(lat, Bd, s["alpha"])
+    Bd_ = B.toarray()
+    ev = np.linalg.eigvalsh(Bd_)
+    ld = np.sum(np.log(ev))
+    assert abs(linalg.logdet_sparse(B) - ld) <= 1e-10 * abs(ld)
+    assert abs(linalg.logdet_dense(B) - ld) <= 1e-10 * abs(ld)
+    n = Bd_.shape[0]
+    Z = philox.rademacher(3, np.arange(n), 64, 0, philox.TAG_PROBE, 0)   # (n, 64)
+    exact = linalg.logm_quadform_dense(Bd_, Z)
+    z = Z[:, 0]
+    v = linalg.slq_quadform(lambda x: B @ x, z, n)
+    assert abs(v - exact[0]) <= 1e-8 * abs(exact[0])
+    Lg = np.linalg.eigh(Bd_)
+    logB = Lg[1] @ np.diag(np.log(Lg[0])) @ Lg[1].T
+    sigma = np.sqrt(2 * (np.sum(logB ** 2) - np.sum(np.diag(logB) ** 2)) / Z.shape[1])
+    assert abs(exact.mean() - ld) < 4 * sigma
