@@ -1,0 +1,204 @@
+/*
+ * bfmri -- GB300 (sm_103a) sampler for the spatial Bayesian fMRI GLM of
+ * Siden, Eklund, Bolin & Villani, "Fast Bayesian whole-brain fMRI analysis with spatial 3D
+ * priors" (the "paper" below).
+ *
+ * Model (Section 2; Appendix A, temporal noise model): Y = X W + E for T time points and N
+ * in-mask voxels, AR(P) noise per voxel with coefficients A (P x N) and innovation
+ * precisions lambda (N), priors W_k ~ N(0, (alpha_k D_w)^-1) and A_p ~ N(0, (beta_p D_a)^-1)
+ * with D_w = D_a the unweighted graph Laplacian (UGL) of the in-mask voxel lattice, Gamma
+ * hyperpriors on lambda, alpha, beta.
+ *
+ * Conventions for every call:
+ *  - Every function returns a bfmri_status: BFMRI_OK (0) or a negative error code; no C++
+ *    exception crosses this boundary. bfmri_last_error() gives a message.
+ *  - Matrices indexed by voxel use the mask's compact raster order (x fastest, then y, then
+ *    z), independent of the device layout. W is K x N row-major (the paper's W), A is P x N
+ *    row-major, lambda is N, alpha is K, beta is P. All FP64.
+ *  - Unless stated otherwise, pointer arguments are HOST pointers; the library copies them.
+ *    Outputs named *_out may be NULL (nothing is copied back).
+ *  - A handle is not thread-safe: serialise calls on one handle. All device work of a handle
+ *    runs on the CUDA stream given in its options, in issue order.
+ *  - Device memory is obtained through the allocator callbacks in the options (the Python
+ *    binding routes them to PyTorch's caching allocator); with NULL callbacks the library
+ *    calls cudaMalloc / cudaFree itself.
+ */
+#ifndef BFMRI_H
+#define BFMRI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int bfmri_status;
+
+#define BFMRI_OK                 0
+#define BFMRI_ERR_INVALID_ARG   -1  /* bad size, NULL pointer, non-finite input, bad option */
+#define BFMRI_ERR_OOM           -2  /* the allocator returned NULL */
+#define BFMRI_ERR_NOT_SPD       -3  /* a per-voxel block failed its Cholesky factorisation */
+#define BFMRI_ERR_NOT_CONVERGED -4  /* PCG hit max_iter; the last iterate is kept */
+#define BFMRI_ERR_TIMEOUT       -5  /* a device-side grid barrier waited past its limit */
+#define BFMRI_ERR_CUDA          -6  /* a CUDA runtime call failed */
+#define BFMRI_ERR_INTERNAL      -7
+#define BFMRI_ERR_STATE         -8  /* call out of order, e.g. sampling before statistics */
+
+/* Voxel lattice: nx * ny * nz sites; neighbourhood 6 (3D: +-x, +-y, +-z) or 4 (slice-wise
+ * 2D: +-x, +-y only). The UGL prior of Section 2 links in-mask face neighbours. */
+typedef struct {
+  int nx, ny, nz;
+  int neighbourhood;
+} bfmri_lattice;
+
+#define BFMRI_F32 0
+#define BFMRI_F64 1
+
+#define BFMRI_PRECOND_NONE         0
+#define BFMRI_PRECOND_BLOCK_JACOBI 1  /* per-voxel (block + alpha * degree) Cholesky */
+
+#define BFMRI_PREC_FP64  0  /* FP64 PCG */
+#define BFMRI_PREC_MIXED 1  /* FP32 inner PCG inside an FP64 iterative-refinement loop */
+
+#define BFMRI_AR_SPATIAL     0  /* A_p ~ N(0, (beta_p D_a)^-1), D_a = D_w (paper's model) */
+#define BFMRI_AR_INDEPENDENT 1  /* no spatial prior on A: per-voxel AR draws, beta unused */
+
+#define BFMRI_Y_MASKED  0  /* Y is T x N, columns = in-mask voxels in compact order */
+#define BFMRI_Y_LATTICE 1  /* Y is T x (nx ny nz), columns = all lattice sites */
+
+typedef void* (*bfmri_alloc_fn)(size_t bytes, void* ctx);
+typedef void (*bfmri_free_fn)(void* ptr, void* ctx);
+
+typedef struct {
+  /* Gamma hyperpriors Ga(scale, shape) of Section 2: q1, q2 (alpha), u1, u2 (lambda),
+   * r1, r2 (beta). Defaults 10, 0.1, 10, 0.1, 10000, 0.1. */
+  double q1, q2, u1, u2, r1, r2;
+  double eps;          /* ridge added to every per-voxel data block of W (default 0) */
+  double delta;        /* PCG stop: true relative residual ||b - B x|| / ||b|| <= delta */
+  int max_iter;        /* PCG iteration cap per solve (default 2000) */
+  int precond;         /* BFMRI_PRECOND_* (default block-Jacobi) */
+  int precision;       /* BFMRI_PREC_* (default FP64) */
+  int ar_prior;        /* BFMRI_AR_* (default spatial) */
+  int y_layout;        /* BFMRI_Y_* (default masked) */
+  double inner_tol;    /* mixed precision: relative tolerance of each FP32 inner solve */
+  uint64_t seed;       /* Philox key */
+  uint32_t stream_id;  /* 24-bit chain id folded into every Philox counter */
+  void* cuda_stream;   /* cudaStream_t for all device work (NULL = legacy default stream) */
+  bfmri_alloc_fn dev_alloc;  /* device allocator (NULL: cudaMalloc) */
+  bfmri_free_fn dev_free;
+  void* alloc_ctx;
+  double barrier_timeout_s;  /* limit of each device-side grid-barrier wait (default 2 s) */
+  int debug_skip_block;      /* test hook: this CTA never arrives at the first barrier of the
+                                next solve (forces BFMRI_ERR_TIMEOUT); -1 = off (default) */
+} bfmri_options;
+
+/* Fills *opt with the defaults listed above. */
+void bfmri_default_options(bfmri_options* opt);
+
+typedef struct bfmri_handle bfmri_handle;
+
+typedef struct {
+  int iterations;        /* PCG iterations (mixed: total inner FP32 iterations) */
+  int refinements;       /* mixed: FP64 outer refinement steps; FP64: true-residual restarts */
+  double rel_residual;   /* final true relative residual in FP64 */
+  double rel_residual0;  /* relative residual of the starting value */
+} bfmri_solve_info;
+
+typedef struct {
+  int sweeps;
+  long long pcg_iterations_W;  /* summed over sweeps */
+  long long pcg_iterations_A;
+  double last_rel_residual_W;
+  long long gamma_exhausted;   /* Marsaglia-Tsang draws that used all attempts */
+} bfmri_sweep_info;
+
+/* Creates a handle for one subject (paper Section 2, Eq. Pennymodel; Appendix A).
+ *  lat, mask: lattice and nx*ny*nz mask bytes (x fastest; nonzero = in mask).
+ *  X: T x K design, column-major FP64 (X[t + T k]).
+ *  Y: T x N (or T x nx ny nz with y_layout = BFMRI_Y_LATTICE) row-major, element (t, n) at
+ *     Y[t * N + n], FP32 or FP64 per y_dtype. Copied to the device; the host array is not
+ *     referenced after return.
+ *  K in [1, 12], P in [0, 4], T > P + K.
+ * The state starts at the prior means (Appendix C, trick 2): W = 0, A = 0, lambda = u1 u2,
+ * alpha = q1 q2, beta = r1 r2. Errors: INVALID_ARG (sizes, empty mask, non-finite X or Y),
+ * OOM, CUDA. On error *out is NULL; the message is available from bfmri_last_error(NULL). */
+bfmri_status bfmri_create(const bfmri_lattice* lat, const uint8_t* mask, const double* X,
+                          const void* Y, int y_dtype, int T, int K, int P,
+                          const bfmri_options* opt, bfmri_handle** out);
+
+/* Releases all device memory of the handle (after synchronising its stream). NULL is a no-op. */
+bfmri_status bfmri_destroy(bfmri_handle* h);
+
+/* Message of the last failed call on h (handle-owned), or of the last failed bfmri_create
+ * when h is NULL (process-wide). Never NULL. */
+const char* bfmri_last_error(const bfmri_handle* h);
+
+/* Number of in-mask voxels N, and the problem sizes. */
+int bfmri_num_voxels(const bfmri_handle* h);
+bfmri_status bfmri_sizes(const bfmri_handle* h, int* N, int* T, int* K, int* P);
+
+/* Sufficient statistics (Appendix A, Eq. log-like: Y enters only through lagged
+ * cross-products, "pre-computed outside the Gibbs algorithm"). For every voxel and lags
+ * p, q in 0..P, summed over t = P+1..T:
+ *   Syy[p][q]    = sum_t y_{t-p} y_{t-q}              (p <= q stored)
+ *   Sxy[p][q][k] = sum_t y_{t-p} x_{t-q,k}
+ * The device copy of Y is released afterwards. Must precede every sampling call. */
+bfmri_status bfmri_precompute_stats(bfmri_handle* h);
+
+/* Copies the statistics to the host: out is N x S row-major with S = (P+1)(P+2)/2 + K (P+1)^2,
+ * per voxel first Syy (p <= q, row-major over p), then Sxy in (p, q, k) order. */
+bfmri_status bfmri_get_stats(bfmri_handle* h, double* out);
+
+/* Sets / reads the chain state (any pointer may be NULL to leave that part unchanged / not
+ * read). Values are validated: lambda, alpha, beta > 0 and finite. */
+bfmri_status bfmri_set_state(bfmri_handle* h, const double* W, const double* A,
+                             const double* lambda, const double* alpha, const double* beta);
+bfmri_status bfmri_get_state(bfmri_handle* h, double* W, double* A, double* lambda,
+                             double* alpha, double* beta);
+
+/* One draw of W from its full conditional (Eq. full cond W temporal) by Algorithm 2:
+ * b = b_w + sum_k sqrt(alpha_k) G_w' z1_k + H_w' L_data H_w z2 (normals from Philox with
+ * draw counter `counter`), then PCG on B~ w = b from the current W (warm start) until the
+ * true relative residual is <= delta. The draw replaces W in the state; W_out (K x N) may be
+ * NULL. info may be NULL; when given, the call waits for the device.
+ * Errors: STATE (no statistics), NOT_SPD, NOT_CONVERGED, TIMEOUT, CUDA. */
+bfmri_status bfmri_sample_W(bfmri_handle* h, uint64_t counter, double* W_out,
+                            bfmri_solve_info* info);
+
+/* One draw of A from its full conditional (Eq. fullcondTempA) given the current W, lambda,
+ * beta: spatial prior -> the same perturbation + PCG with P in place of K and beta in place
+ * of alpha; independent prior -> per-voxel P x P Cholesky draws. No-op when P = 0. */
+bfmri_status bfmri_sample_A(bfmri_handle* h, uint64_t counter, double* A_out,
+                            bfmri_solve_info* info);
+
+/* lambda_n ~ Ga(1 / (1/u1 + RSS_n / 2), (T - P)/2 + u2) (Eq. fullcondTemplambda). */
+bfmri_status bfmri_sample_lambda(bfmri_handle* h, uint64_t counter, double* lambda_out);
+
+/* alpha_k ~ Ga(1 / (W_k D_w W_k' / 2 + 1/q1), N/2 + q2) (Eq. fullcondTempa). */
+bfmri_status bfmri_sample_alpha(bfmri_handle* h, uint64_t counter, double* alpha_out);
+
+/* beta_p ~ Ga(1 / (A_p D_a A_p' / 2 + 1/r1), N/2 + r2) (Eq. fullcondTempbeta); spatial AR
+ * prior only (a no-op otherwise). */
+bfmri_status bfmri_sample_beta(bfmri_handle* h, uint64_t counter, double* beta_out);
+
+/* n_sweeps Gibbs sweeps (Section 3.2) W -> A -> lambda -> alpha -> beta; sweep s uses draw
+ * counter first_counter + s. No host synchronisation inside; info (may be NULL) waits. */
+bfmri_status bfmri_gibbs_sweep(bfmri_handle* h, int n_sweeps, uint64_t first_counter,
+                               bfmri_sweep_info* info);
+
+/* Inspection of the W or A system (which = 0: W with K, 1: A with P) at the current state.
+ *  bfmri_apply_precision: y = B~ x (x, y dim x N row-major) with B~ the full-conditional
+ *    precision (block diagonal data term + scale (x) D).
+ *  bfmri_build_system: per-voxel data blocks (N x dim x dim, full symmetric), the mean
+ *    right-hand side b_w (dim x N) and the perturbed right-hand side b of Algorithm 2
+ *    for draw counter `counter` (dim x N). Any output may be NULL. */
+bfmri_status bfmri_apply_precision(bfmri_handle* h, int which, const double* x, double* y);
+bfmri_status bfmri_build_system(bfmri_handle* h, int which, uint64_t counter, double* blocks,
+                                double* b_mean, double* b_pert);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BFMRI_H */

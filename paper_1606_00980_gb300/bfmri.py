@@ -1,0 +1,308 @@
+"""Python binding of the bfmri C ABI (include/bfmri.h): argument marshalling only.
+
+Every step of the sampler runs in the CUDA library ``_lib/libbfmri.so``; this module only
+converts numpy arrays to pointers, routes the library's device allocations to PyTorch's
+caching allocator, and passes PyTorch's current CUDA stream. There is no CPU fallback:
+if the library is missing, ``load_library`` raises.
+
+The function names are those of the C ABI; ``Model`` is a small convenience wrapper that
+owns a handle.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libbfmri.so")
+
+BFMRI_OK = 0
+STATUS_NAMES = {0: "OK", -1: "INVALID_ARG", -2: "OOM", -3: "NOT_SPD", -4: "NOT_CONVERGED",
+                -5: "TIMEOUT", -6: "CUDA", -7: "INTERNAL", -8: "STATE"}
+BFMRI_F32, BFMRI_F64 = 0, 1
+PRECOND_NONE, PRECOND_BLOCK_JACOBI = 0, 1
+PREC_FP64, PREC_MIXED = 0, 1
+AR_SPATIAL, AR_INDEPENDENT = 0, 1
+Y_MASKED, Y_LATTICE = 0, 1
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
+class bfmri_lattice(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("neighbourhood", C.c_int)]
+
+
+class bfmri_options(C.Structure):
+    _fields_ = [("q1", C.c_double), ("q2", C.c_double), ("u1", C.c_double), ("u2", C.c_double),
+                ("r1", C.c_double), ("r2", C.c_double), ("eps", C.c_double),
+                ("delta", C.c_double), ("max_iter", C.c_int), ("precond", C.c_int),
+                ("precision", C.c_int), ("ar_prior", C.c_int), ("y_layout", C.c_int),
+                ("inner_tol", C.c_double), ("seed", C.c_uint64), ("stream_id", C.c_uint32),
+                ("cuda_stream", C.c_void_p), ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN),
+                ("alloc_ctx", C.c_void_p), ("barrier_timeout_s", C.c_double),
+                ("debug_skip_block", C.c_int)]
+
+
+class bfmri_solve_info(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("refinements", C.c_int),
+                ("rel_residual", C.c_double), ("rel_residual0", C.c_double)]
+
+
+class bfmri_sweep_info(C.Structure):
+    _fields_ = [("sweeps", C.c_int), ("pcg_iterations_W", C.c_longlong),
+                ("pcg_iterations_A", C.c_longlong), ("last_rel_residual_W", C.c_double),
+                ("gamma_exhausted", C.c_longlong)]
+
+
+_P = C.POINTER
+_dp = _P(C.c_double)
+_vp = C.c_void_p
+_h = C.c_void_p
+
+# (name, restype, argtypes): the ABI as declared in include/bfmri.h
+SIGNATURES = [
+    ("bfmri_default_options", None, [_P(bfmri_options)]),
+    ("bfmri_create", C.c_int, [_P(bfmri_lattice), _P(C.c_uint8), _dp, _vp, C.c_int, C.c_int,
+                               C.c_int, C.c_int, _P(bfmri_options), _P(_h)]),
+    ("bfmri_destroy", C.c_int, [_h]),
+    ("bfmri_last_error", C.c_char_p, [_h]),
+    ("bfmri_num_voxels", C.c_int, [_h]),
+    ("bfmri_sizes", C.c_int, [_h, _P(C.c_int), _P(C.c_int), _P(C.c_int), _P(C.c_int)]),
+    ("bfmri_precompute_stats", C.c_int, [_h]),
+    ("bfmri_get_stats", C.c_int, [_h, _dp]),
+    ("bfmri_set_state", C.c_int, [_h, _dp, _dp, _dp, _dp, _dp]),
+    ("bfmri_get_state", C.c_int, [_h, _dp, _dp, _dp, _dp, _dp]),
+    ("bfmri_sample_W", C.c_int, [_h, C.c_uint64, _dp, _P(bfmri_solve_info)]),
+    ("bfmri_sample_A", C.c_int, [_h, C.c_uint64, _dp, _P(bfmri_solve_info)]),
+    ("bfmri_sample_lambda", C.c_int, [_h, C.c_uint64, _dp]),
+    ("bfmri_sample_alpha", C.c_int, [_h, C.c_uint64, _dp]),
+    ("bfmri_sample_beta", C.c_int, [_h, C.c_uint64, _dp]),
+    ("bfmri_gibbs_sweep", C.c_int, [_h, C.c_int, C.c_uint64, _P(bfmri_sweep_info)]),
+    ("bfmri_apply_precision", C.c_int, [_h, C.c_int, _dp, _dp]),
+    ("bfmri_build_system", C.c_int, [_h, C.c_int, C.c_uint64, _dp, _dp, _dp]),
+]
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Loads libbfmri.so (raises if it has not been built: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"bfmri CUDA library not found at {path}; build it first "
+                           "(python -c 'import __graft_entry__ as g; g.build()')")
+    lib = C.CDLL(path)
+    for name, res, args in SIGNATURES:
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+class BfmriError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+def _check(status, handle=None):
+    if status != BFMRI_OK:
+        msg = load_library().bfmri_last_error(handle)
+        raise BfmriError(status, msg.decode() if msg else "")
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    return a.ctypes.data_as(_dp)
+
+
+def _f64(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if shape is not None and a.shape != tuple(shape):
+        a = a.reshape(shape)
+    return a
+
+
+class TorchDeviceMemory:
+    """Device allocator callbacks backed by PyTorch's caching allocator."""
+
+    def __init__(self):
+        import torch
+        self._torch = torch
+        self._live = {}
+        self.alloc = ALLOC_FN(self._alloc)
+        self.free = FREE_FN(self._free)
+
+    def _alloc(self, nbytes, ctx):
+        try:
+            t = self._torch.empty(int(nbytes), dtype=self._torch.uint8, device="cuda")
+        except Exception:   # OOM -> NULL, the library reports BFMRI_ERR_OOM
+            return None
+        p = t.data_ptr()
+        self._live[p] = t
+        return p
+
+    def _free(self, ptr, ctx):
+        self._live.pop(ptr, None)
+
+    @property
+    def bytes_held(self):
+        return sum(t.numel() for t in self._live.values())
+
+
+def bfmri_default_options():
+    o = bfmri_options()
+    load_library().bfmri_default_options(C.byref(o))
+    return o
+
+
+def bfmri_create(lattice, mask, X, Y, K, P, opts=None, torch_memory=True):
+    """Returns (handle, keepalive). lattice = (nx, ny, nz, neighbourhood); mask is an
+    (nz, ny, nx) uint8 array; X is T x K; Y is T x N (float32 or float64)."""
+    lib = load_library()
+    nx, ny, nz, nb = lattice
+    lat = bfmri_lattice(nx, ny, nz, nb)
+    mask = np.ascontiguousarray(mask, dtype=np.uint8).reshape(-1)
+    X = np.asfortranarray(np.asarray(X, dtype=np.float64))
+    T = X.shape[0]
+    Y = np.ascontiguousarray(Y)
+    if Y.dtype == np.float64:
+        ydt = BFMRI_F64
+    elif Y.dtype == np.float32:
+        ydt = BFMRI_F32
+    else:
+        Y = Y.astype(np.float64)
+        ydt = BFMRI_F64
+    if opts is None:
+        opts = bfmri_default_options()
+    mem = None
+    if torch_memory:
+        import torch
+        mem = TorchDeviceMemory()
+        opts.dev_alloc = mem.alloc
+        opts.dev_free = mem.free
+        if opts.cuda_stream is None:
+            opts.cuda_stream = torch.cuda.current_stream().cuda_stream
+    h = _h()
+    st = lib.bfmri_create(C.byref(lat), mask.ctypes.data_as(_P(C.c_uint8)),
+                          X.ctypes.data_as(_dp), Y.ctypes.data_as(_vp), ydt, T, K, P,
+                          C.byref(opts), C.byref(h))
+    _check(st, None)
+    return h, (mem, opts)
+
+
+def bfmri_destroy(h):
+    _check(load_library().bfmri_destroy(h))
+
+
+class Model:
+    """Owns one handle: a subject's data, its statistics and its chain state on the GPU."""
+
+    def __init__(self, lattice, mask, X, Y, K, P, opts=None, **opt_fields):
+        o = opts if opts is not None else bfmri_default_options()
+        for k, v in opt_fields.items():
+            setattr(o, k, v)
+        self.handle, self._keep = bfmri_create(lattice, mask, X, Y, K, P, o)
+        self.lib = load_library()
+        N, T, Kc, Pc = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        _check(self.lib.bfmri_sizes(self.handle, C.byref(N), C.byref(T), C.byref(Kc), C.byref(Pc)), self.handle)
+        self.N, self.T, self.K, self.P = N.value, T.value, Kc.value, Pc.value
+
+    @classmethod
+    def from_workload(cls, w, **opt_fields):
+        nx, ny, nz = w.dims
+        opt_fields.setdefault("eps", w.eps)
+        opt_fields.setdefault("delta", w.delta)
+        return cls((nx, ny, nz, w.neighbourhood), w.mask, w.X, w.Y, w.K, w.P, **opt_fields)
+
+    def close(self):
+        if self.handle:
+            bfmri_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _c(self, st):
+        _check(st, self.handle)
+
+    def precompute_stats(self):
+        self._c(self.lib.bfmri_precompute_stats(self.handle))
+
+    def get_stats(self):
+        from_s = (self.P + 1) * (self.P + 2) // 2 + self.K * (self.P + 1) ** 2
+        out = np.empty((self.N, from_s))
+        self._c(self.lib.bfmri_get_stats(self.handle, _ptr(out)))
+        return out
+
+    def set_state(self, W=None, A=None, lam=None, alpha=None, beta=None):
+        arrs = [None if v is None else _f64(v) for v in (W, A, lam, alpha, beta)]
+        self._c(self.lib.bfmri_set_state(self.handle, *[_ptr(a) for a in arrs]))
+
+    def get_state(self):
+        W = np.empty((self.K, self.N))
+        A = np.empty((self.P, self.N))
+        lam = np.empty(self.N)
+        alpha = np.empty(self.K)
+        beta = np.empty(max(self.P, 1))
+        self._c(self.lib.bfmri_get_state(self.handle, _ptr(W), _ptr(A), _ptr(lam), _ptr(alpha), _ptr(beta)))
+        return dict(W=W, A=A, lam=lam, alpha=alpha, beta=beta[:self.P])
+
+    def sample_W(self, counter, out=True):
+        W = np.empty((self.K, self.N)) if out else None
+        info = bfmri_solve_info()
+        self._c(self.lib.bfmri_sample_W(self.handle, counter, _ptr(W), C.byref(info)))
+        return W, info
+
+    def sample_A(self, counter, out=True):
+        A = np.empty((self.P, self.N)) if out else None
+        info = bfmri_solve_info()
+        self._c(self.lib.bfmri_sample_A(self.handle, counter, _ptr(A), C.byref(info)))
+        return A, info
+
+    def sample_lambda(self, counter):
+        lam = np.empty(self.N)
+        self._c(self.lib.bfmri_sample_lambda(self.handle, counter, _ptr(lam)))
+        return lam
+
+    def sample_alpha(self, counter):
+        a = np.empty(self.K)
+        self._c(self.lib.bfmri_sample_alpha(self.handle, counter, _ptr(a)))
+        return a
+
+    def sample_beta(self, counter):
+        b = np.empty(max(self.P, 1))
+        self._c(self.lib.bfmri_sample_beta(self.handle, counter, _ptr(b)))
+        return b[:self.P]
+
+    def gibbs_sweep(self, n_sweeps, first_counter=0, info=True):
+        inf = bfmri_sweep_info()
+        self._c(self.lib.bfmri_gibbs_sweep(self.handle, n_sweeps, first_counter,
+                                           C.byref(inf) if info else None))
+        return inf
+
+    def apply_precision(self, which, x):
+        D = self.K if which == 0 else self.P
+        x = _f64(x, (D, self.N))
+        y = np.empty((D, self.N))
+        self._c(self.lib.bfmri_apply_precision(self.handle, which, _ptr(x), _ptr(y)))
+        return y
+
+    def build_system(self, which, counter):
+        D = self.K if which == 0 else self.P
+        blocks = np.empty((self.N, D, D))
+        bmean = np.empty((D, self.N))
+        bpert = np.empty((D, self.N))
+        self._c(self.lib.bfmri_build_system(self.handle, which, counter, _ptr(blocks),
+                                            _ptr(bmean), _ptr(bpert)))
+        return blocks, bmean, bpert

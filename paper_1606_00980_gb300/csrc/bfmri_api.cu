@@ -1,0 +1,781 @@
+// C ABI of the bfmri library (include/bfmri.h): handle life cycle, state transfer, and the
+// host-side orchestration of one Gibbs sweep (Section 3.2) as a fixed sequence of kernel
+// launches on the handle's stream, with no host synchronisation inside a sweep.
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/bfmri.h"
+#include "model.cuh"
+#include "pcg.cuh"
+
+using namespace bfmri;
+
+namespace {
+std::mutex g_err_mu;
+std::string g_create_err = "no error";
+}  // namespace
+
+struct bfmri_handle {
+  int nx = 0, ny = 0, nz = 0, nbh = 6, ndir = 6;
+  int N = 0, T = 0, K = 0, P = 0, D = 0;
+  size_t ld = 0;
+  bfmri_options opt{};
+  cudaStream_t stream = nullptr;
+  std::string err = "no error";
+  std::vector<void*> allocs;
+  int* d_nbr = nullptr;
+  int* d_lin = nullptr;
+  void* d_Y = nullptr;
+  int y_f64 = 1;
+  double* d_X = nullptr;
+  double* d_stats = nullptr;
+  double* d_Sxx = nullptr;
+  double *d_W = nullptr, *d_A = nullptr, *d_lam = nullptr, *d_alpha = nullptr, *d_beta = nullptr;
+  double* d_G = nullptr;
+  double *d_blocks = nullptr, *d_mfac = nullptr, *d_rhs = nullptr, *d_bmean = nullptr;
+  double *d_r = nullptr, *d_z = nullptr, *d_q = nullptr, *d_p0 = nullptr, *d_p1 = nullptr;
+  double *d_part = nullptr, *d_hpart = nullptr;
+  unsigned int* d_bar = nullptr;
+  int* d_err = nullptr;
+  PcgCtrl* d_ctrl = nullptr;  // [0] W solves, [1] A solves
+  int* d_flags = nullptr;     // [0] bad voxel (min index), [1] Gamma draws out of attempts
+  bool stats_ready = false;
+  int part_rows = 0;
+  std::vector<double> Sxx;
+  int stride[3] = {1, 1, 1};
+};
+
+namespace {
+
+bfmri_status fail(bfmri_handle* h, bfmri_status code, const std::string& msg) {
+  if (h) {
+    h->err = msg;
+  } else {
+    std::lock_guard<std::mutex> lk(g_err_mu);
+    g_create_err = msg;
+  }
+  return code;
+}
+
+bfmri_status cuda_fail(bfmri_handle* h, cudaError_t e, const char* where) {
+  return fail(h, BFMRI_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CU(h, call)                                    \
+  do {                                                 \
+    cudaError_t e_ = (call);                           \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
+  } while (0)
+
+void* dalloc(bfmri_handle* h, size_t bytes) {
+  if (bytes == 0) bytes = 256;
+  bytes = (bytes + 255) & ~size_t(255);
+  void* p = nullptr;
+  if (h->opt.dev_alloc) {
+    p = h->opt.dev_alloc(bytes, h->opt.alloc_ctx);
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    p = nullptr;
+  }
+  if (p) h->allocs.push_back(p);
+  return p;
+}
+
+void dfree(bfmri_handle* h, void* p) {
+  if (!p) return;
+  for (size_t i = 0; i < h->allocs.size(); ++i) {
+    if (h->allocs[i] == p) {
+      h->allocs.erase(h->allocs.begin() + i);
+      break;
+    }
+  }
+  if (h->opt.dev_alloc) {
+    if (h->opt.dev_free) h->opt.dev_free(p, h->opt.alloc_ctx);
+  } else {
+    cudaFree(p);
+  }
+}
+
+Geometry geom(const bfmri_handle* h) {
+  Geometry g;
+  g.N = h->N;
+  g.ld = h->ld;
+  g.ndir = h->ndir;
+  g.nbr = h->d_nbr;
+  g.lin = h->d_lin;
+  g.stride[0] = h->stride[0];
+  g.stride[1] = h->stride[1];
+  g.stride[2] = h->stride[2];
+  return g;
+}
+
+Rng rng_of(const bfmri_handle* h, uint64_t counter, uint32_t tag) {
+  Rng r;
+  r.k0 = (uint32_t)(h->opt.seed & 0xFFFFFFFFull);
+  r.k1 = (uint32_t)(h->opt.seed >> 32);
+  r.counter = (uint32_t)counter;
+  r.c3 = (tag << 24) | (h->opt.stream_id & 0xFFFFFFu);
+  return r;
+}
+
+// host (rows x N row-major) <-> device planes (rows x ld)
+bfmri_status to_dev(bfmri_handle* h, double* d, const double* src, int rows) {
+  if (rows == 0) return BFMRI_OK;
+  CU(h, cudaMemcpy2DAsync(d, h->ld * sizeof(double), src, (size_t)h->N * sizeof(double),
+                          (size_t)h->N * sizeof(double), rows, cudaMemcpyHostToDevice, h->stream));
+  return BFMRI_OK;
+}
+
+bfmri_status to_host(bfmri_handle* h, double* dst, const double* d, int rows) {
+  if (rows == 0) return BFMRI_OK;
+  CU(h, cudaMemcpy2DAsync(dst, (size_t)h->N * sizeof(double), d, h->ld * sizeof(double),
+                          (size_t)h->N * sizeof(double), rows, cudaMemcpyDeviceToHost, h->stream));
+  CU(h, cudaStreamSynchronize(h->stream));
+  return BFMRI_OK;
+}
+
+bool all_finite(const double* v, size_t n) {
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite(v[i])) return false;
+  return true;
+}
+
+bool all_positive(const double* v, size_t n) {
+  for (size_t i = 0; i < n; ++i)
+    if (!(v[i] > 0.0) || !std::isfinite(v[i])) return false;
+  return true;
+}
+
+// Clears the sticky device error words before a group of launches.
+bfmri_status begin_call(bfmri_handle* h) {
+  CU(h, cudaMemsetAsync(h->d_bar, 0, 2 * sizeof(unsigned int), h->stream));
+  CU(h, cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream));
+  CU(h, cudaMemsetAsync(h->d_ctrl, 0, 2 * sizeof(PcgCtrl), h->stream));
+  CU(h, cudaMemsetAsync(h->d_flags, 0x7f, sizeof(int), h->stream));
+  CU(h, cudaMemsetAsync(h->d_flags + 1, 0, 3 * sizeof(int), h->stream));
+  return BFMRI_OK;
+}
+
+// Reads the device error words after synchronising; maps them to a status.
+bfmri_status end_call(bfmri_handle* h, PcgCtrl* ctrl_out /* [2] or null */, int* exhausted) {
+  CU(h, cudaStreamSynchronize(h->stream));
+  PcgCtrl ctrl[2];
+  int flags[4], err = 0;
+  CU(h, cudaMemcpy(ctrl, h->d_ctrl, sizeof(ctrl), cudaMemcpyDeviceToHost));
+  CU(h, cudaMemcpy(flags, h->d_flags, sizeof(flags), cudaMemcpyDeviceToHost));
+  CU(h, cudaMemcpy(&err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (ctrl_out) {
+    ctrl_out[0] = ctrl[0];
+    ctrl_out[1] = ctrl[1];
+  }
+  if (exhausted) *exhausted = flags[1];
+  if (err == ERR_TIMEOUT_CODE)
+    return fail(h, BFMRI_ERR_TIMEOUT, "device grid barrier wait exceeded its time limit");
+  if (flags[0] != 0x7f7f7f7f)
+    return fail(h, BFMRI_ERR_NOT_SPD,
+                "per-voxel block not positive definite at voxel " + std::to_string(flags[0]));
+  for (int i = 0; i < 2; ++i) {
+    const int st = ctrl[i].status_any;
+    if (st == 4) return fail(h, BFMRI_ERR_NOT_CONVERGED, "PCG reached max_iter");
+    if (st == 3) return fail(h, BFMRI_ERR_NOT_SPD, "PCG breakdown (p'Bp <= 0)");
+    if (st == 7) return fail(h, BFMRI_ERR_INVALID_ARG, "non-finite value in PCG");
+  }
+  return BFMRI_OK;
+}
+
+bfmri_status run_pcg(bfmri_handle* h, int D, const double* scale, double* x, int which) {
+  PcgArgs a;
+  a.N = h->N;
+  a.ld = h->ld;
+  a.ndir = h->ndir;
+  a.nbr = h->d_nbr;
+  a.blocks = h->d_blocks;
+  a.mfac = h->opt.precond == BFMRI_PRECOND_BLOCK_JACOBI ? h->d_mfac : nullptr;
+  a.scale = scale;
+  a.b = h->d_rhs;
+  a.x = x;
+  a.r = h->d_r;
+  a.z = h->d_z;
+  a.q = h->d_q;
+  a.p0 = h->d_p0;
+  a.p1 = h->d_p1;
+  a.part = h->d_part;
+  a.bar.count = h->d_bar;
+  a.bar.gen = h->d_bar + 1;
+  a.bar.err = h->d_err;
+  a.bar.timeout_ns = (unsigned long long)(h->opt.barrier_timeout_s * 1e9);
+  a.ctrl = h->d_ctrl + which;
+  a.delta = h->opt.delta;
+  a.max_iter = h->opt.max_iter;
+  a.skip_block = h->opt.debug_skip_block;
+  a.max_grid = h->part_rows;
+  h->opt.debug_skip_block = -1;  // the hook fires once
+  int grid = 0;
+  cudaError_t e = launch_pcg(D, a, h->stream, &grid);
+  if (e != cudaSuccess) return cuda_fail(h, e, "launch_pcg");
+  return BFMRI_OK;
+}
+
+AssembleArgs assemble_args(bfmri_handle* h, const double* scale, uint64_t counter, uint32_t tag) {
+  AssembleArgs a;
+  memset(&a, 0, sizeof(a));
+  a.g = geom(h);
+  a.K = h->K;
+  a.P = h->P;
+  a.stats = h->d_stats;
+  a.Sxx = h->d_Sxx;
+  a.W = h->d_W;
+  a.A = h->d_A;
+  a.lam = h->d_lam;
+  a.scale = scale;
+  a.eps = h->opt.eps;
+  a.spatial = h->opt.ar_prior == BFMRI_AR_SPATIAL;
+  a.perturb = 1;
+  a.precond = h->opt.precond == BFMRI_PRECOND_BLOCK_JACOBI;
+  a.rng = rng_of(h, counter, tag);
+  a.blocks = h->d_blocks;
+  a.mfac = h->d_mfac;
+  a.rhs = h->d_rhs;
+  a.G = h->d_G;
+  a.bad_voxel = h->d_flags;
+  return a;
+}
+
+// --- the five steps of a sweep, enqueued without synchronisation ---
+bfmri_status enqueue_W(bfmri_handle* h, uint64_t counter) {
+  AssembleArgs a = assemble_args(h, h->d_alpha, counter, TAG_W);
+  cudaError_t e = launch_assemble_w(a, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "assemble_w");
+  return run_pcg(h, h->K, h->d_alpha, h->d_W, 0);
+}
+
+bfmri_status enqueue_A(bfmri_handle* h, uint64_t counter) {
+  AssembleArgs a = assemble_args(h, h->d_beta, counter, TAG_A);
+  const bool spatial = h->opt.ar_prior == BFMRI_AR_SPATIAL;
+  if (h->P == 0) {
+    a.g_only = 1;
+  } else if (!spatial) {
+    a.rhs = nullptr;
+    a.x_direct = h->d_A;
+    a.precond = 0;
+  }
+  cudaError_t e = launch_assemble_a(a, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "assemble_a");
+  if (h->P > 0 && spatial) return run_pcg(h, h->P, h->d_beta, h->d_A, 1);
+  return BFMRI_OK;
+}
+
+bfmri_status enqueue_gram(bfmri_handle* h) {
+  AssembleArgs a = assemble_args(h, h->d_beta, 0, TAG_A);
+  a.g_only = 1;
+  cudaError_t e = launch_assemble_a(a, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "assemble_a(gram)");
+  return BFMRI_OK;
+}
+
+bfmri_status enqueue_lambda(bfmri_handle* h, uint64_t counter) {
+  LambdaArgs a;
+  a.g = geom(h);
+  a.P = h->P;
+  a.T = h->T;
+  a.u1 = h->opt.u1;
+  a.u2 = h->opt.u2;
+  a.G = h->d_G;
+  a.A = h->d_A;
+  a.lam = h->d_lam;
+  a.rng = rng_of(h, counter, TAG_LAMBDA);
+  a.exhausted = h->d_flags + 1;
+  cudaError_t e = launch_lambda(a, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "lambda");
+  return BFMRI_OK;
+}
+
+bfmri_status enqueue_hyper(bfmri_handle* h, uint64_t counter, bool beta) {
+  HyperArgs a;
+  a.g = geom(h);
+  a.D = beta ? h->P : h->K;
+  a.V = beta ? h->d_A : h->d_W;
+  a.part = h->d_hpart;
+  a.prior1 = beta ? h->opt.r1 : h->opt.q1;
+  a.prior2 = beta ? h->opt.r2 : h->opt.q2;
+  a.out = beta ? h->d_beta : h->d_alpha;
+  a.Q_out = nullptr;
+  a.rng = rng_of(h, counter, beta ? TAG_BETA : TAG_ALPHA);
+  a.exhausted = h->d_flags + 1;
+  cudaError_t e = launch_hyper(a, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "hyper");
+  return BFMRI_OK;
+}
+
+bfmri_status require_stats(bfmri_handle* h) {
+  if (!h) return BFMRI_ERR_INVALID_ARG;
+  if (!h->stats_ready) return fail(h, BFMRI_ERR_STATE, "bfmri_precompute_stats has not run");
+  return BFMRI_OK;
+}
+
+void fill_info(bfmri_solve_info* info, const PcgCtrl& c) {
+  if (!info) return;
+  info->iterations = c.iterations;
+  info->refinements = c.restarts;
+  info->rel_residual = c.rel_res;
+  info->rel_residual0 = c.rel_res0;
+}
+
+}  // namespace
+
+#define RET(x)                          \
+  do {                                  \
+    bfmri_status s_ = (x);              \
+    if (s_ != BFMRI_OK) return s_;      \
+  } while (0)
+
+extern "C" {
+
+void bfmri_default_options(bfmri_options* o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->q1 = 10.0;
+  o->q2 = 0.1;
+  o->u1 = 10.0;
+  o->u2 = 0.1;
+  o->r1 = 10000.0;
+  o->r2 = 0.1;
+  o->eps = 0.0;
+  o->delta = 1e-8;
+  o->max_iter = 2000;
+  o->precond = BFMRI_PRECOND_BLOCK_JACOBI;
+  o->precision = BFMRI_PREC_FP64;
+  o->ar_prior = BFMRI_AR_SPATIAL;
+  o->y_layout = BFMRI_Y_MASKED;
+  o->inner_tol = 1e-5;
+  o->seed = 0x5eed5eedULL;
+  o->stream_id = 0;
+  o->cuda_stream = nullptr;
+  o->barrier_timeout_s = 2.0;
+  o->debug_skip_block = -1;
+}
+
+const char* bfmri_last_error(const bfmri_handle* h) {
+  if (h) return h->err.c_str();
+  std::lock_guard<std::mutex> lk(g_err_mu);
+  static thread_local std::string copy;
+  copy = g_create_err;
+  return copy.c_str();
+}
+
+int bfmri_num_voxels(const bfmri_handle* h) { return h ? h->N : 0; }
+
+bfmri_status bfmri_sizes(const bfmri_handle* h, int* N, int* T, int* K, int* P) {
+  if (!h) return BFMRI_ERR_INVALID_ARG;
+  if (N) *N = h->N;
+  if (T) *T = h->T;
+  if (K) *K = h->K;
+  if (P) *P = h->P;
+  return BFMRI_OK;
+}
+
+bfmri_status bfmri_create(const bfmri_lattice* lat, const uint8_t* mask, const double* X,
+                          const void* Y, int y_dtype, int T, int K, int P,
+                          const bfmri_options* opt, bfmri_handle** out) {
+  if (!out) return fail(nullptr, BFMRI_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!lat || !mask || !X || !Y) return fail(nullptr, BFMRI_ERR_INVALID_ARG, "NULL input");
+  if (lat->nx < 1 || lat->ny < 1 || lat->nz < 1)
+    return fail(nullptr, BFMRI_ERR_INVALID_ARG, "lattice dimensions must be positive");
+  if (lat->neighbourhood != 4 && lat->neighbourhood != 6)
+    return fail(nullptr, BFMRI_ERR_INVALID_ARG, "neighbourhood must be 4 or 6");
+  if (K < 1 || K > KMAX) return fail(nullptr, BFMRI_ERR_INVALID_ARG, "K must be in [1, 12]");
+  if (P < 0 || P > PMAX) return fail(nullptr, BFMRI_ERR_INVALID_ARG, "P must be in [0, 4]");
+  if (T <= P + K) return fail(nullptr, BFMRI_ERR_INVALID_ARG, "T must exceed P + K");
+  if (y_dtype != BFMRI_F32 && y_dtype != BFMRI_F64)
+    return fail(nullptr, BFMRI_ERR_INVALID_ARG, "y_dtype must be BFMRI_F32 or BFMRI_F64");
+  const long long nsite = (long long)lat->nx * lat->ny * lat->nz;
+  if (nsite >= (1LL << 30)) return fail(nullptr, BFMRI_ERR_INVALID_ARG, "lattice too large (>= 2^30 sites)");
+  bfmri_options o;
+  if (opt) o = *opt; else bfmri_default_options(&o);
+  if (!(o.delta > 0.0) || o.max_iter < 1 || !(o.barrier_timeout_s > 0.0) || o.eps < 0.0 ||
+      !(o.q1 > 0) || !(o.q2 > 0) || !(o.u1 > 0) || !(o.u2 > 0) || !(o.r1 > 0) || !(o.r2 > 0))
+    return fail(nullptr, BFMRI_ERR_INVALID_ARG, "invalid option value");
+  if (o.precond != BFMRI_PRECOND_NONE && o.precond != BFMRI_PRECOND_BLOCK_JACOBI)
+    return fail(nullptr, BFMRI_ERR_INVALID_ARG, "unknown preconditioner");
+  if (o.precision != BFMRI_PREC_FP64)
+    return fail(nullptr, BFMRI_ERR_INVALID_ARG, "precision mode not available in this build");
+  if (!all_finite(X, (size_t)T * K)) return fail(nullptr, BFMRI_ERR_INVALID_ARG, "X has non-finite values");
+
+  // in-mask voxels in raster order and their neighbour planes
+  std::vector<int> index_of((size_t)nsite, -1), lin;
+  for (long long l = 0; l < nsite; ++l)
+    if (mask[l]) {
+      index_of[(size_t)l] = (int)lin.size();
+      lin.push_back((int)l);
+    }
+  const int N = (int)lin.size();
+  if (N == 0) return fail(nullptr, BFMRI_ERR_INVALID_ARG, "mask is empty");
+
+  bfmri_handle* h = new bfmri_handle();
+  h->opt = o;
+  h->nx = lat->nx;
+  h->ny = lat->ny;
+  h->nz = lat->nz;
+  h->nbh = lat->neighbourhood;
+  h->ndir = lat->neighbourhood;
+  h->N = N;
+  h->T = T;
+  h->K = K;
+  h->P = P;
+  h->D = K > P ? K : P;
+  h->ld = ((size_t)N + 31) & ~size_t(31);
+  h->stream = (cudaStream_t)o.cuda_stream;
+  h->stride[0] = 1;
+  h->stride[1] = lat->nx;
+  h->stride[2] = lat->nx * lat->ny;
+  const size_t ld = h->ld;
+
+  std::vector<int> nbr(6 * ld, -1);
+  for (int n = 0; n < N; ++n) {
+    const int l = lin[n];
+    const int x = l % lat->nx, y = (l / lat->nx) % lat->ny, z = l / (lat->nx * lat->ny);
+    const int dx[6] = {-1, 1, 0, 0, 0, 0}, dy[6] = {0, 0, -1, 1, 0, 0}, dz[6] = {0, 0, 0, 0, -1, 1};
+    for (int d = 0; d < h->ndir; ++d) {
+      const int xx = x + dx[d], yy = y + dy[d], zz = z + dz[d];
+      if (xx < 0 || yy < 0 || zz < 0 || xx >= lat->nx || yy >= lat->ny || zz >= lat->nz) continue;
+      nbr[d * ld + n] = index_of[(size_t)zz * lat->nx * lat->ny + (size_t)yy * lat->nx + xx];
+    }
+  }
+  // Y restricted to the mask, validated
+  const size_t ycols = o.y_layout == BFMRI_Y_LATTICE ? (size_t)nsite : (size_t)N;
+  const size_t esz = y_dtype == BFMRI_F64 ? 8 : 4;
+  std::vector<unsigned char> ymask;
+  const void* ysrc = Y;
+  if (o.y_layout == BFMRI_Y_LATTICE) {
+    ymask.resize((size_t)T * N * esz);
+    for (int t = 0; t < T; ++t)
+      for (int n = 0; n < N; ++n)
+        memcpy(&ymask[((size_t)t * N + n) * esz],
+               static_cast<const unsigned char*>(Y) + ((size_t)t * ycols + lin[n]) * esz, esz);
+    ysrc = ymask.data();
+  }
+  bool finite = true;
+  if (y_dtype == BFMRI_F64) {
+    finite = all_finite(static_cast<const double*>(ysrc), (size_t)T * N);
+  } else {
+    const float* yf = static_cast<const float*>(ysrc);
+    for (size_t i = 0; i < (size_t)T * N && finite; ++i) finite = std::isfinite(yf[i]);
+  }
+  if (!finite) {
+    delete h;
+    return fail(nullptr, BFMRI_ERR_INVALID_ARG, "Y has non-finite values");
+  }
+  // voxel-independent lagged X products Sxx[p][q][i][j] over t = P+1..T (1-based)
+  h->Sxx.assign((size_t)(P + 1) * (P + 1) * K * K, 0.0);
+  for (int p = 0; p <= P; ++p)
+    for (int q = 0; q <= P; ++q)
+      for (int i = 0; i < K; ++i)
+        for (int j = 0; j < K; ++j) {
+          double s = 0.0;
+          for (int t = P; t < T; ++t) s += X[(t - p) + (size_t)T * i] * X[(t - q) + (size_t)T * j];
+          h->Sxx[(((size_t)p * (P + 1) + q) * K + i) * K + j] = s;
+        }
+
+  // device memory
+  auto A = [&](size_t bytes) { return dalloc(h, bytes); };
+  const int D = h->D;
+  const int Pa = P > 0 ? P : 1;
+  int maxgrid = pcg_max_grid(K);
+  if (P > 0) maxgrid = std::max(maxgrid, pcg_max_grid(P));
+  if (maxgrid < 1) maxgrid = 1024;
+  h->part_rows = maxgrid;
+  h->d_nbr = (int*)A(6 * ld * sizeof(int));
+  h->d_lin = (int*)A(ld * sizeof(int));
+  h->d_Y = A((size_t)T * N * esz);
+  h->y_f64 = y_dtype == BFMRI_F64;
+  h->d_X = (double*)A((size_t)T * K * sizeof(double));
+  h->d_stats = (double*)A((size_t)n_stats(K, P) * ld * sizeof(double));
+  h->d_Sxx = (double*)A(h->Sxx.size() * sizeof(double));
+  h->d_W = (double*)A((size_t)K * ld * sizeof(double));
+  h->d_A = (double*)A((size_t)Pa * ld * sizeof(double));
+  h->d_lam = (double*)A(ld * sizeof(double));
+  h->d_alpha = (double*)A((size_t)K * sizeof(double));
+  h->d_beta = (double*)A((size_t)Pa * sizeof(double));
+  h->d_G = (double*)A((size_t)n_syy(P) * ld * sizeof(double));
+  h->d_blocks = (double*)A((size_t)ntri(D) * ld * sizeof(double));
+  h->d_mfac = (double*)A((size_t)ntri(D) * ld * sizeof(double));
+  h->d_rhs = (double*)A((size_t)D * ld * sizeof(double));
+  h->d_bmean = (double*)A((size_t)D * ld * sizeof(double));
+  h->d_r = (double*)A((size_t)D * ld * sizeof(double));
+  h->d_z = (double*)A((size_t)D * ld * sizeof(double));
+  h->d_q = (double*)A((size_t)D * ld * sizeof(double));
+  h->d_p0 = (double*)A((size_t)D * ld * sizeof(double));
+  h->d_p1 = (double*)A((size_t)D * ld * sizeof(double));
+  h->d_part = (double*)A((size_t)2 * maxgrid * 4 * sizeof(double));
+  h->d_hpart = (double*)A((size_t)hyper_grid(N) * D * sizeof(double));
+  h->d_bar = (unsigned int*)A(2 * sizeof(unsigned int));
+  h->d_err = (int*)A(sizeof(int));
+  h->d_ctrl = (PcgCtrl*)A(2 * sizeof(PcgCtrl));
+  h->d_flags = (int*)A(4 * sizeof(int));
+  void* must[] = {h->d_nbr, h->d_lin, h->d_Y, h->d_X, h->d_stats, h->d_Sxx, h->d_W, h->d_A,
+                  h->d_lam, h->d_alpha, h->d_beta, h->d_G, h->d_blocks, h->d_mfac, h->d_rhs,
+                  h->d_bmean, h->d_r, h->d_z, h->d_q, h->d_p0, h->d_p1, h->d_part, h->d_hpart,
+                  h->d_bar, h->d_err, h->d_ctrl, h->d_flags};
+  for (void* p : must) {
+    if (!p) {
+      bfmri_destroy(h);
+      return fail(nullptr, BFMRI_ERR_OOM, "device allocation failed");
+    }
+  }
+  cudaStream_t s = h->stream;
+  cudaError_t e = cudaSuccess;
+  std::vector<int> linp(ld, 0);
+  for (int n = 0; n < N; ++n) linp[n] = lin[n];
+  if (!e) e = cudaMemcpyAsync(h->d_nbr, nbr.data(), nbr.size() * sizeof(int), cudaMemcpyHostToDevice, s);
+  if (!e) e = cudaMemcpyAsync(h->d_lin, linp.data(), ld * sizeof(int), cudaMemcpyHostToDevice, s);
+  if (!e) e = cudaMemcpyAsync(h->d_Y, ysrc, (size_t)T * N * esz, cudaMemcpyHostToDevice, s);
+  if (!e) e = cudaMemcpyAsync(h->d_X, X, (size_t)T * K * sizeof(double), cudaMemcpyHostToDevice, s);
+  if (!e) e = cudaMemcpyAsync(h->d_Sxx, h->Sxx.data(), h->Sxx.size() * sizeof(double), cudaMemcpyHostToDevice, s);
+  // prior means (Appendix C, trick 2); W = 0, A = 0
+  std::vector<double> init((size_t)D * ld, 0.0);
+  if (!e) e = cudaMemcpyAsync(h->d_W, init.data(), (size_t)K * ld * sizeof(double), cudaMemcpyHostToDevice, s);
+  if (!e) e = cudaMemcpyAsync(h->d_A, init.data(), (size_t)Pa * ld * sizeof(double), cudaMemcpyHostToDevice, s);
+  std::vector<double> lam0(ld, o.u1 * o.u2), al0(K, o.q1 * o.q2), be0(Pa, o.r1 * o.r2);
+  if (!e) e = cudaMemcpyAsync(h->d_lam, lam0.data(), ld * sizeof(double), cudaMemcpyHostToDevice, s);
+  if (!e) e = cudaMemcpyAsync(h->d_alpha, al0.data(), K * sizeof(double), cudaMemcpyHostToDevice, s);
+  if (!e) e = cudaMemcpyAsync(h->d_beta, be0.data(), Pa * sizeof(double), cudaMemcpyHostToDevice, s);
+  if (!e) e = cudaMemsetAsync(h->d_ctrl, 0, 2 * sizeof(PcgCtrl), s);
+  if (!e) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    std::string msg = std::string("bfmri_create: ") + cudaGetErrorString(e);
+    bfmri_destroy(h);
+    return fail(nullptr, BFMRI_ERR_CUDA, msg);
+  }
+  *out = h;
+  return BFMRI_OK;
+}
+
+bfmri_status bfmri_destroy(bfmri_handle* h) {
+  if (!h) return BFMRI_OK;
+  cudaStreamSynchronize(h->stream);
+  std::vector<void*> all = h->allocs;
+  for (void* p : all) dfree(h, p);
+  delete h;
+  return BFMRI_OK;
+}
+
+bfmri_status bfmri_precompute_stats(bfmri_handle* h) {
+  if (!h) return BFMRI_ERR_INVALID_ARG;
+  if (!h->d_Y) return fail(h, BFMRI_ERR_STATE, "statistics already computed (Y released)");
+  StatsArgs a;
+  a.N = h->N;
+  a.T = h->T;
+  a.K = h->K;
+  a.P = h->P;
+  a.ld = h->ld;
+  a.Y = h->d_Y;
+  a.y_is_f64 = h->y_f64;
+  a.X = h->d_X;
+  a.stats = h->d_stats;
+  cudaError_t e = launch_stats(a, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "stats");
+  CU(h, cudaStreamSynchronize(h->stream));
+  dfree(h, h->d_Y);
+  h->d_Y = nullptr;
+  h->stats_ready = true;
+  return BFMRI_OK;
+}
+
+bfmri_status bfmri_get_stats(bfmri_handle* h, double* out) {
+  RET(require_stats(h));
+  if (!out) return fail(h, BFMRI_ERR_INVALID_ARG, "out is NULL");
+  const int S = n_stats(h->K, h->P);
+  std::vector<double> planes((size_t)S * h->N);
+  CU(h, cudaMemcpy2DAsync(planes.data(), (size_t)h->N * sizeof(double), h->d_stats,
+                          h->ld * sizeof(double), (size_t)h->N * sizeof(double), S,
+                          cudaMemcpyDeviceToHost, h->stream));
+  CU(h, cudaStreamSynchronize(h->stream));
+  for (int n = 0; n < h->N; ++n)
+    for (int j = 0; j < S; ++j) out[(size_t)n * S + j] = planes[(size_t)j * h->N + n];
+  return BFMRI_OK;
+}
+
+bfmri_status bfmri_set_state(bfmri_handle* h, const double* W, const double* A,
+                             const double* lambda, const double* alpha, const double* beta) {
+  if (!h) return BFMRI_ERR_INVALID_ARG;
+  if (W && !all_finite(W, (size_t)h->K * h->N)) return fail(h, BFMRI_ERR_INVALID_ARG, "W not finite");
+  if (A && !all_finite(A, (size_t)h->P * h->N)) return fail(h, BFMRI_ERR_INVALID_ARG, "A not finite");
+  if (lambda && !all_positive(lambda, h->N)) return fail(h, BFMRI_ERR_INVALID_ARG, "lambda must be > 0");
+  if (alpha && !all_positive(alpha, h->K)) return fail(h, BFMRI_ERR_INVALID_ARG, "alpha must be > 0");
+  if (beta && h->P > 0 && !all_positive(beta, h->P)) return fail(h, BFMRI_ERR_INVALID_ARG, "beta must be > 0");
+  if (W) RET(to_dev(h, h->d_W, W, h->K));
+  if (A) RET(to_dev(h, h->d_A, A, h->P));
+  if (lambda) RET(to_dev(h, h->d_lam, lambda, 1));
+  if (alpha) CU(h, cudaMemcpyAsync(h->d_alpha, alpha, h->K * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  if (beta && h->P > 0)
+    CU(h, cudaMemcpyAsync(h->d_beta, beta, h->P * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  CU(h, cudaStreamSynchronize(h->stream));
+  return BFMRI_OK;
+}
+
+bfmri_status bfmri_get_state(bfmri_handle* h, double* W, double* A, double* lambda,
+                             double* alpha, double* beta) {
+  if (!h) return BFMRI_ERR_INVALID_ARG;
+  if (W) RET(to_host(h, W, h->d_W, h->K));
+  if (A) RET(to_host(h, A, h->d_A, h->P));
+  if (lambda) RET(to_host(h, lambda, h->d_lam, 1));
+  if (alpha) CU(h, cudaMemcpyAsync(alpha, h->d_alpha, h->K * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  if (beta && h->P > 0)
+    CU(h, cudaMemcpyAsync(beta, h->d_beta, h->P * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CU(h, cudaStreamSynchronize(h->stream));
+  return BFMRI_OK;
+}
+
+bfmri_status bfmri_sample_W(bfmri_handle* h, uint64_t counter, double* W_out, bfmri_solve_info* info) {
+  RET(require_stats(h));
+  RET(begin_call(h));
+  RET(enqueue_W(h, counter));
+  PcgCtrl c[2];
+  RET(end_call(h, c, nullptr));
+  fill_info(info, c[0]);
+  if (W_out) RET(to_host(h, W_out, h->d_W, h->K));
+  return BFMRI_OK;
+}
+
+bfmri_status bfmri_sample_A(bfmri_handle* h, uint64_t counter, double* A_out, bfmri_solve_info* info) {
+  RET(require_stats(h));
+  if (h->P == 0) return BFMRI_OK;
+  RET(begin_call(h));
+  RET(enqueue_A(h, counter));
+  PcgCtrl c[2];
+  RET(end_call(h, c, nullptr));
+  fill_info(info, c[1]);
+  if (A_out) RET(to_host(h, A_out, h->d_A, h->P));
+  return BFMRI_OK;
+}
+
+bfmri_status bfmri_sample_lambda(bfmri_handle* h, uint64_t counter, double* lambda_out) {
+  RET(require_stats(h));
+  RET(begin_call(h));
+  RET(enqueue_gram(h));
+  RET(enqueue_lambda(h, counter));
+  RET(end_call(h, nullptr, nullptr));
+  if (lambda_out) RET(to_host(h, lambda_out, h->d_lam, 1));
+  return BFMRI_OK;
+}
+
+bfmri_status bfmri_sample_alpha(bfmri_handle* h, uint64_t counter, double* alpha_out) {
+  RET(require_stats(h));
+  RET(begin_call(h));
+  RET(enqueue_hyper(h, counter, false));
+  RET(end_call(h, nullptr, nullptr));
+  if (alpha_out) {
+    CU(h, cudaMemcpy(alpha_out, h->d_alpha, h->K * sizeof(double), cudaMemcpyDeviceToHost));
+  }
+  return BFMRI_OK;
+}
+
+bfmri_status bfmri_sample_beta(bfmri_handle* h, uint64_t counter, double* beta_out) {
+  RET(require_stats(h));
+  if (h->P == 0 || h->opt.ar_prior != BFMRI_AR_SPATIAL) return BFMRI_OK;
+  RET(begin_call(h));
+  RET(enqueue_hyper(h, counter, true));
+  RET(end_call(h, nullptr, nullptr));
+  if (beta_out) {
+    CU(h, cudaMemcpy(beta_out, h->d_beta, h->P * sizeof(double), cudaMemcpyDeviceToHost));
+  }
+  return BFMRI_OK;
+}
+
+bfmri_status bfmri_gibbs_sweep(bfmri_handle* h, int n_sweeps, uint64_t first_counter,
+                               bfmri_sweep_info* info) {
+  RET(require_stats(h));
+  if (n_sweeps < 0) return fail(h, BFMRI_ERR_INVALID_ARG, "n_sweeps < 0");
+  RET(begin_call(h));
+  const bool spatial = h->opt.ar_prior == BFMRI_AR_SPATIAL;
+  for (int s = 0; s < n_sweeps; ++s) {
+    const uint64_t c = first_counter + (uint64_t)s;
+    RET(enqueue_W(h, c));
+    RET(enqueue_A(h, c));
+    RET(enqueue_lambda(h, c));
+    RET(enqueue_hyper(h, c, false));
+    if (h->P > 0 && spatial) RET(enqueue_hyper(h, c, true));
+  }
+  PcgCtrl c[2];
+  int exhausted = 0;
+  bfmri_status st = end_call(h, c, &exhausted);
+  if (info) {
+    info->sweeps = n_sweeps;
+    info->pcg_iterations_W = c[0].iter_total;
+    info->pcg_iterations_A = c[1].iter_total;
+    info->last_rel_residual_W = c[0].rel_res;
+    info->gamma_exhausted = exhausted;
+  }
+  return st;
+}
+
+bfmri_status bfmri_apply_precision(bfmri_handle* h, int which, const double* x, double* y) {
+  RET(require_stats(h));
+  if (!x || !y || (which != 0 && which != 1)) return fail(h, BFMRI_ERR_INVALID_ARG, "bad arguments");
+  const int D = which == 0 ? h->K : h->P;
+  if (D == 0) return BFMRI_OK;
+  RET(begin_call(h));
+  AssembleArgs a = assemble_args(h, which == 0 ? h->d_alpha : h->d_beta, 0, which == 0 ? TAG_W : TAG_A);
+  a.perturb = 0;
+  a.precond = 0;
+  cudaError_t e = which == 0 ? launch_assemble_w(a, h->stream) : launch_assemble_a(a, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "assemble");
+  RET(to_dev(h, h->d_r, x, D));
+  ApplyArgs ap;
+  ap.g = geom(h);
+  ap.D = D;
+  ap.blocks = h->d_blocks;
+  ap.scale = which == 0 ? h->d_alpha : h->d_beta;
+  // the independent AR prior has no spatial term
+  static const double zeros[PMAX] = {0, 0, 0, 0};
+  if (which == 1 && h->opt.ar_prior != BFMRI_AR_SPATIAL) {
+    CU(h, cudaMemcpyAsync(h->d_bmean, zeros, D * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    ap.scale = h->d_bmean;
+  }
+  ap.x = h->d_r;
+  ap.y = h->d_z;
+  e = launch_apply(ap, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "apply");
+  RET(end_call(h, nullptr, nullptr));
+  return to_host(h, y, h->d_z, D);
+}
+
+bfmri_status bfmri_build_system(bfmri_handle* h, int which, uint64_t counter, double* blocks,
+                                double* b_mean, double* b_pert) {
+  RET(require_stats(h));
+  if (which != 0 && which != 1) return fail(h, BFMRI_ERR_INVALID_ARG, "which must be 0 or 1");
+  const int D = which == 0 ? h->K : h->P;
+  if (D == 0) return BFMRI_OK;
+  RET(begin_call(h));
+  AssembleArgs a = assemble_args(h, which == 0 ? h->d_alpha : h->d_beta, counter, which == 0 ? TAG_W : TAG_A);
+  a.precond = 0;
+  a.bmean = h->d_bmean;
+  cudaError_t e = which == 0 ? launch_assemble_w(a, h->stream) : launch_assemble_a(a, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "assemble");
+  RET(end_call(h, nullptr, nullptr));
+  if (blocks) {
+    const int nt = ntri(D);
+    std::vector<double> planes((size_t)nt * h->N);
+    CU(h, cudaMemcpy2DAsync(planes.data(), (size_t)h->N * sizeof(double), h->d_blocks,
+                            h->ld * sizeof(double), (size_t)h->N * sizeof(double), nt,
+                            cudaMemcpyDeviceToHost, h->stream));
+    CU(h, cudaStreamSynchronize(h->stream));
+    for (int n = 0; n < h->N; ++n)
+      for (int i = 0; i < D; ++i)
+        for (int j = 0; j < D; ++j) {
+          const int e2 = i >= j ? tri(i, j) : tri(j, i);
+          blocks[((size_t)n * D + i) * D + j] = planes[(size_t)e2 * h->N + n];
+        }
+  }
+  if (b_mean) RET(to_host(h, b_mean, h->d_bmean, D));
+  if (b_pert) RET(to_host(h, b_pert, h->d_rhs, D));
+  return BFMRI_OK;
+}
+
+}  // extern "C"

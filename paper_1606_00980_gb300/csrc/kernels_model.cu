@@ -1,0 +1,527 @@
+// Per-voxel model kernels: sufficient statistics (Appendix A, Eq. log-like), assembly of the
+// W and A full conditionals (Eq. full cond W temporal, Eq. fullcondTempA) fused with the
+// Algorithm 2 perturbation and the block-Jacobi factorisation, and the Gamma full
+// conditionals of lambda, alpha, beta (Eq. fullcondTemplambda, fullcondTempa, fullcondTempbeta).
+#include <climits>
+
+#include "model.cuh"
+
+namespace bfmri {
+
+namespace {
+
+constexpr int STATS_THREADS = 128;
+constexpr int VOX_THREADS = 128;
+constexpr int HYPER_THREADS = 256;
+
+__device__ __forceinline__ size_t sxy_plane(int p, int q, int k, int K, int P) {
+  return (size_t)(n_syy(P) + (p * (P + 1) + q) * K + k);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------
+// Sufficient statistics. Thread (n, p): for lag p it accumulates, over t = P+1..T (1-based),
+// Syy[p][q] (q >= p) and Sxy[p][q][k] for all q, k. X is staged in shared memory (row-major
+// T x K); a register window holds y_t .. y_{t-P}.
+// ---------------------------------------------------------------------------------------
+template <int K, typename TY>
+__global__ void __launch_bounds__(STATS_THREADS) k_stats(StatsArgs a) {
+  extern __shared__ double shX[];
+  const int T = a.T, P = a.P, N = a.N;
+  for (int i = threadIdx.x; i < T * K; i += blockDim.x) {
+    const int t = i / K, k = i - t * K;
+    shX[i] = a.X[t + (size_t)T * k];
+  }
+  __syncthreads();
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  const int p = blockIdx.y;
+  if (n >= N) return;
+  const TY* Y = static_cast<const TY*>(a.Y);
+  double axy[PMAX + 1][K];
+  double ayy[PMAX + 1];
+  double yw[PMAX + 1];
+#pragma unroll
+  for (int q = 0; q <= PMAX; ++q) {
+    ayy[q] = 0.0;
+    yw[q] = 0.0;
+#pragma unroll
+    for (int k = 0; k < K; ++k) axy[q][k] = 0.0;
+  }
+#pragma unroll
+  for (int j = 0; j <= PMAX; ++j)
+    if (j <= P) yw[j] = (double)Y[(size_t)(P - j) * N + n];
+  for (int t = P; t < T; ++t) {
+    if (t > P) {
+#pragma unroll
+      for (int j = PMAX; j > 0; --j) yw[j] = yw[j - 1];
+      yw[0] = (double)Y[(size_t)t * N + n];
+    }
+    const double v = (double)Y[(size_t)(t - p) * N + n];
+#pragma unroll
+    for (int q = 0; q <= PMAX; ++q) {
+      if (q <= P) {
+        ayy[q] += v * yw[q];
+        const double* xr = shX + (size_t)(t - q) * K;
+#pragma unroll
+        for (int k = 0; k < K; ++k) axy[q][k] += v * xr[k];
+      }
+    }
+  }
+  const size_t ld = a.ld;
+#pragma unroll
+  for (int q = 0; q <= PMAX; ++q) {
+    if (q <= P) {
+      if (q >= p) a.stats[(size_t)syy_index(p, q, P) * ld + n] = ayy[q];
+#pragma unroll
+      for (int k = 0; k < K; ++k) a.stats[sxy_plane(p, q, k, K, P) * ld + n] = axy[q][k];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Algorithm 2 perturbation for one voxel: rhs += sum_k sqrt(s_k) (G' z1_k)_n over the
+// voxel's edges. Edge (i, i + stride_d) carries +z at i and -z at its upper endpoint; its
+// normals come from site lattice-linear(i) * 4 + d.
+// ---------------------------------------------------------------------------------------
+template <int D>
+__device__ __forceinline__ void add_edge_noise(const Geometry& g, const Rng& rng, int n, int lin,
+                                               const double* sq, double* rhs) {
+  double z[D];
+  for (int d = 0; d < g.ndir / 2; ++d) {
+    if (__ldg(g.nbr + (size_t)(2 * d + 1) * g.ld + n) >= 0) {
+      site_normals<D>(rng, (uint32_t)lin * 4u + (uint32_t)d, z);
+#pragma unroll
+      for (int k = 0; k < D; ++k) rhs[k] += sq[k] * z[k];
+    }
+    if (__ldg(g.nbr + (size_t)(2 * d) * g.ld + n) >= 0) {
+      site_normals<D>(rng, (uint32_t)(lin - g.stride[d]) * 4u + (uint32_t)d, z);
+#pragma unroll
+      for (int k = 0; k < D; ++k) rhs[k] -= sq[k] * z[k];
+    }
+  }
+}
+
+__device__ __forceinline__ int degree(const Geometry& g, int n) {
+  int deg = 0;
+  for (int d = 0; d < g.ndir; ++d) deg += __ldg(g.nbr + (size_t)d * g.ld + n) >= 0 ? 1 : 0;
+  return deg;
+}
+
+// ---------------------------------------------------------------------------------------
+// W system. Bd_n = lambda_n sum_pq c_p c_q Sxx[p][q] + eps I, b_n = lambda_n sum_pq c_p c_q
+// Sxy[p][q] with c = (1, -a_n); perturbed rhs = b_n + L_n z2_n + sum_k sqrt(alpha_k) (G'z1_k)_n
+// with L_n = chol(Bd_n); preconditioner factor chol(Bd_n + diag(alpha) deg_n).
+// ---------------------------------------------------------------------------------------
+template <int K>
+__global__ void __launch_bounds__(VOX_THREADS) k_assemble_w(AssembleArgs a) {
+  extern __shared__ double shS[];
+  const int P = a.P;
+  const int nS = (P + 1) * (P + 1) * K * K;
+  for (int i = threadIdx.x; i < nS; i += blockDim.x) shS[i] = a.Sxx[i];
+  __syncthreads();
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= a.g.N) return;
+  const size_t ld = a.g.ld;
+  double c[PMAX + 1];
+  c[0] = 1.0;
+#pragma unroll
+  for (int p = 1; p <= PMAX; ++p) c[p] = (p <= P) ? -a.A[(size_t)(p - 1) * ld + n] : 0.0;
+  double B[ntri(K)], bw[K];
+#pragma unroll
+  for (int e = 0; e < ntri(K); ++e) B[e] = 0.0;
+#pragma unroll
+  for (int k = 0; k < K; ++k) bw[k] = 0.0;
+#pragma unroll
+  for (int p = 0; p <= PMAX; ++p) {
+#pragma unroll
+    for (int q = 0; q <= PMAX; ++q) {
+      if (p <= P && q <= P) {
+        const double cpq = c[p] * c[q];
+        const double* S = shS + (size_t)(p * (P + 1) + q) * K * K;
+#pragma unroll
+        for (int i = 0; i < K; ++i)
+#pragma unroll
+          for (int j = 0; j <= i; ++j) B[tri(i, j)] += cpq * S[i * K + j];
+#pragma unroll
+        for (int k = 0; k < K; ++k) bw[k] += cpq * __ldg(a.stats + sxy_plane(p, q, k, K, P) * ld + n);
+      }
+    }
+  }
+  const double lam = a.lam[n];
+#pragma unroll
+  for (int e = 0; e < ntri(K); ++e) B[e] *= lam;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    B[tri(k, k)] += a.eps;
+    bw[k] *= lam;
+  }
+  store_packed<K>(a.blocks, ld, n, B);
+  if (a.bmean) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) a.bmean[k * ld + n] = bw[k];
+  }
+  double sq[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) sq[k] = sqrt(a.scale[k]);
+  double rhs[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) rhs[k] = bw[k];
+  double L[ntri(K)];
+#pragma unroll
+  for (int e = 0; e < ntri(K); ++e) L[e] = B[e];
+  bool ok = chol_packed_invdiag<K>(L);
+  if (a.perturb) {
+    const int lin = a.g.lin[n];
+    double z[K], Lz[K];
+    site_normals<K>(a.rng, (uint32_t)lin * 4u + 3u, z);
+    lower_mul_invdiag<K>(L, z, Lz);
+#pragma unroll
+    for (int k = 0; k < K; ++k) rhs[k] += Lz[k];
+    add_edge_noise<K>(a.g, a.rng, n, lin, sq, rhs);
+  }
+#pragma unroll
+  for (int k = 0; k < K; ++k) a.rhs[k * ld + n] = rhs[k];
+  if (a.precond) {
+    const double deg = (double)degree(a.g, n);
+#pragma unroll
+    for (int k = 0; k < K; ++k) B[tri(k, k)] += a.scale[k] * deg;
+    ok = chol_packed_invdiag<K>(B) && ok;
+    store_packed<K>(a.mfac, ld, n, B);
+  }
+  if (!ok) atomicMin(a.bad_voxel, n);
+}
+
+// ---------------------------------------------------------------------------------------
+// A system and the lagged residual Gram. With e = y - X w_n:
+//   G[p][q] = (L^p e)'(L^q e) = Syy[p][q] - w.Sxy[q][p] - w.Sxy[p][q] + w' Sxx[p][q] w,
+// the block lambda_n G[1:,1:], the right-hand side lambda_n G[1:,0] (Eq. fullcondTempA),
+// perturbed with beta (spatial prior) or drawn per voxel directly (independent prior).
+// The P x P matrices are embedded in PMAX x PMAX with identity padding.
+// ---------------------------------------------------------------------------------------
+template <int K>
+__global__ void __launch_bounds__(VOX_THREADS) k_assemble_a(AssembleArgs a) {
+  extern __shared__ double shS[];
+  const int P = a.P;
+  const int nS = (P + 1) * (P + 1) * K * K;
+  for (int i = threadIdx.x; i < nS; i += blockDim.x) shS[i] = a.Sxx[i];
+  __syncthreads();
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= a.g.N) return;
+  const size_t ld = a.g.ld;
+  double w[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) w[k] = a.W[(size_t)k * ld + n];
+  double Gm[PMAX + 1][PMAX + 1];
+#pragma unroll
+  for (int p = 0; p <= PMAX; ++p) {
+#pragma unroll
+    for (int q = p; q <= PMAX; ++q) {
+      double g = 0.0;
+      if (q <= P) {
+        double t1 = 0.0, t2 = 0.0, quad = 0.0;
+        const double* S = shS + (size_t)(p * (P + 1) + q) * K * K;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+          t1 += w[k] * __ldg(a.stats + sxy_plane(q, p, k, K, P) * ld + n);
+          t2 += w[k] * __ldg(a.stats + sxy_plane(p, q, k, K, P) * ld + n);
+          double sk = 0.0;
+#pragma unroll
+          for (int j = 0; j < K; ++j) sk += S[k * K + j] * w[j];
+          quad += w[k] * sk;
+        }
+        g = __ldg(a.stats + (size_t)syy_index(p, q, P) * ld + n) - t1 - t2 + quad;
+        a.G[(size_t)syy_index(p, q, P) * ld + n] = g;
+      }
+      Gm[p][q] = g;
+      Gm[q][p] = g;
+    }
+  }
+  if (P == 0 || a.g_only) return;
+  const double lam = a.lam[n];
+  constexpr int PM = PMAX;
+  double J[ntri(PM)], rhs[PM];
+#pragma unroll
+  for (int i = 0; i < PM; ++i) {
+    rhs[i] = (i < P) ? lam * Gm[i + 1][0] : 0.0;
+#pragma unroll
+    for (int j = 0; j <= i; ++j)
+      J[tri(i, j)] = (i < P) ? lam * Gm[i + 1][j + 1] : (i == j ? 1.0 : 0.0);
+  }
+  if (a.bmean) {
+#pragma unroll
+    for (int i = 0; i < PM; ++i)
+      if (i < P) a.bmean[i * ld + n] = rhs[i];
+  }
+  double L[ntri(PM)];
+#pragma unroll
+  for (int e = 0; e < ntri(PM); ++e) L[e] = J[e];
+  bool ok = chol_packed_invdiag<PM>(L);
+  const int lin = a.g.lin[n];
+  if (a.perturb) {
+    double z[PM], Lz[PM];
+    site_normals<PM>(a.rng, (uint32_t)lin * 4u + 3u, z);
+#pragma unroll
+    for (int i = 0; i < PM; ++i)
+      if (i >= P) z[i] = 0.0;
+    lower_mul_invdiag<PM>(L, z, Lz);
+#pragma unroll
+    for (int i = 0; i < PM; ++i) rhs[i] += (i < P) ? Lz[i] : 0.0;
+    if (a.spatial) {
+      double sq[PM];
+#pragma unroll
+      for (int i = 0; i < PM; ++i) sq[i] = (i < P) ? sqrt(a.scale[i]) : 0.0;
+      add_edge_noise<PM>(a.g, a.rng, n, lin, sq, rhs);
+    }
+  }
+  if (a.x_direct) {
+    // independent voxels: the draw is J^-1 rhs
+    double x[PM];
+    chol_solve_invdiag<PM>(L, rhs, x);
+#pragma unroll
+    for (int i = 0; i < PM; ++i)
+      if (i < P) a.x_direct[i * ld + n] = x[i];
+  }
+  if (a.rhs) {
+#pragma unroll
+    for (int e = 0; e < ntri(PM); ++e)
+      if (e < ntri(P)) a.blocks[(size_t)e * ld + n] = J[e];
+#pragma unroll
+    for (int i = 0; i < PM; ++i)
+      if (i < P) a.rhs[i * ld + n] = rhs[i];
+    if (a.precond) {
+      const double deg = a.spatial ? (double)degree(a.g, n) : 0.0;
+#pragma unroll
+      for (int i = 0; i < PM; ++i)
+        if (i < P) J[tri(i, i)] += a.scale[i] * deg;
+      ok = chol_packed_invdiag<PM>(J) && ok;
+#pragma unroll
+      for (int e = 0; e < ntri(PM); ++e)
+        if (e < ntri(P)) a.mfac[(size_t)e * ld + n] = J[e];
+    }
+  }
+  if (!ok) atomicMin(a.bad_voxel, n);
+}
+
+// ---------------------------------------------------------------------------------------
+// lambda: RSS_n = c' G c with c = (1, -a_n) (the bracket of Eq. fullcondTemplambda).
+// ---------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(VOX_THREADS) k_lambda(LambdaArgs a) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= a.g.N) return;
+  const int P = a.P;
+  const size_t ld = a.g.ld;
+  double c[PMAX + 1];
+  c[0] = 1.0;
+#pragma unroll
+  for (int p = 1; p <= PMAX; ++p) c[p] = (p <= P) ? -a.A[(size_t)(p - 1) * ld + n] : 0.0;
+  double rss = 0.0;
+#pragma unroll
+  for (int p = 0; p <= PMAX; ++p) {
+#pragma unroll
+    for (int q = 0; q <= PMAX; ++q) {
+      if (p <= P && q <= P) {
+        const int pp = p < q ? p : q, qq = p < q ? q : p;
+        rss += c[p] * c[q] * a.G[(size_t)syy_index(pp, qq, P) * ld + n];
+      }
+    }
+  }
+  const double shape = 0.5 * (double)(a.T - P) + a.u2;
+  const double scale = 1.0 / (1.0 / a.u1 + 0.5 * rss);
+  int ex = 0;
+  a.lam[n] = gamma_draw(a.rng, (uint32_t)a.g.lin[n] * 4u + 3u, shape, scale, &ex);
+  if (ex) atomicAdd(a.exhausted, 1);
+}
+
+// ---------------------------------------------------------------------------------------
+// alpha / beta: deterministic two-level reduction of Q_k = sum_edges (v_i - v_j)^2.
+// ---------------------------------------------------------------------------------------
+template <int D>
+__global__ void __launch_bounds__(HYPER_THREADS) k_quadform(HyperArgs a) {
+  __shared__ double sh[HYPER_THREADS / 32][D];
+  double acc[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) acc[k] = 0.0;
+  const size_t ld = a.g.ld;
+  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < a.g.N; n += gridDim.x * blockDim.x) {
+    double v[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) v[k] = a.V[(size_t)k * ld + n];
+    for (int d = 0; d < a.g.ndir / 2; ++d) {
+      const int m = __ldg(a.g.nbr + (size_t)(2 * d + 1) * ld + n);
+      if (m >= 0) {
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          const double df = v[k] - a.V[(size_t)k * ld + m];
+          acc[k] += df * df;
+        }
+      }
+    }
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_down_sync(0xffffffffu, acc[k], o);
+    if (lane == 0) sh[warp][k] = acc[k];
+  }
+  __syncthreads();
+  if (threadIdx.x < D) {
+    double s = 0.0;
+    for (int w = 0; w < HYPER_THREADS / 32; ++w) s += sh[w][threadIdx.x];
+    a.part[(size_t)blockIdx.x * D + threadIdx.x] = s;
+  }
+}
+
+__global__ void k_hyper_draw(HyperArgs a, int nblocks) {
+  const int k = threadIdx.x;
+  if (k >= a.D) return;
+  double Q = 0.0;
+  for (int b = 0; b < nblocks; ++b) Q += a.part[(size_t)b * a.D + k];
+  if (a.Q_out) a.Q_out[k] = Q;
+  const double scale = 1.0 / (0.5 * Q + 1.0 / a.prior1);
+  const double shape = 0.5 * (double)a.g.N + a.prior2;
+  int ex = 0;
+  a.out[k] = gamma_draw(a.rng, (uint32_t)k, shape, scale, &ex);
+  if (ex) atomicAdd(a.exhausted, 1);
+}
+
+// ---------------------------------------------------------------------------------------
+// y = B~ x for inspection.
+// ---------------------------------------------------------------------------------------
+template <int D>
+__global__ void k_apply(ApplyArgs a) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= a.g.N) return;
+  const size_t ld = a.g.ld;
+  double xn[D], y[D], B[ntri(D)];
+#pragma unroll
+  for (int k = 0; k < D; ++k) xn[k] = a.x[(size_t)k * ld + n];
+  load_packed<D>(a.blocks, ld, n, B);
+  sym_mul<D>(B, xn, y);
+  double sum[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) sum[k] = 0.0;
+  int deg = 0;
+  for (int d = 0; d < a.g.ndir; ++d) {
+    const int m = a.g.nbr[(size_t)d * ld + n];
+    if (m >= 0) {
+      ++deg;
+#pragma unroll
+      for (int k = 0; k < D; ++k) sum[k] += a.x[(size_t)k * ld + m];
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < D; ++k) a.y[(size_t)k * ld + n] = y[k] + a.scale[k] * ((double)deg * xn[k] - sum[k]);
+}
+
+// ---------------------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------------------
+#define BFMRI_K_CASES(X) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12)
+
+template <int K>
+static cudaError_t stats_k(const StatsArgs& a, cudaStream_t s) {
+  const size_t shm = (size_t)a.T * K * sizeof(double);
+  dim3 grid((a.N + STATS_THREADS - 1) / STATS_THREADS, a.P + 1);
+  if (a.y_is_f64) {
+    cudaFuncSetAttribute(k_stats<K, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    k_stats<K, double><<<grid, STATS_THREADS, shm, s>>>(a);
+  } else {
+    cudaFuncSetAttribute(k_stats<K, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    k_stats<K, float><<<grid, STATS_THREADS, shm, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stats(const StatsArgs& a, cudaStream_t s) {
+  if (a.N <= 0) return cudaSuccess;
+  switch (a.K) {
+#define CASE(k) case k: return stats_k<k>(a, s);
+    BFMRI_K_CASES(CASE)
+#undef CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int K>
+static cudaError_t assemble_w_k(const AssembleArgs& a, cudaStream_t s) {
+  const size_t shm = (size_t)(a.P + 1) * (a.P + 1) * K * K * sizeof(double);
+  cudaFuncSetAttribute(k_assemble_w<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+  k_assemble_w<K><<<(a.g.N + VOX_THREADS - 1) / VOX_THREADS, VOX_THREADS, shm, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int K>
+static cudaError_t assemble_a_k(const AssembleArgs& a, cudaStream_t s) {
+  const size_t shm = (size_t)(a.P + 1) * (a.P + 1) * K * K * sizeof(double);
+  cudaFuncSetAttribute(k_assemble_a<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+  k_assemble_a<K><<<(a.g.N + VOX_THREADS - 1) / VOX_THREADS, VOX_THREADS, shm, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_assemble_w(const AssembleArgs& a, cudaStream_t s) {
+  if (a.g.N <= 0) return cudaSuccess;
+  switch (a.K) {
+#define CASE(k) case k: return assemble_w_k<k>(a, s);
+    BFMRI_K_CASES(CASE)
+#undef CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_assemble_a(const AssembleArgs& a, cudaStream_t s) {
+  if (a.g.N <= 0) return cudaSuccess;
+  switch (a.K) {
+#define CASE(k) case k: return assemble_a_k<k>(a, s);
+    BFMRI_K_CASES(CASE)
+#undef CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_lambda(const LambdaArgs& a, cudaStream_t s) {
+  if (a.g.N <= 0) return cudaSuccess;
+  k_lambda<<<(a.g.N + VOX_THREADS - 1) / VOX_THREADS, VOX_THREADS, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+int hyper_grid(int N) {
+  int g = (N + HYPER_THREADS - 1) / HYPER_THREADS;
+  return g < 1 ? 1 : (g > 1024 ? 1024 : g);
+}
+
+template <int D>
+static cudaError_t hyper_d(const HyperArgs& a, cudaStream_t s) {
+  const int grid = hyper_grid(a.g.N);
+  k_quadform<D><<<grid, HYPER_THREADS, 0, s>>>(a);
+  k_hyper_draw<<<1, 32, 0, s>>>(a, grid);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_hyper(const HyperArgs& a, cudaStream_t s) {
+  switch (a.D) {
+#define CASE(k) case k: return hyper_d<k>(a, s);
+    BFMRI_K_CASES(CASE)
+#undef CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int D>
+static cudaError_t apply_d(const ApplyArgs& a, cudaStream_t s) {
+  k_apply<D><<<(a.g.N + VOX_THREADS - 1) / VOX_THREADS, VOX_THREADS, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_apply(const ApplyArgs& a, cudaStream_t s) {
+  if (a.g.N <= 0) return cudaSuccess;
+  switch (a.D) {
+#define CASE(k) case k: return apply_d<k>(a, s);
+    BFMRI_K_CASES(CASE)
+#undef CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace bfmri

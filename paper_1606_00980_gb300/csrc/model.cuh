@@ -1,0 +1,113 @@
+// Host interface of the per-voxel model kernels: sufficient statistics, assembly of the W and
+// A full conditionals with the Algorithm 2 perturbation, and the Gamma full conditionals.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "device_common.cuh"
+
+namespace bfmri {
+
+constexpr int PMAX = 4;   // largest AR order
+constexpr int KMAX = 12;  // largest number of regressors
+
+// Layout of the per-voxel statistics record (planes of length ld):
+//   Syy[p][q] (p <= q)      plane syy_index(p, q)
+//   Sxy[p][q][k]            plane n_syy(P) + (p (P+1) + q) K + k
+__host__ __device__ inline int n_syy(int P) { return (P + 1) * (P + 2) / 2; }
+__host__ __device__ inline int syy_index(int p, int q, int P) {
+  // row-major over p of the upper triangle p <= q
+  return p * (P + 1) - p * (p - 1) / 2 + (q - p);
+}
+__host__ __device__ inline int n_stats(int K, int P) { return n_syy(P) + K * (P + 1) * (P + 1); }
+
+struct Geometry {
+  int N;
+  size_t ld;
+  int ndir;           // 4 or 6
+  const int* nbr;     // [6][ld]
+  const int* lin;     // [ld] lattice-linear index of each voxel
+  int stride[3];      // lattice-linear strides of +x, +y, +z
+};
+
+struct StatsArgs {
+  int N, T, K, P;
+  size_t ld;
+  const void* Y;      // T x N row-major (float or double)
+  int y_is_f64;
+  const double* X;    // T x K column-major
+  double* stats;      // [n_stats][ld]
+};
+cudaError_t launch_stats(const StatsArgs& a, cudaStream_t s);
+
+// W system: blocks Bd_n = lambda_n X~'X~ + eps I, b_w, block-Jacobi factor of
+// Bd_n + diag(alpha) deg_n, and the perturbed right-hand side of Algorithm 2.
+struct AssembleArgs {
+  Geometry g;
+  int K, P;
+  const double* stats;
+  const double* Sxx;    // [(P+1)^2][K][K] voxel-independent lagged X products
+  const double* W;      // [K][ld]
+  const double* A;      // [P][ld]
+  const double* lam;    // [ld]
+  const double* scale;  // alpha [K] (W system) or beta [P] (A system)
+  double eps;
+  int spatial;          // A system: 1 = beta D_a prior, 0 = independent voxels
+  int perturb;          // 1: rhs = perturbed b; 0: rhs = b_w (mean system)
+  int precond;          // 1: write block-Jacobi factor
+  int g_only;           // A system: compute only the Gram G (for lambda)
+  Rng rng;
+  // outputs
+  double* blocks;       // [ntri(D)][ld]
+  double* mfac;         // [ntri(D)][ld]
+  double* rhs;          // [D][ld]
+  double* bmean;        // [D][ld] (may be null)
+  double* G;            // A system: [n_syy(P)][ld] lagged residual Gram (for lambda)
+  double* x_direct;     // A system, independent prior: if set, the draw is written here
+  int* bad_voxel;       // min index of a voxel whose block failed Cholesky (init INT_MAX)
+};
+cudaError_t launch_assemble_w(const AssembleArgs& a, cudaStream_t s);
+cudaError_t launch_assemble_a(const AssembleArgs& a, cudaStream_t s);
+
+// lambda_n ~ Ga(1/(1/u1 + RSS_n/2), (T-P)/2 + u2) from the Gram of launch_assemble_a.
+struct LambdaArgs {
+  Geometry g;
+  int P, T;
+  double u1, u2;
+  const double* G;
+  const double* A;
+  double* lam;
+  Rng rng;
+  int* exhausted;
+};
+cudaError_t launch_lambda(const LambdaArgs& a, cudaStream_t s);
+
+// alpha / beta: Q_k = sum over edges (v_i - v_j)^2, then Ga(1/(Q_k/2 + 1/prior1), N/2 + prior2).
+struct HyperArgs {
+  Geometry g;
+  int D;
+  const double* V;      // [D][ld]
+  double* part;         // [grid][D] partials (grid = hyper_grid(N))
+  double prior1, prior2;
+  double* out;          // [D]
+  double* Q_out;        // [D] (may be null)
+  Rng rng;
+  int* exhausted;
+};
+cudaError_t launch_hyper(const HyperArgs& a, cudaStream_t s);
+int hyper_grid(int N);
+
+// y = B~ x (inspection).
+struct ApplyArgs {
+  Geometry g;
+  int D;
+  const double* blocks;
+  const double* scale;
+  const double* x;
+  double* y;
+};
+cudaError_t launch_apply(const ApplyArgs& a, cudaStream_t s);
+
+}  // namespace bfmri

@@ -1,0 +1,61 @@
+// Host/device interface of the persistent PCG solver for the block + stencil precision
+//   B~ = blkdiag_n(B_n) + diag(s) (x) D        (paper Eq. wr full conditional; Section 3.1)
+// over the in-mask voxel graph, in voxel-index structure-of-arrays layout: component k of
+// voxel n of a vector lives at v[k * ld + n].
+#pragma once
+
+#include <cstddef>
+#include <cuda_runtime.h>
+
+#include "device_common.cuh"
+
+namespace bfmri {
+
+// Written by CTA 0 at the end of each solve. iter_total and status_any accumulate over
+// solves until the host clears them.
+struct PcgCtrl {
+  int iterations;
+  int restarts;       // FP64: true-residual restarts; mixed: outer refinement steps
+  double rel_res;     // final true relative residual
+  double rel_res0;    // relative residual of the start value
+  int status;         // 0 ok, 3 breakdown (not SPD), 4 max_iter, 7 non-finite
+  int status_any;     // first nonzero status since the last clear
+  long long iter_total;
+  long long solves;
+};
+
+struct PcgArgs {
+  int N;
+  size_t ld;             // plane stride (>= N, multiple of 32)
+  int ndir;              // 4 or 6 neighbour planes used
+  const int* nbr;        // [6][ld] compact neighbour index or -1 (-x,+x,-y,+y,-z,+z)
+  const double* blocks;  // [ntri(D)][ld] data blocks (packed symmetric)
+  const double* mfac;    // [ntri(D)][ld] preconditioner Cholesky factor (inverted diag) or null
+  const double* scale;   // [D] prior scales (alpha or beta)
+  const double* b;       // [D][ld] right-hand side
+  double* x;             // [D][ld] start value in, solution out
+  double* r;             // [D][ld] work
+  double* z;
+  double* q;
+  double* p0;
+  double* p1;
+  double* part;          // [2][grid][4] reduction partials
+  GridBarrier bar;
+  PcgCtrl* ctrl;
+  double delta;          // stop when ||b - B x|| <= delta ||b|| (true residual, FP64)
+  int max_iter;
+  int skip_block;        // test hook (-1 off): this CTA never reaches the first barrier
+  int max_grid;          // rows of each partial buffer: the launch never uses more CTAs
+};
+
+// Launches the cooperative persistent PCG kernel for dimension D (1..12) on `stream`.
+// grid_out (may be null) receives the grid size used.
+cudaError_t launch_pcg(int D, const PcgArgs& a, cudaStream_t stream, int* grid_out);
+
+// Largest grid the cooperative launch of dimension D can use on the current device.
+int pcg_max_grid(int D);
+
+constexpr int PCG_THREADS = 256;
+constexpr int DMAX = 12;
+
+}  // namespace bfmri

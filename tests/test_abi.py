@@ -1,0 +1,75 @@
+"""The C ABI library builds, loads without a GPU and exports every function include/bfmri.h
+declares; the Python binding declares exactly that set (CPU only)."""
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", f)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(bfmri_\w+)\s*\(", src))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1606_00980_gb300 import build
+    build.build()
+    from paper_1606_00980_gb300 import bfmri
+    return bfmri.load_library()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ["bfmri_create", "bfmri_precompute_stats", "bfmri_sample_W",
+                     "bfmri_gibbs_sweep", "bfmri_destroy", "bfmri_last_error"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in sorted(declared_functions()):
+        assert hasattr(lib, name), f"{name} declared in include/ but not exported"
+
+
+def test_binding_matches_header(lib):
+    from paper_1606_00980_gb300 import bfmri
+    bound = {n for n, _, _ in bfmri.SIGNATURES}
+    assert bound == declared_functions()
+
+
+def test_default_options_without_gpu(lib):
+    from paper_1606_00980_gb300 import bfmri
+    o = bfmri.bfmri_default_options()
+    assert (o.q1, o.q2, o.u1, o.u2, o.r1, o.r2) == (10.0, 0.1, 10.0, 0.1, 10000.0, 0.1)
+    assert o.delta == 1e-8 and o.precond == bfmri.PRECOND_BLOCK_JACOBI
+    assert o.debug_skip_block == -1
+
+
+def test_create_rejects_bad_arguments_without_touching_the_gpu(lib):
+    """Host-side validation runs before any device call: these fail with INVALID_ARG."""
+    import numpy as np
+    from paper_1606_00980_gb300 import bfmri
+    mask = np.ones((2, 3, 4), np.uint8)
+    X = np.ones((20, 2))
+    Y = np.ones((20, 24))
+    cases = [((4, 3, 2, 5), mask, X, Y, 2, 1),      # bad neighbourhood
+             ((4, 3, 2, 6), mask, X, Y, 13, 1),     # K too large
+             ((4, 3, 2, 6), mask, X, Y, 2, 5),      # P too large
+             ((4, 3, 2, 6), np.zeros_like(mask), X, Y, 2, 1)]   # empty mask
+    for lat, m, x, y, K, P in cases:
+        with pytest.raises(bfmri.BfmriError) as ei:
+            bfmri.bfmri_create(lat, m, x[:, :K] if K <= 2 else np.ones((20, K)), y, K, P,
+                               torch_memory=False)
+        assert ei.value.status == -1
+    Yn = Y.copy()
+    Yn[3, 5] = np.nan
+    with pytest.raises(bfmri.BfmriError) as ei:
+        bfmri.bfmri_create((4, 3, 2, 6), mask, X, Yn, 2, 1, torch_memory=False)
+    assert ei.value.status == -1 and "non-finite" in str(ei.value)
