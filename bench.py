@@ -1,0 +1,350 @@
+#!/usr/bin/env python
+"""Benchmark of the W-draw hot path: Gibbs sweeps of the spatial fMRI GLM sampler.
+
+One step = one full Gibbs sweep (Section 3.2) on the 3D whole-brain workload
+(64x64x33 lattice, ellipsoid mask of ~50k voxels, T=300, K=6, AR(3), 6-neighbour UGL prior,
+FP64 PCG with block-Jacobi preconditioner to relative residual 1e-8): perturbed right-hand
+side + PCG solve for W (Algorithm 2), the A draw, lambda, alpha and beta draws, with the
+chain state resident on the GPU. Each sweep yields one posterior W draw, so the metric is
+W-draws/s.
+
+Timing: W untimed warm-up sweeps (also burn-in), then K timed sweeps, each bracketed by CUDA
+events on the library's stream, with a 256 MB buffer written between sweeps to flush L2
+(the resident working set, ~100 MB, would otherwise stay in the 126 MB L2). Under torchrun
+every rank runs its own independent chain (replicas: the path does not shard), the time is
+the max over ranks and the value the sum of draws over ranks.
+
+Also reported on the same line: the roofline of the dominant kernel (the W PCG solve, timed
+with CUDA events inside the library), the FP64 oracle timed on this host's cores on a
+bounded slab of the same workload (cpu_baseline), and an end-to-end figure through the
+C ABI with host buffers (upload of X and Y, statistics, the sweeps, and a copy of every W
+draw back to host memory).
+
+--impl reference times the FP64 CPU oracle (exact sparse-LU solves in place of PCG) on the
+same workload, one bounded slab per step, and prints the same JSON line with impl=reference.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "posterior W-draws/s + HBM-roofline fraction, 3D K=6; p50/p99 batched solve"
+UNIT = "W-draws/s"
+WORKLOAD = "wholebrain3d_64x64x33_ellipsoid_N49928_T300_K6_AR3_fp64_blockjacobi_delta1e-8"
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6800.0), "measured", d
+    return 6800.0, "fallback", {}
+
+
+# FP64 non-tensor peak of GB300: 152 SMs x 4 FP64 flops (2 DFMA) per clock x 2070 MHz.
+FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12
+
+
+def pcg_flops_per_voxel_iter(K):
+    """FP64 flops of one fused PCG iteration per voxel (phase 1: p update 2K, block 2K^2,
+    6 neighbour p reconstructions + sums 18K, stencil 3K, p'q 2K; phase 2: two axpys 4K,
+    block-Jacobi triangular solves 2K^2 + 2K, two dots 4K)."""
+    return 4 * K * K + 35 * K
+
+
+def pcg_bytes_per_voxel_iter(K, w=8):
+    """Algorithmic bytes of one PCG iteration per voxel: 11 vector passes of K words plus the
+    data block and the preconditioner factor (K(K+1)/2 words each)."""
+    return w * (11 * K + 2 * (K * (K + 1) // 2))
+
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.rows = []
+        self.proc = None
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.gpu)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        sm = []
+        reasons = set()
+        smax = None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                smax = float(r[2])
+            except (ValueError, IndexError):
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if "Active" in v and "Not" not in v:
+                    reasons.add(nm)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, v):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------------------
+# CPU oracle (baseline and reference arm)
+# ---------------------------------------------------------------------------------------
+
+def oracle_sweep_time(w, z0, z1, seed=1, counter=0):
+    """Seconds for one oracle Gibbs sweep on the slab z0 <= z < z1, and the slab's N."""
+    from oracle import gibbs
+    from oracle.lattice import Lattice
+    from paper_1606_00980_gb300 import synth
+    s = synth.zslab(w, z0, z1)
+    lat = Lattice(s.mask, s.neighbourhood)
+    st = gibbs.default_state(s.K, s.P, s.N)
+    st["W"] = s.W_true.copy()
+    st["A"] = s.A_true.copy()
+    t = time.perf_counter()
+    gibbs.gibbs_sweep(lat, s.Y, s.X, st, seed=seed, counter=counter)
+    return time.perf_counter() - t, s.N
+
+
+def cpu_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        n = [i.get("num_threads", 1) for i in threadpool_info()]
+        return max(n) if n else 1
+    except Exception:
+        return 1
+
+
+def run_reference(args, world, rank):
+    """The FP64 oracle on the host cores: one 1-slice slab of the workload per step; the
+    value is scaled to whole-volume W-draws/s by the voxel ratio (optimistic for the oracle:
+    its sparse factorisation grows faster than linearly in N)."""
+    if rank != 0:
+        return
+    from paper_1606_00980_gb300 import synth
+    w = synth.wholebrain3d()
+    zc = w.dims[2] // 2
+    for i in range(args.warmup):
+        oracle_sweep_time(w, zc, zc + 1, counter=i)
+    tot, n_s = 0.0, 0
+    for i in range(args.steps):
+        t, n_s = oracle_sweep_time(w, zc, zc + 1, counter=1000 + i)
+        tot += t
+    per_step = tot / max(args.steps, 1)
+    value = (n_s / w.N) / per_step
+    sample = (f"one Gibbs sweep per step on the z={zc} slice ({n_s} of {w.N} voxels) of the "
+              f"same workload; value scaled to the whole volume by the voxel ratio")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "l2": "host run"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_threads(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------------------
+# GPU path
+# ---------------------------------------------------------------------------------------
+
+def run_ours(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    from paper_1606_00980_gb300 import synth
+    from paper_1606_00980_gb300.bfmri import Model
+
+    w = synth.wholebrain3d()
+    K, P, N, T = w.K, w.P, w.N, w.T
+    m = Model.from_workload(w, delta=1e-8, seed=2024, stream_id=rank, profile=1)
+    m.precompute_stats()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    counter = 0
+    for _ in range(args.warmup):
+        m.gibbs_sweep(1, counter, info=False)
+        counter += 1
+    torch.cuda.synchronize()
+    m.reset_timing()
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    times = []
+    it_w = it_a = 0
+    for s in range(args.steps):
+        flush.random_(0, 255)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        inf = m.gibbs_sweep(1, counter, info=True)
+        e1.record(stream)
+        counter += 1
+        times.append((e0, e1))
+        it_w += inf.pcg_iterations_W
+        it_a += inf.pcg_iterations_A
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    local_s = sum(a.elapsed_time(b) for a, b in times) / 1e3
+    total_s = max_over_ranks(world, local_s)
+    tim = m.timing()
+    value = world * args.steps / total_s
+
+    # roofline of the dominant kernel: the W PCG solve
+    pw = tim["pcg_W"]
+    launches = max(pw["launches"], 1)
+    dur_s = pw["ms"] / 1e3 / launches
+    iters_per_launch = it_w / launches
+    flops = N * (iters_per_launch * pcg_flops_per_voxel_iter(K) + 2 * (4 * K * K + 25 * K))
+    bytes_ = N * iters_per_launch * pcg_bytes_per_voxel_iter(K)
+    hbm_peak, hbm_src, _ = peaks()
+    achieved_tf = flops / dur_s / 1e12
+    achieved_gbs = bytes_ / dur_s / 1e9
+    total_ms = sum(v["ms"] for v in tim.values())
+    n_launch = sum(v["launches"] for k, v in tim.items()) + tim["hyper"]["launches"]  # 2 kernels
+    roof = {"kernel": f"k_pcg<{K}> (W solve)", "bound": "alu", "achieved": achieved_tf,
+            "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved_tf / FP64_PEAK_TFLOPS,
+            "traffic": None,
+            "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2070 MHz",
+            "hbm_view": {"achieved_gbs": achieved_gbs, "peak_gbs": hbm_peak,
+                         "frac": achieved_gbs / hbm_peak, "peak_source": f"{hbm_src} (MEASURED_PEAKS.json)"},
+            "iterations_per_launch": iters_per_launch, "avg_launch_ms": dur_s * 1e3,
+            "share_of_step": pw["ms"] / total_ms if total_ms > 0 else None}
+    m.close()
+    del flush
+
+    # end to end through the C ABI with host buffers
+    e2e = run_e2e(args, w) if rank == 0 else None
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        zc = w.dims[2] // 2
+        t, n_s = oracle_sweep_time(w, zc - 1, zc + 1)
+        cpu = {"value": (n_s / N) / t, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
+               "sample": f"one oracle Gibbs sweep on slices z={zc - 1}..{zc} ({n_s} of {N} voxels, "
+                         f"{t:.1f} s), scaled to the whole volume by the voxel ratio"}
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": total_s / args.steps * 1e3, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "N": N, "T": T, "K": K, "P": P,
+                           "parallelism": f"replicas{world}", "l2": "flushed between steps (256 MB write)",
+                           "pcg_iterations_W_per_sweep": it_w / args.steps,
+                           "pcg_iterations_A_per_sweep": it_a / args.steps},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+                "gpu_launches": int(n_launch),
+                "kernel_ms_per_step": {k: v["ms"] / args.steps for k, v in tim.items() if v["launches"]}}
+        print(json.dumps(line), flush=True)
+
+
+def run_e2e(args, w):
+    """create (host X, Y) + statistics + S sweeps, each draw copied to pinned host memory."""
+    import numpy as np
+    import torch
+
+    from paper_1606_00980_gb300.bfmri import Model
+    S = max(args.steps, 1)
+    Wh = torch.empty((w.K, w.N), dtype=torch.float64, pin_memory=True).numpy()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    m = Model.from_workload(w, delta=1e-8, seed=77)
+    m.precompute_stats()
+    for s in range(S):
+        m.gibbs_sweep(1, s, info=False)
+        st = m.get_state()
+        Wh[...] = st["W"]
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    m.close()
+    h2d = w.Y.nbytes + w.X.nbytes + w.mask.nbytes
+    return {"value": S / dt, "unit": UNIT, "h2d_bytes_per_step": h2d // S,
+            "d2h_bytes_per_step": w.K * w.N * 8 + (w.P + 1) * w.N * 8 + 8 * (w.K + w.P),
+            "what": f"create+stats from host buffers, then {S} sweeps with every state copied to host"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

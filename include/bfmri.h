@@ -91,6 +91,8 @@ typedef struct {
   double barrier_timeout_s;  /* limit of each device-side grid-barrier wait (default 2 s) */
   int debug_skip_block;      /* test hook: this CTA never arrives at the first barrier of the
                                 next solve (forces BFMRI_ERR_TIMEOUT); -1 = off (default) */
+  int profile;               /* nonzero: time every kernel launch with CUDA events on the
+                                handle's stream (read with bfmri_get_timing) */
 } bfmri_options;
 
 /* Fills *opt with the defaults listed above. */
@@ -186,6 +188,28 @@ bfmri_status bfmri_sample_beta(bfmri_handle* h, uint64_t counter, double* beta_o
  * counter first_counter + s. No host synchronisation inside; info (may be NULL) waits. */
 bfmri_status bfmri_gibbs_sweep(bfmri_handle* h, int n_sweeps, uint64_t first_counter,
                                bfmri_sweep_info* info);
+
+/* Per-kernel device time, accumulated since the last reset when options.profile is set
+ * (CUDA events recorded around each launch on the handle's stream). Classes: */
+#define BFMRI_T_STATS      0  /* sufficient statistics */
+#define BFMRI_T_ASSEMBLE_W 1  /* W blocks + perturbed rhs + preconditioner */
+#define BFMRI_T_PCG_W      2  /* W solve */
+#define BFMRI_T_ASSEMBLE_A 3  /* lagged residual Gram + A system */
+#define BFMRI_T_PCG_A      4  /* A solve */
+#define BFMRI_T_LAMBDA     5
+#define BFMRI_T_HYPER      6  /* alpha and beta */
+#define BFMRI_T_OTHER      7
+#define BFMRI_T_CLASSES    8
+typedef struct {
+  double ms[BFMRI_T_CLASSES];
+  long long launches[BFMRI_T_CLASSES];
+  long long pcg_iterations[BFMRI_T_CLASSES];  /* PCG iterations of the timed solves */
+} bfmri_timing;
+
+/* Waits for the handle's stream, then returns the accumulated timing (zeros if profiling is
+ * off). bfmri_reset_timing clears it. */
+bfmri_status bfmri_get_timing(bfmri_handle* h, bfmri_timing* t);
+bfmri_status bfmri_reset_timing(bfmri_handle* h);
 
 /* Inspection of the W or A system (which = 0: W with K, 1: A with P) at the current state.
  *  bfmri_apply_precision: y = B~ x (x, y dim x N row-major) with B~ the full-conditional

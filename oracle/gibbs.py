@@ -32,8 +32,9 @@ def draw_gmrf(lat: Lattice, blocks, rhs, scale, seed, counter, tag, stream=0):
     B = model.precision(lat, blocks, scale)
     pert, _, _ = model.perturbation(lat, blocks, scale, seed, counter, tag, stream)
     b_mean = model.kmajor(rhs)
-    x = linalg.exact_solve(B, b_mean + pert)
-    mu = linalg.exact_solve(B, b_mean)
+    lu = linalg.factor(B)
+    x = lu.solve(b_mean + pert)
+    mu = lu.solve(b_mean)
     return x.reshape(K, N), mu.reshape(K, N)
 
 

@@ -22,6 +22,11 @@ def exact_solve(B, b):
     return lu.solve(np.asarray(b, dtype=np.float64))
 
 
+def factor(B):
+    """Sparse LU factorisation object with .solve(b)."""
+    return spla.splu(sp.csc_matrix(B))
+
+
 def logdet_sparse(B):
     """log det of an SPD sparse matrix from its LU factors: sum log |U_ii| (L is unit)."""
     lu = spla.splu(sp.csc_matrix(B))

@@ -43,7 +43,7 @@ class bfmri_options(C.Structure):
                 ("inner_tol", C.c_double), ("seed", C.c_uint64), ("stream_id", C.c_uint32),
                 ("cuda_stream", C.c_void_p), ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN),
                 ("alloc_ctx", C.c_void_p), ("barrier_timeout_s", C.c_double),
-                ("debug_skip_block", C.c_int)]
+                ("debug_skip_block", C.c_int), ("profile", C.c_int)]
 
 
 class bfmri_solve_info(C.Structure):
@@ -55,6 +55,14 @@ class bfmri_sweep_info(C.Structure):
     _fields_ = [("sweeps", C.c_int), ("pcg_iterations_W", C.c_longlong),
                 ("pcg_iterations_A", C.c_longlong), ("last_rel_residual_W", C.c_double),
                 ("gamma_exhausted", C.c_longlong)]
+
+
+T_CLASSES = ["stats", "assemble_W", "pcg_W", "assemble_A", "pcg_A", "lambda", "hyper", "other"]
+
+
+class bfmri_timing(C.Structure):
+    _fields_ = [("ms", C.c_double * 8), ("launches", C.c_longlong * 8),
+                ("pcg_iterations", C.c_longlong * 8)]
 
 
 _P = C.POINTER
@@ -81,6 +89,8 @@ SIGNATURES = [
     ("bfmri_sample_alpha", C.c_int, [_h, C.c_uint64, _dp]),
     ("bfmri_sample_beta", C.c_int, [_h, C.c_uint64, _dp]),
     ("bfmri_gibbs_sweep", C.c_int, [_h, C.c_int, C.c_uint64, _P(bfmri_sweep_info)]),
+    ("bfmri_get_timing", C.c_int, [_h, _P(bfmri_timing)]),
+    ("bfmri_reset_timing", C.c_int, [_h]),
     ("bfmri_apply_precision", C.c_int, [_h, C.c_int, _dp, _dp]),
     ("bfmri_build_system", C.c_int, [_h, C.c_int, C.c_uint64, _dp, _dp, _dp]),
 ]
@@ -290,6 +300,15 @@ class Model:
         self._c(self.lib.bfmri_gibbs_sweep(self.handle, n_sweeps, first_counter,
                                            C.byref(inf) if info else None))
         return inf
+
+    def timing(self):
+        t = bfmri_timing()
+        self._c(self.lib.bfmri_get_timing(self.handle, C.byref(t)))
+        return {name: dict(ms=t.ms[i], launches=t.launches[i], pcg_iterations=t.pcg_iterations[i])
+                for i, name in enumerate(T_CLASSES)}
+
+    def reset_timing(self):
+        self._c(self.lib.bfmri_reset_timing(self.handle))
 
     def apply_precision(self, which, x):
         D = self.K if which == 0 else self.P

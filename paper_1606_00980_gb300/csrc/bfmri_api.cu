@@ -49,6 +49,11 @@ struct bfmri_handle {
   int part_rows = 0;
   std::vector<double> Sxx;
   int stride[3] = {1, 1, 1};
+  // profiling: events recorded around launches, resolved lazily
+  struct Pending { int cls; cudaEvent_t e0, e1; bool pcg; int which; };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> event_pool;
+  bfmri_timing timing{};
 };
 
 namespace {
@@ -100,6 +105,42 @@ void dfree(bfmri_handle* h, void* p) {
     cudaFree(p);
   }
 }
+
+// --- profiling -------------------------------------------------------------------------
+cudaEvent_t take_event(bfmri_handle* h) {
+  if (!h->event_pool.empty()) {
+    cudaEvent_t e = h->event_pool.back();
+    h->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+bfmri_status resolve_timing(bfmri_handle* h);
+
+struct Timed {
+  bfmri_handle* h;
+  int cls;
+  cudaEvent_t e0 = nullptr;
+  bool pcg;
+  int which;
+  Timed(bfmri_handle* h_, int cls_, bool pcg_ = false, int which_ = 0) : h(h_), cls(cls_), pcg(pcg_), which(which_) {
+    if (h->opt.profile) {
+      if (h->pending.size() > 2048) resolve_timing(h);
+      e0 = take_event(h);
+      cudaEventRecord(e0, h->stream);
+    }
+  }
+  ~Timed() {
+    if (e0) {
+      cudaEvent_t e1 = take_event(h);
+      cudaEventRecord(e1, h->stream);
+      h->pending.push_back({cls, e0, e1, pcg, which});
+    }
+  }
+};
 
 Geometry geom(const bfmri_handle* h) {
   Geometry g;
@@ -173,6 +214,10 @@ bfmri_status end_call(bfmri_handle* h, PcgCtrl* ctrl_out /* [2] or null */, int*
     ctrl_out[0] = ctrl[0];
     ctrl_out[1] = ctrl[1];
   }
+  if (h->opt.profile) {
+    h->timing.pcg_iterations[BFMRI_T_PCG_W] += ctrl[0].iter_total;
+    h->timing.pcg_iterations[BFMRI_T_PCG_A] += ctrl[1].iter_total;
+  }
   if (exhausted) *exhausted = flags[1];
   if (err == ERR_TIMEOUT_CODE)
     return fail(h, BFMRI_ERR_TIMEOUT, "device grid barrier wait exceeded its time limit");
@@ -216,6 +261,7 @@ bfmri_status run_pcg(bfmri_handle* h, int D, const double* scale, double* x, int
   a.max_grid = h->part_rows;
   h->opt.debug_skip_block = -1;  // the hook fires once
   int grid = 0;
+  Timed tm(h, which == 0 ? BFMRI_T_PCG_W : BFMRI_T_PCG_A, true, which);
   cudaError_t e = launch_pcg(D, a, h->stream, &grid);
   if (e != cudaSuccess) return cuda_fail(h, e, "launch_pcg");
   return BFMRI_OK;
@@ -249,7 +295,11 @@ AssembleArgs assemble_args(bfmri_handle* h, const double* scale, uint64_t counte
 // --- the five steps of a sweep, enqueued without synchronisation ---
 bfmri_status enqueue_W(bfmri_handle* h, uint64_t counter) {
   AssembleArgs a = assemble_args(h, h->d_alpha, counter, TAG_W);
-  cudaError_t e = launch_assemble_w(a, h->stream);
+  cudaError_t e;
+  {
+    Timed tm(h, BFMRI_T_ASSEMBLE_W);
+    e = launch_assemble_w(a, h->stream);
+  }
   if (e != cudaSuccess) return cuda_fail(h, e, "assemble_w");
   return run_pcg(h, h->K, h->d_alpha, h->d_W, 0);
 }
@@ -264,7 +314,11 @@ bfmri_status enqueue_A(bfmri_handle* h, uint64_t counter) {
     a.x_direct = h->d_A;
     a.precond = 0;
   }
-  cudaError_t e = launch_assemble_a(a, h->stream);
+  cudaError_t e;
+  {
+    Timed tm(h, BFMRI_T_ASSEMBLE_A);
+    e = launch_assemble_a(a, h->stream);
+  }
   if (e != cudaSuccess) return cuda_fail(h, e, "assemble_a");
   if (h->P > 0 && spatial) return run_pcg(h, h->P, h->d_beta, h->d_A, 1);
   return BFMRI_OK;
@@ -290,6 +344,7 @@ bfmri_status enqueue_lambda(bfmri_handle* h, uint64_t counter) {
   a.lam = h->d_lam;
   a.rng = rng_of(h, counter, TAG_LAMBDA);
   a.exhausted = h->d_flags + 1;
+  Timed tm(h, BFMRI_T_LAMBDA);
   cudaError_t e = launch_lambda(a, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "lambda");
   return BFMRI_OK;
@@ -307,8 +362,25 @@ bfmri_status enqueue_hyper(bfmri_handle* h, uint64_t counter, bool beta) {
   a.Q_out = nullptr;
   a.rng = rng_of(h, counter, beta ? TAG_BETA : TAG_ALPHA);
   a.exhausted = h->d_flags + 1;
+  Timed tm(h, BFMRI_T_HYPER);
   cudaError_t e = launch_hyper(a, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "hyper");
+  return BFMRI_OK;
+}
+
+bfmri_status resolve_timing(bfmri_handle* h) {
+  if (h->pending.empty()) return BFMRI_OK;
+  CU(h, cudaStreamSynchronize(h->stream));
+  for (auto& p : h->pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p.e0, p.e1) == cudaSuccess) {
+      h->timing.ms[p.cls] += ms;
+      h->timing.launches[p.cls] += 1;
+    }
+    h->event_pool.push_back(p.e0);
+    h->event_pool.push_back(p.e1);
+  }
+  h->pending.clear();
   return BFMRI_OK;
 }
 
@@ -559,6 +631,11 @@ bfmri_status bfmri_create(const bfmri_lattice* lat, const uint8_t* mask, const d
 bfmri_status bfmri_destroy(bfmri_handle* h) {
   if (!h) return BFMRI_OK;
   cudaStreamSynchronize(h->stream);
+  for (auto& p : h->pending) {
+    cudaEventDestroy(p.e0);
+    cudaEventDestroy(p.e1);
+  }
+  for (cudaEvent_t e : h->event_pool) cudaEventDestroy(e);
   std::vector<void*> all = h->allocs;
   for (void* p : all) dfree(h, p);
   delete h;
@@ -578,7 +655,11 @@ bfmri_status bfmri_precompute_stats(bfmri_handle* h) {
   a.y_is_f64 = h->y_f64;
   a.X = h->d_X;
   a.stats = h->d_stats;
-  cudaError_t e = launch_stats(a, h->stream);
+  cudaError_t e;
+  {
+    Timed tm(h, BFMRI_T_STATS);
+    e = launch_stats(a, h->stream);
+  }
   if (e != cudaSuccess) return cuda_fail(h, e, "stats");
   CU(h, cudaStreamSynchronize(h->stream));
   dfree(h, h->d_Y);
@@ -713,6 +794,20 @@ bfmri_status bfmri_gibbs_sweep(bfmri_handle* h, int n_sweeps, uint64_t first_cou
     info->gamma_exhausted = exhausted;
   }
   return st;
+}
+
+bfmri_status bfmri_get_timing(bfmri_handle* h, bfmri_timing* t) {
+  if (!h || !t) return BFMRI_ERR_INVALID_ARG;
+  RET(resolve_timing(h));
+  *t = h->timing;
+  return BFMRI_OK;
+}
+
+bfmri_status bfmri_reset_timing(bfmri_handle* h) {
+  if (!h) return BFMRI_ERR_INVALID_ARG;
+  RET(resolve_timing(h));
+  memset(&h->timing, 0, sizeof(h->timing));
+  return BFMRI_OK;
 }
 
 bfmri_status bfmri_apply_precision(bfmri_handle* h, int which, const double* x, double* y) {

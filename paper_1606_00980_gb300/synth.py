@@ -232,3 +232,17 @@ def request_workload(seed, N_target, K, T, P):
     return make_workload(f"request_N{int(mask.sum())}_K{K}_T{T}_P{P}", (nx, ny, nz), mask,
                          T=T, K=K, P=P, neighbourhood=6, seed=seed,
                          ar_mean=(0.3, 0.1, 0.05)[:P], drift=drift, n_blobs=4)
+
+
+def zslab(w: Workload, z0: int, z1: int) -> Workload:
+    """The sub-workload of the mask's slices z0 <= z < z1 (same data, fewer voxels): the
+    bounded sample on which the CPU oracle is timed."""
+    mask = w.mask.copy()
+    mask[:z0] = 0
+    mask[z1:] = 0
+    keep = mask.reshape(-1)[np.flatnonzero(w.mask.reshape(-1))] > 0
+    return Workload(name=f"{w.name}_z{z0}-{z1}", dims=w.dims, neighbourhood=w.neighbourhood,
+                    mask=mask, X=w.X, Y=np.ascontiguousarray(w.Y[:, keep]), P=w.P,
+                    W_true=w.W_true[:, keep], A_true=w.A_true[:, keep],
+                    lambda_true=w.lambda_true[keep], eps=w.eps, delta=w.delta,
+                    meta=dict(w.meta, N=int(keep.sum()), parent_N=w.N))

@@ -98,11 +98,21 @@ def test_system_and_perturbation(case, which):
     else:
         Bd, bw = model.a_blocks_direct(w.Y, w.X, s["W"], s["lam"], w.P)
         scale, tag = s["beta"], philox.TAG_A
-    assert np.max(np.abs(blocks - Bd)) <= 1e-12 * np.abs(Bd).max()
-    assert np.max(np.abs(bmean - bw.T)) <= 1e-12 * np.abs(bw).max()
+    if which == 0:
+        tol_b, tol_r = 1e-12 * np.abs(Bd).max(), 1e-12 * np.abs(bw).max()
+    else:
+        # the A system is a difference of lagged y'y products (~T * 100^2 for fMRI-scaled
+        # data) that cancel to the residual scale; bound the error by the summands' size
+        yy = (s["lam"] * st["Syy"][:, 0, 0]).max()
+        tol_b = tol_r = 1e-12 * yy
+    assert np.max(np.abs(blocks - Bd)) <= tol_b
+    assert np.max(np.abs(bmean - bw.T)) <= tol_r
     pert, _, _ = model.perturbation(lat, Bd, scale, SEED, 21, tag)
-    ref = model.kmajor(bw) + pert
-    assert rel(bpert, ref.reshape(bpert.shape)) <= 1e-12
+    ref = (model.kmajor(bw) + pert).reshape(bpert.shape)
+    if which == 0:
+        assert rel(bpert, ref) <= 1e-12
+    else:
+        assert np.max(np.abs(bpert - ref)) <= tol_r + 1e-12 * np.abs(ref).max()
     m.close()
 
 
@@ -122,7 +132,12 @@ def test_apply_precision(case, which):
         Bd, _ = model.a_blocks_direct(w.Y, w.X, s["W"], s["lam"], w.P)
         B = model.precision(lat, Bd, s["beta"])
     ref = (B @ x.reshape(-1)).reshape(D, w.N)
-    assert rel(y, ref) <= 1e-13
+    if which == 0:
+        assert rel(y, ref) <= 1e-13
+    else:
+        # cancellation-limited blocks (see test_system_and_perturbation)
+        yy = (s["lam"] * st["Syy"][:, 0, 0]).max()
+        assert np.max(np.abs(y - ref)) <= 1e-12 * yy * np.abs(x).max() * D + 1e-13 * np.abs(ref).max()
     m.close()
 
 
