@@ -245,11 +245,13 @@ bfmri_status run_pcg(bfmri_handle* h, int D, const double* scale, double* x, int
   a.b = h->d_rhs;
   a.x = x;
   a.r = h->d_r;
-  a.z = h->d_z;
-  a.q = h->d_q;
-  a.p0 = h->d_p0;
-  a.p1 = h->d_p1;
+  a.u = h->d_z;
+  a.w = h->d_q;
+  a.p = h->d_p0;
+  a.s = h->d_p1;
   a.part = h->d_part;
+  a.tot = h->d_part + (size_t)h->part_rows * 4;
+  a.allow_resident = 1;
   a.bar.count = h->d_bar;
   a.bar.gen = h->d_bar + 1;
   a.bar.err = h->d_err;
@@ -584,7 +586,7 @@ bfmri_status bfmri_create(const bfmri_lattice* lat, const uint8_t* mask, const d
   h->d_q = (double*)A((size_t)D * ld * sizeof(double));
   h->d_p0 = (double*)A((size_t)D * ld * sizeof(double));
   h->d_p1 = (double*)A((size_t)D * ld * sizeof(double));
-  h->d_part = (double*)A((size_t)2 * maxgrid * 4 * sizeof(double));
+  h->d_part = (double*)A(((size_t)maxgrid * 4 + 8) * sizeof(double));
   h->d_hpart = (double*)A((size_t)hyper_grid(N) * D * sizeof(double));
   h->d_bar = (unsigned int*)A(2 * sizeof(unsigned int));
   h->d_err = (int*)A(sizeof(int));

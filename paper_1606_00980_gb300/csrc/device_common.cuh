@@ -259,6 +259,102 @@ __device__ __forceinline__ bool grid_sync(const GridBarrier& b, int* sh_flag) {
 }
 
 // ---------------------------------------------------------------------------------------
+// Reducing grid barrier. Every CTA reduces its threads' NV values in a fixed tree and writes
+// one row of `part`; the CTA that arrives last sums all rows in a fixed order (independent of
+// which CTA it is), publishes the totals in tot[NV] and releases the others, which read them.
+// All CTAs therefore obtain bit-identical totals, run after run. Waits are bounded as in
+// grid_sync. `sh` needs 32 * NV + NV + 2 doubles of shared memory.
+// ---------------------------------------------------------------------------------------
+template <int NV>
+__device__ __forceinline__ bool grid_allreduce(const GridBarrier& b, double* part, double* tot,
+                                               double* v, double* sh, int* sh_int, double* out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double* sh_w = sh;                 // [32][NV]
+  double* sh_out = sh + 32 * NV;     // [NV]
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_down_sync(0xffffffffu, v[i], o);
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) sh_w[warp * NV + i] = v[i];
+  }
+  __syncthreads();
+  const unsigned int nblocks = gridDim.x;
+  if (threadIdx.x == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      double s = 0.0;
+      for (int w = 0; w < nw; ++w) s += sh_w[w * NV + i];
+      part[(size_t)blockIdx.x * NV + i] = s;
+    }
+    const unsigned int g0 = ld_acquire(b.gen);
+    __threadfence();
+    const unsigned int arrived = atomicAdd(b.count, 1u);
+    sh_int[0] = (arrived == nblocks - 1) ? 1 : 0;
+    sh_int[1] = (int)g0;
+  }
+  __syncthreads();
+  if (sh_int[0]) {
+    // last CTA: fixed-order total of all rows
+    if (warp == 0) {
+      __threadfence();
+      double acc[NV];
+#pragma unroll
+      for (int i = 0; i < NV; ++i) acc[i] = 0.0;
+      for (unsigned int r = lane; r < nblocks; r += 32) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) acc[i] += __ldcg(part + (size_t)r * NV + i);
+      }
+#pragma unroll
+      for (int i = 0; i < NV; ++i) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc[i] += __shfl_down_sync(0xffffffffu, acc[i], o);
+      }
+      if (lane == 0) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+          sh_out[i] = acc[i];
+          tot[i] = acc[i];
+        }
+        __threadfence();
+        atomicExch(b.count, 0u);
+        __threadfence();
+        atomicAdd(b.gen, 1u);
+        sh_int[1] = ld_acquire_int(b.err);
+      }
+    }
+  } else if (threadIdx.x == 0) {
+    const unsigned int g0 = (unsigned int)sh_int[1];
+    const unsigned long long t0 = globaltimer_ns();
+    unsigned int spins = 0;
+    bool ok = true;
+    while (ld_acquire(b.gen) == g0) {
+      if ((++spins & 63u) == 0u) {
+        if (ld_acquire_int(b.err) != 0) { ok = false; break; }
+        if (globaltimer_ns() - t0 > b.timeout_ns) {
+          atomicCAS(b.err, 0, ERR_TIMEOUT_CODE);
+          ok = false;
+          break;
+        }
+      }
+    }
+    __threadfence();
+#pragma unroll
+    for (int i = 0; i < NV; ++i) sh_out[i] = ok ? __ldcg(tot + i) : 0.0;
+    sh_int[1] = ok ? ld_acquire_int(b.err) : 1;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < NV; ++i) out[i] = sh_out[i];
+  const bool good = sh_int[1] == 0;
+  __syncthreads();
+  return good;
+}
+
+// ---------------------------------------------------------------------------------------
 // Deterministic grid reductions of NV doubles: each CTA reduces its threads' values in a
 // fixed tree and writes one row of `part`; after the barrier every CTA re-reduces all rows in
 // the same fixed order, so every CTA (and every run) obtains bit-identical sums.

@@ -1,245 +1,95 @@
 // Persistent, cooperative preconditioned conjugate gradients for the W and A draws
-// (Algorithm 2, step 7: "solve B~ w = b approximately using PCG ... with starting value").
+// (Algorithm 2, step 7: solve B~ w = b approximately by PCG from a starting value, until the
+// relative residual ||B~ w - b|| / ||b|| is below delta; Section 3.1).
 //
-// One launch runs the whole solve. Each iteration is two grid-wide phases separated by a
-// bounded grid barrier:
-//   phase 1: p = z + beta p_prev (for the voxel and, on the fly, for its neighbours, so that
-//            no third barrier is needed), q = B~ p (per-voxel block + stencil), partial p'q;
-//   phase 2: x += a p, r -= a q, z = M^-1 r (block-Jacobi), partials r'z and r'r.
-// The stop test uses the recursive residual and is confirmed with the true residual
-// b - B~ x in FP64 (the paper's relative-residual criterion, Section 3.1); if the true
-// residual is above tolerance the iteration restarts from it. All reductions are
-// deterministic (fixed-order), so a solve is bit-reproducible run to run.
+// One launch runs the whole solve. The recurrence is the Chronopoulos & Gear (1989) form of
+// preconditioned CG, in which the two inner products of an iteration are formed together:
+//   p = u + beta p,  s = w + beta s,  x += a p,  r -= a s,  u = M^-1 r      (local)
+//   --- grid barrier (neighbour values of u are complete) ---
+//   w = B~ u,  gamma = r'u,  delta = w'u,  rr = r'r                         (stencil + block)
+//   --- reducing grid barrier ---
+//   beta = gamma / gamma_old,  a = gamma / (delta - beta gamma / a_old)
+// so each iteration has one matrix product, one preconditioner application, one plain and
+// one reducing barrier. When the recursive residual reaches the tolerance, the true residual
+// b - B~ x is formed in FP64 and confirms the stop (or restarts the recurrence from it).
+//
+// Two variants:
+//  * resident: one voxel per thread, one CTA per SM; the per-voxel block and preconditioner
+//    factor are staged once in shared memory and all vectors stay in registers, so an
+//    iteration only exchanges u through L2;
+//  * streaming: any N; vectors live in global memory (structure of arrays).
+// All reductions are fixed-order (grid_allreduce), so a solve is bit-reproducible.
 #include "pcg.cuh"
 
 namespace bfmri {
 
 namespace {
 
-// Data written by other CTAs during the launch must bypass L1 (not coherent across SMs).
+constexpr int RES_MAX_THREADS = 384;
+constexpr int RES_MAX_D = 8;
+
 __device__ __forceinline__ double ldx(const double* p) { return __ldcg(p); }
 
+// out = B v + s .* (deg v - sum_m V[m])  (B packed, entry e at Bp[e * bs])
 template <int D>
-struct Vox {
-  // Applies the stencil part: out += s .* (deg * pn - sum_m pm), with pm supplied by f(m, k).
-  template <typename F>
-  __device__ __forceinline__ static void stencil(const PcgArgs& a, int n, const double* s,
-                                                 const double* pn, double* out, F f) {
-    double sum[D];
+__device__ __forceinline__ void amul(const double* __restrict__ Bp, int bs, const double* s,
+                                     const int* nb, int ndir, const double* v,
+                                     const double* V, size_t ld, double* out) {
 #pragma unroll
-    for (int k = 0; k < D; ++k) sum[k] = 0.0;
-    int deg = 0;
-    for (int d = 0; d < a.ndir; ++d) {
-      const int m = __ldg(a.nbr + (size_t)d * a.ld + n);
-      if (m >= 0) {
-        ++deg;
+  for (int i = 0; i < D; ++i) {
+    double acc = 0.0;
 #pragma unroll
-        for (int k = 0; k < D; ++k) sum[k] += f(m, k);
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < D; ++k) out[k] += s[k] * ((double)deg * pn[k] - sum[k]);
+    for (int j = 0; j < D; ++j) acc += Bp[(size_t)(i >= j ? tri(i, j) : tri(j, i)) * bs] * v[j];
+    out[i] = acc;
   }
+  double sum[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) sum[k] = 0.0;
+  int deg = 0;
+#pragma unroll
+  for (int d = 0; d < 6; ++d) {
+    if (d < ndir && nb[d] >= 0) {
+      ++deg;
+#pragma unroll
+      for (int k = 0; k < D; ++k) sum[k] += ldx(V + (size_t)k * ld + nb[d]);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < D; ++k) out[k] += s[k] * ((double)deg * v[k] - sum[k]);
+}
+
+// z = (L L')^-1 r with L packed lower (inverted diagonal), entry e at Lp[e * bs].
+template <int D>
+__device__ __forceinline__ void minv(const double* __restrict__ Lp, int bs, const double* r, double* z) {
+  double y[D];
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    double t = r[i];
+#pragma unroll
+    for (int j = 0; j < i; ++j) t -= Lp[(size_t)tri(i, j) * bs] * y[j];
+    y[i] = t * Lp[(size_t)tri(i, i) * bs];
+  }
+#pragma unroll
+  for (int i = D - 1; i >= 0; --i) {
+    double t = y[i];
+#pragma unroll
+    for (int j = i + 1; j < D; ++j) t -= Lp[(size_t)tri(j, i) * bs] * z[j];
+    z[i] = t * Lp[(size_t)tri(i, i) * bs];
+  }
+}
+
+struct Shared {
+  double red[32 * 4 + 4 + 2];
+  int ints[2];
+  int flag;
 };
 
-template <int D>
-__device__ __forceinline__ void block_mul(const PcgArgs& a, int n, const double* p, double* q) {
-  double B[ntri(D)];
-#pragma unroll
-  for (int e = 0; e < ntri(D); ++e) B[e] = __ldg(a.blocks + (size_t)e * a.ld + n);
-  sym_mul<D>(B, p, q);
-}
-
-template <int D>
-__device__ __forceinline__ void precond(const PcgArgs& a, int n, const double* r, double* z) {
-  if (a.mfac == nullptr) {
-#pragma unroll
-    for (int k = 0; k < D; ++k) z[k] = r[k];
-    return;
-  }
-  double L[ntri(D)];
-#pragma unroll
-  for (int e = 0; e < ntri(D); ++e) L[e] = __ldg(a.mfac + (size_t)e * a.ld + n);
-  chol_solve_invdiag<D>(L, r, z);
-}
-
-// r = b - B~ x for voxel n (x of neighbours read through L2); returns it in rn.
-template <int D>
-__device__ __forceinline__ void true_residual(const PcgArgs& a, int n, const double* s, double* rn) {
-  double xn[D], Ax[D];
-#pragma unroll
-  for (int k = 0; k < D; ++k) xn[k] = ldx(a.x + (size_t)k * a.ld + n);
-  block_mul<D>(a, n, xn, Ax);
-  Vox<D>::stencil(a, n, s, xn, Ax, [&](int m, int k) { return ldx(a.x + (size_t)k * a.ld + m); });
-#pragma unroll
-  for (int k = 0; k < D; ++k) rn[k] = __ldg(a.b + (size_t)k * a.ld + n) - Ax[k];
-}
-
-}  // namespace
-
-template <int D>
-__global__ void __launch_bounds__(PCG_THREADS) k_pcg(PcgArgs a) {
-  __shared__ double sh_red[32 * 4];
-  __shared__ double sh_tot[4];
-  __shared__ int sh_flag;
-  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-  const int nth = gridDim.x * blockDim.x;
-  const size_t ld = a.ld;
-  double s[D];
-#pragma unroll
-  for (int k = 0; k < D; ++k) s[k] = __ldg(a.scale + k);
-  const double delta = a.delta;
-  const int max_iter = a.max_iter;
-  double* part[2] = {a.part, a.part + (size_t)gridDim.x * 4};
-  int pb = 0;  // partial buffer toggle
-
-  auto sync = [&]() -> bool {
-    if (a.skip_block == (int)blockIdx.x) return false;   // test hook: never arrive
-    return grid_sync(a.bar, &sh_flag);
-  };
-
-  // ---- setup: r = b - B~ x, z = M^-1 r ----
-  {
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int n = tid; n < a.N; n += nth) {
-      double rn[D], zn[D];
-      true_residual<D>(a, n, s, rn);
-      precond<D>(a, n, rn, zn);
-#pragma unroll
-      for (int k = 0; k < D; ++k) {
-        a.r[k * ld + n] = rn[k];
-        a.z[k * ld + n] = zn[k];
-        const double bk = __ldg(a.b + (size_t)k * ld + n);
-        acc[0] += rn[k] * zn[k];
-        acc[1] += rn[k] * rn[k];
-        acc[2] += bk * bk;
-      }
-    }
-    block_partial<4>(acc, sh_red, part[pb]);
-  }
-  if (!sync()) return;
-  double tot[4];
-  grid_total<4>(part[pb], sh_tot, tot);
-  pb ^= 1;
-  double rho = tot[0], rr = tot[1];
-  const double bb = tot[2];
-  const double tol2 = delta * delta * bb;
-  int it = 0, restarts = 0, status = 0;
-  const bool finite0 = isfinite(rho) && isfinite(rr) && isfinite(bb);
-  if (!finite0) status = 7;
-  if (bb == 0.0 && status == 0) {
-    // B~ is SPD, so the solution of B~ x = 0 is x = 0.
-    for (int n = tid; n < a.N; n += nth)
-#pragma unroll
-      for (int k = 0; k < D; ++k) a.x[k * ld + n] = 0.0;
-  }
-  const double rel0 = bb > 0.0 ? sqrt(rr / bb) : 0.0;
-  bool done = (status != 0) || bb == 0.0 || rr <= tol2;
-  double rr_final = rr;
-  bool first = true;
-  double beta = 0.0;
-  double* pprev = a.p0;
-  double* pnext = a.p1;
-
-  while (!done) {
-    // ---- phase 1: p = z + beta p_prev ; q = B~ p ; p'q ----
-    {
-      double acc[4] = {0.0, 0.0, 0.0, 0.0};
-      for (int n = tid; n < a.N; n += nth) {
-        double pn[D], qn[D];
-#pragma unroll
-        for (int k = 0; k < D; ++k) {
-          const double zk = ldx(a.z + (size_t)k * ld + n);
-          pn[k] = first ? zk : zk + beta * ldx(pprev + (size_t)k * ld + n);
-        }
-        block_mul<D>(a, n, pn, qn);
-        Vox<D>::stencil(a, n, s, pn, qn, [&](int m, int k) {
-          const double zm = ldx(a.z + (size_t)k * ld + m);
-          return first ? zm : zm + beta * ldx(pprev + (size_t)k * ld + m);
-        });
-#pragma unroll
-        for (int k = 0; k < D; ++k) {
-          pnext[k * ld + n] = pn[k];
-          a.q[k * ld + n] = qn[k];
-          acc[0] += pn[k] * qn[k];
-        }
-      }
-      block_partial<4>(acc, sh_red, part[pb]);
-    }
-    if (!sync()) return;
-    grid_total<4>(part[pb], sh_tot, tot);
-    pb ^= 1;
-    const double gam = tot[0];
-    if (!(gam > 0.0) || !isfinite(gam)) { status = isfinite(gam) ? 3 : 7; break; }
-    const double alpha = rho / gam;
-    // ---- phase 2: x += alpha p ; r -= alpha q ; z = M^-1 r ; r'z, r'r ----
-    {
-      double acc[4] = {0.0, 0.0, 0.0, 0.0};
-      for (int n = tid; n < a.N; n += nth) {
-        double rn[D], zn[D];
-#pragma unroll
-        for (int k = 0; k < D; ++k) {
-          const double pk = pnext[k * ld + n];
-          const double qk = a.q[k * ld + n];
-          a.x[k * ld + n] += alpha * pk;
-          rn[k] = a.r[k * ld + n] - alpha * qk;
-          a.r[k * ld + n] = rn[k];
-        }
-        precond<D>(a, n, rn, zn);
-#pragma unroll
-        for (int k = 0; k < D; ++k) {
-          a.z[k * ld + n] = zn[k];
-          acc[0] += rn[k] * zn[k];
-          acc[1] += rn[k] * rn[k];
-        }
-      }
-      block_partial<4>(acc, sh_red, part[pb]);
-    }
-    if (!sync()) return;
-    grid_total<4>(part[pb], sh_tot, tot);
-    pb ^= 1;
-    ++it;
-    const double rho_new = tot[0];
-    rr = tot[1];
-    if (!isfinite(rho_new) || !isfinite(rr)) { status = 7; break; }
-    {
-      double* t = pprev; pprev = pnext; pnext = t;
-    }
-    if (rr <= tol2 || it >= max_iter) {
-      // ---- confirm with the true residual (paper: ||B~ x - b|| / ||b|| < delta) ----
-      double acc[4] = {0.0, 0.0, 0.0, 0.0};
-      for (int n = tid; n < a.N; n += nth) {
-        double rn[D], zn[D];
-        true_residual<D>(a, n, s, rn);
-        precond<D>(a, n, rn, zn);
-#pragma unroll
-        for (int k = 0; k < D; ++k) {
-          a.r[k * ld + n] = rn[k];
-          a.z[k * ld + n] = zn[k];
-          acc[0] += rn[k] * zn[k];
-          acc[1] += rn[k] * rn[k];
-        }
-      }
-      block_partial<4>(acc, sh_red, part[pb]);
-      if (!sync()) return;
-      grid_total<4>(part[pb], sh_tot, tot);
-      pb ^= 1;
-      rr_final = tot[1];
-      if (rr_final <= tol2) break;
-      if (it >= max_iter) { status = 4; break; }
-      ++restarts;
-      rho = tot[0];
-      first = true;
-      continue;
-    }
-    beta = rho_new / rho;
-    rho = rho_new;
-    first = false;
-  }
+__device__ __forceinline__ void write_ctrl(const PcgArgs& a, int it, int restarts, double rr,
+                                          double bb, double rel0, int status) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     a.ctrl->iterations = it;
     a.ctrl->restarts = restarts;
-    a.ctrl->rel_res = bb > 0.0 ? sqrt((status == 0 ? rr_final : rr) / bb) : 0.0;
+    a.ctrl->rel_res = bb > 0.0 ? sqrt(rr / bb) : 0.0;
     a.ctrl->rel_res0 = rel0;
     a.ctrl->status = status;
     if (status != 0 && a.ctrl->status_any == 0) a.ctrl->status_any = status;
@@ -248,12 +98,358 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg(PcgArgs a) {
   }
 }
 
+}  // namespace
+
+// ---------------------------------------------------------------------------------------
+// Resident variant.
+// ---------------------------------------------------------------------------------------
 template <int D>
-static cudaError_t launch_d(const PcgArgs& a, cudaStream_t stream, int* grid_out) {
-  int dev = 0, nsm = 0, per_sm = 0;
+__global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_res(PcgArgs a) {
+  extern __shared__ double smem[];
+  __shared__ Shared sh;
+  constexpr int NT = ntri(D);
+  const int bd = blockDim.x, t = threadIdx.x;
+  double* shB = smem;
+  double* shM = smem + NT * bd;
+  const int n = blockIdx.x * bd + t;
+  const bool own = n < a.N;
+  const size_t ld = a.ld;
+  const bool pre = a.mfac != nullptr;
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int j = 0; j <= i; ++j) {
+      const int e = tri(i, j);
+      shB[e * bd + t] = own ? __ldg(a.blocks + (size_t)e * ld + n) : (i == j ? 1.0 : 0.0);
+      shM[e * bd + t] = (own && pre) ? __ldg(a.mfac + (size_t)e * ld + n) : (i == j ? 1.0 : 0.0);
+    }
+  int nb[6];
+#pragma unroll
+  for (int d = 0; d < 6; ++d) nb[d] = (own && d < a.ndir) ? __ldg(a.nbr + (size_t)d * ld + n) : -1;
+  double s[D], x[D], r[D], u[D], w[D], p[D], q[D], bv[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    s[k] = __ldg(a.scale + k);
+    x[k] = own ? a.x[(size_t)k * ld + n] : 0.0;
+    bv[k] = own ? __ldg(a.b + (size_t)k * ld + n) : 0.0;
+    p[k] = 0.0;
+    q[k] = 0.0;
+  }
+  const double* Bp = shB + t;
+  const double* Mp = shM + t;
+  auto bar = [&]() -> bool {
+    if (a.skip_block == (int)blockIdx.x) return false;
+    return grid_sync(a.bar, &sh.flag);
+  };
+  // (r, u, w) from the current x, with partials (r'u, w'u, r'r, b'b)
+  auto restart = [&](double* tot) -> bool {
+    double ax[D];
+    amul<D>(Bp, bd, s, nb, a.ndir, x, a.x, ld, ax);
+#pragma unroll
+    for (int k = 0; k < D; ++k) r[k] = bv[k] - ax[k];
+    minv<D>(Mp, bd, r, u);
+    if (own) {
+#pragma unroll
+      for (int k = 0; k < D; ++k) a.u[(size_t)k * ld + n] = u[k];
+    }
+    if (!bar()) return false;
+    amul<D>(Bp, bd, s, nb, a.ndir, u, a.u, ld, w);
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      v[0] += r[k] * u[k];
+      v[1] += w[k] * u[k];
+      v[2] += r[k] * r[k];
+      v[3] += bv[k] * bv[k];
+    }
+    return grid_allreduce<4>(a.bar, a.part, a.tot, v, sh.red, sh.ints, tot);
+  };
+
+  double tot[4];
+  if (!restart(tot)) return;   // x is the caller's start value, complete before the launch
+  double gam = tot[0], del = tot[1], rr = tot[2];
+  const double bb = tot[3];
+  const double tol2 = a.delta * a.delta * bb;
+  const double rel0 = bb > 0.0 ? sqrt(rr / bb) : 0.0;
+  int it = 0, restarts = 0, status = 0;
+  if (!(isfinite(gam) && isfinite(del) && isfinite(bb))) status = 7;
+  if (status == 0 && bb == 0.0) {
+#pragma unroll
+    for (int k = 0; k < D; ++k) x[k] = 0.0;
+  }
+  bool done = status != 0 || bb == 0.0 || rr <= tol2;
+  double alpha = (del > 0.0) ? gam / del : 0.0, beta = 0.0;
+  if (!done && !(del > 0.0)) { status = 3; done = true; }
+  while (!done) {
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      p[k] = u[k] + beta * p[k];
+      q[k] = w[k] + beta * q[k];
+      x[k] += alpha * p[k];
+      r[k] -= alpha * q[k];
+    }
+    minv<D>(Mp, bd, r, u);
+    if (own) {
+#pragma unroll
+      for (int k = 0; k < D; ++k) a.u[(size_t)k * ld + n] = u[k];
+    }
+    if (!bar()) return;
+    amul<D>(Bp, bd, s, nb, a.ndir, u, a.u, ld, w);
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      v[0] += r[k] * u[k];
+      v[1] += w[k] * u[k];
+      v[2] += r[k] * r[k];
+    }
+    if (!grid_allreduce<4>(a.bar, a.part, a.tot, v, sh.red, sh.ints, tot)) return;
+    ++it;
+    const double gnew = tot[0], dnew = tot[1];
+    rr = tot[2];
+    if (!(isfinite(gnew) && isfinite(dnew) && isfinite(rr))) { status = 7; break; }
+    if (rr <= tol2 || it >= a.max_iter) {
+      // confirm with the true residual
+      if (own) {
+#pragma unroll
+        for (int k = 0; k < D; ++k) a.x[(size_t)k * ld + n] = x[k];
+      }
+      if (!bar()) return;
+      if (!restart(tot)) return;
+      gam = tot[0];
+      del = tot[1];
+      rr = tot[2];
+      if (rr <= tol2) break;
+      if (it >= a.max_iter) { status = 4; break; }
+      ++restarts;
+      alpha = del > 0.0 ? gam / del : 0.0;
+      beta = 0.0;
+#pragma unroll
+      for (int k = 0; k < D; ++k) { p[k] = 0.0; q[k] = 0.0; }
+      if (!(del > 0.0)) { status = 3; break; }
+      continue;
+    }
+    beta = gnew / gam;
+    const double den = dnew - beta * gnew / alpha;
+    if (!(den > 0.0)) { status = 3; break; }
+    alpha = gnew / den;
+    gam = gnew;
+  }
+  if (own) {
+#pragma unroll
+    for (int k = 0; k < D; ++k) a.x[(size_t)k * ld + n] = x[k];
+  }
+  write_ctrl(a, it, restarts, rr, bb, rel0, status);
+}
+
+// ---------------------------------------------------------------------------------------
+// Streaming variant: same recurrence, vectors in global memory (x, r, u, w, p, s planes).
+// ---------------------------------------------------------------------------------------
+template <int D>
+__global__ void __launch_bounds__(PCG_THREADS) k_pcg_stream(PcgArgs a) {
+  __shared__ Shared sh;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nth = gridDim.x * blockDim.x;
+  const size_t ld = a.ld;
+  const bool pre = a.mfac != nullptr;
+  double s[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) s[k] = __ldg(a.scale + k);
+  double* R = a.r;
+  double* U = a.u;
+  double* Wv = a.w;
+  double* Pv = a.p;
+  double* Sv = a.s;
+  auto bar = [&]() -> bool {
+    if (a.skip_block == (int)blockIdx.x) return false;
+    return grid_sync(a.bar, &sh.flag);
+  };
+  auto load_nb = [&](int n, int* nb) {
+#pragma unroll
+    for (int d = 0; d < 6; ++d) nb[d] = d < a.ndir ? __ldg(a.nbr + (size_t)d * ld + n) : -1;
+  };
+  auto precond = [&](int n, const double* rn, double* un) {
+    if (pre) {
+      minv<D>(a.mfac + n, (int)ld, rn, un);
+    } else {
+#pragma unroll
+      for (int k = 0; k < D; ++k) un[k] = rn[k];
+    }
+  };
+  // r = b - B~ x, u = M^-1 r (published); then w = B~ u and partials.
+  auto restart = [&](double* tot) -> bool {
+    for (int n = tid; n < a.N; n += nth) {
+      int nb[6];
+      load_nb(n, nb);
+      double xn[D], ax[D], rn[D], un[D];
+#pragma unroll
+      for (int k = 0; k < D; ++k) xn[k] = ldx(a.x + (size_t)k * ld + n);
+      amul<D>(a.blocks + n, (int)ld, s, nb, a.ndir, xn, a.x, ld, ax);
+#pragma unroll
+      for (int k = 0; k < D; ++k) rn[k] = __ldg(a.b + (size_t)k * ld + n) - ax[k];
+      precond(n, rn, un);
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        R[(size_t)k * ld + n] = rn[k];
+        U[(size_t)k * ld + n] = un[k];
+        Pv[(size_t)k * ld + n] = 0.0;
+        Sv[(size_t)k * ld + n] = 0.0;
+      }
+    }
+    if (!bar()) return false;
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int n = tid; n < a.N; n += nth) {
+      int nb[6];
+      load_nb(n, nb);
+      double un[D], wn[D];
+#pragma unroll
+      for (int k = 0; k < D; ++k) un[k] = U[(size_t)k * ld + n];
+      amul<D>(a.blocks + n, (int)ld, s, nb, a.ndir, un, U, ld, wn);
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        const double rk = R[(size_t)k * ld + n], bk = __ldg(a.b + (size_t)k * ld + n);
+        Wv[(size_t)k * ld + n] = wn[k];
+        v[0] += rk * un[k];
+        v[1] += wn[k] * un[k];
+        v[2] += rk * rk;
+        v[3] += bk * bk;
+      }
+    }
+    return grid_allreduce<4>(a.bar, a.part, a.tot, v, sh.red, sh.ints, tot);
+  };
+
+  double tot[4];
+  if (!restart(tot)) return;
+  double gam = tot[0], del = tot[1], rr = tot[2];
+  const double bb = tot[3];
+  const double tol2 = a.delta * a.delta * bb;
+  const double rel0 = bb > 0.0 ? sqrt(rr / bb) : 0.0;
+  int it = 0, restarts = 0, status = 0;
+  if (!(isfinite(gam) && isfinite(del) && isfinite(bb))) status = 7;
+  if (status == 0 && bb == 0.0) {
+    for (int n = tid; n < a.N; n += nth)
+#pragma unroll
+      for (int k = 0; k < D; ++k) a.x[(size_t)k * ld + n] = 0.0;
+  }
+  bool done = status != 0 || bb == 0.0 || rr <= tol2;
+  double alpha = (del > 0.0) ? gam / del : 0.0, beta = 0.0;
+  if (!done && !(del > 0.0)) { status = 3; done = true; }
+  while (!done) {
+    for (int n = tid; n < a.N; n += nth) {
+      double rn[D], un[D];
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        const size_t o = (size_t)k * ld + n;
+        const double pk = U[o] + beta * Pv[o];
+        const double sk = Wv[o] + beta * Sv[o];
+        Pv[o] = pk;
+        Sv[o] = sk;
+        a.x[o] += alpha * pk;
+        rn[k] = R[o] - alpha * sk;
+        R[o] = rn[k];
+      }
+      precond(n, rn, un);
+#pragma unroll
+      for (int k = 0; k < D; ++k) U[(size_t)k * ld + n] = un[k];
+    }
+    if (!bar()) return;
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int n = tid; n < a.N; n += nth) {
+      int nb[6];
+      load_nb(n, nb);
+      double un[D], wn[D];
+#pragma unroll
+      for (int k = 0; k < D; ++k) un[k] = U[(size_t)k * ld + n];
+      amul<D>(a.blocks + n, (int)ld, s, nb, a.ndir, un, U, ld, wn);
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        const double rk = R[(size_t)k * ld + n];
+        Wv[(size_t)k * ld + n] = wn[k];
+        v[0] += rk * un[k];
+        v[1] += wn[k] * un[k];
+        v[2] += rk * rk;
+      }
+    }
+    if (!grid_allreduce<4>(a.bar, a.part, a.tot, v, sh.red, sh.ints, tot)) return;
+    ++it;
+    const double gnew = tot[0], dnew = tot[1];
+    rr = tot[2];
+    if (!(isfinite(gnew) && isfinite(dnew) && isfinite(rr))) { status = 7; break; }
+    if (rr <= tol2 || it >= a.max_iter) {
+      // x was last updated before the reducing barrier above, so it is complete
+      if (!restart(tot)) return;
+      gam = tot[0];
+      del = tot[1];
+      rr = tot[2];
+      if (rr <= tol2) break;
+      if (it >= a.max_iter) { status = 4; break; }
+      ++restarts;
+      alpha = del > 0.0 ? gam / del : 0.0;
+      beta = 0.0;
+      if (!(del > 0.0)) { status = 3; break; }
+      continue;
+    }
+    beta = gnew / gam;
+    const double den = dnew - beta * gnew / alpha;
+    if (!(den > 0.0)) { status = 3; break; }
+    alpha = gnew / den;
+    gam = gnew;
+  }
+  write_ctrl(a, it, restarts, rr, bb, rel0, status);
+}
+
+// ---------------------------------------------------------------------------------------
+// launch
+// ---------------------------------------------------------------------------------------
+namespace {
+
+int num_sms() {
+  int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg<D>, PCG_THREADS, 0);
+  return nsm;
+}
+
+template <int D>
+cudaError_t launch_resident(const PcgArgs& a, cudaStream_t stream, int* grid_out, bool* launched) {
+  *launched = false;
+  const int nsm = num_sms();
+  int threads = (a.N + nsm - 1) / nsm;
+  threads = ((threads + 31) / 32) * 32;
+  if (threads < 64) threads = 64;
+  if (threads > RES_MAX_THREADS) return cudaSuccess;
+  const int grid = (a.N + threads - 1) / threads;
+  if (a.max_grid > 0 && grid > a.max_grid) return cudaSuccess;
+  const size_t shm = (size_t)2 * ntri(D) * threads * sizeof(double);
+  if (cudaFuncSetAttribute(k_pcg_res<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm) != cudaSuccess) {
+    cudaGetLastError();
+    return cudaSuccess;
+  }
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_res<D>, threads, shm) != cudaSuccess) {
+    cudaGetLastError();
+    return cudaSuccess;
+  }
+  if (per_sm < 1 || grid > per_sm * nsm) return cudaSuccess;
+  if (grid_out) *grid_out = grid;
+  *launched = true;
+  void* args[] = {(void*)&a};
+  return cudaLaunchCooperativeKernel((const void*)k_pcg_res<D>, dim3(grid), dim3(threads), args, shm, stream);
+}
+
+}  // namespace
+
+template <int D>
+static cudaError_t launch_d(const PcgArgs& a, cudaStream_t stream, int* grid_out) {
+  if constexpr (D <= RES_MAX_D) {
+    if (a.allow_resident) {
+      bool launched = false;
+      cudaError_t e = launch_resident<D>(a, stream, grid_out, &launched);
+      if (launched || e != cudaSuccess) return e;
+    }
+  }
+  const int nsm = num_sms();
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_stream<D>, PCG_THREADS, 0);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   const int need = (a.N + PCG_THREADS - 1) / PCG_THREADS;
@@ -262,16 +458,15 @@ static cudaError_t launch_d(const PcgArgs& a, cudaStream_t stream, int* grid_out
   if (a.max_grid > 0 && grid > a.max_grid) grid = a.max_grid;
   if (grid_out) *grid_out = grid;
   void* args[] = {(void*)&a};
-  return cudaLaunchCooperativeKernel((const void*)k_pcg<D>, dim3(grid), dim3(PCG_THREADS), args, 0, stream);
+  return cudaLaunchCooperativeKernel((const void*)k_pcg_stream<D>, dim3(grid), dim3(PCG_THREADS), args, 0, stream);
 }
 
 template <int D>
 static int max_grid_d() {
-  int dev = 0, nsm = 0, per_sm = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg<D>, PCG_THREADS, 0);
-  return nsm * per_sm;
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_stream<D>, PCG_THREADS, 0);
+  const int nsm = num_sms();
+  return nsm * (per_sm > 1 ? per_sm : 1);
 }
 
 #define BFMRI_PCG_CASES(X) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12)

@@ -34,18 +34,20 @@ struct PcgArgs {
   const double* scale;   // [D] prior scales (alpha or beta)
   const double* b;       // [D][ld] right-hand side
   double* x;             // [D][ld] start value in, solution out
-  double* r;             // [D][ld] work
-  double* z;
-  double* q;
-  double* p0;
-  double* p1;
-  double* part;          // [2][grid][4] reduction partials
+  double* r;             // [D][ld] work (streaming variant)
+  double* u;             // [D][ld] preconditioned residual, exchanged between CTAs
+  double* w;             // [D][ld] work (streaming variant)
+  double* p;
+  double* s;
+  double* part;          // [grid][4] reduction partials
+  double* tot;           // [4] reduction totals
   GridBarrier bar;
   PcgCtrl* ctrl;
   double delta;          // stop when ||b - B x|| <= delta ||b|| (true residual, FP64)
   int max_iter;
   int skip_block;        // test hook (-1 off): this CTA never reaches the first barrier
-  int max_grid;          // rows of each partial buffer: the launch never uses more CTAs
+  int max_grid;          // rows of the partial buffer: the launch never uses more CTAs
+  int allow_resident;    // 1: use the register/shared-memory resident variant when N fits
 };
 
 // Launches the cooperative persistent PCG kernel for dimension D (1..12) on `stream`.
