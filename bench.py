@@ -56,10 +56,10 @@ FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12
 
 
 def pcg_flops_per_voxel_iter(K):
-    """FP64 flops of one fused PCG iteration per voxel (phase 1: p update 2K, block 2K^2,
-    6 neighbour p reconstructions + sums 18K, stencil 3K, p'q 2K; phase 2: two axpys 4K,
-    block-Jacobi triangular solves 2K^2 + 2K, two dots 4K)."""
-    return 4 * K * K + 35 * K
+    """FP64 flops of one Chronopoulos-Gear PCG iteration per voxel: four axpys (p, s, x, r)
+    8K, block-Jacobi triangular solves 2K^2 + 2K, block product 2K^2, stencil with up to six
+    neighbours 6K + 3K, three inner products 6K."""
+    return 4 * K * K + 25 * K
 
 
 def pcg_bytes_per_voxel_iter(K, w=8):
@@ -275,6 +275,9 @@ def run_ours(args, world, rank, local):
             "iterations_per_launch": iters_per_launch, "avg_launch_ms": dur_s * 1e3,
             "share_of_step": pw["ms"] / total_ms if total_ms > 0 else None}
     m.close()
+
+    # the same chain with the mixed-precision solver (FP32 inner, FP64 refinement, same delta)
+    mixed = run_mixed(args, w, flush, stream) if not args.no_mixed else None
     del flush
 
     # end to end through the C ABI with host buffers
@@ -296,9 +299,48 @@ def run_ours(args, world, rank, local):
                            "pcg_iterations_W_per_sweep": it_w / args.steps,
                            "pcg_iterations_A_per_sweep": it_a / args.steps},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+                "mixed_precision": mixed,
                 "gpu_launches": int(n_launch),
                 "kernel_ms_per_step": {k: v["ms"] / args.steps for k, v in tim.items() if v["launches"]}}
         print(json.dumps(line), flush=True)
+
+
+def run_mixed(args, w, flush, stream):
+    """Sweeps/s of the same workload with the FP32-inner / FP64-refinement solver at the same
+    delta (1e-8), timed like the headline."""
+    import torch
+
+    from paper_1606_00980_gb300 import bfmri
+    from paper_1606_00980_gb300.bfmri import Model
+    m = Model.from_workload(w, delta=1e-8, seed=2024, precision=bfmri.PREC_MIXED, inner_tol=1e-4,
+                            profile=1)
+    m.precompute_stats()
+    counter = 0
+    for _ in range(args.warmup):
+        m.gibbs_sweep(1, counter, info=False)
+        counter += 1
+    torch.cuda.synchronize()
+    m.reset_timing()
+    times = []
+    it_w = ref_w = 0
+    for s in range(args.steps):
+        flush.random_(0, 255)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        inf = m.gibbs_sweep(1, counter, info=True)
+        e1.record(stream)
+        counter += 1
+        times.append((e0, e1))
+        it_w += inf.pcg_iterations_W
+    torch.cuda.synchronize()
+    tot = sum(a.elapsed_time(b) for a, b in times) / 1e3
+    tim = m.timing()
+    m.close()
+    return {"value": args.steps / tot, "unit": UNIT, "ms_per_step": tot / args.steps * 1e3,
+            "delta": 1e-8, "inner_tol": 1e-4,
+            "inner_iterations_W_per_sweep": it_w / args.steps,
+            "kernel_ms_per_step": {k: v["ms"] / args.steps for k, v in tim.items() if v["launches"]}}
 
 
 def run_e2e(args, w):
@@ -333,6 +375,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -93,7 +93,13 @@ typedef struct {
                                 next solve (forces BFMRI_ERR_TIMEOUT); -1 = off (default) */
   int profile;               /* nonzero: time every kernel launch with CUDA events on the
                                 handle's stream (read with bfmri_get_timing) */
+  int pcg_variant;           /* BFMRI_PCG_AUTO (default): the register-resident solver when the
+                                voxels fit one CTA per SM, else the streaming one;
+                                BFMRI_PCG_STREAMING: always the streaming solver */
 } bfmri_options;
+
+#define BFMRI_PCG_AUTO      0
+#define BFMRI_PCG_STREAMING 1
 
 /* Fills *opt with the defaults listed above. */
 void bfmri_default_options(bfmri_options* opt);

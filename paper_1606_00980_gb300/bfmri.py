@@ -26,6 +26,7 @@ PRECOND_NONE, PRECOND_BLOCK_JACOBI = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
 AR_SPATIAL, AR_INDEPENDENT = 0, 1
 Y_MASKED, Y_LATTICE = 0, 1
+PCG_AUTO, PCG_STREAMING = 0, 1
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
@@ -43,7 +44,7 @@ class bfmri_options(C.Structure):
                 ("inner_tol", C.c_double), ("seed", C.c_uint64), ("stream_id", C.c_uint32),
                 ("cuda_stream", C.c_void_p), ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN),
                 ("alloc_ctx", C.c_void_p), ("barrier_timeout_s", C.c_double),
-                ("debug_skip_block", C.c_int), ("profile", C.c_int)]
+                ("debug_skip_block", C.c_int), ("profile", C.c_int), ("pcg_variant", C.c_int)]
 
 
 class bfmri_solve_info(C.Structure):

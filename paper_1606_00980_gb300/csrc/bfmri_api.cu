@@ -41,6 +41,9 @@ struct bfmri_handle {
   double *d_blocks = nullptr, *d_mfac = nullptr, *d_rhs = nullptr, *d_bmean = nullptr;
   double *d_r = nullptr, *d_z = nullptr, *d_q = nullptr, *d_p0 = nullptr, *d_p1 = nullptr;
   double *d_part = nullptr, *d_hpart = nullptr;
+  // mixed precision (FP32 inner solver)
+  float *d_blocks32 = nullptr, *d_mfac32 = nullptr, *d_u32 = nullptr, *d_r32 = nullptr;
+  float *d_w32 = nullptr, *d_p32 = nullptr, *d_s32 = nullptr, *d_d32 = nullptr;
   unsigned int* d_bar = nullptr;
   int* d_err = nullptr;
   PcgCtrl* d_ctrl = nullptr;  // [0] W solves, [1] A solves
@@ -251,7 +254,18 @@ bfmri_status run_pcg(bfmri_handle* h, int D, const double* scale, double* x, int
   a.s = h->d_p1;
   a.part = h->d_part;
   a.tot = h->d_part + (size_t)h->part_rows * 4;
-  a.allow_resident = 1;
+  a.allow_resident = h->opt.pcg_variant == BFMRI_PCG_AUTO;
+  a.mixed = h->opt.precision == BFMRI_PREC_MIXED;
+  a.blocks32 = h->d_blocks32;
+  a.mfac32 = h->opt.precond == BFMRI_PRECOND_BLOCK_JACOBI ? h->d_mfac32 : nullptr;
+  a.u32 = h->d_u32;
+  a.r32 = h->d_r32;
+  a.w32 = h->d_w32;
+  a.p32 = h->d_p32;
+  a.s32 = h->d_s32;
+  a.d32 = h->d_d32;
+  a.inner_tol = h->opt.inner_tol;
+  a.max_inner = 1000;
   a.bar.count = h->d_bar;
   a.bar.gen = h->d_bar + 1;
   a.bar.err = h->d_err;
@@ -288,6 +302,8 @@ AssembleArgs assemble_args(bfmri_handle* h, const double* scale, uint64_t counte
   a.rng = rng_of(h, counter, tag);
   a.blocks = h->d_blocks;
   a.mfac = h->d_mfac;
+  a.blocks32 = h->d_blocks32;
+  a.mfac32 = h->d_mfac32;
   a.rhs = h->d_rhs;
   a.G = h->d_G;
   a.bad_voxel = h->d_flags;
@@ -475,10 +491,14 @@ bfmri_status bfmri_create(const bfmri_lattice* lat, const uint8_t* mask, const d
   if (!(o.delta > 0.0) || o.max_iter < 1 || !(o.barrier_timeout_s > 0.0) || o.eps < 0.0 ||
       !(o.q1 > 0) || !(o.q2 > 0) || !(o.u1 > 0) || !(o.u2 > 0) || !(o.r1 > 0) || !(o.r2 > 0))
     return fail(nullptr, BFMRI_ERR_INVALID_ARG, "invalid option value");
+  if (o.pcg_variant != BFMRI_PCG_AUTO && o.pcg_variant != BFMRI_PCG_STREAMING)
+    return fail(nullptr, BFMRI_ERR_INVALID_ARG, "unknown pcg_variant");
   if (o.precond != BFMRI_PRECOND_NONE && o.precond != BFMRI_PRECOND_BLOCK_JACOBI)
     return fail(nullptr, BFMRI_ERR_INVALID_ARG, "unknown preconditioner");
-  if (o.precision != BFMRI_PREC_FP64)
-    return fail(nullptr, BFMRI_ERR_INVALID_ARG, "precision mode not available in this build");
+  if (o.precision != BFMRI_PREC_FP64 && o.precision != BFMRI_PREC_MIXED)
+    return fail(nullptr, BFMRI_ERR_INVALID_ARG, "unknown precision mode");
+  if (o.precision == BFMRI_PREC_MIXED && !(o.inner_tol > 0.0 && o.inner_tol < 1.0))
+    return fail(nullptr, BFMRI_ERR_INVALID_ARG, "inner_tol must be in (0, 1)");
   if (!all_finite(X, (size_t)T * K)) return fail(nullptr, BFMRI_ERR_INVALID_ARG, "X has non-finite values");
 
   // in-mask voxels in raster order and their neighbour planes
@@ -592,6 +612,17 @@ bfmri_status bfmri_create(const bfmri_lattice* lat, const uint8_t* mask, const d
   h->d_err = (int*)A(sizeof(int));
   h->d_ctrl = (PcgCtrl*)A(2 * sizeof(PcgCtrl));
   h->d_flags = (int*)A(4 * sizeof(int));
+  if (o.precision == BFMRI_PREC_MIXED) {
+    h->d_blocks32 = (float*)A((size_t)ntri(D) * ld * sizeof(float));
+    h->d_mfac32 = (float*)A((size_t)ntri(D) * ld * sizeof(float));
+    float** f32[] = {&h->d_u32, &h->d_r32, &h->d_w32, &h->d_p32, &h->d_s32, &h->d_d32};
+    for (float** pp : f32) *pp = (float*)A((size_t)D * ld * sizeof(float));
+    if (!h->d_blocks32 || !h->d_mfac32 || !h->d_u32 || !h->d_r32 || !h->d_w32 || !h->d_p32 ||
+        !h->d_s32 || !h->d_d32) {
+      bfmri_destroy(h);
+      return fail(nullptr, BFMRI_ERR_OOM, "device allocation failed");
+    }
+  }
   void* must[] = {h->d_nbr, h->d_lin, h->d_Y, h->d_X, h->d_stats, h->d_Sxx, h->d_W, h->d_A,
                   h->d_lam, h->d_alpha, h->d_beta, h->d_G, h->d_blocks, h->d_mfac, h->d_rhs,
                   h->d_bmean, h->d_r, h->d_z, h->d_q, h->d_p0, h->d_p1, h->d_part, h->d_hpart,

@@ -195,9 +195,11 @@ __device__ __forceinline__ void sym_mul(const T* B, const U* p, U* q) {
 }
 
 // ---------------------------------------------------------------------------------------
-// Bounded grid barrier for cooperative (co-resident) launches. Every wait has a time limit
-// read from %globaltimer; on expiry the waiting CTA records BFMRI timeout in *err and
-// returns false, and every CTA leaves at its next barrier. The barrier never traps.
+// Bounded grid barrier for cooperative (co-resident) launches. Thread 0 of every CTA arrives
+// with an acquire-release atomic on a counter; the last to arrive resets it and releases a
+// generation word that the others poll with acquire loads. Every wait has a time limit read
+// from %globaltimer: on expiry the CTA records a timeout in *err and returns false, and
+// every CTA leaves at its next barrier. The barrier never traps.
 // ---------------------------------------------------------------------------------------
 struct GridBarrier {
   unsigned int* count;
@@ -224,192 +226,165 @@ __device__ __forceinline__ int ld_acquire_int(const int* p) {
   return v;
 }
 
+__device__ __forceinline__ unsigned int atom_add_acq_rel(unsigned int* p, unsigned int v) {
+  unsigned int old;
+  asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+
+__device__ __forceinline__ void red_add_release(unsigned int* p, unsigned int v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void st_relaxed(unsigned int* p, unsigned int v) {
+  asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 constexpr int ERR_TIMEOUT_CODE = 5;
 constexpr int ERR_NOT_SPD_CODE = 3;
+
+// Polls the generation word until it differs from g0; false on error or time-out.
+__device__ __forceinline__ bool wait_generation(const GridBarrier& b, unsigned int g0) {
+  const unsigned long long t0 = globaltimer_ns();
+  unsigned int spins = 0;
+  while (ld_acquire(b.gen) == g0) {
+    if ((++spins & 255u) == 0u) {
+      if (ld_acquire_int(b.err) != 0) return false;
+      if (globaltimer_ns() - t0 > b.timeout_ns) {
+        atomicCAS(b.err, 0, ERR_TIMEOUT_CODE);
+        return false;
+      }
+    }
+  }
+  return true;
+}
 
 __device__ __forceinline__ bool grid_sync(const GridBarrier& b, int* sh_flag) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    const unsigned int nblocks = gridDim.x * gridDim.y * gridDim.z;
     const unsigned int g0 = ld_acquire(b.gen);
-    __threadfence();
-    const unsigned int arrived = atomicAdd(b.count, 1u);
-    if (arrived == nblocks - 1) {
-      atomicExch(b.count, 0u);
-      __threadfence();
-      atomicAdd(b.gen, 1u);
+    const unsigned int arrived = atom_add_acq_rel(b.count, 1u);
+    bool ok = true;
+    if (arrived == gridDim.x - 1) {
+      st_relaxed(b.count, 0u);
+      red_add_release(b.gen, 1u);
     } else {
-      const unsigned long long t0 = globaltimer_ns();
-      unsigned int spins = 0;
-      while (ld_acquire(b.gen) == g0) {
-        if ((++spins & 63u) == 0u) {
-          if (ld_acquire_int(b.err) != 0) break;
-          if (globaltimer_ns() - t0 > b.timeout_ns) {
-            atomicCAS(b.err, 0, ERR_TIMEOUT_CODE);
-            break;
-          }
-        }
-      }
+      ok = wait_generation(b, g0);
     }
-    __threadfence();
-    *sh_flag = ld_acquire_int(b.err);
+    *sh_flag = ok ? 0 : 1;
   }
   __syncthreads();
   return *sh_flag == 0;
 }
 
 // ---------------------------------------------------------------------------------------
-// Reducing grid barrier. Every CTA reduces its threads' NV values in a fixed tree and writes
-// one row of `part`; the CTA that arrives last sums all rows in a fixed order (independent of
-// which CTA it is), publishes the totals in tot[NV] and releases the others, which read them.
-// All CTAs therefore obtain bit-identical totals, run after run. Waits are bounded as in
-// grid_sync. `sh` needs 32 * NV + NV + 2 doubles of shared memory.
+// Warp reduction of 4 doubles with 6 FP64 additions per warp instead of 20 (FP64 issue is
+// scarce on this part): the first two exchange levels split the values between lane halves
+// and quarters, the last three are a plain butterfly. Afterwards value j is complete in
+// lanes [8j, 8j + 8).
 // ---------------------------------------------------------------------------------------
-template <int NV>
-__device__ __forceinline__ bool grid_allreduce(const GridBarrier& b, double* part, double* tot,
-                                               double* v, double* sh, int* sh_int, double* out) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  double* sh_w = sh;                 // [32][NV]
-  double* sh_out = sh + 32 * NV;     // [NV]
-#pragma unroll
-  for (int i = 0; i < NV; ++i) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_down_sync(0xffffffffu, v[i], o);
-  }
-  if (lane == 0) {
-#pragma unroll
-    for (int i = 0; i < NV; ++i) sh_w[warp * NV + i] = v[i];
+__device__ __forceinline__ double warp_reduce4(const double* v) {
+  const int l = threadIdx.x & 31;
+  const bool hi16 = (l & 16) != 0;
+  const double a_keep = hi16 ? v[2] : v[0], b_keep = hi16 ? v[3] : v[1];
+  const double a_send = hi16 ? v[0] : v[2], b_send = hi16 ? v[1] : v[3];
+  const double a = a_keep + __shfl_xor_sync(0xffffffffu, a_send, 16);
+  const double b = b_keep + __shfl_xor_sync(0xffffffffu, b_send, 16);
+  const bool hi8 = (l & 8) != 0;
+  double c = (hi8 ? b : a) + __shfl_xor_sync(0xffffffffu, hi8 ? a : b, 8);
+  c += __shfl_xor_sync(0xffffffffu, c, 4);
+  c += __shfl_xor_sync(0xffffffffu, c, 2);
+  c += __shfl_xor_sync(0xffffffffu, c, 1);
+  return c;
+}
+
+// Block totals of 4 doubles per thread, fixed order; every thread receives them in out.
+// sh needs 4 * 32 + 4 doubles.
+__device__ __forceinline__ void block_reduce4(const double* v, double* sh, double* out) {
+  const int l = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const double c = warp_reduce4(v);
+  if ((l & 7) == 0) sh[warp * 4 + (l >> 3)] = c;
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    const int j = l & 3;
+    double acc = 0.0;
+    for (int w = l >> 2; w < nw; w += 8) acc += sh[w * 4 + j];
+    acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 8);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 16);
+    if (l < 4) sh[128 + l] = acc;
   }
   __syncthreads();
+#pragma unroll
+  for (int i = 0; i < 4; ++i) out[i] = sh[128 + i];
+}
+
+// ---------------------------------------------------------------------------------------
+// Reducing grid barrier over 4 doubles. Every CTA writes its block totals to one row of
+// `part` and arrives; the CTA that arrives last sums all rows in a fixed order (independent
+// of which CTA it is), publishes the totals in tot[4] and releases the others, which read
+// them. All CTAs therefore obtain bit-identical totals, run after run. sh needs 4 * 32 + 8
+// doubles, sh_int 2 ints.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ bool grid_allreduce4(const GridBarrier& b, double* part, double* tot,
+                                                const double* v, double* sh, int* sh_int, double* out) {
+  double bt[4];
+  block_reduce4(v, sh, bt);
+  const int l = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned int nblocks = gridDim.x;
   if (threadIdx.x == 0) {
-    const int nw = (blockDim.x + 31) >> 5;
 #pragma unroll
-    for (int i = 0; i < NV; ++i) {
-      double s = 0.0;
-      for (int w = 0; w < nw; ++w) s += sh_w[w * NV + i];
-      part[(size_t)blockIdx.x * NV + i] = s;
-    }
+    for (int i = 0; i < 4; ++i) part[(size_t)blockIdx.x * 4 + i] = bt[i];
     const unsigned int g0 = ld_acquire(b.gen);
-    __threadfence();
-    const unsigned int arrived = atomicAdd(b.count, 1u);
+    const unsigned int arrived = atom_add_acq_rel(b.count, 1u);
     sh_int[0] = (arrived == nblocks - 1) ? 1 : 0;
     sh_int[1] = (int)g0;
   }
   __syncthreads();
+  double* sh_out = sh + 132;
   if (sh_int[0]) {
-    // last CTA: fixed-order total of all rows
     if (warp == 0) {
-      __threadfence();
-      double acc[NV];
+      // lane l sums value (l & 3) over rows (l >> 2) + 8 i, i = 0, 1, ...
+      const int j = l & 3;
+      constexpr int RU = 8;  // rows loaded before summing, for memory-level parallelism
+      double acc = 0.0;
+      for (unsigned int r0 = (unsigned int)(l >> 2); r0 < nblocks; r0 += 8u * RU) {
+        double buf[RU];
 #pragma unroll
-      for (int i = 0; i < NV; ++i) acc[i] = 0.0;
-      for (unsigned int r = lane; r < nblocks; r += 32) {
-#pragma unroll
-        for (int i = 0; i < NV; ++i) acc[i] += __ldcg(part + (size_t)r * NV + i);
-      }
-#pragma unroll
-      for (int i = 0; i < NV; ++i) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc[i] += __shfl_down_sync(0xffffffffu, acc[i], o);
-      }
-      if (lane == 0) {
-#pragma unroll
-        for (int i = 0; i < NV; ++i) {
-          sh_out[i] = acc[i];
-          tot[i] = acc[i];
+        for (int i = 0; i < RU; ++i) {
+          const unsigned int r = r0 + 8u * i;
+          buf[i] = r < nblocks ? __ldcg(part + (size_t)r * 4 + j) : 0.0;
         }
-        __threadfence();
-        atomicExch(b.count, 0u);
-        __threadfence();
-        atomicAdd(b.gen, 1u);
-        sh_int[1] = ld_acquire_int(b.err);
+#pragma unroll
+        for (int i = 0; i < RU; ++i) acc += buf[i];
+      }
+      acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+      acc += __shfl_xor_sync(0xffffffffu, acc, 8);
+      acc += __shfl_xor_sync(0xffffffffu, acc, 16);
+      if (l < 4) {
+        sh_out[l] = acc;
+        tot[l] = acc;
+      }
+      __syncwarp();
+      if (l == 0) {
+        st_relaxed(b.count, 0u);
+        red_add_release(b.gen, 1u);
+        sh_int[1] = 0;
       }
     }
   } else if (threadIdx.x == 0) {
-    const unsigned int g0 = (unsigned int)sh_int[1];
-    const unsigned long long t0 = globaltimer_ns();
-    unsigned int spins = 0;
-    bool ok = true;
-    while (ld_acquire(b.gen) == g0) {
-      if ((++spins & 63u) == 0u) {
-        if (ld_acquire_int(b.err) != 0) { ok = false; break; }
-        if (globaltimer_ns() - t0 > b.timeout_ns) {
-          atomicCAS(b.err, 0, ERR_TIMEOUT_CODE);
-          ok = false;
-          break;
-        }
-      }
-    }
-    __threadfence();
+    const bool ok = wait_generation(b, (unsigned int)sh_int[1]);
 #pragma unroll
-    for (int i = 0; i < NV; ++i) sh_out[i] = ok ? __ldcg(tot + i) : 0.0;
-    sh_int[1] = ok ? ld_acquire_int(b.err) : 1;
+    for (int i = 0; i < 4; ++i) sh_out[i] = ok ? __ldcg(tot + i) : 0.0;
+    sh_int[1] = ok ? 0 : 1;
   }
   __syncthreads();
 #pragma unroll
-  for (int i = 0; i < NV; ++i) out[i] = sh_out[i];
+  for (int i = 0; i < 4; ++i) out[i] = sh_out[i];
   const bool good = sh_int[1] == 0;
   __syncthreads();
   return good;
-}
-
-// ---------------------------------------------------------------------------------------
-// Deterministic grid reductions of NV doubles: each CTA reduces its threads' values in a
-// fixed tree and writes one row of `part`; after the barrier every CTA re-reduces all rows in
-// the same fixed order, so every CTA (and every run) obtains bit-identical sums.
-// ---------------------------------------------------------------------------------------
-template <int NV>
-__device__ __forceinline__ void block_partial(double* v, double* sh /* [32][NV] */, double* part) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int i = 0; i < NV; ++i) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_down_sync(0xffffffffu, v[i], o);
-  }
-  if (lane == 0) {
-#pragma unroll
-    for (int i = 0; i < NV; ++i) sh[warp * NV + i] = v[i];
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const int nw = (blockDim.x + 31) >> 5;
-#pragma unroll
-    for (int i = 0; i < NV; ++i) {
-      double s = 0.0;
-      for (int w = 0; w < nw; ++w) s += sh[w * NV + i];
-      part[(size_t)blockIdx.x * NV + i] = s;
-    }
-  }
-  __syncthreads();
-}
-
-// After the barrier: all threads get the grid totals.
-template <int NV>
-__device__ __forceinline__ void grid_total(const double* part, double* sh /* [NV] */, double* out) {
-  if (threadIdx.x < 32) {
-    const int lane = threadIdx.x;
-    double acc[NV];
-#pragma unroll
-    for (int i = 0; i < NV; ++i) acc[i] = 0.0;
-    for (int b = lane; b < (int)gridDim.x; b += 32) {
-#pragma unroll
-      for (int i = 0; i < NV; ++i) acc[i] += __ldcg(part + (size_t)b * NV + i);
-    }
-#pragma unroll
-    for (int i = 0; i < NV; ++i) {
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) acc[i] += __shfl_down_sync(0xffffffffu, acc[i], o);
-    }
-    if (lane == 0) {
-#pragma unroll
-      for (int i = 0; i < NV; ++i) sh[i] = acc[i];
-    }
-  }
-  __syncthreads();
-#pragma unroll
-  for (int i = 0; i < NV; ++i) out[i] = sh[i];
-  __syncthreads();
 }
 
 }  // namespace bfmri

@@ -157,6 +157,10 @@ __global__ void __launch_bounds__(VOX_THREADS) k_assemble_w(AssembleArgs a) {
     bw[k] *= lam;
   }
   store_packed<K>(a.blocks, ld, n, B);
+  if (a.blocks32) {
+#pragma unroll
+    for (int e = 0; e < ntri(K); ++e) a.blocks32[(size_t)e * ld + n] = (float)B[e];
+  }
   if (a.bmean) {
 #pragma unroll
     for (int k = 0; k < K; ++k) a.bmean[k * ld + n] = bw[k];
@@ -188,6 +192,10 @@ __global__ void __launch_bounds__(VOX_THREADS) k_assemble_w(AssembleArgs a) {
     for (int k = 0; k < K; ++k) B[tri(k, k)] += a.scale[k] * deg;
     ok = chol_packed_invdiag<K>(B) && ok;
     store_packed<K>(a.mfac, ld, n, B);
+    if (a.mfac32) {
+#pragma unroll
+      for (int e = 0; e < ntri(K); ++e) a.mfac32[(size_t)e * ld + n] = (float)B[e];
+    }
   }
   if (!ok) atomicMin(a.bad_voxel, n);
 }
@@ -285,7 +293,10 @@ __global__ void __launch_bounds__(VOX_THREADS) k_assemble_a(AssembleArgs a) {
   if (a.rhs) {
 #pragma unroll
     for (int e = 0; e < ntri(PM); ++e)
-      if (e < ntri(P)) a.blocks[(size_t)e * ld + n] = J[e];
+      if (e < ntri(P)) {
+        a.blocks[(size_t)e * ld + n] = J[e];
+        if (a.blocks32) a.blocks32[(size_t)e * ld + n] = (float)J[e];
+      }
 #pragma unroll
     for (int i = 0; i < PM; ++i)
       if (i < P) a.rhs[i * ld + n] = rhs[i];
@@ -297,7 +308,10 @@ __global__ void __launch_bounds__(VOX_THREADS) k_assemble_a(AssembleArgs a) {
       ok = chol_packed_invdiag<PM>(J) && ok;
 #pragma unroll
       for (int e = 0; e < ntri(PM); ++e)
-        if (e < ntri(P)) a.mfac[(size_t)e * ld + n] = J[e];
+        if (e < ntri(P)) {
+          a.mfac[(size_t)e * ld + n] = J[e];
+          if (a.mfac32) a.mfac32[(size_t)e * ld + n] = (float)J[e];
+        }
     }
   }
   if (!ok) atomicMin(a.bad_voxel, n);

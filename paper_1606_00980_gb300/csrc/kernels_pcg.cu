@@ -18,7 +18,7 @@
 //    factor are staged once in shared memory and all vectors stay in registers, so an
 //    iteration only exchanges u through L2;
 //  * streaming: any N; vectors live in global memory (structure of arrays).
-// All reductions are fixed-order (grid_allreduce), so a solve is bit-reproducible.
+// All reductions are fixed-order (grid_allreduce4), so a solve is bit-reproducible.
 #include "pcg.cuh"
 
 namespace bfmri {
@@ -30,21 +30,23 @@ constexpr int RES_MAX_D = 8;
 
 __device__ __forceinline__ double ldx(const double* p) { return __ldcg(p); }
 
-// out = B v + s .* (deg v - sum_m V[m])  (B packed, entry e at Bp[e * bs])
-template <int D>
-__device__ __forceinline__ void amul(const double* __restrict__ Bp, int bs, const double* s,
-                                     const int* nb, int ndir, const double* v,
-                                     const double* V, size_t ld, double* out) {
+__device__ __forceinline__ float ldx(const float* p) { return __ldcg(p); }
+
+// out = B v + s .* (deg v - sum_m V[m])  (B packed, entry e at Bp[e * bs]); element type T.
+template <int D, typename T>
+__device__ __forceinline__ void amul(const T* __restrict__ Bp, int bs, const T* s,
+                                     const int* nb, int ndir, const T* v,
+                                     const T* V, size_t ld, T* out) {
 #pragma unroll
   for (int i = 0; i < D; ++i) {
-    double acc = 0.0;
+    T acc = T(0);
 #pragma unroll
     for (int j = 0; j < D; ++j) acc += Bp[(size_t)(i >= j ? tri(i, j) : tri(j, i)) * bs] * v[j];
     out[i] = acc;
   }
-  double sum[D];
+  T sum[D];
 #pragma unroll
-  for (int k = 0; k < D; ++k) sum[k] = 0.0;
+  for (int k = 0; k < D; ++k) sum[k] = T(0);
   int deg = 0;
 #pragma unroll
   for (int d = 0; d < 6; ++d) {
@@ -55,23 +57,23 @@ __device__ __forceinline__ void amul(const double* __restrict__ Bp, int bs, cons
     }
   }
 #pragma unroll
-  for (int k = 0; k < D; ++k) out[k] += s[k] * ((double)deg * v[k] - sum[k]);
+  for (int k = 0; k < D; ++k) out[k] += s[k] * ((T)deg * v[k] - sum[k]);
 }
 
 // z = (L L')^-1 r with L packed lower (inverted diagonal), entry e at Lp[e * bs].
-template <int D>
-__device__ __forceinline__ void minv(const double* __restrict__ Lp, int bs, const double* r, double* z) {
-  double y[D];
+template <int D, typename T>
+__device__ __forceinline__ void minv(const T* __restrict__ Lp, int bs, const T* r, T* z) {
+  T y[D];
 #pragma unroll
   for (int i = 0; i < D; ++i) {
-    double t = r[i];
+    T t = r[i];
 #pragma unroll
     for (int j = 0; j < i; ++j) t -= Lp[(size_t)tri(i, j) * bs] * y[j];
     y[i] = t * Lp[(size_t)tri(i, i) * bs];
   }
 #pragma unroll
   for (int i = D - 1; i >= 0; --i) {
-    double t = y[i];
+    T t = y[i];
 #pragma unroll
     for (int j = i + 1; j < D; ++j) t -= Lp[(size_t)tri(j, i) * bs] * z[j];
     z[i] = t * Lp[(size_t)tri(i, i) * bs];
@@ -79,7 +81,7 @@ __device__ __forceinline__ void minv(const double* __restrict__ Lp, int bs, cons
 }
 
 struct Shared {
-  double red[32 * 4 + 4 + 2];
+  double red[32 * 4 + 8];
   int ints[2];
   int flag;
 };
@@ -144,16 +146,16 @@ __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_res(PcgArgs a) {
   // (r, u, w) from the current x, with partials (r'u, w'u, r'r, b'b)
   auto restart = [&](double* tot) -> bool {
     double ax[D];
-    amul<D>(Bp, bd, s, nb, a.ndir, x, a.x, ld, ax);
+    amul<D, double>(Bp, bd, s, nb, a.ndir, x, a.x, ld, ax);
 #pragma unroll
     for (int k = 0; k < D; ++k) r[k] = bv[k] - ax[k];
-    minv<D>(Mp, bd, r, u);
+    minv<D, double>(Mp, bd, r, u);
     if (own) {
 #pragma unroll
       for (int k = 0; k < D; ++k) a.u[(size_t)k * ld + n] = u[k];
     }
     if (!bar()) return false;
-    amul<D>(Bp, bd, s, nb, a.ndir, u, a.u, ld, w);
+    amul<D, double>(Bp, bd, s, nb, a.ndir, u, a.u, ld, w);
     double v[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
     for (int k = 0; k < D; ++k) {
@@ -162,7 +164,7 @@ __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_res(PcgArgs a) {
       v[2] += r[k] * r[k];
       v[3] += bv[k] * bv[k];
     }
-    return grid_allreduce<4>(a.bar, a.part, a.tot, v, sh.red, sh.ints, tot);
+    return grid_allreduce4(a.bar, a.part, a.tot, v, sh.red, sh.ints, tot);
   };
 
   double tot[4];
@@ -188,13 +190,13 @@ __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_res(PcgArgs a) {
       x[k] += alpha * p[k];
       r[k] -= alpha * q[k];
     }
-    minv<D>(Mp, bd, r, u);
+    minv<D, double>(Mp, bd, r, u);
     if (own) {
 #pragma unroll
       for (int k = 0; k < D; ++k) a.u[(size_t)k * ld + n] = u[k];
     }
     if (!bar()) return;
-    amul<D>(Bp, bd, s, nb, a.ndir, u, a.u, ld, w);
+    amul<D, double>(Bp, bd, s, nb, a.ndir, u, a.u, ld, w);
     double v[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
     for (int k = 0; k < D; ++k) {
@@ -202,7 +204,7 @@ __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_res(PcgArgs a) {
       v[1] += w[k] * u[k];
       v[2] += r[k] * r[k];
     }
-    if (!grid_allreduce<4>(a.bar, a.part, a.tot, v, sh.red, sh.ints, tot)) return;
+    if (!grid_allreduce4(a.bar, a.part, a.tot, v, sh.red, sh.ints, tot)) return;
     ++it;
     const double gnew = tot[0], dnew = tot[1];
     rr = tot[2];
@@ -269,7 +271,7 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_stream(PcgArgs a) {
   };
   auto precond = [&](int n, const double* rn, double* un) {
     if (pre) {
-      minv<D>(a.mfac + n, (int)ld, rn, un);
+      minv<D, double>(a.mfac + n, (int)ld, rn, un);
     } else {
 #pragma unroll
       for (int k = 0; k < D; ++k) un[k] = rn[k];
@@ -283,7 +285,7 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_stream(PcgArgs a) {
       double xn[D], ax[D], rn[D], un[D];
 #pragma unroll
       for (int k = 0; k < D; ++k) xn[k] = ldx(a.x + (size_t)k * ld + n);
-      amul<D>(a.blocks + n, (int)ld, s, nb, a.ndir, xn, a.x, ld, ax);
+      amul<D, double>(a.blocks + n, (int)ld, s, nb, a.ndir, xn, a.x, ld, ax);
 #pragma unroll
       for (int k = 0; k < D; ++k) rn[k] = __ldg(a.b + (size_t)k * ld + n) - ax[k];
       precond(n, rn, un);
@@ -303,7 +305,7 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_stream(PcgArgs a) {
       double un[D], wn[D];
 #pragma unroll
       for (int k = 0; k < D; ++k) un[k] = U[(size_t)k * ld + n];
-      amul<D>(a.blocks + n, (int)ld, s, nb, a.ndir, un, U, ld, wn);
+      amul<D, double>(a.blocks + n, (int)ld, s, nb, a.ndir, un, U, ld, wn);
 #pragma unroll
       for (int k = 0; k < D; ++k) {
         const double rk = R[(size_t)k * ld + n], bk = __ldg(a.b + (size_t)k * ld + n);
@@ -314,7 +316,7 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_stream(PcgArgs a) {
         v[3] += bk * bk;
       }
     }
-    return grid_allreduce<4>(a.bar, a.part, a.tot, v, sh.red, sh.ints, tot);
+    return grid_allreduce4(a.bar, a.part, a.tot, v, sh.red, sh.ints, tot);
   };
 
   double tot[4];
@@ -359,7 +361,7 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_stream(PcgArgs a) {
       double un[D], wn[D];
 #pragma unroll
       for (int k = 0; k < D; ++k) un[k] = U[(size_t)k * ld + n];
-      amul<D>(a.blocks + n, (int)ld, s, nb, a.ndir, un, U, ld, wn);
+      amul<D, double>(a.blocks + n, (int)ld, s, nb, a.ndir, un, U, ld, wn);
 #pragma unroll
       for (int k = 0; k < D; ++k) {
         const double rk = R[(size_t)k * ld + n];
@@ -369,7 +371,7 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_stream(PcgArgs a) {
         v[2] += rk * rk;
       }
     }
-    if (!grid_allreduce<4>(a.bar, a.part, a.tot, v, sh.red, sh.ints, tot)) return;
+    if (!grid_allreduce4(a.bar, a.part, a.tot, v, sh.red, sh.ints, tot)) return;
     ++it;
     const double gnew = tot[0], dnew = tot[1];
     rr = tot[2];
@@ -397,6 +399,349 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_stream(PcgArgs a) {
   write_ctrl(a, it, restarts, rr, bb, rel0, status);
 }
 
+
+// ---------------------------------------------------------------------------------------
+// Mixed precision (resident): FP64 iterative refinement around FP32 CG-CG inner solves.
+//   outer: r = b - B~ x (FP64 blocks, FP64 arithmetic), stop when ||r|| <= delta ||b||;
+//   inner: B~ d = r in FP32 (FP32 blocks, preconditioner and vectors) to ||r_in|| <=
+//          inner_tol ||r||, then x += d in FP64.
+// Per-thread inner-product terms are formed in FP32 over the voxel's D components and
+// accumulated across threads and CTAs in FP64 (fixed order).
+// ---------------------------------------------------------------------------------------
+template <int D>
+__global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_mixed_res(PcgArgs a) {
+  extern __shared__ double smem[];
+  __shared__ Shared sh;
+  constexpr int NT = ntri(D);
+  const int bd = blockDim.x, t = threadIdx.x;
+  double* shB = smem;                                   // [NT][bd] FP64 blocks
+  float* shB32 = reinterpret_cast<float*>(smem + NT * bd);   // [NT][bd]
+  float* shM32 = shB32 + NT * bd;                       // [NT][bd]
+  const int n = blockIdx.x * bd + t;
+  const bool own = n < a.N;
+  const size_t ld = a.ld;
+  const bool pre = a.mfac32 != nullptr;
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int j = 0; j <= i; ++j) {
+      const int e = tri(i, j);
+      shB[e * bd + t] = own ? __ldg(a.blocks + (size_t)e * ld + n) : (i == j ? 1.0 : 0.0);
+      shB32[e * bd + t] = own ? __ldg(a.blocks32 + (size_t)e * ld + n) : (i == j ? 1.f : 0.f);
+      shM32[e * bd + t] = (own && pre) ? __ldg(a.mfac32 + (size_t)e * ld + n) : (i == j ? 1.f : 0.f);
+    }
+  int nb[6];
+#pragma unroll
+  for (int d = 0; d < 6; ++d) nb[d] = (own && d < a.ndir) ? __ldg(a.nbr + (size_t)d * ld + n) : -1;
+  double s[D], x[D], bv[D];
+  float s32[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    s[k] = __ldg(a.scale + k);
+    s32[k] = (float)s[k];
+    x[k] = own ? a.x[(size_t)k * ld + n] : 0.0;
+    bv[k] = own ? __ldg(a.b + (size_t)k * ld + n) : 0.0;
+  }
+  const double* Bp = shB + t;
+  const float* Bp32 = shB32 + t;
+  const float* Mp32 = shM32 + t;
+  auto bar = [&]() -> bool {
+    if (a.skip_block == (int)blockIdx.x) return false;
+    return grid_sync(a.bar, &sh.flag);
+  };
+  double tot[4];
+  int outer = 0, inner_total = 0, status = 0;
+  double bb = 0.0, rr = 0.0, rel0 = 0.0, tol2 = 0.0;
+  while (true) {
+    // ---- FP64 true residual (x of every voxel is complete: start value or published) ----
+    double r64[D];
+    {
+      double ax[D];
+      amul<D, double>(Bp, bd, s, nb, a.ndir, x, a.x, ld, ax);
+      double v[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        r64[k] = bv[k] - ax[k];
+        v[0] += r64[k] * r64[k];
+        v[1] += bv[k] * bv[k];
+      }
+      if (!grid_allreduce4(a.bar, a.part, a.tot, v, sh.red, sh.ints, tot)) return;
+    }
+    rr = tot[0];
+    if (outer == 0) {
+      bb = tot[1];
+      tol2 = a.delta * a.delta * bb;
+      rel0 = bb > 0.0 ? sqrt(rr / bb) : 0.0;
+      if (!(isfinite(rr) && isfinite(bb))) { status = 7; break; }
+      if (bb == 0.0) {
+#pragma unroll
+        for (int k = 0; k < D; ++k) x[k] = 0.0;
+        break;
+      }
+    }
+    if (!isfinite(rr)) { status = 7; break; }
+    if (rr <= tol2) break;
+    if (inner_total >= a.max_iter) { status = 4; break; }
+    ++outer;
+    // ---- FP32 inner CG-CG on B~ d = r ----
+    float r[D], u[D], w[D], p[D], q[D], d[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      r[k] = (float)r64[k];
+      d[k] = 0.f;
+      p[k] = 0.f;
+      q[k] = 0.f;
+    }
+    const double itol2 = a.inner_tol * a.inner_tol * rr;
+    minv<D, float>(Mp32, bd, r, u);
+    if (own) {
+#pragma unroll
+      for (int k = 0; k < D; ++k) a.u32[(size_t)k * ld + n] = u[k];
+    }
+    if (!bar()) return;
+    amul<D, float>(Bp32, bd, s32, nb, a.ndir, u, a.u32, ld, w);
+    {
+      float g = 0.f, dl = 0.f, q2 = 0.f;
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        g += r[k] * u[k];
+        dl += w[k] * u[k];
+        q2 += r[k] * r[k];
+      }
+      double v[4] = {(double)g, (double)dl, (double)q2, 0.0};
+      if (!grid_allreduce4(a.bar, a.part, a.tot, v, sh.red, sh.ints, tot)) return;
+    }
+    double gam = tot[0], del = tot[1];
+    if (!(del > 0.0) || !isfinite(del)) { status = isfinite(del) ? 3 : 7; break; }
+    double alpha = gam / del, beta = 0.0;
+    int it = 0;
+    while (true) {
+      const float fa = (float)alpha, fb = (float)beta;
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        p[k] = u[k] + fb * p[k];
+        q[k] = w[k] + fb * q[k];
+        d[k] += fa * p[k];
+        r[k] -= fa * q[k];
+      }
+      minv<D, float>(Mp32, bd, r, u);
+      if (own) {
+#pragma unroll
+        for (int k = 0; k < D; ++k) a.u32[(size_t)k * ld + n] = u[k];
+      }
+      if (!bar()) return;
+      amul<D, float>(Bp32, bd, s32, nb, a.ndir, u, a.u32, ld, w);
+      float g = 0.f, dl = 0.f, q2 = 0.f;
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        g += r[k] * u[k];
+        dl += w[k] * u[k];
+        q2 += r[k] * r[k];
+      }
+      double v[4] = {(double)g, (double)dl, (double)q2, 0.0};
+      if (!grid_allreduce4(a.bar, a.part, a.tot, v, sh.red, sh.ints, tot)) return;
+      ++it;
+      const double gnew = tot[0], dnew = tot[1], rin = tot[2];
+      if (!(isfinite(gnew) && isfinite(dnew) && isfinite(rin))) { status = 7; break; }
+      if (rin <= itol2 || it >= a.max_inner || inner_total + it >= a.max_iter) break;
+      beta = gnew / gam;
+      const double den = dnew - beta * gnew / alpha;
+      if (!(den > 0.0)) break;   // loss of conjugacy in FP32: refine from here
+      alpha = gnew / den;
+      gam = gnew;
+    }
+    inner_total += it;
+    if (status != 0) break;
+#pragma unroll
+    for (int k = 0; k < D; ++k) x[k] += (double)d[k];
+    if (own) {
+#pragma unroll
+      for (int k = 0; k < D; ++k) a.x[(size_t)k * ld + n] = x[k];
+    }
+    if (!bar()) return;
+  }
+  if (own) {
+#pragma unroll
+    for (int k = 0; k < D; ++k) a.x[(size_t)k * ld + n] = x[k];
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    a.ctrl->iterations = inner_total;
+    a.ctrl->restarts = outer;
+    a.ctrl->rel_res = bb > 0.0 ? sqrt(rr / bb) : 0.0;
+    a.ctrl->rel_res0 = rel0;
+    a.ctrl->status = status;
+    if (status != 0 && a.ctrl->status_any == 0) a.ctrl->status_any = status;
+    a.ctrl->iter_total += inner_total;
+    a.ctrl->solves += 1;
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Mixed precision (streaming): the same refinement with vectors in global memory.
+// ---------------------------------------------------------------------------------------
+template <int D>
+__global__ void __launch_bounds__(PCG_THREADS) k_pcg_mixed_stream(PcgArgs a) {
+  __shared__ Shared sh;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nth = gridDim.x * blockDim.x;
+  const size_t ld = a.ld;
+  const bool pre = a.mfac32 != nullptr;
+  double s[D];
+  float s32[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    s[k] = __ldg(a.scale + k);
+    s32[k] = (float)s[k];
+  }
+  auto bar = [&]() -> bool {
+    if (a.skip_block == (int)blockIdx.x) return false;
+    return grid_sync(a.bar, &sh.flag);
+  };
+  auto load_nb = [&](int n, int* nb) {
+#pragma unroll
+    for (int d = 0; d < 6; ++d) nb[d] = d < a.ndir ? __ldg(a.nbr + (size_t)d * ld + n) : -1;
+  };
+  auto precond = [&](int n, const float* rn, float* un) {
+    if (pre) {
+      minv<D, float>(a.mfac32 + n, (int)ld, rn, un);
+    } else {
+#pragma unroll
+      for (int k = 0; k < D; ++k) un[k] = rn[k];
+    }
+  };
+  // inner matvec phase: w = B~ u and the three partial sums
+  auto matvec_partials = [&](double* tot) -> bool {
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int n = tid; n < a.N; n += nth) {
+      int nb[6];
+      load_nb(n, nb);
+      float un[D], wn[D];
+#pragma unroll
+      for (int k = 0; k < D; ++k) un[k] = a.u32[(size_t)k * ld + n];
+      amul<D, float>(a.blocks32 + n, (int)ld, s32, nb, a.ndir, un, a.u32, ld, wn);
+      float g = 0.f, dl = 0.f, q2 = 0.f;
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        const float rk = a.r32[(size_t)k * ld + n];
+        a.w32[(size_t)k * ld + n] = wn[k];
+        g += rk * un[k];
+        dl += wn[k] * un[k];
+        q2 += rk * rk;
+      }
+      v[0] += g;
+      v[1] += dl;
+      v[2] += q2;
+    }
+    return grid_allreduce4(a.bar, a.part, a.tot, v, sh.red, sh.ints, tot);
+  };
+  double tot[4];
+  int outer = 0, inner_total = 0, status = 0;
+  double bb = 0.0, rr = 0.0, rel0 = 0.0, tol2 = 0.0;
+  while (true) {
+    {
+      double v[4] = {0.0, 0.0, 0.0, 0.0};
+      for (int n = tid; n < a.N; n += nth) {
+        int nb[6];
+        load_nb(n, nb);
+        double xn[D], ax[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) xn[k] = ldx(a.x + (size_t)k * ld + n);
+        amul<D, double>(a.blocks + n, (int)ld, s, nb, a.ndir, xn, a.x, ld, ax);
+        float rn[D], un[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          const double bk = __ldg(a.b + (size_t)k * ld + n);
+          const double rk = bk - ax[k];
+          v[0] += rk * rk;
+          v[1] += bk * bk;
+          rn[k] = (float)rk;
+        }
+        precond(n, rn, un);
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          a.r32[(size_t)k * ld + n] = rn[k];
+          a.u32[(size_t)k * ld + n] = un[k];
+          a.d32[(size_t)k * ld + n] = 0.f;
+          a.p32[(size_t)k * ld + n] = 0.f;
+          a.s32[(size_t)k * ld + n] = 0.f;
+        }
+      }
+      if (!grid_allreduce4(a.bar, a.part, a.tot, v, sh.red, sh.ints, tot)) return;
+    }
+    rr = tot[0];
+    if (outer == 0) {
+      bb = tot[1];
+      tol2 = a.delta * a.delta * bb;
+      rel0 = bb > 0.0 ? sqrt(rr / bb) : 0.0;
+      if (!(isfinite(rr) && isfinite(bb))) { status = 7; break; }
+      if (bb == 0.0) {
+        for (int n = tid; n < a.N; n += nth)
+#pragma unroll
+          for (int k = 0; k < D; ++k) a.x[(size_t)k * ld + n] = 0.0;
+        break;
+      }
+    }
+    if (!isfinite(rr)) { status = 7; break; }
+    if (rr <= tol2) break;
+    if (inner_total >= a.max_iter) { status = 4; break; }
+    ++outer;
+    const double itol2 = a.inner_tol * a.inner_tol * rr;
+    // u was published by the residual phase, whose reducing barrier has completed
+    if (!matvec_partials(tot)) return;
+    double gam = tot[0], del = tot[1];
+    if (!(del > 0.0) || !isfinite(del)) { status = isfinite(del) ? 3 : 7; break; }
+    double alpha = gam / del, beta = 0.0;
+    int it = 0;
+    while (true) {
+      const float fa = (float)alpha, fb = (float)beta;
+      for (int n = tid; n < a.N; n += nth) {
+        float rn[D], un[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          const size_t o = (size_t)k * ld + n;
+          const float pk = a.u32[o] + fb * a.p32[o];
+          const float sk = a.w32[o] + fb * a.s32[o];
+          a.p32[o] = pk;
+          a.s32[o] = sk;
+          a.d32[o] += fa * pk;
+          rn[k] = a.r32[o] - fa * sk;
+          a.r32[o] = rn[k];
+        }
+        precond(n, rn, un);
+#pragma unroll
+        for (int k = 0; k < D; ++k) a.u32[(size_t)k * ld + n] = un[k];
+      }
+      if (!bar()) return;
+      if (!matvec_partials(tot)) return;
+      ++it;
+      const double gnew = tot[0], dnew = tot[1], rin = tot[2];
+      if (!(isfinite(gnew) && isfinite(dnew) && isfinite(rin))) { status = 7; break; }
+      if (rin <= itol2 || it >= a.max_inner || inner_total + it >= a.max_iter) break;
+      beta = gnew / gam;
+      const double den = dnew - beta * gnew / alpha;
+      if (!(den > 0.0)) break;
+      alpha = gnew / den;
+      gam = gnew;
+    }
+    inner_total += it;
+    if (status != 0) break;
+    for (int n = tid; n < a.N; n += nth)
+#pragma unroll
+      for (int k = 0; k < D; ++k) a.x[(size_t)k * ld + n] += (double)a.d32[(size_t)k * ld + n];
+    if (!bar()) return;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    a.ctrl->iterations = inner_total;
+    a.ctrl->restarts = outer;
+    a.ctrl->rel_res = bb > 0.0 ? sqrt(rr / bb) : 0.0;
+    a.ctrl->rel_res0 = rel0;
+    a.ctrl->status = status;
+    if (status != 0 && a.ctrl->status_any == 0) a.ctrl->status_any = status;
+    a.ctrl->iter_total += inner_total;
+    a.ctrl->solves += 1;
+  }
+}
+
 // ---------------------------------------------------------------------------------------
 // launch
 // ---------------------------------------------------------------------------------------
@@ -419,13 +764,16 @@ cudaError_t launch_resident(const PcgArgs& a, cudaStream_t stream, int* grid_out
   if (threads > RES_MAX_THREADS) return cudaSuccess;
   const int grid = (a.N + threads - 1) / threads;
   if (a.max_grid > 0 && grid > a.max_grid) return cudaSuccess;
-  const size_t shm = (size_t)2 * ntri(D) * threads * sizeof(double);
-  if (cudaFuncSetAttribute(k_pcg_res<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm) != cudaSuccess) {
+  // FP64: blocks + factor in FP64; mixed: FP64 blocks + FP32 blocks + FP32 factor
+  const size_t shm = a.mixed ? (size_t)ntri(D) * threads * (sizeof(double) + 2 * sizeof(float))
+                             : (size_t)2 * ntri(D) * threads * sizeof(double);
+  const void* kern = a.mixed ? (const void*)k_pcg_mixed_res<D> : (const void*)k_pcg_res<D>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm) != cudaSuccess) {
     cudaGetLastError();
     return cudaSuccess;
   }
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_res<D>, threads, shm) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, shm) != cudaSuccess) {
     cudaGetLastError();
     return cudaSuccess;
   }
@@ -433,7 +781,7 @@ cudaError_t launch_resident(const PcgArgs& a, cudaStream_t stream, int* grid_out
   if (grid_out) *grid_out = grid;
   *launched = true;
   void* args[] = {(void*)&a};
-  return cudaLaunchCooperativeKernel((const void*)k_pcg_res<D>, dim3(grid), dim3(threads), args, shm, stream);
+  return cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(threads), args, shm, stream);
 }
 
 }  // namespace
@@ -448,8 +796,9 @@ static cudaError_t launch_d(const PcgArgs& a, cudaStream_t stream, int* grid_out
     }
   }
   const int nsm = num_sms();
+  const void* kern = a.mixed ? (const void*)k_pcg_mixed_stream<D> : (const void*)k_pcg_stream<D>;
   int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_stream<D>, PCG_THREADS, 0);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, PCG_THREADS, 0);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   const int need = (a.N + PCG_THREADS - 1) / PCG_THREADS;
@@ -458,15 +807,16 @@ static cudaError_t launch_d(const PcgArgs& a, cudaStream_t stream, int* grid_out
   if (a.max_grid > 0 && grid > a.max_grid) grid = a.max_grid;
   if (grid_out) *grid_out = grid;
   void* args[] = {(void*)&a};
-  return cudaLaunchCooperativeKernel((const void*)k_pcg_stream<D>, dim3(grid), dim3(PCG_THREADS), args, 0, stream);
+  return cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(PCG_THREADS), args, 0, stream);
 }
 
 template <int D>
 static int max_grid_d() {
-  int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_stream<D>, PCG_THREADS, 0);
-  const int nsm = num_sms();
-  return nsm * (per_sm > 1 ? per_sm : 1);
+  int p1 = 0, p2 = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p1, k_pcg_stream<D>, PCG_THREADS, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p2, k_pcg_mixed_stream<D>, PCG_THREADS, 0);
+  const int per_sm = p1 > p2 ? p1 : p2;
+  return num_sms() * (per_sm > 1 ? per_sm : 1);
 }
 
 #define BFMRI_PCG_CASES(X) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12)

@@ -62,6 +62,8 @@ struct AssembleArgs {
   // outputs
   double* blocks;       // [ntri(D)][ld]
   double* mfac;         // [ntri(D)][ld]
+  float* blocks32;      // [ntri(D)][ld] FP32 copies for the mixed-precision solver (or null)
+  float* mfac32;
   double* rhs;          // [D][ld]
   double* bmean;        // [D][ld] (may be null)
   double* G;            // A system: [n_syy(P)][ld] lagged residual Gram (for lambda)

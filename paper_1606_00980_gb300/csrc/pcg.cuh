@@ -48,6 +48,18 @@ struct PcgArgs {
   int skip_block;        // test hook (-1 off): this CTA never reaches the first barrier
   int max_grid;          // rows of the partial buffer: the launch never uses more CTAs
   int allow_resident;    // 1: use the register/shared-memory resident variant when N fits
+  // mixed precision: FP32 inner PCG inside FP64 iterative refinement
+  int mixed;
+  const float* blocks32; // [ntri(D)][ld] FP32 copies of blocks / mfac
+  const float* mfac32;
+  float* u32;            // [D][ld] inner preconditioned residual, exchanged between CTAs
+  float* r32;            // [D][ld] streaming-variant work
+  float* w32;
+  float* p32;
+  float* s32;
+  float* d32;
+  double inner_tol;      // relative tolerance of each inner solve
+  int max_inner;         // inner iteration cap per refinement step
 };
 
 // Launches the cooperative persistent PCG kernel for dimension D (1..12) on `stream`.

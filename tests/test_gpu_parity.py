@@ -141,25 +141,48 @@ def test_apply_precision(case, which):
     m.close()
 
 
-def test_sample_W_matches_exact_solve(case):
+@pytest.mark.parametrize("variant", ["auto", "streaming"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_sample_W_matches_exact_solve(case, variant, precision):
+    """Both solver variants (register-resident and streaming) and both precisions reach the
+    oracle's exact draw: FP64 and FP32-inner/FP64-refined solves to relative residual 1e-12."""
+    from paper_1606_00980_gb300 import bfmri
     w, lat, st, s = case
-    m = make(w, s)
+    m = make(w, s, pcg_variant=bfmri.PCG_AUTO if variant == "auto" else bfmri.PCG_STREAMING,
+             precision=bfmri.PREC_FP64 if precision == "fp64" else bfmri.PREC_MIXED)
     W, info = m.sample_W(counter=3)
     Bd, bw = model.w_blocks_direct(w.Y, w.X, s["A"], s["lam"], w.eps)
     ref, mu = gibbs.draw_gmrf(lat, Bd, bw, s["alpha"], SEED, 3, philox.TAG_W)
     assert info.rel_residual <= 1e-12
     assert rel(W, ref) <= 1e-8
     assert rel(W, mu) > 1e-4          # it is a draw, not the mean
+    if precision == "mixed":
+        assert info.refinements >= 1
     m.close()
 
 
-@pytest.mark.parametrize("spatial", [True, False])
-def test_sample_A_matches_exact_solve(case, spatial):
+def test_mixed_precision_at_delta_1e8(case):
+    """Mixed precision stopped at the paper's delta = 1e-8: the draw is within 1e-5 (relative
+    L2) of the FP64 oracle's exact draw."""
+    from paper_1606_00980_gb300 import bfmri
+    w, lat, st, s = case
+    m = make(w, s, precision=bfmri.PREC_MIXED, delta=1e-8)
+    W, info = m.sample_W(counter=8)
+    Bd, bw = model.w_blocks_direct(w.Y, w.X, s["A"], s["lam"], w.eps)
+    ref, _ = gibbs.draw_gmrf(lat, Bd, bw, s["alpha"], SEED, 8, philox.TAG_W)
+    assert info.rel_residual <= 1e-8
+    assert rel(W, ref) <= 1e-5
+    m.close()
+
+
+@pytest.mark.parametrize("spatial,variant", [(True, "auto"), (True, "streaming"), (False, "auto")])
+def test_sample_A_matches_exact_solve(case, spatial, variant):
     w, lat, st, s = case
     if w.P == 0:
         pytest.skip("no AR part")
     from paper_1606_00980_gb300 import bfmri
-    m = make(w, s, ar_prior=bfmri.AR_SPATIAL if spatial else bfmri.AR_INDEPENDENT)
+    m = make(w, s, ar_prior=bfmri.AR_SPATIAL if spatial else bfmri.AR_INDEPENDENT,
+             pcg_variant=bfmri.PCG_AUTO if variant == "auto" else bfmri.PCG_STREAMING)
     A, info = m.sample_A(counter=4)
     ref = gibbs.sample_A(lat, w.Y, w.X, s, SEED, 4, spatial=spatial)
     assert rel(A, ref) <= 1e-8
