@@ -227,6 +227,46 @@ bfmri_status bfmri_apply_precision(bfmri_handle* h, int which, const double* x, 
 bfmri_status bfmri_build_system(bfmri_handle* h, int which, uint64_t counter, double* blocks,
                                 double* b_mean, double* b_pert);
 
+/* ---------------------------------------------------------------------------------------
+ * Allocation-free solve (the paper has no counterpart: this is an interface addition).
+ *
+ * For callers that cannot allocate device memory while they run: code that executes inside
+ * another framework's memory pool or arena and may not call cudaMalloc behind its back, a
+ * process that must not grow its device footprint after start-up, or a real-time loop where
+ * an allocation (and the implicit device synchronisation of cudaMalloc / cudaFree) would
+ * stall. bfmri_pcg_solve_static solves B~ x = b with the same FP64 block-Jacobi PCG as
+ * bfmri_sample_W, on device arrays the caller owns, and allocates nothing: its scratch (the
+ * preconditioner factor, five work vectors, reduction and barrier words) lives in one
+ * static device array of bfmri_pcg_static_capacity() bytes (32 MiB) that every GPU which
+ * loads the library holds until the process exits.
+ *
+ *  N, D          voxels and unknowns per voxel (1 <= D <= 12)
+ *  neighbourhood 4 or 6: how many of the six neighbour planes are used
+ *  nbr           device, int32 [6][ld]: compact index of the -x,+x,-y,+y,-z,+z neighbour of
+ *                each voxel, or -1
+ *  ld            leading dimension (>= N) of every [rows][ld] device array
+ *  blocks        device, FP64 [D(D+1)/2][ld]: per-voxel data block, packed lower triangle
+ *                (entry (i, j), i >= j, in plane i(i+1)/2 + j)
+ *  scale         device, FP64 [D]: prior scale per component (alpha or beta)
+ *  b             device, FP64 [D][ld]: right-hand side
+ *  x             device, FP64 [D][ld]: start value in, solution out (stop when
+ *                ||b - B~ x|| <= delta ||b||, or after max_iter iterations)
+ *  cuda_stream   stream for all work (NULL: legacy default stream); the call waits for it
+ *  info          may be NULL
+ * Set-up: the first call on each device looks up the device address of the static array
+ * (cudaGetSymbolAddress, with that device current) and caches it; make that first call before
+ * any stream capture on the device. Every call reuses the same array and clears what must
+ * start at zero, so calls that overlap on the GPU (other streams or threads, same device)
+ * race and must be serialised by the caller. Problems whose scratch need
+ * (bfmri_pcg_static_bytes(ld, D)) exceeds the capacity are rejected with
+ * BFMRI_ERR_INVALID_ARG; errors are reported through bfmri_last_error(NULL). */
+size_t bfmri_pcg_static_capacity(void);
+size_t bfmri_pcg_static_bytes(size_t ld, int D);
+bfmri_status bfmri_pcg_solve_static(int N, int D, int neighbourhood, const int* nbr, size_t ld,
+                                    const double* blocks, const double* scale, const double* b,
+                                    double* x, double delta, int max_iter, void* cuda_stream,
+                                    bfmri_solve_info* info);
+
 #ifdef __cplusplus
 }
 #endif

@@ -94,6 +94,11 @@ SIGNATURES = [
     ("bfmri_reset_timing", C.c_int, [_h]),
     ("bfmri_apply_precision", C.c_int, [_h, C.c_int, _dp, _dp]),
     ("bfmri_build_system", C.c_int, [_h, C.c_int, C.c_uint64, _dp, _dp, _dp]),
+    ("bfmri_pcg_static_capacity", C.c_size_t, []),
+    ("bfmri_pcg_static_bytes", C.c_size_t, [C.c_size_t, C.c_int]),
+    ("bfmri_pcg_solve_static", C.c_int, [C.c_int, C.c_int, C.c_int, _vp, C.c_size_t, _vp, _vp,
+                                         _vp, _vp, C.c_double, C.c_int, _vp,
+                                         _P(bfmri_solve_info)]),
 ]
 
 _lib = None
@@ -211,6 +216,17 @@ def bfmri_create(lattice, mask, X, Y, K, P, opts=None, torch_memory=True):
 
 def bfmri_destroy(h):
     _check(load_library().bfmri_destroy(h))
+
+
+def bfmri_pcg_solve_static(N, D, neighbourhood, nbr_ptr, ld, blocks_ptr, scale_ptr, b_ptr,
+                           x_ptr, delta, max_iter, stream=None):
+    """The allocation-free solve on caller-owned device arrays (pointers as integers)."""
+    info = bfmri_solve_info()
+    st = load_library().bfmri_pcg_solve_static(N, D, neighbourhood, nbr_ptr, ld, blocks_ptr,
+                                               scale_ptr, b_ptr, x_ptr, delta, max_iter, stream,
+                                               C.byref(info))
+    _check(st, None)
+    return info
 
 
 class Model:

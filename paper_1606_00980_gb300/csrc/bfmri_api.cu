@@ -21,6 +21,14 @@ std::mutex g_err_mu;
 std::string g_create_err = "no error";
 }  // namespace
 
+namespace bfmri {
+// Process-wide error message (what bfmri_last_error(NULL) returns), for calls without a handle.
+void set_global_error(const std::string& msg) {
+  std::lock_guard<std::mutex> lk(g_err_mu);
+  g_create_err = msg;
+}
+}  // namespace bfmri
+
 struct bfmri_handle {
   int nx = 0, ny = 0, nz = 0, nbh = 6, ndir = 6;
   int N = 0, T = 0, K = 0, P = 0, D = 0;
