@@ -195,6 +195,31 @@ bfmri_status bfmri_sample_beta(bfmri_handle* h, uint64_t counter, double* beta_o
 bfmri_status bfmri_gibbs_sweep(bfmri_handle* h, int n_sweeps, uint64_t first_counter,
                                bfmri_sweep_info* info);
 
+/* Log-determinant and trace probes of the W (which = 0) or A (which = 1) full-conditional
+ * precision B~ at the current state. The paper leaves the log-determinant to future work
+ * (Discussion: model evidence, collapsed alpha); this is stochastic Lanczos quadrature:
+ *   log det B~ = log det M + tr log(L^-1 B~ L^-T),  M = L L' the block-Jacobi preconditioner,
+ * with n_probes Rademacher vectors v_i (Philox, draw counter `counter`, stream = probe
+ * index), each solved by the multi-right-hand-side PCG from x = 0 on B~ x = L v_i to relative
+ * residual `delta` of the options (at most lanczos_steps iterations, whose CG coefficients
+ * form the Lanczos tridiagonal T_i): estimate_i = ||v_i||^2 e1' log(T_i) e1.
+ *  logdet   : log det M + mean_i estimate_i
+ *  std_err  : standard error of the mean over probes (may be NULL)
+ *  traces   : dim values, mean_i (L^-T v_i)' D_w^(k) y_i with y_i = B~^-1 L v_i, an unbiased
+ *             estimate of tr(D_w^(k) B~^-1), the trace term of the SVB alpha update
+ *             (Eq. quad-form-expectation); may be NULL
+ *  per_probe: n_probes values estimate_i (may be NULL)
+ * Errors: STATE, NOT_CONVERGED (a probe hit lanczos_steps), NOT_SPD, CUDA, OOM. */
+bfmri_status bfmri_logdet_probe(bfmri_handle* h, int which, int n_probes, int lanczos_steps,
+                                uint64_t counter, double* logdet, double* std_err,
+                                double* traces, double* per_probe);
+
+/* Gauss quadrature value e1' log(T) e1 of the Lanczos tridiagonal T built from m CG
+ * coefficients (alpha_0..alpha_{m-1}, beta_0..beta_{m-2}) of a preconditioned CG run from
+ * x = 0; host-only helper used by bfmri_logdet_probe. */
+bfmri_status bfmri_lanczos_log_quadrature(int m, const double* cg_alpha, const double* cg_beta,
+                                          double* value);
+
 /* Per-kernel device time, accumulated since the last reset when options.profile is set
  * (CUDA events recorded around each launch on the handle's stream). Classes: */
 #define BFMRI_T_STATS      0  /* sufficient statistics */

@@ -90,6 +90,8 @@ SIGNATURES = [
     ("bfmri_sample_alpha", C.c_int, [_h, C.c_uint64, _dp]),
     ("bfmri_sample_beta", C.c_int, [_h, C.c_uint64, _dp]),
     ("bfmri_gibbs_sweep", C.c_int, [_h, C.c_int, C.c_uint64, _P(bfmri_sweep_info)]),
+    ("bfmri_logdet_probe", C.c_int, [_h, C.c_int, C.c_int, C.c_int, C.c_uint64, _dp, _dp, _dp, _dp]),
+    ("bfmri_lanczos_log_quadrature", C.c_int, [C.c_int, _dp, _dp, _dp]),
     ("bfmri_get_timing", C.c_int, [_h, _P(bfmri_timing)]),
     ("bfmri_reset_timing", C.c_int, [_h]),
     ("bfmri_apply_precision", C.c_int, [_h, C.c_int, _dp, _dp]),
@@ -229,6 +231,14 @@ def bfmri_pcg_solve_static(N, D, neighbourhood, nbr_ptr, ld, blocks_ptr, scale_p
     return info
 
 
+def lanczos_log_quadrature(cg_alpha, cg_beta):
+    a = _f64(cg_alpha)
+    b = _f64(cg_beta) if len(cg_beta) else np.zeros(1)
+    v = C.c_double()
+    _check(load_library().bfmri_lanczos_log_quadrature(len(a), _ptr(a), _ptr(b), C.byref(v)))
+    return v.value
+
+
 class Model:
     """Owns one handle: a subject's data, its statistics and its chain state on the GPU."""
 
@@ -317,6 +327,16 @@ class Model:
         self._c(self.lib.bfmri_gibbs_sweep(self.handle, n_sweeps, first_counter,
                                            C.byref(inf) if info else None))
         return inf
+
+    def logdet_probe(self, which, n_probes, lanczos_steps, counter, traces=True):
+        D = self.K if which == 0 else self.P
+        ld = C.c_double()
+        se = C.c_double()
+        tr = np.empty(D) if traces else None
+        pp = np.empty(n_probes)
+        self._c(self.lib.bfmri_logdet_probe(self.handle, which, n_probes, lanczos_steps, counter,
+                                            C.byref(ld), C.byref(se), _ptr(tr), _ptr(pp)))
+        return dict(logdet=ld.value, stderr=se.value, traces=tr, per_probe=pp)
 
     def timing(self):
         t = bfmri_timing()

@@ -12,6 +12,7 @@
 
 #include "../../include/bfmri.h"
 #include "model.cuh"
+#include "mrhs.cuh"
 #include "pcg.cuh"
 
 using namespace bfmri;
@@ -60,6 +61,14 @@ struct bfmri_handle {
   int part_rows = 0;
   std::vector<double> Sxx;
   int stride[3] = {1, 1, 1};
+  // multi-right-hand-side workspace, grown on demand
+  int mr_S = 0, mr_D = 0, mr_hist_len = 0, mr_units = 0;
+  size_t mr_vs = 0;
+  double *mr_b = nullptr, *mr_x = nullptr, *mr_r = nullptr, *mr_u = nullptr, *mr_w = nullptr;
+  double *mr_p = nullptr, *mr_s = nullptr, *mr_part = nullptr, *mr_hist = nullptr, *mr_out = nullptr;
+  size_t mr_out_len = 0;
+  RhsState* mr_st = nullptr;
+  int* mr_flags = nullptr;
   // profiling: events recorded around launches, resolved lazily
   struct Pending { int cls; cudaEvent_t e0, e1; bool pcg; int which; };
   std::vector<Pending> pending;
@@ -408,6 +417,79 @@ bfmri_status resolve_timing(bfmri_handle* h) {
   }
   h->pending.clear();
   return BFMRI_OK;
+}
+
+// Multi-RHS buffers for S right-hand sides of dimension D and hist_len recorded iterations.
+bfmri_status ensure_mrhs(bfmri_handle* h, int D, int S, int hist_len) {
+  const size_t vs = (size_t)D * h->ld;
+  const int units = mrhs_max_units(D, S);
+  const size_t out_len = std::max((size_t)h->ld, (size_t)((h->N + 127) / 128) * S * D);
+  if (S <= h->mr_S && D <= h->mr_D && hist_len <= h->mr_hist_len && units <= h->mr_units &&
+      out_len <= h->mr_out_len)
+    return BFMRI_OK;
+  double** vecs[] = {&h->mr_b, &h->mr_x, &h->mr_r, &h->mr_u, &h->mr_w, &h->mr_p, &h->mr_s};
+  for (double** v : vecs) {
+    dfree(h, *v);
+    *v = nullptr;
+  }
+  dfree(h, h->mr_part);
+  dfree(h, h->mr_hist);
+  dfree(h, h->mr_out);
+  dfree(h, h->mr_st);
+  dfree(h, h->mr_flags);
+  h->mr_S = h->mr_D = h->mr_hist_len = h->mr_units = 0;
+  for (double** v : vecs) {
+    *v = (double*)dalloc(h, (size_t)S * vs * sizeof(double));
+    if (!*v) return fail(h, BFMRI_ERR_OOM, "multi-RHS workspace allocation failed");
+  }
+  h->mr_part = (double*)dalloc(h, (size_t)units * 4 * sizeof(double));
+  h->mr_hist = (double*)dalloc(h, (size_t)std::max(hist_len, 1) * S * 2 * sizeof(double));
+  h->mr_out = (double*)dalloc(h, out_len * sizeof(double));
+  h->mr_st = (RhsState*)dalloc(h, (size_t)S * sizeof(RhsState));
+  h->mr_flags = (int*)dalloc(h, 4 * sizeof(int));
+  if (!h->mr_part || !h->mr_hist || !h->mr_out || !h->mr_st || !h->mr_flags)
+    return fail(h, BFMRI_ERR_OOM, "multi-RHS workspace allocation failed");
+  h->mr_S = S;
+  h->mr_D = D;
+  h->mr_vs = vs;
+  h->mr_hist_len = hist_len;
+  h->mr_units = units;
+  h->mr_out_len = out_len;
+  return BFMRI_OK;
+}
+
+MrhsArgs mrhs_args(bfmri_handle* h, int D, int S, const double* scale, int max_iter, bool hist) {
+  MrhsArgs m;
+  memset(&m, 0, sizeof(m));
+  m.N = h->N;
+  m.ld = h->ld;
+  m.ndir = h->ndir;
+  m.nbr = h->d_nbr;
+  m.blocks = h->d_blocks;
+  m.mfac = h->opt.precond == BFMRI_PRECOND_BLOCK_JACOBI ? h->d_mfac : nullptr;
+  m.scale = scale;
+  m.S = S;
+  m.vs = h->mr_vs;
+  m.b = h->mr_b;
+  m.x = h->mr_x;
+  m.r = h->mr_r;
+  m.u = h->mr_u;
+  m.w = h->mr_w;
+  m.p = h->mr_p;
+  m.s = h->mr_s;
+  m.part = h->mr_part;
+  m.st = h->mr_st;
+  m.hist = hist ? h->mr_hist : nullptr;
+  m.hist_len = hist ? h->mr_hist_len : 0;
+  m.flags = h->mr_flags;
+  m.bar.count = h->d_bar;
+  m.bar.gen = h->d_bar + 1;
+  m.bar.err = h->d_err;
+  m.bar.timeout_ns = (unsigned long long)(h->opt.barrier_timeout_s * 1e9);
+  m.delta = h->opt.delta;
+  m.max_iter = max_iter;
+  m.max_restarts = 4;
+  return m;
 }
 
 bfmri_status require_stats(bfmri_handle* h) {
@@ -848,6 +930,118 @@ bfmri_status bfmri_reset_timing(bfmri_handle* h) {
   if (!h) return BFMRI_ERR_INVALID_ARG;
   RET(resolve_timing(h));
   memset(&h->timing, 0, sizeof(h->timing));
+  return BFMRI_OK;
+}
+
+bfmri_status bfmri_logdet_probe(bfmri_handle* h, int which, int n_probes, int lanczos_steps,
+                                uint64_t counter, double* logdet, double* std_err,
+                                double* traces, double* per_probe) {
+  RET(require_stats(h));
+  if ((which != 0 && which != 1) || n_probes < 1 || n_probes > 4096 || lanczos_steps < 1)
+    return fail(h, BFMRI_ERR_INVALID_ARG, "bad arguments");
+  const int D = which == 0 ? h->K : h->P;
+  if (D == 0) return fail(h, BFMRI_ERR_INVALID_ARG, "no AR part (P = 0)");
+  RET(begin_call(h));
+  const double* scale = which == 0 ? h->d_alpha : h->d_beta;
+  if (which == 1 && h->opt.ar_prior != BFMRI_AR_SPATIAL) {
+    static const double zeros[PMAX] = {0, 0, 0, 0};
+    CU(h, cudaMemcpyAsync(h->d_bmean, zeros, D * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    scale = h->d_bmean;
+  }
+  AssembleArgs a = assemble_args(h, scale, 0, which == 0 ? TAG_W : TAG_A);
+  a.perturb = 0;
+  a.blocks32 = nullptr;
+  a.mfac32 = nullptr;
+  {
+    Timed tm(h, which == 0 ? BFMRI_T_ASSEMBLE_W : BFMRI_T_ASSEMBLE_A);
+    cudaError_t e = which == 0 ? launch_assemble_w(a, h->stream) : launch_assemble_a(a, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "assemble");
+  }
+  RET(ensure_mrhs(h, D, n_probes, lanczos_steps));
+  const bool pre = h->opt.precond == BFMRI_PRECOND_BLOCK_JACOBI;
+  ProbeArgs pa;
+  pa.N = h->N;
+  pa.ld = h->ld;
+  pa.ndir = h->ndir;
+  pa.nbr = h->d_nbr;
+  pa.lin = h->d_lin;
+  pa.mfac = pre ? h->d_mfac : nullptr;
+  pa.S = n_probes;
+  pa.vs = h->mr_vs;
+  pa.b = h->mr_b;
+  pa.x = h->mr_x;
+  pa.rng = rng_of(h, counter, TAG_PROBE);
+  cudaError_t e = launch_probe(D, pa, 0, nullptr, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "probe rhs");
+  MrhsArgs m = mrhs_args(h, D, n_probes, scale, lanczos_steps, true);
+  {
+    Timed tm(h, BFMRI_T_OTHER, true, 0);
+    int units = 0;
+    e = launch_mrhs(D, m, h->stream, &units);
+    if (e != cudaSuccess) return cuda_fail(h, e, "multi-RHS PCG");
+  }
+  RET(end_call(h, nullptr, nullptr));
+  std::vector<RhsState> st(n_probes);
+  CU(h, cudaMemcpy(st.data(), h->mr_st, n_probes * sizeof(RhsState), cudaMemcpyDeviceToHost));
+  for (int i = 0; i < n_probes; ++i) {
+    if (st[i].status == 4) return fail(h, BFMRI_ERR_NOT_CONVERGED, "probe solve reached lanczos_steps");
+    if (st[i].status == 3) return fail(h, BFMRI_ERR_NOT_SPD, "probe solve breakdown");
+    if (st[i].status != 0) return fail(h, BFMRI_ERR_INVALID_ARG, "non-finite value in probe solve");
+  }
+  std::vector<double> hist((size_t)lanczos_steps * n_probes * 2);
+  CU(h, cudaMemcpy(hist.data(), h->mr_hist, hist.size() * sizeof(double), cudaMemcpyDeviceToHost));
+  // log det M
+  double ldm = 0.0;
+  if (pre) {
+    e = launch_probe(D, pa, 1, h->mr_out, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "logdet M");
+    std::vector<double> v(h->N);
+    CU(h, cudaMemcpyAsync(v.data(), h->mr_out, h->N * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CU(h, cudaStreamSynchronize(h->stream));
+    for (int n = 0; n < h->N; ++n) ldm += v[n];
+  }
+  // Lanczos quadrature per probe
+  const double vnorm2 = (double)D * h->N;
+  std::vector<double> est(n_probes);
+  for (int i = 0; i < n_probes; ++i) {
+    const int mi = std::min(st[i].iters, lanczos_steps);
+    if (mi < 1) {
+      est[i] = 0.0;
+      continue;
+    }
+    std::vector<double> al(mi), be(mi);
+    for (int j = 0; j < mi; ++j) {
+      al[j] = hist[((size_t)j * n_probes + i) * 2 + 0];
+      be[j] = hist[((size_t)j * n_probes + i) * 2 + 1];
+    }
+    double q = 0.0;
+    bfmri_status qs = bfmri_lanczos_log_quadrature(mi, al.data(), be.data(), &q);
+    if (qs != BFMRI_OK) return fail(h, qs, "Lanczos quadrature failed");
+    est[i] = vnorm2 * q;
+  }
+  double mean = 0.0;
+  for (double v : est) mean += v;
+  mean /= n_probes;
+  double var = 0.0;
+  for (double v : est) var += (v - mean) * (v - mean);
+  if (logdet) *logdet = ldm + mean;
+  if (std_err) *std_err = n_probes > 1 ? std::sqrt(var / (n_probes - 1) / n_probes) : 0.0;
+  if (per_probe)
+    for (int i = 0; i < n_probes; ++i) per_probe[i] = est[i];
+  if (traces) {
+    e = launch_probe(D, pa, 2, h->mr_out, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "traces");
+    const int gx = (h->N + 127) / 128;
+    std::vector<double> part((size_t)gx * n_probes * D);
+    CU(h, cudaMemcpyAsync(part.data(), h->mr_out, part.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CU(h, cudaStreamSynchronize(h->stream));
+    for (int k = 0; k < D; ++k) {
+      double t = 0.0;
+      for (int i = 0; i < n_probes; ++i)
+        for (int g = 0; g < gx; ++g) t += part[((size_t)g * n_probes + i) * D + k];
+      traces[k] = t / n_probes;
+    }
+  }
   return BFMRI_OK;
 }
 

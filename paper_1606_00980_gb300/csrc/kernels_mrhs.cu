@@ -1,0 +1,553 @@
+// Multi-right-hand-side PCG (one matrix, S right-hand sides) in one cooperative launch.
+// Used by the log-determinant / trace probes and by the spatial-VB step, whose N_s samples
+// share B~_SVB (Section 3.3: "the same pre-conditioner can be used for all samples").
+//
+// Work decomposition: the grid's warps are split into S x C units (right-hand side r, voxel
+// chunk c); lanes of a warp take consecutive voxels of the chunk, so every vector access is
+// coalesced, and each unit produces one row of partial sums. At each reducing barrier the CTA
+// that arrives last sums the rows of every right-hand side in a fixed order and advances its
+// CG scalars (Chronopoulos-Gear recurrence, as in the single solve), records the CG
+// coefficients (alpha_j, beta_j) of the first run for Lanczos quadrature, and marks converged
+// right-hand sides, which then stop moving. Converged right-hand sides are confirmed with the
+// true residual b - B~ x before they are released.
+#include "mrhs.cuh"
+
+namespace bfmri {
+
+namespace {
+
+constexpr int MRHS_THREADS = 256;
+
+__device__ __forceinline__ double ldc(const double* p) { return __ldcg(p); }
+
+template <int D>
+__device__ __forceinline__ void block_apply(const MrhsArgs& a, int n, const double* v, const double* V, double* out) {
+  const size_t ld = a.ld;
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    double acc = 0.0;
+#pragma unroll
+    for (int j = 0; j < D; ++j) acc += __ldg(a.blocks + (size_t)(i >= j ? tri(i, j) : tri(j, i)) * ld + n) * v[j];
+    out[i] = acc;
+  }
+  double sum[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) sum[k] = 0.0;
+  int deg = 0;
+  for (int d = 0; d < a.ndir; ++d) {
+    const int m = __ldg(a.nbr + (size_t)d * ld + n);
+    if (m >= 0) {
+      ++deg;
+#pragma unroll
+      for (int k = 0; k < D; ++k) sum[k] += ldc(V + (size_t)k * ld + m);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < D; ++k) out[k] += __ldg(a.scale + k) * ((double)deg * v[k] - sum[k]);
+}
+
+template <int D>
+__device__ __forceinline__ void precond_apply(const MrhsArgs& a, int n, const double* r, double* z) {
+  if (a.mfac == nullptr) {
+#pragma unroll
+    for (int k = 0; k < D; ++k) z[k] = r[k];
+    return;
+  }
+  double L[ntri(D)];
+#pragma unroll
+  for (int e = 0; e < ntri(D); ++e) L[e] = __ldg(a.mfac + (size_t)e * a.ld + n);
+  chol_solve_invdiag<D>(L, r, z);
+}
+
+struct Units {
+  int S, chunks, units, csize, gw, nw, lane;
+};
+
+__device__ __forceinline__ Units units_of(const MrhsArgs& a) {
+  Units u;
+  u.S = a.S;
+  u.nw = (gridDim.x * blockDim.x) >> 5;
+  u.gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  u.lane = threadIdx.x & 31;
+  u.chunks = u.nw / a.S;
+  if (u.chunks < 1) u.chunks = 1;
+  u.units = a.S * u.chunks;
+  int cs = (a.N + u.chunks - 1) / u.chunks;
+  u.csize = ((cs + 31) / 32) * 32;
+  return u;
+}
+
+// RHS state written by whichever CTA completed an earlier reduction: read through L2.
+__device__ __forceinline__ RhsState load_state(const RhsState* p) {
+  RhsState s;
+  s.gam = __ldcg(&p->gam);
+  s.alpha = __ldcg(&p->alpha);
+  s.beta = __ldcg(&p->beta);
+  s.bb = __ldcg(&p->bb);
+  s.rr = __ldcg(&p->rr);
+  s.rr0 = __ldcg(&p->rr0);
+  s.active = __ldcg(&p->active);
+  s.iters = __ldcg(&p->iters);
+  s.total = __ldcg(&p->total);
+  s.restarts = __ldcg(&p->restarts);
+  s.hist_ok = __ldcg(&p->hist_ok);
+  s.status = __ldcg(&p->status);
+  return s;
+}
+
+// mode 0: (re)start pass for right-hand sides in phase 1 (pending check) or all (first pass);
+// mode 1: iteration pass for active right-hand sides.
+// Scalar logic run by the last CTA; returns (through flags[0]) whether any RHS is active.
+__device__ __forceinline__ void scalar_logic(const MrhsArgs& a, int r, const double* t, int mode, bool first) {
+  RhsState st = load_state(a.st + r);
+  const double tol2 = a.delta * a.delta * (first ? t[3] : st.bb);
+  if (mode == 0) {
+    if (first) {
+      st.bb = t[3];
+      st.rr0 = t[2];
+      st.iters = 0;
+      st.total = 0;
+      st.restarts = 0;
+      st.hist_ok = 1;
+      st.status = 0;
+      st.active = 1;
+    }
+    if (!(st.active == 1 || st.active == 2)) {  // already done
+      a.st[r] = st;
+      return;
+    }
+    st.rr = t[2];
+    if (!(isfinite(t[0]) && isfinite(t[1]) && isfinite(t[2]))) {
+      st.status = 7;
+      st.active = 0;
+    } else if (st.bb == 0.0 || t[2] <= tol2) {
+      st.active = 0;                      // confirmed
+    } else if (st.total >= a.max_iter || st.restarts > a.max_restarts) {
+      st.status = 4;
+      st.active = 0;
+    } else {
+      if (!first) {
+        st.restarts += 1;
+        st.hist_ok = 0;
+      }
+      st.gam = t[0];
+      st.alpha = t[1] > 0.0 ? t[0] / t[1] : 0.0;
+      st.beta = 0.0;
+      st.active = t[1] > 0.0 ? 1 : 0;
+      if (!(t[1] > 0.0)) st.status = 3;
+    }
+  } else {
+    if (st.active != 1) {
+      a.st[r] = st;
+      return;
+    }
+    const double gnew = t[0], dnew = t[1];
+    st.rr = t[2];
+    st.total += 1;
+    if (st.hist_ok) st.iters += 1;
+    if (!(isfinite(gnew) && isfinite(dnew) && isfinite(st.rr))) {
+      st.status = 7;
+      st.active = 0;
+      a.st[r] = st;
+      return;
+    }
+    const double beta = gnew / st.gam;
+    if (a.hist && st.hist_ok && st.iters <= a.hist_len) {
+      a.hist[((size_t)(st.iters - 1) * a.S + r) * 2 + 0] = st.alpha;
+      a.hist[((size_t)(st.iters - 1) * a.S + r) * 2 + 1] = beta;
+    }
+    if (st.rr <= tol2 || st.total >= a.max_iter) {
+      st.active = 2;                      // pending confirmation by the true residual
+    } else {
+      const double den = dnew - beta * gnew / st.alpha;
+      if (!(den > 0.0)) {
+        st.status = 3;
+        st.active = 0;
+      } else {
+        st.beta = beta;
+        st.alpha = gnew / den;
+        st.gam = gnew;
+      }
+    }
+  }
+  a.st[r] = st;
+}
+
+// Reducing barrier: per-unit partials -> per-RHS totals -> scalar logic (last CTA).
+// Returns false on barrier failure; *any_active / *any_pending report the RHS states.
+__device__ __forceinline__ bool mrhs_reduce(const MrhsArgs& a, const Units& U, int mode, bool first,
+                                            int* sh_int, int* any_active, int* any_pending) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned int g0 = ld_acquire(a.bar.gen);
+    const unsigned int arrived = atom_add_acq_rel(a.bar.count, 1u);
+    sh_int[0] = (arrived == gridDim.x - 1) ? 1 : 0;
+    sh_int[1] = (int)g0;
+    sh_int[2] = 0;
+    sh_int[3] = 0;
+  }
+  __syncthreads();
+  if (sh_int[0]) {
+    const int warp = threadIdx.x >> 5, nwc = blockDim.x >> 5, lane = threadIdx.x & 31;
+    for (int r = warp; r < a.S; r += nwc) {
+      double acc[4] = {0.0, 0.0, 0.0, 0.0};
+      for (int c = lane; c < U.chunks; c += 32) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) acc[i] += __ldcg(a.part + ((size_t)c * a.S + r) * 4 + i);
+      }
+      const double v = warp_reduce4(acc);
+      double t[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) t[i] = __shfl_sync(0xffffffffu, v, 8 * i);
+      if (lane == 0) {
+        scalar_logic(a, r, t, mode, first);
+        const int act = __ldcg(&a.st[r].active);
+        if (act == 1) atomicOr(&sh_int[2], 1);
+        if (act == 2) atomicOr(&sh_int[3], 1);
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      a.flags[0] = sh_int[2];
+      a.flags[1] = sh_int[3];
+      __threadfence();
+      st_relaxed(a.bar.count, 0u);
+      red_add_release(a.bar.gen, 1u);
+    }
+    __syncthreads();
+  } else {
+    if (threadIdx.x == 0) {
+      const bool ok = wait_generation(a.bar, (unsigned int)sh_int[1]);
+      sh_int[2] = ok ? __ldcg(a.flags + 0) : 0;
+      sh_int[3] = ok ? __ldcg(a.flags + 1) : 0;
+      sh_int[0] = ok ? 0 : 1;
+    }
+    __syncthreads();
+    if (sh_int[0]) return false;
+  }
+  *any_active = sh_int[2];
+  *any_pending = sh_int[3];
+  __syncthreads();
+  return true;
+}
+
+}  // namespace
+
+template <int D>
+__global__ void __launch_bounds__(MRHS_THREADS) k_mrhs(MrhsArgs a) {
+  __shared__ int sh_int[4];
+  __shared__ int sh_flag;
+  const Units U = units_of(a);
+  const size_t ld = a.ld;
+  auto unit_rhs = [&](int u) { return u % U.S; };
+  auto unit_chunk = [&](int u) { return u / U.S; };
+  auto write_partials = [&](int u, double* acc) {
+    const double v = warp_reduce4(acc);
+    if ((U.lane & 7) == 0) a.part[(size_t)u * 4 + (U.lane >> 3)] = v;
+  };
+  // mode-0 pass: r = b - B~ x, u = M^-1 r, publish u; then w = B~ u and partials
+  // for every RHS selected by `sel` (state 1 on the first pass, 2 afterwards).
+  auto restart_pass = [&](bool first) -> bool {
+    for (int u = U.gw; u < U.units; u += U.nw) {
+      const int r = unit_rhs(u), c = unit_chunk(u);
+      const int act = first ? 1 : __ldcg(&a.st[r].active);
+      if (!first && act != 2) continue;
+      const double* b = a.b + (size_t)r * a.vs;
+      double *x = a.x + (size_t)r * a.vs, *R = a.r + (size_t)r * a.vs, *Uu = a.u + (size_t)r * a.vs;
+      double *P = a.p + (size_t)r * a.vs, *Sv = a.s + (size_t)r * a.vs;
+      const int n1 = min(a.N, (c + 1) * U.csize);
+      for (int n = c * U.csize + U.lane; n < n1; n += 32) {
+        double xn[D], ax[D], rn[D], un[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) xn[k] = ldc(x + (size_t)k * ld + n);
+        block_apply<D>(a, n, xn, x, ax);
+#pragma unroll
+        for (int k = 0; k < D; ++k) rn[k] = __ldg(b + (size_t)k * ld + n) - ax[k];
+        precond_apply<D>(a, n, rn, un);
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          R[(size_t)k * ld + n] = rn[k];
+          Uu[(size_t)k * ld + n] = un[k];
+          P[(size_t)k * ld + n] = 0.0;
+          Sv[(size_t)k * ld + n] = 0.0;
+        }
+      }
+    }
+    if (!grid_sync(a.bar, &sh_flag)) return false;
+    for (int u = U.gw; u < U.units; u += U.nw) {
+      const int r = unit_rhs(u), c = unit_chunk(u);
+      const int act = first ? 1 : __ldcg(&a.st[r].active);
+      double acc[4] = {0.0, 0.0, 0.0, 0.0};
+      if (first || act == 2) {
+        const double* b = a.b + (size_t)r * a.vs;
+        const double* R = a.r + (size_t)r * a.vs;
+        const double* Uu = a.u + (size_t)r * a.vs;
+        double* Wv = a.w + (size_t)r * a.vs;
+        const int n1 = min(a.N, (c + 1) * U.csize);
+        for (int n = c * U.csize + U.lane; n < n1; n += 32) {
+          double un[D], wn[D];
+#pragma unroll
+          for (int k = 0; k < D; ++k) un[k] = Uu[(size_t)k * ld + n];
+          block_apply<D>(a, n, un, Uu, wn);
+#pragma unroll
+          for (int k = 0; k < D; ++k) {
+            const double rk = R[(size_t)k * ld + n], bk = __ldg(b + (size_t)k * ld + n);
+            Wv[(size_t)k * ld + n] = wn[k];
+            acc[0] += rk * un[k];
+            acc[1] += wn[k] * un[k];
+            acc[2] += rk * rk;
+            acc[3] += bk * bk;
+          }
+        }
+      }
+      write_partials(u, acc);
+    }
+    return true;
+  };
+
+  int any_active = 0, any_pending = 0;
+  if (!restart_pass(true)) return;
+  if (!mrhs_reduce(a, U, 0, true, sh_int, &any_active, &any_pending)) return;
+  while (any_active || any_pending) {
+    if (any_active) {
+      // local update of active right-hand sides
+      for (int u = U.gw; u < U.units; u += U.nw) {
+        const int r = unit_rhs(u), c = unit_chunk(u);
+        if (__ldcg(&a.st[r].active) != 1) continue;
+        const double al = __ldcg(&a.st[r].alpha), be = __ldcg(&a.st[r].beta);
+        double *x = a.x + (size_t)r * a.vs, *R = a.r + (size_t)r * a.vs, *Uu = a.u + (size_t)r * a.vs;
+        double *P = a.p + (size_t)r * a.vs, *Sv = a.s + (size_t)r * a.vs;
+        const double* Wv = a.w + (size_t)r * a.vs;
+        const int n1 = min(a.N, (c + 1) * U.csize);
+        for (int n = c * U.csize + U.lane; n < n1; n += 32) {
+          double rn[D], un[D];
+#pragma unroll
+          for (int k = 0; k < D; ++k) {
+            const size_t o = (size_t)k * ld + n;
+            const double pk = Uu[o] + be * P[o];
+            const double sk = Wv[o] + be * Sv[o];
+            P[o] = pk;
+            Sv[o] = sk;
+            x[o] += al * pk;
+            rn[k] = R[o] - al * sk;
+            R[o] = rn[k];
+          }
+          precond_apply<D>(a, n, rn, un);
+#pragma unroll
+          for (int k = 0; k < D; ++k) Uu[(size_t)k * ld + n] = un[k];
+        }
+      }
+      if (!grid_sync(a.bar, &sh_flag)) return;
+      for (int u = U.gw; u < U.units; u += U.nw) {
+        const int r = unit_rhs(u), c = unit_chunk(u);
+        double acc[4] = {0.0, 0.0, 0.0, 0.0};
+        if (__ldcg(&a.st[r].active) == 1) {
+          const double* R = a.r + (size_t)r * a.vs;
+          const double* Uu = a.u + (size_t)r * a.vs;
+          double* Wv = a.w + (size_t)r * a.vs;
+          const int n1 = min(a.N, (c + 1) * U.csize);
+          for (int n = c * U.csize + U.lane; n < n1; n += 32) {
+            double un[D], wn[D];
+#pragma unroll
+            for (int k = 0; k < D; ++k) un[k] = Uu[(size_t)k * ld + n];
+            block_apply<D>(a, n, un, Uu, wn);
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+              const double rk = R[(size_t)k * ld + n];
+              Wv[(size_t)k * ld + n] = wn[k];
+              acc[0] += rk * un[k];
+              acc[1] += wn[k] * un[k];
+              acc[2] += rk * rk;
+            }
+          }
+        }
+        write_partials(u, acc);
+      }
+      if (!mrhs_reduce(a, U, 1, false, sh_int, &any_active, &any_pending)) return;
+    } else {
+      // every moving RHS has stopped: confirm the pending ones with the true residual
+      if (!restart_pass(false)) return;
+      if (!mrhs_reduce(a, U, 0, false, sh_int, &any_active, &any_pending)) return;
+    }
+  }
+}
+
+template <int D>
+static cudaError_t launch_d(const MrhsArgs& a, cudaStream_t stream, int* units_out) {
+  int dev = 0, nsm = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mrhs<D>, MRHS_THREADS, 0);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  // enough warps for every RHS and for a chunk of at least 32 voxels per warp
+  const long long want_warps = (long long)a.S * ((a.N + 31) / 32);
+  long long grid = (want_warps * 32 + MRHS_THREADS - 1) / MRHS_THREADS;
+  if (grid > (long long)nsm * per_sm) grid = (long long)nsm * per_sm;
+  if (grid < 1) grid = 1;
+  const int nw = (int)grid * (MRHS_THREADS / 32);
+  int chunks = nw / a.S;
+  if (chunks < 1) chunks = 1;
+  if (units_out) *units_out = a.S * chunks;
+  void* args[] = {(void*)&a};
+  return cudaLaunchCooperativeKernel((const void*)k_mrhs<D>, dim3((unsigned)grid), dim3(MRHS_THREADS), args, 0, stream);
+}
+
+template <int D>
+static int max_units_d(int S) {
+  int dev = 0, nsm = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mrhs<D>, MRHS_THREADS, 0);
+  const int nw = nsm * (per_sm > 0 ? per_sm : 1) * (MRHS_THREADS / 32);
+  const int chunks = nw / S > 0 ? nw / S : 1;
+  return S * chunks;
+}
+
+#define BFMRI_MRHS_CASES(X) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12)
+
+cudaError_t launch_mrhs(int D, const MrhsArgs& a, cudaStream_t stream, int* units_out) {
+  switch (D) {
+#define CASE(d) case d: return launch_d<d>(a, stream, units_out);
+    BFMRI_MRHS_CASES(CASE)
+#undef CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+int mrhs_max_units(int D, int S) {
+  switch (D) {
+#define CASE(d) case d: return max_units_d<d>(S);
+    BFMRI_MRHS_CASES(CASE)
+#undef CASE
+    default: return 0;
+  }
+}
+
+}  // namespace bfmri
+
+// ---------------------------------------------------------------------------------------
+// Probe right-hand sides, log det of the preconditioner, and trace terms.
+// ---------------------------------------------------------------------------------------
+namespace bfmri {
+
+// b_i = L v_i (v_i Rademacher, site lattice-linear * 4 + 3, stream i), x_i = 0.
+template <int D>
+__global__ void k_probe_rhs(ProbeArgs a) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.y;
+  if (n >= a.N) return;
+  Rng g = a.rng;
+  g.c3 = (a.rng.c3 & 0xFF000000u) | ((uint32_t)i & 0xFFFFFFu);
+  double v[D], bv[D];
+  site_rademacher<D>(g, (uint32_t)a.lin[n] * 4u + 3u, v);
+  if (a.mfac) {
+    double L[ntri(D)];
+#pragma unroll
+    for (int e = 0; e < ntri(D); ++e) L[e] = a.mfac[(size_t)e * a.ld + n];
+    lower_mul_invdiag<D>(L, v, bv);
+  } else {
+#pragma unroll
+    for (int k = 0; k < D; ++k) bv[k] = v[k];
+  }
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    a.b[(size_t)i * a.vs + (size_t)k * a.ld + n] = bv[k];
+    a.x[(size_t)i * a.vs + (size_t)k * a.ld + n] = 0.0;
+  }
+}
+
+// per-voxel log det of the preconditioner block: 2 sum_k log L_kk (stored inverted)
+template <int D>
+__global__ void k_logdet_m(ProbeArgs a, double* out) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= a.N) return;
+  double s = 0.0;
+#pragma unroll
+  for (int k = 0; k < D; ++k) s -= 2.0 * log(a.mfac[(size_t)tri(k, k) * a.ld + n]);
+  out[n] = s;
+}
+
+// Trace terms t_{i,k} = sum_n (L^-T v_i)_{n,k} (D_w y_{i,k})_n with y_i = B~^-1 L v_i, whose
+// mean over probes estimates tr(D_w^(k) B~^-1) (cyclic invariance: E[L^-T v v' L'] = I).
+// Per-CTA partials [grid.x][S][D] in a fixed order.
+template <int D>
+__global__ void k_probe_traces(ProbeArgs a, double* part) {
+  __shared__ double sh[128][D];
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.y;
+  double c[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) c[k] = 0.0;
+  if (n < a.N) {
+    Rng g = a.rng;
+    g.c3 = (a.rng.c3 & 0xFF000000u) | ((uint32_t)i & 0xFFFFFFu);
+    double v[D], t[D];
+    site_rademacher<D>(g, (uint32_t)a.lin[n] * 4u + 3u, v);
+    if (a.mfac) {
+      double L[ntri(D)];
+#pragma unroll
+      for (int e = 0; e < ntri(D); ++e) L[e] = a.mfac[(size_t)e * a.ld + n];
+      // solve L' t = v (L lower, inverted diagonal)
+#pragma unroll
+      for (int r = D - 1; r >= 0; --r) {
+        double acc = v[r];
+#pragma unroll
+        for (int j = r + 1; j < D; ++j) acc -= L[tri(j, r)] * t[j];
+        t[r] = acc * L[tri(r, r)];
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < D; ++k) t[k] = v[k];
+    }
+    const double* y = a.x + (size_t)i * a.vs;
+    double yn[D], sum[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      yn[k] = y[(size_t)k * a.ld + n];
+      sum[k] = 0.0;
+    }
+    int deg = 0;
+    for (int d = 0; d < a.ndir; ++d) {
+      const int m = a.nbr[(size_t)d * a.ld + n];
+      if (m >= 0) {
+        ++deg;
+#pragma unroll
+        for (int k = 0; k < D; ++k) sum[k] += y[(size_t)k * a.ld + m];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < D; ++k) c[k] = t[k] * ((double)deg * yn[k] - sum[k]);
+  }
+#pragma unroll
+  for (int k = 0; k < D; ++k) sh[threadIdx.x][k] = c[k];
+  __syncthreads();
+  for (int off = 64; off > 0; off >>= 1) {
+    if ((int)threadIdx.x < off) {
+#pragma unroll
+      for (int k = 0; k < D; ++k) sh[threadIdx.x][k] += sh[threadIdx.x + off][k];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x < D) part[((size_t)blockIdx.x * a.S + i) * D + threadIdx.x] = sh[0][threadIdx.x];
+}
+
+template <int D>
+static cudaError_t probe_launch_d(const ProbeArgs& a, int what, double* out, cudaStream_t s) {
+  const dim3 grid((a.N + 127) / 128, a.S);
+  if (what == 0) k_probe_rhs<D><<<grid, 128, 0, s>>>(a);
+  else if (what == 1) k_logdet_m<D><<<(a.N + 127) / 128, 128, 0, s>>>(a, out);
+  else k_probe_traces<D><<<grid, 128, 0, s>>>(a, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_probe(int D, const ProbeArgs& a, int what, double* out, cudaStream_t s) {
+  switch (D) {
+#define CASE(d) case d: return probe_launch_d<d>(a, what, out, s);
+    BFMRI_MRHS_CASES(CASE)
+#undef CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace bfmri

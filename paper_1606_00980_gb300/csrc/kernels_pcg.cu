@@ -82,9 +82,46 @@ __device__ __forceinline__ void minv(const T* __restrict__ Lp, int bs, const T* 
 
 struct Shared {
   double red[32 * 4 + 8];
+  double scal[4];   // CG scalars computed once per CTA by thread 0
   int ints[2];
   int flag;
+  int code;         // broadcast control code
 };
+
+// One CG step of the scalar recurrence (Chronopoulos & Gear), evaluated by thread 0 of each
+// CTA and broadcast through shared memory: FP64 division is a long instruction sequence on
+// this part, so it is not repeated by every thread. Returns in sh.code: 0 continue,
+// 1 check the true residual, 3 breakdown, 7 non-finite.
+__device__ __forceinline__ void cg_scalar_step(Shared& sh, double gnew, double dnew, double rr,
+                                               double tol2, int it, int max_iter, double& alpha,
+                                               double& beta, double& gam) {
+  if (threadIdx.x == 0) {
+    int code = 0;
+    double a = alpha, b = beta, g = gam;
+    if (!(isfinite(gnew) && isfinite(dnew) && isfinite(rr))) {
+      code = 7;
+    } else if (rr <= tol2 || it >= max_iter) {
+      code = 1;
+    } else {
+      b = gnew / g;
+      const double den = dnew - b * gnew / a;
+      if (!(den > 0.0)) {
+        code = 3;
+      } else {
+        a = gnew / den;
+        g = gnew;
+      }
+    }
+    sh.scal[0] = a;
+    sh.scal[1] = b;
+    sh.scal[2] = g;
+    sh.code = code;
+  }
+  __syncthreads();
+  alpha = sh.scal[0];
+  beta = sh.scal[1];
+  gam = sh.scal[2];
+}
 
 __device__ __forceinline__ void write_ctrl(const PcgArgs& a, int it, int restarts, double rr,
                                           double bb, double rel0, int status) {
@@ -206,10 +243,13 @@ __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_res(PcgArgs a) {
     }
     if (!grid_allreduce4(a.bar, a.part, a.tot, v, sh.red, sh.ints, tot)) return;
     ++it;
-    const double gnew = tot[0], dnew = tot[1];
     rr = tot[2];
-    if (!(isfinite(gnew) && isfinite(dnew) && isfinite(rr))) { status = 7; break; }
-    if (rr <= tol2 || it >= a.max_iter) {
+    cg_scalar_step(sh, tot[0], tot[1], rr, tol2, it, a.max_iter, alpha, beta, gam);
+    const int code = sh.code;
+    __syncthreads();
+    if (code == 7) { status = 7; break; }
+    if (code == 3) { status = 3; break; }
+    if (code == 1) {
       // confirm with the true residual
       if (own) {
 #pragma unroll
@@ -230,11 +270,6 @@ __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_res(PcgArgs a) {
       if (!(del > 0.0)) { status = 3; break; }
       continue;
     }
-    beta = gnew / gam;
-    const double den = dnew - beta * gnew / alpha;
-    if (!(den > 0.0)) { status = 3; break; }
-    alpha = gnew / den;
-    gam = gnew;
   }
   if (own) {
 #pragma unroll
@@ -373,10 +408,13 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_stream(PcgArgs a) {
     }
     if (!grid_allreduce4(a.bar, a.part, a.tot, v, sh.red, sh.ints, tot)) return;
     ++it;
-    const double gnew = tot[0], dnew = tot[1];
     rr = tot[2];
-    if (!(isfinite(gnew) && isfinite(dnew) && isfinite(rr))) { status = 7; break; }
-    if (rr <= tol2 || it >= a.max_iter) {
+    cg_scalar_step(sh, tot[0], tot[1], rr, tol2, it, a.max_iter, alpha, beta, gam);
+    const int code = sh.code;
+    __syncthreads();
+    if (code == 7) { status = 7; break; }
+    if (code == 3) { status = 3; break; }
+    if (code == 1) {
       // x was last updated before the reducing barrier above, so it is complete
       if (!restart(tot)) return;
       gam = tot[0];
@@ -390,11 +428,6 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_stream(PcgArgs a) {
       if (!(del > 0.0)) { status = 3; break; }
       continue;
     }
-    beta = gnew / gam;
-    const double den = dnew - beta * gnew / alpha;
-    if (!(den > 0.0)) { status = 3; break; }
-    alpha = gnew / den;
-    gam = gnew;
   }
   write_ctrl(a, it, restarts, rr, bb, rel0, status);
 }
@@ -541,14 +574,12 @@ __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_mixed_res(PcgArgs a)
       double v[4] = {(double)g, (double)dl, (double)q2, 0.0};
       if (!grid_allreduce4(a.bar, a.part, a.tot, v, sh.red, sh.ints, tot)) return;
       ++it;
-      const double gnew = tot[0], dnew = tot[1], rin = tot[2];
-      if (!(isfinite(gnew) && isfinite(dnew) && isfinite(rin))) { status = 7; break; }
-      if (rin <= itol2 || it >= a.max_inner || inner_total + it >= a.max_iter) break;
-      beta = gnew / gam;
-      const double den = dnew - beta * gnew / alpha;
-      if (!(den > 0.0)) break;   // loss of conjugacy in FP32: refine from here
-      alpha = gnew / den;
-      gam = gnew;
+      const bool capped = it >= a.max_inner || inner_total + it >= a.max_iter;
+      cg_scalar_step(sh, tot[0], tot[1], tot[2], itol2, capped ? 1 : 0, 1, alpha, beta, gam);
+      const int code = sh.code;
+      __syncthreads();
+      if (code == 7) { status = 7; break; }
+      if (code != 0) break;   // inner tolerance, iteration cap, or loss of conjugacy in FP32
     }
     inner_total += it;
     if (status != 0) break;
@@ -714,14 +745,12 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_mixed_stream(PcgArgs a) {
       if (!bar()) return;
       if (!matvec_partials(tot)) return;
       ++it;
-      const double gnew = tot[0], dnew = tot[1], rin = tot[2];
-      if (!(isfinite(gnew) && isfinite(dnew) && isfinite(rin))) { status = 7; break; }
-      if (rin <= itol2 || it >= a.max_inner || inner_total + it >= a.max_iter) break;
-      beta = gnew / gam;
-      const double den = dnew - beta * gnew / alpha;
-      if (!(den > 0.0)) break;
-      alpha = gnew / den;
-      gam = gnew;
+      const bool capped = it >= a.max_inner || inner_total + it >= a.max_iter;
+      cg_scalar_step(sh, tot[0], tot[1], tot[2], itol2, capped ? 1 : 0, 1, alpha, beta, gam);
+      const int code = sh.code;
+      __syncthreads();
+      if (code == 7) { status = 7; break; }
+      if (code != 0) break;   // inner tolerance, iteration cap, or loss of conjugacy in FP32
     }
     inner_total += it;
     if (status != 0) break;

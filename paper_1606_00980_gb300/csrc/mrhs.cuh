@@ -1,0 +1,79 @@
+// Multi-right-hand-side PCG: S systems with one matrix B~ (probes, SVB samples) advance in
+// lock-step inside one cooperative launch, each with its own CG scalars and stop test.
+#pragma once
+
+#include <cstddef>
+#include <cuda_runtime.h>
+
+#include "device_common.cuh"
+
+namespace bfmri {
+
+// Per-RHS scalar state kept by the CTA that completes each reduction.
+struct RhsState {
+  double gam;      // r'M^-1 r of the previous iteration
+  double alpha;    // current step
+  double beta;     // current direction update
+  double bb;       // ||b||^2
+  double rr;       // latest ||r||^2
+  double rr0;      // ||r||^2 of the start value
+  int active;      // 1 while iterating
+  int iters;       // iterations of the first (Lanczos-consistent) run
+  int total;       // iterations including restarts
+  int restarts;
+  int hist_ok;     // 1 while no restart has happened (history is a Lanczos run)
+  int status;      // 0 ok, 3 breakdown, 4 max_iter, 7 non-finite
+};
+
+struct MrhsArgs {
+  int N;
+  size_t ld;
+  int ndir;
+  const int* nbr;        // [6][ld]
+  const double* blocks;  // [ntri(D)][ld]
+  const double* mfac;    // [ntri(D)][ld] block-Jacobi factor (inverted diag) or null
+  const double* scale;   // [D]
+  int S;                 // number of right-hand sides
+  size_t vs;             // stride between RHS (>= D * ld)
+  const double* b;       // [S] x [D][ld]
+  double* x;             // [S] x [D][ld]: start values in, solutions out
+  double* r;             // [S] x [D][ld] work
+  double* u;
+  double* w;
+  double* p;
+  double* s;
+  double* part;          // [units][4]
+  RhsState* st;          // [S]
+  double* hist;          // [hist_len][S][2] CG (alpha, beta) of the first run, or null
+  int hist_len;
+  int* flags;            // [2]: any active, iteration counter
+  GridBarrier bar;
+  double delta;
+  int max_iter;
+  int max_restarts;
+};
+
+// Probe set-up and post-processing (log-determinant and trace probes).
+struct ProbeArgs {
+  int N;
+  size_t ld;
+  int ndir;
+  const int* nbr;
+  const int* lin;
+  const double* mfac;   // block-Jacobi factor (inverted diagonal), or null
+  int S;
+  size_t vs;
+  double* b;            // [S][D][ld]
+  double* x;            // [S][D][ld]
+  Rng rng;              // tag in c3's top byte; the probe index is the stream
+};
+// what: 0 = probe right-hand sides b_i = L v_i and x_i = 0; 1 = per-voxel log det of the
+// preconditioner into out[N]; 2 = trace partials into out[grid.x][S][D] (grid.x = ceil(N/128)).
+cudaError_t launch_probe(int D, const ProbeArgs& a, int what, double* out, cudaStream_t s);
+
+// Launches the cooperative multi-RHS PCG for dimension D on `stream`.
+cudaError_t launch_mrhs(int D, const MrhsArgs& a, cudaStream_t stream, int* units_out);
+// Rows of the partial buffer the launch may need: S * chunks, bounded by this value.
+int mrhs_max_units(int D, int S);
+
+}  // namespace bfmri

@@ -229,3 +229,21 @@ def test_logdet_and_slq():
     logB = Lg[1] @ np.diag(np.log(Lg[0])) @ Lg[1].T
     sigma = np.sqrt(2 * (np.sum(logB ** 2) - np.sum(np.diag(logB) ** 2)) / Z.shape[1])
     assert abs(exact.mean() - ld) < 4 * sigma
+
+
+def test_probe_estimators_are_unbiased_for_logdet_and_traces():
+    """The oracle's probe terms: their mean over many probes approaches log det B~ - log det M
+    (tr log C) and tr(D_w^(k) B~^-1) (exact dense values), within 5 standard errors."""
+    from oracle import probes
+    w, lat = tiny(dims=(3, 3, 2), K=2, P=1, T=30, nb=6)
+    s = random_state(w, np.random.default_rng(9))
+    Bd, _ = model.w_blocks_direct(w.Y, w.X, s["A"], s["lam"])
+    V = probes.probe_vectors(lat, 2, 400, seed=5, counter=1)
+    ldm, quad, tr, ldb = probes.exact_probe_terms(lat, Bd, s["alpha"], V)
+    assert abs(quad.mean() - (ldb - ldm)) < 5 * quad.std() / np.sqrt(len(quad))
+    exact = probes.exact_traces(lat, Bd, s["alpha"])
+    se = tr.std(axis=0) / np.sqrt(len(tr))
+    assert np.all(np.abs(tr.mean(axis=0) - exact) < 5 * se)
+    # log det M from the factor equals the dense log det of the preconditioner
+    M = model.precision(lat, probes.precond_blocks(lat, Bd, s["alpha"]), np.zeros(2))
+    assert abs(ldm - np.linalg.slogdet(M.toarray())[1]) < 1e-10 * abs(ldm)
