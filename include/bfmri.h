@@ -214,6 +214,33 @@ bfmri_status bfmri_logdet_probe(bfmri_handle* h, int which, int n_probes, int la
                                 uint64_t counter, double* logdet, double* std_err,
                                 double* traces, double* per_probe);
 
+/* One spatial-VB iteration (Section 3.3; Appendix B, Eq. NFVBw / NFVBbB; Appendix C).
+ * The handle's lambda, alpha, beta are the current means E[lambda], E[alpha], E[beta]; the
+ * handle keeps n_samples samples of W and A (created from the current W and A on the first
+ * call or when n_samples changes, later samples kept as warm starts):
+ *  1. q(W): per-voxel blocks and right-hand sides averaged over the A samples with E[lambda],
+ *     and E[alpha] on the prior; n_samples draws by Algorithm 2 with the SAME random numbers
+ *     at every iteration (draw counter `counter`, stream = sample index), solved together by
+ *     the multi-right-hand-side PCG from the previous samples;
+ *  2. q(A): the same with the lagged residual Gram averaged over the new W samples;
+ *  3. E[lambda_n] from the mean over sample pairs of RSS_n (paired by index);
+ *  4. E[alpha_k] (E[beta_p]) from the mean over samples of W_k D_w W_k' (A_p D_a A_p');
+ *     with `extrapolate`, every other iteration from the third on, Appendix C's trick 1.
+ * alpha_vb / beta_vb (may be NULL) receive the VB values before the extrapolation. */
+typedef struct {
+  int iteration;               /* SVB iterations run on this handle */
+  int samples;
+  long long pcg_iterations_W;  /* summed over samples */
+  long long pcg_iterations_A;
+  double max_rel_residual_W;
+  int extrapolated;            /* 1 if trick 1 replaced the VB value this iteration */
+} bfmri_svb_info;
+bfmri_status bfmri_spvb_step(bfmri_handle* h, int n_samples, uint64_t counter, int extrapolate,
+                             double* alpha_vb, double* beta_vb, bfmri_svb_info* info);
+/* Read / overwrite SVB sample j (W is K x N, A is P x N; either may be NULL). */
+bfmri_status bfmri_svb_get_sample(bfmri_handle* h, int j, double* W, double* A);
+bfmri_status bfmri_svb_set_sample(bfmri_handle* h, int j, const double* W, const double* A);
+
 /* Gauss quadrature value e1' log(T) e1 of the Lanczos tridiagonal T built from m CG
  * coefficients (alpha_0..alpha_{m-1}, beta_0..beta_{m-2}) of a preconditioned CG run from
  * x = 0; host-only helper used by bfmri_logdet_probe. */

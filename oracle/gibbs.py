@@ -85,3 +85,84 @@ def gibbs_sweep(lat, Y, X, state, seed, counter, eps=0.0, spatial_ar=True,
     if s["A"].shape[0] > 0 and spatial_ar:
         s["beta"] = sample_beta(lat, s, seed, counter, priors, stream)
     return s
+
+
+# ----------------------------------------------------------------------------------------
+# Spatial VB (Section 3.3; Appendix B, Eq. NFVBw / NFVBbB; Appendix C tricks)
+# ----------------------------------------------------------------------------------------
+# One SVB iteration, in the order W -> A -> lambda -> alpha -> beta. Expectations over W and A
+# are Monte Carlo averages over N_s samples paired by index j (Eq. MC approx); the samples are
+# drawn with Algorithm 2 from the averaged systems with the SAME random numbers at every
+# iteration (stream j, a fixed draw counter), warm-started from the previous samples (the
+# oracle solves exactly, so warm starts do not change its results).
+
+def svb_w_system(Y, X, A_samples, lam_bar, eps=0.0):
+    """B~_SVB blocks and b_SVB: the averages over j of the W-system blocks and right-hand
+    sides evaluated at A^(j) with lambda replaced by its mean (Eq. NFVBbB)."""
+    Bs, bs = zip(*[model.w_blocks_direct(Y, X, A, lam_bar, eps) for A in A_samples])
+    return np.mean(Bs, axis=0), np.mean(bs, axis=0)
+
+
+def svb_a_system(Y, X, W_samples, lam_bar, P):
+    Js, bs = zip(*[model.a_blocks_direct(Y, X, W, lam_bar, P) for W in W_samples])
+    return np.mean(Js, axis=0), np.mean(bs, axis=0)
+
+
+def svb_draw(lat, blocks, rhs, scale, seed, counter, tag, n_samples):
+    return [draw_gmrf(lat, blocks, rhs, scale, seed, counter, tag, stream=j)[0]
+            for j in range(n_samples)]
+
+
+def svb_lambda_mean(Y, X, W_samples, A_samples, priors=model.PRIORS):
+    """E[lambda_n] = u~1n u~2 with 1/u~1n = 1/u1 + mean_j RSS_n(W^(j), A^(j)) / 2."""
+    T = Y.shape[0]
+    P = A_samples[0].shape[0]
+    rss = np.mean([model.rss_direct(Y, X, W, A) for W, A in zip(W_samples, A_samples)], axis=0)
+    scale, shape = model.lambda_params(rss, T, P, priors["u1"], priors["u2"])
+    return scale * shape
+
+
+def svb_hyper_mean(lat, samples, prior1, prior2):
+    """E[alpha_k] = q~1k q~2 with 1/q~1k = mean_j W_k^(j) D W_k^(j)' / 2 + 1/q1
+    (Eq. NFVB-alpha-parameters with Eq. MC approx); the same form for beta."""
+    Q = np.mean([model.quad_forms_edges(lat, V) for V in samples], axis=0)
+    scale, shape = model.alpha_params(Q, lat.N, prior1, prior2)
+    return scale * shape, Q
+
+
+def svb_extrapolate(history, proposal):
+    """Appendix C, trick 1 (parity unpinned: the paper prints no iterate values). history
+    holds the values used at iterations j-2 and j-1, proposal is the VB value at j. Fit a
+    parabola through the three points; if its vertex lies after j use the vertex value, else
+    step 20 times the last change; keep within a factor 5 of the proposal; fall back to the
+    proposal when the prediction is not positive."""
+    a2, a1 = history
+    a0 = proposal
+    # parabola through (-2, a2), (-1, a1), (0, a0): y = c x^2 + d x + a0
+    c = 0.5 * (a2 - 2.0 * a1 + a0)
+    d = 0.5 * (a2 - 4.0 * a1 + 3.0 * a0)
+    pred = np.where((c != 0.0) & (-d / np.where(c != 0.0, 2.0 * c, 1.0) > 0.0),
+                    a0 - d * d / np.where(c != 0.0, 4.0 * c, 1.0), a1 + 20.0 * (a0 - a1))
+    pred = np.where(pred > 0.0, pred, a0)
+    return np.clip(pred, a0 / 5.0, 5.0 * a0)
+
+
+def svb_step(lat, Y, X, state, W_samples, A_samples, seed, counter, eps=0.0, spatial_ar=True,
+             priors=model.PRIORS):
+    """One SVB iteration without the Appendix C extrapolation; returns the new means and
+    samples. state holds lam (E[lambda]), alpha (E[alpha]), beta (E[beta])."""
+    Ns = len(W_samples)
+    P = A_samples[0].shape[0]
+    Bd, bw = svb_w_system(Y, X, A_samples, state["lam"], eps)
+    Wn = svb_draw(lat, Bd, bw, state["alpha"], seed, counter, philox.TAG_W, Ns)
+    An = list(A_samples)
+    if P > 0:
+        Ja, ba = svb_a_system(Y, X, Wn, state["lam"], P)
+        scale = state["beta"] if spatial_ar else np.zeros(P)
+        An = svb_draw(lat, Ja, ba, scale, seed, counter, philox.TAG_A, Ns)
+    lam = svb_lambda_mean(Y, X, Wn, An, priors)
+    alpha, QW = svb_hyper_mean(lat, Wn, priors["q1"], priors["q2"])
+    beta = state["beta"]
+    if P > 0 and spatial_ar:
+        beta, _ = svb_hyper_mean(lat, An, priors["r1"], priors["r2"])
+    return dict(lam=lam, alpha=alpha, beta=beta, QW=QW), Wn, An

@@ -52,6 +52,12 @@ class bfmri_solve_info(C.Structure):
                 ("rel_residual", C.c_double), ("rel_residual0", C.c_double)]
 
 
+class bfmri_svb_info(C.Structure):
+    _fields_ = [("iteration", C.c_int), ("samples", C.c_int), ("pcg_iterations_W", C.c_longlong),
+                ("pcg_iterations_A", C.c_longlong), ("max_rel_residual_W", C.c_double),
+                ("extrapolated", C.c_int)]
+
+
 class bfmri_sweep_info(C.Structure):
     _fields_ = [("sweeps", C.c_int), ("pcg_iterations_W", C.c_longlong),
                 ("pcg_iterations_A", C.c_longlong), ("last_rel_residual_W", C.c_double),
@@ -92,6 +98,9 @@ SIGNATURES = [
     ("bfmri_gibbs_sweep", C.c_int, [_h, C.c_int, C.c_uint64, _P(bfmri_sweep_info)]),
     ("bfmri_logdet_probe", C.c_int, [_h, C.c_int, C.c_int, C.c_int, C.c_uint64, _dp, _dp, _dp, _dp]),
     ("bfmri_lanczos_log_quadrature", C.c_int, [C.c_int, _dp, _dp, _dp]),
+    ("bfmri_spvb_step", C.c_int, [_h, C.c_int, C.c_uint64, C.c_int, _dp, _dp, _P(bfmri_svb_info)]),
+    ("bfmri_svb_get_sample", C.c_int, [_h, C.c_int, _dp, _dp]),
+    ("bfmri_svb_set_sample", C.c_int, [_h, C.c_int, _dp, _dp]),
     ("bfmri_get_timing", C.c_int, [_h, _P(bfmri_timing)]),
     ("bfmri_reset_timing", C.c_int, [_h]),
     ("bfmri_apply_precision", C.c_int, [_h, C.c_int, _dp, _dp]),
@@ -337,6 +346,20 @@ class Model:
         self._c(self.lib.bfmri_logdet_probe(self.handle, which, n_probes, lanczos_steps, counter,
                                             C.byref(ld), C.byref(se), _ptr(tr), _ptr(pp)))
         return dict(logdet=ld.value, stderr=se.value, traces=tr, per_probe=pp)
+
+    def spvb_step(self, n_samples, counter, extrapolate=True):
+        avb = np.empty(self.K)
+        bvb = np.empty(max(self.P, 1))
+        info = bfmri_svb_info()
+        self._c(self.lib.bfmri_spvb_step(self.handle, n_samples, counter, 1 if extrapolate else 0,
+                                         _ptr(avb), _ptr(bvb), C.byref(info)))
+        return avb, bvb[:self.P], info
+
+    def svb_sample(self, j):
+        W = np.empty((self.K, self.N))
+        A = np.empty((self.P, self.N))
+        self._c(self.lib.bfmri_svb_get_sample(self.handle, j, _ptr(W), _ptr(A)))
+        return W, A
 
     def timing(self):
         t = bfmri_timing()

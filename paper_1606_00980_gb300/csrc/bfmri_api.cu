@@ -69,6 +69,11 @@ struct bfmri_handle {
   size_t mr_out_len = 0;
   RhsState* mr_st = nullptr;
   int* mr_flags = nullptr;
+  // spatial VB state: N_s samples of W and A (warm starts), work planes, extrapolation history
+  int svb_S = 0, svb_iter = 0;
+  double *svb_W = nullptr, *svb_A = nullptr, *svb_cmom = nullptr, *svb_gin = nullptr;
+  double *svb_ldata = nullptr, *svb_part = nullptr, *d_zero = nullptr;
+  std::vector<double> svb_alpha_hist[2], svb_beta_hist[2];
   // profiling: events recorded around launches, resolved lazily
   struct Pending { int cls; cudaEvent_t e0, e1; bool pcg; int which; };
   std::vector<Pending> pending;
@@ -422,7 +427,11 @@ bfmri_status resolve_timing(bfmri_handle* h) {
 // Multi-RHS buffers for S right-hand sides of dimension D and hist_len recorded iterations.
 bfmri_status ensure_mrhs(bfmri_handle* h, int D, int S, int hist_len) {
   const size_t vs = (size_t)D * h->ld;
-  const int units = mrhs_max_units(D, S);
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  // rows of the partial buffer: one per (RHS, chunk) unit, never more than max(warps, S)
+  const int units = std::max(std::max(nsm, 1) * 64, S);
   const size_t out_len = std::max((size_t)h->ld, (size_t)((h->N + 127) / 128) * S * D);
   if (S <= h->mr_S && D <= h->mr_D && hist_len <= h->mr_hist_len && units <= h->mr_units &&
       out_len <= h->mr_out_len)
@@ -1042,6 +1051,239 @@ bfmri_status bfmri_logdet_probe(bfmri_handle* h, int which, int n_probes, int la
       traces[k] = t / n_probes;
     }
   }
+  return BFMRI_OK;
+}
+
+bfmri_status bfmri_spvb_step(bfmri_handle* h, int n_samples, uint64_t counter, int extrapolate,
+                             double* alpha_vb, double* beta_vb, bfmri_svb_info* info) {
+  RET(require_stats(h));
+  if (n_samples < 1 || n_samples > 4096) return fail(h, BFMRI_ERR_INVALID_ARG, "n_samples must be in [1, 4096]");
+  const int K = h->K, P = h->P, S = n_samples;
+  const size_t ld = h->ld;
+  const bool spatial = h->opt.ar_prior == BFMRI_AR_SPATIAL;
+  // (re)size the sample store; new samples start from the current W and A
+  if (S != h->svb_S) {
+    double* nW = (double*)dalloc(h, (size_t)S * K * ld * sizeof(double));
+    double* nA = (double*)dalloc(h, (size_t)S * std::max(P, 1) * ld * sizeof(double));
+    if (!nW || !nA) return fail(h, BFMRI_ERR_OOM, "SVB sample allocation failed");
+    for (int j = 0; j < S; ++j) {
+      const bool keep = j < h->svb_S;
+      CU(h, cudaMemcpyAsync(nW + (size_t)j * K * ld, keep ? h->svb_W + (size_t)j * K * ld : h->d_W,
+                            (size_t)K * ld * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+      if (P > 0)
+        CU(h, cudaMemcpyAsync(nA + (size_t)j * P * ld, keep ? h->svb_A + (size_t)j * P * ld : h->d_A,
+                              (size_t)P * ld * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    }
+    CU(h, cudaStreamSynchronize(h->stream));
+    dfree(h, h->svb_W);
+    dfree(h, h->svb_A);
+    h->svb_W = nW;
+    h->svb_A = nA;
+    h->svb_S = S;
+  }
+  if (!h->svb_cmom) {
+    h->svb_cmom = (double*)dalloc(h, (size_t)n_syy(P) * ld * sizeof(double));
+    h->svb_gin = (double*)dalloc(h, (size_t)n_syy(P) * ld * sizeof(double));
+    h->svb_ldata = (double*)dalloc(h, (size_t)ntri(h->D) * ld * sizeof(double));
+    h->svb_part = (double*)dalloc(h, (size_t)1024 * h->D * sizeof(double));
+    h->d_zero = (double*)dalloc(h, (size_t)(PMAX + KMAX) * sizeof(double));
+    if (!h->svb_cmom || !h->svb_gin || !h->svb_ldata || !h->svb_part || !h->d_zero)
+      return fail(h, BFMRI_ERR_OOM, "SVB workspace allocation failed");
+    CU(h, cudaMemsetAsync(h->d_zero, 0, (PMAX + KMAX) * sizeof(double), h->stream));
+  }
+  RET(ensure_mrhs(h, h->D, S, 0));
+  RET(begin_call(h));
+  SvbArgs sv;
+  memset(&sv, 0, sizeof(sv));
+  sv.g = geom(h);
+  sv.K = K;
+  sv.P = P;
+  sv.T = h->T;
+  sv.S = S;
+  sv.stats = h->d_stats;
+  sv.Sxx = h->d_Sxx;
+  sv.Ws = h->svb_W;
+  sv.As = h->svb_A;
+  sv.Cmom = h->svb_cmom;
+  sv.Gin = h->svb_gin;
+  sv.bmean = h->d_bmean;
+  sv.ldata = h->svb_ldata;
+  sv.u1 = h->opt.u1;
+  sv.u2 = h->opt.u2;
+  sv.lam = h->d_lam;
+  sv.part = h->svb_part;
+  sv.rhs = h->mr_b;
+  cudaError_t e;
+  // ---- q(W): averaged system (Eq. NFVBbB), N_s draws with fixed random numbers ----
+  if (P > 0) {
+    e = launch_svb(0, K, sv, h->stream, nullptr);
+    if (e != cudaSuccess) return cuda_fail(h, e, "svb moments");
+  }
+  AssembleArgs a = assemble_args(h, h->d_alpha, 0, TAG_W);
+  a.perturb = 0;
+  a.blocks32 = nullptr;
+  a.mfac32 = nullptr;
+  a.bmean = h->d_bmean;
+  a.ldata = h->svb_ldata;
+  a.Cmom = P > 0 ? h->svb_cmom : nullptr;
+  {
+    Timed tm(h, BFMRI_T_ASSEMBLE_W);
+    e = launch_assemble_w(a, h->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(h, e, "svb assemble W");
+  sv.scale = h->d_alpha;
+  sv.spatial = 1;
+  sv.vs = (size_t)K * ld;
+  sv.rng = rng_of(h, counter, TAG_W);
+  e = launch_svb(2, K, sv, h->stream, nullptr);
+  if (e != cudaSuccess) return cuda_fail(h, e, "svb rhs W");
+  MrhsArgs m = mrhs_args(h, K, S, h->d_alpha, h->opt.max_iter, false);
+  m.vs = (size_t)K * ld;
+  m.x = h->svb_W;
+  {
+    Timed tm(h, BFMRI_T_PCG_W, true, 0);
+    e = launch_mrhs(K, m, h->stream, nullptr);
+  }
+  if (e != cudaSuccess) return cuda_fail(h, e, "svb solve W");
+  std::vector<RhsState> stW(S), stA;
+  CU(h, cudaMemcpyAsync(stW.data(), h->mr_st, S * sizeof(RhsState), cudaMemcpyDeviceToHost, h->stream));
+  CU(h, cudaStreamSynchronize(h->stream));
+  // ---- q(A): system averaged over the new W samples ----
+  const double* bscale = spatial ? h->d_beta : h->d_zero;
+  if (P > 0) {
+    e = launch_svb(1, K, sv, h->stream, nullptr);
+    if (e != cudaSuccess) return cuda_fail(h, e, "svb gram");
+    AssembleArgs b = assemble_args(h, bscale, 0, TAG_A);
+    b.perturb = 0;
+    b.blocks32 = nullptr;
+    b.mfac32 = nullptr;
+    b.bmean = h->d_bmean;
+    b.ldata = h->svb_ldata;
+    b.Gin = h->svb_gin;
+    b.G = h->d_G;
+    {
+      Timed tm(h, BFMRI_T_ASSEMBLE_A);
+      e = launch_assemble_a(b, h->stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "svb assemble A");
+    sv.scale = bscale;
+    sv.spatial = spatial ? 1 : 0;
+    sv.vs = (size_t)P * ld;
+    sv.rng = rng_of(h, counter, TAG_A);
+    e = launch_svb(2, P, sv, h->stream, nullptr);
+    if (e != cudaSuccess) return cuda_fail(h, e, "svb rhs A");
+    MrhsArgs ma = mrhs_args(h, P, S, bscale, h->opt.max_iter, false);
+    ma.vs = (size_t)P * ld;
+    ma.x = h->svb_A;
+    {
+      Timed tm(h, BFMRI_T_PCG_A, true, 1);
+      e = launch_mrhs(P, ma, h->stream, nullptr);
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "svb solve A");
+    stA.resize(S);
+    CU(h, cudaMemcpyAsync(stA.data(), h->mr_st, S * sizeof(RhsState), cudaMemcpyDeviceToHost, h->stream));
+  }
+  // ---- q(lambda), then the quadratic forms for q(alpha), q(beta) ----
+  {
+    Timed tm(h, BFMRI_T_LAMBDA);
+    e = launch_svb(3, K, sv, h->stream, nullptr);
+  }
+  if (e != cudaSuccess) return cuda_fail(h, e, "svb lambda");
+  int grid = 0;
+  e = launch_svb(4, K, sv, h->stream, &grid);
+  if (e != cudaSuccess) return cuda_fail(h, e, "svb quad W");
+  std::vector<double> partW((size_t)grid * K), partA;
+  CU(h, cudaMemcpyAsync(partW.data(), h->svb_part, partW.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  if (P > 0 && spatial) {
+    CU(h, cudaStreamSynchronize(h->stream));
+    int gridA = 0;
+    e = launch_svb(5, P, sv, h->stream, &gridA);
+    if (e != cudaSuccess) return cuda_fail(h, e, "svb quad A");
+    partA.resize((size_t)gridA * P);
+    CU(h, cudaMemcpyAsync(partA.data(), h->svb_part, partA.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  }
+  RET(end_call(h, nullptr, nullptr));
+  long long itW = 0, itA = 0;
+  double worst = 0.0;
+  for (const RhsState& r : stW) {
+    if (r.status == 4) return fail(h, BFMRI_ERR_NOT_CONVERGED, "SVB W solve reached max_iter");
+    if (r.status != 0) return fail(h, BFMRI_ERR_NOT_SPD, "SVB W solve breakdown");
+    itW += r.total;
+    worst = std::max(worst, r.bb > 0 ? std::sqrt(r.rr / r.bb) : 0.0);
+  }
+  for (const RhsState& r : stA) {
+    if (r.status == 4) return fail(h, BFMRI_ERR_NOT_CONVERGED, "SVB A solve reached max_iter");
+    if (r.status != 0) return fail(h, BFMRI_ERR_NOT_SPD, "SVB A solve breakdown");
+    itA += r.total;
+  }
+  // E[alpha_k] = q~1k q~2, 1/q~1k = mean_j Q_k / 2 + 1/q1 (Eq. NFVB-alpha-parameters)
+  auto hyper = [&](const std::vector<double>& part, int D, double r1, double r2, std::vector<double>& out) {
+    const int g = (int)(part.size() / std::max(D, 1));
+    out.assign(D, 0.0);
+    for (int k = 0; k < D; ++k) {
+      double q = 0.0;
+      for (int b = 0; b < g; ++b) q += part[(size_t)b * D + k];
+      q /= S;
+      out[k] = (0.5 * h->N + r2) / (0.5 * q + 1.0 / r1);
+    }
+  };
+  std::vector<double> avb, bvb;
+  hyper(partW, K, h->opt.q1, h->opt.q2, avb);
+  if (P > 0 && spatial) hyper(partA, P, h->opt.r1, h->opt.r2, bvb);
+  if (alpha_vb) std::copy(avb.begin(), avb.end(), alpha_vb);
+  if (beta_vb) std::copy(bvb.begin(), bvb.end(), beta_vb);
+  // Appendix C, trick 1: every other iteration extrapolate from the last three values
+  h->svb_iter += 1;
+  bool extrapolated = false;
+  auto trick = [&](std::vector<double>& vb, std::vector<double>* hist) -> std::vector<double> {
+    std::vector<double> use = vb;
+    if (extrapolate && h->svb_iter >= 3 && (h->svb_iter % 2) == 1 && hist[0].size() == vb.size() &&
+        hist[1].size() == vb.size()) {
+      for (size_t k = 0; k < vb.size(); ++k) {
+        const double a2 = hist[0][k], a1 = hist[1][k], a0 = vb[k];
+        const double c = 0.5 * (a2 - 2.0 * a1 + a0), d = 0.5 * (a2 - 4.0 * a1 + 3.0 * a0);
+        double pred = (c != 0.0 && -d / (2.0 * c) > 0.0) ? a0 - d * d / (4.0 * c) : a1 + 20.0 * (a0 - a1);
+        if (!(pred > 0.0)) pred = a0;
+        use[k] = std::min(std::max(pred, a0 / 5.0), 5.0 * a0);
+      }
+      extrapolated = true;
+    }
+    hist[0] = hist[1];
+    hist[1] = use;
+    return use;
+  };
+  std::vector<double> au = trick(avb, h->svb_alpha_hist);
+  CU(h, cudaMemcpyAsync(h->d_alpha, au.data(), K * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  if (P > 0 && spatial) {
+    std::vector<double> bu = trick(bvb, h->svb_beta_hist);
+    CU(h, cudaMemcpyAsync(h->d_beta, bu.data(), P * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  }
+  CU(h, cudaStreamSynchronize(h->stream));
+  if (info) {
+    info->iteration = h->svb_iter;
+    info->samples = S;
+    info->pcg_iterations_W = itW;
+    info->pcg_iterations_A = itA;
+    info->max_rel_residual_W = worst;
+    info->extrapolated = extrapolated ? 1 : 0;
+  }
+  return BFMRI_OK;
+}
+
+bfmri_status bfmri_svb_get_sample(bfmri_handle* h, int j, double* W, double* A) {
+  if (!h) return BFMRI_ERR_INVALID_ARG;
+  if (j < 0 || j >= h->svb_S) return fail(h, BFMRI_ERR_INVALID_ARG, "no such SVB sample");
+  if (W) RET(to_host(h, W, h->svb_W + (size_t)j * h->K * h->ld, h->K));
+  if (A && h->P > 0) RET(to_host(h, A, h->svb_A + (size_t)j * h->P * h->ld, h->P));
+  return BFMRI_OK;
+}
+
+bfmri_status bfmri_svb_set_sample(bfmri_handle* h, int j, const double* W, const double* A) {
+  if (!h) return BFMRI_ERR_INVALID_ARG;
+  if (j < 0 || j >= h->svb_S) return fail(h, BFMRI_ERR_INVALID_ARG, "no such SVB sample");
+  if (W) RET(to_dev(h, h->svb_W + (size_t)j * h->K * h->ld, W, h->K));
+  if (A && h->P > 0) RET(to_dev(h, h->svb_A + (size_t)j * h->P * h->ld, A, h->P));
+  CU(h, cudaStreamSynchronize(h->stream));
   return BFMRI_OK;
 }
 

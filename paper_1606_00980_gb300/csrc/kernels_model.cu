@@ -80,35 +80,6 @@ __global__ void __launch_bounds__(STATS_THREADS) k_stats(StatsArgs a) {
 }
 
 // ---------------------------------------------------------------------------------------
-// Algorithm 2 perturbation for one voxel: rhs += sum_k sqrt(s_k) (G' z1_k)_n over the
-// voxel's edges. Edge (i, i + stride_d) carries +z at i and -z at its upper endpoint; its
-// normals come from site lattice-linear(i) * 4 + d.
-// ---------------------------------------------------------------------------------------
-template <int D>
-__device__ __forceinline__ void add_edge_noise(const Geometry& g, const Rng& rng, int n, int lin,
-                                               const double* sq, double* rhs) {
-  double z[D];
-  for (int d = 0; d < g.ndir / 2; ++d) {
-    if (__ldg(g.nbr + (size_t)(2 * d + 1) * g.ld + n) >= 0) {
-      site_normals<D>(rng, (uint32_t)lin * 4u + (uint32_t)d, z);
-#pragma unroll
-      for (int k = 0; k < D; ++k) rhs[k] += sq[k] * z[k];
-    }
-    if (__ldg(g.nbr + (size_t)(2 * d) * g.ld + n) >= 0) {
-      site_normals<D>(rng, (uint32_t)(lin - g.stride[d]) * 4u + (uint32_t)d, z);
-#pragma unroll
-      for (int k = 0; k < D; ++k) rhs[k] -= sq[k] * z[k];
-    }
-  }
-}
-
-__device__ __forceinline__ int degree(const Geometry& g, int n) {
-  int deg = 0;
-  for (int d = 0; d < g.ndir; ++d) deg += __ldg(g.nbr + (size_t)d * g.ld + n) >= 0 ? 1 : 0;
-  return deg;
-}
-
-// ---------------------------------------------------------------------------------------
 // W system. Bd_n = lambda_n sum_pq c_p c_q Sxx[p][q] + eps I, b_n = lambda_n sum_pq c_p c_q
 // Sxy[p][q] with c = (1, -a_n); perturbed rhs = b_n + L_n z2_n + sum_k sqrt(alpha_k) (G'z1_k)_n
 // with L_n = chol(Bd_n); preconditioner factor chol(Bd_n + diag(alpha) deg_n).
@@ -137,7 +108,8 @@ __global__ void __launch_bounds__(VOX_THREADS) k_assemble_w(AssembleArgs a) {
 #pragma unroll
     for (int q = 0; q <= PMAX; ++q) {
       if (p <= P && q <= P) {
-        const double cpq = c[p] * c[q];
+        const double cpq = a.Cmom ? __ldg(a.Cmom + (size_t)syy_index(p < q ? p : q, p < q ? q : p, P) * ld + n)
+                                  : c[p] * c[q];
         const double* S = shS + (size_t)(p * (P + 1) + q) * K * K;
 #pragma unroll
         for (int i = 0; i < K; ++i)
@@ -175,6 +147,7 @@ __global__ void __launch_bounds__(VOX_THREADS) k_assemble_w(AssembleArgs a) {
 #pragma unroll
   for (int e = 0; e < ntri(K); ++e) L[e] = B[e];
   bool ok = chol_packed_invdiag<K>(L);
+  if (a.ldata) store_packed<K>(a.ldata, ld, n, L);
   if (a.perturb) {
     const int lin = a.g.lin[n];
     double z[K], Lz[K];
@@ -219,14 +192,16 @@ __global__ void __launch_bounds__(VOX_THREADS) k_assemble_a(AssembleArgs a) {
   const size_t ld = a.g.ld;
   double w[K];
 #pragma unroll
-  for (int k = 0; k < K; ++k) w[k] = a.W[(size_t)k * ld + n];
+  for (int k = 0; k < K; ++k) w[k] = a.Gin ? 0.0 : a.W[(size_t)k * ld + n];
   double Gm[PMAX + 1][PMAX + 1];
 #pragma unroll
   for (int p = 0; p <= PMAX; ++p) {
 #pragma unroll
     for (int q = p; q <= PMAX; ++q) {
       double g = 0.0;
-      if (q <= P) {
+      if (q <= P && a.Gin) {
+        g = __ldg(a.Gin + (size_t)syy_index(p, q, P) * ld + n);
+      } else if (q <= P) {
         double t1 = 0.0, t2 = 0.0, quad = 0.0;
         const double* S = shS + (size_t)(p * (P + 1) + q) * K * K;
 #pragma unroll
@@ -265,6 +240,11 @@ __global__ void __launch_bounds__(VOX_THREADS) k_assemble_a(AssembleArgs a) {
 #pragma unroll
   for (int e = 0; e < ntri(PM); ++e) L[e] = J[e];
   bool ok = chol_packed_invdiag<PM>(L);
+  if (a.ldata) {
+#pragma unroll
+    for (int e = 0; e < ntri(PM); ++e)
+      if (e < ntri(P)) a.ldata[(size_t)e * ld + n] = L[e];
+  }
   const int lin = a.g.lin[n];
   if (a.perturb) {
     double z[PM], Lz[PM];

@@ -32,6 +32,91 @@ struct Geometry {
   int stride[3];      // lattice-linear strides of +x, +y, +z
 };
 
+// ---------------------------------------------------------------------------------------
+// Algorithm 2 perturbation for one voxel: rhs += sum_k sqrt(s_k) (G' z1_k)_n over the
+// voxel's edges. Edge (i, i + stride_d) carries +z at i and -z at its upper endpoint; its
+// normals come from site lattice-linear(i) * 4 + d.
+// ---------------------------------------------------------------------------------------
+template <int D>
+__device__ __forceinline__ void add_edge_noise(const Geometry& g, const Rng& rng, int n, int lin,
+                                               const double* sq, double* rhs) {
+  double z[D];
+  for (int d = 0; d < g.ndir / 2; ++d) {
+    if (__ldg(g.nbr + (size_t)(2 * d + 1) * g.ld + n) >= 0) {
+      site_normals<D>(rng, (uint32_t)lin * 4u + (uint32_t)d, z);
+#pragma unroll
+      for (int k = 0; k < D; ++k) rhs[k] += sq[k] * z[k];
+    }
+    if (__ldg(g.nbr + (size_t)(2 * d) * g.ld + n) >= 0) {
+      site_normals<D>(rng, (uint32_t)(lin - g.stride[d]) * 4u + (uint32_t)d, z);
+#pragma unroll
+      for (int k = 0; k < D; ++k) rhs[k] -= sq[k] * z[k];
+    }
+  }
+}
+
+__device__ __forceinline__ int degree(const Geometry& g, int n) {
+  int deg = 0;
+  for (int d = 0; d < g.ndir; ++d) deg += __ldg(g.nbr + (size_t)d * g.ld + n) >= 0 ? 1 : 0;
+  return deg;
+}
+
+// Lagged residual Gram G[p][q] = (L^p e)'(L^q e), e = y - X w, for p <= q <= P from the
+// statistics of voxel n and Sxx in shared memory ([(P+1)^2][K][K]); G is PMAX+1 square.
+template <int K>
+__device__ __forceinline__ void lagged_gram(const double* __restrict__ stats, const double* shS,
+                                            const double* w, int P, size_t ld, int n,
+                                            double G[PMAX + 1][PMAX + 1]) {
+#pragma unroll
+  for (int p = 0; p <= PMAX; ++p) {
+#pragma unroll
+    for (int q = p; q <= PMAX; ++q) {
+      double g = 0.0;
+      if (q <= P) {
+        double t1 = 0.0, t2 = 0.0, quad = 0.0;
+        const double* S = shS + (size_t)(p * (P + 1) + q) * K * K;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+          t1 += w[k] * __ldg(stats + (size_t)(n_syy(P) + (q * (P + 1) + p) * K + k) * ld + n);
+          t2 += w[k] * __ldg(stats + (size_t)(n_syy(P) + (p * (P + 1) + q) * K + k) * ld + n);
+          double sk = 0.0;
+#pragma unroll
+          for (int j = 0; j < K; ++j) sk += S[k * K + j] * w[j];
+          quad += w[k] * sk;
+        }
+        g = __ldg(stats + (size_t)syy_index(p, q, P) * ld + n) - t1 - t2 + quad;
+      }
+      G[p][q] = g;
+      G[q][p] = g;
+    }
+  }
+}
+
+// Spatial-VB kernels (kernels_svb.cu).
+struct SvbArgs {
+  Geometry g;
+  int K, P, T, S;
+  const double* stats;
+  const double* Sxx;
+  const double* Ws;     // [S][K][ld] W samples
+  const double* As;     // [S][P][ld] A samples
+  double* Cmom;         // [n_syy(P)][ld]
+  double* Gin;          // [n_syy(P)][ld]
+  const double* bmean;  // [D][ld]
+  const double* ldata;  // [ntri(D)][ld]
+  const double* scale;  // [D]
+  int spatial;          // A system: 1 with the beta D_a prior
+  double* rhs;          // [S][D][ld]
+  size_t vs;            // stride between samples of rhs
+  Rng rng;              // the sample index is the stream
+  double u1, u2;
+  double* lam;          // out: E[lambda]
+  double* part;         // [grid][D] quadratic-form partials
+};
+// what: 0 Cmom, 1 Gin, 2 perturbed rhs (dimension D), 3 E[lambda], 4 Q partials of W (D = K),
+// 5 Q partials of A (D = P). Returns the grid used for what 4/5 in *grid_out.
+cudaError_t launch_svb(int what, int D, const SvbArgs& a, cudaStream_t s, int* grid_out);
+
 struct StatsArgs {
   int N, T, K, P;
   size_t ld;
@@ -69,6 +154,10 @@ struct AssembleArgs {
   double* G;            // A system: [n_syy(P)][ld] lagged residual Gram (for lambda)
   double* x_direct;     // A system, independent prior: if set, the draw is written here
   int* bad_voxel;       // min index of a voxel whose block failed Cholesky (init INT_MAX)
+  // spatial VB
+  const double* Cmom;   // W system: [n_syy(P)][ld] E[c_p c_q] over A samples, replaces c c'
+  const double* Gin;    // A system: [n_syy(P)][ld] lagged residual Gram averaged over W samples
+  double* ldata;        // [ntri(D)][ld] Cholesky factor of the data block (or null)
 };
 cudaError_t launch_assemble_w(const AssembleArgs& a, cudaStream_t s);
 cudaError_t launch_assemble_a(const AssembleArgs& a, cudaStream_t s);

@@ -247,3 +247,49 @@ def test_probe_estimators_are_unbiased_for_logdet_and_traces():
     # log det M from the factor equals the dense log det of the preconditioner
     M = model.precision(lat, probes.precond_blocks(lat, Bd, s["alpha"]), np.zeros(2))
     assert abs(ldm - np.linalg.slogdet(M.toarray())[1]) < 1e-10 * abs(ldm)
+
+
+def test_svb_means_reduce_to_gibbs_parameters_for_one_sample():
+    """With one sample the SVB expectations are the Gibbs full-conditional parameters at that
+    sample: E[lambda] = scale * shape of Eq. fullcondTemplambda, E[alpha] likewise."""
+    w, lat = tiny(dims=(4, 3, 2), K=2, P=1, T=30, nb=6)
+    s = random_state(w, np.random.default_rng(11))
+    lam = gibbs.svb_lambda_mean(w.Y, w.X, [s["W"]], [s["A"]])
+    rss = model.rss_direct(w.Y, w.X, s["W"], s["A"])
+    sc, sh = model.lambda_params(rss, w.T, 1, 10.0, 0.1)
+    assert np.allclose(lam, sc * sh, rtol=1e-14)
+    a, Q = gibbs.svb_hyper_mean(lat, [s["W"]], 10.0, 0.1)
+    sc, sh = model.alpha_params(model.quad_forms_laplacian(lat, s["W"]), w.N, 10.0, 0.1)
+    assert np.allclose(a, sc * sh, rtol=1e-12)
+
+
+def test_svb_w_system_is_average_of_sample_systems():
+    """Eq. NFVBbB: averaging the blocks over A samples equals using E[c c'] of the whitening
+    coefficients c = (1, -a) in the sufficient-statistics expansion."""
+    w, lat = tiny(dims=(3, 3, 2), K=3, P=2, T=40, nb=6)
+    rng = np.random.default_rng(12)
+    A_s = [w.A_true + 0.05 * rng.standard_normal(w.A_true.shape) for _ in range(4)]
+    lam = rng.uniform(0.5, 2.0, w.N)
+    Bd, bw = gibbs.svb_w_system(w.Y, w.X, A_s, lam)
+    st = model.sufficient_stats(w.Y, w.X, 2)
+    C = [np.concatenate([np.ones((1, w.N)), -A], axis=0) for A in A_s]
+    Ecc = np.mean([np.einsum("pn,qn->npq", c, c) for c in C], axis=0)
+    XtX = np.einsum("npq,pqij->nij", Ecc, st["Sxx"])
+    Xty = np.einsum("npq,npqk->nk", Ecc, st["Sxy"])
+    assert np.allclose(Bd, lam[:, None, None] * XtX, rtol=1e-11)
+    assert np.allclose(bw, lam[:, None] * Xty, rtol=1e-11)
+
+
+def test_svb_extrapolation_rules():
+    """Appendix C trick 1: vertex after j -> vertex value; otherwise a 20x step; clamped to a
+    factor 5 of the VB proposal (self-consistency only: parity unpinned)."""
+    # 1, 1.5, 1.75 at j-2, j-1, j: parabola -x^2/8 + x/8 + 1.75 (x = iteration - j), vertex
+    # at x = 0.5 (after j) with value 1.78125
+    v = gibbs.svb_extrapolate((np.array([1.0]), np.array([1.5])), np.array([1.75]))
+    assert abs(v[0] - 1.78125) < 1e-12
+    # straight line -> no curvature -> 20x step, clamped at 5x
+    v = gibbs.svb_extrapolate((np.array([1.0]), np.array([2.0])), np.array([3.0]))
+    assert v[0] == 15.0
+    # decreasing toward zero: negative prediction falls back to the proposal
+    v = gibbs.svb_extrapolate((np.array([3.0]), np.array([2.0])), np.array([1.0]))
+    assert v[0] >= 1.0 / 5.0
