@@ -44,6 +44,7 @@ typedef int bfmri_status;
 #define BFMRI_ERR_CUDA          -6  /* a CUDA runtime call failed */
 #define BFMRI_ERR_INTERNAL      -7
 #define BFMRI_ERR_STATE         -8  /* call out of order, e.g. sampling before statistics */
+#define BFMRI_PENDING            1  /* server: the request has not finished yet (not an error) */
 
 /* Voxel lattice: nx * ny * nz sites; neighbourhood 6 (3D: +-x, +-y, +-z) or 4 (slice-wise
  * 2D: +-x, +-y only). The UGL prior of Section 2 links in-mask face neighbours. */
@@ -96,6 +97,9 @@ typedef struct {
   int pcg_variant;           /* BFMRI_PCG_AUTO (default): the register-resident solver when the
                                 voxels fit one CTA per SM, else the streaming one;
                                 BFMRI_PCG_STREAMING: always the streaming solver */
+  int sm_budget;             /* most SMs one solver grid may span (0 = all). Concurrent
+                                handles whose budgets sum to at most the SM count can run
+                                their cooperative solves side by side. */
 } bfmri_options;
 
 #define BFMRI_PCG_AUTO      0
@@ -278,6 +282,60 @@ bfmri_status bfmri_reset_timing(bfmri_handle* h);
 bfmri_status bfmri_apply_precision(bfmri_handle* h, int which, const double* x, double* y);
 bfmri_status bfmri_build_system(bfmri_handle* h, int which, uint64_t counter, double* blocks,
                                 double* b_mean, double* b_pert);
+
+/* ---------------------------------------------------------------------------------------
+ * Serving: many subjects on one GPU with continuous admission.
+ *
+ * A server owns max_slots slots, each with a host worker thread and a CUDA stream, and a
+ * device-memory budget. Submitted requests wait in FIFO order; the oldest starts as soon as
+ * a slot is free and its device-memory estimate (bfmri_request_device_bytes) fits in the
+ * budget left by the running requests, so requests that arrive while others run are
+ * admitted as slots and memory free up, and their kernels overlap on the device. A request
+ * runs bfmri_create, bfmri_precompute_stats, n_sweeps Gibbs sweeps (draw counters
+ * first_counter, first_counter + 1, ...) and copies the final W (and alpha) to the caller's
+ * buffers, then releases its memory. Each slot's solver grids span at most sm_budget SMs
+ * (0 = all); budgets whose sum does not exceed the SM count let every slot's cooperative
+ * solve be resident at once. A request's result does not depend on what else runs (fixed
+ * grids, fixed-order reductions, counter-based random numbers). The server is internally
+ * synchronised; the host arrays of a request must stay valid until it completes. */
+typedef struct bfmri_server bfmri_server;
+
+typedef struct {
+  bfmri_lattice lat;
+  const uint8_t* mask;
+  const double* X;
+  const void* Y;
+  int y_dtype;
+  int T, K, P;
+  bfmri_options opt;        /* per-request options (cuda_stream and sm_budget are set by the
+                               server; allocator callbacks are used from worker threads) */
+  int n_sweeps;
+  uint64_t first_counter;
+  double* W_out;            /* K x N, may be NULL */
+  double* alpha_out;        /* K, may be NULL */
+} bfmri_request;
+
+typedef struct {
+  int status;               /* BFMRI_OK, an error code, or BFMRI_PENDING */
+  int N;
+  double submit_s, start_s, end_s;  /* host clock, seconds since the server was created */
+  long long pcg_iterations;
+  size_t device_bytes;      /* the admission estimate */
+} bfmri_result;
+
+size_t bfmri_request_device_bytes(int N, int T, int K, int P, int y_dtype, int precision);
+bfmri_status bfmri_server_create(size_t budget_bytes, int max_slots, int sm_budget,
+                                 bfmri_server** out);
+/* Errors: INVALID_ARG, OOM (the request alone exceeds the budget). */
+bfmri_status bfmri_server_submit(bfmri_server* s, const bfmri_request* req, long long* ticket);
+/* BFMRI_OK with the result when the request has finished (the ticket is then released),
+ * BFMRI_PENDING otherwise; wait != 0 blocks until it finishes. */
+bfmri_status bfmri_server_poll(bfmri_server* s, long long ticket, int wait, bfmri_result* res);
+/* Largest device-memory estimate and number of requests in flight at once so far. */
+bfmri_status bfmri_server_stats(bfmri_server* s, size_t* peak_bytes, int* peak_running,
+                                size_t* in_use);
+/* Waits for every submitted request, then stops the workers. */
+bfmri_status bfmri_server_destroy(bfmri_server* s);
 
 /* ---------------------------------------------------------------------------------------
  * Allocation-free solve (the paper has no counterpart: this is an interface addition).

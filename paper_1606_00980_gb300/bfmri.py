@@ -44,7 +44,8 @@ class bfmri_options(C.Structure):
                 ("inner_tol", C.c_double), ("seed", C.c_uint64), ("stream_id", C.c_uint32),
                 ("cuda_stream", C.c_void_p), ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN),
                 ("alloc_ctx", C.c_void_p), ("barrier_timeout_s", C.c_double),
-                ("debug_skip_block", C.c_int), ("profile", C.c_int), ("pcg_variant", C.c_int)]
+                ("debug_skip_block", C.c_int), ("profile", C.c_int), ("pcg_variant", C.c_int),
+                ("sm_budget", C.c_int)]
 
 
 class bfmri_solve_info(C.Structure):
@@ -72,6 +73,20 @@ class bfmri_timing(C.Structure):
                 ("pcg_iterations", C.c_longlong * 8)]
 
 
+class bfmri_request(C.Structure):
+    _fields_ = [("lat", bfmri_lattice), ("mask", C.c_void_p), ("X", C.c_void_p), ("Y", C.c_void_p),
+                ("y_dtype", C.c_int), ("T", C.c_int), ("K", C.c_int), ("P", C.c_int),
+                ("opt", bfmri_options), ("n_sweeps", C.c_int), ("first_counter", C.c_uint64),
+                ("W_out", C.c_void_p), ("alpha_out", C.c_void_p)]
+
+
+class bfmri_result(C.Structure):
+    _fields_ = [("status", C.c_int), ("N", C.c_int), ("submit_s", C.c_double),
+                ("start_s", C.c_double), ("end_s", C.c_double), ("pcg_iterations", C.c_longlong),
+                ("device_bytes", C.c_size_t)]
+
+
+BFMRI_PENDING = 1
 _P = C.POINTER
 _dp = _P(C.c_double)
 _vp = C.c_void_p
@@ -105,6 +120,12 @@ SIGNATURES = [
     ("bfmri_reset_timing", C.c_int, [_h]),
     ("bfmri_apply_precision", C.c_int, [_h, C.c_int, _dp, _dp]),
     ("bfmri_build_system", C.c_int, [_h, C.c_int, C.c_uint64, _dp, _dp, _dp]),
+    ("bfmri_request_device_bytes", C.c_size_t, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int]),
+    ("bfmri_server_create", C.c_int, [C.c_size_t, C.c_int, C.c_int, _P(C.c_void_p)]),
+    ("bfmri_server_submit", C.c_int, [C.c_void_p, _P(bfmri_request), _P(C.c_longlong)]),
+    ("bfmri_server_poll", C.c_int, [C.c_void_p, C.c_longlong, C.c_int, _P(bfmri_result)]),
+    ("bfmri_server_stats", C.c_int, [C.c_void_p, _P(C.c_size_t), _P(C.c_int), _P(C.c_size_t)]),
+    ("bfmri_server_destroy", C.c_int, [C.c_void_p]),
     ("bfmri_pcg_static_capacity", C.c_size_t, []),
     ("bfmri_pcg_static_bytes", C.c_size_t, [C.c_size_t, C.c_int]),
     ("bfmri_pcg_solve_static", C.c_int, [C.c_int, C.c_int, C.c_int, _vp, C.c_size_t, _vp, _vp,
@@ -227,6 +248,65 @@ def bfmri_create(lattice, mask, X, Y, K, P, opts=None, torch_memory=True):
 
 def bfmri_destroy(h):
     _check(load_library().bfmri_destroy(h))
+
+
+class Server:
+    """A bfmri_server: requests (synthetic workloads) are submitted with their host arrays,
+    which this object keeps alive until the request has finished."""
+
+    def __init__(self, budget_bytes, slots, sm_budget=0):
+        self.lib = load_library()
+        h = C.c_void_p()
+        _check(self.lib.bfmri_server_create(int(budget_bytes), slots, sm_budget, C.byref(h)))
+        self.h = h
+        self._keep = {}
+
+    def submit(self, w, n_sweeps, first_counter=0, **opt_fields):
+        o = bfmri_default_options()
+        o.eps = w.eps
+        o.delta = w.delta
+        for k, v in opt_fields.items():
+            setattr(o, k, v)
+        mask = np.ascontiguousarray(w.mask, dtype=np.uint8).reshape(-1)
+        X = np.asfortranarray(w.X, dtype=np.float64)
+        Y = np.ascontiguousarray(w.Y)
+        W = np.empty((w.K, w.N))
+        alpha = np.empty(w.K)
+        nx, ny, nz = w.dims
+        r = bfmri_request(lat=bfmri_lattice(nx, ny, nz, w.neighbourhood),
+                          mask=mask.ctypes.data, X=X.ctypes.data, Y=Y.ctypes.data,
+                          y_dtype=BFMRI_F64 if Y.dtype == np.float64 else BFMRI_F32,
+                          T=w.T, K=w.K, P=w.P, opt=o, n_sweeps=n_sweeps,
+                          first_counter=first_counter, W_out=W.ctypes.data,
+                          alpha_out=alpha.ctypes.data)
+        t = C.c_longlong()
+        _check(self.lib.bfmri_server_submit(self.h, C.byref(r), C.byref(t)))
+        self._keep[t.value] = (mask, X, Y, W, alpha, r)
+        return t.value
+
+    def poll(self, ticket, wait=True):
+        res = bfmri_result()
+        st = self.lib.bfmri_server_poll(self.h, ticket, 1 if wait else 0, C.byref(res))
+        if st == BFMRI_PENDING:
+            return None
+        _check(st)
+        if res.status != BFMRI_OK:
+            raise BfmriError(res.status, "request failed")
+        mask, X, Y, W, alpha, r = self._keep.pop(ticket)
+        return dict(W=W, alpha=alpha, N=res.N, submit_s=res.submit_s, start_s=res.start_s,
+                    end_s=res.end_s, pcg_iterations=res.pcg_iterations,
+                    device_bytes=res.device_bytes)
+
+    def stats(self):
+        pb, pr, iu = C.c_size_t(), C.c_int(), C.c_size_t()
+        _check(self.lib.bfmri_server_stats(self.h, C.byref(pb), C.byref(pr), C.byref(iu)))
+        return dict(peak_bytes=pb.value, peak_running=pr.value, in_use=iu.value)
+
+    def close(self):
+        if self.h:
+            _check(self.lib.bfmri_server_destroy(self.h))
+            self.h = None
+            self._keep.clear()
 
 
 def bfmri_pcg_solve_static(N, D, neighbourhood, nbr_ptr, ld, blocks_ptr, scale_ptr, b_ptr,
@@ -354,6 +434,11 @@ class Model:
         self._c(self.lib.bfmri_spvb_step(self.handle, n_samples, counter, 1 if extrapolate else 0,
                                          _ptr(avb), _ptr(bvb), C.byref(info)))
         return avb, bvb[:self.P], info
+
+    def svb_set_sample(self, j, W=None, A=None):
+        W = None if W is None else _f64(W)
+        A = None if A is None else _f64(A)
+        self._c(self.lib.bfmri_svb_set_sample(self.handle, j, _ptr(W), _ptr(A)))
 
     def svb_sample(self, j):
         W = np.empty((self.K, self.N))

@@ -277,6 +277,7 @@ bfmri_status run_pcg(bfmri_handle* h, int D, const double* scale, double* x, int
   a.part = h->d_part;
   a.tot = h->d_part + (size_t)h->part_rows * 4;
   a.allow_resident = h->opt.pcg_variant == BFMRI_PCG_AUTO;
+  a.sm_cap = h->opt.sm_budget;
   a.mixed = h->opt.precision == BFMRI_PREC_MIXED;
   a.blocks32 = h->d_blocks32;
   a.mfac32 = h->opt.precond == BFMRI_PRECOND_BLOCK_JACOBI ? h->d_mfac32 : nullptr;
@@ -498,6 +499,7 @@ MrhsArgs mrhs_args(bfmri_handle* h, int D, int S, const double* scale, int max_i
   m.delta = h->opt.delta;
   m.max_iter = max_iter;
   m.max_restarts = 4;
+  m.sm_cap = h->opt.sm_budget;
   return m;
 }
 
@@ -590,6 +592,7 @@ bfmri_status bfmri_create(const bfmri_lattice* lat, const uint8_t* mask, const d
   if (!(o.delta > 0.0) || o.max_iter < 1 || !(o.barrier_timeout_s > 0.0) || o.eps < 0.0 ||
       !(o.q1 > 0) || !(o.q2 > 0) || !(o.u1 > 0) || !(o.u2 > 0) || !(o.r1 > 0) || !(o.r2 > 0))
     return fail(nullptr, BFMRI_ERR_INVALID_ARG, "invalid option value");
+  if (o.sm_budget < 0) return fail(nullptr, BFMRI_ERR_INVALID_ARG, "sm_budget must be >= 0");
   if (o.pcg_variant != BFMRI_PCG_AUTO && o.pcg_variant != BFMRI_PCG_STREAMING)
     return fail(nullptr, BFMRI_ERR_INVALID_ARG, "unknown pcg_variant");
   if (o.precond != BFMRI_PRECOND_NONE && o.precond != BFMRI_PRECOND_BLOCK_JACOBI)

@@ -377,6 +377,7 @@ static cudaError_t launch_d(const MrhsArgs& a, cudaStream_t stream, int* units_o
   int dev = 0, nsm = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (a.sm_cap > 0 && a.sm_cap < nsm) nsm = a.sm_cap;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mrhs<D>, MRHS_THREADS, 0);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;

@@ -783,10 +783,15 @@ int num_sms() {
   return nsm;
 }
 
+int capped_sms(int cap) {
+  const int n = num_sms();
+  return (cap > 0 && cap < n) ? cap : n;
+}
+
 template <int D>
 cudaError_t launch_resident(const PcgArgs& a, cudaStream_t stream, int* grid_out, bool* launched) {
   *launched = false;
-  const int nsm = num_sms();
+  const int nsm = capped_sms(a.sm_cap);
   int threads = (a.N + nsm - 1) / nsm;
   threads = ((threads + 31) / 32) * 32;
   if (threads < 64) threads = 64;
@@ -824,7 +829,7 @@ static cudaError_t launch_d(const PcgArgs& a, cudaStream_t stream, int* grid_out
       if (launched || e != cudaSuccess) return e;
     }
   }
-  const int nsm = num_sms();
+  const int nsm = capped_sms(a.sm_cap);
   const void* kern = a.mixed ? (const void*)k_pcg_mixed_stream<D> : (const void*)k_pcg_stream<D>;
   int per_sm = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, PCG_THREADS, 0);

@@ -51,6 +51,7 @@ struct MrhsArgs {
   double delta;
   int max_iter;
   int max_restarts;
+  int sm_cap;            // most SMs the grid may span (0 = all)
 };
 
 // Probe set-up and post-processing (log-determinant and trace probes).

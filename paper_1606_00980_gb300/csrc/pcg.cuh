@@ -48,6 +48,7 @@ struct PcgArgs {
   int skip_block;        // test hook (-1 off): this CTA never reaches the first barrier
   int max_grid;          // rows of the partial buffer: the launch never uses more CTAs
   int allow_resident;    // 1: use the register/shared-memory resident variant when N fits
+  int sm_cap;            // most SMs the grid may span (0 = all)
   // mixed precision: FP32 inner PCG inside FP64 iterative refinement
   int mixed;
   const float* blocks32; // [ntri(D)][ld] FP32 copies of blocks / mfac

@@ -1,0 +1,75 @@
+"""Serving (continuous admission of subjects into slots under a memory budget), needs a GB300.
+
+Each request's result must not depend on what else runs: the same request alone and in the
+mix gives bit-identical W and alpha (fixed grids under the slot's SM budget, fixed-order
+reductions, counter-based random numbers), and equals the single-handle API with the same
+options. The device-memory estimate of the requests in flight never exceeds the budget.
+"""
+import numpy as np
+import pytest
+
+from paper_1606_00980_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def requests():
+    out = []
+    for i, (dims, K, P, T) in enumerate([((9, 8, 6), 3, 1, 40), ((12, 10, 8), 4, 2, 50),
+                                          ((7, 7, 5), 2, 3, 36), ((14, 12, 9), 5, 2, 60),
+                                          ((10, 9, 7), 6, 3, 48), ((8, 8, 8), 4, 1, 44)]):
+        out.append(synth.small3d(seed=100 + i, dims=dims, K=K, P=P, T=T))
+    return out
+
+
+def run(server, ws, n_sweeps=3):
+    from paper_1606_00980_gb300 import bfmri
+    tickets = [server.submit(w, n_sweeps, first_counter=7 * i, precision=bfmri.PREC_MIXED,
+                             delta=1e-8, seed=555 + i) for i, w in enumerate(ws)]
+    return [server.poll(t) for t in tickets]
+
+
+def test_result_is_the_same_alone_and_in_the_mix():
+    from paper_1606_00980_gb300 import bfmri
+    ws = requests()
+    s = bfmri.Server(budget_bytes=8 << 30, slots=3, sm_budget=48)
+    mixed = run(s, ws)
+    st = s.stats()
+    s.close()
+    assert st["peak_running"] >= 2          # requests overlapped
+    for i, w in enumerate(ws):
+        s1 = bfmri.Server(budget_bytes=8 << 30, slots=3, sm_budget=48)
+        tick = s1.submit(w, 3, first_counter=7 * i, precision=bfmri.PREC_MIXED, delta=1e-8,
+                         seed=555 + i)
+        alone = s1.poll(tick)
+        s1.close()
+        assert np.array_equal(alone["W"], mixed[i]["W"])
+        assert np.array_equal(alone["alpha"], mixed[i]["alpha"])
+        # and the same as the single-handle API with the same options
+        m = bfmri.Model.from_workload(w, precision=bfmri.PREC_MIXED, delta=1e-8, seed=555 + i,
+                                      sm_budget=48)
+        m.precompute_stats()
+        m.gibbs_sweep(3, 7 * i)
+        assert np.array_equal(m.get_state()["W"], mixed[i]["W"])
+        m.close()
+
+
+def test_admission_respects_the_memory_budget():
+    from paper_1606_00980_gb300 import bfmri
+    ws = requests()
+    lib = bfmri.load_library()
+    sizes = [lib.bfmri_request_device_bytes(w.N, w.T, w.K, w.P, bfmri.BFMRI_F64, bfmri.PREC_MIXED)
+             for w in ws]
+    budget = int(max(sizes) * 1.6)          # at most one large request at a time
+    s = bfmri.Server(budget_bytes=budget, slots=4, sm_budget=38)
+    res = run(s, ws)
+    st = s.stats()
+    s.close()
+    assert st["peak_bytes"] <= budget
+    assert all(r["end_s"] >= r["start_s"] >= r["submit_s"] for r in res)
+    with pytest.raises(bfmri.BfmriError):
+        s2 = bfmri.Server(budget_bytes=min(sizes) // 2, slots=1)
+        try:
+            s2.submit(ws[0], 1)
+        finally:
+            s2.close()

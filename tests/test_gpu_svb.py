@@ -72,7 +72,15 @@ def test_svb_step_single_step_parity(spatial):
     Wo2 = gibbs.svb_draw(lat, Bd2, bw2, st1["alpha"], SEED, c, philox.TAG_W, Ns)
     for j in range(Ns):
         assert rel(Wg2[j], Wo2[j]) <= 1e-8
-    assert info2.pcg_iterations_W < info.pcg_iterations_W   # warm starts pay
+    # the same second iteration from cold (zero) samples needs more PCG iterations
+    for j in range(Ns):
+        m.svb_set_sample(j, W=np.zeros((w.K, w.N)), A=Ag[j])
+    m.set_state(lam=st1["lam"], alpha=st1["alpha"], beta=st1["beta"] if w.P else None)
+    _, _, info_cold = m.spvb_step(Ns, c, extrapolate=False)
+    Wc = [m.svb_sample(j)[0] for j in range(Ns)]
+    for j in range(Ns):
+        assert rel(Wc[j], Wo2[j]) <= 1e-8
+    assert info2.pcg_iterations_W < info_cold.pcg_iterations_W
     m.close()
 
 
