@@ -282,6 +282,7 @@ def run_ours(args, world, rank, local):
 
     # end to end through the C ABI with host buffers
     e2e = run_e2e(args, w) if rank == 0 else None
+    serving = run_serving(args) if (rank == 0 and not args.no_serving) else None
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         zc = w.dims[2] // 2
@@ -299,7 +300,7 @@ def run_ours(args, world, rank, local):
                            "pcg_iterations_W_per_sweep": it_w / args.steps,
                            "pcg_iterations_A_per_sweep": it_a / args.steps},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-                "mixed_precision": mixed,
+                "mixed_precision": mixed, "serving": serving,
                 "gpu_launches": int(n_launch),
                 "kernel_ms_per_step": {k: v["ms"] / args.steps for k, v in tim.items() if v["launches"]}}
         print(json.dumps(line), flush=True)
@@ -343,6 +344,65 @@ def run_mixed(args, w, flush, stream):
             "kernel_ms_per_step": {k: v["ms"] / args.steps for k, v in tim.items() if v["launches"]}}
 
 
+def run_serving(args):
+    """Serving workload: a Poisson stream of requests, each a synthetic subject (ellipsoid mask
+    of 5k-300k voxels, log-uniform; K in {4,6,8,10}; T in {150,300,600}; AR(1)-AR(3)), each
+    running create + statistics + 8 mixed-precision Gibbs sweeps at delta = 1e-8 with its state
+    resident on the device, admitted into 4 slots under a 64 GB device-memory budget. The
+    distinct subjects are a pool of 8 that spans those ranges (generating hundreds of distinct
+    subjects on the host would dominate the run); requests draw from it uniformly in log N.
+    Latency = submission -> result readable on the host."""
+    import numpy as np
+
+    from paper_1606_00980_gb300 import bfmri, synth
+    rng = np.random.default_rng(11)
+    Ks, Ts = [4, 6, 8, 10], [150, 300, 600]
+    pool = []
+    for i, n_target in enumerate(np.geomspace(5000, 300000, 8)):
+        T = Ts[i % 3] if n_target < 150000 else 150
+        w = synth.request_workload(seed=300 + i, N_target=int(n_target), K=Ks[i % 4], T=T,
+                                   P=1 + i % 3)
+        w.Y = w.Y.astype(np.float32)
+        pool.append(w)
+    slots, sm_budget, budget = 4, 38, 64 << 30
+    opts = dict(precision=bfmri.PREC_MIXED, delta=1e-8, inner_tol=1e-4)
+    # service-time pilot: every pool member alone, one slot
+    srv = bfmri.Server(budget, 1, sm_budget)
+    pilot = []
+    for i, w in enumerate(pool):
+        t = srv.submit(w, 8, first_counter=0, seed=1000 + i, **opts)
+        r = srv.poll(t)
+        pilot.append(r["end_s"] - r["start_s"])
+    srv.close()
+    mean_service = float(np.mean(pilot))
+    rate = 0.8 * slots / mean_service          # offered load ~0.8 of the slots' capacity
+    n_req = args.serving_requests
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, n_req))
+    picks = rng.integers(0, len(pool), n_req)
+    srv = bfmri.Server(budget, slots, sm_budget)
+    t0 = time.perf_counter()
+    tickets = []
+    for i in range(n_req):
+        delay = arrivals[i] - (time.perf_counter() - t0)
+        if delay > 0:
+            time.sleep(delay)
+        tickets.append(srv.submit(pool[picks[i]], 8, first_counter=17 * i, seed=5000 + i, **opts))
+    results = [srv.poll(t) for t in tickets]
+    makespan = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    lat = np.array([r["end_s"] - r["submit_s"] for r in results]) * 1e3
+    return {"requests": n_req, "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
+            "draws_per_s": 8 * n_req / makespan, "unit": UNIT, "makespan_s": makespan,
+            "offered_rate_per_s": rate, "mean_service_ms_alone": mean_service * 1e3,
+            "slots": slots, "sm_budget_per_slot": sm_budget, "budget_bytes": budget,
+            "peak_in_flight": st["peak_running"], "peak_bytes": st["peak_bytes"],
+            "pool_N": [int(w.N) for w in pool], "pool_K": [int(w.K) for w in pool],
+            "pool_T": [int(w.T) for w in pool], "pool_P": [int(w.P) for w in pool],
+            "work_per_request": "create + stats + 8 mixed-precision Gibbs sweeps (delta 1e-8)"}
+
+
 def run_e2e(args, w):
     """create (host X, Y) + statistics + S sweeps, each draw copied to pinned host memory."""
     import numpy as np
@@ -376,6 +436,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serving-requests", type=int, default=96)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -57,6 +57,7 @@ def workloads():
                                            neighbourhood=6, seed=14, ar_mean=(0.3,), drift=True),
         "P0_K2": synth.make_workload("p0", (6, 5, 4), np.ones((4, 5, 6), np.uint8), T=30, K=2,
                                      P=0, neighbourhood=6, seed=15),
+        "K10_P2": synth.small3d(seed=16, dims=(9, 8, 6), K=10, P=2, T=70),
     }
 
 
@@ -227,6 +228,24 @@ def test_gibbs_sweep_single_step_parity(case):
         br = gibbs.sample_beta(lat, s1, SEED, 9)
         assert np.max(np.abs(g["beta"] / br - 1)) <= 1e-10
     assert info.pcg_iterations_W > 0
+    m.close()
+
+
+def test_stats_from_float32_series():
+    """Single-precision Y (the serving input format): statistics equal the FP64 oracle's for
+    the same rounded values."""
+    w = WL["slab_K6_P3"]
+    from paper_1606_00980_gb300.bfmri import Model
+    Y32 = w.Y.astype(np.float32)
+    nx, ny, nz = w.dims
+    m = Model((nx, ny, nz, w.neighbourhood), w.mask, w.X, Y32, w.K, w.P, seed=SEED)
+    m.precompute_stats()
+    got = m.get_stats()
+    st = model.sufficient_stats(Y32.astype(np.float64), w.X, w.P)
+    iu = [(p, q) for p in range(w.P + 1) for q in range(p, w.P + 1)]
+    ref = np.concatenate([np.stack([st["Syy"][:, p, q] for p, q in iu], axis=1),
+                          st["Sxy"].reshape(w.N, -1)], axis=1)
+    assert np.max(np.abs(got - ref)) <= 1e-12 * np.abs(ref).max()
     m.close()
 
 
