@@ -283,6 +283,7 @@ def run_ours(args, world, rank, local):
     # end to end through the C ABI with host buffers
     e2e = run_e2e(args, w) if rank == 0 else None
     serving = run_serving(args) if (rank == 0 and not args.no_serving) else None
+    batched = run_batched(args) if (rank == 0 and not args.no_batched) else None
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         zc = w.dims[2] // 2
@@ -300,7 +301,7 @@ def run_ours(args, world, rank, local):
                            "pcg_iterations_W_per_sweep": it_w / args.steps,
                            "pcg_iterations_A_per_sweep": it_a / args.steps},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-                "mixed_precision": mixed, "serving": serving,
+                "mixed_precision": mixed, "serving": serving, "batched_probes": batched,
                 "gpu_launches": int(n_launch),
                 "kernel_ms_per_step": {k: v["ms"] / args.steps for k, v in tim.items() if v["launches"]}}
         print(json.dumps(line), flush=True)
@@ -344,6 +345,52 @@ def run_mixed(args, w, flush, stream):
             "kernel_ms_per_step": {k: v["ms"] / args.steps for k, v in tim.items() if v["launches"]}}
 
 
+def mrhs_bytes_per_voxel_iter_rhs(D, S, w=4):
+    """Bytes one multi-RHS iteration must move per voxel and right-hand side: the local phase
+    reads u, w, p, s, x, r and writes p, s, x, r, u (11 D words), the product phase reads u and
+    r and writes w (3 D words); the block and the preconditioner factor (D(D+1)/2 words each)
+    are shared by the S right-hand sides."""
+    return w * (14 * D) + w * 2 * (D * (D + 1) // 2) / S
+
+
+def run_batched(args):
+    """Batched probes: the 96x96x60 lattice (ellipsoid, ~250k voxels, K = 8, AR(3), T = 300),
+    64 Rademacher probes for log det B~ solved together by the FP32-storage multi-RHS PCG
+    (FP64 scalars and sums) to relative residual 1e-5, after 3 mixed-precision Gibbs sweeps
+    from the prior means. Reports the probe solve's achieved HBM bandwidth."""
+    import torch
+
+    from paper_1606_00980_gb300 import bfmri, synth
+    from paper_1606_00980_gb300.bfmri import Model
+    w = synth.batch3d()
+    m = Model.from_workload(w, delta=1e-5, precision=bfmri.PREC_MIXED, seed=4242, profile=1)
+    m.precompute_stats()
+    m.gibbs_sweep(3, 0)
+    S = 64
+    m.logdet_probe(0, S, 3000, counter=1)            # warm-up (workspace allocation)
+    m.reset_timing()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res = m.logdet_probe(0, S, 3000, counter=2)
+    wall = time.perf_counter() - t0
+    tim = m.timing()
+    m.close()
+    solve_s = tim["other"]["ms"] / 1e3
+    iters = int(res["iterations"].sum())
+    bytes_ = iters * w.N * mrhs_bytes_per_voxel_iter_rhs(w.K, S)
+    hbm_peak, hbm_src, _ = peaks()
+    gbs = bytes_ / solve_s / 1e9
+    return {"workload": f"batch3d_96x96x60_ellipsoid_N{w.N}_K{w.K}_T{w.T}_AR3",
+            "probes": S, "logdet": res["logdet"], "stderr": res["stderr"],
+            "probe_iterations_mean": float(res["iterations"].mean()),
+            "probe_iterations_max": int(res["iterations"].max()),
+            "solve_ms": solve_s * 1e3, "call_ms": wall * 1e3,
+            "roofline": {"kernel": f"k_mrhs<{w.K}, float>", "bound": "hbm", "achieved": gbs,
+                         "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                         "traffic": None, "peak_source": f"{hbm_src} (MEASURED_PEAKS.json)",
+                         "bytes_per_voxel_iter_rhs": mrhs_bytes_per_voxel_iter_rhs(w.K, S)}}
+
+
 def run_serving(args):
     """Serving workload: a Poisson stream of requests, each a synthetic subject (ellipsoid mask
     of 5k-300k voxels, log-uniform; K in {4,6,8,10}; T in {150,300,600}; AR(1)-AR(3)), each
@@ -366,16 +413,23 @@ def run_serving(args):
         pool.append(w)
     slots, sm_budget, budget = 4, 38, 64 << 30
     opts = dict(precision=bfmri.PREC_MIXED, delta=1e-8, inner_tol=1e-4)
-    # service-time pilot: every pool member alone, one slot
-    srv = bfmri.Server(budget, 1, sm_budget)
+    # capacity pilot: every pool member alone (service time), then a saturating burst of
+    # 4 x the pool through all slots (sustained requests/s)
+    srv = bfmri.Server(budget, slots, sm_budget)
     pilot = []
     for i, w in enumerate(pool):
         t = srv.submit(w, 8, first_counter=0, seed=1000 + i, **opts)
         r = srv.poll(t)
         pilot.append(r["end_s"] - r["start_s"])
-    srv.close()
     mean_service = float(np.mean(pilot))
-    rate = 0.8 * slots / mean_service          # offered load ~0.8 of the slots' capacity
+    t0 = time.perf_counter()
+    burst = [srv.submit(pool[i % len(pool)], 8, first_counter=i, seed=2000 + i, **opts)
+             for i in range(4 * len(pool))]
+    for t in burst:
+        srv.poll(t)
+    capacity = 4 * len(pool) / (time.perf_counter() - t0)
+    srv.close()
+    rate = 0.8 * capacity                      # offered load 0.8 of the measured capacity
     n_req = args.serving_requests
     arrivals = np.cumsum(rng.exponential(1.0 / rate, n_req))
     picks = rng.integers(0, len(pool), n_req)
@@ -395,7 +449,8 @@ def run_serving(args):
     return {"requests": n_req, "p50_ms": float(np.percentile(lat, 50)),
             "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
             "draws_per_s": 8 * n_req / makespan, "unit": UNIT, "makespan_s": makespan,
-            "offered_rate_per_s": rate, "mean_service_ms_alone": mean_service * 1e3,
+            "offered_rate_per_s": rate, "capacity_per_s": capacity,
+            "mean_service_ms_alone": mean_service * 1e3,
             "slots": slots, "sm_budget_per_slot": sm_budget, "budget_bytes": budget,
             "peak_in_flight": st["peak_running"], "peak_bytes": st["peak_bytes"],
             "pool_N": [int(w.N) for w in pool], "pool_K": [int(w.K) for w in pool],
@@ -437,6 +492,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=96)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":

@@ -213,10 +213,14 @@ bfmri_status bfmri_gibbs_sweep(bfmri_handle* h, int n_sweeps, uint64_t first_cou
  *             estimate of tr(D_w^(k) B~^-1), the trace term of the SVB alpha update
  *             (Eq. quad-form-expectation); may be NULL
  *  per_probe: n_probes values estimate_i (may be NULL)
+ *  iterations: n_probes PCG iteration counts (may be NULL)
+ * With precision BFMRI_PREC_MIXED the probe solves run in FP32 storage and arithmetic per
+ * voxel (CG scalars, inner-product sums, quadrature and log det accumulation in FP64); use a
+ * delta an FP32 recurrence can reach (e.g. 1e-5).
  * Errors: STATE, NOT_CONVERGED (a probe hit lanczos_steps), NOT_SPD, CUDA, OOM. */
 bfmri_status bfmri_logdet_probe(bfmri_handle* h, int which, int n_probes, int lanczos_steps,
                                 uint64_t counter, double* logdet, double* std_err,
-                                double* traces, double* per_probe);
+                                double* traces, double* per_probe, int* iterations);
 
 /* One spatial-VB iteration (Section 3.3; Appendix B, Eq. NFVBw / NFVBbB; Appendix C).
  * The handle's lambda, alpha, beta are the current means E[lambda], E[alpha], E[beta]; the
@@ -307,8 +311,8 @@ typedef struct {
   const void* Y;
   int y_dtype;
   int T, K, P;
-  bfmri_options opt;        /* per-request options (cuda_stream and sm_budget are set by the
-                               server; allocator callbacks are used from worker threads) */
+  bfmri_options opt;        /* per-request options; the server sets cuda_stream, sm_budget
+                               and the allocator (stream-ordered, from the server's pool) */
   int n_sweeps;
   uint64_t first_counter;
   double* W_out;            /* K x N, may be NULL */

@@ -111,7 +111,8 @@ SIGNATURES = [
     ("bfmri_sample_alpha", C.c_int, [_h, C.c_uint64, _dp]),
     ("bfmri_sample_beta", C.c_int, [_h, C.c_uint64, _dp]),
     ("bfmri_gibbs_sweep", C.c_int, [_h, C.c_int, C.c_uint64, _P(bfmri_sweep_info)]),
-    ("bfmri_logdet_probe", C.c_int, [_h, C.c_int, C.c_int, C.c_int, C.c_uint64, _dp, _dp, _dp, _dp]),
+    ("bfmri_logdet_probe", C.c_int, [_h, C.c_int, C.c_int, C.c_int, C.c_uint64, _dp, _dp, _dp, _dp,
+                                     _P(C.c_int)]),
     ("bfmri_lanczos_log_quadrature", C.c_int, [C.c_int, _dp, _dp, _dp]),
     ("bfmri_spvb_step", C.c_int, [_h, C.c_int, C.c_uint64, C.c_int, _dp, _dp, _P(bfmri_svb_info)]),
     ("bfmri_svb_get_sample", C.c_int, [_h, C.c_int, _dp, _dp]),
@@ -423,9 +424,11 @@ class Model:
         se = C.c_double()
         tr = np.empty(D) if traces else None
         pp = np.empty(n_probes)
+        its = np.empty(n_probes, dtype=np.int32)
         self._c(self.lib.bfmri_logdet_probe(self.handle, which, n_probes, lanczos_steps, counter,
-                                            C.byref(ld), C.byref(se), _ptr(tr), _ptr(pp)))
-        return dict(logdet=ld.value, stderr=se.value, traces=tr, per_probe=pp)
+                                            C.byref(ld), C.byref(se), _ptr(tr), _ptr(pp),
+                                            its.ctypes.data_as(_P(C.c_int))))
+        return dict(logdet=ld.value, stderr=se.value, traces=tr, per_probe=pp, iterations=its)
 
     def spvb_step(self, n_samples, counter, extrapolate=True):
         avb = np.empty(self.K)

@@ -474,6 +474,7 @@ MrhsArgs mrhs_args(bfmri_handle* h, int D, int S, const double* scale, int max_i
   m.N = h->N;
   m.ld = h->ld;
   m.ndir = h->ndir;
+  m.f32 = 0;
   m.nbr = h->d_nbr;
   m.blocks = h->d_blocks;
   m.mfac = h->opt.precond == BFMRI_PRECOND_BLOCK_JACOBI ? h->d_mfac : nullptr;
@@ -947,7 +948,7 @@ bfmri_status bfmri_reset_timing(bfmri_handle* h) {
 
 bfmri_status bfmri_logdet_probe(bfmri_handle* h, int which, int n_probes, int lanczos_steps,
                                 uint64_t counter, double* logdet, double* std_err,
-                                double* traces, double* per_probe) {
+                                double* traces, double* per_probe, int* iterations) {
   RET(require_stats(h));
   if ((which != 0 && which != 1) || n_probes < 1 || n_probes > 4096 || lanczos_steps < 1)
     return fail(h, BFMRI_ERR_INVALID_ARG, "bad arguments");
@@ -960,10 +961,13 @@ bfmri_status bfmri_logdet_probe(bfmri_handle* h, int which, int n_probes, int la
     CU(h, cudaMemcpyAsync(h->d_bmean, zeros, D * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     scale = h->d_bmean;
   }
+  const bool f32 = h->opt.precision == BFMRI_PREC_MIXED;
   AssembleArgs a = assemble_args(h, scale, 0, which == 0 ? TAG_W : TAG_A);
   a.perturb = 0;
-  a.blocks32 = nullptr;
-  a.mfac32 = nullptr;
+  if (!f32) {
+    a.blocks32 = nullptr;
+    a.mfac32 = nullptr;
+  }
   {
     Timed tm(h, which == 0 ? BFMRI_T_ASSEMBLE_W : BFMRI_T_ASSEMBLE_A);
     cudaError_t e = which == 0 ? launch_assemble_w(a, h->stream) : launch_assemble_a(a, h->stream);
@@ -975,9 +979,11 @@ bfmri_status bfmri_logdet_probe(bfmri_handle* h, int which, int n_probes, int la
   pa.N = h->N;
   pa.ld = h->ld;
   pa.ndir = h->ndir;
+  pa.f32 = f32 ? 1 : 0;
   pa.nbr = h->d_nbr;
   pa.lin = h->d_lin;
-  pa.mfac = pre ? h->d_mfac : nullptr;
+  pa.mfac = nullptr;
+  pa.mfac64 = pre ? h->d_mfac : nullptr;
   pa.S = n_probes;
   pa.vs = h->mr_vs;
   pa.b = h->mr_b;
@@ -986,6 +992,11 @@ bfmri_status bfmri_logdet_probe(bfmri_handle* h, int which, int n_probes, int la
   cudaError_t e = launch_probe(D, pa, 0, nullptr, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "probe rhs");
   MrhsArgs m = mrhs_args(h, D, n_probes, scale, lanczos_steps, true);
+  if (f32) {
+    m.f32 = 1;
+    m.blocks = h->d_blocks32;
+    m.mfac = pre ? h->d_mfac32 : nullptr;
+  }
   {
     Timed tm(h, BFMRI_T_OTHER, true, 0);
     int units = 0;
@@ -995,6 +1006,8 @@ bfmri_status bfmri_logdet_probe(bfmri_handle* h, int which, int n_probes, int la
   RET(end_call(h, nullptr, nullptr));
   std::vector<RhsState> st(n_probes);
   CU(h, cudaMemcpy(st.data(), h->mr_st, n_probes * sizeof(RhsState), cudaMemcpyDeviceToHost));
+  if (iterations)
+    for (int i = 0; i < n_probes; ++i) iterations[i] = st[i].total;
   for (int i = 0; i < n_probes; ++i) {
     if (st[i].status == 4) return fail(h, BFMRI_ERR_NOT_CONVERGED, "probe solve reached lanczos_steps");
     if (st[i].status == 3) return fail(h, BFMRI_ERR_NOT_SPD, "probe solve breakdown");

@@ -18,21 +18,23 @@ namespace {
 
 constexpr int MRHS_THREADS = 256;
 
-__device__ __forceinline__ double ldc(const double* p) { return __ldcg(p); }
+template <typename T>
+__device__ __forceinline__ T ldc(const T* p) { return __ldcg(p); }
 
-template <int D>
-__device__ __forceinline__ void block_apply(const MrhsArgs& a, int n, const double* v, const double* V, double* out) {
+template <int D, typename T>
+__device__ __forceinline__ void block_apply(const MrhsArgs& a, int n, const T* v, const T* V, T* out) {
   const size_t ld = a.ld;
+  const T* B = static_cast<const T*>(a.blocks);
 #pragma unroll
   for (int i = 0; i < D; ++i) {
-    double acc = 0.0;
+    T acc = T(0);
 #pragma unroll
-    for (int j = 0; j < D; ++j) acc += __ldg(a.blocks + (size_t)(i >= j ? tri(i, j) : tri(j, i)) * ld + n) * v[j];
+    for (int j = 0; j < D; ++j) acc += __ldg(B + (size_t)(i >= j ? tri(i, j) : tri(j, i)) * ld + n) * v[j];
     out[i] = acc;
   }
-  double sum[D];
+  T sum[D];
 #pragma unroll
-  for (int k = 0; k < D; ++k) sum[k] = 0.0;
+  for (int k = 0; k < D; ++k) sum[k] = T(0);
   int deg = 0;
   for (int d = 0; d < a.ndir; ++d) {
     const int m = __ldg(a.nbr + (size_t)d * ld + n);
@@ -43,19 +45,20 @@ __device__ __forceinline__ void block_apply(const MrhsArgs& a, int n, const doub
     }
   }
 #pragma unroll
-  for (int k = 0; k < D; ++k) out[k] += __ldg(a.scale + k) * ((double)deg * v[k] - sum[k]);
+  for (int k = 0; k < D; ++k) out[k] += (T)__ldg(a.scale + k) * ((T)deg * v[k] - sum[k]);
 }
 
-template <int D>
-__device__ __forceinline__ void precond_apply(const MrhsArgs& a, int n, const double* r, double* z) {
+template <int D, typename T>
+__device__ __forceinline__ void precond_apply(const MrhsArgs& a, int n, const T* r, T* z) {
   if (a.mfac == nullptr) {
 #pragma unroll
     for (int k = 0; k < D; ++k) z[k] = r[k];
     return;
   }
-  double L[ntri(D)];
+  const T* M = static_cast<const T*>(a.mfac);
+  T L[ntri(D)];
 #pragma unroll
-  for (int e = 0; e < ntri(D); ++e) L[e] = __ldg(a.mfac + (size_t)e * a.ld + n);
+  for (int e = 0; e < ntri(D); ++e) L[e] = __ldg(M + (size_t)e * a.ld + n);
   chol_solve_invdiag<D>(L, r, z);
 }
 
@@ -233,8 +236,15 @@ __device__ __forceinline__ bool mrhs_reduce(const MrhsArgs& a, const Units& U, i
 
 }  // namespace
 
-template <int D>
+template <int D, typename T>
 __global__ void __launch_bounds__(MRHS_THREADS) k_mrhs(MrhsArgs a) {
+  const T* Bv = static_cast<const T*>(a.b);
+  T* Xv = static_cast<T*>(a.x);
+  T* Rv = static_cast<T*>(a.r);
+  T* UUv = static_cast<T*>(a.u);
+  T* WWv = static_cast<T*>(a.w);
+  T* PPv = static_cast<T*>(a.p);
+  T* SSv = static_cast<T*>(a.s);
   __shared__ int sh_int[4];
   __shared__ int sh_flag;
   const Units U = units_of(a);
@@ -252,24 +262,24 @@ __global__ void __launch_bounds__(MRHS_THREADS) k_mrhs(MrhsArgs a) {
       const int r = unit_rhs(u), c = unit_chunk(u);
       const int act = first ? 1 : __ldcg(&a.st[r].active);
       if (!first && act != 2) continue;
-      const double* b = a.b + (size_t)r * a.vs;
-      double *x = a.x + (size_t)r * a.vs, *R = a.r + (size_t)r * a.vs, *Uu = a.u + (size_t)r * a.vs;
-      double *P = a.p + (size_t)r * a.vs, *Sv = a.s + (size_t)r * a.vs;
+      const T* b = Bv + (size_t)r * a.vs;
+      T *x = Xv + (size_t)r * a.vs, *R = Rv + (size_t)r * a.vs, *Uu = UUv + (size_t)r * a.vs;
+      T *P = PPv + (size_t)r * a.vs, *Sv = SSv + (size_t)r * a.vs;
       const int n1 = min(a.N, (c + 1) * U.csize);
       for (int n = c * U.csize + U.lane; n < n1; n += 32) {
-        double xn[D], ax[D], rn[D], un[D];
+        T xn[D], ax[D], rn[D], un[D];
 #pragma unroll
         for (int k = 0; k < D; ++k) xn[k] = ldc(x + (size_t)k * ld + n);
-        block_apply<D>(a, n, xn, x, ax);
+        block_apply<D, T>(a, n, xn, x, ax);
 #pragma unroll
         for (int k = 0; k < D; ++k) rn[k] = __ldg(b + (size_t)k * ld + n) - ax[k];
-        precond_apply<D>(a, n, rn, un);
+        precond_apply<D, T>(a, n, rn, un);
 #pragma unroll
         for (int k = 0; k < D; ++k) {
           R[(size_t)k * ld + n] = rn[k];
           Uu[(size_t)k * ld + n] = un[k];
-          P[(size_t)k * ld + n] = 0.0;
-          Sv[(size_t)k * ld + n] = 0.0;
+          P[(size_t)k * ld + n] = T(0);
+          Sv[(size_t)k * ld + n] = T(0);
         }
       }
     }
@@ -279,25 +289,30 @@ __global__ void __launch_bounds__(MRHS_THREADS) k_mrhs(MrhsArgs a) {
       const int act = first ? 1 : __ldcg(&a.st[r].active);
       double acc[4] = {0.0, 0.0, 0.0, 0.0};
       if (first || act == 2) {
-        const double* b = a.b + (size_t)r * a.vs;
-        const double* R = a.r + (size_t)r * a.vs;
-        const double* Uu = a.u + (size_t)r * a.vs;
-        double* Wv = a.w + (size_t)r * a.vs;
+        const T* b = Bv + (size_t)r * a.vs;
+        const T* R = Rv + (size_t)r * a.vs;
+        const T* Uu = UUv + (size_t)r * a.vs;
+        T* Wv = WWv + (size_t)r * a.vs;
         const int n1 = min(a.N, (c + 1) * U.csize);
         for (int n = c * U.csize + U.lane; n < n1; n += 32) {
-          double un[D], wn[D];
+          T un[D], wn[D];
 #pragma unroll
           for (int k = 0; k < D; ++k) un[k] = Uu[(size_t)k * ld + n];
-          block_apply<D>(a, n, un, Uu, wn);
+          block_apply<D, T>(a, n, un, Uu, wn);
+          T g = T(0), dl = T(0), rr2 = T(0), b2 = T(0);
 #pragma unroll
           for (int k = 0; k < D; ++k) {
-            const double rk = R[(size_t)k * ld + n], bk = __ldg(b + (size_t)k * ld + n);
+            const T rk = R[(size_t)k * ld + n], bk = __ldg(b + (size_t)k * ld + n);
             Wv[(size_t)k * ld + n] = wn[k];
-            acc[0] += rk * un[k];
-            acc[1] += wn[k] * un[k];
-            acc[2] += rk * rk;
-            acc[3] += bk * bk;
+            g += rk * un[k];
+            dl += wn[k] * un[k];
+            rr2 += rk * rk;
+            b2 += bk * bk;
           }
+          acc[0] += (double)g;
+          acc[1] += (double)dl;
+          acc[2] += (double)rr2;
+          acc[3] += (double)b2;
         }
       }
       write_partials(u, acc);
@@ -314,25 +329,25 @@ __global__ void __launch_bounds__(MRHS_THREADS) k_mrhs(MrhsArgs a) {
       for (int u = U.gw; u < U.units; u += U.nw) {
         const int r = unit_rhs(u), c = unit_chunk(u);
         if (__ldcg(&a.st[r].active) != 1) continue;
-        const double al = __ldcg(&a.st[r].alpha), be = __ldcg(&a.st[r].beta);
-        double *x = a.x + (size_t)r * a.vs, *R = a.r + (size_t)r * a.vs, *Uu = a.u + (size_t)r * a.vs;
-        double *P = a.p + (size_t)r * a.vs, *Sv = a.s + (size_t)r * a.vs;
-        const double* Wv = a.w + (size_t)r * a.vs;
+        const T al = (T)__ldcg(&a.st[r].alpha), be = (T)__ldcg(&a.st[r].beta);
+        T *x = Xv + (size_t)r * a.vs, *R = Rv + (size_t)r * a.vs, *Uu = UUv + (size_t)r * a.vs;
+        T *P = PPv + (size_t)r * a.vs, *Sv = SSv + (size_t)r * a.vs;
+        const T* Wv = WWv + (size_t)r * a.vs;
         const int n1 = min(a.N, (c + 1) * U.csize);
         for (int n = c * U.csize + U.lane; n < n1; n += 32) {
-          double rn[D], un[D];
+          T rn[D], un[D];
 #pragma unroll
           for (int k = 0; k < D; ++k) {
             const size_t o = (size_t)k * ld + n;
-            const double pk = Uu[o] + be * P[o];
-            const double sk = Wv[o] + be * Sv[o];
+            const T pk = Uu[o] + be * P[o];
+            const T sk = Wv[o] + be * Sv[o];
             P[o] = pk;
             Sv[o] = sk;
             x[o] += al * pk;
             rn[k] = R[o] - al * sk;
             R[o] = rn[k];
           }
-          precond_apply<D>(a, n, rn, un);
+          precond_apply<D, T>(a, n, rn, un);
 #pragma unroll
           for (int k = 0; k < D; ++k) Uu[(size_t)k * ld + n] = un[k];
         }
@@ -342,23 +357,27 @@ __global__ void __launch_bounds__(MRHS_THREADS) k_mrhs(MrhsArgs a) {
         const int r = unit_rhs(u), c = unit_chunk(u);
         double acc[4] = {0.0, 0.0, 0.0, 0.0};
         if (__ldcg(&a.st[r].active) == 1) {
-          const double* R = a.r + (size_t)r * a.vs;
-          const double* Uu = a.u + (size_t)r * a.vs;
-          double* Wv = a.w + (size_t)r * a.vs;
+          const T* R = Rv + (size_t)r * a.vs;
+          const T* Uu = UUv + (size_t)r * a.vs;
+          T* Wv = WWv + (size_t)r * a.vs;
           const int n1 = min(a.N, (c + 1) * U.csize);
           for (int n = c * U.csize + U.lane; n < n1; n += 32) {
-            double un[D], wn[D];
+            T un[D], wn[D];
 #pragma unroll
             for (int k = 0; k < D; ++k) un[k] = Uu[(size_t)k * ld + n];
-            block_apply<D>(a, n, un, Uu, wn);
+            block_apply<D, T>(a, n, un, Uu, wn);
+            T g = T(0), dl = T(0), rr2 = T(0);
 #pragma unroll
             for (int k = 0; k < D; ++k) {
-              const double rk = R[(size_t)k * ld + n];
+              const T rk = R[(size_t)k * ld + n];
               Wv[(size_t)k * ld + n] = wn[k];
-              acc[0] += rk * un[k];
-              acc[1] += wn[k] * un[k];
-              acc[2] += rk * rk;
+              g += rk * un[k];
+              dl += wn[k] * un[k];
+              rr2 += rk * rk;
             }
+            acc[0] += (double)g;
+            acc[1] += (double)dl;
+            acc[2] += (double)rr2;
           }
         }
         write_partials(u, acc);
@@ -378,7 +397,8 @@ static cudaError_t launch_d(const MrhsArgs& a, cudaStream_t stream, int* units_o
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   if (a.sm_cap > 0 && a.sm_cap < nsm) nsm = a.sm_cap;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mrhs<D>, MRHS_THREADS, 0);
+  const void* kern = a.f32 ? (const void*)k_mrhs<D, float> : (const void*)k_mrhs<D, double>;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, MRHS_THREADS, 0);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   // enough warps for every RHS and for a chunk of at least 32 voxels per warp
@@ -391,7 +411,7 @@ static cudaError_t launch_d(const MrhsArgs& a, cudaStream_t stream, int* units_o
   if (chunks < 1) chunks = 1;
   if (units_out) *units_out = a.S * chunks;
   void* args[] = {(void*)&a};
-  return cudaLaunchCooperativeKernel((const void*)k_mrhs<D>, dim3((unsigned)grid), dim3(MRHS_THREADS), args, 0, stream);
+  return cudaLaunchCooperativeKernel(kern, dim3((unsigned)grid), dim3(MRHS_THREADS), args, 0, stream);
 }
 
 template <int D>
@@ -399,7 +419,7 @@ static int max_units_d(int S) {
   int dev = 0, nsm = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mrhs<D>, MRHS_THREADS, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mrhs<D, double>, MRHS_THREADS, 0);
   const int nw = nsm * (per_sm > 0 ? per_sm : 1) * (MRHS_THREADS / 32);
   const int chunks = nw / S > 0 ? nw / S : 1;
   return S * chunks;
@@ -433,7 +453,7 @@ int mrhs_max_units(int D, int S) {
 namespace bfmri {
 
 // b_i = L v_i (v_i Rademacher, site lattice-linear * 4 + 3, stream i), x_i = 0.
-template <int D>
+template <int D, typename T>
 __global__ void k_probe_rhs(ProbeArgs a) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   const int i = blockIdx.y;
@@ -442,19 +462,21 @@ __global__ void k_probe_rhs(ProbeArgs a) {
   g.c3 = (a.rng.c3 & 0xFF000000u) | ((uint32_t)i & 0xFFFFFFu);
   double v[D], bv[D];
   site_rademacher<D>(g, (uint32_t)a.lin[n] * 4u + 3u, v);
-  if (a.mfac) {
+  if (a.mfac64) {
     double L[ntri(D)];
 #pragma unroll
-    for (int e = 0; e < ntri(D); ++e) L[e] = a.mfac[(size_t)e * a.ld + n];
+    for (int e = 0; e < ntri(D); ++e) L[e] = a.mfac64[(size_t)e * a.ld + n];
     lower_mul_invdiag<D>(L, v, bv);
   } else {
 #pragma unroll
     for (int k = 0; k < D; ++k) bv[k] = v[k];
   }
+  T* b = static_cast<T*>(a.b);
+  T* x = static_cast<T*>(a.x);
 #pragma unroll
   for (int k = 0; k < D; ++k) {
-    a.b[(size_t)i * a.vs + (size_t)k * a.ld + n] = bv[k];
-    a.x[(size_t)i * a.vs + (size_t)k * a.ld + n] = 0.0;
+    b[(size_t)i * a.vs + (size_t)k * a.ld + n] = (T)bv[k];
+    x[(size_t)i * a.vs + (size_t)k * a.ld + n] = T(0);
   }
 }
 
@@ -465,14 +487,14 @@ __global__ void k_logdet_m(ProbeArgs a, double* out) {
   if (n >= a.N) return;
   double s = 0.0;
 #pragma unroll
-  for (int k = 0; k < D; ++k) s -= 2.0 * log(a.mfac[(size_t)tri(k, k) * a.ld + n]);
+  for (int k = 0; k < D; ++k) s -= 2.0 * log(a.mfac64[(size_t)tri(k, k) * a.ld + n]);
   out[n] = s;
 }
 
 // Trace terms t_{i,k} = sum_n (L^-T v_i)_{n,k} (D_w y_{i,k})_n with y_i = B~^-1 L v_i, whose
 // mean over probes estimates tr(D_w^(k) B~^-1) (cyclic invariance: E[L^-T v v' L'] = I).
 // Per-CTA partials [grid.x][S][D] in a fixed order.
-template <int D>
+template <int D, typename T>
 __global__ void k_probe_traces(ProbeArgs a, double* part) {
   __shared__ double sh[128][D];
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
@@ -485,10 +507,10 @@ __global__ void k_probe_traces(ProbeArgs a, double* part) {
     g.c3 = (a.rng.c3 & 0xFF000000u) | ((uint32_t)i & 0xFFFFFFu);
     double v[D], t[D];
     site_rademacher<D>(g, (uint32_t)a.lin[n] * 4u + 3u, v);
-    if (a.mfac) {
+    if (a.mfac64) {
       double L[ntri(D)];
 #pragma unroll
-      for (int e = 0; e < ntri(D); ++e) L[e] = a.mfac[(size_t)e * a.ld + n];
+      for (int e = 0; e < ntri(D); ++e) L[e] = a.mfac64[(size_t)e * a.ld + n];
       // solve L' t = v (L lower, inverted diagonal)
 #pragma unroll
       for (int r = D - 1; r >= 0; --r) {
@@ -501,11 +523,11 @@ __global__ void k_probe_traces(ProbeArgs a, double* part) {
 #pragma unroll
       for (int k = 0; k < D; ++k) t[k] = v[k];
     }
-    const double* y = a.x + (size_t)i * a.vs;
+    const T* y = static_cast<const T*>(a.x) + (size_t)i * a.vs;
     double yn[D], sum[D];
 #pragma unroll
     for (int k = 0; k < D; ++k) {
-      yn[k] = y[(size_t)k * a.ld + n];
+      yn[k] = (double)y[(size_t)k * a.ld + n];
       sum[k] = 0.0;
     }
     int deg = 0;
@@ -514,7 +536,7 @@ __global__ void k_probe_traces(ProbeArgs a, double* part) {
       if (m >= 0) {
         ++deg;
 #pragma unroll
-        for (int k = 0; k < D; ++k) sum[k] += y[(size_t)k * a.ld + m];
+        for (int k = 0; k < D; ++k) sum[k] += (double)y[(size_t)k * a.ld + m];
       }
     }
 #pragma unroll
@@ -536,9 +558,15 @@ __global__ void k_probe_traces(ProbeArgs a, double* part) {
 template <int D>
 static cudaError_t probe_launch_d(const ProbeArgs& a, int what, double* out, cudaStream_t s) {
   const dim3 grid((a.N + 127) / 128, a.S);
-  if (what == 0) k_probe_rhs<D><<<grid, 128, 0, s>>>(a);
-  else if (what == 1) k_logdet_m<D><<<(a.N + 127) / 128, 128, 0, s>>>(a, out);
-  else k_probe_traces<D><<<grid, 128, 0, s>>>(a, out);
+  if (what == 0) {
+    if (a.f32) k_probe_rhs<D, float><<<grid, 128, 0, s>>>(a);
+    else k_probe_rhs<D, double><<<grid, 128, 0, s>>>(a);
+  } else if (what == 1) {
+    k_logdet_m<D><<<(a.N + 127) / 128, 128, 0, s>>>(a, out);
+  } else {
+    if (a.f32) k_probe_traces<D, float><<<grid, 128, 0, s>>>(a, out);
+    else k_probe_traces<D, double><<<grid, 128, 0, s>>>(a, out);
+  }
   return cudaGetLastError();
 }
 

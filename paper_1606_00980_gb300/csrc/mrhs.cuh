@@ -25,23 +25,26 @@ struct RhsState {
   int status;      // 0 ok, 3 breakdown, 4 max_iter, 7 non-finite
 };
 
+// Vector and operator arrays hold FP64 (f32 = 0) or FP32 (f32 = 1) elements; CG scalars,
+// inner-product sums across threads and the stop test are FP64 in both cases.
 struct MrhsArgs {
   int N;
   size_t ld;
   int ndir;
+  int f32;
   const int* nbr;        // [6][ld]
-  const double* blocks;  // [ntri(D)][ld]
-  const double* mfac;    // [ntri(D)][ld] block-Jacobi factor (inverted diag) or null
+  const void* blocks;    // [ntri(D)][ld]
+  const void* mfac;      // [ntri(D)][ld] block-Jacobi factor (inverted diag) or null
   const double* scale;   // [D]
   int S;                 // number of right-hand sides
-  size_t vs;             // stride between RHS (>= D * ld)
-  const double* b;       // [S] x [D][ld]
-  double* x;             // [S] x [D][ld]: start values in, solutions out
-  double* r;             // [S] x [D][ld] work
-  double* u;
-  double* w;
-  double* p;
-  double* s;
+  size_t vs;             // stride between RHS (>= D * ld), in elements
+  const void* b;         // [S] x [D][ld]
+  void* x;               // [S] x [D][ld]: start values in, solutions out
+  void* r;               // [S] x [D][ld] work
+  void* u;
+  void* w;
+  void* p;
+  void* s;
   double* part;          // [units][4]
   RhsState* st;          // [S]
   double* hist;          // [hist_len][S][2] CG (alpha, beta) of the first run, or null
@@ -59,13 +62,15 @@ struct ProbeArgs {
   int N;
   size_t ld;
   int ndir;
+  int f32;              // b, x (and mfac for the right-hand sides) are FP32
   const int* nbr;
   const int* lin;
-  const double* mfac;   // block-Jacobi factor (inverted diagonal), or null
+  const void* mfac;     // block-Jacobi factor (inverted diagonal), or null
+  const double* mfac64; // FP64 factor for log det M
   int S;
   size_t vs;
-  double* b;            // [S][D][ld]
-  double* x;            // [S][D][ld]
+  void* b;              // [S][D][ld]
+  void* x;              // [S][D][ld]
   Rng rng;              // tag in c3's top byte; the probe index is the stream
 };
 // what: 0 = probe right-hand sides b_i = L v_i and x_i = 0; 1 = per-voxel log det of the

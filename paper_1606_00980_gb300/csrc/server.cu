@@ -40,6 +40,28 @@ struct Job {
 
 size_t ceil32(size_t n) { return (n + 31) & ~size_t(31); }
 
+// Stream-ordered allocation from the server's pool: neither allocation nor release
+// synchronises the device, so one slot's set-up does not stall the other slots' kernels.
+struct SlotAlloc {
+  cudaStream_t stream = nullptr;
+  cudaMemPool_t pool = nullptr;
+};
+
+void* pool_alloc(size_t bytes, void* ctx) {
+  SlotAlloc* c = static_cast<SlotAlloc*>(ctx);
+  void* p = nullptr;
+  if (cudaMallocFromPoolAsync(&p, bytes, c->pool, c->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return p;
+}
+
+void pool_free(void* p, void* ctx) {
+  SlotAlloc* c = static_cast<SlotAlloc*>(ctx);
+  cudaFreeAsync(p, c->stream);
+}
+
 }  // namespace
 
 struct bfmri_server {
@@ -55,6 +77,8 @@ struct bfmri_server {
   std::vector<Job*> slot_job;
   std::vector<std::thread> workers;
   std::vector<cudaStream_t> streams;
+  std::vector<SlotAlloc> alloc;
+  cudaMemPool_t pool = nullptr;
   size_t in_use = 0, peak_in_use = 0;
   long long next_ticket = 1;
   bool stop = false;
@@ -95,6 +119,9 @@ struct bfmri_server {
       bfmri_options o = j->req.opt;
       o.cuda_stream = streams[slot];
       o.sm_budget = sm_budget;
+      o.dev_alloc = pool_alloc;
+      o.dev_free = pool_free;
+      o.alloc_ctx = &alloc[slot];
       bfmri_handle* h = nullptr;
       bfmri_status st = bfmri_create(&j->req.lat, j->req.mask, j->req.X, j->req.Y, j->req.y_dtype,
                                      j->req.T, j->req.K, j->req.P, &o, &h);
@@ -159,6 +186,24 @@ bfmri_status bfmri_server_create(size_t budget_bytes, int max_slots, int sm_budg
       bfmri::set_global_error("bfmri_server_create: stream creation failed");
       return BFMRI_ERR_CUDA;
     }
+  }
+  cudaMemPoolProps props;
+  memset(&props, 0, sizeof(props));
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = s->device;
+  if (cudaMemPoolCreate(&s->pool, &props) != cudaSuccess) {
+    for (int k = 0; k < max_slots; ++k) cudaStreamDestroy(s->streams[k]);
+    delete s;
+    bfmri::set_global_error("bfmri_server_create: memory pool creation failed");
+    return BFMRI_ERR_CUDA;
+  }
+  uint64_t keep = budget_bytes;   // keep released memory cached up to the budget
+  cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  s->alloc.resize(max_slots);
+  for (int i = 0; i < max_slots; ++i) {
+    s->alloc[i].stream = s->streams[i];
+    s->alloc[i].pool = s->pool;
   }
   for (int i = 0; i < max_slots; ++i) s->workers.emplace_back([s, i] { s->run(i); });
   *out = s;
@@ -228,7 +273,11 @@ bfmri_status bfmri_server_destroy(bfmri_server* s) {
   }
   s->cv_work.notify_all();
   for (auto& t : s->workers) t.join();
-  for (cudaStream_t st : s->streams) cudaStreamDestroy(st);
+  for (cudaStream_t st : s->streams) {
+    cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+  }
+  if (s->pool) cudaMemPoolDestroy(s->pool);
   for (auto& kv : s->jobs) delete kv.second;
   delete s;
   return BFMRI_OK;

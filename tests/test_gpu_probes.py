@@ -38,8 +38,10 @@ CASES = {
 
 @pytest.mark.parametrize("name", sorted(CASES))
 @pytest.mark.parametrize("which", [0, 1])
-@pytest.mark.parametrize("variant", ["pcg", "nopre"])
+@pytest.mark.parametrize("variant", ["pcg", "nopre", "fp32"])
 def test_logdet_probe_matches_oracle(name, which, variant):
+    """fp32: the mixed-precision handle runs the probe solves in FP32 to delta 1e-5; the
+    per-probe quadrature then agrees with the exact value to 1e-4 and the traces to 1e-3."""
     from paper_1606_00980_gb300 import bfmri
     w = CASES[name]()
     lat = Lattice(w.mask, w.neighbourhood)
@@ -47,7 +49,9 @@ def test_logdet_probe_matches_oracle(name, which, variant):
     s = dict(W=w.W_true + 0.1 * rng.standard_normal(w.W_true.shape), A=w.A_true,
              lam=rng.uniform(0.5, 2.0, w.N), alpha=rng.uniform(0.3, 3.0, w.K),
              beta=rng.uniform(2.0, 9.0, w.P))
-    m = make(w, s, precond=bfmri.PRECOND_BLOCK_JACOBI if variant == "pcg" else bfmri.PRECOND_NONE)
+    extra = dict(precision=bfmri.PREC_MIXED, delta=1e-5) if variant == "fp32" else {}
+    m = make(w, s, precond=bfmri.PRECOND_NONE if variant == "nopre" else bfmri.PRECOND_BLOCK_JACOBI,
+             **extra)
     n_probes = 12
     res = m.logdet_probe(which, n_probes, 2000, counter=6)
     D = w.K if which == 0 else w.P
@@ -72,8 +76,10 @@ def test_logdet_probe_matches_oracle(name, which, variant):
     else:
         ldm, quad, tr, ldb = probes.exact_probe_terms(lat, Bd, scale, V)
     got = res["per_probe"]
-    assert np.max(np.abs(got - quad) / np.abs(quad)) <= 1e-6
-    assert abs(res["logdet"] - (ldm + quad.mean())) <= 1e-6 * abs(ldm + quad.mean()) + 1e-6
-    assert np.allclose(res["traces"], tr.mean(axis=0), rtol=1e-8, atol=1e-10)
+    tq, tt = (1e-4, 1e-3) if variant == "fp32" else (1e-6, 1e-8)
+    assert np.max(np.abs(got - quad) / np.abs(quad)) <= tq
+    assert abs(res["logdet"] - (ldm + quad.mean())) <= tq * abs(ldm + quad.mean()) + 1e-6
+    assert np.allclose(res["traces"], tr.mean(axis=0), rtol=tt, atol=tt * np.abs(tr).mean())
+    assert np.all(res["iterations"] > 0)
     assert abs(res["logdet"] - ldb) <= 5 * max(res["stderr"], 1e-9) + 1e-6 * abs(ldb)
     m.close()
