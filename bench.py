@@ -366,7 +366,7 @@ def run_batched(args):
     m = Model.from_workload(w, delta=1e-5, precision=bfmri.PREC_MIXED, seed=4242, profile=1)
     m.precompute_stats()
     m.gibbs_sweep(3, 0)
-    S = 64
+    S = args.probes
     m.logdet_probe(0, S, 3000, counter=1)            # warm-up (workspace allocation)
     m.reset_timing()
     torch.cuda.synchronize()
@@ -493,6 +493,9 @@ def main():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--probes", type=int, default=64)
+    ap.add_argument("--only-batched", action="store_true",
+                    help="run only the batched-probe measurement (profiling entry point)")
     ap.add_argument("--serving-requests", type=int, default=96)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
@@ -500,6 +503,9 @@ def main():
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, world, rank)
+    elif args.only_batched:
+        if rank == 0:
+            print(json.dumps(run_batched(args)), flush=True)
     else:
         run_ours(args, world, rank, local)
     if world > 1:

@@ -22,7 +22,7 @@ template <typename T>
 __device__ __forceinline__ T ldc(const T* p) { return __ldcg(p); }
 
 template <int D, typename T>
-__device__ __forceinline__ void block_apply(const MrhsArgs& a, int n, const T* v, const T* V, T* out) {
+__device__ __forceinline__ void block_apply(const MrhsArgs& a, const T* sc, int n, const T* v, const T* V, T* out) {
   const size_t ld = a.ld;
   const T* B = static_cast<const T*>(a.blocks);
 #pragma unroll
@@ -45,8 +45,23 @@ __device__ __forceinline__ void block_apply(const MrhsArgs& a, int n, const T* v
     }
   }
 #pragma unroll
-  for (int k = 0; k < D; ++k) out[k] += (T)__ldg(a.scale + k) * ((T)deg * v[k] - sum[k]);
+  for (int k = 0; k < D; ++k) out[k] += sc[k] * ((T)deg * v[k] - sum[k]);
 }
+
+// Compensated (Kahan) accumulation in the storage type: per-thread partial sums stay
+// accurate without a per-voxel FP64 operation (FP64 issue is scarce on this part); each
+// work unit converts its sums to FP64 once.
+template <typename T>
+struct KSum {
+  T s = T(0), c = T(0);
+  __device__ __forceinline__ void add(T v) {
+    const T y = v - c;
+    const T t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
 
 template <int D, typename T>
 __device__ __forceinline__ void precond_apply(const MrhsArgs& a, int n, const T* r, T* z) {
@@ -237,7 +252,10 @@ __device__ __forceinline__ bool mrhs_reduce(const MrhsArgs& a, const Units& U, i
 }  // namespace
 
 template <int D, typename T>
-__global__ void __launch_bounds__(MRHS_THREADS) k_mrhs(MrhsArgs a) {
+__global__ void __launch_bounds__(MRHS_THREADS, 2) k_mrhs(MrhsArgs a) {
+  T sc[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) sc[k] = (T)__ldg(a.scale + k);
   const T* Bv = static_cast<const T*>(a.b);
   T* Xv = static_cast<T*>(a.x);
   T* Rv = static_cast<T*>(a.r);
@@ -270,7 +288,7 @@ __global__ void __launch_bounds__(MRHS_THREADS) k_mrhs(MrhsArgs a) {
         T xn[D], ax[D], rn[D], un[D];
 #pragma unroll
         for (int k = 0; k < D; ++k) xn[k] = ldc(x + (size_t)k * ld + n);
-        block_apply<D, T>(a, n, xn, x, ax);
+        block_apply<D, T>(a, sc, n, xn, x, ax);
 #pragma unroll
         for (int k = 0; k < D; ++k) rn[k] = __ldg(b + (size_t)k * ld + n) - ax[k];
         precond_apply<D, T>(a, n, rn, un);
@@ -287,7 +305,7 @@ __global__ void __launch_bounds__(MRHS_THREADS) k_mrhs(MrhsArgs a) {
     for (int u = U.gw; u < U.units; u += U.nw) {
       const int r = unit_rhs(u), c = unit_chunk(u);
       const int act = first ? 1 : __ldcg(&a.st[r].active);
-      double acc[4] = {0.0, 0.0, 0.0, 0.0};
+      KSum<T> ks[4];
       if (first || act == 2) {
         const T* b = Bv + (size_t)r * a.vs;
         const T* R = Rv + (size_t)r * a.vs;
@@ -298,7 +316,7 @@ __global__ void __launch_bounds__(MRHS_THREADS) k_mrhs(MrhsArgs a) {
           T un[D], wn[D];
 #pragma unroll
           for (int k = 0; k < D; ++k) un[k] = Uu[(size_t)k * ld + n];
-          block_apply<D, T>(a, n, un, Uu, wn);
+          block_apply<D, T>(a, sc, n, un, Uu, wn);
           T g = T(0), dl = T(0), rr2 = T(0), b2 = T(0);
 #pragma unroll
           for (int k = 0; k < D; ++k) {
@@ -309,12 +327,13 @@ __global__ void __launch_bounds__(MRHS_THREADS) k_mrhs(MrhsArgs a) {
             rr2 += rk * rk;
             b2 += bk * bk;
           }
-          acc[0] += (double)g;
-          acc[1] += (double)dl;
-          acc[2] += (double)rr2;
-          acc[3] += (double)b2;
+          ks[0].add(g);
+          ks[1].add(dl);
+          ks[2].add(rr2);
+          ks[3].add(b2);
         }
       }
+      double acc[4] = {ks[0].value(), ks[1].value(), ks[2].value(), ks[3].value()};
       write_partials(u, acc);
     }
     return true;
@@ -355,7 +374,7 @@ __global__ void __launch_bounds__(MRHS_THREADS) k_mrhs(MrhsArgs a) {
       if (!grid_sync(a.bar, &sh_flag)) return;
       for (int u = U.gw; u < U.units; u += U.nw) {
         const int r = unit_rhs(u), c = unit_chunk(u);
-        double acc[4] = {0.0, 0.0, 0.0, 0.0};
+        KSum<T> ks[3];
         if (__ldcg(&a.st[r].active) == 1) {
           const T* R = Rv + (size_t)r * a.vs;
           const T* Uu = UUv + (size_t)r * a.vs;
@@ -365,7 +384,7 @@ __global__ void __launch_bounds__(MRHS_THREADS) k_mrhs(MrhsArgs a) {
             T un[D], wn[D];
 #pragma unroll
             for (int k = 0; k < D; ++k) un[k] = Uu[(size_t)k * ld + n];
-            block_apply<D, T>(a, n, un, Uu, wn);
+            block_apply<D, T>(a, sc, n, un, Uu, wn);
             T g = T(0), dl = T(0), rr2 = T(0);
 #pragma unroll
             for (int k = 0; k < D; ++k) {
@@ -375,11 +394,12 @@ __global__ void __launch_bounds__(MRHS_THREADS) k_mrhs(MrhsArgs a) {
               dl += wn[k] * un[k];
               rr2 += rk * rk;
             }
-            acc[0] += (double)g;
-            acc[1] += (double)dl;
-            acc[2] += (double)rr2;
+            ks[0].add(g);
+            ks[1].add(dl);
+            ks[2].add(rr2);
           }
         }
+        double acc[4] = {ks[0].value(), ks[1].value(), ks[2].value(), 0.0};
         write_partials(u, acc);
       }
       if (!mrhs_reduce(a, U, 1, false, sh_int, &any_active, &any_pending)) return;
