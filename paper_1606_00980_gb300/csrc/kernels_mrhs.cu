@@ -313,20 +313,24 @@ __global__ void __launch_bounds__(MRHS_THREADS, 2) k_mrhs(MrhsArgs a) {
         T* Wv = WWv + (size_t)r * a.vs;
         const int n1 = min(a.N, (c + 1) * U.csize);
         for (int n = c * U.csize + U.lane; n < n1; n += 32) {
-          T un[D], wn[D];
+          T un[D], wn[D], rk[D], bk[D];
 #pragma unroll
-          for (int k = 0; k < D; ++k) un[k] = Uu[(size_t)k * ld + n];
+          for (int k = 0; k < D; ++k) {
+            un[k] = Uu[(size_t)k * ld + n];
+            rk[k] = R[(size_t)k * ld + n];
+            bk[k] = __ldg(b + (size_t)k * ld + n);
+          }
           block_apply<D, T>(a, sc, n, un, Uu, wn);
           T g = T(0), dl = T(0), rr2 = T(0), b2 = T(0);
 #pragma unroll
           for (int k = 0; k < D; ++k) {
-            const T rk = R[(size_t)k * ld + n], bk = __ldg(b + (size_t)k * ld + n);
-            Wv[(size_t)k * ld + n] = wn[k];
-            g += rk * un[k];
+            g += rk[k] * un[k];
             dl += wn[k] * un[k];
-            rr2 += rk * rk;
-            b2 += bk * bk;
+            rr2 += rk[k] * rk[k];
+            b2 += bk[k] * bk[k];
           }
+#pragma unroll
+          for (int k = 0; k < D; ++k) Wv[(size_t)k * ld + n] = wn[k];
           ks[0].add(g);
           ks[1].add(dl);
           ks[2].add(rr2);
@@ -354,21 +358,36 @@ __global__ void __launch_bounds__(MRHS_THREADS, 2) k_mrhs(MrhsArgs a) {
         const T* Wv = WWv + (size_t)r * a.vs;
         const int n1 = min(a.N, (c + 1) * U.csize);
         for (int n = c * U.csize + U.lane; n < n1; n += 32) {
-          T rn[D], un[D];
+          // all loads first: the six vectors are distinct arrays, but the compiler cannot
+          // prove it, and interleaved stores would serialise the loads
+          T rn[D], un[D], pk[D], sk[D], xk[D], wk[D];
 #pragma unroll
           for (int k = 0; k < D; ++k) {
             const size_t o = (size_t)k * ld + n;
-            const T pk = Uu[o] + be * P[o];
-            const T sk = Wv[o] + be * Sv[o];
-            P[o] = pk;
-            Sv[o] = sk;
-            x[o] += al * pk;
-            rn[k] = R[o] - al * sk;
-            R[o] = rn[k];
+            un[k] = Uu[o];
+            pk[k] = P[o];
+            wk[k] = Wv[o];
+            sk[k] = Sv[o];
+            xk[k] = x[o];
+            rn[k] = R[o];
+          }
+#pragma unroll
+          for (int k = 0; k < D; ++k) {
+            pk[k] = un[k] + be * pk[k];
+            sk[k] = wk[k] + be * sk[k];
+            xk[k] += al * pk[k];
+            rn[k] -= al * sk[k];
           }
           precond_apply<D, T>(a, n, rn, un);
 #pragma unroll
-          for (int k = 0; k < D; ++k) Uu[(size_t)k * ld + n] = un[k];
+          for (int k = 0; k < D; ++k) {
+            const size_t o = (size_t)k * ld + n;
+            P[o] = pk[k];
+            Sv[o] = sk[k];
+            x[o] = xk[k];
+            R[o] = rn[k];
+            Uu[o] = un[k];
+          }
         }
       }
       if (!grid_sync(a.bar, &sh_flag)) return;
@@ -381,19 +400,22 @@ __global__ void __launch_bounds__(MRHS_THREADS, 2) k_mrhs(MrhsArgs a) {
           T* Wv = WWv + (size_t)r * a.vs;
           const int n1 = min(a.N, (c + 1) * U.csize);
           for (int n = c * U.csize + U.lane; n < n1; n += 32) {
-            T un[D], wn[D];
+            T un[D], wn[D], rk[D];
 #pragma unroll
-            for (int k = 0; k < D; ++k) un[k] = Uu[(size_t)k * ld + n];
+            for (int k = 0; k < D; ++k) {
+              un[k] = Uu[(size_t)k * ld + n];
+              rk[k] = R[(size_t)k * ld + n];
+            }
             block_apply<D, T>(a, sc, n, un, Uu, wn);
             T g = T(0), dl = T(0), rr2 = T(0);
 #pragma unroll
             for (int k = 0; k < D; ++k) {
-              const T rk = R[(size_t)k * ld + n];
-              Wv[(size_t)k * ld + n] = wn[k];
-              g += rk * un[k];
+              g += rk[k] * un[k];
               dl += wn[k] * un[k];
-              rr2 += rk * rk;
+              rr2 += rk[k] * rk[k];
             }
+#pragma unroll
+            for (int k = 0; k < D; ++k) Wv[(size_t)k * ld + n] = wn[k];
             ks[0].add(g);
             ks[1].add(dl);
             ks[2].add(rr2);

@@ -372,39 +372,56 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_stream(PcgArgs a) {
   if (!done && !(del > 0.0)) { status = 3; done = true; }
   while (!done) {
     for (int n = tid; n < a.N; n += nth) {
-      double rn[D], un[D];
+      // all loads first (the compiler cannot prove the vectors distinct)
+      double rn[D], un[D], pk[D], sk[D], xk[D], wk[D];
 #pragma unroll
       for (int k = 0; k < D; ++k) {
         const size_t o = (size_t)k * ld + n;
-        const double pk = U[o] + beta * Pv[o];
-        const double sk = Wv[o] + beta * Sv[o];
-        Pv[o] = pk;
-        Sv[o] = sk;
-        a.x[o] += alpha * pk;
-        rn[k] = R[o] - alpha * sk;
-        R[o] = rn[k];
+        un[k] = U[o];
+        pk[k] = Pv[o];
+        wk[k] = Wv[o];
+        sk[k] = Sv[o];
+        xk[k] = a.x[o];
+        rn[k] = R[o];
+      }
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        pk[k] = un[k] + beta * pk[k];
+        sk[k] = wk[k] + beta * sk[k];
+        xk[k] += alpha * pk[k];
+        rn[k] -= alpha * sk[k];
       }
       precond(n, rn, un);
 #pragma unroll
-      for (int k = 0; k < D; ++k) U[(size_t)k * ld + n] = un[k];
+      for (int k = 0; k < D; ++k) {
+        const size_t o = (size_t)k * ld + n;
+        Pv[o] = pk[k];
+        Sv[o] = sk[k];
+        a.x[o] = xk[k];
+        R[o] = rn[k];
+        U[o] = un[k];
+      }
     }
     if (!bar()) return;
     double v[4] = {0.0, 0.0, 0.0, 0.0};
     for (int n = tid; n < a.N; n += nth) {
       int nb[6];
       load_nb(n, nb);
-      double un[D], wn[D];
+      double un[D], wn[D], rk[D];
 #pragma unroll
-      for (int k = 0; k < D; ++k) un[k] = U[(size_t)k * ld + n];
+      for (int k = 0; k < D; ++k) {
+        un[k] = U[(size_t)k * ld + n];
+        rk[k] = R[(size_t)k * ld + n];
+      }
       amul<D, double>(a.blocks + n, (int)ld, s, nb, a.ndir, un, U, ld, wn);
 #pragma unroll
       for (int k = 0; k < D; ++k) {
-        const double rk = R[(size_t)k * ld + n];
-        Wv[(size_t)k * ld + n] = wn[k];
-        v[0] += rk * un[k];
+        v[0] += rk[k] * un[k];
         v[1] += wn[k] * un[k];
-        v[2] += rk * rk;
+        v[2] += rk[k] * rk[k];
       }
+#pragma unroll
+      for (int k = 0; k < D; ++k) Wv[(size_t)k * ld + n] = wn[k];
     }
     if (!grid_allreduce4(a.bar, a.part, a.tot, v, sh.red, sh.ints, tot)) return;
     ++it;
@@ -646,19 +663,22 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_mixed_stream(PcgArgs a) {
     for (int n = tid; n < a.N; n += nth) {
       int nb[6];
       load_nb(n, nb);
-      float un[D], wn[D];
+      float un[D], wn[D], rk[D];
 #pragma unroll
-      for (int k = 0; k < D; ++k) un[k] = a.u32[(size_t)k * ld + n];
+      for (int k = 0; k < D; ++k) {
+        un[k] = a.u32[(size_t)k * ld + n];
+        rk[k] = a.r32[(size_t)k * ld + n];
+      }
       amul<D, float>(a.blocks32 + n, (int)ld, s32, nb, a.ndir, un, a.u32, ld, wn);
       float g = 0.f, dl = 0.f, q2 = 0.f;
 #pragma unroll
       for (int k = 0; k < D; ++k) {
-        const float rk = a.r32[(size_t)k * ld + n];
-        a.w32[(size_t)k * ld + n] = wn[k];
-        g += rk * un[k];
+        g += rk[k] * un[k];
         dl += wn[k] * un[k];
-        q2 += rk * rk;
+        q2 += rk[k] * rk[k];
       }
+#pragma unroll
+      for (int k = 0; k < D; ++k) a.w32[(size_t)k * ld + n] = wn[k];
       v[0] += g;
       v[1] += dl;
       v[2] += q2;
@@ -726,21 +746,34 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_mixed_stream(PcgArgs a) {
     while (true) {
       const float fa = (float)alpha, fb = (float)beta;
       for (int n = tid; n < a.N; n += nth) {
-        float rn[D], un[D];
+        float rn[D], un[D], pk[D], sk[D], dk[D], wk[D];
 #pragma unroll
         for (int k = 0; k < D; ++k) {
           const size_t o = (size_t)k * ld + n;
-          const float pk = a.u32[o] + fb * a.p32[o];
-          const float sk = a.w32[o] + fb * a.s32[o];
-          a.p32[o] = pk;
-          a.s32[o] = sk;
-          a.d32[o] += fa * pk;
-          rn[k] = a.r32[o] - fa * sk;
-          a.r32[o] = rn[k];
+          un[k] = a.u32[o];
+          pk[k] = a.p32[o];
+          wk[k] = a.w32[o];
+          sk[k] = a.s32[o];
+          dk[k] = a.d32[o];
+          rn[k] = a.r32[o];
+        }
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          pk[k] = un[k] + fb * pk[k];
+          sk[k] = wk[k] + fb * sk[k];
+          dk[k] += fa * pk[k];
+          rn[k] -= fa * sk[k];
         }
         precond(n, rn, un);
 #pragma unroll
-        for (int k = 0; k < D; ++k) a.u32[(size_t)k * ld + n] = un[k];
+        for (int k = 0; k < D; ++k) {
+          const size_t o = (size_t)k * ld + n;
+          a.p32[o] = pk[k];
+          a.s32[o] = sk[k];
+          a.d32[o] = dk[k];
+          a.r32[o] = rn[k];
+          a.u32[o] = un[k];
+        }
       }
       if (!bar()) return;
       if (!matvec_partials(tot)) return;
