@@ -265,7 +265,9 @@ def run_ours(args, world, rank, local):
     achieved_tf = flops / dur_s / 1e12
     achieved_gbs = bytes_ / dur_s / 1e9
     total_ms = sum(v["ms"] for v in tim.values())
-    n_launch = sum(v["launches"] for k, v in tim.items()) + tim["hyper"]["launches"]  # 2 kernels
+    # kernels per timed launch group: edge terms + assembly (W, A), quadratic form + draw (hyper)
+    per_group = {"assemble_W": 2, "assemble_A": 2, "hyper": 2}
+    n_launch = sum(v["launches"] * per_group.get(k, 1) for k, v in tim.items())
     roof = {"kernel": f"k_pcg<{K}> (W solve)", "bound": "alu", "achieved": achieved_tf,
             "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved_tf / FP64_PEAK_TFLOPS,
             "traffic": None,

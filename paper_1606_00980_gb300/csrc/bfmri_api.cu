@@ -53,6 +53,7 @@ struct bfmri_handle {
   // mixed precision (FP32 inner solver)
   float *d_blocks32 = nullptr, *d_mfac32 = nullptr, *d_u32 = nullptr, *d_r32 = nullptr;
   float *d_w32 = nullptr, *d_p32 = nullptr, *d_s32 = nullptr, *d_d32 = nullptr;
+  double* d_edge = nullptr;   // [3][D][ld] perturbation edge terms
   unsigned int* d_bar = nullptr;
   int* d_err = nullptr;
   PcgCtrl* d_ctrl = nullptr;  // [0] W solves, [1] A solves
@@ -339,7 +340,9 @@ bfmri_status enqueue_W(bfmri_handle* h, uint64_t counter) {
   cudaError_t e;
   {
     Timed tm(h, BFMRI_T_ASSEMBLE_W);
-    e = launch_assemble_w(a, h->stream);
+    e = launch_edge_noise(a.g, h->K, h->d_alpha, a.rng, h->d_edge, h->stream);
+    a.edge = h->d_edge;
+    if (e == cudaSuccess) e = launch_assemble_w(a, h->stream);
   }
   if (e != cudaSuccess) return cuda_fail(h, e, "assemble_w");
   return run_pcg(h, h->K, h->d_alpha, h->d_W, 0);
@@ -355,10 +358,14 @@ bfmri_status enqueue_A(bfmri_handle* h, uint64_t counter) {
     a.x_direct = h->d_A;
     a.precond = 0;
   }
-  cudaError_t e;
+  cudaError_t e = cudaSuccess;
   {
     Timed tm(h, BFMRI_T_ASSEMBLE_A);
-    e = launch_assemble_a(a, h->stream);
+    if (h->P > 0 && spatial) {
+      e = launch_edge_noise(a.g, h->P, h->d_beta, a.rng, h->d_edge, h->stream);
+      a.edge = h->d_edge;
+    }
+    if (e == cudaSuccess) e = launch_assemble_a(a, h->stream);
   }
   if (e != cudaSuccess) return cuda_fail(h, e, "assemble_a");
   if (h->P > 0 && spatial) return run_pcg(h, h->P, h->d_beta, h->d_A, 1);
@@ -715,6 +722,11 @@ bfmri_status bfmri_create(const bfmri_lattice* lat, const uint8_t* mask, const d
   h->d_err = (int*)A(sizeof(int));
   h->d_ctrl = (PcgCtrl*)A(2 * sizeof(PcgCtrl));
   h->d_flags = (int*)A(4 * sizeof(int));
+  h->d_edge = (double*)A((size_t)3 * D * ld * sizeof(double));
+  if (!h->d_edge) {
+    bfmri_destroy(h);
+    return fail(nullptr, BFMRI_ERR_OOM, "device allocation failed");
+  }
   if (o.precision == BFMRI_PREC_MIXED) {
     h->d_blocks32 = (float*)A((size_t)ntri(D) * ld * sizeof(float));
     h->d_mfac32 = (float*)A((size_t)ntri(D) * ld * sizeof(float));

@@ -155,7 +155,8 @@ __global__ void __launch_bounds__(VOX_THREADS) k_assemble_w(AssembleArgs a) {
     lower_mul_invdiag<K>(L, z, Lz);
 #pragma unroll
     for (int k = 0; k < K; ++k) rhs[k] += Lz[k];
-    add_edge_noise<K>(a.g, a.rng, n, lin, sq, rhs);
+    if (a.edge) add_edge_terms<K>(a.g, a.edge, n, rhs);
+    else add_edge_noise<K>(a.g, a.rng, n, lin, sq, rhs);
   }
 #pragma unroll
   for (int k = 0; k < K; ++k) a.rhs[k * ld + n] = rhs[k];
@@ -259,7 +260,20 @@ __global__ void __launch_bounds__(VOX_THREADS) k_assemble_a(AssembleArgs a) {
       double sq[PM];
 #pragma unroll
       for (int i = 0; i < PM; ++i) sq[i] = (i < P) ? sqrt(a.scale[i]) : 0.0;
-      add_edge_noise<PM>(a.g, a.rng, n, lin, sq, rhs);
+      if (a.edge) {
+        // terms generated for dimension P; the padded components stay zero
+        double part[PM];
+#pragma unroll
+        for (int i = 0; i < PM; ++i) part[i] = 0.0;
+        if (P == 1) add_edge_terms<1>(a.g, a.edge, n, part);
+        else if (P == 2) add_edge_terms<2>(a.g, a.edge, n, part);
+        else if (P == 3) add_edge_terms<3>(a.g, a.edge, n, part);
+        else add_edge_terms<4>(a.g, a.edge, n, part);
+#pragma unroll
+        for (int i = 0; i < PM; ++i) rhs[i] += part[i];
+      } else {
+        add_edge_noise<PM>(a.g, a.rng, n, lin, sq, rhs);
+      }
     }
   }
   if (a.x_direct) {
@@ -295,6 +309,27 @@ __global__ void __launch_bounds__(VOX_THREADS) k_assemble_a(AssembleArgs a) {
     }
   }
   if (!ok) atomicMin(a.bad_voxel, n);
+}
+
+// ---------------------------------------------------------------------------------------
+// Edge terms of the perturbation, generated once per edge.
+// ---------------------------------------------------------------------------------------
+template <int D>
+__global__ void __launch_bounds__(VOX_THREADS) k_edge_noise(Geometry g, const double* scale, Rng rng,
+                                                            double* E) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= g.N) return;
+  const uint32_t lin = (uint32_t)g.lin[n];
+  double sq[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) sq[k] = sqrt(scale[k]);
+  for (int d = 0; d < g.ndir / 2; ++d) {
+    double z[D];
+    const bool has = __ldg(g.nbr + (size_t)(2 * d + 1) * g.ld + n) >= 0;
+    if (has) site_normals<D>(rng, lin * 4u + (uint32_t)d, z);
+#pragma unroll
+    for (int k = 0; k < D; ++k) E[((size_t)d * D + k) * g.ld + n] = has ? sq[k] * z[k] : 0.0;
+  }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -478,6 +513,23 @@ cudaError_t launch_lambda(const LambdaArgs& a, cudaStream_t s) {
   if (a.g.N <= 0) return cudaSuccess;
   k_lambda<<<(a.g.N + VOX_THREADS - 1) / VOX_THREADS, VOX_THREADS, 0, s>>>(a);
   return cudaGetLastError();
+}
+
+template <int D>
+static cudaError_t edge_d(const Geometry& g, const double* scale, Rng rng, double* E, cudaStream_t s) {
+  k_edge_noise<D><<<(g.N + VOX_THREADS - 1) / VOX_THREADS, VOX_THREADS, 0, s>>>(g, scale, rng, E);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_edge_noise(const Geometry& g, int D, const double* scale, Rng rng, double* E,
+                              cudaStream_t s) {
+  if (g.N <= 0) return cudaSuccess;
+  switch (D) {
+#define CASE(k) case k: return edge_d<k>(g, scale, rng, E, s);
+    BFMRI_K_CASES(CASE)
+#undef CASE
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 int hyper_grid(int N) {

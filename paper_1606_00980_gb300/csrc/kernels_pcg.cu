@@ -35,7 +35,7 @@ __device__ __forceinline__ float ldx(const float* p) { return __ldcg(p); }
 // out = B v + s .* (deg v - sum_m V[m])  (B packed, entry e at Bp[e * bs]); element type T.
 template <int D, typename T>
 __device__ __forceinline__ void amul(const T* __restrict__ Bp, int bs, const T* s,
-                                     const int* nb, int ndir, const T* v,
+                                     const int* nb, int ndir, T degT, const T* v,
                                      const T* V, size_t ld, T* out) {
 #pragma unroll
   for (int i = 0; i < D; ++i) {
@@ -47,17 +47,24 @@ __device__ __forceinline__ void amul(const T* __restrict__ Bp, int bs, const T* 
   T sum[D];
 #pragma unroll
   for (int k = 0; k < D; ++k) sum[k] = T(0);
-  int deg = 0;
 #pragma unroll
   for (int d = 0; d < 6; ++d) {
     if (d < ndir && nb[d] >= 0) {
-      ++deg;
 #pragma unroll
       for (int k = 0; k < D; ++k) sum[k] += ldx(V + (size_t)k * ld + nb[d]);
     }
   }
 #pragma unroll
-  for (int k = 0; k < D; ++k) out[k] += s[k] * ((T)deg * v[k] - sum[k]);
+  for (int k = 0; k < D; ++k) out[k] += s[k] * (degT * v[k] - sum[k]);
+}
+
+// number of in-mask neighbours, in the element type (converted once per voxel)
+template <typename T>
+__device__ __forceinline__ T degree_of(const int* nb, int ndir) {
+  int deg = 0;
+#pragma unroll
+  for (int d = 0; d < 6; ++d) deg += (d < ndir && nb[d] >= 0) ? 1 : 0;
+  return (T)deg;
 }
 
 // z = (L L')^-1 r with L packed lower (inverted diagonal), entry e at Lp[e * bs].
@@ -150,8 +157,8 @@ __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_res(PcgArgs a) {
   const int bd = blockDim.x, t = threadIdx.x;
   double* shB = smem;
   double* shM = smem + NT * bd;
-  const int n = blockIdx.x * bd + t;
-  const bool own = n < a.N;
+  const int n = blockIdx.x * a.res_per + t;
+  const bool own = t < a.res_per && n < a.N;
   const size_t ld = a.ld;
   const bool pre = a.mfac != nullptr;
 #pragma unroll
@@ -165,6 +172,7 @@ __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_res(PcgArgs a) {
   int nb[6];
 #pragma unroll
   for (int d = 0; d < 6; ++d) nb[d] = (own && d < a.ndir) ? __ldg(a.nbr + (size_t)d * ld + n) : -1;
+  const double degd = degree_of<double>(nb, a.ndir);
   double s[D], x[D], r[D], u[D], w[D], p[D], q[D], bv[D];
 #pragma unroll
   for (int k = 0; k < D; ++k) {
@@ -183,7 +191,7 @@ __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_res(PcgArgs a) {
   // (r, u, w) from the current x, with partials (r'u, w'u, r'r, b'b)
   auto restart = [&](double* tot) -> bool {
     double ax[D];
-    amul<D, double>(Bp, bd, s, nb, a.ndir, x, a.x, ld, ax);
+    amul<D, double>(Bp, bd, s, nb, a.ndir, degd, x, a.x, ld, ax);
 #pragma unroll
     for (int k = 0; k < D; ++k) r[k] = bv[k] - ax[k];
     minv<D, double>(Mp, bd, r, u);
@@ -192,7 +200,7 @@ __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_res(PcgArgs a) {
       for (int k = 0; k < D; ++k) a.u[(size_t)k * ld + n] = u[k];
     }
     if (!bar()) return false;
-    amul<D, double>(Bp, bd, s, nb, a.ndir, u, a.u, ld, w);
+    amul<D, double>(Bp, bd, s, nb, a.ndir, degd, u, a.u, ld, w);
     double v[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
     for (int k = 0; k < D; ++k) {
@@ -233,7 +241,7 @@ __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_res(PcgArgs a) {
       for (int k = 0; k < D; ++k) a.u[(size_t)k * ld + n] = u[k];
     }
     if (!bar()) return;
-    amul<D, double>(Bp, bd, s, nb, a.ndir, u, a.u, ld, w);
+    amul<D, double>(Bp, bd, s, nb, a.ndir, degd, u, a.u, ld, w);
     double v[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
     for (int k = 0; k < D; ++k) {
@@ -320,7 +328,7 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_stream(PcgArgs a) {
       double xn[D], ax[D], rn[D], un[D];
 #pragma unroll
       for (int k = 0; k < D; ++k) xn[k] = ldx(a.x + (size_t)k * ld + n);
-      amul<D, double>(a.blocks + n, (int)ld, s, nb, a.ndir, xn, a.x, ld, ax);
+      amul<D, double>(a.blocks + n, (int)ld, s, nb, a.ndir, degree_of<double>(nb, a.ndir), xn, a.x, ld, ax);
 #pragma unroll
       for (int k = 0; k < D; ++k) rn[k] = __ldg(a.b + (size_t)k * ld + n) - ax[k];
       precond(n, rn, un);
@@ -340,7 +348,7 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_stream(PcgArgs a) {
       double un[D], wn[D];
 #pragma unroll
       for (int k = 0; k < D; ++k) un[k] = U[(size_t)k * ld + n];
-      amul<D, double>(a.blocks + n, (int)ld, s, nb, a.ndir, un, U, ld, wn);
+      amul<D, double>(a.blocks + n, (int)ld, s, nb, a.ndir, degree_of<double>(nb, a.ndir), un, U, ld, wn);
 #pragma unroll
       for (int k = 0; k < D; ++k) {
         const double rk = R[(size_t)k * ld + n], bk = __ldg(a.b + (size_t)k * ld + n);
@@ -413,7 +421,7 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_stream(PcgArgs a) {
         un[k] = U[(size_t)k * ld + n];
         rk[k] = R[(size_t)k * ld + n];
       }
-      amul<D, double>(a.blocks + n, (int)ld, s, nb, a.ndir, un, U, ld, wn);
+      amul<D, double>(a.blocks + n, (int)ld, s, nb, a.ndir, degree_of<double>(nb, a.ndir), un, U, ld, wn);
 #pragma unroll
       for (int k = 0; k < D; ++k) {
         v[0] += rk[k] * un[k];
@@ -467,8 +475,8 @@ __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_mixed_res(PcgArgs a)
   double* shB = smem;                                   // [NT][bd] FP64 blocks
   float* shB32 = reinterpret_cast<float*>(smem + NT * bd);   // [NT][bd]
   float* shM32 = shB32 + NT * bd;                       // [NT][bd]
-  const int n = blockIdx.x * bd + t;
-  const bool own = n < a.N;
+  const int n = blockIdx.x * a.res_per + t;
+  const bool own = t < a.res_per && n < a.N;
   const size_t ld = a.ld;
   const bool pre = a.mfac32 != nullptr;
 #pragma unroll
@@ -483,6 +491,8 @@ __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_mixed_res(PcgArgs a)
   int nb[6];
 #pragma unroll
   for (int d = 0; d < 6; ++d) nb[d] = (own && d < a.ndir) ? __ldg(a.nbr + (size_t)d * ld + n) : -1;
+  const double degd = degree_of<double>(nb, a.ndir);
+  const float degf = (float)degd;
   double s[D], x[D], bv[D];
   float s32[D];
 #pragma unroll
@@ -507,7 +517,7 @@ __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_mixed_res(PcgArgs a)
     double r64[D];
     {
       double ax[D];
-      amul<D, double>(Bp, bd, s, nb, a.ndir, x, a.x, ld, ax);
+      amul<D, double>(Bp, bd, s, nb, a.ndir, degd, x, a.x, ld, ax);
       double v[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
       for (int k = 0; k < D; ++k) {
@@ -549,7 +559,7 @@ __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_mixed_res(PcgArgs a)
       for (int k = 0; k < D; ++k) a.u32[(size_t)k * ld + n] = u[k];
     }
     if (!bar()) return;
-    amul<D, float>(Bp32, bd, s32, nb, a.ndir, u, a.u32, ld, w);
+    amul<D, float>(Bp32, bd, s32, nb, a.ndir, degf, u, a.u32, ld, w);
     {
       float g = 0.f, dl = 0.f, q2 = 0.f;
 #pragma unroll
@@ -580,7 +590,7 @@ __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_mixed_res(PcgArgs a)
         for (int k = 0; k < D; ++k) a.u32[(size_t)k * ld + n] = u[k];
       }
       if (!bar()) return;
-      amul<D, float>(Bp32, bd, s32, nb, a.ndir, u, a.u32, ld, w);
+      amul<D, float>(Bp32, bd, s32, nb, a.ndir, degf, u, a.u32, ld, w);
       float g = 0.f, dl = 0.f, q2 = 0.f;
 #pragma unroll
       for (int k = 0; k < D; ++k) {
@@ -669,7 +679,7 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_mixed_stream(PcgArgs a) {
         un[k] = a.u32[(size_t)k * ld + n];
         rk[k] = a.r32[(size_t)k * ld + n];
       }
-      amul<D, float>(a.blocks32 + n, (int)ld, s32, nb, a.ndir, un, a.u32, ld, wn);
+      amul<D, float>(a.blocks32 + n, (int)ld, s32, nb, a.ndir, degree_of<float>(nb, a.ndir), un, a.u32, ld, wn);
       float g = 0.f, dl = 0.f, q2 = 0.f;
 #pragma unroll
       for (int k = 0; k < D; ++k) {
@@ -697,7 +707,7 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_mixed_stream(PcgArgs a) {
         double xn[D], ax[D];
 #pragma unroll
         for (int k = 0; k < D; ++k) xn[k] = ldx(a.x + (size_t)k * ld + n);
-        amul<D, double>(a.blocks + n, (int)ld, s, nb, a.ndir, xn, a.x, ld, ax);
+        amul<D, double>(a.blocks + n, (int)ld, s, nb, a.ndir, degree_of<double>(nb, a.ndir), xn, a.x, ld, ax);
         float rn[D], un[D];
 #pragma unroll
         for (int k = 0; k < D; ++k) {
@@ -825,11 +835,15 @@ template <int D>
 cudaError_t launch_resident(const PcgArgs& a, cudaStream_t stream, int* grid_out, bool* launched) {
   *launched = false;
   const int nsm = capped_sms(a.sm_cap);
-  int threads = (a.N + nsm - 1) / nsm;
-  threads = ((threads + 31) / 32) * 32;
+  // spread the voxels evenly over the SMs: CTA b owns voxels [b per, (b + 1) per)
+  int grid = nsm;
+  if ((a.N + 63) / 64 < grid) grid = (a.N + 63) / 64;
+  if (grid < 1) grid = 1;
+  const int per = (a.N + grid - 1) / grid;
+  grid = (a.N + per - 1) / per;
+  int threads = ((per + 31) / 32) * 32;
   if (threads < 64) threads = 64;
   if (threads > RES_MAX_THREADS) return cudaSuccess;
-  const int grid = (a.N + threads - 1) / threads;
   if (a.max_grid > 0 && grid > a.max_grid) return cudaSuccess;
   // FP64: blocks + factor in FP64; mixed: FP64 blocks + FP32 blocks + FP32 factor
   const size_t shm = a.mixed ? (size_t)ntri(D) * threads * (sizeof(double) + 2 * sizeof(float))
@@ -847,7 +861,9 @@ cudaError_t launch_resident(const PcgArgs& a, cudaStream_t stream, int* grid_out
   if (per_sm < 1 || grid > per_sm * nsm) return cudaSuccess;
   if (grid_out) *grid_out = grid;
   *launched = true;
-  void* args[] = {(void*)&a};
+  PcgArgs b = a;
+  b.res_per = per;
+  void* args[] = {(void*)&b};
   return cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(threads), args, shm, stream);
 }
 

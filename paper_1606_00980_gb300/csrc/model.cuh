@@ -55,6 +55,24 @@ __device__ __forceinline__ void add_edge_noise(const Geometry& g, const Rng& rng
   }
 }
 
+// The same sum from pre-generated edge terms E[d][k][n] = sqrt(s_k) z1_k of the edge from
+// voxel n in direction +d (launch_edge_noise): + own forward edges, - backward neighbours'.
+template <int D>
+__device__ __forceinline__ void add_edge_terms(const Geometry& g, const double* __restrict__ E,
+                                               int n, double* rhs) {
+  for (int d = 0; d < g.ndir / 2; ++d) {
+    if (__ldg(g.nbr + (size_t)(2 * d + 1) * g.ld + n) >= 0) {
+#pragma unroll
+      for (int k = 0; k < D; ++k) rhs[k] += __ldg(E + ((size_t)d * D + k) * g.ld + n);
+    }
+    const int m = __ldg(g.nbr + (size_t)(2 * d) * g.ld + n);
+    if (m >= 0) {
+#pragma unroll
+      for (int k = 0; k < D; ++k) rhs[k] -= __ldg(E + ((size_t)d * D + k) * g.ld + m);
+    }
+  }
+}
+
 __device__ __forceinline__ int degree(const Geometry& g, int n) {
   int deg = 0;
   for (int d = 0; d < g.ndir; ++d) deg += __ldg(g.nbr + (size_t)d * g.ld + n) >= 0 ? 1 : 0;
@@ -158,7 +176,13 @@ struct AssembleArgs {
   const double* Cmom;   // W system: [n_syy(P)][ld] E[c_p c_q] over A samples, replaces c c'
   const double* Gin;    // A system: [n_syy(P)][ld] lagged residual Gram averaged over W samples
   double* ldata;        // [ntri(D)][ld] Cholesky factor of the data block (or null)
+  const double* edge;   // [3][D][ld] pre-generated edge terms (launch_edge_noise), or null
 };
+
+// E[d][k][n] = sqrt(scale_k) z1_k for the edge from voxel n in direction +d (zero when absent):
+// each edge's normals are generated once instead of by both of its endpoints.
+cudaError_t launch_edge_noise(const Geometry& g, int D, const double* scale, Rng rng, double* E,
+                              cudaStream_t s);
 cudaError_t launch_assemble_w(const AssembleArgs& a, cudaStream_t s);
 cudaError_t launch_assemble_a(const AssembleArgs& a, cudaStream_t s);
 

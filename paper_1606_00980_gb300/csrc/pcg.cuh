@@ -49,6 +49,7 @@ struct PcgArgs {
   int max_grid;          // rows of the partial buffer: the launch never uses more CTAs
   int allow_resident;    // 1: use the register/shared-memory resident variant when N fits
   int sm_cap;            // most SMs the grid may span (0 = all)
+  int res_per;           // resident variant: voxels per CTA (set by the launcher)
   // mixed precision: FP32 inner PCG inside FP64 iterative refinement
   int mixed;
   const float* blocks32; // [ntri(D)][ld] FP32 copies of blocks / mfac
