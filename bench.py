@@ -316,7 +316,7 @@ def run_mixed(args, w, flush, stream):
 
     from paper_1606_00980_gb300 import bfmri
     from paper_1606_00980_gb300.bfmri import Model
-    m = Model.from_workload(w, delta=1e-8, seed=2024, precision=bfmri.PREC_MIXED, inner_tol=1e-4,
+    m = Model.from_workload(w, delta=1e-8, seed=2024, precision=bfmri.PREC_MIXED, inner_tol=1e-6,
                             profile=1)
     m.precompute_stats()
     counter = 0
@@ -342,7 +342,7 @@ def run_mixed(args, w, flush, stream):
     tim = m.timing()
     m.close()
     return {"value": args.steps / tot, "unit": UNIT, "ms_per_step": tot / args.steps * 1e3,
-            "delta": 1e-8, "inner_tol": 1e-4,
+            "delta": 1e-8, "inner_tol": 1e-6,
             "inner_iterations_W_per_sweep": it_w / args.steps,
             "kernel_ms_per_step": {k: v["ms"] / args.steps for k, v in tim.items() if v["launches"]}}
 
@@ -414,7 +414,7 @@ def run_serving(args):
         w.Y = w.Y.astype(np.float32)
         pool.append(w)
     slots, sm_budget, budget = 4, 38, 64 << 30
-    opts = dict(precision=bfmri.PREC_MIXED, delta=1e-8, inner_tol=1e-4)
+    opts = dict(precision=bfmri.PREC_MIXED, delta=1e-8, inner_tol=1e-6)
     # capacity pilot: every pool member alone (service time), then a saturating burst of
     # 4 x the pool through all slots (sustained requests/s)
     srv = bfmri.Server(budget, slots, sm_budget)

@@ -82,7 +82,8 @@ typedef struct {
   int precision;       /* BFMRI_PREC_* (default FP64) */
   int ar_prior;        /* BFMRI_AR_* (default spatial) */
   int y_layout;        /* BFMRI_Y_* (default masked) */
-  double inner_tol;    /* mixed precision: relative tolerance of each FP32 inner solve */
+  double inner_tol;    /* mixed precision: relative tolerance of each FP32 inner solve
+                          (default 1e-6; the last one stops where the outer delta is met) */
   uint64_t seed;       /* Philox key */
   uint32_t stream_id;  /* 24-bit chain id folded into every Philox counter */
   void* cuda_stream;   /* cudaStream_t for all device work (NULL = legacy default stream) */

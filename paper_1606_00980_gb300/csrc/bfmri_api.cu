@@ -551,7 +551,7 @@ void bfmri_default_options(bfmri_options* o) {
   o->precision = BFMRI_PREC_FP64;
   o->ar_prior = BFMRI_AR_SPATIAL;
   o->y_layout = BFMRI_Y_MASKED;
-  o->inner_tol = 1e-5;
+  o->inner_tol = 1e-6;
   o->seed = 0x5eed5eedULL;
   o->stream_id = 0;
   o->cuda_stream = nullptr;

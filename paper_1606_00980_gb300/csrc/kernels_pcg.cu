@@ -552,7 +552,8 @@ __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_mixed_res(PcgArgs a)
       p[k] = 0.f;
       q[k] = 0.f;
     }
-    const double itol2 = a.inner_tol * a.inner_tol * rr;
+    // inner target: inner_tol relative, but no further than the outer stop needs
+    const double itol2 = fmax(a.inner_tol * a.inner_tol * rr, 0.25 * tol2);
     minv<D, float>(Mp32, bd, r, u);
     if (own) {
 #pragma unroll
@@ -746,7 +747,8 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_mixed_stream(PcgArgs a) {
     if (rr <= tol2) break;
     if (inner_total >= a.max_iter) { status = 4; break; }
     ++outer;
-    const double itol2 = a.inner_tol * a.inner_tol * rr;
+    // inner target: inner_tol relative, but no further than the outer stop needs
+    const double itol2 = fmax(a.inner_tol * a.inner_tol * rr, 0.25 * tol2);
     // u was published by the residual phase, whose reducing barrier has completed
     if (!matvec_partials(tot)) return;
     double gam = tot[0], del = tot[1];

@@ -49,7 +49,7 @@ def test_default_options_without_gpu(lib):
     o = bfmri.bfmri_default_options()
     assert (o.q1, o.q2, o.u1, o.u2, o.r1, o.r2) == (10.0, 0.1, 10.0, 0.1, 10000.0, 0.1)
     assert o.delta == 1e-8 and o.precond == bfmri.PRECOND_BLOCK_JACOBI
-    assert o.debug_skip_block == -1
+    assert o.debug_skip_block == -1 and o.inner_tol == 1e-6
 
 
 def test_create_rejects_bad_arguments_without_touching_the_gpu(lib):
