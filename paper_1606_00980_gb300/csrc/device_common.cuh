@@ -107,6 +107,22 @@ __device__ __forceinline__ double gamma_draw(const Rng& g, uint32_t site, double
 }
 
 // ---------------------------------------------------------------------------------------
+// Asynchronous global -> shared copies (cp.async): the copy completes in the background and
+// cp.async.wait_group blocks only this thread until its own earlier groups have landed.
+// A false predicate copies nothing and fills the destination with zeros.
+// ---------------------------------------------------------------------------------------
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* sdst, const void* gsrc, bool pred) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
+  const int src_size = pred ? BYTES : 0;
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"(s), "l"(gsrc), "n"(BYTES), "r"(src_size)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// ---------------------------------------------------------------------------------------
 // Packed symmetric / lower-triangular D x D blocks, stored as D(D+1)/2 planes of length
 // ld (structure of arrays): entry (i, j), i >= j, is plane i(i+1)/2 + j.
 // ---------------------------------------------------------------------------------------

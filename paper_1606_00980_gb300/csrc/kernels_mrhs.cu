@@ -251,8 +251,20 @@ __device__ __forceinline__ bool mrhs_reduce(const MrhsArgs& a, const Units& U, i
 
 }  // namespace
 
+// FP32 solves stage their vector streams through shared memory (cp.async); FP64 solves,
+// whose stages would not fit twice per SM, load directly.
+template <typename T>
+constexpr bool kStaged = sizeof(T) == 4;
+
+template <int D, typename T>
+constexpr size_t mrhs_stage_bytes() {
+  return kStaged<T> ? (size_t)(MRHS_THREADS / 32) * 2 * (6 * D) * 32 * sizeof(T) : 0;
+}
+
 template <int D, typename T>
 __global__ void __launch_bounds__(MRHS_THREADS, 2) k_mrhs(MrhsArgs a) {
+  extern __shared__ __align__(16) unsigned char mrhs_smem[];
+  T* stage = reinterpret_cast<T*>(mrhs_smem);
   T sc[D];
 #pragma unroll
   for (int k = 0; k < D; ++k) sc[k] = (T)__ldg(a.scale + k);
@@ -356,21 +368,9 @@ __global__ void __launch_bounds__(MRHS_THREADS, 2) k_mrhs(MrhsArgs a) {
         T *x = Xv + (size_t)r * a.vs, *R = Rv + (size_t)r * a.vs, *Uu = UUv + (size_t)r * a.vs;
         T *P = PPv + (size_t)r * a.vs, *Sv = SSv + (size_t)r * a.vs;
         const T* Wv = WWv + (size_t)r * a.vs;
+        const int n0 = c * U.csize;
         const int n1 = min(a.N, (c + 1) * U.csize);
-        for (int n = c * U.csize + U.lane; n < n1; n += 32) {
-          // all loads first: the six vectors are distinct arrays, but the compiler cannot
-          // prove it, and interleaved stores would serialise the loads
-          T rn[D], un[D], pk[D], sk[D], xk[D], wk[D];
-#pragma unroll
-          for (int k = 0; k < D; ++k) {
-            const size_t o = (size_t)k * ld + n;
-            un[k] = Uu[o];
-            pk[k] = P[o];
-            wk[k] = Wv[o];
-            sk[k] = Sv[o];
-            xk[k] = x[o];
-            rn[k] = R[o];
-          }
+        auto update = [&](int n, T* un, T* pk, T* wk, T* sk, T* xk, T* rn) {
 #pragma unroll
           for (int k = 0; k < D; ++k) {
             pk[k] = un[k] + be * pk[k];
@@ -387,6 +387,64 @@ __global__ void __launch_bounds__(MRHS_THREADS, 2) k_mrhs(MrhsArgs a) {
             x[o] = xk[k];
             R[o] = rn[k];
             Uu[o] = un[k];
+          }
+        };
+        if constexpr (kStaged<T>) {
+          // The six vectors of the next group of 32 voxels stream into this warp's shared
+          // stage (cp.async) while the current group is updated: every lane reads back only
+          // the column it copied itself, so no warp synchronisation is needed.
+          T* st0 = stage + (size_t)(threadIdx.x >> 5) * 2 * (6 * D) * 32;
+          const T* src[6] = {Uu, P, Wv, Sv, x, R};
+          auto issue = [&](T* buf, int g0) {
+            const int n = g0 + U.lane;
+            const bool ok = n < n1;
+            const int nn = ok ? n : n0;
+#pragma unroll
+            for (int v = 0; v < 6; ++v)
+#pragma unroll
+              for (int k = 0; k < D; ++k)
+                cp_async<sizeof(T)>(buf + (size_t)(v * D + k) * 32 + U.lane, src[v] + (size_t)k * ld + nn, ok);
+            cp_async_commit();
+          };
+          if (n0 < n1) issue(st0, n0);
+          for (int g0 = n0; g0 < n1; g0 += 32) {
+            T* cur = st0 + (size_t)(((g0 - n0) >> 5) & 1) * (6 * D) * 32;
+            T* nxt = st0 + (size_t)((((g0 - n0) >> 5) + 1) & 1) * (6 * D) * 32;
+            if (g0 + 32 < n1) issue(nxt, g0 + 32);
+            else cp_async_commit();               // empty group keeps the wait count uniform
+            cp_async_wait<1>();
+            const int n = g0 + U.lane;
+            if (n < n1) {
+              T un[D], pk[D], wk[D], sk[D], xk[D], rn[D];
+#pragma unroll
+              for (int k = 0; k < D; ++k) {
+                un[k] = cur[(0 * D + k) * 32 + U.lane];
+                pk[k] = cur[(1 * D + k) * 32 + U.lane];
+                wk[k] = cur[(2 * D + k) * 32 + U.lane];
+                sk[k] = cur[(3 * D + k) * 32 + U.lane];
+                xk[k] = cur[(4 * D + k) * 32 + U.lane];
+                rn[k] = cur[(5 * D + k) * 32 + U.lane];
+              }
+              update(n, un, pk, wk, sk, xk, rn);
+            }
+          }
+          cp_async_wait<0>();
+        } else {
+          for (int n = n0 + U.lane; n < n1; n += 32) {
+            // all loads first: the six vectors are distinct arrays, but the compiler cannot
+            // prove it, and interleaved stores would serialise the loads
+            T rn[D], un[D], pk[D], sk[D], xk[D], wk[D];
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+              const size_t o = (size_t)k * ld + n;
+              un[k] = Uu[o];
+              pk[k] = P[o];
+              wk[k] = Wv[o];
+              sk[k] = Sv[o];
+              xk[k] = x[o];
+              rn[k] = R[o];
+            }
+            update(n, un, pk, wk, sk, xk, rn);
           }
         }
       }
@@ -440,7 +498,12 @@ static cudaError_t launch_d(const MrhsArgs& a, cudaStream_t stream, int* units_o
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   if (a.sm_cap > 0 && a.sm_cap < nsm) nsm = a.sm_cap;
   const void* kern = a.f32 ? (const void*)k_mrhs<D, float> : (const void*)k_mrhs<D, double>;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, MRHS_THREADS, 0);
+  const size_t shm = a.f32 ? mrhs_stage_bytes<D, float>() : mrhs_stage_bytes<D, double>();
+  if (shm > 0) {
+    cudaError_t ea = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    if (ea != cudaSuccess) return ea;
+  }
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, MRHS_THREADS, shm);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   // enough warps for every RHS and for a chunk of at least 32 voxels per warp
@@ -453,7 +516,7 @@ static cudaError_t launch_d(const MrhsArgs& a, cudaStream_t stream, int* units_o
   if (chunks < 1) chunks = 1;
   if (units_out) *units_out = a.S * chunks;
   void* args[] = {(void*)&a};
-  return cudaLaunchCooperativeKernel(kern, dim3((unsigned)grid), dim3(MRHS_THREADS), args, 0, stream);
+  return cudaLaunchCooperativeKernel(kern, dim3((unsigned)grid), dim3(MRHS_THREADS), args, shm, stream);
 }
 
 template <int D>
