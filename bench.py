@@ -340,8 +340,20 @@ def run_mixed(args, w, flush, stream):
     torch.cuda.synchronize()
     tot = sum(a.elapsed_time(b) for a, b in times) / 1e3
     tim = m.timing()
+    # accuracy of one mixed-precision draw against the FP64 draw of the same system and random
+    # numbers (FP64 solved to 1e-12; the parity tests bound that within 1e-8 of the exact draw)
+    st = m.get_state()
+    W_mixed, _ = m.sample_W(counter + 1)
     m.close()
+    m64 = Model.from_workload(w, delta=1e-12, seed=2024)
+    m64.precompute_stats()
+    m64.set_state(W=st["W"], A=st["A"], lam=st["lam"], alpha=st["alpha"], beta=st["beta"])
+    W64, _ = m64.sample_W(counter + 1)
+    m64.close()
+    import numpy as np
+    err = float(np.linalg.norm(W_mixed - W64) / np.linalg.norm(W64))
     return {"value": args.steps / tot, "unit": UNIT, "ms_per_step": tot / args.steps * 1e3,
+            "draw_rel_l2_vs_fp64": err,
             "delta": 1e-8, "inner_tol": 1e-6,
             "inner_iterations_W_per_sweep": it_w / args.steps,
             "kernel_ms_per_step": {k: v["ms"] / args.steps for k, v in tim.items() if v["launches"]}}
@@ -379,6 +391,27 @@ def run_batched(args):
     m.close()
     solve_s = tim["other"]["ms"] / 1e3
     iters = int(res["iterations"].sum())
+    svb = None
+    if not args.no_svb:
+        # one spatial-VB iteration (N_s = 100 samples of W and A, FP64 multi-RHS solves with the
+        # fixed random numbers of Section 3.3), after a first iteration that creates the samples
+        ms = Model.from_workload(w, delta=1e-8, seed=4243, profile=1)
+        ms.precompute_stats()
+        ms.gibbs_sweep(3, 0)
+        ms.spvb_step(100, 7)
+        torch.cuda.synchronize()
+        ms.reset_timing()
+        t1 = time.perf_counter()
+        _, _, info = ms.spvb_step(100, 7)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t1
+        tsv = ms.timing()
+        ms.close()
+        svb = {"samples": 100, "iteration_ms": dt * 1e3,
+               "pcg_iterations_W_total": int(info.pcg_iterations_W),
+               "pcg_iterations_A_total": int(info.pcg_iterations_A),
+               "W_solve_ms": tsv["pcg_W"]["ms"], "A_solve_ms": tsv["pcg_A"]["ms"],
+               "max_rel_residual_W": info.max_rel_residual_W}
     bytes_ = iters * w.N * mrhs_bytes_per_voxel_iter_rhs(w.K, S)
     hbm_peak, hbm_src, _ = peaks()
     gbs = bytes_ / solve_s / 1e9
@@ -386,7 +419,7 @@ def run_batched(args):
             "probes": S, "logdet": res["logdet"], "stderr": res["stderr"],
             "probe_iterations_mean": float(res["iterations"].mean()),
             "probe_iterations_max": int(res["iterations"].max()),
-            "solve_ms": solve_s * 1e3, "call_ms": wall * 1e3,
+            "solve_ms": solve_s * 1e3, "call_ms": wall * 1e3, "svb_iteration": svb,
             "roofline": {"kernel": f"k_mrhs<{w.K}, float>", "bound": "hbm", "achieved": gbs,
                          "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
                          "traffic": None, "peak_source": f"{hbm_src} (MEASURED_PEAKS.json)",
@@ -496,6 +529,7 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--probes", type=int, default=64)
+    ap.add_argument("--no-svb", action="store_true")
     ap.add_argument("--only-batched", action="store_true",
                     help="run only the batched-probe measurement (profiling entry point)")
     ap.add_argument("--serving-requests", type=int, default=96)
