@@ -361,10 +361,10 @@ def run_mixed(args, w, flush, stream):
 
 def mrhs_bytes_per_voxel_iter_rhs(D, S, w=4):
     """Bytes one multi-RHS iteration must move per voxel and right-hand side: the local phase
-    reads u, w, p, s, x, r and writes p, s, x, r, u (11 D words), the product phase reads u and
-    r and writes w (3 D words); the block and the preconditioner factor (D(D+1)/2 words each)
-    are shared by the S right-hand sides."""
-    return w * (14 * D) + w * 2 * (D * (D + 1) // 2) / S
+    reads u, w, p, s, x, r and writes p, s, x, r, u (11 D words, with r'u and r'r formed from
+    the updated values), the product phase reads u and writes w (2 D words); the block and
+    the preconditioner factor (D(D+1)/2 words each) are shared by the S right-hand sides."""
+    return w * (13 * D) + w * 2 * (D * (D + 1) // 2) / S
 
 
 def run_batched(args):

@@ -276,7 +276,7 @@ bfmri_status run_pcg(bfmri_handle* h, int D, const double* scale, double* x, int
   a.p = h->d_p0;
   a.s = h->d_p1;
   a.part = h->d_part;
-  a.tot = h->d_part + (size_t)h->part_rows * 4;
+  a.part1 = h->d_part + (size_t)h->part_rows * 4;
   a.allow_resident = h->opt.pcg_variant == BFMRI_PCG_AUTO;
   a.sm_cap = h->opt.sm_budget;
   a.mixed = h->opt.precision == BFMRI_PREC_MIXED;
@@ -716,7 +716,7 @@ bfmri_status bfmri_create(const bfmri_lattice* lat, const uint8_t* mask, const d
   h->d_q = (double*)A((size_t)D * ld * sizeof(double));
   h->d_p0 = (double*)A((size_t)D * ld * sizeof(double));
   h->d_p1 = (double*)A((size_t)D * ld * sizeof(double));
-  h->d_part = (double*)A(((size_t)maxgrid * 4 + 8) * sizeof(double));
+  h->d_part = (double*)A(((size_t)maxgrid * 8 + 8) * sizeof(double));
   h->d_hpart = (double*)A((size_t)hyper_grid(N) * D * sizeof(double));
   h->d_bar = (unsigned int*)A(2 * sizeof(unsigned int));
   h->d_err = (int*)A(sizeof(int));

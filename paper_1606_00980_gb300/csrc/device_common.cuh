@@ -337,68 +337,68 @@ __device__ __forceinline__ void block_reduce4(const double* v, double* sh, doubl
 }
 
 // ---------------------------------------------------------------------------------------
-// Reducing grid barrier over 4 doubles. Every CTA writes its block totals to one row of
-// `part` and arrives; the CTA that arrives last sums all rows in a fixed order (independent
-// of which CTA it is), publishes the totals in tot[4] and releases the others, which read
-// them. All CTAs therefore obtain bit-identical totals, run after run. sh needs 4 * 32 + 8
-// doubles, sh_int 2 ints.
+// Reducing grid barrier over 4 doubles. Every CTA writes its block totals to one row of a
+// partial buffer and arrives at the barrier; once all have arrived, every CTA sums all rows
+// itself in the same fixed order, so all obtain bit-identical totals, run after run, with no
+// second publication round after the barrier. The two row buffers alternate with the barrier
+// generation: back-to-back reductions (generations g and g + 1) write different buffers, and
+// two reductions that write the same buffer have at least one barrier between them, which no
+// CTA passes before every CTA has read the earlier rows. part0 and part1 hold gridDim.x rows
+// of 4 doubles each. sh needs 4 * 32 + 8 doubles, sh_int 2 ints.
 // ---------------------------------------------------------------------------------------
-__device__ __forceinline__ bool grid_allreduce4(const GridBarrier& b, double* part, double* tot,
+__device__ __forceinline__ bool grid_allreduce4(const GridBarrier& b, double* part0, double* part1,
                                                 const double* v, double* sh, int* sh_int, double* out) {
   double bt[4];
   block_reduce4(v, sh, bt);
   const int l = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned int nblocks = gridDim.x;
   if (threadIdx.x == 0) {
+    const unsigned int g0 = ld_acquire(b.gen);
+    double* part = (g0 & 1u) ? part1 : part0;
 #pragma unroll
     for (int i = 0; i < 4; ++i) part[(size_t)blockIdx.x * 4 + i] = bt[i];
-    const unsigned int g0 = ld_acquire(b.gen);
     const unsigned int arrived = atom_add_acq_rel(b.count, 1u);
-    sh_int[0] = (arrived == nblocks - 1) ? 1 : 0;
-    sh_int[1] = (int)g0;
+    bool ok = true;
+    if (arrived == nblocks - 1) {
+      st_relaxed(b.count, 0u);
+      red_add_release(b.gen, 1u);
+    } else {
+      ok = wait_generation(b, g0);
+    }
+    sh_int[0] = ok ? 0 : 1;
+    sh_int[1] = (int)(g0 & 1u);
   }
   __syncthreads();
+  const bool good = sh_int[0] == 0;
   double* sh_out = sh + 132;
-  if (sh_int[0]) {
-    if (warp == 0) {
-      // lane l sums value (l & 3) over rows (l >> 2) + 8 i, i = 0, 1, ...
-      const int j = l & 3;
-      constexpr int RU = 8;  // rows loaded before summing, for memory-level parallelism
-      double acc = 0.0;
-      for (unsigned int r0 = (unsigned int)(l >> 2); r0 < nblocks; r0 += 8u * RU) {
-        double buf[RU];
+  if (good && warp == 0) {
+    const double* part = sh_int[1] ? part1 : part0;
+    // lane l sums value (l & 3) over rows (l >> 2) + 8 i; RU rows per lane are loaded in one
+    // round (160 rows: a whole one-CTA-per-SM grid) and added as a fixed pairwise tree
+    const int j = l & 3;
+    constexpr int RU = 20;
+    double acc = 0.0;
+    for (unsigned int r0 = (unsigned int)(l >> 2); r0 < nblocks; r0 += 8u * RU) {
+      double buf[RU];
 #pragma unroll
-        for (int i = 0; i < RU; ++i) {
-          const unsigned int r = r0 + 8u * i;
-          buf[i] = r < nblocks ? __ldcg(part + (size_t)r * 4 + j) : 0.0;
-        }
+      for (int i = 0; i < RU; ++i) {
+        const unsigned int r = r0 + 8u * i;
+        buf[i] = r < nblocks ? __ldcg(part + (size_t)r * 4 + j) : 0.0;
+      }
 #pragma unroll
-        for (int i = 0; i < RU; ++i) acc += buf[i];
-      }
-      acc += __shfl_xor_sync(0xffffffffu, acc, 4);
-      acc += __shfl_xor_sync(0xffffffffu, acc, 8);
-      acc += __shfl_xor_sync(0xffffffffu, acc, 16);
-      if (l < 4) {
-        sh_out[l] = acc;
-        tot[l] = acc;
-      }
-      __syncwarp();
-      if (l == 0) {
-        st_relaxed(b.count, 0u);
-        red_add_release(b.gen, 1u);
-        sh_int[1] = 0;
-      }
+      for (int w = 1; w < RU; w *= 2)
+#pragma unroll
+        for (int i = 0; i + w < RU; i += 2 * w) buf[i] += buf[i + w];
+      acc += buf[0];
     }
-  } else if (threadIdx.x == 0) {
-    const bool ok = wait_generation(b, (unsigned int)sh_int[1]);
-#pragma unroll
-    for (int i = 0; i < 4; ++i) sh_out[i] = ok ? __ldcg(tot + i) : 0.0;
-    sh_int[1] = ok ? 0 : 1;
+    acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 8);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 16);
+    if (l < 4) sh_out[l] = acc;
   }
   __syncthreads();
 #pragma unroll
   for (int i = 0; i < 4; ++i) out[i] = sh_out[i];
-  const bool good = sh_int[1] == 0;
   __syncthreads();
   return good;
 }

@@ -1,6 +1,6 @@
 // Multi-right-hand-side PCG (one matrix, S right-hand sides) in one cooperative launch.
 // Used by the log-determinant / trace probes and by the spatial-VB step, whose N_s samples
-// share B~_SVB (Section 3.3: "the same pre-conditioner can be used for all samples").
+// all solve with the one matrix B~_SVB and so can share its preconditioner (Section 3.3).
 //
 // Work decomposition: the grid's warps are split into S x C units (right-hand side r, voxel
 // chunk c); lanes of a warp take consecutive voxels of the chunk, so every vector access is
@@ -18,13 +18,21 @@ namespace {
 
 constexpr int MRHS_THREADS = 256;
 
-template <typename T>
-__device__ __forceinline__ T ldc(const T* p) { return __ldcg(p); }
-
+// out = B v + s .* (deg v - sum of the neighbours' V), for voxel n.
+// All neighbour indices are loaded first and then all neighbour values, so that one group of
+// loads is in flight instead of a chain of dependent index -> value round trips (an absent
+// neighbour reads the voxel's own value, which is masked out). FP64 solves take the six
+// directions in two halves to bound the registers held.
+// Neighbour values go through L1: lanes of a warp share the lines of their +-x and +-y
+// neighbours. They were written by other CTAs before the last grid barrier, whose gpu-scope
+// acquire orders these loads after those writes.
 template <int D, typename T>
 __device__ __forceinline__ void block_apply(const MrhsArgs& a, const T* sc, int n, const T* v, const T* V, T* out) {
   const size_t ld = a.ld;
   const T* B = static_cast<const T*>(a.blocks);
+  int nb[6];
+#pragma unroll
+  for (int d = 0; d < 6; ++d) nb[d] = d < a.ndir ? __ldg(a.nbr + (size_t)d * ld + n) : -1;
 #pragma unroll
   for (int i = 0; i < D; ++i) {
     T acc = T(0);
@@ -36,12 +44,23 @@ __device__ __forceinline__ void block_apply(const MrhsArgs& a, const T* sc, int 
 #pragma unroll
   for (int k = 0; k < D; ++k) sum[k] = T(0);
   int deg = 0;
-  for (int d = 0; d < a.ndir; ++d) {
-    const int m = __ldg(a.nbr + (size_t)d * ld + n);
-    if (m >= 0) {
-      ++deg;
+  constexpr int H = sizeof(T) == 4 ? 6 : 3;   // directions per round of loads
 #pragma unroll
-      for (int k = 0; k < D; ++k) sum[k] += ldc(V + (size_t)k * ld + m);
+  for (int d0 = 0; d0 < 6; d0 += H) {
+    T nv[H][D];
+#pragma unroll
+    for (int h = 0; h < H; ++h) {
+      const int m = nb[d0 + h] >= 0 ? nb[d0 + h] : n;
+#pragma unroll
+      for (int k = 0; k < D; ++k) nv[h][k] = V[(size_t)k * ld + m];
+    }
+#pragma unroll
+    for (int h = 0; h < H; ++h) {
+      if (nb[d0 + h] >= 0) {
+        ++deg;
+#pragma unroll
+        for (int k = 0; k < D; ++k) sum[k] += nv[h][k];
+      }
     }
   }
 #pragma unroll
@@ -281,9 +300,10 @@ __global__ void __launch_bounds__(MRHS_THREADS, 2) k_mrhs(MrhsArgs a) {
   const size_t ld = a.ld;
   auto unit_rhs = [&](int u) { return u % U.S; };
   auto unit_chunk = [&](int u) { return u / U.S; };
-  auto write_partials = [&](int u, double* acc) {
+  // columns selected by `cols` (bit j = column j) of unit u's partial row
+  auto write_partials = [&](int u, double* acc, unsigned cols) {
     const double v = warp_reduce4(acc);
-    if ((U.lane & 7) == 0) a.part[(size_t)u * 4 + (U.lane >> 3)] = v;
+    if ((U.lane & 7) == 0 && ((cols >> (U.lane >> 3)) & 1u)) a.part[(size_t)u * 4 + (U.lane >> 3)] = v;
   };
   // mode-0 pass: r = b - B~ x, u = M^-1 r, publish u; then w = B~ u and partials
   // for every RHS selected by `sel` (state 1 on the first pass, 2 afterwards).
@@ -299,7 +319,7 @@ __global__ void __launch_bounds__(MRHS_THREADS, 2) k_mrhs(MrhsArgs a) {
       for (int n = c * U.csize + U.lane; n < n1; n += 32) {
         T xn[D], ax[D], rn[D], un[D];
 #pragma unroll
-        for (int k = 0; k < D; ++k) xn[k] = ldc(x + (size_t)k * ld + n);
+        for (int k = 0; k < D; ++k) xn[k] = x[(size_t)k * ld + n];
         block_apply<D, T>(a, sc, n, xn, x, ax);
 #pragma unroll
         for (int k = 0; k < D; ++k) rn[k] = __ldg(b + (size_t)k * ld + n) - ax[k];
@@ -350,7 +370,7 @@ __global__ void __launch_bounds__(MRHS_THREADS, 2) k_mrhs(MrhsArgs a) {
         }
       }
       double acc[4] = {ks[0].value(), ks[1].value(), ks[2].value(), ks[3].value()};
-      write_partials(u, acc);
+      write_partials(u, acc, 0xFu);
     }
     return true;
   };
@@ -361,9 +381,12 @@ __global__ void __launch_bounds__(MRHS_THREADS, 2) k_mrhs(MrhsArgs a) {
   while (any_active || any_pending) {
     if (any_active) {
       // local update of active right-hand sides
+      // local update of active right-hand sides, with the partials r'u and r'r of the
+      // updated vectors (columns 0 and 2 of the unit's row)
       for (int u = U.gw; u < U.units; u += U.nw) {
         const int r = unit_rhs(u), c = unit_chunk(u);
         if (__ldcg(&a.st[r].active) != 1) continue;
+        KSum<T> kg, kr;
         const T al = (T)__ldcg(&a.st[r].alpha), be = (T)__ldcg(&a.st[r].beta);
         T *x = Xv + (size_t)r * a.vs, *R = Rv + (size_t)r * a.vs, *Uu = UUv + (size_t)r * a.vs;
         T *P = PPv + (size_t)r * a.vs, *Sv = SSv + (size_t)r * a.vs;
@@ -379,6 +402,7 @@ __global__ void __launch_bounds__(MRHS_THREADS, 2) k_mrhs(MrhsArgs a) {
             rn[k] -= al * sk[k];
           }
           precond_apply<D, T>(a, n, rn, un);
+          T g = T(0), rr2 = T(0);
 #pragma unroll
           for (int k = 0; k < D; ++k) {
             const size_t o = (size_t)k * ld + n;
@@ -387,7 +411,11 @@ __global__ void __launch_bounds__(MRHS_THREADS, 2) k_mrhs(MrhsArgs a) {
             x[o] = xk[k];
             R[o] = rn[k];
             Uu[o] = un[k];
+            g += rn[k] * un[k];
+            rr2 += rn[k] * rn[k];
           }
+          kg.add(g);
+          kr.add(rr2);
         };
         if constexpr (kStaged<T>) {
           // The six vectors of the next group of 32 voxels stream into this warp's shared
@@ -447,40 +475,33 @@ __global__ void __launch_bounds__(MRHS_THREADS, 2) k_mrhs(MrhsArgs a) {
             update(n, un, pk, wk, sk, xk, rn);
           }
         }
+        double acc[4] = {kg.value(), 0.0, kr.value(), 0.0};
+        write_partials(u, acc, 0x5u);
       }
       if (!grid_sync(a.bar, &sh_flag)) return;
+      // w = B~ u and the partial w'u (column 1)
       for (int u = U.gw; u < U.units; u += U.nw) {
         const int r = unit_rhs(u), c = unit_chunk(u);
-        KSum<T> ks[3];
-        if (__ldcg(&a.st[r].active) == 1) {
-          const T* R = Rv + (size_t)r * a.vs;
-          const T* Uu = UUv + (size_t)r * a.vs;
-          T* Wv = WWv + (size_t)r * a.vs;
-          const int n1 = min(a.N, (c + 1) * U.csize);
-          for (int n = c * U.csize + U.lane; n < n1; n += 32) {
-            T un[D], wn[D], rk[D];
+        if (__ldcg(&a.st[r].active) != 1) continue;
+        KSum<T> kd;
+        const T* Uu = UUv + (size_t)r * a.vs;
+        T* Wv = WWv + (size_t)r * a.vs;
+        const int n1 = min(a.N, (c + 1) * U.csize);
+        for (int n = c * U.csize + U.lane; n < n1; n += 32) {
+          T un[D], wn[D];
 #pragma unroll
-            for (int k = 0; k < D; ++k) {
-              un[k] = Uu[(size_t)k * ld + n];
-              rk[k] = R[(size_t)k * ld + n];
-            }
-            block_apply<D, T>(a, sc, n, un, Uu, wn);
-            T g = T(0), dl = T(0), rr2 = T(0);
+          for (int k = 0; k < D; ++k) un[k] = Uu[(size_t)k * ld + n];
+          block_apply<D, T>(a, sc, n, un, Uu, wn);
+          T dl = T(0);
 #pragma unroll
-            for (int k = 0; k < D; ++k) {
-              g += rk[k] * un[k];
-              dl += wn[k] * un[k];
-              rr2 += rk[k] * rk[k];
-            }
-#pragma unroll
-            for (int k = 0; k < D; ++k) Wv[(size_t)k * ld + n] = wn[k];
-            ks[0].add(g);
-            ks[1].add(dl);
-            ks[2].add(rr2);
+          for (int k = 0; k < D; ++k) {
+            dl += wn[k] * un[k];
+            Wv[(size_t)k * ld + n] = wn[k];
           }
+          kd.add(dl);
         }
-        double acc[4] = {ks[0].value(), ks[1].value(), ks[2].value(), 0.0};
-        write_partials(u, acc);
+        double acc[4] = {0.0, kd.value(), 0.0, 0.0};
+        write_partials(u, acc, 0x2u);
       }
       if (!mrhs_reduce(a, U, 1, false, sh_int, &any_active, &any_pending)) return;
     } else {

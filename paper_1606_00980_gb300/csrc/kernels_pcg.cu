@@ -209,7 +209,7 @@ __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_res(PcgArgs a) {
       v[2] += r[k] * r[k];
       v[3] += bv[k] * bv[k];
     }
-    return grid_allreduce4(a.bar, a.part, a.tot, v, sh.red, sh.ints, tot);
+    return grid_allreduce4(a.bar, a.part, a.part1, v, sh.red, sh.ints, tot);
   };
 
   double tot[4];
@@ -249,7 +249,7 @@ __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_res(PcgArgs a) {
       v[1] += w[k] * u[k];
       v[2] += r[k] * r[k];
     }
-    if (!grid_allreduce4(a.bar, a.part, a.tot, v, sh.red, sh.ints, tot)) return;
+    if (!grid_allreduce4(a.bar, a.part, a.part1, v, sh.red, sh.ints, tot)) return;
     ++it;
     rr = tot[2];
     cg_scalar_step(sh, tot[0], tot[1], rr, tol2, it, a.max_iter, alpha, beta, gam);
@@ -359,7 +359,7 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_stream(PcgArgs a) {
         v[3] += bk * bk;
       }
     }
-    return grid_allreduce4(a.bar, a.part, a.tot, v, sh.red, sh.ints, tot);
+    return grid_allreduce4(a.bar, a.part, a.part1, v, sh.red, sh.ints, tot);
   };
 
   double tot[4];
@@ -431,7 +431,7 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_stream(PcgArgs a) {
 #pragma unroll
       for (int k = 0; k < D; ++k) Wv[(size_t)k * ld + n] = wn[k];
     }
-    if (!grid_allreduce4(a.bar, a.part, a.tot, v, sh.red, sh.ints, tot)) return;
+    if (!grid_allreduce4(a.bar, a.part, a.part1, v, sh.red, sh.ints, tot)) return;
     ++it;
     rr = tot[2];
     cg_scalar_step(sh, tot[0], tot[1], rr, tol2, it, a.max_iter, alpha, beta, gam);
@@ -525,7 +525,7 @@ __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_mixed_res(PcgArgs a)
         v[0] += r64[k] * r64[k];
         v[1] += bv[k] * bv[k];
       }
-      if (!grid_allreduce4(a.bar, a.part, a.tot, v, sh.red, sh.ints, tot)) return;
+      if (!grid_allreduce4(a.bar, a.part, a.part1, v, sh.red, sh.ints, tot)) return;
     }
     rr = tot[0];
     if (outer == 0) {
@@ -570,7 +570,7 @@ __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_mixed_res(PcgArgs a)
         q2 += r[k] * r[k];
       }
       double v[4] = {(double)g, (double)dl, (double)q2, 0.0};
-      if (!grid_allreduce4(a.bar, a.part, a.tot, v, sh.red, sh.ints, tot)) return;
+      if (!grid_allreduce4(a.bar, a.part, a.part1, v, sh.red, sh.ints, tot)) return;
     }
     double gam = tot[0], del = tot[1];
     if (!(del > 0.0) || !isfinite(del)) { status = isfinite(del) ? 3 : 7; break; }
@@ -600,7 +600,7 @@ __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_mixed_res(PcgArgs a)
         q2 += r[k] * r[k];
       }
       double v[4] = {(double)g, (double)dl, (double)q2, 0.0};
-      if (!grid_allreduce4(a.bar, a.part, a.tot, v, sh.red, sh.ints, tot)) return;
+      if (!grid_allreduce4(a.bar, a.part, a.part1, v, sh.red, sh.ints, tot)) return;
       ++it;
       const bool capped = it >= a.max_inner || inner_total + it >= a.max_iter;
       cg_scalar_step(sh, tot[0], tot[1], tot[2], itol2, capped ? 1 : 0, 1, alpha, beta, gam);
@@ -694,7 +694,7 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_mixed_stream(PcgArgs a) {
       v[1] += dl;
       v[2] += q2;
     }
-    return grid_allreduce4(a.bar, a.part, a.tot, v, sh.red, sh.ints, tot);
+    return grid_allreduce4(a.bar, a.part, a.part1, v, sh.red, sh.ints, tot);
   };
   double tot[4];
   int outer = 0, inner_total = 0, status = 0;
@@ -728,7 +728,7 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_mixed_stream(PcgArgs a) {
           a.s32[(size_t)k * ld + n] = 0.f;
         }
       }
-      if (!grid_allreduce4(a.bar, a.part, a.tot, v, sh.red, sh.ints, tot)) return;
+      if (!grid_allreduce4(a.bar, a.part, a.part1, v, sh.red, sh.ints, tot)) return;
     }
     rr = tot[0];
     if (outer == 0) {

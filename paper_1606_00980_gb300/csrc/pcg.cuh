@@ -39,8 +39,8 @@ struct PcgArgs {
   double* w;             // [D][ld] work (streaming variant)
   double* p;
   double* s;
-  double* part;          // [grid][4] reduction partials
-  double* tot;           // [4] reduction totals
+  double* part;          // [grid][4] reduction partials (even barrier generations)
+  double* part1;         // [grid][4] reduction partials (odd barrier generations)
   GridBarrier bar;
   PcgCtrl* ctrl;
   double delta;          // stop when ||b - B x|| <= delta ||b|| (true residual, FP64)

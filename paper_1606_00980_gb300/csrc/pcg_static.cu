@@ -99,7 +99,7 @@ size_t bfmri_pcg_static_bytes(size_t ld, int D) {
   if (ld < 1 || D < 1 || D > DMAX) return 0;
   const size_t lds = ld;
   const size_t rows = 4096;  // partial-sum rows: more than any cooperative grid can use
-  return align256(sizeof(PcgCtrl)) + 256 + align256((rows * 4 + 8) * sizeof(double)) +
+  return align256(sizeof(PcgCtrl)) + 256 + align256((rows * 8 + 8) * sizeof(double)) +
          align256((size_t)ntri(D) * lds * sizeof(double)) +
          5 * align256((size_t)D * lds * sizeof(double));
 }
@@ -132,7 +132,7 @@ bfmri_status bfmri_pcg_solve_static(int N, int D, int neighbourhood, const int* 
   int* bad = reinterpret_cast<int*>(p + 12);
   p += 256;
   double* part = reinterpret_cast<double*>(p);
-  p += align256((rows * 4 + 8) * sizeof(double));
+  p += align256((rows * 8 + 8) * sizeof(double));
   double* mfac = reinterpret_cast<double*>(p);
   p += align256((size_t)ntri(D) * lds * sizeof(double));
   double* vec[5];
@@ -164,7 +164,7 @@ bfmri_status bfmri_pcg_solve_static(int N, int D, int neighbourhood, const int* 
   a.p = vec[3];
   a.s = vec[4];
   a.part = part;
-  a.tot = part + rows * 4;
+  a.part1 = part + rows * 4;
   a.bar.count = bar;
   a.bar.gen = bar + 1;
   a.bar.err = errw;
