@@ -371,10 +371,28 @@ __device__ __forceinline__ bool grid_allreduce4(const GridBarrier& b, double* pa
   __syncthreads();
   const bool good = sh_int[0] == 0;
   double* sh_out = sh + 132;
-  if (good && warp == 0) {
-    const double* part = sh_int[1] ? part1 : part0;
-    // lane l sums value (l & 3) over rows (l >> 2) + 8 i; RU rows per lane are loaded in one
-    // round (160 rows: a whole one-CTA-per-SM grid) and added as a fixed pairwise tree
+  const double* part = sh_int[1] ? part1 : part0;
+  if (good && blockDim.x >= 128) {
+    // warp j < 4 sums value j: lane l over rows l + 32 i (5 rows per lane and round, as a
+    // fixed pairwise tree), then a butterfly; the four warps run on different SM sub-partitions
+    if (warp < 4) {
+      constexpr int RU = 5;
+      double acc = 0.0;
+      for (unsigned int r0 = (unsigned int)l; r0 < nblocks; r0 += 32u * RU) {
+        double buf[RU];
+#pragma unroll
+        for (int i = 0; i < RU; ++i) {
+          const unsigned int r = r0 + 32u * i;
+          buf[i] = r < nblocks ? __ldcg(part + (size_t)r * 4 + warp) : 0.0;
+        }
+        acc += ((buf[0] + buf[1]) + (buf[2] + buf[3])) + buf[4];
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (l == 0) sh_out[warp] = acc;
+    }
+  } else if (good && warp == 0) {
+    // lane l sums value (l & 3) over rows (l >> 2) + 8 i (20 rows per lane and round)
     const int j = l & 3;
     constexpr int RU = 20;
     double acc = 0.0;
@@ -395,6 +413,112 @@ __device__ __forceinline__ bool grid_allreduce4(const GridBarrier& b, double* pa
     acc += __shfl_xor_sync(0xffffffffu, acc, 8);
     acc += __shfl_xor_sync(0xffffffffu, acc, 16);
     if (l < 4) sh_out[l] = acc;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < 4; ++i) out[i] = sh_out[i];
+  __syncthreads();
+  return good;
+}
+
+// ---------------------------------------------------------------------------------------
+// Float-float (double-single) sums for the FP32 inner solves: a value is hi + lo with
+// |lo| <= ulp(hi) / 2, about 48 significant bits. Addition is Knuth's TwoSum of the leading
+// parts plus the trailing parts, renormalised by Dekker's FastTwoSum. Every step runs on
+// the FP32 pipe, whose dependent latency is a small fraction of an FP64 operation's on this
+// part, so reduction trees of these pairs finish far sooner than FP64 trees.
+// ---------------------------------------------------------------------------------------
+struct FF {
+  float hi, lo;
+};
+
+__device__ __forceinline__ FF ff_of(float x) { return FF{x, 0.f}; }
+
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+  const float s = a.hi + b.hi;
+  const float bv = s - a.hi;
+  const float e = (a.hi - (s - bv)) + (b.hi - bv);
+  const float t = (a.lo + b.lo) + e;
+  const float hi = s + t;
+  return FF{hi, t - (hi - s)};
+}
+
+__device__ __forceinline__ FF ff_shfl_xor(FF a, int o) {
+  return FF{__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
+}
+
+__device__ __forceinline__ double ff_to_double(FF a) { return (double)a.hi + (double)a.lo; }
+
+// Reducing grid barrier over 4 float-float values: the same protocol as grid_allreduce4
+// (rows alternating with the barrier generation, every CTA summing all rows in a fixed
+// order), with the block and cross-CTA sums done in float-float; totals are returned as
+// doubles. A row holds 4 (hi, lo) pairs, the size of a grid_allreduce4 row.
+__device__ __forceinline__ bool grid_allreduce4_ff(const GridBarrier& b, double* part0, double* part1,
+                                                   const FF* v, double* sh, int* sh_int, double* out) {
+  const int l = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwc = (blockDim.x + 31) >> 5;
+  float* shw = reinterpret_cast<float*>(sh);   // [warp][4][2] floats: 96 floats = 48 doubles
+  double* sh_out = sh + 132;
+  FF w4[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    w4[i] = v[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) w4[i] = ff_add(w4[i], ff_shfl_xor(w4[i], o));
+  }
+  if (l == 0) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      shw[(warp * 4 + i) * 2 + 0] = w4[i].hi;
+      shw[(warp * 4 + i) * 2 + 1] = w4[i].lo;
+    }
+  }
+  __syncthreads();
+  const unsigned int nblocks = gridDim.x;
+  if (warp == 0) {
+    FF c4[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      c4[i] = l < nwc ? FF{shw[(l * 4 + i) * 2 + 0], shw[(l * 4 + i) * 2 + 1]} : FF{0.f, 0.f};
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) c4[i] = ff_add(c4[i], ff_shfl_xor(c4[i], o));
+    }
+    if (l == 0) {
+      const unsigned int g0 = ld_acquire(b.gen);
+      float* row = reinterpret_cast<float*>((g0 & 1u) ? part1 : part0) + (size_t)blockIdx.x * 8;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        row[2 * i + 0] = c4[i].hi;
+        row[2 * i + 1] = c4[i].lo;
+      }
+      const unsigned int arrived = atom_add_acq_rel(b.count, 1u);
+      bool ok = true;
+      if (arrived == nblocks - 1) {
+        st_relaxed(b.count, 0u);
+        red_add_release(b.gen, 1u);
+      } else {
+        ok = wait_generation(b, g0);
+      }
+      sh_int[0] = ok ? 0 : 1;
+      sh_int[1] = (int)(g0 & 1u);
+    }
+  }
+  __syncthreads();
+  const bool good = sh_int[0] == 0;
+  const float* part = reinterpret_cast<const float*>(sh_int[1] ? part1 : part0);
+  // warp j < 4 (warp 0 for all four when the CTA has fewer warps) sums value j over the rows
+  const int nsum = nwc >= 4 ? 4 : 1;
+  if (good && warp < nsum) {
+    for (int j = warp; j < 4; j += nsum) {
+      FF acc{0.f, 0.f};
+      for (unsigned int r = (unsigned int)l; r < nblocks; r += 32u) {
+        const float2 p = __ldcg(reinterpret_cast<const float2*>(part + (size_t)r * 8 + 2 * j));
+        acc = ff_add(acc, FF{p.x, p.y});
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc = ff_add(acc, ff_shfl_xor(acc, o));
+      if (l == 0) sh_out[j] = ff_to_double(acc);
+    }
   }
   __syncthreads();
 #pragma unroll

@@ -18,7 +18,9 @@
 //    factor are staged once in shared memory and all vectors stay in registers, so an
 //    iteration only exchanges u through L2;
 //  * streaming: any N; vectors live in global memory (structure of arrays).
-// All reductions are fixed-order (grid_allreduce4), so a solve is bit-reproducible.
+// All reductions are fixed-order, so a solve is bit-reproducible: FP64 sums (grid_allreduce4)
+// for the FP64 solves and the outer residuals of the mixed solves, float-float sums
+// (grid_allreduce4_ff) for the FP32 inner iterations of the mixed solves.
 #include "pcg.cuh"
 
 namespace bfmri {
@@ -95,39 +97,66 @@ struct Shared {
   int code;         // broadcast control code
 };
 
+// Reciprocal by Newton-Raphson refinement, x <- x + x (1 - d x), of the hardware's
+// approximate FP64 reciprocal: each step squares the relative error, and two steps bring the
+// approximation's error to the FP64 rounding level. The CG scalars need no correctly
+// rounded quotient, and this is a short dependent chain on the one thread that runs it.
+__device__ __forceinline__ double recip_nr(double d) {
+  double x;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(x) : "d"(d));
+  double e = fma(-d, x, 1.0);
+  x = fma(x, e, x);
+  e = fma(-d, x, 1.0);
+  return fma(x, e, x);
+}
+
+// 1/gamma and 1/alpha = delta/gamma for a (re)started recurrence with alpha = gamma/delta.
+__device__ __forceinline__ void cg_recips(double gam, double del, double& rgam, double& ralpha) {
+  rgam = gam > 0.0 ? recip_nr(gam) : 0.0;
+  ralpha = del * rgam;
+}
+
 // One CG step of the scalar recurrence (Chronopoulos & Gear), evaluated by thread 0 of each
-// CTA and broadcast through shared memory: FP64 division is a long instruction sequence on
-// this part, so it is not repeated by every thread. Returns in sh.code: 0 continue,
-// 1 check the true residual, 3 breakdown, 7 non-finite.
+// CTA and broadcast through shared memory. With 1/gamma_old and 1/alpha_old kept from the
+// previous step, the critical path holds a single reciprocal (of the new denominator);
+// the reciprocals for the next step are formed after the broadcast, while the other threads
+// move on. Returns in sh.code: 0 continue, 1 check the true residual, 3 breakdown,
+// 7 non-finite.
 __device__ __forceinline__ void cg_scalar_step(Shared& sh, double gnew, double dnew, double rr,
                                                double tol2, int it, int max_iter, double& alpha,
-                                               double& beta, double& gam) {
+                                               double& beta, double& gam, double& rgam,
+                                               double& ralpha) {
   if (threadIdx.x == 0) {
     int code = 0;
-    double a = alpha, b = beta, g = gam;
+    double a = alpha, b = beta, g = gam, den = 0.0;
     if (!(isfinite(gnew) && isfinite(dnew) && isfinite(rr))) {
       code = 7;
     } else if (rr <= tol2 || it >= max_iter) {
       code = 1;
     } else {
-      b = gnew / g;
-      const double den = dnew - b * gnew / a;
+      b = gnew * rgam;
+      den = fma(-(b * gnew), ralpha, dnew);
       if (!(den > 0.0)) {
         code = 3;
       } else {
-        a = gnew / den;
+        a = gnew * recip_nr(den);
         g = gnew;
       }
     }
     sh.scal[0] = a;
     sh.scal[1] = b;
     sh.scal[2] = g;
+    sh.scal[3] = den;
     sh.code = code;
   }
   __syncthreads();
   alpha = sh.scal[0];
   beta = sh.scal[1];
   gam = sh.scal[2];
+  if (threadIdx.x == 0 && sh.code == 0) {
+    rgam = recip_nr(gam);
+    ralpha = sh.scal[3] * rgam;
+  }
 }
 
 __device__ __forceinline__ void write_ctrl(const PcgArgs& a, int it, int restarts, double rr,
@@ -226,6 +255,8 @@ __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_res(PcgArgs a) {
   }
   bool done = status != 0 || bb == 0.0 || rr <= tol2;
   double alpha = (del > 0.0) ? gam / del : 0.0, beta = 0.0;
+  double rgam = 0.0, ralpha = 0.0;
+  cg_recips(gam, del, rgam, ralpha);
   if (!done && !(del > 0.0)) { status = 3; done = true; }
   while (!done) {
 #pragma unroll
@@ -252,7 +283,7 @@ __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_res(PcgArgs a) {
     if (!grid_allreduce4(a.bar, a.part, a.part1, v, sh.red, sh.ints, tot)) return;
     ++it;
     rr = tot[2];
-    cg_scalar_step(sh, tot[0], tot[1], rr, tol2, it, a.max_iter, alpha, beta, gam);
+    cg_scalar_step(sh, tot[0], tot[1], rr, tol2, it, a.max_iter, alpha, beta, gam, rgam, ralpha);
     const int code = sh.code;
     __syncthreads();
     if (code == 7) { status = 7; break; }
@@ -273,6 +304,7 @@ __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_res(PcgArgs a) {
       ++restarts;
       alpha = del > 0.0 ? gam / del : 0.0;
       beta = 0.0;
+      cg_recips(gam, del, rgam, ralpha);
 #pragma unroll
       for (int k = 0; k < D; ++k) { p[k] = 0.0; q[k] = 0.0; }
       if (!(del > 0.0)) { status = 3; break; }
@@ -377,6 +409,8 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_stream(PcgArgs a) {
   }
   bool done = status != 0 || bb == 0.0 || rr <= tol2;
   double alpha = (del > 0.0) ? gam / del : 0.0, beta = 0.0;
+  double rgam = 0.0, ralpha = 0.0;
+  cg_recips(gam, del, rgam, ralpha);
   if (!done && !(del > 0.0)) { status = 3; done = true; }
   while (!done) {
     for (int n = tid; n < a.N; n += nth) {
@@ -434,7 +468,7 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_stream(PcgArgs a) {
     if (!grid_allreduce4(a.bar, a.part, a.part1, v, sh.red, sh.ints, tot)) return;
     ++it;
     rr = tot[2];
-    cg_scalar_step(sh, tot[0], tot[1], rr, tol2, it, a.max_iter, alpha, beta, gam);
+    cg_scalar_step(sh, tot[0], tot[1], rr, tol2, it, a.max_iter, alpha, beta, gam, rgam, ralpha);
     const int code = sh.code;
     __syncthreads();
     if (code == 7) { status = 7; break; }
@@ -450,6 +484,7 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_stream(PcgArgs a) {
       ++restarts;
       alpha = del > 0.0 ? gam / del : 0.0;
       beta = 0.0;
+      cg_recips(gam, del, rgam, ralpha);
       if (!(del > 0.0)) { status = 3; break; }
       continue;
     }
@@ -569,12 +604,14 @@ __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_mixed_res(PcgArgs a)
         dl += w[k] * u[k];
         q2 += r[k] * r[k];
       }
-      double v[4] = {(double)g, (double)dl, (double)q2, 0.0};
-      if (!grid_allreduce4(a.bar, a.part, a.part1, v, sh.red, sh.ints, tot)) return;
+      const FF v[4] = {ff_of(g), ff_of(dl), ff_of(q2), ff_of(0.f)};
+      if (!grid_allreduce4_ff(a.bar, a.part, a.part1, v, sh.red, sh.ints, tot)) return;
     }
     double gam = tot[0], del = tot[1];
     if (!(del > 0.0) || !isfinite(del)) { status = isfinite(del) ? 3 : 7; break; }
     double alpha = gam / del, beta = 0.0;
+    double rgam = 0.0, ralpha = 0.0;
+    cg_recips(gam, del, rgam, ralpha);
     int it = 0;
     while (true) {
       const float fa = (float)alpha, fb = (float)beta;
@@ -599,11 +636,11 @@ __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_mixed_res(PcgArgs a)
         dl += w[k] * u[k];
         q2 += r[k] * r[k];
       }
-      double v[4] = {(double)g, (double)dl, (double)q2, 0.0};
-      if (!grid_allreduce4(a.bar, a.part, a.part1, v, sh.red, sh.ints, tot)) return;
+      const FF v[4] = {ff_of(g), ff_of(dl), ff_of(q2), ff_of(0.f)};
+      if (!grid_allreduce4_ff(a.bar, a.part, a.part1, v, sh.red, sh.ints, tot)) return;
       ++it;
       const bool capped = it >= a.max_inner || inner_total + it >= a.max_iter;
-      cg_scalar_step(sh, tot[0], tot[1], tot[2], itol2, capped ? 1 : 0, 1, alpha, beta, gam);
+      cg_scalar_step(sh, tot[0], tot[1], tot[2], itol2, capped ? 1 : 0, 1, alpha, beta, gam, rgam, ralpha);
       const int code = sh.code;
       __syncthreads();
       if (code == 7) { status = 7; break; }
@@ -670,7 +707,7 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_mixed_stream(PcgArgs a) {
   };
   // inner matvec phase: w = B~ u and the three partial sums
   auto matvec_partials = [&](double* tot) -> bool {
-    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    FF v[4] = {ff_of(0.f), ff_of(0.f), ff_of(0.f), ff_of(0.f)};
     for (int n = tid; n < a.N; n += nth) {
       int nb[6];
       load_nb(n, nb);
@@ -690,11 +727,11 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_mixed_stream(PcgArgs a) {
       }
 #pragma unroll
       for (int k = 0; k < D; ++k) a.w32[(size_t)k * ld + n] = wn[k];
-      v[0] += g;
-      v[1] += dl;
-      v[2] += q2;
+      v[0] = ff_add(v[0], ff_of(g));
+      v[1] = ff_add(v[1], ff_of(dl));
+      v[2] = ff_add(v[2], ff_of(q2));
     }
-    return grid_allreduce4(a.bar, a.part, a.part1, v, sh.red, sh.ints, tot);
+    return grid_allreduce4_ff(a.bar, a.part, a.part1, v, sh.red, sh.ints, tot);
   };
   double tot[4];
   int outer = 0, inner_total = 0, status = 0;
@@ -754,6 +791,8 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_mixed_stream(PcgArgs a) {
     double gam = tot[0], del = tot[1];
     if (!(del > 0.0) || !isfinite(del)) { status = isfinite(del) ? 3 : 7; break; }
     double alpha = gam / del, beta = 0.0;
+    double rgam = 0.0, ralpha = 0.0;
+    cg_recips(gam, del, rgam, ralpha);
     int it = 0;
     while (true) {
       const float fa = (float)alpha, fb = (float)beta;
@@ -791,7 +830,7 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_mixed_stream(PcgArgs a) {
       if (!matvec_partials(tot)) return;
       ++it;
       const bool capped = it >= a.max_inner || inner_total + it >= a.max_iter;
-      cg_scalar_step(sh, tot[0], tot[1], tot[2], itol2, capped ? 1 : 0, 1, alpha, beta, gam);
+      cg_scalar_step(sh, tot[0], tot[1], tot[2], itol2, capped ? 1 : 0, 1, alpha, beta, gam, rgam, ralpha);
       const int code = sh.code;
       __syncthreads();
       if (code == 7) { status = 7; break; }
