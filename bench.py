@@ -280,9 +280,11 @@ def run_ours(args, world, rank, local):
 
     # the same chain with the mixed-precision solver (FP32 inner, FP64 refinement, same delta)
     mixed = run_mixed(args, w, flush, stream) if not args.no_mixed else None
-    del flush
 
+    # independent chains of the same subject advanced together (one multi-RHS launch per solve)
+    chains = run_chains(args, w, flush, stream, value) if not args.no_chains else None
     # end to end through the C ABI with host buffers
+    del flush
     e2e = run_e2e(args, w) if rank == 0 else None
     serving = run_serving(args) if (rank == 0 and not args.no_serving) else None
     batched = run_batched(args) if (rank == 0 and not args.no_batched) else None
@@ -303,7 +305,7 @@ def run_ours(args, world, rank, local):
                            "pcg_iterations_W_per_sweep": it_w / args.steps,
                            "pcg_iterations_A_per_sweep": it_a / args.steps},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-                "mixed_precision": mixed, "serving": serving, "batched_probes": batched,
+                "mixed_precision": mixed, "grouped_chains": chains, "serving": serving, "batched_probes": batched,
                 "gpu_launches": int(n_launch),
                 "kernel_ms_per_step": {k: v["ms"] / args.steps for k, v in tim.items() if v["launches"]}}
         print(json.dumps(line), flush=True)
@@ -357,6 +359,51 @@ def run_mixed(args, w, flush, stream):
             "delta": 1e-8, "inner_tol": 1e-6,
             "inner_iterations_W_per_sweep": it_w / args.steps,
             "kernel_ms_per_step": {k: v["ms"] / args.steps for k, v in tim.items() if v["launches"]}}
+
+
+def run_chains(args, w, flush, stream, single_value, n_chains=8):
+    """n_chains independent chains of the headline workload (seeds 3000 + c), FP64 and
+    delta 1e-8 as the headline, advanced by bfmri_gibbs_sweep_group: per sweep step every
+    chain's W (then A) system is solved by one multi-RHS launch with a matrix per chain.
+    Timed like the headline (CUDA events on the library's stream, L2 flushed between group
+    sweeps); value = W-draws/s over all chains."""
+    import torch
+
+    from paper_1606_00980_gb300.bfmri import Model, gibbs_sweep_group
+    models = []
+    for c in range(n_chains):
+        m = Model.from_workload(w, delta=1e-8, seed=3000 + c)
+        m.precompute_stats()
+        models.append(m)
+    counter = 0
+    for _ in range(args.warmup):
+        gibbs_sweep_group(models, 1, counter)
+        counter += 1
+    torch.cuda.synchronize()
+    times = []
+    it_w = it_a = 0
+    for _ in range(args.steps):
+        flush.random_(0, 255)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        infos = gibbs_sweep_group(models, 1, counter)
+        e1.record(stream)
+        counter += 1
+        times.append((e0, e1))
+        it_w += sum(i.pcg_iterations_W for i in infos)
+        it_a += sum(i.pcg_iterations_A for i in infos)
+    torch.cuda.synchronize()
+    tot = sum(a.elapsed_time(b) for a, b in times) / 1e3
+    for m in models:
+        m.close()
+    value = n_chains * args.steps / tot
+    return {"chains": n_chains, "value": value, "unit": UNIT,
+            "ms_per_group_sweep": tot / args.steps * 1e3,
+            "pcg_iterations_W_per_chain_sweep": it_w / (n_chains * args.steps),
+            "pcg_iterations_A_per_chain_sweep": it_a / (n_chains * args.steps),
+            "vs_single_chain": value / single_value if single_value else None,
+            "delta": 1e-8, "dtype": "f64"}
 
 
 def mrhs_bytes_per_voxel_iter_rhs(D, S, w=4):
@@ -530,6 +577,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--probes", type=int, default=64)
     ap.add_argument("--no-svb", action="store_true")
+    ap.add_argument("--no-chains", action="store_true")
     ap.add_argument("--only-batched", action="store_true",
                     help="run only the batched-probe measurement (profiling entry point)")
     ap.add_argument("--serving-requests", type=int, default=96)

@@ -200,6 +200,23 @@ bfmri_status bfmri_sample_beta(bfmri_handle* h, uint64_t counter, double* beta_o
 bfmri_status bfmri_gibbs_sweep(bfmri_handle* h, int n_sweeps, uint64_t first_counter,
                                bfmri_sweep_info* info);
 
+/* n independent chains advanced together, each by n_sweeps Gibbs sweeps of Section 3.2
+ * (the chains are the handles hs[0..n-1], each with its own state and seed, so their draws
+ * are independent). Each sweep step runs for every chain; the n W systems (one matrix per
+ * chain) are solved by one cooperative multi-right-hand-side PCG launch, which shares its
+ * barriers and reductions among the chains, and likewise the n A systems under the spatial
+ * AR prior. Chain c's draws follow the same equations, random numbers and stop rule
+ * (relative residual <= delta, confirmed by the true residual) as bfmri_gibbs_sweep on
+ * hs[c]; they agree with it to the solver tolerance, not bitwise.
+ * Requirements: 1 <= n <= 64; all handles on one lattice and mask, with equal K, P, AR
+ * prior, delta and max_iter, FP64 precision, statistics precomputed, on the current device.
+ * All work runs on hs[0]'s stream; the call returns when it has finished.
+ * info: [n] per-chain results (may be NULL). hs and info are host arrays the caller owns.
+ * Errors: INVALID_ARG (mismatched or bad handles), STATE, NOT_SPD, NOT_CONVERGED, TIMEOUT,
+ * CUDA; on error the states of all n chains are unspecified. */
+bfmri_status bfmri_gibbs_sweep_group(bfmri_handle* const* hs, int n, int n_sweeps,
+                                     uint64_t first_counter, bfmri_sweep_info* info);
+
 /* Log-determinant and trace probes of the W (which = 0) or A (which = 1) full-conditional
  * precision B~ at the current state. The paper leaves the log-determinant to future work
  * (Discussion: model evidence, collapsed alpha); this is stochastic Lanczos quadrature:

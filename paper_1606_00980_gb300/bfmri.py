@@ -111,6 +111,7 @@ SIGNATURES = [
     ("bfmri_sample_alpha", C.c_int, [_h, C.c_uint64, _dp]),
     ("bfmri_sample_beta", C.c_int, [_h, C.c_uint64, _dp]),
     ("bfmri_gibbs_sweep", C.c_int, [_h, C.c_int, C.c_uint64, _P(bfmri_sweep_info)]),
+    ("bfmri_gibbs_sweep_group", C.c_int, [_P(_h), C.c_int, C.c_int, C.c_uint64, _P(bfmri_sweep_info)]),
     ("bfmri_logdet_probe", C.c_int, [_h, C.c_int, C.c_int, C.c_int, C.c_uint64, _dp, _dp, _dp, _dp,
                                      _P(C.c_int)]),
     ("bfmri_lanczos_log_quadrature", C.c_int, [C.c_int, _dp, _dp, _dp]),
@@ -319,6 +320,20 @@ def bfmri_pcg_solve_static(N, D, neighbourhood, nbr_ptr, ld, blocks_ptr, scale_p
                                                C.byref(info))
     _check(st, None)
     return info
+
+
+def gibbs_sweep_group(models, n_sweeps, first_counter=0):
+    """Advances the chains of `models` (Model objects on one lattice and mask) together by
+    n_sweeps Gibbs sweeps, their W and A systems solved as one multi-RHS launch per step
+    (bfmri_gibbs_sweep_group); returns one bfmri_sweep_info per chain."""
+    lib = load_library()
+    n = len(models)
+    hs = (_h * n)(*[m.handle for m in models])
+    infos = (bfmri_sweep_info * n)()
+    st = lib.bfmri_gibbs_sweep_group(hs, n, n_sweeps, first_counter, infos)
+    if st != BFMRI_OK:
+        _check(st, models[0].handle)
+    return list(infos)
 
 
 def lanczos_log_quadrature(cg_alpha, cg_beta):

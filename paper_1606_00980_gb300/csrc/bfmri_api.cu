@@ -62,6 +62,11 @@ struct bfmri_handle {
   int part_rows = 0;
   std::vector<double> Sxx;
   int stride[3] = {1, 1, 1};
+  uint64_t mask_hash = 0;   // identity of the mask (FNV-1a of the in-mask lattice indices)
+  // grouped chains: per-chain operator tables [2][cap] and tallies [2][cap]
+  MrhsRhsPtrs* d_gtab = nullptr;
+  MrhsTally* d_gtally = nullptr;
+  int g_cap = 0;
   // multi-right-hand-side workspace, grown on demand
   int mr_S = 0, mr_D = 0, mr_hist_len = 0, mr_units = 0;
   size_t mr_vs = 0;
@@ -97,6 +102,12 @@ bfmri_status fail(bfmri_handle* h, bfmri_status code, const std::string& msg) {
 bfmri_status cuda_fail(bfmri_handle* h, cudaError_t e, const char* where) {
   return fail(h, BFMRI_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
+
+#define RET(x)                          \
+  do {                                  \
+    bfmri_status s_ = (x);              \
+    if (s_ != BFMRI_OK) return s_;      \
+  } while (0)
 
 #define CU(h, call)                                    \
   do {                                                 \
@@ -335,7 +346,8 @@ AssembleArgs assemble_args(bfmri_handle* h, const double* scale, uint64_t counte
 }
 
 // --- the five steps of a sweep, enqueued without synchronisation ---
-bfmri_status enqueue_W(bfmri_handle* h, uint64_t counter) {
+// W system of the current state with perturbed right-hand side (Algorithm 2, steps 1-6).
+bfmri_status assemble_W(bfmri_handle* h, uint64_t counter) {
   AssembleArgs a = assemble_args(h, h->d_alpha, counter, TAG_W);
   cudaError_t e;
   {
@@ -345,10 +357,17 @@ bfmri_status enqueue_W(bfmri_handle* h, uint64_t counter) {
     if (e == cudaSuccess) e = launch_assemble_w(a, h->stream);
   }
   if (e != cudaSuccess) return cuda_fail(h, e, "assemble_w");
+  return BFMRI_OK;
+}
+
+bfmri_status enqueue_W(bfmri_handle* h, uint64_t counter) {
+  RET(assemble_W(h, counter));
   return run_pcg(h, h->K, h->d_alpha, h->d_W, 0);
 }
 
-bfmri_status enqueue_A(bfmri_handle* h, uint64_t counter) {
+// A system (spatial prior) or the per-voxel A draw (independent prior, or the lagged Gram
+// alone when P = 0).
+bfmri_status assemble_A(bfmri_handle* h, uint64_t counter) {
   AssembleArgs a = assemble_args(h, h->d_beta, counter, TAG_A);
   const bool spatial = h->opt.ar_prior == BFMRI_AR_SPATIAL;
   if (h->P == 0) {
@@ -368,7 +387,12 @@ bfmri_status enqueue_A(bfmri_handle* h, uint64_t counter) {
     if (e == cudaSuccess) e = launch_assemble_a(a, h->stream);
   }
   if (e != cudaSuccess) return cuda_fail(h, e, "assemble_a");
-  if (h->P > 0 && spatial) return run_pcg(h, h->P, h->d_beta, h->d_A, 1);
+  return BFMRI_OK;
+}
+
+bfmri_status enqueue_A(bfmri_handle* h, uint64_t counter) {
+  RET(assemble_A(h, counter));
+  if (h->P > 0 && h->opt.ar_prior == BFMRI_AR_SPATIAL) return run_pcg(h, h->P, h->d_beta, h->d_A, 1);
   return BFMRI_OK;
 }
 
@@ -527,12 +551,6 @@ void fill_info(bfmri_solve_info* info, const PcgCtrl& c) {
 
 }  // namespace
 
-#define RET(x)                          \
-  do {                                  \
-    bfmri_status s_ = (x);              \
-    if (s_ != BFMRI_OK) return s_;      \
-  } while (0)
-
 extern "C" {
 
 void bfmri_default_options(bfmri_options* o) {
@@ -623,6 +641,13 @@ bfmri_status bfmri_create(const bfmri_lattice* lat, const uint8_t* mask, const d
 
   bfmri_handle* h = new bfmri_handle();
   h->opt = o;
+  h->mask_hash = 1469598103934665603ull;
+  for (int l : lin) {
+    for (int byte = 0; byte < 4; ++byte) {
+      h->mask_hash ^= (uint64_t)(((unsigned)l >> (8 * byte)) & 0xFFu);
+      h->mask_hash *= 1099511628211ull;
+    }
+  }
   h->nx = lat->nx;
   h->ny = lat->ny;
   h->nz = lat->nz;
@@ -942,6 +967,122 @@ bfmri_status bfmri_gibbs_sweep(bfmri_handle* h, int n_sweeps, uint64_t first_cou
     info->gamma_exhausted = exhausted;
   }
   return st;
+}
+
+bfmri_status bfmri_gibbs_sweep_group(bfmri_handle* const* hs, int n, int n_sweeps,
+                                     uint64_t first_counter, bfmri_sweep_info* info) {
+  if (!hs || n < 1 || n > 64 || n_sweeps < 0) {
+    set_global_error("bfmri_gibbs_sweep_group: need 1 <= n <= 64 handles and n_sweeps >= 0");
+    return BFMRI_ERR_INVALID_ARG;
+  }
+  for (int c = 0; c < n; ++c) {
+    if (!hs[c]) {
+      set_global_error("bfmri_gibbs_sweep_group: NULL handle");
+      return BFMRI_ERR_INVALID_ARG;
+    }
+    for (int d = 0; d < c; ++d)
+      if (hs[d] == hs[c]) return fail(hs[0], BFMRI_ERR_INVALID_ARG, "a handle appears twice in the group");
+  }
+  bfmri_handle* h0 = hs[0];
+  for (int c = 0; c < n; ++c) {
+    RET(require_stats(hs[c]));
+    const bfmri_handle* h = hs[c];
+    if (h->nx != h0->nx || h->ny != h0->ny || h->nz != h0->nz || h->ndir != h0->ndir ||
+        h->N != h0->N || h->ld != h0->ld || h->mask_hash != h0->mask_hash)
+      return fail(h0, BFMRI_ERR_INVALID_ARG, "grouped chains must share one lattice and mask");
+    if (h->K != h0->K || h->P != h0->P || h->opt.ar_prior != h0->opt.ar_prior ||
+        h->opt.delta != h0->opt.delta || h->opt.max_iter != h0->opt.max_iter ||
+        h->opt.precond != h0->opt.precond)
+      return fail(h0, BFMRI_ERR_INVALID_ARG,
+                  "grouped chains must share K, P, the AR prior, delta, max_iter and the preconditioner");
+    if (h->opt.precision != BFMRI_PREC_FP64)
+      return fail(h0, BFMRI_ERR_INVALID_ARG, "grouped chains solve in FP64 precision only");
+  }
+  if (info)
+    for (int c = 0; c < n; ++c) info[c] = bfmri_sweep_info{};
+  if (n_sweeps == 0) return BFMRI_OK;
+  const int K = h0->K, P = h0->P;
+  const bool spatial_A = P > 0 && h0->opt.ar_prior == BFMRI_AR_SPATIAL;
+  RET(ensure_mrhs(h0, std::max(K, P), n, 0));
+  if (h0->g_cap < n) {
+    dfree(h0, h0->d_gtab);
+    dfree(h0, h0->d_gtally);
+    h0->g_cap = 0;
+    h0->d_gtab = (MrhsRhsPtrs*)dalloc(h0, 2 * (size_t)n * sizeof(MrhsRhsPtrs));
+    h0->d_gtally = (MrhsTally*)dalloc(h0, 2 * (size_t)n * sizeof(MrhsTally));
+    if (!h0->d_gtab || !h0->d_gtally) return fail(h0, BFMRI_ERR_OOM, "group table allocation failed");
+    h0->g_cap = n;
+  }
+  const bool pre = h0->opt.precond == BFMRI_PRECOND_BLOCK_JACOBI;
+  std::vector<MrhsRhsPtrs> tab(2 * (size_t)n);
+  for (int c = 0; c < n; ++c) {
+    bfmri_handle* h = hs[c];
+    tab[c] = MrhsRhsPtrs{h->d_blocks, pre ? h->d_mfac : nullptr, h->d_alpha, h->d_rhs, h->d_W};
+    tab[n + c] = MrhsRhsPtrs{h->d_blocks, pre ? h->d_mfac : nullptr, h->d_beta, h->d_rhs, h->d_A};
+  }
+  cudaStream_t st0 = h0->stream;
+  CU(h0, cudaMemcpyAsync(h0->d_gtab, tab.data(), tab.size() * sizeof(MrhsRhsPtrs), cudaMemcpyHostToDevice, st0));
+  CU(h0, cudaMemsetAsync(h0->d_gtally, 0, 2 * (size_t)n * sizeof(MrhsTally), st0));
+  // every chain's work goes to the first handle's stream for the duration of the call
+  std::vector<cudaStream_t> saved((size_t)n);
+  for (int c = 0; c < n; ++c) {
+    saved[c] = hs[c]->stream;
+    hs[c]->stream = st0;
+  }
+  auto solve = [&](int D, int which) -> bfmri_status {
+    MrhsArgs m = mrhs_args(h0, D, n, nullptr, h0->opt.max_iter, false);
+    m.tab = h0->d_gtab + (size_t)which * n;
+    m.tally = h0->d_gtally + (size_t)which * n;
+    m.blocks = nullptr;
+    m.mfac = nullptr;
+    m.b = nullptr;
+    m.x = nullptr;
+    Timed tm(h0, which == 0 ? BFMRI_T_PCG_W : BFMRI_T_PCG_A);
+    const cudaError_t e = launch_mrhs(D, m, st0, nullptr);
+    if (e != cudaSuccess) return cuda_fail(h0, e, "grouped multi-RHS PCG");
+    return BFMRI_OK;
+  };
+  bfmri_status st = BFMRI_OK;
+  for (int c = 0; c < n && st == BFMRI_OK; ++c) st = begin_call(hs[c]);
+  for (int sw = 0; sw < n_sweeps && st == BFMRI_OK; ++sw) {
+    const uint64_t cnt = first_counter + (uint64_t)sw;
+    for (int c = 0; c < n && st == BFMRI_OK; ++c) st = assemble_W(hs[c], cnt);
+    if (st == BFMRI_OK) st = solve(K, 0);
+    for (int c = 0; c < n && st == BFMRI_OK; ++c) st = assemble_A(hs[c], cnt);
+    if (st == BFMRI_OK && spatial_A) st = solve(P, 1);
+    for (int c = 0; c < n && st == BFMRI_OK; ++c) {
+      bfmri_handle* h = hs[c];
+      st = enqueue_lambda(h, cnt);
+      if (st == BFMRI_OK) st = enqueue_hyper(h, cnt, false);
+      if (st == BFMRI_OK && spatial_A) st = enqueue_hyper(h, cnt, true);
+    }
+  }
+  std::vector<int> exhausted((size_t)n, 0);
+  for (int c = 0; c < n; ++c) {
+    const bfmri_status sc = end_call(hs[c], nullptr, &exhausted[c]);
+    if (st == BFMRI_OK) st = sc;
+  }
+  for (int c = 0; c < n; ++c) hs[c]->stream = saved[c];
+  if (st != BFMRI_OK) return st;
+  std::vector<MrhsTally> tally(2 * (size_t)n);
+  CU(h0, cudaMemcpy(tally.data(), h0->d_gtally, tally.size() * sizeof(MrhsTally), cudaMemcpyDeviceToHost));
+  for (int c = 0; c < n; ++c) {
+    if (info) {
+      info[c].sweeps = n_sweeps;
+      info[c].pcg_iterations_W = tally[c].iters;
+      info[c].pcg_iterations_A = spatial_A ? tally[n + c].iters : 0;
+      info[c].last_rel_residual_W = tally[c].rel_res;
+      info[c].gamma_exhausted = exhausted[c];
+    }
+    for (int w = 0; w < (spatial_A ? 2 : 1); ++w) {
+      const int code = tally[(size_t)w * n + c].status_any;
+      const std::string who = "chain " + std::to_string(c) + (w ? " (A)" : " (W)");
+      if (code == 4) return fail(h0, BFMRI_ERR_NOT_CONVERGED, "PCG reached max_iter in " + who);
+      if (code == 3) return fail(h0, BFMRI_ERR_NOT_SPD, "PCG breakdown (p'Bp <= 0) in " + who);
+      if (code == 7) return fail(h0, BFMRI_ERR_INVALID_ARG, "non-finite value in PCG of " + who);
+    }
+  }
+  return BFMRI_OK;
 }
 
 bfmri_status bfmri_get_timing(bfmri_handle* h, bfmri_timing* t) {

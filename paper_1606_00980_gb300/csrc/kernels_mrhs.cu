@@ -27,9 +27,9 @@ constexpr int MRHS_THREADS = 256;
 // neighbours. They were written by other CTAs before the last grid barrier, whose gpu-scope
 // acquire orders these loads after those writes.
 template <int D, typename T>
-__device__ __forceinline__ void block_apply(const MrhsArgs& a, const T* sc, int n, const T* v, const T* V, T* out) {
+__device__ __forceinline__ void block_apply(const MrhsArgs& a, const T* B, const T* sc, int n, const T* v,
+                                            const T* V, T* out) {
   const size_t ld = a.ld;
-  const T* B = static_cast<const T*>(a.blocks);
   int nb[6];
 #pragma unroll
   for (int d = 0; d < 6; ++d) nb[d] = d < a.ndir ? __ldg(a.nbr + (size_t)d * ld + n) : -1;
@@ -82,18 +82,58 @@ struct KSum {
   __device__ __forceinline__ double value() const { return (double)s - (double)c; }
 };
 
+// FP64 partial sums need no compensation: plain accumulation (one FP64 add per term).
+template <>
+struct KSum<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double v) { s += v; }
+  __device__ __forceinline__ double value() const { return s; }
+};
+
 template <int D, typename T>
-__device__ __forceinline__ void precond_apply(const MrhsArgs& a, int n, const T* r, T* z) {
-  if (a.mfac == nullptr) {
+__device__ __forceinline__ void precond_apply(const MrhsArgs& a, const T* M, int n, const T* r, T* z) {
+  if (M == nullptr) {
 #pragma unroll
     for (int k = 0; k < D; ++k) z[k] = r[k];
     return;
   }
-  const T* M = static_cast<const T*>(a.mfac);
   T L[ntri(D)];
 #pragma unroll
   for (int e = 0; e < ntri(D); ++e) L[e] = __ldg(M + (size_t)e * a.ld + n);
   chol_solve_invdiag<D>(L, r, z);
+}
+
+// Operator, scales, b and x of right-hand side r.
+template <int D, typename T>
+struct RhsOp {
+  const T* B;
+  const T* M;
+  const T* b;
+  T* x;
+  T sc[D];
+};
+
+template <int D, typename T>
+__device__ __forceinline__ RhsOp<D, T> rhs_op(const MrhsArgs& a, int r) {
+  RhsOp<D, T> o;
+  const double* scale;
+  if (a.tab != nullptr) {
+    const MrhsRhsPtrs t = a.tab[r];
+    o.B = static_cast<const T*>(t.blocks);
+    o.M = static_cast<const T*>(t.mfac);
+    o.b = static_cast<const T*>(t.b);
+    o.x = static_cast<T*>(t.x);
+    scale = t.scale;
+  } else {
+    o.B = static_cast<const T*>(a.blocks);
+    o.M = static_cast<const T*>(a.mfac);
+    o.b = static_cast<const T*>(a.b) + (size_t)r * a.vs;
+    o.x = static_cast<T*>(a.x) + (size_t)r * a.vs;
+    scale = a.scale;
+  }
+#pragma unroll
+  for (int k = 0; k < D; ++k) o.sc[k] = (T)__ldg(scale + k);
+  return o;
 }
 
 struct Units {
@@ -280,15 +320,12 @@ constexpr size_t mrhs_stage_bytes() {
   return kStaged<T> ? (size_t)(MRHS_THREADS / 32) * 2 * (6 * D) * 32 * sizeof(T) : 0;
 }
 
+// FP32 solves and small FP64 systems run two CTAs per SM; FP64 systems with D > 4 take the
+// whole register file of one CTA per SM, which removes their register spills.
 template <int D, typename T>
-__global__ void __launch_bounds__(MRHS_THREADS, 2) k_mrhs(MrhsArgs a) {
+__global__ void __launch_bounds__(MRHS_THREADS, (sizeof(T) == 4 || D <= 4) ? 2 : 1) k_mrhs(MrhsArgs a) {
   extern __shared__ __align__(16) unsigned char mrhs_smem[];
   T* stage = reinterpret_cast<T*>(mrhs_smem);
-  T sc[D];
-#pragma unroll
-  for (int k = 0; k < D; ++k) sc[k] = (T)__ldg(a.scale + k);
-  const T* Bv = static_cast<const T*>(a.b);
-  T* Xv = static_cast<T*>(a.x);
   T* Rv = static_cast<T*>(a.r);
   T* UUv = static_cast<T*>(a.u);
   T* WWv = static_cast<T*>(a.w);
@@ -312,18 +349,19 @@ __global__ void __launch_bounds__(MRHS_THREADS, 2) k_mrhs(MrhsArgs a) {
       const int r = unit_rhs(u), c = unit_chunk(u);
       const int act = first ? 1 : __ldcg(&a.st[r].active);
       if (!first && act != 2) continue;
-      const T* b = Bv + (size_t)r * a.vs;
-      T *x = Xv + (size_t)r * a.vs, *R = Rv + (size_t)r * a.vs, *Uu = UUv + (size_t)r * a.vs;
+      const RhsOp<D, T> op = rhs_op<D, T>(a, r);
+      const T* b = op.b;
+      T *x = op.x, *R = Rv + (size_t)r * a.vs, *Uu = UUv + (size_t)r * a.vs;
       T *P = PPv + (size_t)r * a.vs, *Sv = SSv + (size_t)r * a.vs;
       const int n1 = min(a.N, (c + 1) * U.csize);
       for (int n = c * U.csize + U.lane; n < n1; n += 32) {
         T xn[D], ax[D], rn[D], un[D];
 #pragma unroll
         for (int k = 0; k < D; ++k) xn[k] = x[(size_t)k * ld + n];
-        block_apply<D, T>(a, sc, n, xn, x, ax);
+        block_apply<D, T>(a, op.B, op.sc, n, xn, x, ax);
 #pragma unroll
         for (int k = 0; k < D; ++k) rn[k] = __ldg(b + (size_t)k * ld + n) - ax[k];
-        precond_apply<D, T>(a, n, rn, un);
+        precond_apply<D, T>(a, op.M, n, rn, un);
 #pragma unroll
         for (int k = 0; k < D; ++k) {
           R[(size_t)k * ld + n] = rn[k];
@@ -339,7 +377,8 @@ __global__ void __launch_bounds__(MRHS_THREADS, 2) k_mrhs(MrhsArgs a) {
       const int act = first ? 1 : __ldcg(&a.st[r].active);
       KSum<T> ks[4];
       if (first || act == 2) {
-        const T* b = Bv + (size_t)r * a.vs;
+        const RhsOp<D, T> op = rhs_op<D, T>(a, r);
+        const T* b = op.b;
         const T* R = Rv + (size_t)r * a.vs;
         const T* Uu = UUv + (size_t)r * a.vs;
         T* Wv = WWv + (size_t)r * a.vs;
@@ -352,7 +391,7 @@ __global__ void __launch_bounds__(MRHS_THREADS, 2) k_mrhs(MrhsArgs a) {
             rk[k] = R[(size_t)k * ld + n];
             bk[k] = __ldg(b + (size_t)k * ld + n);
           }
-          block_apply<D, T>(a, sc, n, un, Uu, wn);
+          block_apply<D, T>(a, op.B, op.sc, n, un, Uu, wn);
           T g = T(0), dl = T(0), rr2 = T(0), b2 = T(0);
 #pragma unroll
           for (int k = 0; k < D; ++k) {
@@ -380,7 +419,6 @@ __global__ void __launch_bounds__(MRHS_THREADS, 2) k_mrhs(MrhsArgs a) {
   if (!mrhs_reduce(a, U, 0, true, sh_int, &any_active, &any_pending)) return;
   while (any_active || any_pending) {
     if (any_active) {
-      // local update of active right-hand sides
       // local update of active right-hand sides, with the partials r'u and r'r of the
       // updated vectors (columns 0 and 2 of the unit's row)
       for (int u = U.gw; u < U.units; u += U.nw) {
@@ -388,7 +426,8 @@ __global__ void __launch_bounds__(MRHS_THREADS, 2) k_mrhs(MrhsArgs a) {
         if (__ldcg(&a.st[r].active) != 1) continue;
         KSum<T> kg, kr;
         const T al = (T)__ldcg(&a.st[r].alpha), be = (T)__ldcg(&a.st[r].beta);
-        T *x = Xv + (size_t)r * a.vs, *R = Rv + (size_t)r * a.vs, *Uu = UUv + (size_t)r * a.vs;
+        const RhsOp<D, T> op = rhs_op<D, T>(a, r);
+        T *x = op.x, *R = Rv + (size_t)r * a.vs, *Uu = UUv + (size_t)r * a.vs;
         T *P = PPv + (size_t)r * a.vs, *Sv = SSv + (size_t)r * a.vs;
         const T* Wv = WWv + (size_t)r * a.vs;
         const int n0 = c * U.csize;
@@ -401,7 +440,7 @@ __global__ void __launch_bounds__(MRHS_THREADS, 2) k_mrhs(MrhsArgs a) {
             xk[k] += al * pk[k];
             rn[k] -= al * sk[k];
           }
-          precond_apply<D, T>(a, n, rn, un);
+          precond_apply<D, T>(a, op.M, n, rn, un);
           T g = T(0), rr2 = T(0);
 #pragma unroll
           for (int k = 0; k < D; ++k) {
@@ -484,6 +523,7 @@ __global__ void __launch_bounds__(MRHS_THREADS, 2) k_mrhs(MrhsArgs a) {
         const int r = unit_rhs(u), c = unit_chunk(u);
         if (__ldcg(&a.st[r].active) != 1) continue;
         KSum<T> kd;
+        const RhsOp<D, T> op = rhs_op<D, T>(a, r);
         const T* Uu = UUv + (size_t)r * a.vs;
         T* Wv = WWv + (size_t)r * a.vs;
         const int n1 = min(a.N, (c + 1) * U.csize);
@@ -491,7 +531,7 @@ __global__ void __launch_bounds__(MRHS_THREADS, 2) k_mrhs(MrhsArgs a) {
           T un[D], wn[D];
 #pragma unroll
           for (int k = 0; k < D; ++k) un[k] = Uu[(size_t)k * ld + n];
-          block_apply<D, T>(a, sc, n, un, Uu, wn);
+          block_apply<D, T>(a, op.B, op.sc, n, un, Uu, wn);
           T dl = T(0);
 #pragma unroll
           for (int k = 0; k < D; ++k) {
@@ -508,6 +548,17 @@ __global__ void __launch_bounds__(MRHS_THREADS, 2) k_mrhs(MrhsArgs a) {
       // every moving RHS has stopped: confirm the pending ones with the true residual
       if (!restart_pass(false)) return;
       if (!mrhs_reduce(a, U, 0, false, sh_int, &any_active, &any_pending)) return;
+    }
+  }
+  // states are final (the last reduction's barrier has been passed): accumulate the tally
+  if (a.tally != nullptr && blockIdx.x == 0) {
+    for (int r = threadIdx.x; r < a.S; r += blockDim.x) {
+      const RhsState st = load_state(a.st + r);
+      MrhsTally& t = a.tally[r];
+      t.iters += st.total;
+      t.solves += 1;
+      if (st.status != 0 && t.status_any == 0) t.status_any = st.status;
+      t.rel_res = st.bb > 0.0 ? sqrt(st.rr / st.bb) : 0.0;
     }
   }
 }

@@ -25,6 +25,26 @@ struct RhsState {
   int status;      // 0 ok, 3 breakdown, 4 max_iter, 7 non-finite
 };
 
+// Operator and vectors of one right-hand side when the right-hand sides do not share a
+// matrix (independent chains): packed blocks [ntri(D)][ld], block-Jacobi factor (or null),
+// GMRF scales [D], b and x [D][ld].
+struct MrhsRhsPtrs {
+  const void* blocks;
+  const void* mfac;
+  const double* scale;
+  const void* b;
+  void* x;
+};
+
+// Per right-hand side, accumulated over launches: iterations, solves, the first nonzero
+// status (RhsState codes) and the relative residual of the last solve.
+struct MrhsTally {
+  long long iters;
+  int solves;
+  int status_any;
+  double rel_res;
+};
+
 // Vector and operator arrays hold FP64 (f32 = 0) or FP32 (f32 = 1) elements; CG scalars,
 // inner-product sums across threads and the stop test are FP64 in both cases.
 struct MrhsArgs {
@@ -55,6 +75,9 @@ struct MrhsArgs {
   int max_iter;
   int max_restarts;
   int sm_cap;            // most SMs the grid may span (0 = all)
+  const MrhsRhsPtrs* tab;  // [S] per-RHS operators, b and x (device), or null: all share
+                           // blocks/mfac/scale and b, x are strided by vs
+  MrhsTally* tally;      // [S] (device) or null
 };
 
 // Probe set-up and post-processing (log-determinant and trace probes).
