@@ -21,6 +21,9 @@ model    -- whitening, sufficient statistics, full conditionals of W, A, lambda,
             beta (Appendix A, temporal noise model), perturbed right-hand side (Algorithm 2)
 linalg   -- exact sparse solves, log-determinants, Lanczos / stochastic Lanczos quadrature
 gibbs    -- one Gibbs sweep (Section 3.2) and one spatial-VB step (Section 3.3, Appendix B/C)
+probes   -- exact log-determinant and trace terms behind the stochastic probes
+precond  -- block-Jacobi and red-black symmetric SOR preconditioners (replacing the
+            incomplete Cholesky of Section 3.1), factored form and voxel-by-voxel sweeps
 
 Parity status: every function is pinned by a ``-m "not gpu"`` test against a closed form,
 an invariant, an independent library routine or brute force, except the SVB convergence

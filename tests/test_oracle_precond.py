@@ -1,0 +1,72 @@
+"""Pins of the oracle's preconditioners (CPU only): the red-black symmetric SOR operator in
+factored form against the voxel-by-voxel forward/backward SOR sweeps (brute force, tiny
+lattices), its SPD-ness and the SSOR bound 0 < eig(M^-1 B~) <= 1, the reduction to
+block-Jacobi without couplings, and the two-colouring of the lattice."""
+import numpy as np
+import pytest
+
+from oracle import model, precond
+from oracle.lattice import Lattice
+
+
+def small_problem(seed, D=2, neighbourhood=6):
+    rng = np.random.default_rng(seed)
+    if neighbourhood == 6:
+        mask = np.ones((3, 3, 4), np.uint8)
+        mask[1, 1, 1] = 0
+        mask[2, 0, 3] = 0
+    else:
+        mask = np.ones((1, 4, 5), np.uint8)
+        mask[0, 2, 2] = 0
+    lat = Lattice(mask, neighbourhood)
+    N = lat.N
+    G = rng.standard_normal((N, D, D))
+    blocks = np.einsum("nij,nkj->nik", G, G) + 0.5 * np.eye(D)[None]
+    scale = rng.uniform(0.3, 2.0, D)
+    v = rng.standard_normal((N, D))
+    return lat, blocks, scale, v
+
+
+@pytest.mark.parametrize("omega", [0.7, 1.0, 1.3])
+@pytest.mark.parametrize("neighbourhood", [6, 4])
+def test_factored_form_equals_sor_sweeps(omega, neighbourhood):
+    lat, blocks, scale, v = small_problem(3, neighbourhood=neighbourhood)
+    z = precond.ssor_apply(lat, blocks, scale, v, omega)
+    zs = precond.ssor_apply_sweeps(lat, blocks, scale, v, omega)
+    assert np.max(np.abs(z - zs)) <= 1e-12 * np.max(np.abs(zs))
+
+
+@pytest.mark.parametrize("omega", [0.7, 1.0, 1.3])
+def test_ssor_is_spd_and_bounds_the_spectrum(omega):
+    lat, blocks, scale, v = small_problem(5, D=3)
+    M = precond.ssor_matrix(lat, blocks, scale, omega)
+    assert np.max(np.abs(M - M.T)) <= 1e-12 * np.max(np.abs(M))
+    assert np.linalg.eigvalsh(0.5 * (M + M.T)).min() > 0
+    B = model.precision(lat, blocks, scale).toarray()
+    ev = np.linalg.eigvals(np.linalg.solve(M, B)).real
+    assert ev.min() > 0 and ev.max() <= 1 + 1e-10
+
+
+def test_apply_inverts_matrix_form():
+    lat, blocks, scale, _ = small_problem(7, D=3)
+    v = np.random.default_rng(2).standard_normal((lat.N, 3))
+    M = precond.ssor_matrix(lat, blocks, scale, 1.2)
+    z = precond.ssor_apply(lat, blocks, scale, v, 1.2)
+    vz = model.from_kmajor(M @ model.kmajor(z), 3).T
+    assert np.max(np.abs(vz - v)) <= 1e-11 * np.max(np.abs(v))
+
+
+def test_without_couplings_sgs_is_block_jacobi():
+    lat, blocks, _, v = small_problem(9)
+    z = precond.ssor_apply(lat, blocks, np.zeros(2), v, 1.0)
+    zb = np.stack([np.linalg.solve(blocks[n], v[n]) for n in range(lat.N)])
+    assert np.max(np.abs(z - zb)) <= 1e-13 * np.max(np.abs(zb))
+
+
+@pytest.mark.parametrize("neighbourhood", [6, 4])
+def test_every_edge_joins_two_colours(neighbourhood):
+    lat, _, _, _ = small_problem(1, neighbourhood=neighbourhood)
+    c = precond.colours(lat)
+    E = lat.edges()
+    assert np.all(c[E[:, 0]] != c[E[:, 1]])
+    assert 0 < c.sum() < lat.N
