@@ -283,6 +283,7 @@ def run_ours(args, world, rank, local):
 
     # independent chains of the same subject advanced together (one multi-RHS launch per solve)
     chains = run_chains(args, w, flush, stream, value) if not args.no_chains else None
+    precs = run_precond_compare(args, w) if (rank == 0 and not args.no_precond) else None
     # end to end through the C ABI with host buffers
     del flush
     e2e = run_e2e(args, w) if rank == 0 else None
@@ -305,7 +306,7 @@ def run_ours(args, world, rank, local):
                            "pcg_iterations_W_per_sweep": it_w / args.steps,
                            "pcg_iterations_A_per_sweep": it_a / args.steps},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-                "mixed_precision": mixed, "grouped_chains": chains, "serving": serving, "batched_probes": batched,
+                "mixed_precision": mixed, "grouped_chains": chains, "preconditioners": precs, "serving": serving, "batched_probes": batched,
                 "gpu_launches": int(n_launch),
                 "kernel_ms_per_step": {k: v["ms"] / args.steps for k, v in tim.items() if v["launches"]}}
         print(json.dumps(line), flush=True)
@@ -404,6 +405,41 @@ def run_chains(args, w, flush, stream, single_value, n_chains=8):
             "pcg_iterations_A_per_chain_sweep": it_a / (n_chains * args.steps),
             "vs_single_chain": value / single_value if single_value else None,
             "delta": 1e-8, "dtype": "f64"}
+
+
+def run_precond_compare(args, w, n_draws=10):
+    """W and A solves of the headline workload with each preconditioner (after 3 sweeps from
+    the prior means, same state and random numbers for all): PCG iterations and solve time
+    per draw (CUDA events around every launch)."""
+    import torch
+
+    from paper_1606_00980_gb300 import bfmri
+    from paper_1606_00980_gb300.bfmri import Model
+    cases = [("block_jacobi_resident", dict(precond=bfmri.PRECOND_BLOCK_JACOBI)),
+             ("block_jacobi_streaming", dict(precond=bfmri.PRECOND_BLOCK_JACOBI,
+                                             pcg_variant=bfmri.PCG_STREAMING)),
+             ("ssor_omega1.0_resident", dict(precond=bfmri.PRECOND_SSOR, ssor_omega=1.0)),
+             ("ssor_omega1.0_streaming", dict(precond=bfmri.PRECOND_SSOR, ssor_omega=1.0,
+                                              pcg_variant=bfmri.PCG_STREAMING)),
+             ("ssor_omega1.2_resident", dict(precond=bfmri.PRECOND_SSOR, ssor_omega=1.2))]
+    out = {}
+    for name, opts in cases:
+        m = Model.from_workload(w, delta=1e-8, seed=2024, profile=1, **opts)
+        m.precompute_stats()
+        m.gibbs_sweep(3, 0, info=False)
+        torch.cuda.synchronize()
+        m.reset_timing()
+        for i in range(n_draws):
+            m.sample_W(100 + i, out=False)
+            m.sample_A(100 + i, out=False)
+        torch.cuda.synchronize()
+        t = m.timing()
+        m.close()
+        out[name] = {"W_iterations_per_draw": t["pcg_W"]["pcg_iterations"] / n_draws,
+                     "W_solve_ms_per_draw": t["pcg_W"]["ms"] / n_draws,
+                     "A_iterations_per_draw": t["pcg_A"]["pcg_iterations"] / n_draws,
+                     "A_solve_ms_per_draw": t["pcg_A"]["ms"] / n_draws}
+    return out
 
 
 def mrhs_bytes_per_voxel_iter_rhs(D, S, w=4):
@@ -578,6 +614,7 @@ def main():
     ap.add_argument("--probes", type=int, default=64)
     ap.add_argument("--no-svb", action="store_true")
     ap.add_argument("--no-chains", action="store_true")
+    ap.add_argument("--no-precond", action="store_true")
     ap.add_argument("--only-batched", action="store_true",
                     help="run only the batched-probe measurement (profiling entry point)")
     ap.add_argument("--serving-requests", type=int, default=96)

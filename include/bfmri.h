@@ -58,6 +58,11 @@ typedef struct {
 
 #define BFMRI_PRECOND_NONE         0
 #define BFMRI_PRECOND_BLOCK_JACOBI 1  /* per-voxel (block + alpha * degree) Cholesky */
+#define BFMRI_PRECOND_SSOR         2  /* red-black symmetric SOR over those voxel blocks:
+                                         M = (Dg + w L) Dg^-1 (Dg + w U) / (w (2 - w)), w =
+                                         ssor_omega, red = voxels with x + y + z even. FP64
+                                         single solves only (creation with the mixed precision
+                                         fails); multi-RHS solves use the block-Jacobi blocks */
 
 #define BFMRI_PREC_FP64  0  /* FP64 PCG */
 #define BFMRI_PREC_MIXED 1  /* FP32 inner PCG inside an FP64 iterative-refinement loop */
@@ -101,6 +106,8 @@ typedef struct {
   int sm_budget;             /* most SMs one solver grid may span (0 = all). Concurrent
                                 handles whose budgets sum to at most the SM count can run
                                 their cooperative solves side by side. */
+  double ssor_omega;         /* relaxation of BFMRI_PRECOND_SSOR, in (0, 2) (default 1:
+                                symmetric Gauss-Seidel) */
 } bfmri_options;
 
 #define BFMRI_PCG_AUTO      0
@@ -302,6 +309,11 @@ bfmri_status bfmri_reset_timing(bfmri_handle* h);
  *    right-hand side b_w (dim x N) and the perturbed right-hand side b of Algorithm 2
  *    for draw counter `counter` (dim x N). Any output may be NULL. */
 bfmri_status bfmri_apply_precision(bfmri_handle* h, int which, const double* x, double* y);
+/*  bfmri_apply_preconditioner: y = M^-1 x (dim x N row-major) with M the solver's
+ *    preconditioner for the current state's system: block-Jacobi (blocks B_n + diag(scale)
+ *    deg_n), identity, or red-black SSOR over those blocks (Section 3.1 uses an incomplete
+ *    Cholesky factor instead). */
+bfmri_status bfmri_apply_preconditioner(bfmri_handle* h, int which, const double* x, double* y);
 bfmri_status bfmri_build_system(bfmri_handle* h, int which, uint64_t counter, double* blocks,
                                 double* b_mean, double* b_pert);
 

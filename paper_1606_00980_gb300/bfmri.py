@@ -22,7 +22,7 @@ BFMRI_OK = 0
 STATUS_NAMES = {0: "OK", -1: "INVALID_ARG", -2: "OOM", -3: "NOT_SPD", -4: "NOT_CONVERGED",
                 -5: "TIMEOUT", -6: "CUDA", -7: "INTERNAL", -8: "STATE"}
 BFMRI_F32, BFMRI_F64 = 0, 1
-PRECOND_NONE, PRECOND_BLOCK_JACOBI = 0, 1
+PRECOND_NONE, PRECOND_BLOCK_JACOBI, PRECOND_SSOR = 0, 1, 2
 PREC_FP64, PREC_MIXED = 0, 1
 AR_SPATIAL, AR_INDEPENDENT = 0, 1
 Y_MASKED, Y_LATTICE = 0, 1
@@ -45,7 +45,7 @@ class bfmri_options(C.Structure):
                 ("cuda_stream", C.c_void_p), ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN),
                 ("alloc_ctx", C.c_void_p), ("barrier_timeout_s", C.c_double),
                 ("debug_skip_block", C.c_int), ("profile", C.c_int), ("pcg_variant", C.c_int),
-                ("sm_budget", C.c_int)]
+                ("sm_budget", C.c_int), ("ssor_omega", C.c_double)]
 
 
 class bfmri_solve_info(C.Structure):
@@ -121,6 +121,7 @@ SIGNATURES = [
     ("bfmri_get_timing", C.c_int, [_h, _P(bfmri_timing)]),
     ("bfmri_reset_timing", C.c_int, [_h]),
     ("bfmri_apply_precision", C.c_int, [_h, C.c_int, _dp, _dp]),
+    ("bfmri_apply_preconditioner", C.c_int, [_h, C.c_int, _dp, _dp]),
     ("bfmri_build_system", C.c_int, [_h, C.c_int, C.c_uint64, _dp, _dp, _dp]),
     ("bfmri_request_device_bytes", C.c_size_t, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int]),
     ("bfmri_server_create", C.c_int, [C.c_size_t, C.c_int, C.c_int, _P(C.c_void_p)]),
@@ -478,6 +479,13 @@ class Model:
         x = _f64(x, (D, self.N))
         y = np.empty((D, self.N))
         self._c(self.lib.bfmri_apply_precision(self.handle, which, _ptr(x), _ptr(y)))
+        return y
+
+    def apply_preconditioner(self, which, x):
+        D = self.K if which == 0 else self.P
+        x = _f64(x, (D, self.N))
+        y = np.empty((D, self.N))
+        self._c(self.lib.bfmri_apply_preconditioner(self.handle, which, _ptr(x), _ptr(y)))
         return y
 
     def build_system(self, which, counter):

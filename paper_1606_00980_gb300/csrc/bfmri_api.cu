@@ -62,6 +62,10 @@ struct bfmri_handle {
   int part_rows = 0;
   std::vector<double> Sxx;
   int stride[3] = {1, 1, 1};
+  int* d_red = nullptr;     // compact indices of the voxels with x + y + z even
+  int* d_black = nullptr;   // and of the others (red-black SSOR phases)
+  int n_red = 0, n_black = 0;
+  unsigned char* d_colour = nullptr;   // [ld] 0 red, 1 black
   uint64_t mask_hash = 0;   // identity of the mask (FNV-1a of the in-mask lattice indices)
   // grouped chains: per-chain operator tables [2][cap] and tallies [2][cap]
   MrhsRhsPtrs* d_gtab = nullptr;
@@ -272,12 +276,13 @@ bfmri_status end_call(bfmri_handle* h, PcgCtrl* ctrl_out /* [2] or null */, int*
 
 bfmri_status run_pcg(bfmri_handle* h, int D, const double* scale, double* x, int which) {
   PcgArgs a;
+  memset(&a, 0, sizeof(a));
   a.N = h->N;
   a.ld = h->ld;
   a.ndir = h->ndir;
   a.nbr = h->d_nbr;
   a.blocks = h->d_blocks;
-  a.mfac = h->opt.precond == BFMRI_PRECOND_BLOCK_JACOBI ? h->d_mfac : nullptr;
+  a.mfac = h->opt.precond != BFMRI_PRECOND_NONE ? h->d_mfac : nullptr;
   a.scale = scale;
   a.b = h->d_rhs;
   a.x = x;
@@ -292,7 +297,14 @@ bfmri_status run_pcg(bfmri_handle* h, int D, const double* scale, double* x, int
   a.sm_cap = h->opt.sm_budget;
   a.mixed = h->opt.precision == BFMRI_PREC_MIXED;
   a.blocks32 = h->d_blocks32;
-  a.mfac32 = h->opt.precond == BFMRI_PRECOND_BLOCK_JACOBI ? h->d_mfac32 : nullptr;
+  a.mfac32 = h->opt.precond != BFMRI_PRECOND_NONE ? h->d_mfac32 : nullptr;
+  a.ssor = h->opt.precond == BFMRI_PRECOND_SSOR && h->opt.precision == BFMRI_PREC_FP64;
+  a.omega = h->opt.ssor_omega;
+  a.red = h->d_red;
+  a.n_red = h->n_red;
+  a.black = h->d_black;
+  a.n_black = h->n_black;
+  a.colour = h->d_colour;
   a.u32 = h->d_u32;
   a.r32 = h->d_r32;
   a.w32 = h->d_w32;
@@ -333,7 +345,7 @@ AssembleArgs assemble_args(bfmri_handle* h, const double* scale, uint64_t counte
   a.eps = h->opt.eps;
   a.spatial = h->opt.ar_prior == BFMRI_AR_SPATIAL;
   a.perturb = 1;
-  a.precond = h->opt.precond == BFMRI_PRECOND_BLOCK_JACOBI;
+  a.precond = h->opt.precond != BFMRI_PRECOND_NONE;
   a.rng = rng_of(h, counter, tag);
   a.blocks = h->d_blocks;
   a.mfac = h->d_mfac;
@@ -508,7 +520,7 @@ MrhsArgs mrhs_args(bfmri_handle* h, int D, int S, const double* scale, int max_i
   m.f32 = 0;
   m.nbr = h->d_nbr;
   m.blocks = h->d_blocks;
-  m.mfac = h->opt.precond == BFMRI_PRECOND_BLOCK_JACOBI ? h->d_mfac : nullptr;
+  m.mfac = h->opt.precond != BFMRI_PRECOND_NONE ? h->d_mfac : nullptr;   // block-Jacobi
   m.scale = scale;
   m.S = S;
   m.vs = h->mr_vs;
@@ -566,6 +578,7 @@ void bfmri_default_options(bfmri_options* o) {
   o->delta = 1e-8;
   o->max_iter = 2000;
   o->precond = BFMRI_PRECOND_BLOCK_JACOBI;
+  o->ssor_omega = 1.0;
   o->precision = BFMRI_PREC_FP64;
   o->ar_prior = BFMRI_AR_SPATIAL;
   o->y_layout = BFMRI_Y_MASKED;
@@ -621,8 +634,13 @@ bfmri_status bfmri_create(const bfmri_lattice* lat, const uint8_t* mask, const d
   if (o.sm_budget < 0) return fail(nullptr, BFMRI_ERR_INVALID_ARG, "sm_budget must be >= 0");
   if (o.pcg_variant != BFMRI_PCG_AUTO && o.pcg_variant != BFMRI_PCG_STREAMING)
     return fail(nullptr, BFMRI_ERR_INVALID_ARG, "unknown pcg_variant");
-  if (o.precond != BFMRI_PRECOND_NONE && o.precond != BFMRI_PRECOND_BLOCK_JACOBI)
+  if (o.precond != BFMRI_PRECOND_NONE && o.precond != BFMRI_PRECOND_BLOCK_JACOBI &&
+      o.precond != BFMRI_PRECOND_SSOR)
     return fail(nullptr, BFMRI_ERR_INVALID_ARG, "unknown preconditioner");
+  if (o.precond == BFMRI_PRECOND_SSOR && !(o.ssor_omega > 0.0 && o.ssor_omega < 2.0))
+    return fail(nullptr, BFMRI_ERR_INVALID_ARG, "ssor_omega must be in (0, 2)");
+  if (o.precond == BFMRI_PRECOND_SSOR && o.precision != BFMRI_PREC_FP64)
+    return fail(nullptr, BFMRI_ERR_INVALID_ARG, "SSOR preconditioning is implemented for the FP64 solver only");
   if (o.precision != BFMRI_PREC_FP64 && o.precision != BFMRI_PREC_MIXED)
     return fail(nullptr, BFMRI_ERR_INVALID_ARG, "unknown precision mode");
   if (o.precision == BFMRI_PREC_MIXED && !(o.inner_tol > 0.0 && o.inner_tol < 1.0))
@@ -721,6 +739,9 @@ bfmri_status bfmri_create(const bfmri_lattice* lat, const uint8_t* mask, const d
   h->part_rows = maxgrid;
   h->d_nbr = (int*)A(6 * ld * sizeof(int));
   h->d_lin = (int*)A(ld * sizeof(int));
+  h->d_red = (int*)A(ld * sizeof(int));
+  h->d_black = (int*)A(ld * sizeof(int));
+  h->d_colour = (unsigned char*)A(ld);
   h->d_Y = A((size_t)T * N * esz);
   h->y_f64 = y_dtype == BFMRI_F64;
   h->d_X = (double*)A((size_t)T * K * sizeof(double));
@@ -763,7 +784,7 @@ bfmri_status bfmri_create(const bfmri_lattice* lat, const uint8_t* mask, const d
       return fail(nullptr, BFMRI_ERR_OOM, "device allocation failed");
     }
   }
-  void* must[] = {h->d_nbr, h->d_lin, h->d_Y, h->d_X, h->d_stats, h->d_Sxx, h->d_W, h->d_A,
+  void* must[] = {h->d_nbr, h->d_lin, h->d_red, h->d_black, h->d_colour, h->d_Y, h->d_X, h->d_stats, h->d_Sxx, h->d_W, h->d_A,
                   h->d_lam, h->d_alpha, h->d_beta, h->d_G, h->d_blocks, h->d_mfac, h->d_rhs,
                   h->d_bmean, h->d_r, h->d_z, h->d_q, h->d_p0, h->d_p1, h->d_part, h->d_hpart,
                   h->d_bar, h->d_err, h->d_ctrl, h->d_flags};
@@ -775,8 +796,20 @@ bfmri_status bfmri_create(const bfmri_lattice* lat, const uint8_t* mask, const d
   }
   cudaStream_t s = h->stream;
   cudaError_t e = cudaSuccess;
-  std::vector<int> linp(ld, 0);
-  for (int n = 0; n < N; ++n) linp[n] = lin[n];
+  std::vector<int> linp(ld, 0), red, black;
+  std::vector<unsigned char> colour(ld, 0);
+  for (int n = 0; n < N; ++n) {
+    linp[n] = lin[n];
+    const long long l = lin[n];
+    const long long xyz = l % lat->nx + (l / lat->nx) % lat->ny + l / ((long long)lat->nx * lat->ny);
+    colour[n] = (unsigned char)(xyz % 2);
+    (xyz % 2 == 0 ? red : black).push_back(n);
+  }
+  h->n_red = (int)red.size();
+  h->n_black = (int)black.size();
+  if (!e) e = cudaMemcpyAsync(h->d_colour, colour.data(), ld, cudaMemcpyHostToDevice, s);
+  if (!e && !red.empty()) e = cudaMemcpyAsync(h->d_red, red.data(), red.size() * sizeof(int), cudaMemcpyHostToDevice, s);
+  if (!e && !black.empty()) e = cudaMemcpyAsync(h->d_black, black.data(), black.size() * sizeof(int), cudaMemcpyHostToDevice, s);
   if (!e) e = cudaMemcpyAsync(h->d_nbr, nbr.data(), nbr.size() * sizeof(int), cudaMemcpyHostToDevice, s);
   if (!e) e = cudaMemcpyAsync(h->d_lin, linp.data(), ld * sizeof(int), cudaMemcpyHostToDevice, s);
   if (!e) e = cudaMemcpyAsync(h->d_Y, ysrc, (size_t)T * N * esz, cudaMemcpyHostToDevice, s);
@@ -1013,7 +1046,7 @@ bfmri_status bfmri_gibbs_sweep_group(bfmri_handle* const* hs, int n, int n_sweep
     if (!h0->d_gtab || !h0->d_gtally) return fail(h0, BFMRI_ERR_OOM, "group table allocation failed");
     h0->g_cap = n;
   }
-  const bool pre = h0->opt.precond == BFMRI_PRECOND_BLOCK_JACOBI;
+  const bool pre = h0->opt.precond != BFMRI_PRECOND_NONE;   // multi-RHS: block-Jacobi
   std::vector<MrhsRhsPtrs> tab(2 * (size_t)n);
   for (int c = 0; c < n; ++c) {
     bfmri_handle* h = hs[c];
@@ -1127,7 +1160,7 @@ bfmri_status bfmri_logdet_probe(bfmri_handle* h, int which, int n_probes, int la
     if (e != cudaSuccess) return cuda_fail(h, e, "assemble");
   }
   RET(ensure_mrhs(h, D, n_probes, lanczos_steps));
-  const bool pre = h->opt.precond == BFMRI_PRECOND_BLOCK_JACOBI;
+  const bool pre = h->opt.precond != BFMRI_PRECOND_NONE;
   ProbeArgs pa;
   pa.N = h->N;
   pa.ld = h->ld;
@@ -1483,6 +1516,46 @@ bfmri_status bfmri_apply_precision(bfmri_handle* h, int which, const double* x, 
   ap.y = h->d_z;
   e = launch_apply(ap, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "apply");
+  RET(end_call(h, nullptr, nullptr));
+  return to_host(h, y, h->d_z, D);
+}
+
+bfmri_status bfmri_apply_preconditioner(bfmri_handle* h, int which, const double* x, double* y) {
+  RET(require_stats(h));
+  if (!x || !y || (which != 0 && which != 1)) return fail(h, BFMRI_ERR_INVALID_ARG, "bad arguments");
+  const int D = which == 0 ? h->K : h->P;
+  if (D == 0) return BFMRI_OK;
+  RET(begin_call(h));
+  AssembleArgs a = assemble_args(h, which == 0 ? h->d_alpha : h->d_beta, 0, which == 0 ? TAG_W : TAG_A);
+  a.perturb = 0;
+  cudaError_t e = which == 0 ? launch_assemble_w(a, h->stream) : launch_assemble_a(a, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "assemble");
+  RET(to_dev(h, h->d_r, x, D));
+  PcgArgs p;
+  memset(&p, 0, sizeof(p));
+  p.N = h->N;
+  p.ld = h->ld;
+  p.ndir = h->ndir;
+  p.nbr = h->d_nbr;
+  p.mfac = h->opt.precond != BFMRI_PRECOND_NONE ? h->d_mfac : nullptr;
+  p.scale = which == 0 ? h->d_alpha : h->d_beta;
+  // the independent AR prior has no spatial term
+  static const double zeros[PMAX] = {0, 0, 0, 0};
+  if (which == 1 && h->opt.ar_prior != BFMRI_AR_SPATIAL) {
+    CU(h, cudaMemcpyAsync(h->d_bmean, zeros, D * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    p.scale = h->d_bmean;
+  }
+  p.r = h->d_r;
+  p.u = h->d_z;
+  p.ssor = h->opt.precond == BFMRI_PRECOND_SSOR;
+  p.omega = h->opt.ssor_omega;
+  p.red = h->d_red;
+  p.n_red = h->n_red;
+  p.black = h->d_black;
+  p.n_black = h->n_black;
+  p.colour = h->d_colour;
+  e = launch_precond_apply(D, p, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "preconditioner apply");
   RET(end_call(h, nullptr, nullptr));
   return to_host(h, y, h->d_z, D);
 }

@@ -159,6 +159,47 @@ __device__ __forceinline__ void cg_scalar_step(Shared& sh, double gnew, double d
   }
 }
 
+// Red-black symmetric SOR: z = M(omega)^-1 r with
+//   M(omega) = (Dg + omega L) Dg^-1 (Dg + omega U) / (omega (2 - omega))
+// in red-black order (Dg: the voxel blocks B_n + diag(scale) deg_n, whose Cholesky factor is
+// mfac; L, U: the couplings -scale_k between neighbours, each joining a red and a black
+// voxel). It equals one forward SOR sweep (red, then black voxels) and one backward sweep
+// (black, then red) from z = 0. The backward half-sweep of the black voxels only rescales
+// them by (2 - omega), so three colour phases remain, with neighbour values exchanged
+// between them (u holds z in place):
+//   1. every voxel: u_n = omega Dg_n^-1 r_n      (read afterwards only for the red voxels)
+//   2. black n:     u_n = (2 - omega) omega Dg_n^-1 (r_n + scale .* sum_m u_m)
+//   3. red n:       u_n = (2 - omega) u_n + omega Dg_n^-1 (scale .* sum_m u_m)
+// Phase 1 is the solver's block-Jacobi step scaled by omega; phases 2 and 3 are below
+// (streaming layout: factor, r and u in global memory).
+template <int D>
+__device__ __forceinline__ void ssor_phase(const PcgArgs& a, const double* s, int n, int phase) {
+  const size_t ld = a.ld;
+  int nb[6];
+#pragma unroll
+  for (int d = 0; d < 6; ++d) nb[d] = d < a.ndir ? __ldg(a.nbr + (size_t)d * ld + n) : -1;
+  double sum[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) sum[k] = 0.0;
+#pragma unroll
+  for (int d = 0; d < 6; ++d) {
+    if (nb[d] >= 0) {
+#pragma unroll
+      for (int k = 0; k < D; ++k) sum[k] += ldx(a.u + (size_t)k * ld + nb[d]);
+    }
+  }
+  double t[D], z[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) t[k] = phase == 2 ? a.r[(size_t)k * ld + n] + s[k] * sum[k] : s[k] * sum[k];
+  minv<D, double>(a.mfac + n, (int)ld, t, z);
+  const double c = 2.0 - a.omega;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    const size_t o = (size_t)k * ld + n;
+    a.u[o] = phase == 2 ? c * a.omega * z[k] : c * a.u[o] + a.omega * z[k];
+  }
+}
+
 __device__ __forceinline__ void write_ctrl(const PcgArgs& a, int it, int restarts, double rr,
                                           double bb, double rel0, int status) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -186,8 +227,40 @@ __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_res(PcgArgs a) {
   const int bd = blockDim.x, t = threadIdx.x;
   double* shB = smem;
   double* shM = smem + NT * bd;
-  const int n = blockIdx.x * a.res_per + t;
-  const bool own = t < a.res_per && n < a.N;
+  int n = blockIdx.x * a.res_per + t;
+  bool own = t < a.res_per && n < a.N;
+  bool is_red = true;
+  if (a.ssor) {
+    // SSOR: the CTA's red voxels take the first threads and its black voxels the next ones
+    // (stable within each colour), so the warps of the colour phases are uniform
+    __shared__ int sh_order[RES_MAX_THREADS];
+    __shared__ int sh_cnt[2 * (RES_MAX_THREADS / 32)];
+    const bool blk = own && a.colour[n] != 0;
+    const bool rd = own && !blk;
+    const int lane = t & 31, warp = t >> 5, nwc = (bd + 31) >> 5;
+    const unsigned mr = __ballot_sync(0xffffffffu, rd), mb = __ballot_sync(0xffffffffu, blk);
+    if (lane == 0) {
+      sh_cnt[2 * warp] = __popc(mr);
+      sh_cnt[2 * warp + 1] = __popc(mb);
+    }
+    __syncthreads();
+    int red_before = 0, black_before = 0, nred = 0, nblack = 0;
+    for (int w = 0; w < nwc; ++w) {
+      if (w < warp) {
+        red_before += sh_cnt[2 * w];
+        black_before += sh_cnt[2 * w + 1];
+      }
+      nred += sh_cnt[2 * w];
+      nblack += sh_cnt[2 * w + 1];
+    }
+    const unsigned below = (1u << lane) - 1u;
+    if (rd) sh_order[red_before + __popc(mr & below)] = n;
+    if (blk) sh_order[nred + black_before + __popc(mb & below)] = n;
+    __syncthreads();
+    own = t < nred + nblack;
+    n = own ? sh_order[t] : 0;
+    is_red = t < nred;
+  }
   const size_t ld = a.ld;
   const bool pre = a.mfac != nullptr;
 #pragma unroll
@@ -217,6 +290,35 @@ __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_res(PcgArgs a) {
     if (a.skip_block == (int)blockIdx.x) return false;
     return grid_sync(a.bar, &sh.flag);
   };
+  const double omega = a.omega, c2 = 2.0 - a.omega;
+  // SSOR phase 1 is the block-Jacobi step scaled by omega (u published by the caller);
+  // phases 2 (black voxels) and 3 (red voxels) follow, each after a barrier
+  auto ssor_phases = [&]() -> bool {
+    for (int phase = 2; phase <= 3; ++phase) {
+      if (!bar()) return false;
+      if (own && (phase == 2) != is_red) {
+        double sum[D], tv[D], z[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) sum[k] = 0.0;
+#pragma unroll
+        for (int d = 0; d < 6; ++d) {
+          if (nb[d] >= 0) {
+#pragma unroll
+            for (int k = 0; k < D; ++k) sum[k] += ldx(a.u + (size_t)k * ld + nb[d]);
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < D; ++k) tv[k] = phase == 2 ? r[k] + s[k] * sum[k] : s[k] * sum[k];
+        minv<D, double>(Mp, bd, tv, z);
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          u[k] = phase == 2 ? c2 * omega * z[k] : c2 * u[k] + omega * z[k];
+          a.u[(size_t)k * ld + n] = u[k];
+        }
+      }
+    }
+    return true;
+  };
   // (r, u, w) from the current x, with partials (r'u, w'u, r'r, b'b)
   auto restart = [&](double* tot) -> bool {
     double ax[D];
@@ -224,10 +326,15 @@ __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_res(PcgArgs a) {
 #pragma unroll
     for (int k = 0; k < D; ++k) r[k] = bv[k] - ax[k];
     minv<D, double>(Mp, bd, r, u);
+    if (a.ssor) {
+#pragma unroll
+      for (int k = 0; k < D; ++k) u[k] *= omega;
+    }
     if (own) {
 #pragma unroll
       for (int k = 0; k < D; ++k) a.u[(size_t)k * ld + n] = u[k];
     }
+    if (a.ssor && !ssor_phases()) return false;
     if (!bar()) return false;
     amul<D, double>(Bp, bd, s, nb, a.ndir, degd, u, a.u, ld, w);
     double v[4] = {0.0, 0.0, 0.0, 0.0};
@@ -267,10 +374,15 @@ __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_res(PcgArgs a) {
       r[k] -= alpha * q[k];
     }
     minv<D, double>(Mp, bd, r, u);
+    if (a.ssor) {
+#pragma unroll
+      for (int k = 0; k < D; ++k) u[k] *= omega;
+    }
     if (own) {
 #pragma unroll
       for (int k = 0; k < D; ++k) a.u[(size_t)k * ld + n] = u[k];
     }
+    if (a.ssor && !ssor_phases()) return;
     if (!bar()) return;
     amul<D, double>(Bp, bd, s, nb, a.ndir, degd, u, a.u, ld, w);
     double v[4] = {0.0, 0.0, 0.0, 0.0};
@@ -347,10 +459,22 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_stream(PcgArgs a) {
   auto precond = [&](int n, const double* rn, double* un) {
     if (pre) {
       minv<D, double>(a.mfac + n, (int)ld, rn, un);
+      if (a.ssor) {
+#pragma unroll
+        for (int k = 0; k < D; ++k) un[k] *= a.omega;   // SSOR phase 1
+      }
     } else {
 #pragma unroll
       for (int k = 0; k < D; ++k) un[k] = rn[k];
     }
+  };
+  // SSOR phases 2 (black voxels) and 3 (red voxels), each after a barrier
+  auto ssor_rest = [&]() -> bool {
+    if (!bar()) return false;
+    for (int i = tid; i < a.n_black; i += nth) ssor_phase<D>(a, s, a.black[i], 2);
+    if (!bar()) return false;
+    for (int i = tid; i < a.n_red; i += nth) ssor_phase<D>(a, s, a.red[i], 3);
+    return true;
   };
   // r = b - B~ x, u = M^-1 r (published); then w = B~ u and partials.
   auto restart = [&](double* tot) -> bool {
@@ -372,6 +496,7 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_stream(PcgArgs a) {
         Sv[(size_t)k * ld + n] = 0.0;
       }
     }
+    if (a.ssor && !ssor_rest()) return false;
     if (!bar()) return false;
     double v[4] = {0.0, 0.0, 0.0, 0.0};
     for (int n = tid; n < a.N; n += nth) {
@@ -444,6 +569,7 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_stream(PcgArgs a) {
         U[o] = un[k];
       }
     }
+    if (a.ssor && !ssor_rest()) return;
     if (!bar()) return;
     double v[4] = {0.0, 0.0, 0.0, 0.0};
     for (int n = tid; n < a.N; n += nth) {
@@ -944,6 +1070,59 @@ static int max_grid_d() {
 }
 
 #define BFMRI_PCG_CASES(X) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12)
+
+// Preconditioner inspection: phase 0 = block-Jacobi (or identity), 1..3 = SSOR phases.
+template <int D>
+__global__ void __launch_bounds__(PCG_THREADS) k_precond_phase(PcgArgs a, int phase) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double s[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) s[k] = __ldg(a.scale + k);
+  if (phase <= 1) {
+    if (i >= a.N) return;
+    double r[D], z[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) r[k] = a.r[(size_t)k * a.ld + i];
+    if (a.mfac != nullptr) {
+      minv<D, double>(a.mfac + i, (int)a.ld, r, z);
+    } else {
+#pragma unroll
+      for (int k = 0; k < D; ++k) z[k] = r[k];
+    }
+    const double f = phase == 1 ? a.omega : 1.0;
+#pragma unroll
+    for (int k = 0; k < D; ++k) a.u[(size_t)k * a.ld + i] = f * z[k];
+  } else if (phase == 2) {
+    if (i < a.n_black) ssor_phase<D>(a, s, a.black[i], 2);
+  } else {
+    if (i < a.n_red) ssor_phase<D>(a, s, a.red[i], 3);
+  }
+}
+
+template <int D>
+static cudaError_t precond_apply_d(const PcgArgs& a, cudaStream_t stream) {
+  const int g = (a.N + PCG_THREADS - 1) / PCG_THREADS;
+  if (!a.ssor) {
+    k_precond_phase<D><<<g, PCG_THREADS, 0, stream>>>(a, 0);
+    return cudaGetLastError();
+  }
+  if (a.mfac == nullptr) return cudaErrorInvalidValue;
+  for (int phase = 1; phase <= 3; ++phase) {
+    k_precond_phase<D><<<g, PCG_THREADS, 0, stream>>>(a, phase);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_precond_apply(int D, const PcgArgs& a, cudaStream_t stream) {
+  switch (D) {
+#define CASE(d) case d: return precond_apply_d<d>(a, stream);
+    BFMRI_PCG_CASES(CASE)
+#undef CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
 
 cudaError_t launch_pcg(int D, const PcgArgs& a, cudaStream_t stream, int* grid_out) {
   switch (D) {

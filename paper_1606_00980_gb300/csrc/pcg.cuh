@@ -62,6 +62,15 @@ struct PcgArgs {
   float* d32;
   double inner_tol;      // relative tolerance of each inner solve
   int max_inner;         // inner iteration cap per refinement step
+  // red-black symmetric SOR preconditioning (FP64 solvers only); mfac holds the
+  // block-Jacobi factor of the diagonal blocks it is built on
+  int ssor;
+  double omega;          // relaxation, 0 < omega < 2
+  const int* red;        // [n_red] compact indices of the voxels with x + y + z even
+  int n_red;
+  const int* black;      // [n_black] compact indices of the others
+  int n_black;
+  const unsigned char* colour;  // [ld] 0 red, 1 black (resident variant)
 };
 
 // Launches the cooperative persistent PCG kernel for dimension D (1..12) on `stream`.
@@ -70,6 +79,12 @@ cudaError_t launch_pcg(int D, const PcgArgs& a, cudaStream_t stream, int* grid_o
 
 // Largest grid the cooperative launch of dimension D can use on the current device.
 int pcg_max_grid(int D);
+
+// One application of the solver's preconditioner, u = M^-1 r (a.r in, a.u out): block-Jacobi
+// (mfac), none (mfac null), or red-black symmetric SOR (a.ssor) in its three colour phases
+// as separate launches. Used to inspect the preconditioner; the solvers run the same
+// per-voxel arithmetic inside their persistent launches.
+cudaError_t launch_precond_apply(int D, const PcgArgs& a, cudaStream_t stream);
 
 constexpr int PCG_THREADS = 256;
 constexpr int DMAX = 12;

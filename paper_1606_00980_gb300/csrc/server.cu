@@ -154,7 +154,7 @@ size_t bfmri_request_device_bytes(int N, int T, int K, int P, int y_dtype, int p
   const size_t ld = ceil32((size_t)N), D = std::max(K, P), Pa = std::max(P, 1);
   const size_t nt = D * (D + 1) / 2, syy = (size_t)(P + 1) * (P + 2) / 2;
   const size_t nstats = syy + (size_t)K * (P + 1) * (P + 1);
-  size_t b = 7 * ld * sizeof(int);                                       // neighbours, lattice index
+  size_t b = 9 * ld * sizeof(int) + ld;                                  // neighbours, lattice index, colours
   b += (size_t)T * N * (y_dtype == BFMRI_F64 ? 8 : 4);                   // Y (released after stats)
   b += (nstats + K + Pa + 1 + syy + 2 * nt + 7 * D) * ld * sizeof(double);
   if (precision == BFMRI_PREC_MIXED) b += (2 * nt + 6 * D) * ld * sizeof(float);

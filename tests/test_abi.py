@@ -49,7 +49,7 @@ def test_default_options_without_gpu(lib):
     o = bfmri.bfmri_default_options()
     assert (o.q1, o.q2, o.u1, o.u2, o.r1, o.r2) == (10.0, 0.1, 10.0, 0.1, 10000.0, 0.1)
     assert o.delta == 1e-8 and o.precond == bfmri.PRECOND_BLOCK_JACOBI
-    assert o.debug_skip_block == -1 and o.inner_tol == 1e-6
+    assert o.debug_skip_block == -1 and o.inner_tol == 1e-6 and o.ssor_omega == 1.0
 
 
 def test_create_rejects_bad_arguments_without_touching_the_gpu(lib):
@@ -67,6 +67,14 @@ def test_create_rejects_bad_arguments_without_touching_the_gpu(lib):
         with pytest.raises(bfmri.BfmriError) as ei:
             bfmri.bfmri_create(lat, m, x[:, :K] if K <= 2 else np.ones((20, K)), y, K, P,
                                torch_memory=False)
+        assert ei.value.status == -1
+    for fields in (dict(precond=2, ssor_omega=2.0), dict(precond=2, ssor_omega=0.0),
+                   dict(precond=2, precision=1), dict(precond=3)):
+        o = bfmri.bfmri_default_options()
+        for k, v in fields.items():
+            setattr(o, k, v)
+        with pytest.raises(bfmri.BfmriError) as ei:
+            bfmri.bfmri_create((4, 3, 2, 6), mask, X, Y, 2, 1, opts=o, torch_memory=False)
         assert ei.value.status == -1
     Yn = Y.copy()
     Yn[3, 5] = np.nan
