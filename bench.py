@@ -39,7 +39,9 @@ if ROOT not in sys.path:
 
 METRIC = "posterior W-draws/s + HBM-roofline fraction, 3D K=6; p50/p99 batched solve"
 UNIT = "W-draws/s"
-WORKLOAD = "wholebrain3d_64x64x33_ellipsoid_N49928_T300_K6_AR3_fp64_blockjacobi_delta1e-8"
+def workload_name(args):
+    pc = "ssor" if getattr(args, "precond", "ssor") == "ssor" else "blockjacobi"
+    return f"wholebrain3d_64x64x33_ellipsoid_N49928_T300_K6_AR3_fp64_{pc}_delta1e-8"
 
 
 def peaks():
@@ -55,17 +57,30 @@ def peaks():
 FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12
 
 
-def pcg_flops_per_voxel_iter(K):
+def pcg_flops_per_voxel_iter(K, ssor=False):
     """FP64 flops of one Chronopoulos-Gear PCG iteration per voxel: four axpys (p, s, x, r)
     8K, block-Jacobi triangular solves 2K^2 + 2K, block product 2K^2, stencil with up to six
-    neighbours 6K + 3K, three inner products 6K."""
-    return 4 * K * K + 25 * K
+    neighbours 6K + 3K, three inner products 6K. Red-black SSOR adds the omega scaling K and
+    its two colour phases, each over half of the voxels: neighbour sum 6K, right-hand side
+    2K (black) or K (red), triangular solves 2K^2, update K (black) or 3K (red)."""
+    base = 4 * K * K + 25 * K
+    if not ssor:
+        return base
+    return base + K + ((6 * K + 2 * K + 2 * K * K + K) + (6 * K + K + 2 * K * K + 3 * K)) / 2
 
 
 def pcg_bytes_per_voxel_iter(K, w=8):
     """Algorithmic bytes of one PCG iteration per voxel: 11 vector passes of K words plus the
     data block and the preconditioner factor (K(K+1)/2 words each)."""
     return w * (11 * K + 2 * (K * (K + 1) // 2))
+
+
+def precond_options(args):
+    """Options of the headline FP64 chain's preconditioner (--precond)."""
+    from paper_1606_00980_gb300 import bfmri
+    if args.precond == "ssor":
+        return {"precond": bfmri.PRECOND_SSOR, "ssor_omega": 1.0}
+    return {"precond": bfmri.PRECOND_BLOCK_JACOBI}
 
 
 class ClockSampler:
@@ -199,7 +214,7 @@ def run_reference(args, world, rank):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "l2": "host run"},
+            "data": "synthetic", "config": {"workload": workload_name(args), "l2": "host run"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_threads(),
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -219,7 +234,8 @@ def run_ours(args, world, rank, local):
 
     w = synth.wholebrain3d()
     K, P, N, T = w.K, w.P, w.N, w.T
-    m = Model.from_workload(w, delta=1e-8, seed=2024, stream_id=rank, profile=1)
+    m = Model.from_workload(w, delta=1e-8, seed=2024, stream_id=rank, profile=1,
+                            **precond_options(args))
     m.precompute_stats()
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
@@ -259,7 +275,9 @@ def run_ours(args, world, rank, local):
     launches = max(pw["launches"], 1)
     dur_s = pw["ms"] / 1e3 / launches
     iters_per_launch = it_w / launches
-    flops = N * (iters_per_launch * pcg_flops_per_voxel_iter(K) + 2 * (4 * K * K + 25 * K))
+    ssor = args.precond == "ssor"
+    flops = N * (iters_per_launch * pcg_flops_per_voxel_iter(K, ssor) +
+                 2 * pcg_flops_per_voxel_iter(K, ssor))
     bytes_ = N * iters_per_launch * pcg_bytes_per_voxel_iter(K)
     hbm_peak, hbm_src, _ = peaks()
     achieved_tf = flops / dur_s / 1e12
@@ -301,7 +319,7 @@ def run_ours(args, world, rank, local):
                 "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": total_s / args.steps * 1e3, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "N": N, "T": T, "K": K, "P": P,
+                "config": {"workload": workload_name(args), "N": N, "T": T, "K": K, "P": P,
                            "parallelism": f"replicas{world}", "l2": "flushed between steps (256 MB write)",
                            "pcg_iterations_W_per_sweep": it_w / args.steps,
                            "pcg_iterations_A_per_sweep": it_a / args.steps},
@@ -586,7 +604,7 @@ def run_e2e(args, w):
     Wh = torch.empty((w.K, w.N), dtype=torch.float64, pin_memory=True).numpy()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    m = Model.from_workload(w, delta=1e-8, seed=77)
+    m = Model.from_workload(w, delta=1e-8, seed=77, **precond_options(args))
     m.precompute_stats()
     for s in range(S):
         m.gibbs_sweep(1, s, info=False)
@@ -615,6 +633,9 @@ def main():
     ap.add_argument("--no-svb", action="store_true")
     ap.add_argument("--no-chains", action="store_true")
     ap.add_argument("--no-precond", action="store_true")
+    ap.add_argument("--precond", choices=["ssor", "bj"], default="ssor",
+                    help="preconditioner of the FP64 headline chain (the mixed-precision and "
+                         "multi-RHS solves use block-Jacobi)")
     ap.add_argument("--only-batched", action="store_true",
                     help="run only the batched-probe measurement (profiling entry point)")
     ap.add_argument("--serving-requests", type=int, default=96)
