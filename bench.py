@@ -75,6 +75,12 @@ def pcg_bytes_per_voxel_iter(K, w=8):
     return w * (11 * K + 2 * (K * (K + 1) // 2))
 
 
+# DRAM bytes (read + write) of one W-solve launch of the current resident SSOR solver on the
+# whole-brain workload, from one ncu capture of this kernel version (22.99 MB + 0.63 MB): the
+# first touch of the staged blocks, factors, b and x; the iterations run from L2.
+NCU_TRAFFIC_W_SSOR = 23.62e6
+
+
 def precond_options(args):
     """Options of the headline FP64 chain's preconditioner (--precond)."""
     from paper_1606_00980_gb300 import bfmri
@@ -286,9 +292,10 @@ def run_ours(args, world, rank, local):
     # kernels per timed launch group: edge terms + assembly (W, A), quadratic form + draw (hyper)
     per_group = {"assemble_W": 2, "assemble_A": 2, "hyper": 2}
     n_launch = sum(v["launches"] * per_group.get(k, 1) for k, v in tim.items())
-    roof = {"kernel": f"k_pcg<{K}> (W solve)", "bound": "alu", "achieved": achieved_tf,
+    roof = {"kernel": f"k_pcg_res<{K}> (W solve, {'SSOR' if ssor else 'block-Jacobi'})",
+            "bound": "alu", "achieved": achieved_tf,
             "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved_tf / FP64_PEAK_TFLOPS,
-            "traffic": None,
+            "traffic": NCU_TRAFFIC_W_SSOR if ssor else None,
             "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2070 MHz",
             "hbm_view": {"achieved_gbs": achieved_gbs, "peak_gbs": hbm_peak,
                          "frac": achieved_gbs / hbm_peak, "peak_source": f"{hbm_src} (MEASURED_PEAKS.json)"},
