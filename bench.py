@@ -345,7 +345,7 @@ def run_mixed(args, w, flush, stream):
     from paper_1606_00980_gb300 import bfmri
     from paper_1606_00980_gb300.bfmri import Model
     m = Model.from_workload(w, delta=1e-8, seed=2024, precision=bfmri.PREC_MIXED, inner_tol=1e-6,
-                            profile=1)
+                            profile=1, **precond_options(args))
     m.precompute_stats()
     counter = 0
     for _ in range(args.warmup):
@@ -373,7 +373,7 @@ def run_mixed(args, w, flush, stream):
     st = m.get_state()
     W_mixed, _ = m.sample_W(counter + 1)
     m.close()
-    m64 = Model.from_workload(w, delta=1e-12, seed=2024)
+    m64 = Model.from_workload(w, delta=1e-12, seed=2024, **precond_options(args))
     m64.precompute_stats()
     m64.set_state(W=st["W"], A=st["A"], lam=st["lam"], alpha=st["alpha"], beta=st["beta"])
     W64, _ = m64.sample_W(counter + 1)
@@ -382,7 +382,7 @@ def run_mixed(args, w, flush, stream):
     err = float(np.linalg.norm(W_mixed - W64) / np.linalg.norm(W64))
     return {"value": args.steps / tot, "unit": UNIT, "ms_per_step": tot / args.steps * 1e3,
             "draw_rel_l2_vs_fp64": err,
-            "delta": 1e-8, "inner_tol": 1e-6,
+            "delta": 1e-8, "inner_tol": 1e-6, "precond": args.precond,
             "inner_iterations_W_per_sweep": it_w / args.steps,
             "kernel_ms_per_step": {k: v["ms"] / args.steps for k, v in tim.items() if v["launches"]}}
 
@@ -446,7 +446,11 @@ def run_precond_compare(args, w, n_draws=10):
              ("ssor_omega1.0_resident", dict(precond=bfmri.PRECOND_SSOR, ssor_omega=1.0)),
              ("ssor_omega1.0_streaming", dict(precond=bfmri.PRECOND_SSOR, ssor_omega=1.0,
                                               pcg_variant=bfmri.PCG_STREAMING)),
-             ("ssor_omega1.2_resident", dict(precond=bfmri.PRECOND_SSOR, ssor_omega=1.2))]
+             ("ssor_omega1.2_resident", dict(precond=bfmri.PRECOND_SSOR, ssor_omega=1.2)),
+             ("mixed_block_jacobi_resident", dict(precond=bfmri.PRECOND_BLOCK_JACOBI,
+                                                  precision=bfmri.PREC_MIXED)),
+             ("mixed_ssor_omega1.0_resident", dict(precond=bfmri.PRECOND_SSOR, ssor_omega=1.0,
+                                                   precision=bfmri.PREC_MIXED))]
     out = {}
     for name, opts in cases:
         m = Model.from_workload(w, delta=1e-8, seed=2024, profile=1, **opts)
@@ -641,8 +645,8 @@ def main():
     ap.add_argument("--no-chains", action="store_true")
     ap.add_argument("--no-precond", action="store_true")
     ap.add_argument("--precond", choices=["ssor", "bj"], default="ssor",
-                    help="preconditioner of the FP64 headline chain (the mixed-precision and "
-                         "multi-RHS solves use block-Jacobi)")
+                    help="preconditioner of the headline chain and of its mixed-precision twin "
+                         "(the multi-RHS solves use block-Jacobi)")
     ap.add_argument("--only-batched", action="store_true",
                     help="run only the batched-probe measurement (profiling entry point)")
     ap.add_argument("--serving-requests", type=int, default=96)

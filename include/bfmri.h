@@ -60,9 +60,9 @@ typedef struct {
 #define BFMRI_PRECOND_BLOCK_JACOBI 1  /* per-voxel (block + alpha * degree) Cholesky */
 #define BFMRI_PRECOND_SSOR         2  /* red-black symmetric SOR over those voxel blocks:
                                          M = (Dg + w L) Dg^-1 (Dg + w U) / (w (2 - w)), w =
-                                         ssor_omega, red = voxels with x + y + z even. FP64
-                                         single solves only (creation with the mixed precision
-                                         fails); multi-RHS solves use the block-Jacobi blocks */
+                                         ssor_omega, red = voxels with x + y + z even. Single
+                                         solves, FP64 and mixed (FP32 inner iterations); the
+                                         multi-RHS solves use the block-Jacobi blocks */
 
 #define BFMRI_PREC_FP64  0  /* FP64 PCG */
 #define BFMRI_PREC_MIXED 1  /* FP32 inner PCG inside an FP64 iterative-refinement loop */

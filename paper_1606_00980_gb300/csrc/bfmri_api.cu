@@ -298,7 +298,7 @@ bfmri_status run_pcg(bfmri_handle* h, int D, const double* scale, double* x, int
   a.mixed = h->opt.precision == BFMRI_PREC_MIXED;
   a.blocks32 = h->d_blocks32;
   a.mfac32 = h->opt.precond != BFMRI_PRECOND_NONE ? h->d_mfac32 : nullptr;
-  a.ssor = h->opt.precond == BFMRI_PRECOND_SSOR && h->opt.precision == BFMRI_PREC_FP64;
+  a.ssor = h->opt.precond == BFMRI_PRECOND_SSOR;
   a.omega = h->opt.ssor_omega;
   a.red = h->d_red;
   a.n_red = h->n_red;
@@ -639,8 +639,6 @@ bfmri_status bfmri_create(const bfmri_lattice* lat, const uint8_t* mask, const d
     return fail(nullptr, BFMRI_ERR_INVALID_ARG, "unknown preconditioner");
   if (o.precond == BFMRI_PRECOND_SSOR && !(o.ssor_omega > 0.0 && o.ssor_omega < 2.0))
     return fail(nullptr, BFMRI_ERR_INVALID_ARG, "ssor_omega must be in (0, 2)");
-  if (o.precond == BFMRI_PRECOND_SSOR && o.precision != BFMRI_PREC_FP64)
-    return fail(nullptr, BFMRI_ERR_INVALID_ARG, "SSOR preconditioning is implemented for the FP64 solver only");
   if (o.precision != BFMRI_PREC_FP64 && o.precision != BFMRI_PREC_MIXED)
     return fail(nullptr, BFMRI_ERR_INVALID_ARG, "unknown precision mode");
   if (o.precision == BFMRI_PREC_MIXED && !(o.inner_tol > 0.0 && o.inner_tol < 1.0))

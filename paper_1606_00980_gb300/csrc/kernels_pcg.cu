@@ -171,32 +171,33 @@ __device__ __forceinline__ void cg_scalar_step(Shared& sh, double gnew, double d
 //   2. black n:     u_n = (2 - omega) omega Dg_n^-1 (r_n + scale .* sum_m u_m)
 //   3. red n:       u_n = (2 - omega) u_n + omega Dg_n^-1 (scale .* sum_m u_m)
 // Phase 1 is the solver's block-Jacobi step scaled by omega; phases 2 and 3 are below
-// (streaming layout: factor, r and u in global memory).
-template <int D>
-__device__ __forceinline__ void ssor_phase(const PcgArgs& a, const double* s, int n, int phase) {
+// (streaming layout: factor Mf, r and u in global memory; element type T).
+template <int D, typename T>
+__device__ __forceinline__ void ssor_phase(const PcgArgs& a, const T* s, const T* Mf, const T* R,
+                                           T* U, int n, int phase) {
   const size_t ld = a.ld;
   int nb[6];
 #pragma unroll
   for (int d = 0; d < 6; ++d) nb[d] = d < a.ndir ? __ldg(a.nbr + (size_t)d * ld + n) : -1;
-  double sum[D];
+  T sum[D];
 #pragma unroll
-  for (int k = 0; k < D; ++k) sum[k] = 0.0;
+  for (int k = 0; k < D; ++k) sum[k] = T(0);
 #pragma unroll
   for (int d = 0; d < 6; ++d) {
     if (nb[d] >= 0) {
 #pragma unroll
-      for (int k = 0; k < D; ++k) sum[k] += ldx(a.u + (size_t)k * ld + nb[d]);
+      for (int k = 0; k < D; ++k) sum[k] += ldx(U + (size_t)k * ld + nb[d]);
     }
   }
-  double t[D], z[D];
+  T t[D], z[D];
 #pragma unroll
-  for (int k = 0; k < D; ++k) t[k] = phase == 2 ? a.r[(size_t)k * ld + n] + s[k] * sum[k] : s[k] * sum[k];
-  minv<D, double>(a.mfac + n, (int)ld, t, z);
-  const double c = 2.0 - a.omega;
+  for (int k = 0; k < D; ++k) t[k] = phase == 2 ? R[(size_t)k * ld + n] + s[k] * sum[k] : s[k] * sum[k];
+  minv<D, T>(Mf + n, (int)ld, t, z);
+  const T omega = (T)a.omega, c = T(2) - omega;
 #pragma unroll
   for (int k = 0; k < D; ++k) {
     const size_t o = (size_t)k * ld + n;
-    a.u[o] = phase == 2 ? c * a.omega * z[k] : c * a.u[o] + a.omega * z[k];
+    U[o] = phase == 2 ? c * omega * z[k] : c * U[o] + omega * z[k];
   }
 }
 
@@ -216,6 +217,75 @@ __device__ __forceinline__ void write_ctrl(const PcgArgs& a, int it, int restart
 
 }  // namespace
 
+// Resident SSOR ownership: the CTA's red voxels take its first threads and its black voxels
+// the next ones (stable within each colour), so the warps of each colour phase are uniform.
+// In: this thread's voxel n and whether it owns one; out: the colour-sorted voxel, ownership
+// and colour.
+__device__ __forceinline__ void colour_sort(const PcgArgs& a, int& n, bool& own, bool& is_red) {
+  __shared__ int sh_order[RES_MAX_THREADS];
+  __shared__ int sh_cnt[2 * (RES_MAX_THREADS / 32)];
+  const int t = threadIdx.x, bd = blockDim.x;
+  const bool blk = own && a.colour[n] != 0;
+  const bool rd = own && !blk;
+  const int lane = t & 31, warp = t >> 5, nwc = (bd + 31) >> 5;
+  const unsigned mr = __ballot_sync(0xffffffffu, rd), mb = __ballot_sync(0xffffffffu, blk);
+  if (lane == 0) {
+    sh_cnt[2 * warp] = __popc(mr);
+    sh_cnt[2 * warp + 1] = __popc(mb);
+  }
+  __syncthreads();
+  int red_before = 0, black_before = 0, nred = 0, nblack = 0;
+  for (int w = 0; w < nwc; ++w) {
+    if (w < warp) {
+      red_before += sh_cnt[2 * w];
+      black_before += sh_cnt[2 * w + 1];
+    }
+    nred += sh_cnt[2 * w];
+    nblack += sh_cnt[2 * w + 1];
+  }
+  const unsigned below = (1u << lane) - 1u;
+  if (rd) sh_order[red_before + __popc(mr & below)] = n;
+  if (blk) sh_order[nred + black_before + __popc(mb & below)] = n;
+  __syncthreads();
+  own = t < nred + nblack;
+  n = own ? sh_order[t] : 0;
+  is_red = t < nred;
+}
+
+// Resident SSOR phases 2 (black voxels) and 3 (red voxels) in element type T (FP64 solves,
+// or the FP32 inner iterations of the mixed ones), each after a grid barrier: u and r are this
+// thread's registers, Mp its factor in shared memory, U the published u of every voxel.
+template <int D, typename T, typename Bar>
+__device__ __forceinline__ bool resident_ssor_phases(const PcgArgs& a, Bar& bar, bool own, bool is_red,
+                                                     const int* nb, const T* s, const T* Mp, int bd,
+                                                     int n, const T* r, T* u, T* U) {
+  const T omega = (T)a.omega, c2 = T(2) - omega;
+  for (int phase = 2; phase <= 3; ++phase) {
+    if (!bar()) return false;
+    if (own && (phase == 2) != is_red) {
+      T sum[D], tv[D], z[D];
+#pragma unroll
+      for (int k = 0; k < D; ++k) sum[k] = T(0);
+#pragma unroll
+      for (int d = 0; d < 6; ++d) {
+        if (nb[d] >= 0) {
+#pragma unroll
+          for (int k = 0; k < D; ++k) sum[k] += ldx(U + (size_t)k * a.ld + nb[d]);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < D; ++k) tv[k] = phase == 2 ? r[k] + s[k] * sum[k] : s[k] * sum[k];
+      minv<D, T>(Mp, bd, tv, z);
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        u[k] = phase == 2 ? c2 * omega * z[k] : c2 * u[k] + omega * z[k];
+        U[(size_t)k * a.ld + n] = u[k];
+      }
+    }
+  }
+  return true;
+}
+
 // ---------------------------------------------------------------------------------------
 // Resident variant.
 // ---------------------------------------------------------------------------------------
@@ -230,37 +300,7 @@ __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_res(PcgArgs a) {
   int n = blockIdx.x * a.res_per + t;
   bool own = t < a.res_per && n < a.N;
   bool is_red = true;
-  if (a.ssor) {
-    // SSOR: the CTA's red voxels take the first threads and its black voxels the next ones
-    // (stable within each colour), so the warps of the colour phases are uniform
-    __shared__ int sh_order[RES_MAX_THREADS];
-    __shared__ int sh_cnt[2 * (RES_MAX_THREADS / 32)];
-    const bool blk = own && a.colour[n] != 0;
-    const bool rd = own && !blk;
-    const int lane = t & 31, warp = t >> 5, nwc = (bd + 31) >> 5;
-    const unsigned mr = __ballot_sync(0xffffffffu, rd), mb = __ballot_sync(0xffffffffu, blk);
-    if (lane == 0) {
-      sh_cnt[2 * warp] = __popc(mr);
-      sh_cnt[2 * warp + 1] = __popc(mb);
-    }
-    __syncthreads();
-    int red_before = 0, black_before = 0, nred = 0, nblack = 0;
-    for (int w = 0; w < nwc; ++w) {
-      if (w < warp) {
-        red_before += sh_cnt[2 * w];
-        black_before += sh_cnt[2 * w + 1];
-      }
-      nred += sh_cnt[2 * w];
-      nblack += sh_cnt[2 * w + 1];
-    }
-    const unsigned below = (1u << lane) - 1u;
-    if (rd) sh_order[red_before + __popc(mr & below)] = n;
-    if (blk) sh_order[nred + black_before + __popc(mb & below)] = n;
-    __syncthreads();
-    own = t < nred + nblack;
-    n = own ? sh_order[t] : 0;
-    is_red = t < nred;
-  }
+  if (a.ssor) colour_sort(a, n, own, is_red);
   const size_t ld = a.ld;
   const bool pre = a.mfac != nullptr;
 #pragma unroll
@@ -290,34 +330,11 @@ __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_res(PcgArgs a) {
     if (a.skip_block == (int)blockIdx.x) return false;
     return grid_sync(a.bar, &sh.flag);
   };
-  const double omega = a.omega, c2 = 2.0 - a.omega;
+  const double omega = a.omega;
   // SSOR phase 1 is the block-Jacobi step scaled by omega (u published by the caller);
   // phases 2 (black voxels) and 3 (red voxels) follow, each after a barrier
   auto ssor_phases = [&]() -> bool {
-    for (int phase = 2; phase <= 3; ++phase) {
-      if (!bar()) return false;
-      if (own && (phase == 2) != is_red) {
-        double sum[D], tv[D], z[D];
-#pragma unroll
-        for (int k = 0; k < D; ++k) sum[k] = 0.0;
-#pragma unroll
-        for (int d = 0; d < 6; ++d) {
-          if (nb[d] >= 0) {
-#pragma unroll
-            for (int k = 0; k < D; ++k) sum[k] += ldx(a.u + (size_t)k * ld + nb[d]);
-          }
-        }
-#pragma unroll
-        for (int k = 0; k < D; ++k) tv[k] = phase == 2 ? r[k] + s[k] * sum[k] : s[k] * sum[k];
-        minv<D, double>(Mp, bd, tv, z);
-#pragma unroll
-        for (int k = 0; k < D; ++k) {
-          u[k] = phase == 2 ? c2 * omega * z[k] : c2 * u[k] + omega * z[k];
-          a.u[(size_t)k * ld + n] = u[k];
-        }
-      }
-    }
-    return true;
+    return resident_ssor_phases<D, double>(a, bar, own, is_red, nb, s, Mp, bd, n, r, u, a.u);
   };
   // (r, u, w) from the current x, with partials (r'u, w'u, r'r, b'b)
   auto restart = [&](double* tot) -> bool {
@@ -471,9 +488,9 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_stream(PcgArgs a) {
   // SSOR phases 2 (black voxels) and 3 (red voxels), each after a barrier
   auto ssor_rest = [&]() -> bool {
     if (!bar()) return false;
-    for (int i = tid; i < a.n_black; i += nth) ssor_phase<D>(a, s, a.black[i], 2);
+    for (int i = tid; i < a.n_black; i += nth) ssor_phase<D, double>(a, s, a.mfac, a.r, a.u, a.black[i], 2);
     if (!bar()) return false;
-    for (int i = tid; i < a.n_red; i += nth) ssor_phase<D>(a, s, a.red[i], 3);
+    for (int i = tid; i < a.n_red; i += nth) ssor_phase<D, double>(a, s, a.mfac, a.r, a.u, a.red[i], 3);
     return true;
   };
   // r = b - B~ x, u = M^-1 r (published); then w = B~ u and partials.
@@ -636,8 +653,10 @@ __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_mixed_res(PcgArgs a)
   double* shB = smem;                                   // [NT][bd] FP64 blocks
   float* shB32 = reinterpret_cast<float*>(smem + NT * bd);   // [NT][bd]
   float* shM32 = shB32 + NT * bd;                       // [NT][bd]
-  const int n = blockIdx.x * a.res_per + t;
-  const bool own = t < a.res_per && n < a.N;
+  int n = blockIdx.x * a.res_per + t;
+  bool own = t < a.res_per && n < a.N;
+  bool is_red = true;
+  if (a.ssor) colour_sort(a, n, own, is_red);
   const size_t ld = a.ld;
   const bool pre = a.mfac32 != nullptr;
 #pragma unroll
@@ -716,10 +735,16 @@ __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_mixed_res(PcgArgs a)
     // inner target: inner_tol relative, but no further than the outer stop needs
     const double itol2 = fmax(a.inner_tol * a.inner_tol * rr, 0.25 * tol2);
     minv<D, float>(Mp32, bd, r, u);
+    if (a.ssor) {
+#pragma unroll
+      for (int k = 0; k < D; ++k) u[k] *= (float)a.omega;
+    }
     if (own) {
 #pragma unroll
       for (int k = 0; k < D; ++k) a.u32[(size_t)k * ld + n] = u[k];
     }
+    if (a.ssor && !resident_ssor_phases<D, float>(a, bar, own, is_red, nb, s32, Mp32, bd, n, r, u, a.u32))
+      return;
     if (!bar()) return;
     amul<D, float>(Bp32, bd, s32, nb, a.ndir, degf, u, a.u32, ld, w);
     {
@@ -749,10 +774,16 @@ __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_mixed_res(PcgArgs a)
         r[k] -= fa * q[k];
       }
       minv<D, float>(Mp32, bd, r, u);
+      if (a.ssor) {
+#pragma unroll
+        for (int k = 0; k < D; ++k) u[k] *= (float)a.omega;
+      }
       if (own) {
 #pragma unroll
         for (int k = 0; k < D; ++k) a.u32[(size_t)k * ld + n] = u[k];
       }
+      if (a.ssor && !resident_ssor_phases<D, float>(a, bar, own, is_red, nb, s32, Mp32, bd, n, r, u, a.u32))
+        return;
       if (!bar()) return;
       amul<D, float>(Bp32, bd, s32, nb, a.ndir, degf, u, a.u32, ld, w);
       float g = 0.f, dl = 0.f, q2 = 0.f;
@@ -826,10 +857,22 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_mixed_stream(PcgArgs a) {
   auto precond = [&](int n, const float* rn, float* un) {
     if (pre) {
       minv<D, float>(a.mfac32 + n, (int)ld, rn, un);
+      if (a.ssor) {
+#pragma unroll
+        for (int k = 0; k < D; ++k) un[k] *= (float)a.omega;   // SSOR phase 1
+      }
     } else {
 #pragma unroll
       for (int k = 0; k < D; ++k) un[k] = rn[k];
     }
+  };
+  // SSOR phases 2 (black voxels) and 3 (red voxels) of the inner iterations, each after a barrier
+  auto ssor_rest = [&]() -> bool {
+    if (!bar()) return false;
+    for (int i = tid; i < a.n_black; i += nth) ssor_phase<D, float>(a, s32, a.mfac32, a.r32, a.u32, a.black[i], 2);
+    if (!bar()) return false;
+    for (int i = tid; i < a.n_red; i += nth) ssor_phase<D, float>(a, s32, a.mfac32, a.r32, a.u32, a.red[i], 3);
+    return true;
   };
   // inner matvec phase: w = B~ u and the three partial sums
   auto matvec_partials = [&](double* tot) -> bool {
@@ -913,6 +956,7 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_mixed_stream(PcgArgs a) {
     // inner target: inner_tol relative, but no further than the outer stop needs
     const double itol2 = fmax(a.inner_tol * a.inner_tol * rr, 0.25 * tol2);
     // u was published by the residual phase, whose reducing barrier has completed
+    if (a.ssor && (!ssor_rest() || !bar())) return;
     if (!matvec_partials(tot)) return;
     double gam = tot[0], del = tot[1];
     if (!(del > 0.0) || !isfinite(del)) { status = isfinite(del) ? 3 : 7; break; }
@@ -952,6 +996,7 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_mixed_stream(PcgArgs a) {
           a.u32[o] = un[k];
         }
       }
+      if (a.ssor && !ssor_rest()) return;
       if (!bar()) return;
       if (!matvec_partials(tot)) return;
       ++it;
@@ -1093,9 +1138,9 @@ __global__ void __launch_bounds__(PCG_THREADS) k_precond_phase(PcgArgs a, int ph
 #pragma unroll
     for (int k = 0; k < D; ++k) a.u[(size_t)k * a.ld + i] = f * z[k];
   } else if (phase == 2) {
-    if (i < a.n_black) ssor_phase<D>(a, s, a.black[i], 2);
+    if (i < a.n_black) ssor_phase<D, double>(a, s, a.mfac, a.r, a.u, a.black[i], 2);
   } else {
-    if (i < a.n_red) ssor_phase<D>(a, s, a.red[i], 3);
+    if (i < a.n_red) ssor_phase<D, double>(a, s, a.mfac, a.r, a.u, a.red[i], 3);
   }
 }
 

@@ -119,3 +119,33 @@ def test_ssor_takes_fewer_iterations_than_block_jacobi(variant):
         its[name] = info.iterations
         m.close()
     assert its["ssor"] < its["bj"]
+
+
+@pytest.mark.parametrize("variant", ["auto", "streaming"])
+def test_mixed_ssor_reaches_the_exact_draw(case, variant):
+    """The mixed solver preconditions its FP32 inner iterations with SSOR (FP32 factor and
+    phases); the FP64 refinement still reaches the exact draw."""
+    from paper_1606_00980_gb300 import bfmri
+    w, lat, s = case
+    m = make(w, s, precond=bfmri.PRECOND_SSOR, precision=bfmri.PREC_MIXED,
+             pcg_variant=bfmri.PCG_AUTO if variant == "auto" else bfmri.PCG_STREAMING)
+    W, info = m.sample_W(counter=3)
+    Bd, bw = model.w_blocks_direct(w.Y, w.X, s["A"], s["lam"], w.eps)
+    ref, _ = gibbs.draw_gmrf(lat, Bd, bw, s["alpha"], SEED, 3, philox.TAG_W)
+    assert info.rel_residual <= 1e-12
+    assert rel(W, ref) <= 1e-8
+    assert info.refinements >= 1
+    m.close()
+
+
+def test_mixed_ssor_takes_fewer_inner_iterations():
+    from paper_1606_00980_gb300 import bfmri
+    w = WL["slab_K6_P3"]
+    s = state_for(w, np.random.default_rng(10))
+    its = {}
+    for name, pc in (("bj", bfmri.PRECOND_BLOCK_JACOBI), ("ssor", bfmri.PRECOND_SSOR)):
+        m = make(w, s, precond=pc, precision=bfmri.PREC_MIXED, delta=1e-8)
+        _, info = m.sample_W(counter=1)
+        its[name] = info.iterations
+        m.close()
+    assert its["ssor"] < its["bj"]
