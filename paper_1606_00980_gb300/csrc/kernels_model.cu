@@ -84,12 +84,30 @@ __global__ void __launch_bounds__(STATS_THREADS) k_stats(StatsArgs a) {
 // Sxy[p][q] with c = (1, -a_n); perturbed rhs = b_n + L_n z2_n + sum_k sqrt(alpha_k) (G'z1_k)_n
 // with L_n = chol(Bd_n); preconditioner factor chol(Bd_n + diag(alpha) deg_n).
 // ---------------------------------------------------------------------------------------
+// The weights c_p c_q (and the SVB moments) are symmetric in (p, q) and Sxx[q][p] =
+// Sxx[p][q]', so the block needs only the pairs p <= q: shT[syy_index(p, q)] holds the packed
+// lower triangle of Sxx[p][p], or of Sxx[p][q] + Sxx[p][q]' for p < q ((P+1)(P+2)/2 packed
+// matrices instead of (P+1)^2 full ones).
 template <int K>
 __global__ void __launch_bounds__(VOX_THREADS) k_assemble_w(AssembleArgs a) {
-  extern __shared__ double shS[];
+  extern __shared__ double shT[];
   const int P = a.P;
-  const int nS = (P + 1) * (P + 1) * K * K;
-  for (int i = threadIdx.x; i < nS; i += blockDim.x) shS[i] = a.Sxx[i];
+  const int nT = n_syy(P) * ntri(K);
+  for (int idx = threadIdx.x; idx < nT; idx += blockDim.x) {
+    const int pq = idx / ntri(K), e = idx % ntri(K);
+    int p = 0, q = 0;
+    for (int pp = 0; pp <= P; ++pp)
+      for (int qq = pp; qq <= P; ++qq)
+        if (syy_index(pp, qq, P) == pq) {
+          p = pp;
+          q = qq;
+        }
+    int i = 0;
+    while ((i + 1) * (i + 2) / 2 <= e) ++i;
+    const int j = e - i * (i + 1) / 2;
+    const double* S = a.Sxx + (size_t)(p * (P + 1) + q) * K * K;
+    shT[idx] = p == q ? S[i * K + j] : S[i * K + j] + S[j * K + i];
+  }
   __syncthreads();
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= a.g.N) return;
@@ -110,11 +128,11 @@ __global__ void __launch_bounds__(VOX_THREADS) k_assemble_w(AssembleArgs a) {
       if (p <= P && q <= P) {
         const double cpq = a.Cmom ? __ldg(a.Cmom + (size_t)syy_index(p < q ? p : q, p < q ? q : p, P) * ld + n)
                                   : c[p] * c[q];
-        const double* S = shS + (size_t)(p * (P + 1) + q) * K * K;
+        if (p <= q) {
+          const double* T = shT + (size_t)syy_index(p, q, P) * ntri(K);
 #pragma unroll
-        for (int i = 0; i < K; ++i)
-#pragma unroll
-          for (int j = 0; j <= i; ++j) B[tri(i, j)] += cpq * S[i * K + j];
+          for (int e = 0; e < ntri(K); ++e) B[e] += cpq * T[e];
+        }
 #pragma unroll
         for (int k = 0; k < K; ++k) bw[k] += cpq * __ldg(a.stats + sxy_plane(p, q, k, K, P) * ld + n);
       }
@@ -475,7 +493,7 @@ cudaError_t launch_stats(const StatsArgs& a, cudaStream_t s) {
 
 template <int K>
 static cudaError_t assemble_w_k(const AssembleArgs& a, cudaStream_t s) {
-  const size_t shm = (size_t)(a.P + 1) * (a.P + 1) * K * K * sizeof(double);
+  const size_t shm = (size_t)n_syy(a.P) * ntri(K) * sizeof(double);
   cudaFuncSetAttribute(k_assemble_w<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
   k_assemble_w<K><<<(a.g.N + VOX_THREADS - 1) / VOX_THREADS, VOX_THREADS, shm, s>>>(a);
   return cudaGetLastError();

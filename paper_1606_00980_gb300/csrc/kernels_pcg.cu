@@ -342,10 +342,17 @@ __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_res(PcgArgs a) {
     amul<D, double>(Bp, bd, s, nb, a.ndir, degd, x, a.x, ld, ax);
 #pragma unroll
     for (int k = 0; k < D; ++k) r[k] = bv[k] - ax[k];
-    minv<D, double>(Mp, bd, r, u);
-    if (a.ssor) {
+    // SSOR phase 1 (red voxels only: the black ones are overwritten by phase 2 before
+    // anyone reads them); the colour-sorted warps keep this branch uniform
+    if (!a.ssor) {
+      minv<D, double>(Mp, bd, r, u);
+    } else if (is_red) {
+      minv<D, double>(Mp, bd, r, u);
 #pragma unroll
       for (int k = 0; k < D; ++k) u[k] *= omega;
+    } else {
+#pragma unroll
+      for (int k = 0; k < D; ++k) u[k] = 0.0;   // defined for threads without a voxel
     }
     if (own) {
 #pragma unroll
@@ -390,10 +397,17 @@ __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_res(PcgArgs a) {
       x[k] += alpha * p[k];
       r[k] -= alpha * q[k];
     }
-    minv<D, double>(Mp, bd, r, u);
-    if (a.ssor) {
+    // SSOR phase 1 (red voxels only: the black ones are overwritten by phase 2 before
+    // anyone reads them); the colour-sorted warps keep this branch uniform
+    if (!a.ssor) {
+      minv<D, double>(Mp, bd, r, u);
+    } else if (is_red) {
+      minv<D, double>(Mp, bd, r, u);
 #pragma unroll
       for (int k = 0; k < D; ++k) u[k] *= omega;
+    } else {
+#pragma unroll
+      for (int k = 0; k < D; ++k) u[k] = 0.0;   // defined for threads without a voxel
     }
     if (own) {
 #pragma unroll
@@ -734,10 +748,15 @@ __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_mixed_res(PcgArgs a)
     }
     // inner target: inner_tol relative, but no further than the outer stop needs
     const double itol2 = fmax(a.inner_tol * a.inner_tol * rr, 0.25 * tol2);
-    minv<D, float>(Mp32, bd, r, u);
-    if (a.ssor) {
+    if (!a.ssor) {
+      minv<D, float>(Mp32, bd, r, u);
+    } else if (is_red) {   // SSOR phase 1, red voxels only
+      minv<D, float>(Mp32, bd, r, u);
 #pragma unroll
       for (int k = 0; k < D; ++k) u[k] *= (float)a.omega;
+    } else {
+#pragma unroll
+      for (int k = 0; k < D; ++k) u[k] = 0.f;   // defined for threads without a voxel
     }
     if (own) {
 #pragma unroll
@@ -773,10 +792,15 @@ __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_mixed_res(PcgArgs a)
         d[k] += fa * p[k];
         r[k] -= fa * q[k];
       }
-      minv<D, float>(Mp32, bd, r, u);
-      if (a.ssor) {
+      if (!a.ssor) {
+        minv<D, float>(Mp32, bd, r, u);
+      } else if (is_red) {   // SSOR phase 1, red voxels only
+        minv<D, float>(Mp32, bd, r, u);
 #pragma unroll
         for (int k = 0; k < D; ++k) u[k] *= (float)a.omega;
+      } else {
+#pragma unroll
+        for (int k = 0; k < D; ++k) u[k] = 0.f;   // defined for threads without a voxel
       }
       if (own) {
 #pragma unroll
