@@ -201,10 +201,9 @@ __global__ void __launch_bounds__(VOX_THREADS) k_assemble_w(AssembleArgs a) {
 // ---------------------------------------------------------------------------------------
 template <int K>
 __global__ void __launch_bounds__(VOX_THREADS) k_assemble_a(AssembleArgs a) {
-  extern __shared__ double shS[];
+  extern __shared__ double shQ[];
   const int P = a.P;
-  const int nS = (P + 1) * (P + 1) * K * K;
-  for (int i = threadIdx.x; i < nS; i += blockDim.x) shS[i] = a.Sxx[i];
+  load_quad_weights(a.Sxx, K, P, shQ);
   __syncthreads();
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= a.g.N) return;
@@ -213,30 +212,18 @@ __global__ void __launch_bounds__(VOX_THREADS) k_assemble_a(AssembleArgs a) {
 #pragma unroll
   for (int k = 0; k < K; ++k) w[k] = a.Gin ? 0.0 : a.W[(size_t)k * ld + n];
   double Gm[PMAX + 1][PMAX + 1];
+  if (!a.Gin) lagged_gram<K>(a.stats, shQ, w, P, ld, n, Gm);
 #pragma unroll
   for (int p = 0; p <= PMAX; ++p) {
 #pragma unroll
     for (int q = p; q <= PMAX; ++q) {
-      double g = 0.0;
       if (q <= P && a.Gin) {
-        g = __ldg(a.Gin + (size_t)syy_index(p, q, P) * ld + n);
+        Gm[p][q] = Gm[q][p] = __ldg(a.Gin + (size_t)syy_index(p, q, P) * ld + n);
       } else if (q <= P) {
-        double t1 = 0.0, t2 = 0.0, quad = 0.0;
-        const double* S = shS + (size_t)(p * (P + 1) + q) * K * K;
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-          t1 += w[k] * __ldg(a.stats + sxy_plane(q, p, k, K, P) * ld + n);
-          t2 += w[k] * __ldg(a.stats + sxy_plane(p, q, k, K, P) * ld + n);
-          double sk = 0.0;
-#pragma unroll
-          for (int j = 0; j < K; ++j) sk += S[k * K + j] * w[j];
-          quad += w[k] * sk;
-        }
-        g = __ldg(a.stats + (size_t)syy_index(p, q, P) * ld + n) - t1 - t2 + quad;
-        a.G[(size_t)syy_index(p, q, P) * ld + n] = g;
+        a.G[(size_t)syy_index(p, q, P) * ld + n] = Gm[p][q];
+      } else {
+        Gm[p][q] = Gm[q][p] = 0.0;
       }
-      Gm[p][q] = g;
-      Gm[q][p] = g;
     }
   }
   if (P == 0 || a.g_only) return;
@@ -501,7 +488,7 @@ static cudaError_t assemble_w_k(const AssembleArgs& a, cudaStream_t s) {
 
 template <int K>
 static cudaError_t assemble_a_k(const AssembleArgs& a, cudaStream_t s) {
-  const size_t shm = (size_t)(a.P + 1) * (a.P + 1) * K * K * sizeof(double);
+  const size_t shm = quad_weight_doubles(K, a.P) * sizeof(double);
   cudaFuncSetAttribute(k_assemble_a<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
   k_assemble_a<K><<<(a.g.N + VOX_THREADS - 1) / VOX_THREADS, VOX_THREADS, shm, s>>>(a);
   return cudaGetLastError();

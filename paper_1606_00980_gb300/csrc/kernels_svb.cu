@@ -44,10 +44,9 @@ __global__ void __launch_bounds__(SVB_THREADS) k_svb_cmom(SvbArgs a) {
 
 template <int K>
 __global__ void __launch_bounds__(SVB_THREADS) k_svb_gram(SvbArgs a) {
-  extern __shared__ double shS[];
+  extern __shared__ double shQ[];
   const int P = a.P;
-  const int nS = (P + 1) * (P + 1) * K * K;
-  for (int i = threadIdx.x; i < nS; i += blockDim.x) shS[i] = a.Sxx[i];
+  load_quad_weights(a.Sxx, K, P, shQ);
   __syncthreads();
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= a.g.N) return;
@@ -61,7 +60,7 @@ __global__ void __launch_bounds__(SVB_THREADS) k_svb_gram(SvbArgs a) {
     double w[K], G[PMAX + 1][PMAX + 1];
 #pragma unroll
     for (int k = 0; k < K; ++k) w[k] = a.Ws[(size_t)j * K * ld + (size_t)k * ld + n];
-    lagged_gram<K>(a.stats, shS, w, P, ld, n, G);
+    lagged_gram<K>(a.stats, shQ, w, P, ld, n, G);
 #pragma unroll
     for (int p = 0; p <= PMAX; ++p)
 #pragma unroll
@@ -103,10 +102,9 @@ __global__ void __launch_bounds__(SVB_THREADS) k_svb_rhs(SvbArgs a) {
 // E[lambda_n] = u~2 / (1/u1 + mean_j RSS_n(W^(j), A^(j)) / 2)
 template <int K>
 __global__ void __launch_bounds__(SVB_THREADS) k_svb_lambda(SvbArgs a) {
-  extern __shared__ double shS[];
+  extern __shared__ double shQ[];
   const int P = a.P;
-  const int nS = (P + 1) * (P + 1) * K * K;
-  for (int i = threadIdx.x; i < nS; i += blockDim.x) shS[i] = a.Sxx[i];
+  load_quad_weights(a.Sxx, K, P, shQ);
   __syncthreads();
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= a.g.N) return;
@@ -116,7 +114,7 @@ __global__ void __launch_bounds__(SVB_THREADS) k_svb_lambda(SvbArgs a) {
     double w[K], G[PMAX + 1][PMAX + 1], c[PMAX + 1];
 #pragma unroll
     for (int k = 0; k < K; ++k) w[k] = a.Ws[(size_t)j * K * ld + (size_t)k * ld + n];
-    lagged_gram<K>(a.stats, shS, w, P, ld, n, G);
+    lagged_gram<K>(a.stats, shQ, w, P, ld, n, G);
     c[0] = 1.0;
 #pragma unroll
     for (int p = 1; p <= PMAX; ++p) c[p] = p <= P ? -a.As[(size_t)j * P * ld + (size_t)(p - 1) * ld + n] : 0.0;
@@ -171,7 +169,7 @@ __global__ void __launch_bounds__(SVB_THREADS) k_svb_quad(SvbArgs a, const doubl
 template <int D>
 static cudaError_t svb_d(int what, const SvbArgs& a, cudaStream_t s, int* grid_out) {
   const int blocks = (a.g.N + SVB_THREADS - 1) / SVB_THREADS;
-  const size_t shm = (size_t)(a.P + 1) * (a.P + 1) * D * D * sizeof(double);
+  const size_t shm = quad_weight_doubles(D, a.P) * sizeof(double);
   switch (what) {
     case 1:
       cudaFuncSetAttribute(k_svb_gram<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);

@@ -79,12 +79,44 @@ __device__ __forceinline__ int degree(const Geometry& g, int n) {
   return deg;
 }
 
-// Lagged residual Gram G[p][q] = (L^p e)'(L^q e), e = y - X w, for p <= q <= P from the
-// statistics of voxel n and Sxx in shared memory ([(P+1)^2][K][K]); G is PMAX+1 square.
+// Quadratic-form weights of the lagged X products for the lag pairs p <= q, filled by the
+// whole CTA (the caller synchronises before use): Q[syy_index(p, q)][tri(i, j)] is
+// Sxx[p][q][i][i] on the diagonal and Sxx[p][q][i][j] + Sxx[p][q][j][i] below it, so that
+// w' Sxx[p][q] w = sum_e Q[e] w_i w_j: K(K+1)/2 multiply-adds per pair instead of K^2 + K.
+__host__ __device__ inline size_t quad_weight_doubles(int K, int P) {
+  return (size_t)n_syy(P) * (size_t)(K * (K + 1) / 2);
+}
+
+__device__ inline void load_quad_weights(const double* Sxx, int K, int P, double* Q) {
+  const int nt = K * (K + 1) / 2, total = n_syy(P) * nt;
+  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+    const int pq = idx / nt, e = idx % nt;
+    int p = 0, q = 0;
+    for (int pp = 0; pp <= P; ++pp)
+      for (int qq = pp; qq <= P; ++qq)
+        if (syy_index(pp, qq, P) == pq) {
+          p = pp;
+          q = qq;
+        }
+    int i = 0;
+    while ((i + 1) * (i + 2) / 2 <= e) ++i;
+    const int j = e - i * (i + 1) / 2;
+    const double* S = Sxx + (size_t)(p * (P + 1) + q) * K * K;
+    Q[idx] = i == j ? S[i * K + i] : S[i * K + j] + S[j * K + i];
+  }
+}
+
+// Lagged residual Gram G[p][q] = (L^p e)'(L^q e) of e = y - X w (symmetric; PMAX-padded with
+// zeros), from the statistics record and the quadratic-form weights Q.
 template <int K>
-__device__ __forceinline__ void lagged_gram(const double* __restrict__ stats, const double* shS,
+__device__ __forceinline__ void lagged_gram(const double* __restrict__ stats, const double* Q,
                                             const double* w, int P, size_t ld, int n,
                                             double G[PMAX + 1][PMAX + 1]) {
+  double ww[ntri(K)];
+#pragma unroll
+  for (int i = 0; i < K; ++i)
+#pragma unroll
+    for (int j = 0; j <= i; ++j) ww[tri(i, j)] = w[i] * w[j];
 #pragma unroll
   for (int p = 0; p <= PMAX; ++p) {
 #pragma unroll
@@ -92,16 +124,14 @@ __device__ __forceinline__ void lagged_gram(const double* __restrict__ stats, co
       double g = 0.0;
       if (q <= P) {
         double t1 = 0.0, t2 = 0.0, quad = 0.0;
-        const double* S = shS + (size_t)(p * (P + 1) + q) * K * K;
+        const double* Qpq = Q + (size_t)syy_index(p, q, P) * ntri(K);
 #pragma unroll
         for (int k = 0; k < K; ++k) {
           t1 += w[k] * __ldg(stats + (size_t)(n_syy(P) + (q * (P + 1) + p) * K + k) * ld + n);
           t2 += w[k] * __ldg(stats + (size_t)(n_syy(P) + (p * (P + 1) + q) * K + k) * ld + n);
-          double sk = 0.0;
-#pragma unroll
-          for (int j = 0; j < K; ++j) sk += S[k * K + j] * w[j];
-          quad += w[k] * sk;
         }
+#pragma unroll
+        for (int e = 0; e < ntri(K); ++e) quad += Qpq[e] * ww[e];
         g = __ldg(stats + (size_t)syy_index(p, q, P) * ld + n) - t1 - t2 + quad;
       }
       G[p][q] = g;
