@@ -401,6 +401,15 @@ class Model:
         self._c(self.lib.bfmri_get_state(self.handle, _ptr(W), _ptr(A), _ptr(lam), _ptr(alpha), _ptr(beta)))
         return dict(W=W, A=A, lam=lam, alpha=alpha, beta=beta[:self.P])
 
+    def get_W(self, out=None):
+        """The current W (K x N) into `out` (a C-contiguous float64 array, e.g. in pinned host
+        memory for a fast copy) or a new array."""
+        W = np.empty((self.K, self.N)) if out is None else out
+        if W.shape != (self.K, self.N) or W.dtype != np.float64 or not W.flags["C_CONTIGUOUS"]:
+            raise ValueError("out must be a C-contiguous float64 array of shape (K, N)")
+        self._c(self.lib.bfmri_get_state(self.handle, _ptr(W), None, None, None, None))
+        return W
+
     def sample_W(self, counter, out=True):
         W = np.empty((self.K, self.N)) if out else None
         info = bfmri_solve_info()

@@ -21,12 +21,12 @@ __device__ __forceinline__ size_t sxy_plane(int p, int q, int k, int K, int P) {
 }  // namespace
 
 // ---------------------------------------------------------------------------------------
-// Sufficient statistics. Thread (n, p): for lag p it accumulates, over t = P+1..T (1-based),
-// Syy[p][q] (q >= p) and Sxy[p][q][k] for all q, k. X is staged in shared memory (row-major
-// T x K); a register window holds y_t .. y_{t-P}.
+// Sufficient statistics, direct form (short series, T < 2P). Thread (n, p): for lag p it
+// accumulates, over t = P+1..T (1-based), Syy[p][q] (q >= p) and Sxy[p][q][k] for all q, k.
+// X is staged in shared memory (row-major T x K); a register window holds y_t .. y_{t-P}.
 // ---------------------------------------------------------------------------------------
 template <int K, typename TY>
-__global__ void __launch_bounds__(STATS_THREADS) k_stats(StatsArgs a) {
+__global__ void __launch_bounds__(STATS_THREADS) k_stats_direct(StatsArgs a) {
   extern __shared__ double shX[];
   const int T = a.T, P = a.P, N = a.N;
   for (int i = threadIdx.x; i < T * K; i += blockDim.x) {
@@ -454,16 +454,97 @@ __global__ void k_apply(ApplyArgs a) {
 // ---------------------------------------------------------------------------------------
 #define BFMRI_K_CASES(X) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12)
 
+// ---------------------------------------------------------------------------------------
+// Sufficient statistics, lag-difference form (T >= 2P). With s = t - p (0-based times),
+//   Sxy[p][q][k] = sum_{s = P-p}^{T-1-p} y_s x_{s+d,k},   d = p - q,
+//   Syy[p][q]    = sum_{s = P-q}^{T-1-q} y_s y_{s+e},     e = q - p >= 0,
+// so every pair with the same lag difference shares the sum over the common window
+// s = P .. T-1-P; each pair adds its own P boundary terms (s below P and above T-1-P).
+// Thread (n, d) handles the lag difference d = p - q in [-P, P]: K + 1 products per time
+// step instead of (P+1)(K+1), then the boundary terms of its pairs. X is staged in shared
+// memory (row-major T x K).
+// ---------------------------------------------------------------------------------------
+template <int K, typename TY>
+__global__ void __launch_bounds__(STATS_THREADS) k_stats(StatsArgs a) {
+  extern __shared__ double shX[];
+  const int T = a.T, P = a.P, N = a.N;
+  for (int i = threadIdx.x; i < T * K; i += blockDim.x) {
+    const int t = i / K, k = i - t * K;
+    shX[i] = a.X[t + (size_t)T * k];
+  }
+  __syncthreads();
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  const int d = (int)blockIdx.y - P;   // p - q
+  if (n >= N) return;
+  const TY* Y = static_cast<const TY*>(a.Y);
+  auto y = [&](int t) { return (double)Y[(size_t)t * N + n]; };
+  const int e = -d;                    // q - p, for the Syy pairs of this thread (e >= 0)
+  double c[K], cyy = 0.0;
+#pragma unroll
+  for (int k = 0; k < K; ++k) c[k] = 0.0;
+  for (int t = P; t <= T - 1 - P; ++t) {
+    const double ys = y(t);
+    const double* xr = shX + (size_t)(t + d) * K;
+#pragma unroll
+    for (int k = 0; k < K; ++k) c[k] += ys * xr[k];
+    if (e >= 0) cyy += ys * y(t + e);
+  }
+  const size_t ld = a.ld;
+  // Sxy pairs (p, q = p - d)
+  for (int p = d > 0 ? d : 0; p <= P && p - d <= P; ++p) {
+    const int q = p - d;
+    double v[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] = c[k];
+    for (int t = P - p; t <= P - 1; ++t) {
+      const double ys = y(t);
+      const double* xr = shX + (size_t)(t + d) * K;
+#pragma unroll
+      for (int k = 0; k < K; ++k) v[k] += ys * xr[k];
+    }
+    for (int t = T - P; t <= T - 1 - p; ++t) {
+      const double ys = y(t);
+      const double* xr = shX + (size_t)(t + d) * K;
+#pragma unroll
+      for (int k = 0; k < K; ++k) v[k] += ys * xr[k];
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) a.stats[sxy_plane(p, q, k, K, P) * ld + n] = v[k];
+  }
+  // Syy pairs (p, q = p + e), p <= q
+  if (e >= 0) {
+    for (int q = e; q <= P; ++q) {
+      const int p = q - e;
+      double v = cyy;
+      for (int t = P - q; t <= P - 1; ++t) v += y(t) * y(t + e);
+      for (int t = T - P; t <= T - 1 - q; ++t) v += y(t) * y(t + e);
+      a.stats[(size_t)syy_index(p, q, P) * ld + n] = v;
+    }
+  }
+}
+
 template <int K>
 static cudaError_t stats_k(const StatsArgs& a, cudaStream_t s) {
   const size_t shm = (size_t)a.T * K * sizeof(double);
-  dim3 grid((a.N + STATS_THREADS - 1) / STATS_THREADS, a.P + 1);
-  if (a.y_is_f64) {
-    cudaFuncSetAttribute(k_stats<K, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
-    k_stats<K, double><<<grid, STATS_THREADS, shm, s>>>(a);
+  const unsigned gx = (unsigned)((a.N + STATS_THREADS - 1) / STATS_THREADS);
+  if (a.T >= 2 * a.P) {
+    const dim3 grid(gx, 2 * a.P + 1);
+    if (a.y_is_f64) {
+      cudaFuncSetAttribute(k_stats<K, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+      k_stats<K, double><<<grid, STATS_THREADS, shm, s>>>(a);
+    } else {
+      cudaFuncSetAttribute(k_stats<K, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+      k_stats<K, float><<<grid, STATS_THREADS, shm, s>>>(a);
+    }
   } else {
-    cudaFuncSetAttribute(k_stats<K, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
-    k_stats<K, float><<<grid, STATS_THREADS, shm, s>>>(a);
+    const dim3 grid(gx, a.P + 1);
+    if (a.y_is_f64) {
+      cudaFuncSetAttribute(k_stats_direct<K, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+      k_stats_direct<K, double><<<grid, STATS_THREADS, shm, s>>>(a);
+    } else {
+      cudaFuncSetAttribute(k_stats_direct<K, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+      k_stats_direct<K, float><<<grid, STATS_THREADS, shm, s>>>(a);
+    }
   }
   return cudaGetLastError();
 }

@@ -231,6 +231,22 @@ def test_gibbs_sweep_single_step_parity(case):
     m.close()
 
 
+@pytest.mark.parametrize("T,K,P", [(7, 1, 4), (8, 2, 4), (9, 3, 3)])
+def test_stats_short_and_boundary_series(T, K, P):
+    """Series shorter than 2P take the direct summation; T = 2P and T = 2P + 1 have an empty
+    or one-step common window in the lag-difference form (all boundary terms)."""
+    w = synth.make_workload("short", (5, 4, 3), np.ones((3, 4, 5), np.uint8), T=T, K=K, P=P,
+                            neighbourhood=6, seed=17 + T, ar_uniform=(0.05, 0.2))
+    m = make(w)
+    got = m.get_stats()
+    st = model.sufficient_stats(w.Y, w.X, P)
+    iu = [(p, q) for p in range(P + 1) for q in range(p, P + 1)]
+    ref = np.concatenate([np.stack([st["Syy"][:, p, q] for p, q in iu], axis=1),
+                          st["Sxy"].reshape(w.N, -1)], axis=1)
+    assert np.max(np.abs(got - ref)) <= 1e-12 * np.abs(ref).max()
+    m.close()
+
+
 def test_stats_from_float32_series():
     """Single-precision Y (the serving input format): statistics equal the FP64 oracle's for
     the same rounded values."""
