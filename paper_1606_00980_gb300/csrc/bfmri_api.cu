@@ -476,7 +476,7 @@ bfmri_status ensure_mrhs(bfmri_handle* h, int D, int S, int hist_len) {
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   // rows of the partial buffer: one per (RHS, chunk) unit, never more than max(warps, S)
   const int units = std::max(std::max(nsm, 1) * 64, S);
-  const size_t out_len = std::max((size_t)h->ld, (size_t)((h->N + 127) / 128) * S * D);
+  const size_t out_len = std::max((size_t)h->ld, (size_t)((h->N + 127) / 128 + 1) * S * D);
   if (S <= h->mr_S && D <= h->mr_D && hist_len <= h->mr_hist_len && units <= h->mr_units &&
       out_len <= h->mr_out_len)
     return BFMRI_OK;
@@ -1202,12 +1202,12 @@ bfmri_status bfmri_logdet_probe(bfmri_handle* h, int which, int n_probes, int la
   // log det M
   double ldm = 0.0;
   if (pre) {
+    // per-voxel terms, summed on the device into h->d_hpart[0]
     e = launch_probe(D, pa, 1, h->mr_out, h->stream);
+    if (e == cudaSuccess) e = launch_sum_columns(h->mr_out, h->N, 1, h->d_hpart, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "logdet M");
-    std::vector<double> v(h->N);
-    CU(h, cudaMemcpyAsync(v.data(), h->mr_out, h->N * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CU(h, cudaMemcpyAsync(&ldm, h->d_hpart, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     CU(h, cudaStreamSynchronize(h->stream));
-    for (int n = 0; n < h->N; ++n) ldm += v[n];
   }
   // Lanczos quadrature per probe
   const double vnorm2 = (double)D * h->N;
@@ -1238,16 +1238,21 @@ bfmri_status bfmri_logdet_probe(bfmri_handle* h, int which, int n_probes, int la
   if (per_probe)
     for (int i = 0; i < n_probes; ++i) per_probe[i] = est[i];
   if (traces) {
+    // partials [gx][n_probes][D], summed over gx on the device (the column sums go to the
+    // part of mr_out after the partials), then over the probes on the host
     e = launch_probe(D, pa, 2, h->mr_out, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "traces");
     const int gx = (h->N + 127) / 128;
-    std::vector<double> part((size_t)gx * n_probes * D);
-    CU(h, cudaMemcpyAsync(part.data(), h->mr_out, part.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    const size_t C = (size_t)n_probes * D;
+    double* colsum = h->mr_out + (size_t)gx * C;
+    e = launch_sum_columns(h->mr_out, gx, (int)C, colsum, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "traces");
+    std::vector<double> part(C);
+    CU(h, cudaMemcpyAsync(part.data(), colsum, C * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     CU(h, cudaStreamSynchronize(h->stream));
     for (int k = 0; k < D; ++k) {
       double t = 0.0;
-      for (int i = 0; i < n_probes; ++i)
-        for (int g = 0; g < gx; ++g) t += part[((size_t)g * n_probes + i) * D + k];
+      for (int i = 0; i < n_probes; ++i) t += part[(size_t)i * D + k];
       traces[k] = t / n_probes;
     }
   }

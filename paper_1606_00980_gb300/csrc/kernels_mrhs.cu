@@ -747,6 +747,29 @@ static cudaError_t probe_launch_d(const ProbeArgs& a, int what, double* out, cud
   return cudaGetLastError();
 }
 
+// out[c] = sum over g of in[g * C + c], one CTA per column, each thread summing the rows
+// t, t + 256, ... in order and the CTA combining its threads in a fixed tree: deterministic.
+__global__ void __launch_bounds__(256) k_sum_columns(const double* __restrict__ in, int G, int C,
+                                                      double* __restrict__ out) {
+  __shared__ double sh[256];
+  const int c = blockIdx.x;
+  double acc = 0.0;
+  for (int g = threadIdx.x; g < G; g += 256) acc += in[(size_t)g * C + c];
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[c] = sh[0];
+}
+
+cudaError_t launch_sum_columns(const double* in, int G, int C, double* out, cudaStream_t s) {
+  if (C < 1) return cudaSuccess;
+  k_sum_columns<<<C, 256, 0, s>>>(in, G, C, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_probe(int D, const ProbeArgs& a, int what, double* out, cudaStream_t s) {
   switch (D) {
 #define CASE(d) case d: return probe_launch_d<d>(a, what, out, s);

@@ -99,6 +99,8 @@ struct ProbeArgs {
 // what: 0 = probe right-hand sides b_i = L v_i and x_i = 0; 1 = per-voxel log det of the
 // preconditioner into out[N]; 2 = trace partials into out[grid.x][S][D] (grid.x = ceil(N/128)).
 cudaError_t launch_probe(int D, const ProbeArgs& a, int what, double* out, cudaStream_t s);
+// out[c] = sum_g in[g * C + c] for c < C (fixed order per column).
+cudaError_t launch_sum_columns(const double* in, int G, int C, double* out, cudaStream_t s);
 
 // Launches the cooperative multi-RHS PCG for dimension D on `stream`.
 cudaError_t launch_mrhs(int D, const MrhsArgs& a, cudaStream_t stream, int* units_out);
