@@ -479,6 +479,48 @@ def mrhs_bytes_per_voxel_iter_rhs(D, S, w=4):
     return w * (13 * D) + w * 2 * (D * (D + 1) // 2) / S
 
 
+def run_batched_chains(w, n_chains=8, sweeps=3):
+    """8 independent FP64 chains of the 96x96x60 workload (seeds 5000 + c, delta 1e-8,
+    block-Jacobi) advanced by bfmri_gibbs_sweep_group after 2 warm-up sweeps: W-draws/s over
+    the chains, and the HBM view of the grouped W solve (one k_mrhs<8, double> launch per
+    sweep; per voxel, iteration and chain 13 K FP64 vector words plus the chain's own block
+    and factor, K(K+1)/2 words each)."""
+    import torch
+
+    from paper_1606_00980_gb300.bfmri import Model, gibbs_sweep_group
+    models = []
+    for c in range(n_chains):
+        m = Model.from_workload(w, delta=1e-8, seed=5000 + c, profile=1 if c == 0 else 0)
+        m.precompute_stats()
+        models.append(m)
+    gibbs_sweep_group(models, 2, 0)
+    torch.cuda.synchronize()
+    models[0].reset_timing()
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    infos = gibbs_sweep_group(models, sweeps, 2)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    dt = e0.elapsed_time(e1) / 1e3
+    tim = models[0].timing()
+    for m in models:
+        m.close()
+    it_w = sum(i.pcg_iterations_W for i in infos)
+    K = w.K
+    bytes_w = it_w * w.N * 8 * (13 * K + 2 * (K * (K + 1) // 2))
+    solve_s = tim["pcg_W"]["ms"] / 1e3
+    hbm_peak, hbm_src, _ = peaks()
+    return {"chains": n_chains, "W_draws_per_s": n_chains * sweeps / dt,
+            "ms_per_group_sweep": dt / sweeps * 1e3,
+            "pcg_iterations_W_per_chain_sweep": it_w / (n_chains * sweeps),
+            "W_solve_ms_per_group_sweep": solve_s / sweeps * 1e3,
+            "W_solve_hbm": {"achieved_gbs": bytes_w / solve_s / 1e9, "peak_gbs": hbm_peak,
+                            "frac": bytes_w / solve_s / 1e9 / hbm_peak},
+            "dtype": "f64", "delta": 1e-8}
+
+
 def run_batched(args):
     """Batched probes: the 96x96x60 lattice (ellipsoid, ~250k voxels, K = 8, AR(3), T = 300),
     64 Rademacher probes for log det B~ solved together by the FP32-storage multi-RHS PCG
@@ -532,6 +574,7 @@ def run_batched(args):
             "probe_iterations_mean": float(res["iterations"].mean()),
             "probe_iterations_max": int(res["iterations"].max()),
             "solve_ms": solve_s * 1e3, "call_ms": wall * 1e3, "svb_iteration": svb,
+            "chains": None if args.no_svb else run_batched_chains(w),
             "roofline": {"kernel": f"k_mrhs<{w.K}, float>", "bound": "hbm", "achieved": gbs,
                          "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
                          "traffic": None, "peak_source": f"{hbm_src} (MEASURED_PEAKS.json)",
