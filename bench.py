@@ -89,6 +89,35 @@ def precond_options(args):
     return {"precond": bfmri.PRECOND_BLOCK_JACOBI}
 
 
+def run_graph_compare(args, w, flush, stream, sweeps=20):
+    """The headline chain without per-launch timing, sweeps launched directly and replayed from
+    a captured CUDA graph (use_graph): ms per sweep each way, timed like the headline."""
+    import torch
+
+    from paper_1606_00980_gb300.bfmri import Model
+    out = {}
+    for name, g in (("direct", 0), ("captured", 1)):
+        m = Model.from_workload(w, delta=1e-8, seed=2024, use_graph=g, **precond_options(args))
+        m.precompute_stats()
+        m.gibbs_sweep(args.warmup, 0, info=False)
+        torch.cuda.synchronize()
+        times, captured = [], 0
+        for s in range(sweeps):
+            flush.random_(0, 255)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            inf = m.gibbs_sweep(1, args.warmup + s, info=True)
+            e1.record(stream)
+            times.append((e0, e1))
+            captured += inf.captured
+        torch.cuda.synchronize()
+        m.close()
+        ms = sum(a.elapsed_time(b) for a, b in times) / sweeps
+        out[name] = {"ms_per_sweep": ms, "W_draws_per_s": 1e3 / ms, "captured_sweeps": captured}
+    return out
+
+
 class ClockSampler:
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -240,7 +269,9 @@ def run_ours(args, world, rank, local):
 
     w = synth.wholebrain3d()
     K, P, N, T = w.K, w.P, w.N, w.T
-    m = Model.from_workload(w, delta=1e-8, seed=2024, stream_id=rank, profile=1,
+    # timed region: CUDA events around every sweep and around every PCG launch (profile 2:
+    # solver launches only, which keeps the event overhead out of the other kernels)
+    m = Model.from_workload(w, delta=1e-8, seed=2024, stream_id=rank, profile=2,
                             **precond_options(args))
     m.precompute_stats()
     stream = torch.cuda.current_stream()
@@ -288,10 +319,24 @@ def run_ours(args, world, rank, local):
     hbm_peak, hbm_src, _ = peaks()
     achieved_tf = flops / dur_s / 1e12
     achieved_gbs = bytes_ / dur_s / 1e9
-    total_ms = sum(v["ms"] for v in tim.values())
+    # per-kernel breakdown: the same chain (same seed and draw counters) run again with every
+    # launch timed (profile 1), over the same sweeps as the timed region
+    m.close()
+    mp = Model.from_workload(w, delta=1e-8, seed=2024, stream_id=rank, profile=1,
+                             **precond_options(args))
+    mp.precompute_stats()
+    mp.gibbs_sweep(args.warmup, 0, info=False)
+    torch.cuda.synchronize()
+    mp.reset_timing()
+    n_prof = args.steps
+    mp.gibbs_sweep(n_prof, args.warmup, info=False)
+    torch.cuda.synchronize()
+    tim_p = mp.timing()
+    mp.close()
+    total_ms = sum(v["ms"] for v in tim_p.values()) / n_prof * args.steps
     # kernels per timed launch group: edge terms + assembly (W, A), quadratic form + draw (hyper)
     per_group = {"assemble_W": 2, "assemble_A": 2, "hyper": 2}
-    n_launch = sum(v["launches"] * per_group.get(k, 1) for k, v in tim.items())
+    n_launch = sum(v["launches"] * per_group.get(k, 1) for k, v in tim_p.items()) / n_prof * args.steps
     roof = {"kernel": f"k_pcg_res<{K}> (W solve, {'SSOR' if ssor else 'block-Jacobi'})",
             "bound": "alu", "achieved": achieved_tf,
             "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved_tf / FP64_PEAK_TFLOPS,
@@ -301,7 +346,6 @@ def run_ours(args, world, rank, local):
                          "frac": achieved_gbs / hbm_peak, "peak_source": f"{hbm_src} (MEASURED_PEAKS.json)"},
             "iterations_per_launch": iters_per_launch, "avg_launch_ms": dur_s * 1e3,
             "share_of_step": pw["ms"] / total_ms if total_ms > 0 else None}
-    m.close()
 
     # the same chain with the mixed-precision solver (FP32 inner, FP64 refinement, same delta)
     mixed = run_mixed(args, w, flush, stream) if not args.no_mixed else None
@@ -309,6 +353,7 @@ def run_ours(args, world, rank, local):
     # independent chains of the same subject advanced together (one multi-RHS launch per solve)
     chains = run_chains(args, w, flush, stream, value) if not args.no_chains else None
     precs = run_precond_compare(args, w) if (rank == 0 and not args.no_precond) else None
+    graphs = run_graph_compare(args, w, flush, stream) if (rank == 0 and not args.no_graph) else None
     # end to end through the C ABI with host buffers
     del flush
     e2e = run_e2e(args, w) if rank == 0 else None
@@ -331,9 +376,12 @@ def run_ours(args, world, rank, local):
                            "pcg_iterations_W_per_sweep": it_w / args.steps,
                            "pcg_iterations_A_per_sweep": it_a / args.steps},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-                "mixed_precision": mixed, "grouped_chains": chains, "preconditioners": precs, "serving": serving, "batched_probes": batched,
+                "mixed_precision": mixed, "grouped_chains": chains, "preconditioners": precs,
+                "captured_sweeps": graphs, "serving": serving, "batched_probes": batched,
                 "gpu_launches": int(n_launch),
-                "kernel_ms_per_step": {k: v["ms"] / args.steps for k, v in tim.items() if v["launches"]}}
+                "kernel_ms_per_step": {k: v["ms"] / n_prof for k, v in tim_p.items() if v["launches"]},
+                "kernel_ms_per_step_note": "the same chain and sweeps rerun with every launch "
+                                           "timed; the timed region times only the solver launches"}
         print(json.dumps(line), flush=True)
 
 
@@ -345,7 +393,7 @@ def run_mixed(args, w, flush, stream):
     from paper_1606_00980_gb300 import bfmri
     from paper_1606_00980_gb300.bfmri import Model
     m = Model.from_workload(w, delta=1e-8, seed=2024, precision=bfmri.PREC_MIXED, inner_tol=1e-6,
-                            profile=1, **precond_options(args))
+                            profile=2, **precond_options(args))
     m.precompute_stats()
     counter = 0
     for _ in range(args.warmup):
@@ -687,6 +735,7 @@ def main():
     ap.add_argument("--no-svb", action="store_true")
     ap.add_argument("--no-chains", action="store_true")
     ap.add_argument("--no-precond", action="store_true")
+    ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--precond", choices=["ssor", "bj"], default="ssor",
                     help="preconditioner of the headline chain and of its mixed-precision twin "
                          "(the multi-RHS solves use block-Jacobi)")

@@ -98,8 +98,9 @@ typedef struct {
   double barrier_timeout_s;  /* limit of each device-side grid-barrier wait (default 2 s) */
   int debug_skip_block;      /* test hook: this CTA never arrives at the first barrier of the
                                 next solve (forces BFMRI_ERR_TIMEOUT); -1 = off (default) */
-  int profile;               /* nonzero: time every kernel launch with CUDA events on the
-                                handle's stream (read with bfmri_get_timing) */
+  int profile;               /* 1: time every kernel launch with CUDA events on the handle's
+                                stream; 2: time only the single-solve PCG launches (less
+                                overhead); read with bfmri_get_timing. 0 (default): off */
   int pcg_variant;           /* BFMRI_PCG_AUTO (default): the register-resident solver when the
                                 voxels fit one CTA per SM, else the streaming one;
                                 BFMRI_PCG_STREAMING: always the streaming solver */
@@ -108,6 +109,12 @@ typedef struct {
                                 their cooperative solves side by side. */
   double ssor_omega;         /* relaxation of BFMRI_PRECOND_SSOR, in (0, 2) (default 1:
                                 symmetric Gauss-Seidel) */
+  int use_graph;             /* nonzero: bfmri_gibbs_sweep replays one captured CUDA graph
+                                per sweep (captured at the first call; the draw counter lives
+                                in device memory and the graph advances it), with the same
+                                results as direct launches. Ignored while profile or
+                                debug_skip_block is set; if capture is unavailable the handle
+                                falls back to direct launches. Default 0. */
 } bfmri_options;
 
 #define BFMRI_PCG_AUTO      0
@@ -131,6 +138,7 @@ typedef struct {
   long long pcg_iterations_A;
   double last_rel_residual_W;
   long long gamma_exhausted;   /* Marsaglia-Tsang draws that used all attempts */
+  int captured;                /* 1 when the sweeps ran as replays of a captured CUDA graph */
 } bfmri_sweep_info;
 
 /* Creates a handle for one subject (paper Section 2, Eq. Pennymodel; Appendix A).

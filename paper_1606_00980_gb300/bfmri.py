@@ -45,7 +45,8 @@ class bfmri_options(C.Structure):
                 ("cuda_stream", C.c_void_p), ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN),
                 ("alloc_ctx", C.c_void_p), ("barrier_timeout_s", C.c_double),
                 ("debug_skip_block", C.c_int), ("profile", C.c_int), ("pcg_variant", C.c_int),
-                ("sm_budget", C.c_int), ("ssor_omega", C.c_double)]
+                ("sm_budget", C.c_int), ("ssor_omega", C.c_double),
+                ("use_graph", C.c_int)]
 
 
 class bfmri_solve_info(C.Structure):
@@ -62,7 +63,7 @@ class bfmri_svb_info(C.Structure):
 class bfmri_sweep_info(C.Structure):
     _fields_ = [("sweeps", C.c_int), ("pcg_iterations_W", C.c_longlong),
                 ("pcg_iterations_A", C.c_longlong), ("last_rel_residual_W", C.c_double),
-                ("gamma_exhausted", C.c_longlong)]
+                ("gamma_exhausted", C.c_longlong), ("captured", C.c_int)]
 
 
 T_CLASSES = ["stats", "assemble_W", "pcg_W", "assemble_A", "pcg_A", "lambda", "hyper", "other"]

@@ -66,7 +66,14 @@ struct bfmri_handle {
   int* d_black = nullptr;   // and of the others (red-black SSOR phases)
   int n_red = 0, n_black = 0;
   unsigned char* d_colour = nullptr;   // [ld] 0 red, 1 black
-  uint64_t mask_hash = 0;   // identity of the mask (FNV-1a of the in-mask lattice indices)
+  uint64_t mask_hash = 0;
+  // captured Gibbs sweep (options.use_graph): one sweep whose draws read the device counter
+  uint32_t* d_sweep_ctr = nullptr;
+  cudaGraph_t sweep_graph = nullptr;
+  cudaGraphExec_t sweep_exec = nullptr;
+  cudaStream_t capture_stream = nullptr;   // capture cannot run on the legacy default stream
+  bool capturing = false;
+  bool graph_failed = false;   // identity of the mask (FNV-1a of the in-mask lattice indices)
   // grouped chains: per-chain operator tables [2][cap] and tallies [2][cap]
   MrhsRhsPtrs* d_gtab = nullptr;
   MrhsTally* d_gtally = nullptr;
@@ -168,7 +175,8 @@ struct Timed {
   bool pcg;
   int which;
   Timed(bfmri_handle* h_, int cls_, bool pcg_ = false, int which_ = 0) : h(h_), cls(cls_), pcg(pcg_), which(which_) {
-    if (h->opt.profile) {
+    // profile 1: every launch; profile 2: the single-solve PCG launches only
+    if (h->opt.profile == 1 || (h->opt.profile == 2 && pcg)) {
       if (h->pending.size() > 2048) resolve_timing(h);
       e0 = take_event(h);
       cudaEventRecord(e0, h->stream);
@@ -202,6 +210,11 @@ Rng rng_of(const bfmri_handle* h, uint64_t counter, uint32_t tag) {
   r.k1 = (uint32_t)(h->opt.seed >> 32);
   r.counter = (uint32_t)counter;
   r.c3 = (tag << 24) | (h->opt.stream_id & 0xFFFFFFu);
+  r.dctr = nullptr;
+  if (h->capturing) {   // the captured sweep reads its draw counter from the device word
+    r.counter = 0u;
+    r.dctr = h->d_sweep_ctr;
+  }
   return r;
 }
 
@@ -579,6 +592,7 @@ void bfmri_default_options(bfmri_options* o) {
   o->max_iter = 2000;
   o->precond = BFMRI_PRECOND_BLOCK_JACOBI;
   o->ssor_omega = 1.0;
+  o->use_graph = 0;
   o->precision = BFMRI_PREC_FP64;
   o->ar_prior = BFMRI_AR_SPATIAL;
   o->y_layout = BFMRI_Y_MASKED;
@@ -740,6 +754,7 @@ bfmri_status bfmri_create(const bfmri_lattice* lat, const uint8_t* mask, const d
   h->d_red = (int*)A(ld * sizeof(int));
   h->d_black = (int*)A(ld * sizeof(int));
   h->d_colour = (unsigned char*)A(ld);
+  h->d_sweep_ctr = (uint32_t*)A(sizeof(uint32_t));
   h->d_Y = A((size_t)T * N * esz);
   h->y_f64 = y_dtype == BFMRI_F64;
   h->d_X = (double*)A((size_t)T * K * sizeof(double));
@@ -782,7 +797,7 @@ bfmri_status bfmri_create(const bfmri_lattice* lat, const uint8_t* mask, const d
       return fail(nullptr, BFMRI_ERR_OOM, "device allocation failed");
     }
   }
-  void* must[] = {h->d_nbr, h->d_lin, h->d_red, h->d_black, h->d_colour, h->d_Y, h->d_X, h->d_stats, h->d_Sxx, h->d_W, h->d_A,
+  void* must[] = {h->d_nbr, h->d_lin, h->d_red, h->d_black, h->d_colour, h->d_sweep_ctr, h->d_Y, h->d_X, h->d_stats, h->d_Sxx, h->d_W, h->d_A,
                   h->d_lam, h->d_alpha, h->d_beta, h->d_G, h->d_blocks, h->d_mfac, h->d_rhs,
                   h->d_bmean, h->d_r, h->d_z, h->d_q, h->d_p0, h->d_p1, h->d_part, h->d_hpart,
                   h->d_bar, h->d_err, h->d_ctrl, h->d_flags};
@@ -840,6 +855,9 @@ bfmri_status bfmri_destroy(bfmri_handle* h) {
     cudaEventDestroy(p.e1);
   }
   for (cudaEvent_t e : h->event_pool) cudaEventDestroy(e);
+  if (h->sweep_exec) cudaGraphExecDestroy(h->sweep_exec);
+  if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
+  if (h->sweep_graph) cudaGraphDestroy(h->sweep_graph);
   std::vector<void*> all = h->allocs;
   for (void* p : all) dfree(h, p);
   delete h;
@@ -979,13 +997,58 @@ bfmri_status bfmri_gibbs_sweep(bfmri_handle* h, int n_sweeps, uint64_t first_cou
   if (n_sweeps < 0) return fail(h, BFMRI_ERR_INVALID_ARG, "n_sweeps < 0");
   RET(begin_call(h));
   const bool spatial = h->opt.ar_prior == BFMRI_AR_SPATIAL;
-  for (int s = 0; s < n_sweeps; ++s) {
-    const uint64_t c = first_counter + (uint64_t)s;
+  auto one_sweep = [&](uint64_t c) -> bfmri_status {
     RET(enqueue_W(h, c));
     RET(enqueue_A(h, c));
     RET(enqueue_lambda(h, c));
     RET(enqueue_hyper(h, c, false));
     if (h->P > 0 && spatial) RET(enqueue_hyper(h, c, true));
+    return BFMRI_OK;
+  };
+  const bool graph = h->opt.use_graph && !h->opt.profile && h->opt.debug_skip_block < 0 &&
+                     !h->graph_failed && n_sweeps > 0;
+  if (graph && !h->sweep_exec) {
+    // capture one sweep (its draws read the device counter) and one counter advance
+    // captured on a private stream; the instantiated graph is launched on the handle's stream
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaSuccess;
+    if (!h->capture_stream) e = cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);   // begin_call's resets are done
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeRelaxed);
+    bfmri_status cs = BFMRI_OK;
+    if (e == cudaSuccess) {
+      cudaStream_t user = h->stream;
+      h->stream = h->capture_stream;
+      h->capturing = true;
+      cs = one_sweep(0);
+      if (cs == BFMRI_OK) e = launch_advance_counter(h->d_sweep_ctr, h->stream);
+      h->capturing = false;
+      h->stream = user;
+      const cudaError_t ee = cudaStreamEndCapture(h->capture_stream, &g);
+      if (e == cudaSuccess) e = ee;
+    }
+    if (e == cudaSuccess && cs == BFMRI_OK && g) e = cudaGraphInstantiate(&h->sweep_exec, g, 0);
+    if (e != cudaSuccess || cs != BFMRI_OK || !h->sweep_exec) {
+      // capture is not available here: sweep with direct launches from now on (the reason is
+      // kept as the handle's last message)
+      h->err = std::string("CUDA graph capture unavailable, sweeps use direct launches: ") +
+               (cs != BFMRI_OK ? h->err : std::string(cudaGetErrorString(e)));
+      cudaGetLastError();
+      if (g) cudaGraphDestroy(g);
+      h->sweep_exec = nullptr;
+      h->graph_failed = true;
+      RET(begin_call(h));
+    } else {
+      h->sweep_graph = g;
+    }
+  }
+  const bool captured = graph && h->sweep_exec;
+  if (captured) {
+    cudaError_t e = launch_set_counter(h->d_sweep_ctr, (uint32_t)first_counter, h->stream);
+    for (int s = 0; s < n_sweeps && e == cudaSuccess; ++s) e = cudaGraphLaunch(h->sweep_exec, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "captured sweep");
+  } else {
+    for (int s = 0; s < n_sweeps; ++s) RET(one_sweep(first_counter + (uint64_t)s));
   }
   PcgCtrl c[2];
   int exhausted = 0;
@@ -996,6 +1059,7 @@ bfmri_status bfmri_gibbs_sweep(bfmri_handle* h, int n_sweeps, uint64_t first_cou
     info->pcg_iterations_A = c[1].iter_total;
     info->last_rel_residual_W = c[0].rel_res;
     info->gamma_exhausted = exhausted;
+    info->captured = captured ? 1 : 0;
   }
   return st;
 }

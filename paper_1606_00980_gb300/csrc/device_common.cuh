@@ -25,10 +25,15 @@ __device__ __forceinline__ uint4 philox(uint4 c, uint32_t k0, uint32_t k1) {
   return c;
 }
 
+// Philox key (k0, k1) and the counter words: (site, sub, draw counter, c3). The draw counter
+// is `counter`, plus the device word *dctr when dctr is set (a captured CUDA graph replays one
+// sweep for every draw counter: the graph advances the device word, not a kernel argument).
 struct Rng {
   uint32_t k0, k1, counter, c3;
+  const uint32_t* dctr;
   __device__ __forceinline__ uint4 call(uint32_t site, uint32_t sub) const {
-    return philox(make_uint4(site, sub, counter, c3), k0, k1);
+    const uint32_t c = dctr ? counter + __ldg(dctr) : counter;
+    return philox(make_uint4(site, sub, c, c3), k0, k1);
   }
 };
 

@@ -575,6 +575,19 @@ static cudaError_t assemble_a_k(const AssembleArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+__global__ void k_set_counter(uint32_t* p, uint32_t v) { *p = v; }
+__global__ void k_advance_counter(uint32_t* p) { *p += 1u; }
+
+cudaError_t launch_set_counter(uint32_t* p, uint32_t v, cudaStream_t s) {
+  k_set_counter<<<1, 1, 0, s>>>(p, v);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_advance_counter(uint32_t* p, cudaStream_t s) {
+  k_advance_counter<<<1, 1, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_assemble_w(const AssembleArgs& a, cudaStream_t s) {
   if (a.g.N <= 0) return cudaSuccess;
   switch (a.K) {

@@ -211,6 +211,9 @@ struct AssembleArgs {
 
 // E[d][k][n] = sqrt(scale_k) z1_k for the edge from voxel n in direction +d (zero when absent):
 // each edge's normals are generated once instead of by both of its endpoints.
+// Device draw counter of captured sweeps: set it, or advance it by one (one-thread kernels).
+cudaError_t launch_set_counter(uint32_t* p, uint32_t v, cudaStream_t s);
+cudaError_t launch_advance_counter(uint32_t* p, cudaStream_t s);
 cudaError_t launch_edge_noise(const Geometry& g, int D, const double* scale, Rng rng, double* E,
                               cudaStream_t s);
 cudaError_t launch_assemble_w(const AssembleArgs& a, cudaStream_t s);
