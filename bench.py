@@ -376,6 +376,7 @@ def run_ours(args, world, rank, local):
                            "pcg_iterations_W_per_sweep": it_w / args.steps,
                            "pcg_iterations_A_per_sweep": it_a / args.steps},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+                "voxel_draws_per_s": value * N,
                 "mixed_precision": mixed, "grouped_chains": chains, "preconditioners": precs,
                 "captured_sweeps": graphs, "serving": serving, "batched_probes": batched,
                 "gpu_launches": int(n_launch),
@@ -687,6 +688,11 @@ def run_serving(args):
     return {"requests": n_req, "p50_ms": float(np.percentile(lat, 50)),
             "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
             "draws_per_s": 8 * n_req / makespan, "unit": UNIT, "makespan_s": makespan,
+            "voxel_draws_per_s": 8 * float(sum(pool[j].N for j in picks)) / makespan,
+            "capacity_draws_per_s": 8 * capacity,
+            "capacity_voxel_draws_per_s": 8 * capacity * float(np.mean([w.N for w in pool])),
+            "note": "draws/s follow the offered load (0.8 of capacity); the requests average "
+                    "more voxels than the headline workload, so voxel-draws/s compare them",
             "offered_rate_per_s": rate, "capacity_per_s": capacity,
             "mean_service_ms_alone": mean_service * 1e3,
             "slots": slots, "sm_budget_per_slot": sm_budget, "budget_bytes": budget,
