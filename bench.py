@@ -287,18 +287,20 @@ def run_ours(args, world, rank, local):
     barrier(world)
     torch.cuda.synchronize()
     times = []
-    it_w = it_a = 0
+    # sweeps are enqueued without a host wait (their errors and PCG counts are read once,
+    # after the loop), so host-side jitter between launches does not idle the GPU inside
+    # the timed events
     for s in range(args.steps):
         flush.random_(0, 255)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        inf = m.gibbs_sweep(1, counter, info=True)
+        m.gibbs_sweep(1, counter, info=False)
         e1.record(stream)
         counter += 1
         times.append((e0, e1))
-        it_w += inf.pcg_iterations_W
-        it_a += inf.pcg_iterations_A
+    span = m.synchronize()
+    it_w, it_a = span.pcg_iterations_W, span.pcg_iterations_A
     torch.cuda.synchronize()
     barrier(world)
     clk = clocks.stop()
@@ -447,7 +449,7 @@ def run_chains(args, w, flush, stream, single_value, n_chains=8):
     from paper_1606_00980_gb300.bfmri import Model, gibbs_sweep_group
     models = []
     for c in range(n_chains):
-        m = Model.from_workload(w, delta=1e-8, seed=3000 + c)
+        m = Model.from_workload(w, delta=1e-8, seed=3000 + c, **precond_options(args))
         m.precompute_stats()
         models.append(m)
     counter = 0
@@ -478,7 +480,7 @@ def run_chains(args, w, flush, stream, single_value, n_chains=8):
             "pcg_iterations_W_per_chain_sweep": it_w / (n_chains * args.steps),
             "pcg_iterations_A_per_chain_sweep": it_a / (n_chains * args.steps),
             "vs_single_chain": value / single_value if single_value else None,
-            "delta": 1e-8, "dtype": "f64"}
+            "precond": args.precond, "delta": 1e-8, "dtype": "f64"}
 
 
 def run_precond_compare(args, w, n_draws=10):
@@ -528,18 +530,20 @@ def mrhs_bytes_per_voxel_iter_rhs(D, S, w=4):
     return w * (13 * D) + w * 2 * (D * (D + 1) // 2) / S
 
 
-def run_batched_chains(w, n_chains=8, sweeps=3):
-    """8 independent FP64 chains of the 96x96x60 workload (seeds 5000 + c, delta 1e-8,
-    block-Jacobi) advanced by bfmri_gibbs_sweep_group after 2 warm-up sweeps: W-draws/s over
-    the chains, and the HBM view of the grouped W solve (one k_mrhs<8, double> launch per
-    sweep; per voxel, iteration and chain 13 K FP64 vector words plus the chain's own block
-    and factor, K(K+1)/2 words each)."""
+def run_batched_chains(args, w, n_chains=8, sweeps=3):
+    """8 independent FP64 chains of the 96x96x60 workload (seeds 5000 + c, delta 1e-8, the
+    --precond preconditioner) advanced by bfmri_gibbs_sweep_group after 2 warm-up sweeps:
+    W-draws/s over the chains, and the HBM view of the grouped W solve (one k_mrhs<8, double>
+    launch per sweep; per voxel, iteration and chain 13 K FP64 vector words plus the chain's
+    own block and factor, K(K+1)/2 words each; SSOR adds its two colour phases, 4 K words
+    and one more factor read)."""
     import torch
 
     from paper_1606_00980_gb300.bfmri import Model, gibbs_sweep_group
     models = []
     for c in range(n_chains):
-        m = Model.from_workload(w, delta=1e-8, seed=5000 + c, profile=1 if c == 0 else 0)
+        m = Model.from_workload(w, delta=1e-8, seed=5000 + c, profile=1 if c == 0 else 0,
+                                **precond_options(args))
         m.precompute_stats()
         models.append(m)
     gibbs_sweep_group(models, 2, 0)
@@ -558,7 +562,9 @@ def run_batched_chains(w, n_chains=8, sweeps=3):
         m.close()
     it_w = sum(i.pcg_iterations_W for i in infos)
     K = w.K
-    bytes_w = it_w * w.N * 8 * (13 * K + 2 * (K * (K + 1) // 2))
+    F = K * (K + 1) // 2
+    ssor = args.precond == "ssor"
+    bytes_w = it_w * w.N * 8 * (13 * K + 2 * F + ((4 * K + F) if ssor else 0))
     solve_s = tim["pcg_W"]["ms"] / 1e3
     hbm_peak, hbm_src, _ = peaks()
     return {"chains": n_chains, "W_draws_per_s": n_chains * sweeps / dt,
@@ -567,7 +573,7 @@ def run_batched_chains(w, n_chains=8, sweeps=3):
             "W_solve_ms_per_group_sweep": solve_s / sweeps * 1e3,
             "W_solve_hbm": {"achieved_gbs": bytes_w / solve_s / 1e9, "peak_gbs": hbm_peak,
                             "frac": bytes_w / solve_s / 1e9 / hbm_peak},
-            "dtype": "f64", "delta": 1e-8}
+            "precond": args.precond, "dtype": "f64", "delta": 1e-8}
 
 
 def run_batched(args):
@@ -597,8 +603,9 @@ def run_batched(args):
     svb = None
     if not args.no_svb:
         # one spatial-VB iteration (N_s = 100 samples of W and A, FP64 multi-RHS solves with the
-        # fixed random numbers of Section 3.3), after a first iteration that creates the samples
-        ms = Model.from_workload(w, delta=1e-8, seed=4243, profile=1)
+        # fixed random numbers of Section 3.3, the --precond preconditioner), after a first
+        # iteration that creates the samples
+        ms = Model.from_workload(w, delta=1e-8, seed=4243, profile=1, **precond_options(args))
         ms.precompute_stats()
         ms.gibbs_sweep(3, 0)
         ms.spvb_step(100, 7)
@@ -610,7 +617,7 @@ def run_batched(args):
         dt = time.perf_counter() - t1
         tsv = ms.timing()
         ms.close()
-        svb = {"samples": 100, "iteration_ms": dt * 1e3,
+        svb = {"samples": 100, "precond": args.precond, "iteration_ms": dt * 1e3,
                "pcg_iterations_W_total": int(info.pcg_iterations_W),
                "pcg_iterations_A_total": int(info.pcg_iterations_A),
                "W_solve_ms": tsv["pcg_W"]["ms"], "A_solve_ms": tsv["pcg_A"]["ms"],
@@ -623,7 +630,7 @@ def run_batched(args):
             "probe_iterations_mean": float(res["iterations"].mean()),
             "probe_iterations_max": int(res["iterations"].max()),
             "solve_ms": solve_s * 1e3, "call_ms": wall * 1e3, "svb_iteration": svb,
-            "chains": None if args.no_svb else run_batched_chains(w),
+            "chains": None if args.no_svb else run_batched_chains(args, w),
             "roofline": {"kernel": f"k_mrhs<{w.K}, float>", "bound": "hbm", "achieved": gbs,
                          "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
                          "traffic": None, "peak_source": f"{hbm_src} (MEASURED_PEAKS.json)",

@@ -61,8 +61,9 @@ typedef struct {
 #define BFMRI_PRECOND_SSOR         2  /* red-black symmetric SOR over those voxel blocks:
                                          M = (Dg + w L) Dg^-1 (Dg + w U) / (w (2 - w)), w =
                                          ssor_omega, red = voxels with x + y + z even. Single
-                                         solves, FP64 and mixed (FP32 inner iterations); the
-                                         multi-RHS solves use the block-Jacobi blocks */
+                                         solves (FP64, and the FP32 inner iterations of mixed),
+                                         SVB samples and grouped chains; the log-det / trace
+                                         probes always use block-Jacobi */
 
 #define BFMRI_PREC_FP64  0  /* FP64 PCG */
 #define BFMRI_PREC_MIXED 1  /* FP32 inner PCG inside an FP64 iterative-refinement loop */
@@ -211,9 +212,20 @@ bfmri_status bfmri_sample_alpha(bfmri_handle* h, uint64_t counter, double* alpha
 bfmri_status bfmri_sample_beta(bfmri_handle* h, uint64_t counter, double* beta_out);
 
 /* n_sweeps Gibbs sweeps (Section 3.2) W -> A -> lambda -> alpha -> beta; sweep s uses draw
- * counter first_counter + s. No host synchronisation inside; info (may be NULL) waits. */
+ * counter first_counter + s.
+ * info != NULL: the call waits for the sweeps and reports their errors and counts.
+ * info == NULL: the call only enqueues the sweeps on the handle's stream and returns
+ * BFMRI_OK (argument and launch errors are still returned at once). The device-side error
+ * words and PCG counters then accumulate over such calls until a synchronising call reads
+ * them: the next bfmri_gibbs_sweep with info, any other compute call, or bfmri_synchronize;
+ * that call reports the first error of the whole span and its counts cover the whole span. */
 bfmri_status bfmri_gibbs_sweep(bfmri_handle* h, int n_sweeps, uint64_t first_counter,
                                bfmri_sweep_info* info);
+
+/* Waits for the handle's enqueued work and reports the errors of the calls since the last
+ * synchronising call (see bfmri_gibbs_sweep). info (may be NULL) receives the PCG counts of
+ * that span (sweeps = 0). Errors: as bfmri_gibbs_sweep, CUDA. */
+bfmri_status bfmri_synchronize(bfmri_handle* h, bfmri_sweep_info* info);
 
 /* n independent chains advanced together, each by n_sweeps Gibbs sweeps of Section 3.2
  * (the chains are the handles hs[0..n-1], each with its own state and seed, so their draws
@@ -224,7 +236,8 @@ bfmri_status bfmri_gibbs_sweep(bfmri_handle* h, int n_sweeps, uint64_t first_cou
  * (relative residual <= delta, confirmed by the true residual) as bfmri_gibbs_sweep on
  * hs[c]; they agree with it to the solver tolerance, not bitwise.
  * Requirements: 1 <= n <= 64; all handles on one lattice and mask, with equal K, P, AR
- * prior, delta and max_iter, FP64 precision, statistics precomputed, on the current device.
+ * prior, delta, max_iter and preconditioner (and ssor_omega under SSOR), FP64 precision,
+ * statistics precomputed, on the current device.
  * All work runs on hs[0]'s stream; the call returns when it has finished.
  * info: [n] per-chain results (may be NULL). hs and info are host arrays the caller owns.
  * Errors: INVALID_ARG (mismatched or bad handles), STATE, NOT_SPD, NOT_CONVERGED, TIMEOUT,

@@ -113,6 +113,7 @@ SIGNATURES = [
     ("bfmri_sample_beta", C.c_int, [_h, C.c_uint64, _dp]),
     ("bfmri_gibbs_sweep", C.c_int, [_h, C.c_int, C.c_uint64, _P(bfmri_sweep_info)]),
     ("bfmri_gibbs_sweep_group", C.c_int, [_P(_h), C.c_int, C.c_int, C.c_uint64, _P(bfmri_sweep_info)]),
+    ("bfmri_synchronize", C.c_int, [_h, _P(bfmri_sweep_info)]),
     ("bfmri_logdet_probe", C.c_int, [_h, C.c_int, C.c_int, C.c_int, C.c_uint64, _dp, _dp, _dp, _dp,
                                      _P(C.c_int)]),
     ("bfmri_lanczos_log_quadrature", C.c_int, [C.c_int, _dp, _dp, _dp]),
@@ -439,9 +440,18 @@ class Model:
         return b[:self.P]
 
     def gibbs_sweep(self, n_sweeps, first_counter=0, info=True):
+        """info=False only enqueues the sweeps (no host wait); their errors and PCG counts are
+        read by the next synchronising call, e.g. synchronize()."""
         inf = bfmri_sweep_info()
         self._c(self.lib.bfmri_gibbs_sweep(self.handle, n_sweeps, first_counter,
                                            C.byref(inf) if info else None))
+        return inf
+
+    def synchronize(self):
+        """Waits for the enqueued work; raises the first error of the asynchronous sweeps
+        since the last synchronising call and returns their PCG counts."""
+        inf = bfmri_sweep_info()
+        self._c(self.lib.bfmri_synchronize(self.handle, C.byref(inf)))
         return inf
 
     def logdet_probe(self, which, n_probes, lanczos_steps, counter, traces=True):

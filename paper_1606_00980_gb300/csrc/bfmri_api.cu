@@ -66,14 +66,17 @@ struct bfmri_handle {
   int* d_black = nullptr;   // and of the others (red-black SSOR phases)
   int n_red = 0, n_black = 0;
   unsigned char* d_colour = nullptr;   // [ld] 0 red, 1 black
-  uint64_t mask_hash = 0;
+  uint64_t mask_hash = 0;     // identity of the mask (FNV-1a of the in-mask lattice indices)
   // captured Gibbs sweep (options.use_graph): one sweep whose draws read the device counter
   uint32_t* d_sweep_ctr = nullptr;
   cudaGraph_t sweep_graph = nullptr;
   cudaGraphExec_t sweep_exec = nullptr;
   cudaStream_t capture_stream = nullptr;   // capture cannot run on the legacy default stream
   bool capturing = false;
-  bool graph_failed = false;   // identity of the mask (FNV-1a of the in-mask lattice indices)
+  bool graph_failed = false;
+  // asynchronous sweeps (bfmri_gibbs_sweep without info) left their error words and PCG
+  // counters unread: they accumulate until the next synchronising call
+  bool deferred = false;
   // grouped chains: per-chain operator tables [2][cap] and tallies [2][cap]
   MrhsRhsPtrs* d_gtab = nullptr;
   MrhsTally* d_gtally = nullptr;
@@ -246,8 +249,10 @@ bool all_positive(const double* v, size_t n) {
   return true;
 }
 
-// Clears the sticky device error words before a group of launches.
+// Clears the sticky device error words before a group of launches (kept, and added to,
+// while the errors of asynchronous sweeps are unread).
 bfmri_status begin_call(bfmri_handle* h) {
+  if (h->deferred) return BFMRI_OK;
   CU(h, cudaMemsetAsync(h->d_bar, 0, 2 * sizeof(unsigned int), h->stream));
   CU(h, cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream));
   CU(h, cudaMemsetAsync(h->d_ctrl, 0, 2 * sizeof(PcgCtrl), h->stream));
@@ -258,6 +263,7 @@ bfmri_status begin_call(bfmri_handle* h) {
 
 // Reads the device error words after synchronising; maps them to a status.
 bfmri_status end_call(bfmri_handle* h, PcgCtrl* ctrl_out /* [2] or null */, int* exhausted) {
+  h->deferred = false;
   CU(h, cudaStreamSynchronize(h->stream));
   PcgCtrl ctrl[2];
   int flags[4], err = 0;
@@ -558,6 +564,17 @@ MrhsArgs mrhs_args(bfmri_handle* h, int D, int S, const double* scale, int max_i
   m.max_restarts = 4;
   m.sm_cap = h->opt.sm_budget;
   return m;
+}
+
+// Red-black SSOR for the plain multi-RHS solves (SVB samples, grouped chains) when the handle
+// asks for it; the probe solves keep block-Jacobi.
+void mrhs_ssor(const bfmri_handle* h, MrhsArgs& m) {
+  m.ssor = h->opt.precond == BFMRI_PRECOND_SSOR;
+  m.omega = h->opt.ssor_omega;
+  m.red = h->d_red;
+  m.n_red = h->n_red;
+  m.black = h->d_black;
+  m.n_black = h->n_black;
 }
 
 bfmri_status require_stats(bfmri_handle* h) {
@@ -1050,16 +1067,42 @@ bfmri_status bfmri_gibbs_sweep(bfmri_handle* h, int n_sweeps, uint64_t first_cou
   } else {
     for (int s = 0; s < n_sweeps; ++s) RET(one_sweep(first_counter + (uint64_t)s));
   }
+  if (!info) {
+    h->deferred = true;        // errors and counts are read by the next synchronising call
+    return BFMRI_OK;
+  }
   PcgCtrl c[2];
   int exhausted = 0;
   bfmri_status st = end_call(h, c, &exhausted);
-  if (info) {
+  {
     info->sweeps = n_sweeps;
     info->pcg_iterations_W = c[0].iter_total;
     info->pcg_iterations_A = c[1].iter_total;
     info->last_rel_residual_W = c[0].rel_res;
     info->gamma_exhausted = exhausted;
     info->captured = captured ? 1 : 0;
+  }
+  return st;
+}
+
+bfmri_status bfmri_synchronize(bfmri_handle* h, bfmri_sweep_info* info) {
+  if (!h) return BFMRI_ERR_INVALID_ARG;
+  PcgCtrl c[2];
+  int exhausted = 0;
+  const bool was_deferred = h->deferred;
+  if (!was_deferred) {
+    // nothing unread: wait for the stream; the counters are those of no work
+    CU(h, cudaStreamSynchronize(h->stream));
+    if (info) memset(info, 0, sizeof(*info));
+    return BFMRI_OK;
+  }
+  const bfmri_status st = end_call(h, c, &exhausted);
+  if (info) {
+    memset(info, 0, sizeof(*info));
+    info->pcg_iterations_W = c[0].iter_total;
+    info->pcg_iterations_A = c[1].iter_total;
+    info->last_rel_residual_W = c[0].rel_res;
+    info->gamma_exhausted = exhausted;
   }
   return st;
 }
@@ -1087,7 +1130,8 @@ bfmri_status bfmri_gibbs_sweep_group(bfmri_handle* const* hs, int n, int n_sweep
       return fail(h0, BFMRI_ERR_INVALID_ARG, "grouped chains must share one lattice and mask");
     if (h->K != h0->K || h->P != h0->P || h->opt.ar_prior != h0->opt.ar_prior ||
         h->opt.delta != h0->opt.delta || h->opt.max_iter != h0->opt.max_iter ||
-        h->opt.precond != h0->opt.precond)
+        h->opt.precond != h0->opt.precond ||
+        (h0->opt.precond == BFMRI_PRECOND_SSOR && h->opt.ssor_omega != h0->opt.ssor_omega))
       return fail(h0, BFMRI_ERR_INVALID_ARG,
                   "grouped chains must share K, P, the AR prior, delta, max_iter and the preconditioner");
     if (h->opt.precision != BFMRI_PREC_FP64)
@@ -1126,6 +1170,7 @@ bfmri_status bfmri_gibbs_sweep_group(bfmri_handle* const* hs, int n, int n_sweep
   }
   auto solve = [&](int D, int which) -> bfmri_status {
     MrhsArgs m = mrhs_args(h0, D, n, nullptr, h0->opt.max_iter, false);
+    mrhs_ssor(h0, m);
     m.tab = h0->d_gtab + (size_t)which * n;
     m.tally = h0->d_gtally + (size_t)which * n;
     m.blocks = nullptr;
@@ -1407,6 +1452,7 @@ bfmri_status bfmri_spvb_step(bfmri_handle* h, int n_samples, uint64_t counter, i
   e = launch_svb(2, K, sv, h->stream, nullptr);
   if (e != cudaSuccess) return cuda_fail(h, e, "svb rhs W");
   MrhsArgs m = mrhs_args(h, K, S, h->d_alpha, h->opt.max_iter, false);
+  mrhs_ssor(h, m);
   m.vs = (size_t)K * ld;
   m.x = h->svb_W;
   {
@@ -1442,6 +1488,7 @@ bfmri_status bfmri_spvb_step(bfmri_handle* h, int n_samples, uint64_t counter, i
     e = launch_svb(2, P, sv, h->stream, nullptr);
     if (e != cudaSuccess) return cuda_fail(h, e, "svb rhs A");
     MrhsArgs ma = mrhs_args(h, P, S, bscale, h->opt.max_iter, false);
+    mrhs_ssor(h, ma);
     ma.vs = (size_t)P * ld;
     ma.x = h->svb_A;
     {

@@ -344,6 +344,56 @@ __global__ void __launch_bounds__(MRHS_THREADS, (sizeof(T) == 4 || D <= 4) ? 2 :
   };
   // mode-0 pass: r = b - B~ x, u = M^-1 r, publish u; then w = B~ u and partials
   // for every RHS selected by `sel` (state 1 on the first pass, 2 afterwards).
+  // SSOR phases 2 (black voxels) and 3 (red voxels) of every right-hand side selected by
+  // `sel(r)`, each after a grid barrier: units (rhs, chunk of the colour list), lanes over
+  // consecutive list entries. u holds z in place (see the single-solve kernels):
+  //   black n: u_n = (2 - omega) omega Dg_n^-1 (r_n + scale .* sum_m u_m)
+  //   red n:   u_n = (2 - omega) u_n + omega Dg_n^-1 (scale .* sum_m u_m)
+  auto ssor_phases = [&](auto sel) -> bool {
+    const T omega = (T)a.omega, c2 = T(2) - omega;
+    for (int phase = 2; phase <= 3; ++phase) {
+      if (!grid_sync(a.bar, &sh_flag)) return false;
+      const int* list = phase == 2 ? a.black : a.red;
+      const int nl = phase == 2 ? a.n_black : a.n_red;
+      const int ch = U.chunks;
+      int cs = (nl + ch - 1) / ch;
+      cs = ((cs + 31) / 32) * 32;
+      for (int u = U.gw; u < U.units; u += U.nw) {
+        const int r = unit_rhs(u), c = unit_chunk(u);
+        if (!sel(r)) continue;
+        const RhsOp<D, T> op = rhs_op<D, T>(a, r);
+        const T* R = Rv + (size_t)r * a.vs;
+        T* Uu = UUv + (size_t)r * a.vs;
+        const int i1 = min(nl, (c + 1) * cs);
+        for (int i = c * cs + U.lane; i < i1; i += 32) {
+          const int n = __ldg(list + i);
+          int nb[6];
+#pragma unroll
+          for (int d = 0; d < 6; ++d) nb[d] = d < a.ndir ? __ldg(a.nbr + (size_t)d * ld + n) : -1;
+          T sum[D];
+#pragma unroll
+          for (int k = 0; k < D; ++k) sum[k] = T(0);
+#pragma unroll
+          for (int d = 0; d < 6; ++d) {
+            if (nb[d] >= 0) {
+#pragma unroll
+              for (int k = 0; k < D; ++k) sum[k] += Uu[(size_t)k * ld + nb[d]];
+            }
+          }
+          T t[D], z[D];
+#pragma unroll
+          for (int k = 0; k < D; ++k) t[k] = phase == 2 ? R[(size_t)k * ld + n] + op.sc[k] * sum[k] : op.sc[k] * sum[k];
+          precond_apply<D, T>(a, op.M, n, t, z);
+#pragma unroll
+          for (int k = 0; k < D; ++k) {
+            const size_t o = (size_t)k * ld + n;
+            Uu[o] = phase == 2 ? c2 * omega * z[k] : c2 * Uu[o] + omega * z[k];
+          }
+        }
+      }
+    }
+    return true;
+  };
   auto restart_pass = [&](bool first) -> bool {
     for (int u = U.gw; u < U.units; u += U.nw) {
       const int r = unit_rhs(u), c = unit_chunk(u);
@@ -362,6 +412,10 @@ __global__ void __launch_bounds__(MRHS_THREADS, (sizeof(T) == 4 || D <= 4) ? 2 :
 #pragma unroll
         for (int k = 0; k < D; ++k) rn[k] = __ldg(b + (size_t)k * ld + n) - ax[k];
         precond_apply<D, T>(a, op.M, n, rn, un);
+        if (a.ssor) {
+#pragma unroll
+          for (int k = 0; k < D; ++k) un[k] *= (T)a.omega;   // SSOR phase 1
+        }
 #pragma unroll
         for (int k = 0; k < D; ++k) {
           R[(size_t)k * ld + n] = rn[k];
@@ -371,6 +425,8 @@ __global__ void __launch_bounds__(MRHS_THREADS, (sizeof(T) == 4 || D <= 4) ? 2 :
         }
       }
     }
+    if (a.ssor && !ssor_phases([&](int r) { return first || __ldcg(&a.st[r].active) == 2; }))
+      return false;
     if (!grid_sync(a.bar, &sh_flag)) return false;
     for (int u = U.gw; u < U.units; u += U.nw) {
       const int r = unit_rhs(u), c = unit_chunk(u);
@@ -441,6 +497,10 @@ __global__ void __launch_bounds__(MRHS_THREADS, (sizeof(T) == 4 || D <= 4) ? 2 :
             rn[k] -= al * sk[k];
           }
           precond_apply<D, T>(a, op.M, n, rn, un);
+          if (a.ssor) {
+#pragma unroll
+            for (int q = 0; q < D; ++q) un[q] *= (T)a.omega;   // SSOR phase 1
+          }
           T g = T(0), rr2 = T(0);
 #pragma unroll
           for (int k = 0; k < D; ++k) {
@@ -515,16 +575,18 @@ __global__ void __launch_bounds__(MRHS_THREADS, (sizeof(T) == 4 || D <= 4) ? 2 :
           }
         }
         double acc[4] = {kg.value(), 0.0, kr.value(), 0.0};
-        write_partials(u, acc, 0x5u);
+        write_partials(u, acc, a.ssor ? 0x4u : 0x5u);   // with SSOR, r'u follows the phases
       }
+      if (a.ssor && !ssor_phases([&](int r) { return __ldcg(&a.st[r].active) == 1; })) return;
       if (!grid_sync(a.bar, &sh_flag)) return;
       // w = B~ u and the partial w'u (column 1)
       for (int u = U.gw; u < U.units; u += U.nw) {
         const int r = unit_rhs(u), c = unit_chunk(u);
         if (__ldcg(&a.st[r].active) != 1) continue;
-        KSum<T> kd;
+        KSum<T> kd, kg;
         const RhsOp<D, T> op = rhs_op<D, T>(a, r);
         const T* Uu = UUv + (size_t)r * a.vs;
+        const T* R = Rv + (size_t)r * a.vs;
         T* Wv = WWv + (size_t)r * a.vs;
         const int n1 = min(a.N, (c + 1) * U.csize);
         for (int n = c * U.csize + U.lane; n < n1; n += 32) {
@@ -532,16 +594,21 @@ __global__ void __launch_bounds__(MRHS_THREADS, (sizeof(T) == 4 || D <= 4) ? 2 :
 #pragma unroll
           for (int k = 0; k < D; ++k) un[k] = Uu[(size_t)k * ld + n];
           block_apply<D, T>(a, op.B, op.sc, n, un, Uu, wn);
-          T dl = T(0);
+          T dl = T(0), g = T(0);
 #pragma unroll
           for (int k = 0; k < D; ++k) {
             dl += wn[k] * un[k];
             Wv[(size_t)k * ld + n] = wn[k];
           }
+          if (a.ssor) {
+#pragma unroll
+            for (int k = 0; k < D; ++k) g += R[(size_t)k * ld + n] * un[k];
+            kg.add(g);
+          }
           kd.add(dl);
         }
-        double acc[4] = {0.0, kd.value(), 0.0, 0.0};
-        write_partials(u, acc, 0x2u);
+        double acc[4] = {kg.value(), kd.value(), 0.0, 0.0};
+        write_partials(u, acc, a.ssor ? 0x3u : 0x2u);
       }
       if (!mrhs_reduce(a, U, 1, false, sh_int, &any_active, &any_pending)) return;
     } else {

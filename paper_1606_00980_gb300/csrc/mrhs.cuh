@@ -78,6 +78,14 @@ struct MrhsArgs {
   const MrhsRhsPtrs* tab;  // [S] per-RHS operators, b and x (device), or null: all share
                            // blocks/mfac/scale and b, x are strided by vs
   MrhsTally* tally;      // [S] (device) or null
+  // red-black symmetric SOR over the block-Jacobi blocks (plain solves only: the probes'
+  // quadrature needs block-Jacobi): lattice colour lists shared by every right-hand side
+  int ssor;
+  double omega;
+  const int* red;
+  int n_red;
+  const int* black;
+  int n_black;
 };
 
 // Probe set-up and post-processing (log-determinant and trace probes).

@@ -48,13 +48,18 @@ WL = {
 }
 
 
+# block-Jacobi (0) and red-black SSOR (2) preconditioning of the multi-RHS solves
+PRECONDS = {"bj": dict(), "ssor": dict(precond=2), "ssor_w1.3": dict(precond=2, ssor_omega=1.3)}
+
+
+@pytest.mark.parametrize("pc", sorted(PRECONDS))
 @pytest.mark.parametrize("name", sorted(WL))
-def test_group_sweep_matches_oracle_per_chain(name):
+def test_group_sweep_matches_oracle_per_chain(name, pc):
     from paper_1606_00980_gb300.bfmri import gibbs_sweep_group
     w = WL[name]
     lat = Lattice(w.mask, w.neighbourhood)
     states = [state_for(w, np.random.default_rng(40 + i)) for i in range(len(SEEDS))]
-    models = [make(w, sd, st) for sd, st in zip(SEEDS, states)]
+    models = [make(w, sd, st, **PRECONDS[pc]) for sd, st in zip(SEEDS, states)]
     infos = gibbs_sweep_group(models, 1, first_counter=9)
     for m, sd, s, inf in zip(models, SEEDS, states, infos):
         g = m.get_state()
@@ -79,14 +84,15 @@ def test_group_sweep_matches_oracle_per_chain(name):
         m.close()
 
 
-def test_group_matches_chains_advanced_alone():
-    """Three sweeps at the bench tolerance (1e-8): grouped and lone chains agree to the
+@pytest.mark.parametrize("pc", ["bj", "ssor"])
+def test_group_matches_chains_advanced_alone(pc):
+    """Three sweeps at a tight tolerance (1e-10): grouped and lone chains agree to the
     solver tolerance, sweep after sweep (the later steps see the earlier draws)."""
     from paper_1606_00980_gb300.bfmri import gibbs_sweep_group
     w = WL["slab_K6_P3"]
     states = [state_for(w, np.random.default_rng(70 + i)) for i in range(len(SEEDS))]
-    grouped = [make(w, sd, st, delta=1e-10) for sd, st in zip(SEEDS, states)]
-    alone = [make(w, sd, st, delta=1e-10) for sd, st in zip(SEEDS, states)]
+    grouped = [make(w, sd, st, delta=1e-10, **PRECONDS[pc]) for sd, st in zip(SEEDS, states)]
+    alone = [make(w, sd, st, delta=1e-10, **PRECONDS[pc]) for sd, st in zip(SEEDS, states)]
     gibbs_sweep_group(grouped, 3, first_counter=4)
     for m in alone:
         m.gibbs_sweep(3, first_counter=4)
@@ -127,11 +133,13 @@ def test_group_rejects_mismatched_chains():
     other = WL["slab_K6_P3"]
     c = make(other, 3, state_for(other, np.random.default_rng(2)))
     d = make(w, 4, s, precision=bfmri.PREC_MIXED)
-    for group in ([a, c], [a, a], [a, d]):
+    e = make(w, 5, s, precond=2)
+    f = make(w, 6, s, precond=2, ssor_omega=1.2)
+    for group in ([a, c], [a, a], [a, d], [a, e], [e, f]):
         with pytest.raises(bfmri.BfmriError) as ei:
             bfmri.gibbs_sweep_group(group, 1)
         assert ei.value.status == -1
     # the valid pair still runs after the rejected calls
     bfmri.gibbs_sweep_group([a, b], 1)
-    for m in (a, b, c, d):
+    for m in (a, b, c, d, e, f):
         m.close()

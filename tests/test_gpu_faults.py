@@ -5,6 +5,7 @@
   context stays usable: the next call succeeds and matches a fresh handle.
 * A singular data block (an all-zero design column, no ridge: a zero pivot): BFMRI_ERR_NOT_SPD.
 * An iteration cap below what the tolerance needs: BFMRI_ERR_NOT_CONVERGED.
+* Asynchronous sweeps (no host wait): their errors and counts are read later.
 * Checkpoint/resume: a chain stopped after s sweeps and resumed from its saved state in a new
   handle continues bit-identically (counter-based random numbers).
 """
@@ -81,3 +82,41 @@ def test_checkpoint_resume_is_bitwise():
     resumed.close()
     for k in end:
         assert np.array_equal(got[k], end[k]), k
+
+
+def test_asynchronous_sweeps_match_and_report_at_synchronize():
+    """Sweeps enqueued without info (no host wait) give the same states as synchronous
+    sweeps; synchronize() reports the PCG counts of the whole asynchronous span."""
+    w = synth.small3d(seed=7, dims=(10, 9, 7), K=3, P=2, T=40)
+    sync = model(w, delta=1e-10)
+    asyn = model(w, delta=1e-10)
+    total_w = total_a = 0
+    for s in range(4):
+        inf = sync.gibbs_sweep(1, 50 + s)
+        total_w += inf.pcg_iterations_W
+        total_a += inf.pcg_iterations_A
+        asyn.gibbs_sweep(1, 50 + s, info=False)
+    got = asyn.synchronize()
+    assert (got.pcg_iterations_W, got.pcg_iterations_A) == (total_w, total_a)
+    a, b = sync.get_state(), asyn.get_state()
+    for k in a:
+        assert np.array_equal(a[k], b[k]), k
+    # nothing unread now: a second synchronize reports no work
+    again = asyn.synchronize()
+    assert (again.pcg_iterations_W, again.pcg_iterations_A) == (0, 0)
+    sync.close()
+    asyn.close()
+
+
+def test_asynchronous_sweep_error_is_reported_later():
+    """An iteration cap hit inside an asynchronous sweep: the enqueueing call succeeds, the
+    next synchronising call raises NOT_CONVERGED, and the one after it starts clean."""
+    from paper_1606_00980_gb300 import bfmri
+    w = synth.small3d(seed=5, dims=(9, 9, 7), K=3, P=1, T=40)
+    m = model(w, max_iter=2, delta=1e-12)
+    m.gibbs_sweep(1, 0, info=False)
+    with pytest.raises(bfmri.BfmriError) as ei:
+        m.synchronize()
+    assert ei.value.status == -4
+    assert m.synchronize().pcg_iterations_W == 0
+    m.close()

@@ -23,7 +23,7 @@ def rel(a, b):
     return np.linalg.norm(np.ravel(a) - np.ravel(b)) / np.linalg.norm(np.ravel(b))
 
 
-def setup(spatial=True, K=3, P=2):
+def setup(spatial=True, K=3, P=2, **opts):
     from paper_1606_00980_gb300 import bfmri
     from paper_1606_00980_gb300.bfmri import Model
     w = synth.small3d(seed=41, dims=(8, 7, 6), K=K, P=P, T=45)
@@ -33,15 +33,17 @@ def setup(spatial=True, K=3, P=2):
              lam=rng.uniform(0.5, 2.0, w.N), alpha=rng.uniform(0.3, 3.0, K),
              beta=rng.uniform(2.0, 9.0, P))
     m = Model.from_workload(w, delta=1e-12, seed=SEED,
-                            ar_prior=bfmri.AR_SPATIAL if spatial else bfmri.AR_INDEPENDENT)
+                            ar_prior=bfmri.AR_SPATIAL if spatial else bfmri.AR_INDEPENDENT, **opts)
     m.precompute_stats()
     m.set_state(W=s["W"], A=s["A"], lam=s["lam"], alpha=s["alpha"], beta=s["beta"])
     return w, lat, s, m
 
 
+@pytest.mark.parametrize("precond", [0, 2])
 @pytest.mark.parametrize("spatial", [True, False])
-def test_svb_step_single_step_parity(spatial):
-    w, lat, s, m = setup(spatial)
+def test_svb_step_single_step_parity(spatial, precond):
+    """precond 0: block-Jacobi multi-RHS solves; 2: red-black SSOR."""
+    w, lat, s, m = setup(spatial, precond=precond)
     Ns, c = 4, 11
     avb, bvb, info = m.spvb_step(Ns, c, extrapolate=False)
     Wg, Ag = zip(*[m.svb_sample(j) for j in range(Ns)])
