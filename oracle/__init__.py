@@ -24,6 +24,9 @@ gibbs    -- one Gibbs sweep (Section 3.2) and one spatial-VB step (Section 3.3, 
 probes   -- exact log-determinant and trace terms behind the stochastic probes
 precond  -- block-Jacobi and red-black symmetric SOR preconditioners (replacing the
             incomplete Cholesky of Section 3.1), factored form and voxel-by-voxel sweeps
+summaries -- posterior summaries: chain PPMs and joint PPMs (Eq. MCMCPPM, Eq. MCMCjointPPM),
+            SVB sample moments and Gaussian PPMs (Section 3.3), the unnormalised log joint
+            posterior (Eq. UnnormalisedJointPosterior)
 
 Parity status: every function is pinned by a ``-m "not gpu"`` test against a closed form,
 an invariant, an independent library routine or brute force, except the SVB convergence
