@@ -351,6 +351,8 @@ def run_ours(args, world, rank, local):
 
     # the same chain with the mixed-precision solver (FP32 inner, FP64 refinement, same delta)
     mixed = run_mixed(args, w, flush, stream) if not args.no_mixed else None
+    # posterior summaries (chain PPMs, moments, log joint) on the same workload
+    summ = run_summaries(args, w) if (rank == 0 and not args.no_summaries) else None
 
     # independent chains of the same subject advanced together (one multi-RHS launch per solve)
     chains = run_chains(args, w, flush, stream, value) if not args.no_chains else None
@@ -379,13 +381,63 @@ def run_ours(args, world, rank, local):
                            "pcg_iterations_A_per_sweep": it_a / args.steps},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                 "voxel_draws_per_s": value * N,
-                "mixed_precision": mixed, "grouped_chains": chains, "preconditioners": precs,
+                "mixed_precision": mixed, "summaries": summ, "grouped_chains": chains,
+                "preconditioners": precs,
                 "captured_sweeps": graphs, "serving": serving, "batched_probes": batched,
                 "gpu_launches": int(n_launch),
                 "kernel_ms_per_step": {k: v["ms"] / n_prof for k, v in tim_p.items() if v["launches"]},
                 "kernel_ms_per_step_note": "the same chain and sweeps rerun with every launch "
                                            "timed; the timed region times only the solver launches"}
         print(json.dumps(line), flush=True)
+
+
+def bench_contrasts(K):
+    """Three contrasts (first regressor, first minus second, a linear ramp) and thresholds."""
+    import numpy as np
+    C = np.zeros((3, K))
+    C[0, 0] = 1.0
+    C[1, 0], C[1, 1 % K] = 1.0, -1.0
+    C[2] = np.linspace(0.5, -0.5, K)
+    return C, np.array([0.5, 0.0, 0.1])
+
+
+def run_summaries(args, w, sweeps=20):
+    """Posterior summaries on the headline workload: the chain accumulation added to every
+    sweep (3 contrast PPMs, a joint-PPM set of 1000 voxels, moments of W; one
+    k_chain_accumulate launch per sweep) and the log joint posterior (Eq.
+    UnnormalisedJointPosterior), each timed with CUDA events around its launches (profile 1).
+    Bytes per accumulation: per voxel W, the reference sample, S1 and S2 read and written
+    (8 B words), the counts read and written (4 B), the set flag (1 B)."""
+    import numpy as np
+
+    from paper_1606_00980_gb300.bfmri import Model
+    m = Model.from_workload(w, delta=1e-8, seed=2024, profile=1, **precond_options(args))
+    m.precompute_stats()
+    m.gibbs_sweep(3, 0)
+    C, g = bench_contrasts(w.K)
+    E = np.random.default_rng(5).choice(w.N, 1000, replace=False)
+    m.summary_begin(C, g, joint_set=E)
+    m.reset_timing()
+    m.gibbs_sweep(sweeps, 3)
+    tim = m.timing()
+    acc = tim["summary"]
+    sweep_ms = sum(v["ms"] for v in tim.values()) / sweeps
+    got = m.summary_get()
+    m.reset_timing()
+    for _ in range(10):
+        lj = m.log_joint()
+    t_lj = m.timing()["summary"]["ms"] / 10
+    m.close()
+    K, N, nc = w.K, w.N, len(g)
+    bytes_acc = N * (8 * (K + K + 2 * K + 2 * (K * (K + 1) // 2)) + 4 * 2 * nc + 1)
+    acc_s = acc["ms"] / max(acc["launches"], 1) / 1e3
+    hbm_peak, hbm_src, _ = peaks()
+    return {"samples": got["n"], "contrasts": nc, "joint_set_voxels": len(E),
+            "accumulate_us": acc_s * 1e6, "share_of_sweep": acc["ms"] / sweeps / sweep_ms,
+            "accumulate_hbm": {"achieved_gbs": bytes_acc / acc_s / 1e9, "peak_gbs": hbm_peak,
+                               "frac": bytes_acc / acc_s / 1e9 / hbm_peak, "bytes": bytes_acc},
+            "joint_ppm": (got["joint_count"] / got["n"]).tolist(),
+            "log_joint_us": t_lj * 1e3, "log_joint": lj["total"]}
 
 
 def run_mixed(args, w, flush, stream):
@@ -616,12 +668,27 @@ def run_batched(args):
         torch.cuda.synchronize()
         dt = time.perf_counter() - t1
         tsv = ms.timing()
+        # Section 3.3 summaries of the 100 samples: moments and Gaussian contrast PPMs (one
+        # k_svb_summary launch streams the samples once)
+        Cs, gs = bench_contrasts(w.K)
+        ms.svb_summary(Cs, gs)
+        ms.reset_timing()
+        ms.svb_summary(Cs, gs)
+        t_sum = ms.timing()["summary"]["ms"]
         ms.close()
+        K = w.K
+        sum_bytes = 100 * K * w.N * 8 + (K + K * (K + 1) // 2 + len(gs)) * w.N * 8
+        hbm_peak, _, _ = peaks()
         svb = {"samples": 100, "precond": args.precond, "iteration_ms": dt * 1e3,
                "pcg_iterations_W_total": int(info.pcg_iterations_W),
                "pcg_iterations_A_total": int(info.pcg_iterations_A),
                "W_solve_ms": tsv["pcg_W"]["ms"], "A_solve_ms": tsv["pcg_A"]["ms"],
-               "max_rel_residual_W": info.max_rel_residual_W}
+               "max_rel_residual_W": info.max_rel_residual_W,
+               "summary": {"contrasts": len(gs), "ms": t_sum,
+                           "hbm": {"achieved_gbs": sum_bytes / (t_sum / 1e3) / 1e9,
+                                   "peak_gbs": hbm_peak,
+                                   "frac": sum_bytes / (t_sum / 1e3) / 1e9 / hbm_peak},
+                           "bytes": sum_bytes}}
     bytes_ = iters * w.N * mrhs_bytes_per_voxel_iter_rhs(w.K, S)
     hbm_peak, hbm_src, _ = peaks()
     gbs = bytes_ / solve_s / 1e9
@@ -749,6 +816,7 @@ def main():
     ap.add_argument("--no-chains", action="store_true")
     ap.add_argument("--no-precond", action="store_true")
     ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--no-summaries", action="store_true")
     ap.add_argument("--precond", choices=["ssor", "bj"], default="ssor",
                     help="preconditioner of the headline chain and of its mixed-precision twin "
                          "(the multi-RHS solves use block-Jacobi)")

@@ -295,6 +295,56 @@ bfmri_status bfmri_spvb_step(bfmri_handle* h, int n_samples, uint64_t counter, i
 bfmri_status bfmri_svb_get_sample(bfmri_handle* h, int j, double* W, double* A);
 bfmri_status bfmri_svb_set_sample(bfmri_handle* h, int j, const double* W, const double* A);
 
+/* ---- Posterior summaries -----------------------------------------------------------
+ * Voxel-indexed outputs are row-major with N columns in the compact order of the mask;
+ * covariances are packed per voxel: row i (i + 1) / 2 + j holds Cov(W_i,n, W_j,n), j <= i.
+ * Contrasts: C is n_contrasts x K row-major, gamma has n_contrasts thresholds,
+ * 0 <= n_contrasts <= BFMRI_MAX_CONTRASTS; a contrast value c'W_.,n is summed over k in
+ * order with one rounding per product and per addition (no fused multiply-add). */
+#define BFMRI_MAX_CONTRASTS 16
+
+/* Opens a chain summary (Section 3.2): from now on every Gibbs sweep of this handle
+ * (bfmri_gibbs_sweep, bfmri_gibbs_sweep_group) adds its W draw as one sample, on the device:
+ * per voxel the sample moments of W_.,n (shifted by the W at this call), per voxel and
+ * contrast the number of samples with c'W_.,n > gamma (the marginal PPM of Eq. MCMCPPM), and
+ * per contrast the number of samples in which every voxel of joint_set exceeds gamma (the
+ * joint probability of Eq. MCMCjointPPM; joint_set holds n_joint compact voxel indices, may
+ * repeat; with n_joint = 0 every sample counts). Reopening discards the previous summary.
+ * The captured sweep graph (options.use_graph) is re-captured with the accumulation.
+ * Errors: INVALID_ARG (contrasts, indices), OOM, CUDA. */
+bfmri_status bfmri_summary_begin(bfmri_handle* h, int n_contrasts, const double* C,
+                                 const double* gamma, const int* joint_set, int n_joint);
+
+/* Adds the current W as one sample (enqueued on the handle's stream; no host wait). */
+bfmri_status bfmri_summary_add(bfmri_handle* h);
+
+/* Waits for the handle's work (reporting errors of asynchronous sweeps) and reads the open
+ * summary: n_samples; mean (K x N); cov (K(K+1)/2 x N, divisor n - 1, zero for n = 1);
+ * ppm (n_contrasts x N, count / n); joint_count (n_contrasts; joint PPM = count / n). Any
+ * output may be NULL. Errors: STATE (no summary, or outputs asked with no sample). */
+bfmri_status bfmri_summary_get(bfmri_handle* h, long long* n_samples, double* mean, double* cov,
+                               double* ppm, long long* joint_count);
+
+/* Closes the summary and frees its device memory (no-op when none is open). */
+bfmri_status bfmri_summary_end(bfmri_handle* h);
+
+/* Summary of the N_s SVB samples of q(W) held by the handle (Section 3.3): sample mean
+ * (K x N), sample covariance (packed, divisor N_s - 1) and, per contrast, the PPM of the
+ * Gaussian with those moments, P(c'W_.,n > gamma) = erfc((gamma - c'mu_n) /
+ * sqrt(2 c'Sigma_n c)) / 2 (the indicator c'mu_n > gamma when c'Sigma_n c = 0). Outputs may
+ * be NULL. Errors: STATE (no SVB samples), INVALID_ARG, OOM, CUDA. */
+bfmri_status bfmri_svb_summary(bfmri_handle* h, int n_contrasts, const double* C,
+                               const double* gamma, double* mean, double* cov, double* ppm);
+
+/* Unnormalised log joint posterior at the current state (Appendix A, Eq.
+ * UnnormalisedJointPosterior): terms[0] log-likelihood without its constant (Eq. log-like,
+ * sums over t = P+1..T), [1] log p~(W | alpha) = sum_k N/2 log alpha_k - alpha_k W_k D_w W_k'/2,
+ * [2] the same for A and beta (0 under the independent AR prior), [3..5] the Gamma
+ * log-priors of lambda, alpha, beta without constants (Ga(scale, shape)), [6] the total.
+ * Differences between two states are log posterior ratios. Errors: STATE (statistics not
+ * computed), INVALID_ARG, CUDA. */
+bfmri_status bfmri_log_joint(bfmri_handle* h, double* terms);
+
 /* Gauss quadrature value e1' log(T) e1 of the Lanczos tridiagonal T built from m CG
  * coefficients (alpha_0..alpha_{m-1}, beta_0..beta_{m-2}) of a preconditioned CG run from
  * x = 0; host-only helper used by bfmri_logdet_probe. */
@@ -311,7 +361,8 @@ bfmri_status bfmri_lanczos_log_quadrature(int m, const double* cg_alpha, const d
 #define BFMRI_T_LAMBDA     5
 #define BFMRI_T_HYPER      6  /* alpha and beta */
 #define BFMRI_T_OTHER      7
-#define BFMRI_T_CLASSES    8
+#define BFMRI_T_SUMMARY    8  /* posterior summaries and the log joint posterior */
+#define BFMRI_T_CLASSES    9
 typedef struct {
   double ms[BFMRI_T_CLASSES];
   long long launches[BFMRI_T_CLASSES];

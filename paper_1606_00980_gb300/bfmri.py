@@ -66,12 +66,16 @@ class bfmri_sweep_info(C.Structure):
                 ("gamma_exhausted", C.c_longlong), ("captured", C.c_int)]
 
 
-T_CLASSES = ["stats", "assemble_W", "pcg_W", "assemble_A", "pcg_A", "lambda", "hyper", "other"]
+T_CLASSES = ["stats", "assemble_W", "pcg_W", "assemble_A", "pcg_A", "lambda", "hyper", "other",
+             "summary"]
+MAX_CONTRASTS = 16
+LOG_JOINT_TERMS = ["loglik", "W_prior", "A_prior", "lambda_prior", "alpha_prior", "beta_prior",
+                   "total"]
 
 
 class bfmri_timing(C.Structure):
-    _fields_ = [("ms", C.c_double * 8), ("launches", C.c_longlong * 8),
-                ("pcg_iterations", C.c_longlong * 8)]
+    _fields_ = [("ms", C.c_double * 9), ("launches", C.c_longlong * 9),
+                ("pcg_iterations", C.c_longlong * 9)]
 
 
 class bfmri_request(C.Structure):
@@ -114,6 +118,14 @@ SIGNATURES = [
     ("bfmri_gibbs_sweep", C.c_int, [_h, C.c_int, C.c_uint64, _P(bfmri_sweep_info)]),
     ("bfmri_gibbs_sweep_group", C.c_int, [_P(_h), C.c_int, C.c_int, C.c_uint64, _P(bfmri_sweep_info)]),
     ("bfmri_synchronize", C.c_int, [_h, _P(bfmri_sweep_info)]),
+    ("bfmri_summary_begin", C.c_int, [_h, C.c_int, _P(C.c_double), _P(C.c_double), _P(C.c_int), C.c_int]),
+    ("bfmri_summary_add", C.c_int, [_h]),
+    ("bfmri_summary_get", C.c_int, [_h, _P(C.c_longlong), _P(C.c_double), _P(C.c_double),
+                                    _P(C.c_double), _P(C.c_longlong)]),
+    ("bfmri_summary_end", C.c_int, [_h]),
+    ("bfmri_svb_summary", C.c_int, [_h, C.c_int, _P(C.c_double), _P(C.c_double), _P(C.c_double),
+                                    _P(C.c_double), _P(C.c_double)]),
+    ("bfmri_log_joint", C.c_int, [_h, _P(C.c_double)]),
     ("bfmri_logdet_probe", C.c_int, [_h, C.c_int, C.c_int, C.c_int, C.c_uint64, _dp, _dp, _dp, _dp,
                                      _P(C.c_int)]),
     ("bfmri_lanczos_log_quadrature", C.c_int, [C.c_int, _dp, _dp, _dp]),
@@ -325,6 +337,16 @@ def bfmri_pcg_solve_static(N, D, neighbourhood, nbr_ptr, ld, blocks_ptr, scale_p
     return info
 
 
+def unpack_cov(packed, K):
+    """(K(K+1)/2, N) packed lower triangles (row i(i+1)/2 + j, j <= i) -> (N, K, K)."""
+    N = packed.shape[1]
+    out = np.empty((N, K, K))
+    for i in range(K):
+        for j in range(i + 1):
+            out[:, i, j] = out[:, j, i] = packed[i * (i + 1) // 2 + j]
+    return out
+
+
 def gibbs_sweep_group(models, n_sweeps, first_counter=0):
     """Advances the chains of `models` (Model objects on one lattice and mask) together by
     n_sweeps Gibbs sweeps, their W and A systems solved as one multi-RHS launch per step
@@ -446,6 +468,56 @@ class Model:
         self._c(self.lib.bfmri_gibbs_sweep(self.handle, n_sweeps, first_counter,
                                            C.byref(inf) if info else None))
         return inf
+
+    def _contrasts(self, contrast, gamma):
+        cm = np.ascontiguousarray(np.atleast_2d(np.asarray(contrast, dtype=np.float64)))
+        gamma = np.ascontiguousarray(np.atleast_1d(np.asarray(gamma, dtype=np.float64)))
+        return cm, gamma
+
+    def summary_begin(self, contrast, gamma, joint_set=None):
+        """Opens a chain summary (marginal / joint contrast PPMs and moments of W); every later
+        sweep adds its draw. joint_set: compact voxel indices of the joint-PPM set."""
+        cm, gamma = self._contrasts(contrast, gamma)
+        js = np.ascontiguousarray(np.asarray([] if joint_set is None else joint_set, dtype=np.int32))
+        self._c(self.lib.bfmri_summary_begin(self.handle, len(gamma), _ptr(cm), _ptr(gamma),
+                                             js.ctypes.data_as(_P(C.c_int)) if len(js) else None,
+                                             len(js)))
+        self._n_contrasts = len(gamma)
+
+    def summary_add(self):
+        self._c(self.lib.bfmri_summary_add(self.handle))
+
+    def summary_get(self):
+        K, N, nc = self.K, self.N, self._n_contrasts
+        n = C.c_longlong()
+        mean = np.empty((K, N))
+        covp = np.empty((K * (K + 1) // 2, N))
+        ppm = np.empty((nc, N))
+        jc = (C.c_longlong * max(nc, 1))()
+        self._c(self.lib.bfmri_summary_get(self.handle, C.byref(n), _ptr(mean), _ptr(covp),
+                                           _ptr(ppm), jc))
+        return dict(n=n.value, mean=mean, cov_packed=covp, cov=unpack_cov(covp, K), ppm=ppm,
+                    joint_count=np.array(jc[:nc], dtype=np.int64))
+
+    def summary_end(self):
+        self._c(self.lib.bfmri_summary_end(self.handle))
+
+    def svb_summary(self, contrast, gamma):
+        """Moments of the SVB samples and the Gaussian contrast PPMs (Section 3.3)."""
+        cm, gamma = self._contrasts(contrast, gamma)
+        K, N = self.K, self.N
+        mean = np.empty((K, N))
+        covp = np.empty((K * (K + 1) // 2, N))
+        ppm = np.empty((len(gamma), N))
+        self._c(self.lib.bfmri_svb_summary(self.handle, len(gamma), _ptr(cm), _ptr(gamma),
+                                           _ptr(mean), _ptr(covp), _ptr(ppm)))
+        return dict(mean=mean, cov_packed=covp, cov=unpack_cov(covp, K), ppm=ppm)
+
+    def log_joint(self):
+        """Unnormalised log joint posterior of the current state, by term."""
+        t = np.empty(7)
+        self._c(self.lib.bfmri_log_joint(self.handle, _ptr(t)))
+        return dict(zip(LOG_JOINT_TERMS, (float(v) for v in t)))
 
     def synchronize(self):
         """Waits for the enqueued work; raises the first error of the asynchronous sweeps

@@ -14,6 +14,7 @@
 #include "model.cuh"
 #include "mrhs.cuh"
 #include "pcg.cuh"
+#include "summary.cuh"
 
 using namespace bfmri;
 
@@ -77,6 +78,20 @@ struct bfmri_handle {
   // asynchronous sweeps (bfmri_gibbs_sweep without info) left their error words and PCG
   // counters unread: they accumulate until the next synchronising call
   bool deferred = false;
+  // posterior summaries of the chain (bfmri_summary_begin .. bfmri_summary_end)
+  struct Summary {
+    bool open = false;
+    int nc = 0;
+    long long n = 0;
+    bool has_set = false;
+    double *ref = nullptr, *S1 = nullptr, *S2 = nullptr, *C = nullptr, *gamma = nullptr;
+    double *mean = nullptr, *cov = nullptr, *ppm = nullptr;   // bfmri_summary_get output planes
+    int* count = nullptr;
+    uint8_t* in_set = nullptr;
+    unsigned long long* joint = nullptr;
+    unsigned int* scratch = nullptr;   // [2] joint-set failure word and CTA ticket
+  } sum;
+  double* d_lj = nullptr;   // log joint: [7] terms, [K] Q of W, [P] Q of A, CTA partials
   // grouped chains: per-chain operator tables [2][cap] and tallies [2][cap]
   MrhsRhsPtrs* d_gtab = nullptr;
   MrhsTally* d_gtally = nullptr;
@@ -450,6 +465,29 @@ bfmri_status enqueue_lambda(bfmri_handle* h, uint64_t counter) {
   Timed tm(h, BFMRI_T_LAMBDA);
   cudaError_t e = launch_lambda(a, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "lambda");
+  return BFMRI_OK;
+}
+
+// Adds the current W as one sample to the open chain summary (kernels_summary.cu).
+bfmri_status enqueue_summary(bfmri_handle* h) {
+  ChainSumArgs a;
+  a.g = geom(h);
+  a.K = h->K;
+  a.nc = h->sum.nc;
+  a.W = h->d_W;
+  a.ref = h->sum.ref;
+  a.C = h->sum.C;
+  a.gamma = h->sum.gamma;
+  a.in_set = h->sum.has_set ? h->sum.in_set : nullptr;
+  a.S1 = h->sum.S1;
+  a.S2 = h->sum.S2;
+  a.count = h->sum.count;
+  a.joint = h->sum.joint;
+  a.fail = h->sum.scratch;
+  a.ticket = h->sum.scratch + 1;
+  Timed tm(h, BFMRI_T_SUMMARY);
+  const cudaError_t e = launch_chain_accumulate(a, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "chain summary");
   return BFMRI_OK;
 }
 
@@ -1020,6 +1058,7 @@ bfmri_status bfmri_gibbs_sweep(bfmri_handle* h, int n_sweeps, uint64_t first_cou
     RET(enqueue_lambda(h, c));
     RET(enqueue_hyper(h, c, false));
     if (h->P > 0 && spatial) RET(enqueue_hyper(h, c, true));
+    if (h->sum.open) RET(enqueue_summary(h));
     return BFMRI_OK;
   };
   const bool graph = h->opt.use_graph && !h->opt.profile && h->opt.debug_skip_block < 0 &&
@@ -1067,6 +1106,7 @@ bfmri_status bfmri_gibbs_sweep(bfmri_handle* h, int n_sweeps, uint64_t first_cou
   } else {
     for (int s = 0; s < n_sweeps; ++s) RET(one_sweep(first_counter + (uint64_t)s));
   }
+  if (h->sum.open) h->sum.n += n_sweeps;
   if (!info) {
     h->deferred = true;        // errors and counts are read by the next synchronising call
     return BFMRI_OK;
@@ -1152,7 +1192,8 @@ bfmri_status bfmri_gibbs_sweep_group(bfmri_handle* const* hs, int n, int n_sweep
     if (!h0->d_gtab || !h0->d_gtally) return fail(h0, BFMRI_ERR_OOM, "group table allocation failed");
     h0->g_cap = n;
   }
-  const bool pre = h0->opt.precond != BFMRI_PRECOND_NONE;   // multi-RHS: block-Jacobi
+  // voxel blocks and their factors (block-Jacobi, and SSOR's block diagonal)
+  const bool pre = h0->opt.precond != BFMRI_PRECOND_NONE;
   std::vector<MrhsRhsPtrs> tab(2 * (size_t)n);
   for (int c = 0; c < n; ++c) {
     bfmri_handle* h = hs[c];
@@ -1195,8 +1236,11 @@ bfmri_status bfmri_gibbs_sweep_group(bfmri_handle* const* hs, int n, int n_sweep
       st = enqueue_lambda(h, cnt);
       if (st == BFMRI_OK) st = enqueue_hyper(h, cnt, false);
       if (st == BFMRI_OK && spatial_A) st = enqueue_hyper(h, cnt, true);
+      if (st == BFMRI_OK && h->sum.open) st = enqueue_summary(h);
     }
   }
+  for (int c = 0; c < n; ++c)
+    if (hs[c]->sum.open) hs[c]->sum.n += n_sweeps;
   std::vector<int> exhausted((size_t)n, 0);
   for (int c = 0; c < n; ++c) {
     const bfmri_status sc = end_call(hs[c], nullptr, &exhausted[c]);
@@ -1222,6 +1266,278 @@ bfmri_status bfmri_gibbs_sweep_group(bfmri_handle* const* hs, int n, int n_sweep
       if (code == 7) return fail(h0, BFMRI_ERR_INVALID_ARG, "non-finite value in PCG of " + who);
     }
   }
+  return BFMRI_OK;
+}
+
+namespace {
+
+// A captured sweep holds the launches it was captured with: opening or closing a summary
+// changes them, so the next sweep captures again.
+bfmri_status drop_sweep_graph(bfmri_handle* h) {
+  if (!h->sweep_exec && !h->sweep_graph) return BFMRI_OK;
+  CU(h, cudaStreamSynchronize(h->stream));
+  if (h->sweep_exec) cudaGraphExecDestroy(h->sweep_exec);
+  if (h->sweep_graph) cudaGraphDestroy(h->sweep_graph);
+  h->sweep_exec = nullptr;
+  h->sweep_graph = nullptr;
+  return BFMRI_OK;
+}
+
+void free_summary(bfmri_handle* h) {
+  auto& m = h->sum;
+  for (void* p : {(void*)m.ref, (void*)m.S1, (void*)m.S2, (void*)m.C, (void*)m.gamma, (void*)m.mean,
+                  (void*)m.cov, (void*)m.ppm, (void*)m.count, (void*)m.in_set, (void*)m.joint,
+                  (void*)m.scratch})
+    dfree(h, p);
+  m = bfmri_handle::Summary{};
+}
+
+bool contrasts_ok(int nc, int K, const double* C, const double* gamma) {
+  if (nc < 0 || nc > MAX_CONTRASTS) return false;
+  if (nc == 0) return true;
+  if (!C || !gamma) return false;
+  for (int i = 0; i < nc * K; ++i)
+    if (!std::isfinite(C[i])) return false;
+  for (int i = 0; i < nc; ++i)
+    if (std::isnan(gamma[i])) return false;
+  return true;
+}
+
+}  // namespace
+
+bfmri_status bfmri_summary_begin(bfmri_handle* h, int n_contrasts, const double* C,
+                                 const double* gamma, const int* joint_set, int n_joint) {
+  if (!h) return BFMRI_ERR_INVALID_ARG;
+  const int K = h->K, nc = n_contrasts;
+  if (!contrasts_ok(nc, K, C, gamma))
+    return fail(h, BFMRI_ERR_INVALID_ARG, "contrasts: 0 <= n_contrasts <= 16, finite C, gamma not NaN");
+  if (n_joint < 0 || (n_joint > 0 && !joint_set))
+    return fail(h, BFMRI_ERR_INVALID_ARG, "joint set: n_joint < 0 or joint_set missing");
+  for (int i = 0; i < n_joint; ++i)
+    if (joint_set[i] < 0 || joint_set[i] >= h->N)
+      return fail(h, BFMRI_ERR_INVALID_ARG, "joint set: voxel index out of range");
+  RET(drop_sweep_graph(h));
+  CU(h, cudaStreamSynchronize(h->stream));
+  free_summary(h);
+  const size_t ld = h->ld;
+  auto& m = h->sum;
+  const int ncs = std::max(nc, 1);
+  m.ref = (double*)dalloc(h, (size_t)K * ld * sizeof(double));
+  m.S1 = (double*)dalloc(h, (size_t)K * ld * sizeof(double));
+  m.S2 = (double*)dalloc(h, (size_t)ntri(K) * ld * sizeof(double));
+  m.mean = (double*)dalloc(h, (size_t)K * ld * sizeof(double));
+  m.cov = (double*)dalloc(h, (size_t)ntri(K) * ld * sizeof(double));
+  m.ppm = (double*)dalloc(h, (size_t)ncs * ld * sizeof(double));
+  m.count = (int*)dalloc(h, (size_t)ncs * ld * sizeof(int));
+  m.C = (double*)dalloc(h, (size_t)ncs * K * sizeof(double));
+  m.gamma = (double*)dalloc(h, (size_t)ncs * sizeof(double));
+  m.in_set = (uint8_t*)dalloc(h, ld);
+  m.joint = (unsigned long long*)dalloc(h, (size_t)ncs * sizeof(unsigned long long));
+  m.scratch = (unsigned int*)dalloc(h, 2 * sizeof(unsigned int));
+  if (!m.ref || !m.S1 || !m.S2 || !m.mean || !m.cov || !m.ppm || !m.count || !m.C || !m.gamma ||
+      !m.in_set || !m.joint || !m.scratch) {
+    free_summary(h);
+    return fail(h, BFMRI_ERR_OOM, "summary allocation failed");
+  }
+  cudaStream_t st = h->stream;
+  CU(h, cudaMemcpyAsync(m.ref, h->d_W, (size_t)K * ld * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  CU(h, cudaMemsetAsync(m.S1, 0, (size_t)K * ld * sizeof(double), st));
+  CU(h, cudaMemsetAsync(m.S2, 0, (size_t)ntri(K) * ld * sizeof(double), st));
+  CU(h, cudaMemsetAsync(m.count, 0, (size_t)ncs * ld * sizeof(int), st));
+  CU(h, cudaMemsetAsync(m.joint, 0, (size_t)ncs * sizeof(unsigned long long), st));
+  CU(h, cudaMemsetAsync(m.scratch, 0, 2 * sizeof(unsigned int), st));
+  std::vector<uint8_t> flags(ld, 0);
+  for (int i = 0; i < n_joint; ++i) flags[(size_t)joint_set[i]] = 1;
+  CU(h, cudaMemcpyAsync(m.in_set, flags.data(), ld, cudaMemcpyHostToDevice, st));
+  if (nc > 0) {
+    CU(h, cudaMemcpyAsync(m.C, C, (size_t)nc * K * sizeof(double), cudaMemcpyHostToDevice, st));
+    CU(h, cudaMemcpyAsync(m.gamma, gamma, (size_t)nc * sizeof(double), cudaMemcpyHostToDevice, st));
+  }
+  CU(h, cudaStreamSynchronize(st));
+  m.nc = nc;
+  m.has_set = n_joint > 0;
+  m.n = 0;
+  m.open = true;
+  return BFMRI_OK;
+}
+
+bfmri_status bfmri_summary_add(bfmri_handle* h) {
+  if (!h) return BFMRI_ERR_INVALID_ARG;
+  if (!h->sum.open) return fail(h, BFMRI_ERR_STATE, "no summary is open (bfmri_summary_begin)");
+  RET(enqueue_summary(h));
+  h->sum.n += 1;
+  return BFMRI_OK;
+}
+
+bfmri_status bfmri_summary_get(bfmri_handle* h, long long* n_samples, double* mean, double* cov,
+                               double* ppm, long long* joint_count) {
+  if (!h) return BFMRI_ERR_INVALID_ARG;
+  auto& m = h->sum;
+  if (!m.open) return fail(h, BFMRI_ERR_STATE, "no summary is open (bfmri_summary_begin)");
+  RET(end_call(h, nullptr, nullptr));   // waits; reports errors of asynchronous sweeps
+  if (n_samples) *n_samples = m.n;
+  if (m.n <= 0) {
+    if (mean || cov || ppm || joint_count)
+      return fail(h, BFMRI_ERR_STATE, "the summary holds no sample yet");
+    return BFMRI_OK;
+  }
+  ChainFinalArgs a;
+  a.g = geom(h);
+  a.K = h->K;
+  a.nc = m.nc;
+  a.n = m.n;
+  a.ref = m.ref;
+  a.S1 = m.S1;
+  a.S2 = m.S2;
+  a.count = m.count;
+  a.mean = m.mean;
+  a.cov = m.cov;
+  a.ppm = m.ppm;
+  {
+    Timed tm(h, BFMRI_T_SUMMARY);
+    const cudaError_t e = launch_chain_finalize(a, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "chain summary finalize");
+  }
+  if (mean) RET(to_host(h, mean, m.mean, h->K));
+  if (cov) RET(to_host(h, cov, m.cov, ntri(h->K)));
+  if (ppm) RET(to_host(h, ppm, m.ppm, m.nc));
+  if (joint_count && m.nc > 0) {
+    std::vector<unsigned long long> j((size_t)m.nc);
+    CU(h, cudaMemcpyAsync(j.data(), m.joint, j.size() * sizeof(unsigned long long),
+                          cudaMemcpyDeviceToHost, h->stream));
+    CU(h, cudaStreamSynchronize(h->stream));
+    for (int c = 0; c < m.nc; ++c) joint_count[c] = (long long)j[(size_t)c];
+  }
+  CU(h, cudaStreamSynchronize(h->stream));
+  return BFMRI_OK;
+}
+
+bfmri_status bfmri_summary_end(bfmri_handle* h) {
+  if (!h) return BFMRI_ERR_INVALID_ARG;
+  if (!h->sum.open) return BFMRI_OK;
+  RET(drop_sweep_graph(h));
+  CU(h, cudaStreamSynchronize(h->stream));
+  free_summary(h);
+  return BFMRI_OK;
+}
+
+bfmri_status bfmri_svb_summary(bfmri_handle* h, int n_contrasts, const double* C,
+                               const double* gamma, double* mean, double* cov, double* ppm) {
+  if (!h) return BFMRI_ERR_INVALID_ARG;
+  if (h->svb_S <= 0) return fail(h, BFMRI_ERR_STATE, "no SVB samples (bfmri_spvb_step)");
+  if (!contrasts_ok(n_contrasts, h->K, C, gamma))
+    return fail(h, BFMRI_ERR_INVALID_ARG, "contrasts: 0 <= n_contrasts <= 16, finite C, gamma not NaN");
+  const size_t ld = h->ld;
+  const int K = h->K, nc = n_contrasts, ncs = std::max(nc, 1);
+  // work planes: mean, packed covariance, PPMs, then the contrasts (freed on return)
+  const size_t doubles = ((size_t)K + ntri(K) + ncs) * ld + (size_t)ncs * (K + 1);
+  double* work = (double*)dalloc(h, doubles * sizeof(double));
+  if (!work) return fail(h, BFMRI_ERR_OOM, "SVB summary allocation failed");
+  double* d_mean = work;
+  double* d_cov = d_mean + (size_t)K * ld;
+  double* d_ppm = d_cov + (size_t)ntri(K) * ld;
+  double* d_C = d_ppm + (size_t)ncs * ld;
+  double* d_g = d_C + (size_t)ncs * K;
+  bfmri_status st = BFMRI_OK;
+  auto body = [&]() -> bfmri_status {
+    RET(begin_call(h));
+    if (nc > 0) {
+      CU(h, cudaMemcpyAsync(d_C, C, (size_t)nc * K * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+      CU(h, cudaMemcpyAsync(d_g, gamma, (size_t)nc * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    }
+    SvbSumArgs a;
+    a.g = geom(h);
+    a.K = K;
+    a.S = h->svb_S;
+    a.nc = nc;
+    a.Ws = h->svb_W;
+    a.C = d_C;
+    a.gamma = d_g;
+    a.mean = d_mean;
+    a.cov = d_cov;
+    a.ppm = d_ppm;
+    {
+      Timed tm(h, BFMRI_T_SUMMARY);
+      const cudaError_t e = launch_svb_summary(a, h->stream);
+      if (e != cudaSuccess) return cuda_fail(h, e, "SVB summary");
+    }
+    RET(end_call(h, nullptr, nullptr));
+    if (mean) RET(to_host(h, mean, d_mean, K));
+    if (cov) RET(to_host(h, cov, d_cov, ntri(K)));
+    if (ppm) RET(to_host(h, ppm, d_ppm, nc));
+    return BFMRI_OK;
+  };
+  st = body();
+  cudaStreamSynchronize(h->stream);
+  dfree(h, work);
+  return st;
+}
+
+bfmri_status bfmri_log_joint(bfmri_handle* h, double* terms) {
+  RET(require_stats(h));
+  if (!terms) return fail(h, BFMRI_ERR_INVALID_ARG, "terms is NULL");
+  const int K = h->K, P = h->P;
+  const int grid = log_joint_grid(h->N);
+  if (!h->d_lj) {
+    h->d_lj = (double*)dalloc(h, (7 + (size_t)K + (size_t)P + 2 * (size_t)grid) * sizeof(double));
+    if (!h->d_lj) return fail(h, BFMRI_ERR_OOM, "log joint allocation failed");
+  }
+  double* d_terms = h->d_lj;
+  double* d_Qw = d_terms + 7;
+  double* d_Qa = d_Qw + K;
+  double* d_part = d_Qa + P;
+  const bool spatial = P > 0 && h->opt.ar_prior == BFMRI_AR_SPATIAL;
+  RET(begin_call(h));
+  {
+    Timed tm(h, BFMRI_T_SUMMARY);
+    // quadratic forms W_k D_w W_k' and A_p D_a A_p' (the Gamma draws are skipped: out = null)
+    HyperArgs q;
+    q.g = geom(h);
+    q.part = h->d_hpart;
+    q.prior1 = q.prior2 = 0.0;
+    q.out = nullptr;
+    q.rng = rng_of(h, 0, TAG_ALPHA);
+    q.exhausted = h->d_flags + 1;
+    q.D = K;
+    q.V = h->d_W;
+    q.Q_out = d_Qw;
+    cudaError_t e = launch_hyper(q, h->stream);
+    if (e == cudaSuccess && spatial) {
+      q.D = P;
+      q.V = h->d_A;
+      q.Q_out = d_Qa;
+      e = launch_hyper(q, h->stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "log joint quadratic forms");
+    LogJointArgs a;
+    a.g = geom(h);
+    a.K = K;
+    a.P = P;
+    a.T = h->T;
+    a.spatial = spatial ? 1 : 0;
+    a.stats = h->d_stats;
+    a.Sxx = h->d_Sxx;
+    a.W = h->d_W;
+    a.A = h->d_A;
+    a.lam = h->d_lam;
+    a.alpha = h->d_alpha;
+    a.beta = h->d_beta;
+    a.Qw = d_Qw;
+    a.Qa = d_Qa;
+    a.u1 = h->opt.u1;
+    a.u2 = h->opt.u2;
+    a.q1 = h->opt.q1;
+    a.q2 = h->opt.q2;
+    a.r1 = h->opt.r1;
+    a.r2 = h->opt.r2;
+    a.part = d_part;
+    a.terms = d_terms;
+    e = launch_log_joint(a, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "log joint");
+  }
+  RET(end_call(h, nullptr, nullptr));
+  CU(h, cudaMemcpyAsync(terms, d_terms, 7 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CU(h, cudaStreamSynchronize(h->stream));
   return BFMRI_OK;
 }
 

@@ -377,16 +377,25 @@ __global__ void __launch_bounds__(HYPER_THREADS) k_quadform(HyperArgs a) {
 #pragma unroll
   for (int k = 0; k < D; ++k) acc[k] = 0.0;
   const size_t ld = a.g.ld;
+  const int nfwd = a.g.ndir / 2;
   for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < a.g.N; n += gridDim.x * blockDim.x) {
-    double v[D];
+    // the forward neighbours' indices, then all their values, in two rounds of loads
+    int m[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) m[d] = d < nfwd ? __ldg(a.g.nbr + (size_t)(2 * d + 1) * ld + n) : -1;
+    double v[D], vn[3][D];
 #pragma unroll
     for (int k = 0; k < D; ++k) v[k] = a.V[(size_t)k * ld + n];
-    for (int d = 0; d < a.g.ndir / 2; ++d) {
-      const int m = __ldg(a.g.nbr + (size_t)(2 * d + 1) * ld + n);
-      if (m >= 0) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+      for (int k = 0; k < D; ++k) vn[d][k] = a.V[(size_t)k * ld + (m[d] >= 0 ? m[d] : n)];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      if (m[d] >= 0) {
 #pragma unroll
         for (int k = 0; k < D; ++k) {
-          const double df = v[k] - a.V[(size_t)k * ld + m];
+          const double df = v[k] - vn[d][k];
           acc[k] += df * df;
         }
       }
@@ -407,12 +416,18 @@ __global__ void __launch_bounds__(HYPER_THREADS) k_quadform(HyperArgs a) {
   }
 }
 
+// One warp per dimension k: the lanes add the CTA partials b = lane, lane + 32, ... and a
+// butterfly combines them (a fixed order, so Q does not depend on timing).
 __global__ void k_hyper_draw(HyperArgs a, int nblocks) {
-  const int k = threadIdx.x;
+  const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (k >= a.D) return;
   double Q = 0.0;
-  for (int b = 0; b < nblocks; ++b) Q += a.part[(size_t)b * a.D + k];
+  for (int b = lane; b < nblocks; b += 32) Q += a.part[(size_t)b * a.D + k];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) Q += __shfl_xor_sync(0xffffffffu, Q, o);
+  if (lane != 0) return;
   if (a.Q_out) a.Q_out[k] = Q;
+  if (!a.out) return;   // quadratic forms only
   const double scale = 1.0 / (0.5 * Q + 1.0 / a.prior1);
   const double shape = 0.5 * (double)a.g.N + a.prior2;
   int ex = 0;
@@ -640,7 +655,7 @@ template <int D>
 static cudaError_t hyper_d(const HyperArgs& a, cudaStream_t s) {
   const int grid = hyper_grid(a.g.N);
   k_quadform<D><<<grid, HYPER_THREADS, 0, s>>>(a);
-  k_hyper_draw<<<1, 32, 0, s>>>(a, grid);
+  k_hyper_draw<<<1, 32 * D, 0, s>>>(a, grid);
   return cudaGetLastError();
 }
 

@@ -239,7 +239,7 @@ struct HyperArgs {
   const double* V;      // [D][ld]
   double* part;         // [grid][D] partials (grid = hyper_grid(N))
   double prior1, prior2;
-  double* out;          // [D]
+  double* out;          // [D], or null: only the quadratic forms are written to Q_out
   double* Q_out;        // [D] (may be null)
   Rng rng;
   int* exhausted;

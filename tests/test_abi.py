@@ -81,3 +81,20 @@ def test_create_rejects_bad_arguments_without_touching_the_gpu(lib):
     with pytest.raises(bfmri.BfmriError) as ei:
         bfmri.bfmri_create((4, 3, 2, 6), mask, X, Yn, 2, 1, torch_memory=False)
     assert ei.value.status == -1 and "non-finite" in str(ei.value)
+
+
+def test_summary_bindings_marshal_without_a_gpu(lib):
+    """The summary and synchronisation bindings build their ctypes arguments and reach the
+    library, which rejects the NULL handle with INVALID_ARG before any device call."""
+    import numpy as np
+    from paper_1606_00980_gb300 import bfmri
+    m = object.__new__(bfmri.Model)
+    m.handle, m.lib, m.K, m.N, m.P, m._n_contrasts = None, lib, 3, 10, 1, 2
+    calls = [lambda: m.summary_begin(np.ones((2, 3)), [0.1, 0.2], joint_set=[1, 2]),
+             lambda: m.summary_begin(np.ones(3), 0.5),
+             m.summary_add, m.summary_get, m.summary_end, m.log_joint, m.synchronize,
+             lambda: m.svb_summary(np.ones((2, 3)), [0.1, 0.2])]
+    for call in calls:
+        with pytest.raises(bfmri.BfmriError) as ei:
+            call()
+        assert ei.value.status == -1
