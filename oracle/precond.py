@@ -111,3 +111,41 @@ def ssor_apply_sweeps(lat: Lattice, blocks, scale, v_nk, omega=1.0):
     for n in reversed(order):
         relax(n)
     return z
+
+
+def schur_system(lat: Lattice, blocks, scale, b_nk):
+    """The red-black reduced system. Eliminating the red voxels from B~ x = b (their rows
+    read Dg_r x_r + U x_b = b_r, with Dg_r block diagonal) leaves for the black voxels
+        S x_b = b^_b,   S = Dg_b - L Dg_r^-1 U,   b^_b = b_b - L Dg_r^-1 b_r,
+    after which x_r = Dg_r^-1 (b_r - U x_b). Returns (S, b^_b, recover, n_red) with S and
+    b^ in the red-black order restricted to the black block and recover(x_b) -> x as
+    (N, D) voxel rows."""
+    N, D, _ = blocks.shape
+    order, Dg, L, U = split(lat, blocks, scale)
+    nr = int((colours(lat) == 0).sum()) * D
+    Dg = Dg.tocsr()
+    Dr = Dg[:nr, :nr].tocsc()
+    Db = Dg[nr:, nr:]
+    Lbr = L.tocsr()[nr:, :nr]
+    Urb = U.tocsr()[:nr, nr:]
+    b = model.kmajor(np.asarray(b_nk, dtype=float))[order]
+    br, bb = b[:nr], b[nr:]
+    DrinvU = spla.spsolve(Dr, Urb.tocsc())
+    DrinvU = sp.csr_matrix(DrinvU) if not sp.issparse(DrinvU) else DrinvU.tocsr()
+    S = (Db - Lbr @ DrinvU).tocsr()
+    bhat = bb - Lbr @ spla.spsolve(Dr, br)
+
+    def recover(xb):
+        xr = spla.spsolve(Dr, br - Urb @ xb)
+        out = np.empty(N * D)
+        out[order] = np.concatenate([xr, xb])
+        return model.from_kmajor(out, D).T.copy()
+
+    return S, bhat, recover, nr
+
+
+def schur_solve(lat: Lattice, blocks, scale, b_nk):
+    """x = B~^-1 b through the reduced system: exact sparse solve of S x_b = b^_b, then the
+    red voxels from their own rows."""
+    S, bhat, recover, _ = schur_system(lat, blocks, scale, b_nk)
+    return recover(spla.spsolve(S.tocsc(), bhat))

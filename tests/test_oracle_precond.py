@@ -70,3 +70,32 @@ def test_every_edge_joins_two_colours(neighbourhood):
     E = lat.edges()
     assert np.all(c[E[:, 0]] != c[E[:, 1]])
     assert 0 < c.sum() < lat.N
+
+
+def test_schur_solve_equals_the_direct_solve():
+    """Block elimination of the red voxels is exact: the reduced solve reproduces the
+    direct sparse solve of B~ x = b."""
+    import scipy.sparse.linalg as spla
+    for nb, K in [(6, 3), (4, 2)]:
+        lat, blocks, scale, b = small_problem(5 + nb, D=K, neighbourhood=nb)
+        x = precond.schur_solve(lat, blocks, scale, b)
+        B = model.precision(lat, blocks, scale).tocsc()
+        xd = model.from_kmajor(spla.spsolve(B, model.kmajor(b)), K).T
+        assert np.linalg.norm(x - xd) <= 1e-12 * np.linalg.norm(xd)
+
+
+def test_ssor_omega1_spectrum_is_one_and_the_reduced_spectrum():
+    """With red-black ordering and omega = 1, M^-1 B~ has the eigenvalue 1 once per red
+    unknown and otherwise the eigenvalues of Dg_b^-1 S: PCG with symmetric Gauss-Seidel is
+    CG on the reduced system preconditioned by its block diagonal (same Krylov spaces, so
+    the same iteration counts up to the red component of the start residual)."""
+    lat, blocks, scale, _ = small_problem(9, D=2, neighbourhood=6)
+    M = precond.ssor_matrix(lat, blocks, scale, omega=1.0)
+    B = model.precision(lat, blocks, scale).toarray()
+    ev = np.sort(np.linalg.eigvals(np.linalg.solve(M, B)).real)
+    S, _, _, nr = precond.schur_system(lat, blocks, scale, np.zeros((lat.N, 2)))
+    order, Dg, _, _ = precond.split(lat, blocks, scale)
+    Db = Dg.toarray()[nr:, nr:]
+    evs = np.linalg.eigvals(np.linalg.solve(Db, S.toarray())).real
+    want = np.sort(np.concatenate([np.ones(nr), evs]))
+    assert np.allclose(ev, want, rtol=0, atol=1e-10)
