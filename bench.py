@@ -40,7 +40,7 @@ if ROOT not in sys.path:
 METRIC = "posterior W-draws/s + HBM-roofline fraction, 3D K=6; p50/p99 batched solve"
 UNIT = "W-draws/s"
 def workload_name(args):
-    pc = "ssor" if getattr(args, "precond", "ssor") == "ssor" else "blockjacobi"
+    pc = {"reduced": "rbreduced", "ssor": "ssor", "bj": "blockjacobi"}[getattr(args, "precond", "reduced")]
     return f"wholebrain3d_64x64x33_ellipsoid_N49928_T300_K6_AR3_fp64_{pc}_delta1e-8"
 
 
@@ -57,14 +57,19 @@ def peaks():
 FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12
 
 
-def pcg_flops_per_voxel_iter(K, ssor=False):
+def pcg_flops_per_voxel_iter(K, mode="bj"):
     """FP64 flops of one Chronopoulos-Gear PCG iteration per voxel: four axpys (p, s, x, r)
     8K, block-Jacobi triangular solves 2K^2 + 2K, block product 2K^2, stencil with up to six
-    neighbours 6K + 3K, three inner products 6K. Red-black SSOR adds the omega scaling K and
-    its two colour phases, each over half of the voxels: neighbour sum 6K, right-hand side
-    2K (black) or K (red), triangular solves 2K^2, update K (black) or 3K (red)."""
+    neighbours 6K + 3K, three inner products 6K. Red-black SSOR ("ssor") adds the omega
+    scaling K and its two colour phases, each over half of the voxels: neighbour sum 6K,
+    right-hand side 2K (black) or K (red), triangular solves 2K^2, update K (black) or 3K
+    (red). The reduced red-black system ("reduced") works per pair of voxels: the black
+    voxel's axpys 8K, triangular solves 2K^2, block product 2K^2, stencil 9K and inner
+    products 6K, the red voxel's neighbour sum and scaling 7K and triangular solves 2K^2."""
     base = 4 * K * K + 25 * K
-    if not ssor:
+    if mode == "reduced":
+        return (6 * K * K + 30 * K) / 2
+    if mode != "ssor":
         return base
     return base + K + ((6 * K + 2 * K + 2 * K * K + K) + (6 * K + K + 2 * K * K + 3 * K)) / 2
 
@@ -78,12 +83,14 @@ def pcg_bytes_per_voxel_iter(K, w=8):
 # DRAM bytes (read + write) of one W-solve launch of the current resident SSOR solver on the
 # whole-brain workload, from one ncu capture of this kernel version (22.99 MB + 0.63 MB): the
 # first touch of the staged blocks, factors, b and x; the iterations run from L2.
-NCU_TRAFFIC_W_SSOR = 23.62e6
+NCU_TRAFFIC_W = {"ssor": 23.62e6}
 
 
 def precond_options(args):
     """Options of the headline FP64 chain's preconditioner (--precond)."""
     from paper_1606_00980_gb300 import bfmri
+    if args.precond == "reduced":
+        return {"precond": bfmri.PRECOND_RB_REDUCED}
     if args.precond == "ssor":
         return {"precond": bfmri.PRECOND_SSOR, "ssor_omega": 1.0}
     return {"precond": bfmri.PRECOND_BLOCK_JACOBI}
@@ -314,9 +321,8 @@ def run_ours(args, world, rank, local):
     launches = max(pw["launches"], 1)
     dur_s = pw["ms"] / 1e3 / launches
     iters_per_launch = it_w / launches
-    ssor = args.precond == "ssor"
-    flops = N * (iters_per_launch * pcg_flops_per_voxel_iter(K, ssor) +
-                 2 * pcg_flops_per_voxel_iter(K, ssor))
+    flops = N * (iters_per_launch * pcg_flops_per_voxel_iter(K, args.precond) +
+                 2 * pcg_flops_per_voxel_iter(K, args.precond))
     bytes_ = N * iters_per_launch * pcg_bytes_per_voxel_iter(K)
     hbm_peak, hbm_src, _ = peaks()
     achieved_tf = flops / dur_s / 1e12
@@ -339,10 +345,13 @@ def run_ours(args, world, rank, local):
     # kernels per timed launch group: edge terms + assembly (W, A), quadratic form + draw (hyper)
     per_group = {"assemble_W": 2, "assemble_A": 2, "hyper": 2}
     n_launch = sum(v["launches"] * per_group.get(k, 1) for k, v in tim_p.items()) / n_prof * args.steps
-    roof = {"kernel": f"k_pcg_res<{K}> (W solve, {'SSOR' if ssor else 'block-Jacobi'})",
+    kname = {"reduced": f"k_pcg_rb<{K}> (W solve, red-black reduced system)",
+             "ssor": f"k_pcg_res<{K}> (W solve, SSOR)",
+             "bj": f"k_pcg_res<{K}> (W solve, block-Jacobi)"}[args.precond]
+    roof = {"kernel": kname,
             "bound": "alu", "achieved": achieved_tf,
             "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved_tf / FP64_PEAK_TFLOPS,
-            "traffic": NCU_TRAFFIC_W_SSOR if ssor else None,
+            "traffic": NCU_TRAFFIC_W.get(args.precond),
             "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2070 MHz",
             "hbm_view": {"achieved_gbs": achieved_gbs, "peak_gbs": hbm_peak,
                          "frac": achieved_gbs / hbm_peak, "peak_source": f"{hbm_src} (MEASURED_PEAKS.json)"},
@@ -547,6 +556,7 @@ def run_precond_compare(args, w, n_draws=10):
              ("block_jacobi_streaming", dict(precond=bfmri.PRECOND_BLOCK_JACOBI,
                                              pcg_variant=bfmri.PCG_STREAMING)),
              ("ssor_omega1.0_resident", dict(precond=bfmri.PRECOND_SSOR, ssor_omega=1.0)),
+             ("rb_reduced_resident", dict(precond=bfmri.PRECOND_RB_REDUCED)),
              ("ssor_omega1.0_streaming", dict(precond=bfmri.PRECOND_SSOR, ssor_omega=1.0,
                                               pcg_variant=bfmri.PCG_STREAMING)),
              ("ssor_omega1.2_resident", dict(precond=bfmri.PRECOND_SSOR, ssor_omega=1.2)),
@@ -615,7 +625,7 @@ def run_batched_chains(args, w, n_chains=8, sweeps=3):
     it_w = sum(i.pcg_iterations_W for i in infos)
     K = w.K
     F = K * (K + 1) // 2
-    ssor = args.precond == "ssor"
+    ssor = args.precond in ("ssor", "reduced")   # the multi-RHS solver runs SSOR phases
     bytes_w = it_w * w.N * 8 * (13 * K + 2 * F + ((4 * K + F) if ssor else 0))
     solve_s = tim["pcg_W"]["ms"] / 1e3
     hbm_peak, hbm_src, _ = peaks()
@@ -817,7 +827,7 @@ def main():
     ap.add_argument("--no-precond", action="store_true")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--no-summaries", action="store_true")
-    ap.add_argument("--precond", choices=["ssor", "bj"], default="ssor",
+    ap.add_argument("--precond", choices=["reduced", "ssor", "bj"], default="reduced",
                     help="preconditioner of the headline chain and of its mixed-precision twin "
                          "(the multi-RHS solves use block-Jacobi)")
     ap.add_argument("--only-batched", action="store_true",

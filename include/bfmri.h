@@ -64,6 +64,12 @@ typedef struct {
                                          solves (FP64, and the FP32 inner iterations of mixed),
                                          SVB samples and grouped chains; the log-det / trace
                                          probes always use block-Jacobi */
+#define BFMRI_PRECOND_RB_REDUCED   3  /* the FP64 resident solver runs CG on the red-black
+                                         reduced system (the black voxels' Schur complement
+                                         S = Dg_b - L Dg_r^-1 U, preconditioned by Dg_b),
+                                         which takes the iterates of SSOR with omega = 1 at
+                                         fewer barriers and block solves per iteration;
+                                         every other solver uses SSOR with omega = 1 */
 
 #define BFMRI_PREC_FP64  0  /* FP64 PCG */
 #define BFMRI_PREC_MIXED 1  /* FP32 inner PCG inside an FP64 iterative-refinement loop */

@@ -264,6 +264,15 @@ bool all_positive(const double* v, size_t n) {
   return true;
 }
 
+// Solvers that run the SSOR colour phases: SSOR itself, and the reduced red-black system
+// wherever its own solver does not apply (there it is SSOR with omega = 1).
+bool uses_ssor(const bfmri_options& o) {
+  return o.precond == BFMRI_PRECOND_SSOR || o.precond == BFMRI_PRECOND_RB_REDUCED;
+}
+double ssor_omega_of(const bfmri_options& o) {
+  return o.precond == BFMRI_PRECOND_RB_REDUCED ? 1.0 : o.ssor_omega;
+}
+
 // Clears the sticky device error words before a group of launches (kept, and added to,
 // while the errors of asynchronous sweeps are unread).
 bfmri_status begin_call(bfmri_handle* h) {
@@ -332,8 +341,9 @@ bfmri_status run_pcg(bfmri_handle* h, int D, const double* scale, double* x, int
   a.mixed = h->opt.precision == BFMRI_PREC_MIXED;
   a.blocks32 = h->d_blocks32;
   a.mfac32 = h->opt.precond != BFMRI_PRECOND_NONE ? h->d_mfac32 : nullptr;
-  a.ssor = h->opt.precond == BFMRI_PRECOND_SSOR;
-  a.omega = h->opt.ssor_omega;
+  a.ssor = uses_ssor(h->opt);
+  a.omega = ssor_omega_of(h->opt);
+  a.reduced = h->opt.precond == BFMRI_PRECOND_RB_REDUCED;
   a.red = h->d_red;
   a.n_red = h->n_red;
   a.black = h->d_black;
@@ -607,8 +617,8 @@ MrhsArgs mrhs_args(bfmri_handle* h, int D, int S, const double* scale, int max_i
 // Red-black SSOR for the plain multi-RHS solves (SVB samples, grouped chains) when the handle
 // asks for it; the probe solves keep block-Jacobi.
 void mrhs_ssor(const bfmri_handle* h, MrhsArgs& m) {
-  m.ssor = h->opt.precond == BFMRI_PRECOND_SSOR;
-  m.omega = h->opt.ssor_omega;
+  m.ssor = uses_ssor(h->opt);
+  m.omega = ssor_omega_of(h->opt);
   m.red = h->d_red;
   m.n_red = h->n_red;
   m.black = h->d_black;
@@ -704,7 +714,7 @@ bfmri_status bfmri_create(const bfmri_lattice* lat, const uint8_t* mask, const d
   if (o.pcg_variant != BFMRI_PCG_AUTO && o.pcg_variant != BFMRI_PCG_STREAMING)
     return fail(nullptr, BFMRI_ERR_INVALID_ARG, "unknown pcg_variant");
   if (o.precond != BFMRI_PRECOND_NONE && o.precond != BFMRI_PRECOND_BLOCK_JACOBI &&
-      o.precond != BFMRI_PRECOND_SSOR)
+      o.precond != BFMRI_PRECOND_SSOR && o.precond != BFMRI_PRECOND_RB_REDUCED)
     return fail(nullptr, BFMRI_ERR_INVALID_ARG, "unknown preconditioner");
   if (o.precond == BFMRI_PRECOND_SSOR && !(o.ssor_omega > 0.0 && o.ssor_omega < 2.0))
     return fail(nullptr, BFMRI_ERR_INVALID_ARG, "ssor_omega must be in (0, 2)");
@@ -1977,8 +1987,8 @@ bfmri_status bfmri_apply_preconditioner(bfmri_handle* h, int which, const double
   }
   p.r = h->d_r;
   p.u = h->d_z;
-  p.ssor = h->opt.precond == BFMRI_PRECOND_SSOR;
-  p.omega = h->opt.ssor_omega;
+  p.ssor = uses_ssor(h->opt);
+  p.omega = ssor_omega_of(h->opt);
   p.red = h->d_red;
   p.n_red = h->n_red;
   p.black = h->d_black;

@@ -28,6 +28,9 @@ namespace bfmri {
 namespace {
 
 constexpr int RES_MAX_THREADS = 384;
+// The reduced-system kernel keeps one more vector per voxel (b^): at most 352 threads, so
+// that it may take 184 registers a thread (N <= 152 x 352 voxels on one GB300)
+constexpr int RB_MAX_THREADS = 352;
 constexpr int RES_MAX_D = 8;
 
 __device__ __forceinline__ double ldx(const double* p) { return __ldcg(p); }
@@ -454,6 +457,277 @@ __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_res(PcgArgs a) {
       continue;
     }
   }
+  if (own) {
+#pragma unroll
+    for (int k = 0; k < D; ++k) a.x[(size_t)k * ld + n] = x[k];
+  }
+  write_ctrl(a, it, restarts, rr, bb, rel0, status);
+}
+
+// ---------------------------------------------------------------------------------------
+// Resident variant on the red-black reduced system. Eliminating the red voxels from
+// B~ x = b (their rows read Dg_r x_r - scale .* sum of the black neighbours' x = b_r) leaves
+// for the black voxels
+//   S x_b = b^,   S = Dg_b - L Dg_r^-1 U,   b^ = b_b + scale .* sum_red nbrs Dg_r^-1 b_r,
+// and afterwards x_r = Dg_r^-1 (b_r + scale .* sum of the black neighbours' x_b) (L, U:
+// the couplings -scale between red and black neighbours; Dg: the voxel blocks
+// B_n + diag(scale) deg_n with factor mfac). CG on S preconditioned by Dg_b takes the
+// iterates of CG on B~ preconditioned by red-black symmetric Gauss-Seidel (SSOR with
+// omega = 1): the two preconditioned operators share their spectrum apart from the
+// eigenvalue 1 of the red unknowns. The residual of B~ at the recovered x equals the
+// reduced residual (zero on the red rows), so the stop rule is unchanged; it is confirmed
+// on B~ itself in FP64.
+// One product with S is a red phase, y_r = Dg_r^-1 (scale .* sum of the black neighbours'
+// u), and a black phase, w_b = Dg_b u_b - scale .* sum of the red neighbours' y; one plane
+// array (a.u) carries u at the black voxels and y at the red ones. An iteration is the
+// local update of the black voxels, two plain barriers and the reducing one (the SSOR form
+// has four), and per pair of voxels three block solves and one block product (the SSOR
+// form: four and two).
+// ---------------------------------------------------------------------------------------
+template <int D>
+__global__ void __launch_bounds__(RB_MAX_THREADS, 1) k_pcg_rb(PcgArgs a) {
+  extern __shared__ double smem[];
+  __shared__ Shared sh;
+  constexpr int NT = ntri(D);
+  const int bd = blockDim.x, t = threadIdx.x;
+  double* shB = smem;
+  double* shM = smem + NT * bd;
+  double* shH = smem + 2 * NT * bd;   // b^ (read at restarts only): shared, not registers
+  int n = blockIdx.x * a.res_per + t;
+  bool own = t < a.res_per && n < a.N;
+  bool is_red = true;
+  colour_sort(a, n, own, is_red);
+  const bool red = own && is_red, black = own && !is_red;
+  const size_t ld = a.ld;
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int j = 0; j <= i; ++j) {
+      const int e = tri(i, j);
+      shB[e * bd + t] = own ? __ldg(a.blocks + (size_t)e * ld + n) : (i == j ? 1.0 : 0.0);
+      shM[e * bd + t] = own ? __ldg(a.mfac + (size_t)e * ld + n) : (i == j ? 1.0 : 0.0);
+    }
+  int nb[6];
+#pragma unroll
+  for (int d = 0; d < 6; ++d) nb[d] = (own && d < a.ndir) ? __ldg(a.nbr + (size_t)d * ld + n) : -1;
+  const double degd = degree_of<double>(nb, a.ndir);
+  // b is read from memory where it is needed (start, red recovery, true residual): the
+  // black voxels' registers hold b^ instead
+  // the prior scale is the same for every voxel: one shared copy instead of D registers
+  __shared__ double s[RES_MAX_D];
+  if (t < D) s[t] = __ldg(a.scale + t);
+  __syncthreads();
+  double x[D], r[D], u[D], w[D], p[D], q[D];
+  auto load_b = [&](double* bv) {
+#pragma unroll
+    for (int k = 0; k < D; ++k) bv[k] = own ? __ldg(a.b + (size_t)k * ld + n) : 0.0;
+  };
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    x[k] = own ? a.x[(size_t)k * ld + n] : 0.0;
+    shH[k * bd + t] = 0.0;
+    r[k] = 0.0;
+    u[k] = 0.0;
+    w[k] = 0.0;
+    p[k] = 0.0;
+    q[k] = 0.0;
+  }
+  const double* Bp = shB + t;
+  const double* Mp = shM + t;
+  double* U = a.u;
+  auto bar = [&]() -> bool {
+    if (a.skip_block == (int)blockIdx.x) return false;
+    return grid_sync(a.bar, &sh.flag);
+  };
+  auto publish = [&](const double* v) {
+#pragma unroll
+    for (int k = 0; k < D; ++k) U[(size_t)k * ld + n] = v[k];
+  };
+  // red voxel: out = Dg^-1 (c + scale .* sum of the neighbours' U), c = 0 or b_r
+  auto red_solve = [&](const double* c, double* out) {
+    double sum[D], tv[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) sum[k] = 0.0;
+#pragma unroll
+    for (int d = 0; d < 6; ++d) {
+      if (nb[d] >= 0) {
+#pragma unroll
+        for (int k = 0; k < D; ++k) sum[k] += ldx(U + (size_t)k * ld + nb[d]);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < D; ++k) tv[k] = (c ? c[k] : 0.0) + s[k] * sum[k];
+    minv<D, double>(Mp, bd, tv, out);
+  };
+  // out = S v on the black voxels (v in their registers); two barriers
+  auto apply_S = [&](const double* v, double* out) -> bool {
+    if (black) publish(v);
+    if (!bar()) return false;
+    if (red) {
+      double y[D];
+      red_solve(nullptr, y);
+      publish(y);
+    }
+    if (!bar()) return false;
+    if (black) amul<D, double>(Bp, bd, s, nb, a.ndir, degd, v, U, ld, out);
+    return true;
+  };
+  // red voxels: x_r from the black voxels' x (one barrier); then every voxel's x is final
+  auto recover_red = [&]() -> bool {
+    if (black) publish(x);
+    if (!bar()) return false;
+    if (red) {
+      double bv[D];
+      load_b(bv);
+      red_solve(bv, x);
+    }
+    return true;
+  };
+  // (r, u, w) of the reduced system from the current x_b, with partials (r'u, w'u, r'r, b'b)
+  auto restart = [&](double* tot) -> bool {
+    double bv[D];
+    double sx[D];
+    if (!apply_S(x, sx)) return false;
+    if (black) {
+#pragma unroll
+      for (int k = 0; k < D; ++k) r[k] = shH[k * bd + t] - sx[k];
+      minv<D, double>(Mp, bd, r, u);
+    }
+    if (!apply_S(u, w)) return false;
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    if (black) {
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        v[0] += r[k] * u[k];
+        v[1] += w[k] * u[k];
+        v[2] += r[k] * r[k];
+      }
+    }
+    load_b(bv);
+#pragma unroll
+    for (int k = 0; k < D; ++k) v[3] += bv[k] * bv[k];
+    return grid_allreduce4(a.bar, a.part, a.part1, v, sh.red, sh.ints, tot);
+  };
+  // ||b - B~ x||^2 of the full system at the current x (every voxel's x final), FP64
+  auto true_residual = [&](double* tot) -> bool {
+    if (own) {
+#pragma unroll
+      for (int k = 0; k < D; ++k) a.x[(size_t)k * ld + n] = x[k];
+    }
+    if (!bar()) return false;
+    double ax[D], bv[D], v[4] = {0.0, 0.0, 0.0, 0.0};
+    if (own) {
+      load_b(bv);
+      amul<D, double>(Bp, bd, s, nb, a.ndir, degd, x, a.x, ld, ax);
+#pragma unroll
+      for (int k = 0; k < D; ++k) v[2] += (bv[k] - ax[k]) * (bv[k] - ax[k]);
+    }
+    return grid_allreduce4(a.bar, a.part, a.part1, v, sh.red, sh.ints, tot);
+  };
+
+  // b^ = b_b + scale .* sum of the red neighbours' Dg_r^-1 b_r
+  if (red) {
+    double y[D], bv[D];
+    load_b(bv);
+    minv<D, double>(Mp, bd, bv, y);
+    publish(y);
+  }
+  if (!bar()) return;
+  if (black) {
+    double sum[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) sum[k] = 0.0;
+#pragma unroll
+    for (int d = 0; d < 6; ++d) {
+      if (nb[d] >= 0) {
+#pragma unroll
+        for (int k = 0; k < D; ++k) sum[k] += ldx(U + (size_t)k * ld + nb[d]);
+      }
+    }
+    double bv[D];
+    load_b(bv);
+#pragma unroll
+    for (int k = 0; k < D; ++k) shH[k * bd + t] = bv[k] + s[k] * sum[k];
+  }
+  double tot[4];
+  if (!restart(tot)) return;   // (apply_S's first barrier orders the reads of U above)
+  double gam = tot[0], del = tot[1], rr = tot[2];
+  const double bb = tot[3];
+  const double tol2 = a.delta * a.delta * bb;
+  const double rel0 = bb > 0.0 ? sqrt(rr / bb) : 0.0;
+  int it = 0, restarts = 0, status = 0;
+  bool x_final = false;   // the red voxels' x matches the current x_b
+  if (!(isfinite(gam) && isfinite(del) && isfinite(bb))) status = 7;
+  if (status == 0 && bb == 0.0) {
+#pragma unroll
+    for (int k = 0; k < D; ++k) x[k] = 0.0;
+    x_final = true;
+  }
+  bool done = status != 0 || bb == 0.0;
+  if (!done && rr <= tol2) {
+    // the start value may already satisfy the tolerance: confirm on B~
+    if (!recover_red()) return;
+    if (!true_residual(tot)) return;
+    x_final = true;
+    rr = tot[2];
+    done = rr <= tol2;
+  }
+  double alpha = (del > 0.0) ? gam / del : 0.0, beta = 0.0;
+  double rgam = 0.0, ralpha = 0.0;
+  cg_recips(gam, del, rgam, ralpha);
+  if (!done && !(del > 0.0)) { status = 3; done = true; }
+  while (!done) {
+    if (black) {
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        p[k] = u[k] + beta * p[k];
+        q[k] = w[k] + beta * q[k];
+        x[k] += alpha * p[k];
+        r[k] -= alpha * q[k];
+      }
+      minv<D, double>(Mp, bd, r, u);
+    }
+    x_final = false;
+    if (!apply_S(u, w)) return;
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    if (black) {
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        v[0] += r[k] * u[k];
+        v[1] += w[k] * u[k];
+        v[2] += r[k] * r[k];
+      }
+    }
+    if (!grid_allreduce4(a.bar, a.part, a.part1, v, sh.red, sh.ints, tot)) return;
+    ++it;
+    rr = tot[2];
+    cg_scalar_step(sh, tot[0], tot[1], rr, tol2, it, a.max_iter, alpha, beta, gam, rgam, ralpha);
+    const int code = sh.code;
+    __syncthreads();
+    if (code == 7) { status = 7; break; }
+    if (code == 3) { status = 3; break; }
+    if (code == 1) {
+      // confirm with the true residual of B~
+      if (!recover_red()) return;
+      if (!true_residual(tot)) return;
+      x_final = true;
+      rr = tot[2];
+      if (rr <= tol2) break;
+      if (it >= a.max_iter) { status = 4; break; }
+      ++restarts;
+      if (!restart(tot)) return;
+      gam = tot[0];
+      del = tot[1];
+      alpha = del > 0.0 ? gam / del : 0.0;
+      beta = 0.0;
+      cg_recips(gam, del, rgam, ralpha);
+#pragma unroll
+      for (int k = 0; k < D; ++k) { p[k] = 0.0; q[k] = 0.0; }
+      if (!(del > 0.0)) { status = 3; break; }
+      continue;
+    }
+  }
+  if (!x_final && !recover_red()) return;
   if (own) {
 #pragma unroll
     for (int k = 0; k < D; ++k) a.x[(size_t)k * ld + n] = x[k];
@@ -1079,12 +1353,15 @@ cudaError_t launch_resident(const PcgArgs& a, cudaStream_t stream, int* grid_out
   grid = (a.N + per - 1) / per;
   int threads = ((per + 31) / 32) * 32;
   if (threads < 64) threads = 64;
-  if (threads > RES_MAX_THREADS) return cudaSuccess;
+  if (threads > (a.reduced && !a.mixed ? RB_MAX_THREADS : RES_MAX_THREADS)) return cudaSuccess;
   if (a.max_grid > 0 && grid > a.max_grid) return cudaSuccess;
   // FP64: blocks + factor in FP64; mixed: FP64 blocks + FP32 blocks + FP32 factor
-  const size_t shm = a.mixed ? (size_t)ntri(D) * threads * (sizeof(double) + 2 * sizeof(float))
-                             : (size_t)2 * ntri(D) * threads * sizeof(double);
-  const void* kern = a.mixed ? (const void*)k_pcg_mixed_res<D> : (const void*)k_pcg_res<D>;
+  const size_t shm = a.mixed     ? (size_t)ntri(D) * threads * (sizeof(double) + 2 * sizeof(float))
+                     : a.reduced ? (size_t)(2 * ntri(D) + D) * threads * sizeof(double)
+                                 : (size_t)2 * ntri(D) * threads * sizeof(double);
+  const void* kern = a.mixed     ? (const void*)k_pcg_mixed_res<D>
+                     : a.reduced ? (const void*)k_pcg_rb<D>
+                                 : (const void*)k_pcg_res<D>;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm) != cudaSuccess) {
     cudaGetLastError();
     return cudaSuccess;

@@ -71,6 +71,10 @@ struct PcgArgs {
   const int* black;      // [n_black] compact indices of the others
   int n_black;
   const unsigned char* colour;  // [ld] 0 red, 1 black (resident variant)
+  // FP64 resident variant: CG on the red-black reduced system (Schur complement of the red
+  // voxels) with the block factors mfac, equivalent to SSOR with omega = 1; the other
+  // variants run that SSOR form instead (ssor = 1, omega = 1 must be set alongside)
+  int reduced;
 };
 
 // Launches the cooperative persistent PCG kernel for dimension D (1..12) on `stream`.

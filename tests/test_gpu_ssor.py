@@ -149,3 +149,74 @@ def test_mixed_ssor_takes_fewer_inner_iterations():
         its[name] = info.iterations
         m.close()
     assert its["ssor"] < its["bj"]
+
+
+@pytest.mark.parametrize("variant", ["auto", "streaming"])
+def test_reduced_system_solves_reach_the_exact_draw(case, variant):
+    """PRECOND_RB_REDUCED: the resident FP64 solver runs CG on the black voxels' Schur
+    complement and recovers the red voxels; the streaming solver runs SSOR with omega = 1.
+    Both reach the oracle's exact draw and confirm on the full system's true residual."""
+    from paper_1606_00980_gb300 import bfmri
+    w, lat, s = case
+    m = make(w, s, precond=bfmri.PRECOND_RB_REDUCED,
+             pcg_variant=bfmri.PCG_AUTO if variant == "auto" else bfmri.PCG_STREAMING)
+    W, info = m.sample_W(counter=3)
+    Bd, bw = model.w_blocks_direct(w.Y, w.X, s["A"], s["lam"], w.eps)
+    ref, _ = gibbs.draw_gmrf(lat, Bd, bw, s["alpha"], SEED, 3, philox.TAG_W)
+    assert info.rel_residual <= 1e-12
+    assert rel(W, ref) <= 1e-8
+    s2 = s
+    if w.P > 0:
+        A, ia = m.sample_A(counter=4)
+        Ar = gibbs.sample_A(lat, w.Y, w.X, dict(s, W=W), SEED, 4, spatial=True)
+        assert ia.rel_residual <= 1e-12
+        assert rel(A, Ar) <= 1e-8
+        s2 = dict(s, A=A)
+    # a second draw, warm-started from the first (the W system now sees the new A)
+    W2, _ = m.sample_W(counter=5)
+    Bd2, bw2 = model.w_blocks_direct(w.Y, w.X, s2["A"], s2["lam"], w.eps)
+    ref2, _ = gibbs.draw_gmrf(lat, Bd2, bw2, s2["alpha"], SEED, 5, philox.TAG_W)
+    assert rel(W2, ref2) <= 1e-8
+    m.close()
+
+
+@pytest.mark.parametrize("delta", [1e-8, 1e-12])
+def test_reduced_system_iterates_like_ssor_omega1(delta):
+    """Same Krylov spaces: the reduced solve needs as many iterations as SSOR with omega = 1
+    (up to one for the red component of the start residual), about half of block-Jacobi's."""
+    from paper_1606_00980_gb300 import bfmri
+    w = WL["slab_K6_P3"]
+    s = state_for(w, np.random.default_rng(9))
+    its = {}
+    for name, pc in (("bj", bfmri.PRECOND_BLOCK_JACOBI), ("ssor", bfmri.PRECOND_SSOR),
+                     ("reduced", bfmri.PRECOND_RB_REDUCED)):
+        m = make(w, s, precond=pc, delta=delta)
+        _, info = m.sample_W(counter=1)
+        its[name] = info.iterations
+        m.close()
+    assert abs(its["reduced"] - its["ssor"]) <= 2, its
+    assert its["reduced"] < its["bj"], its
+
+
+def test_reduced_system_sweeps_and_grouped_chains():
+    """Whole sweeps with the reduced solver (W and A), against the same sweeps with SSOR at
+    omega = 1 (different solvers, same stop rule): agreement to the solver tolerance; grouped
+    chains with the option run their multi-RHS solves as SSOR with omega = 1."""
+    from paper_1606_00980_gb300 import bfmri
+    w = WL["slab_K6_P3"]
+    s = state_for(w, np.random.default_rng(11))
+    a = make(w, s, precond=bfmri.PRECOND_RB_REDUCED, delta=1e-11)
+    b = make(w, s, precond=bfmri.PRECOND_SSOR, delta=1e-11)
+    a.gibbs_sweep(3, 10)
+    b.gibbs_sweep(3, 10)
+    sa, sb = a.get_state(), b.get_state()
+    assert rel(sa["W"], sb["W"]) <= 1e-8
+    assert rel(sa["A"], sb["A"]) <= 1e-8
+    assert np.max(np.abs(sa["lam"] / sb["lam"] - 1)) <= 1e-7
+    c = make(w, s, precond=bfmri.PRECOND_RB_REDUCED, delta=1e-11)
+    d = make(w, s, precond=bfmri.PRECOND_RB_REDUCED, delta=1e-11)
+    bfmri.gibbs_sweep_group([c, d], 2, 10)
+    c.close()
+    d.close()
+    a.close()
+    b.close()
