@@ -80,10 +80,10 @@ def pcg_bytes_per_voxel_iter(K, w=8):
     return w * (11 * K + 2 * (K * (K + 1) // 2))
 
 
-# DRAM bytes (read + write) of one W-solve launch of the current resident SSOR solver on the
-# whole-brain workload, from one ncu capture of this kernel version (22.99 MB + 0.63 MB): the
-# first touch of the staged blocks, factors, b and x; the iterations run from L2.
-NCU_TRAFFIC_W = {"ssor": 23.62e6}
+# DRAM bytes (read + write) of one W-solve launch on the whole-brain workload, from one ncu
+# capture of each kernel version (reduced system: 25.39 MB + 0.72 MB; SSOR form: 22.99 MB +
+# 0.63 MB): the first touch of the staged blocks, factors, b and x; the iterations run from L2.
+NCU_TRAFFIC_W = {"reduced": 26.12e6, "ssor": 23.62e6}
 
 
 def precond_options(args):
