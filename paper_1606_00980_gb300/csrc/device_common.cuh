@@ -264,6 +264,17 @@ __device__ __forceinline__ void st_relaxed(unsigned int* p, unsigned int v) {
 constexpr int ERR_TIMEOUT_CODE = 5;
 constexpr int ERR_NOT_SPD_CODE = 3;
 
+// The barrier generation as thread 0 of this CTA last saw it. grid_barrier_start reads the
+// generation word once when a kernel starts (no CTA can complete a barrier before every CTA
+// has arrived, so all read the same value); every barrier then advances the copy itself, so
+// an arrival is one atomic instead of a dependent load followed by an atomic. Every kernel
+// that uses the barriers below calls grid_barrier_start first.
+static __shared__ unsigned int g_bar_gen;
+
+__device__ __forceinline__ void grid_barrier_start(const GridBarrier& b) {
+  if (threadIdx.x == 0) g_bar_gen = ld_acquire(b.gen);
+}
+
 // Polls the generation word until it differs from g0; false on error or time-out.
 __device__ __forceinline__ bool wait_generation(const GridBarrier& b, unsigned int g0) {
   const unsigned long long t0 = globaltimer_ns();
@@ -283,7 +294,7 @@ __device__ __forceinline__ bool wait_generation(const GridBarrier& b, unsigned i
 __device__ __forceinline__ bool grid_sync(const GridBarrier& b, int* sh_flag) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    const unsigned int g0 = ld_acquire(b.gen);
+    const unsigned int g0 = g_bar_gen;
     const unsigned int arrived = atom_add_acq_rel(b.count, 1u);
     bool ok = true;
     if (arrived == gridDim.x - 1) {
@@ -292,6 +303,7 @@ __device__ __forceinline__ bool grid_sync(const GridBarrier& b, int* sh_flag) {
     } else {
       ok = wait_generation(b, g0);
     }
+    g_bar_gen = g0 + 1u;
     *sh_flag = ok ? 0 : 1;
   }
   __syncthreads();
@@ -358,7 +370,7 @@ __device__ __forceinline__ bool grid_allreduce4(const GridBarrier& b, double* pa
   const int l = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned int nblocks = gridDim.x;
   if (threadIdx.x == 0) {
-    const unsigned int g0 = ld_acquire(b.gen);
+    const unsigned int g0 = g_bar_gen;
     double* part = (g0 & 1u) ? part1 : part0;
 #pragma unroll
     for (int i = 0; i < 4; ++i) part[(size_t)blockIdx.x * 4 + i] = bt[i];
@@ -370,6 +382,7 @@ __device__ __forceinline__ bool grid_allreduce4(const GridBarrier& b, double* pa
     } else {
       ok = wait_generation(b, g0);
     }
+    g_bar_gen = g0 + 1u;
     sh_int[0] = ok ? 0 : 1;
     sh_int[1] = (int)(g0 & 1u);
   }
@@ -489,7 +502,7 @@ __device__ __forceinline__ bool grid_allreduce4_ff(const GridBarrier& b, double*
       for (int o = 16; o > 0; o >>= 1) c4[i] = ff_add(c4[i], ff_shfl_xor(c4[i], o));
     }
     if (l == 0) {
-      const unsigned int g0 = ld_acquire(b.gen);
+      const unsigned int g0 = g_bar_gen;
       float* row = reinterpret_cast<float*>((g0 & 1u) ? part1 : part0) + (size_t)blockIdx.x * 8;
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
@@ -504,6 +517,7 @@ __device__ __forceinline__ bool grid_allreduce4_ff(const GridBarrier& b, double*
       } else {
         ok = wait_generation(b, g0);
       }
+      g_bar_gen = g0 + 1u;
       sh_int[0] = ok ? 0 : 1;
       sh_int[1] = (int)(g0 & 1u);
     }

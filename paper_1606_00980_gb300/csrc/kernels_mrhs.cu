@@ -256,7 +256,7 @@ __device__ __forceinline__ bool mrhs_reduce(const MrhsArgs& a, const Units& U, i
                                             int* sh_int, int* any_active, int* any_pending) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    const unsigned int g0 = ld_acquire(a.bar.gen);
+    const unsigned int g0 = g_bar_gen;
     const unsigned int arrived = atom_add_acq_rel(a.bar.count, 1u);
     sh_int[0] = (arrived == gridDim.x - 1) ? 1 : 0;
     sh_int[1] = (int)g0;
@@ -290,11 +290,13 @@ __device__ __forceinline__ bool mrhs_reduce(const MrhsArgs& a, const Units& U, i
       __threadfence();
       st_relaxed(a.bar.count, 0u);
       red_add_release(a.bar.gen, 1u);
+      g_bar_gen = (unsigned int)sh_int[1] + 1u;
     }
     __syncthreads();
   } else {
     if (threadIdx.x == 0) {
       const bool ok = wait_generation(a.bar, (unsigned int)sh_int[1]);
+      g_bar_gen = (unsigned int)sh_int[1] + 1u;
       sh_int[2] = ok ? __ldcg(a.flags + 0) : 0;
       sh_int[3] = ok ? __ldcg(a.flags + 1) : 0;
       sh_int[0] = ok ? 0 : 1;
@@ -335,6 +337,7 @@ __global__ void __launch_bounds__(MRHS_THREADS, (sizeof(T) == 4 || D <= 4) ? 2 :
   __shared__ int sh_flag;
   const Units U = units_of(a);
   const size_t ld = a.ld;
+  grid_barrier_start(a.bar);
   auto unit_rhs = [&](int u) { return u % U.S; };
   auto unit_chunk = [&](int u) { return u / U.S; };
   // columns selected by `cols` (bit j = column j) of unit u's partial row

@@ -296,6 +296,7 @@ template <int D>
 __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_res(PcgArgs a) {
   extern __shared__ double smem[];
   __shared__ Shared sh;
+  grid_barrier_start(a.bar);
   constexpr int NT = ntri(D);
   const int bd = blockDim.x, t = threadIdx.x;
   double* shB = smem;
@@ -488,6 +489,7 @@ template <int D>
 __global__ void __launch_bounds__(RB_MAX_THREADS, 1) k_pcg_rb(PcgArgs a) {
   extern __shared__ double smem[];
   __shared__ Shared sh;
+  grid_barrier_start(a.bar);
   constexpr int NT = ntri(D);
   const int bd = blockDim.x, t = threadIdx.x;
   double* shB = smem;
@@ -741,6 +743,7 @@ __global__ void __launch_bounds__(RB_MAX_THREADS, 1) k_pcg_rb(PcgArgs a) {
 template <int D>
 __global__ void __launch_bounds__(PCG_THREADS) k_pcg_stream(PcgArgs a) {
   __shared__ Shared sh;
+  grid_barrier_start(a.bar);
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   const int nth = gridDim.x * blockDim.x;
   const size_t ld = a.ld;
@@ -936,6 +939,7 @@ template <int D>
 __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_mixed_res(PcgArgs a) {
   extern __shared__ double smem[];
   __shared__ Shared sh;
+  grid_barrier_start(a.bar);
   constexpr int NT = ntri(D);
   const int bd = blockDim.x, t = threadIdx.x;
   double* shB = smem;                                   // [NT][bd] FP64 blocks
@@ -1133,6 +1137,7 @@ __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_mixed_res(PcgArgs a)
 template <int D>
 __global__ void __launch_bounds__(PCG_THREADS) k_pcg_mixed_stream(PcgArgs a) {
   __shared__ Shared sh;
+  grid_barrier_start(a.bar);
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   const int nth = gridDim.x * blockDim.x;
   const size_t ld = a.ld;
