@@ -146,10 +146,25 @@ __device__ __forceinline__ void store_packed(T* __restrict__ base, size_t ld, in
   for (int e = 0; e < ntri(D); ++e) base[(size_t)e * ld + n] = m[e];
 }
 
-// In-place Cholesky of a packed symmetric matrix; the diagonal is replaced by its inverse.
-// Returns false if a pivot is not positive and finite.
+// 1/sqrt(s) for s > 0 by Newton's iteration for the reciprocal square root,
+// y <- y + y (1 - s y^2) / 2, from the hardware's approximate FP64 value: each step squares
+// the relative error, and two steps take it to the FP64 rounding level. Far fewer FP64
+// instructions than a correctly rounded square root followed by a division, which matters on
+// a part whose FP64 issue rate is 2 lanes per clock per SM.
+__device__ __forceinline__ double rsqrt_nr(double s) {
+  double y;
+  asm("rsqrt.approx.f64 %0, %1;" : "=d"(y) : "d"(s));
+  double h = fma(-s * y, y, 1.0);
+  y = fma(0.5 * y, h, y);
+  h = fma(-s * y, y, 1.0);
+  return fma(0.5 * y, h, y);
+}
+
+// In-place Cholesky of a packed symmetric matrix; the diagonal is replaced by its inverse and,
+// if diag is given, the pivots' square roots l_jj are written there. Returns false if a pivot
+// is not positive and finite.
 template <int D, typename T>
-__device__ __forceinline__ bool chol_packed_invdiag(T* m) {
+__device__ __forceinline__ bool chol_packed_invdiag(T* m, T* diag = nullptr) {
   bool ok = true;
 #pragma unroll
   for (int j = 0; j < D; ++j) {
@@ -157,8 +172,16 @@ __device__ __forceinline__ bool chol_packed_invdiag(T* m) {
 #pragma unroll
     for (int k = 0; k < j; ++k) s -= m[tri(j, k)] * m[tri(j, k)];
     ok = ok && (s > T(0)) && (s < T(1e300));
-    const T ljj = sqrt(s > T(0) ? s : T(1));
-    const T inv = T(1) / ljj;
+    const T sp = s > T(0) ? s : T(1);
+    T ljj, inv;
+    if constexpr (sizeof(T) == 8) {
+      inv = rsqrt_nr(sp);
+      ljj = sp * inv;
+    } else {
+      ljj = sqrt(sp);
+      inv = T(1) / ljj;
+    }
+    if (diag) diag[j] = ljj;
     m[tri(j, j)] = inv;
 #pragma unroll
     for (int i = j + 1; i < D; ++i) {
@@ -169,6 +192,18 @@ __device__ __forceinline__ bool chol_packed_invdiag(T* m) {
     }
   }
   return ok;
+}
+
+// y = L z with L packed lower and its diagonal l_jj given separately (no division).
+template <int D, typename T>
+__device__ __forceinline__ void lower_mul_diag(const T* L, const T* diag, const T* z, T* y) {
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    T s = z[i] * diag[i];
+#pragma unroll
+    for (int j = 0; j < i; ++j) s += L[tri(i, j)] * z[j];
+    y[i] = s;
+  }
 }
 
 // y = L z with L packed lower, inverted diagonal.

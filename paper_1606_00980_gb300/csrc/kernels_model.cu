@@ -155,26 +155,29 @@ __global__ void __launch_bounds__(VOX_THREADS) k_assemble_w(AssembleArgs a) {
 #pragma unroll
     for (int k = 0; k < K; ++k) a.bmean[k * ld + n] = bw[k];
   }
-  double sq[K];
-#pragma unroll
-  for (int k = 0; k < K; ++k) sq[k] = sqrt(a.scale[k]);
   double rhs[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) rhs[k] = bw[k];
-  double L[ntri(K)];
+  double L[ntri(K)], Ld[K];
 #pragma unroll
   for (int e = 0; e < ntri(K); ++e) L[e] = B[e];
-  bool ok = chol_packed_invdiag<K>(L);
+  bool ok = chol_packed_invdiag<K>(L, Ld);
   if (a.ldata) store_packed<K>(a.ldata, ld, n, L);
   if (a.perturb) {
     const int lin = a.g.lin[n];
     double z[K], Lz[K];
     site_normals<K>(a.rng, (uint32_t)lin * 4u + 3u, z);
-    lower_mul_invdiag<K>(L, z, Lz);
+    lower_mul_diag<K>(L, Ld, z, Lz);
 #pragma unroll
     for (int k = 0; k < K; ++k) rhs[k] += Lz[k];
-    if (a.edge) add_edge_terms<K>(a.g, a.edge, n, rhs);
-    else add_edge_noise<K>(a.g, a.rng, n, lin, sq, rhs);
+    if (a.edge) {
+      add_edge_terms<K>(a.g, a.edge, n, rhs);
+    } else {
+      double sq[K];
+#pragma unroll
+      for (int k = 0; k < K; ++k) sq[k] = sqrt(a.scale[k]);
+      add_edge_noise<K>(a.g, a.rng, n, lin, sq, rhs);
+    }
   }
 #pragma unroll
   for (int k = 0; k < K; ++k) a.rhs[k * ld + n] = rhs[k];
@@ -245,7 +248,8 @@ __global__ void __launch_bounds__(VOX_THREADS) k_assemble_a(AssembleArgs a) {
   double L[ntri(PM)];
 #pragma unroll
   for (int e = 0; e < ntri(PM); ++e) L[e] = J[e];
-  bool ok = chol_packed_invdiag<PM>(L);
+  double Ld[PM];
+  bool ok = chol_packed_invdiag<PM>(L, Ld);
   if (a.ldata) {
 #pragma unroll
     for (int e = 0; e < ntri(PM); ++e)
@@ -258,13 +262,10 @@ __global__ void __launch_bounds__(VOX_THREADS) k_assemble_a(AssembleArgs a) {
 #pragma unroll
     for (int i = 0; i < PM; ++i)
       if (i >= P) z[i] = 0.0;
-    lower_mul_invdiag<PM>(L, z, Lz);
+    lower_mul_diag<PM>(L, Ld, z, Lz);
 #pragma unroll
     for (int i = 0; i < PM; ++i) rhs[i] += (i < P) ? Lz[i] : 0.0;
     if (a.spatial) {
-      double sq[PM];
-#pragma unroll
-      for (int i = 0; i < PM; ++i) sq[i] = (i < P) ? sqrt(a.scale[i]) : 0.0;
       if (a.edge) {
         // terms generated for dimension P; the padded components stay zero
         double part[PM];
@@ -277,6 +278,9 @@ __global__ void __launch_bounds__(VOX_THREADS) k_assemble_a(AssembleArgs a) {
 #pragma unroll
         for (int i = 0; i < PM; ++i) rhs[i] += part[i];
       } else {
+        double sq[PM];
+#pragma unroll
+        for (int i = 0; i < PM; ++i) sq[i] = (i < P) ? sqrt(a.scale[i]) : 0.0;
         add_edge_noise<PM>(a.g, a.rng, n, lin, sq, rhs);
       }
     }
@@ -322,12 +326,13 @@ __global__ void __launch_bounds__(VOX_THREADS) k_assemble_a(AssembleArgs a) {
 template <int D>
 __global__ void __launch_bounds__(VOX_THREADS) k_edge_noise(Geometry g, const double* scale, Rng rng,
                                                             double* E) {
+  // sqrt(scale_k) once per CTA
+  __shared__ double sq[D];
+  if (threadIdx.x < D) sq[threadIdx.x] = sqrt(scale[threadIdx.x]);
+  __syncthreads();
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= g.N) return;
   const uint32_t lin = (uint32_t)g.lin[n];
-  double sq[D];
-#pragma unroll
-  for (int k = 0; k < D; ++k) sq[k] = sqrt(scale[k]);
   for (int d = 0; d < g.ndir / 2; ++d) {
     double z[D];
     const bool has = __ldg(g.nbr + (size_t)(2 * d + 1) * g.ld + n) >= 0;
