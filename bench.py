@@ -598,7 +598,8 @@ def run_batched_chains(args, w, n_chains=8, sweeps=3):
     W-draws/s over the chains, and the HBM view of the grouped W solve (one k_mrhs<8, double>
     launch per sweep; per voxel, iteration and chain 13 K FP64 vector words plus the chain's
     own block and factor, K(K+1)/2 words each; SSOR adds its two colour phases, 4 K words
-    and one more factor read)."""
+    and one more factor read; the reduced red-black system moves 8 K words and one factor
+    per voxel)."""
     import torch
 
     from paper_1606_00980_gb300.bfmri import Model, gibbs_sweep_group
@@ -625,8 +626,11 @@ def run_batched_chains(args, w, n_chains=8, sweeps=3):
     it_w = sum(i.pcg_iterations_W for i in infos)
     K = w.K
     F = K * (K + 1) // 2
-    ssor = args.precond in ("ssor", "reduced")   # the multi-RHS solver runs SSOR phases
-    bytes_w = it_w * w.N * 8 * (13 * K + 2 * F + ((4 * K + F) if ssor else 0))
+    # words per voxel, iteration and chain: block-Jacobi 13 K + 2 F; SSOR adds its colour
+    # phases (4 K + F); the reduced system moves 11 K + F per black voxel (local update and
+    # factor) and 5 K + F per voxel pair in the red phase and the black product: 8 K + F
+    words = {"bj": 13 * K + 2 * F, "ssor": 17 * K + 3 * F, "reduced": 8 * K + F}[args.precond]
+    bytes_w = it_w * w.N * 8 * words
     solve_s = tim["pcg_W"]["ms"] / 1e3
     hbm_peak, hbm_src, _ = peaks()
     return {"chains": n_chains, "W_draws_per_s": n_chains * sweeps / dt,

@@ -614,10 +614,11 @@ MrhsArgs mrhs_args(bfmri_handle* h, int D, int S, const double* scale, int max_i
   return m;
 }
 
-// Red-black SSOR for the plain multi-RHS solves (SVB samples, grouped chains) when the handle
-// asks for it; the probe solves keep block-Jacobi.
+// Red-black SSOR, or CG on the red-black reduced system, for the plain multi-RHS solves (SVB
+// samples, grouped chains) when the handle asks for it; the probe solves keep block-Jacobi.
 void mrhs_ssor(const bfmri_handle* h, MrhsArgs& m) {
-  m.ssor = uses_ssor(h->opt);
+  m.reduced = h->opt.precond == BFMRI_PRECOND_RB_REDUCED;
+  m.ssor = uses_ssor(h->opt) && !m.reduced;
   m.omega = ssor_omega_of(h->opt);
   m.red = h->d_red;
   m.n_red = h->n_red;

@@ -397,6 +397,242 @@ __global__ void __launch_bounds__(MRHS_THREADS, (sizeof(T) == 4 || D <= 4) ? 2 :
     }
     return true;
   };
+  // ---- red-black reduced system (a.reduced): CG on the black voxels' Schur complement
+  // S = Dg_b - L Dg_r^-1 U preconditioned by Dg_b (the iterates of SSOR with omega = 1); the
+  // red voxels' x is recovered from their own rows at every (re)start. u lives at the black
+  // voxels of the U planes and y = Dg_r^-1 (scale .* sum of the black neighbours' u) at the
+  // red ones; every warp owns at most one unit (the launcher guarantees S <= warps).
+  auto list_chunk = [&](int nl, int c, int& i0, int& i1) {
+    int cs = (nl + U.chunks - 1) / U.chunks;
+    cs = ((cs + 31) / 32) * 32;
+    i0 = c * cs;
+    i1 = min(nl, (c + 1) * cs);
+  };
+  // sum over the in-mask neighbours m of V[m]
+  auto nsum = [&](int n, const T* V, T* out) {
+    int nb[6];
+#pragma unroll
+    for (int d = 0; d < 6; ++d) nb[d] = d < a.ndir ? __ldg(a.nbr + (size_t)d * ld + n) : -1;
+    T v[6][D];
+#pragma unroll
+    for (int d = 0; d < 6; ++d)
+#pragma unroll
+      for (int k = 0; k < D; ++k) v[d][k] = V[(size_t)k * ld + (nb[d] >= 0 ? nb[d] : n)];
+#pragma unroll
+    for (int k = 0; k < D; ++k) out[k] = T(0);
+#pragma unroll
+    for (int d = 0; d < 6; ++d)
+      if (nb[d] >= 0) {
+#pragma unroll
+        for (int k = 0; k < D; ++k) out[k] += v[d][k];
+      }
+  };
+  // red voxels of the selected right-hand sides: U = Dg^-1 (scale .* sum of the neighbours' U)
+  auto rb_red_phase = [&](auto sel) {
+    for (int u = U.gw; u < U.units; u += U.nw) {
+      const int r = unit_rhs(u), c = unit_chunk(u);
+      if (!sel(r)) continue;
+      const RhsOp<D, T> op = rhs_op<D, T>(a, r);
+      T* Uu = UUv + (size_t)r * a.vs;
+      int i0, i1;
+      list_chunk(a.n_red, c, i0, i1);
+      for (int i = i0 + U.lane; i < i1; i += 32) {
+        const int n = __ldg(a.red + i);
+        T t[D], z[D];
+        nsum(n, Uu, t);
+#pragma unroll
+        for (int k = 0; k < D; ++k) t[k] *= op.sc[k];
+        precond_apply<D, T>(a, op.M, n, t, z);
+#pragma unroll
+        for (int k = 0; k < D; ++k) Uu[(size_t)k * ld + n] = z[k];
+      }
+    }
+  };
+  // (re)start: red x from its rows, black r = b - B~ x (the rows' true residual), u, w = S u;
+  // partials (r'u, w'u, ||b - B~ x||^2 over every voxel, ||b||^2)
+  auto restart_pass_rb = [&](bool first) -> bool {
+    auto sel = [&](int r) { return first || __ldcg(&a.st[r].active) == 2; };
+    KSum<T> kg, kd, krr, kbb;
+    for (int u = U.gw; u < U.units; u += U.nw) {
+      const int r = unit_rhs(u), c = unit_chunk(u);
+      if (!sel(r)) continue;
+      const RhsOp<D, T> op = rhs_op<D, T>(a, r);
+      int i0, i1;
+      list_chunk(a.n_red, c, i0, i1);
+      for (int i = i0 + U.lane; i < i1; i += 32) {
+        const int n = __ldg(a.red + i);
+        T bn[D], t[D], xn[D], ax[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) bn[k] = __ldg(op.b + (size_t)k * ld + n);
+        nsum(n, op.x, t);
+#pragma unroll
+        for (int k = 0; k < D; ++k) t[k] = bn[k] + op.sc[k] * t[k];
+        precond_apply<D, T>(a, op.M, n, t, xn);
+        block_apply<D, T>(a, op.B, op.sc, n, xn, op.x, ax);
+        T rr2 = T(0), b2 = T(0);
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          rr2 += (bn[k] - ax[k]) * (bn[k] - ax[k]);
+          b2 += bn[k] * bn[k];
+          op.x[(size_t)k * ld + n] = xn[k];
+        }
+        krr.add(rr2);
+        kbb.add(b2);
+      }
+    }
+    if (!grid_sync(a.bar, &sh_flag)) return false;
+    for (int u = U.gw; u < U.units; u += U.nw) {
+      const int r = unit_rhs(u), c = unit_chunk(u);
+      if (!sel(r)) continue;
+      const RhsOp<D, T> op = rhs_op<D, T>(a, r);
+      T *R = Rv + (size_t)r * a.vs, *Uu = UUv + (size_t)r * a.vs;
+      T *P = PPv + (size_t)r * a.vs, *Sv = SSv + (size_t)r * a.vs;
+      int i0, i1;
+      list_chunk(a.n_black, c, i0, i1);
+      for (int i = i0 + U.lane; i < i1; i += 32) {
+        const int n = __ldg(a.black + i);
+        T xn[D], bn[D], ax[D], rn[D], un[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          xn[k] = op.x[(size_t)k * ld + n];
+          bn[k] = __ldg(op.b + (size_t)k * ld + n);
+        }
+        block_apply<D, T>(a, op.B, op.sc, n, xn, op.x, ax);
+#pragma unroll
+        for (int k = 0; k < D; ++k) rn[k] = bn[k] - ax[k];
+        precond_apply<D, T>(a, op.M, n, rn, un);
+        T g = T(0), rr2 = T(0), b2 = T(0);
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          const size_t o = (size_t)k * ld + n;
+          R[o] = rn[k];
+          Uu[o] = un[k];
+          P[o] = T(0);
+          Sv[o] = T(0);
+          g += rn[k] * un[k];
+          rr2 += rn[k] * rn[k];
+          b2 += bn[k] * bn[k];
+        }
+        kg.add(g);
+        krr.add(rr2);
+        kbb.add(b2);
+      }
+    }
+    if (!grid_sync(a.bar, &sh_flag)) return false;
+    rb_red_phase(sel);
+    if (!grid_sync(a.bar, &sh_flag)) return false;
+    for (int u = U.gw; u < U.units; u += U.nw) {
+      const int r = unit_rhs(u), c = unit_chunk(u);
+      if (!sel(r)) continue;
+      const RhsOp<D, T> op = rhs_op<D, T>(a, r);
+      const T* Uu = UUv + (size_t)r * a.vs;
+      T* Wv = WWv + (size_t)r * a.vs;
+      int i0, i1;
+      list_chunk(a.n_black, c, i0, i1);
+      for (int i = i0 + U.lane; i < i1; i += 32) {
+        const int n = __ldg(a.black + i);
+        T un[D], wn[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) un[k] = Uu[(size_t)k * ld + n];
+        block_apply<D, T>(a, op.B, op.sc, n, un, Uu, wn);
+        T dl = T(0);
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          dl += wn[k] * un[k];
+          Wv[(size_t)k * ld + n] = wn[k];
+        }
+        kd.add(dl);
+      }
+    }
+    if (U.gw < U.units) {
+      double acc[4] = {kg.value(), kd.value(), krr.value(), kbb.value()};
+      write_partials(U.gw, acc, 0xFu);
+    }
+    return true;
+  };
+  // one iteration for the active right-hand sides: black local update (r'u, r'r), red phase,
+  // black product (w'u); the caller reduces
+  auto iterate_rb = [&]() -> bool {
+    KSum<T> kg, kr, kd;
+    for (int u = U.gw; u < U.units; u += U.nw) {
+      const int r = unit_rhs(u), c = unit_chunk(u);
+      if (__ldcg(&a.st[r].active) != 1) continue;
+      const T al = (T)__ldcg(&a.st[r].alpha), be = (T)__ldcg(&a.st[r].beta);
+      const RhsOp<D, T> op = rhs_op<D, T>(a, r);
+      T *x = op.x, *R = Rv + (size_t)r * a.vs, *Uu = UUv + (size_t)r * a.vs;
+      T *P = PPv + (size_t)r * a.vs, *Sv = SSv + (size_t)r * a.vs;
+      const T* Wv = WWv + (size_t)r * a.vs;
+      int i0, i1;
+      list_chunk(a.n_black, c, i0, i1);
+      for (int i = i0 + U.lane; i < i1; i += 32) {
+        const int n = __ldg(a.black + i);
+        T rn[D], un[D], pk[D], sk[D], xk[D], wk[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          const size_t o = (size_t)k * ld + n;
+          un[k] = Uu[o];
+          pk[k] = P[o];
+          wk[k] = Wv[o];
+          sk[k] = Sv[o];
+          xk[k] = x[o];
+          rn[k] = R[o];
+        }
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          pk[k] = un[k] + be * pk[k];
+          sk[k] = wk[k] + be * sk[k];
+          xk[k] += al * pk[k];
+          rn[k] -= al * sk[k];
+        }
+        precond_apply<D, T>(a, op.M, n, rn, un);
+        T g = T(0), rr2 = T(0);
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          const size_t o = (size_t)k * ld + n;
+          P[o] = pk[k];
+          Sv[o] = sk[k];
+          x[o] = xk[k];
+          R[o] = rn[k];
+          Uu[o] = un[k];
+          g += rn[k] * un[k];
+          rr2 += rn[k] * rn[k];
+        }
+        kg.add(g);
+        kr.add(rr2);
+      }
+    }
+    if (!grid_sync(a.bar, &sh_flag)) return false;
+    rb_red_phase([&](int r) { return __ldcg(&a.st[r].active) == 1; });
+    if (!grid_sync(a.bar, &sh_flag)) return false;
+    for (int u = U.gw; u < U.units; u += U.nw) {
+      const int r = unit_rhs(u), c = unit_chunk(u);
+      if (__ldcg(&a.st[r].active) != 1) continue;
+      const RhsOp<D, T> op = rhs_op<D, T>(a, r);
+      const T* Uu = UUv + (size_t)r * a.vs;
+      T* Wv = WWv + (size_t)r * a.vs;
+      int i0, i1;
+      list_chunk(a.n_black, c, i0, i1);
+      for (int i = i0 + U.lane; i < i1; i += 32) {
+        const int n = __ldg(a.black + i);
+        T un[D], wn[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) un[k] = Uu[(size_t)k * ld + n];
+        block_apply<D, T>(a, op.B, op.sc, n, un, Uu, wn);
+        T dl = T(0);
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          dl += wn[k] * un[k];
+          Wv[(size_t)k * ld + n] = wn[k];
+        }
+        kd.add(dl);
+      }
+    }
+    if (U.gw < U.units) {
+      double acc[4] = {kg.value(), kd.value(), kr.value(), 0.0};
+      write_partials(U.gw, acc, 0x7u);
+    }
+    return true;
+  };
   auto restart_pass = [&](bool first) -> bool {
     for (int u = U.gw; u < U.units; u += U.nw) {
       const int r = unit_rhs(u), c = unit_chunk(u);
@@ -474,10 +710,27 @@ __global__ void __launch_bounds__(MRHS_THREADS, (sizeof(T) == 4 || D <= 4) ? 2 :
   };
 
   int any_active = 0, any_pending = 0;
-  if (!restart_pass(true)) return;
+  // the reduced-system path exists for FP64 solves only (the FP32 storage serves the probes,
+  // which keep block-Jacobi); a.reduced is ignored in FP32
+  constexpr bool kRB = sizeof(T) == 8;
+  const bool rb = kRB && a.reduced;
+  if constexpr (kRB) {
+    if (!(rb ? restart_pass_rb(true) : restart_pass(true))) return;
+  } else {
+    if (!restart_pass(true)) return;
+  }
   if (!mrhs_reduce(a, U, 0, true, sh_int, &any_active, &any_pending)) return;
   while (any_active || any_pending) {
-    if (any_active) {
+    bool handled = false;
+    if constexpr (kRB) {
+      if (any_active && rb) {
+        if (!iterate_rb()) return;
+        if (!mrhs_reduce(a, U, 1, false, sh_int, &any_active, &any_pending)) return;
+        handled = true;
+      }
+    }
+    if (handled) {
+    } else if (any_active) {
       // local update of active right-hand sides, with the partials r'u and r'r of the
       // updated vectors (columns 0 and 2 of the unit's row)
       for (int u = U.gw; u < U.units; u += U.nw) {
@@ -616,7 +869,10 @@ __global__ void __launch_bounds__(MRHS_THREADS, (sizeof(T) == 4 || D <= 4) ? 2 :
       if (!mrhs_reduce(a, U, 1, false, sh_int, &any_active, &any_pending)) return;
     } else {
       // every moving RHS has stopped: confirm the pending ones with the true residual
-      if (!restart_pass(false)) return;
+      bool ok = true;
+      if constexpr (kRB) ok = rb ? restart_pass_rb(false) : restart_pass(false);
+      else ok = restart_pass(false);
+      if (!ok) return;
       if (!mrhs_reduce(a, U, 0, false, sh_int, &any_active, &any_pending)) return;
     }
   }
@@ -657,7 +913,15 @@ static cudaError_t launch_d(const MrhsArgs& a, cudaStream_t stream, int* units_o
   int chunks = nw / a.S;
   if (chunks < 1) chunks = 1;
   if (units_out) *units_out = a.S * chunks;
-  void* args[] = {(void*)&a};
+  // the reduced-system path keeps one unit per warp: with more right-hand sides than warps it
+  // runs the equivalent SSOR form (omega = 1) instead
+  MrhsArgs b = a;
+  if (b.reduced && b.S > nw) {
+    b.reduced = 0;
+    b.ssor = 1;
+    b.omega = 1.0;
+  }
+  void* args[] = {(void*)&b};
   return cudaLaunchCooperativeKernel(kern, dim3((unsigned)grid), dim3(MRHS_THREADS), args, shm, stream);
 }
 

@@ -86,6 +86,9 @@ struct MrhsArgs {
   int n_red;
   const int* black;
   int n_black;
+  // CG on the red-black reduced system instead (plain solves, FP64): needs mfac, the colour
+  // lists and at most one (RHS, chunk) unit per warp (S <= warps of the grid)
+  int reduced;
 };
 
 // Probe set-up and post-processing (log-determinant and trace probes).

@@ -48,8 +48,9 @@ WL = {
 }
 
 
-# block-Jacobi (0) and red-black SSOR (2) preconditioning of the multi-RHS solves
-PRECONDS = {"bj": dict(), "ssor": dict(precond=2), "ssor_w1.3": dict(precond=2, ssor_omega=1.3)}
+# block-Jacobi, red-black SSOR and the red-black reduced system in the multi-RHS solves
+PRECONDS = {"bj": dict(), "ssor": dict(precond=2), "ssor_w1.3": dict(precond=2, ssor_omega=1.3),
+            "reduced": dict(precond=3)}
 
 
 @pytest.mark.parametrize("pc", sorted(PRECONDS))
@@ -84,7 +85,7 @@ def test_group_sweep_matches_oracle_per_chain(name, pc):
         m.close()
 
 
-@pytest.mark.parametrize("pc", ["bj", "ssor"])
+@pytest.mark.parametrize("pc", ["bj", "ssor", "reduced"])
 def test_group_matches_chains_advanced_alone(pc):
     """Three sweeps at a tight tolerance (1e-10): grouped and lone chains agree to the
     solver tolerance, sweep after sweep (the later steps see the earlier draws)."""

@@ -39,10 +39,11 @@ def setup(spatial=True, K=3, P=2, **opts):
     return w, lat, s, m
 
 
-@pytest.mark.parametrize("precond", [0, 2])
+@pytest.mark.parametrize("precond", [0, 2, 3])
 @pytest.mark.parametrize("spatial", [True, False])
 def test_svb_step_single_step_parity(spatial, precond):
-    """precond 0: block-Jacobi multi-RHS solves; 2: red-black SSOR."""
+    """precond 0: block-Jacobi multi-RHS solves; 2: red-black SSOR; 3: the reduced
+    red-black system."""
     w, lat, s, m = setup(spatial, precond=precond)
     Ns, c = 4, 11
     avb, bvb, info = m.spvb_step(Ns, c, extrapolate=False)
