@@ -563,7 +563,9 @@ def run_precond_compare(args, w, n_draws=10):
              ("mixed_block_jacobi_resident", dict(precond=bfmri.PRECOND_BLOCK_JACOBI,
                                                   precision=bfmri.PREC_MIXED)),
              ("mixed_ssor_omega1.0_resident", dict(precond=bfmri.PRECOND_SSOR, ssor_omega=1.0,
-                                                   precision=bfmri.PREC_MIXED))]
+                                                   precision=bfmri.PREC_MIXED)),
+             ("mixed_rb_reduced_resident", dict(precond=bfmri.PRECOND_RB_REDUCED,
+                                                precision=bfmri.PREC_MIXED))]
     out = {}
     for name, opts in cases:
         m = Model.from_workload(w, delta=1e-8, seed=2024, profile=1, **opts)
@@ -692,13 +694,18 @@ def run_batched(args):
         ms.close()
         K = w.K
         sum_bytes = 100 * K * w.N * 8 + (K + K * (K + 1) // 2 + len(gs)) * w.N * 8
+        # FP64 work: per sample and voxel K subtractions, K additions and K(K+1)/2 FMAs
+        sum_flops = 99 * w.N * (2 * K + K * (K + 1))
         hbm_peak, _, _ = peaks()
         svb = {"samples": 100, "precond": args.precond, "iteration_ms": dt * 1e3,
                "pcg_iterations_W_total": int(info.pcg_iterations_W),
                "pcg_iterations_A_total": int(info.pcg_iterations_A),
                "W_solve_ms": tsv["pcg_W"]["ms"], "A_solve_ms": tsv["pcg_A"]["ms"],
                "max_rel_residual_W": info.max_rel_residual_W,
-               "summary": {"contrasts": len(gs), "ms": t_sum,
+               "summary": {"contrasts": len(gs), "ms": t_sum, "bound": "alu",
+                           "fp64": {"achieved_tflops": sum_flops / (t_sum / 1e3) / 1e12,
+                                    "peak_tflops": FP64_PEAK_TFLOPS,
+                                    "frac": sum_flops / (t_sum / 1e3) / 1e12 / FP64_PEAK_TFLOPS},
                            "hbm": {"achieved_gbs": sum_bytes / (t_sum / 1e3) / 1e9,
                                    "peak_gbs": hbm_peak,
                                    "frac": sum_bytes / (t_sum / 1e3) / 1e9 / hbm_peak},

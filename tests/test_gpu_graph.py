@@ -22,6 +22,7 @@ CASES = {
     "streaming_fp64_ssor": dict(precond=2, pcg_variant=1),
     "resident_mixed_ssor": dict(precond=2, precision=1),
     "resident_fp64_reduced": dict(precond=3),
+    "resident_mixed_reduced": dict(precond=3, precision=1),
 }
 
 

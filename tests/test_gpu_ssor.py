@@ -220,3 +220,41 @@ def test_reduced_system_sweeps_and_grouped_chains():
     d.close()
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("variant", ["auto", "streaming"])
+def test_mixed_reduced_system_reaches_the_exact_draw(case, variant):
+    """Mixed precision with PRECOND_RB_REDUCED: FP32 CG on the reduced system for each
+    correction (resident), SSOR with omega = 1 in the streaming variant; the FP64 refinement
+    reaches the exact draw."""
+    from paper_1606_00980_gb300 import bfmri
+    w, lat, s = case
+    m = make(w, s, precond=bfmri.PRECOND_RB_REDUCED, precision=bfmri.PREC_MIXED,
+             pcg_variant=bfmri.PCG_AUTO if variant == "auto" else bfmri.PCG_STREAMING)
+    W, info = m.sample_W(counter=3)
+    Bd, bw = model.w_blocks_direct(w.Y, w.X, s["A"], s["lam"], w.eps)
+    ref, _ = gibbs.draw_gmrf(lat, Bd, bw, s["alpha"], SEED, 3, philox.TAG_W)
+    assert info.rel_residual <= 1e-12
+    assert rel(W, ref) <= 1e-8
+    assert info.refinements >= 1
+    if w.P > 0:
+        A, ia = m.sample_A(counter=4)
+        Ar = gibbs.sample_A(lat, w.Y, w.X, dict(s, W=W), SEED, 4, spatial=True)
+        assert ia.rel_residual <= 1e-12
+        assert rel(A, Ar) <= 1e-8
+    m.close()
+
+
+def test_mixed_reduced_inner_iterations_match_mixed_ssor():
+    from paper_1606_00980_gb300 import bfmri
+    w = WL["slab_K6_P3"]
+    s = state_for(w, np.random.default_rng(10))
+    its = {}
+    for name, pc in (("bj", bfmri.PRECOND_BLOCK_JACOBI), ("ssor", bfmri.PRECOND_SSOR),
+                     ("reduced", bfmri.PRECOND_RB_REDUCED)):
+        m = make(w, s, precond=pc, precision=bfmri.PREC_MIXED, delta=1e-8)
+        _, info = m.sample_W(counter=1)
+        its[name] = info.iterations
+        m.close()
+    assert its["reduced"] < its["bj"], its
+    assert abs(its["reduced"] - its["ssor"]) <= max(3, its["ssor"] // 5), its
