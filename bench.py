@@ -362,6 +362,7 @@ def run_ours(args, world, rank, local):
     mixed = run_mixed(args, w, flush, stream) if not args.no_mixed else None
     # posterior summaries (chain PPMs, moments, log joint) on the same workload
     summ = run_summaries(args, w) if (rank == 0 and not args.no_summaries) else None
+    conv = run_convergence(args) if (rank == 0 and args.convergence) else None
 
     # independent chains of the same subject advanced together (one multi-RHS launch per solve)
     chains = run_chains(args, w, flush, stream, value) if not args.no_chains else None
@@ -390,7 +391,8 @@ def run_ours(args, world, rank, local):
                            "pcg_iterations_A_per_sweep": it_a / args.steps},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                 "voxel_draws_per_s": value * N,
-                "mixed_precision": mixed, "summaries": summ, "grouped_chains": chains,
+                "mixed_precision": mixed, "summaries": summ, "convergence": conv,
+                "grouped_chains": chains,
                 "preconditioners": precs,
                 "captured_sweeps": graphs, "serving": serving, "batched_probes": batched,
                 "gpu_launches": int(n_launch),
@@ -447,6 +449,93 @@ def run_summaries(args, w, sweeps=20):
                                "frac": bytes_acc / acc_s / 1e9 / hbm_peak, "bytes": bytes_acc},
             "joint_ppm": (got["joint_count"] / got["n"]).tolist(),
             "log_joint_us": t_lj * 1e3, "log_joint": lj["total"]}
+
+
+def time_to_within(values, times, tol=0.01):
+    """Time at the first record after which every later record stays within tol of the final
+    value in every component (relative); values (n_records, D)."""
+    import numpy as np
+    v = np.asarray(values)
+    final = v[-1]
+    ok = np.all(np.abs(v / final - 1.0) <= tol, axis=1)
+    for i in range(len(ok)):
+        if ok[i:].all():
+            return float(times[i])
+    return float(times[-1])
+
+
+def run_convergence(args, sizes=(1000, 10000, 100000)):
+    """The paper's simulation study on GB300 (Appendix D data at N = 1e3, 1e4, 1e5; K = 5,
+    P = 1, T = 351; Section 4's metric): processing time until the posterior mean of alpha is
+    within 1 % of its final value. SVB: 50 iterations (N_s = 5 for the first 10, then 100,
+    prior means as start values), once as the plain VB fixed-point iteration and once with the
+    Appendix C extrapolation every other iteration; final = the last iteration's E[alpha]
+    (with the extrapolation the iterates can settle into a cycle, which the per-iteration
+    deviations show). MCMC: 1000 burn-in sweeps,
+    then 4000 sweeps thinned by 5; the cumulative mean of the kept alpha draws against its
+    final value. Device time by CUDA events around each step (statistics included); delta
+    1e-8, the --precond solver."""
+    import numpy as np
+    import torch
+
+    from paper_1606_00980_gb300 import synth
+    from paper_1606_00980_gb300.bfmri import Model
+    out = []
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = fn()
+        e1.record(stream)
+        e1.synchronize()
+        return r, e0.elapsed_time(e1) / 1e3
+
+    for N in sizes:
+        w = synth.paper_simulation(N, seed=21)
+        # SVB, with and without the Appendix C extrapolation (trick 1)
+        svb = {}
+        for name, extrap in (("svb_plain", False), ("svb_extrapolated", True)):
+            m = Model.from_workload(w, delta=1e-8, seed=31, **precond_options(args))
+            _, t_stats = timed(m.precompute_stats)
+            t, times, alphas = t_stats, [], []
+            for it in range(50):
+                ns = 5 if it < 10 else 100
+                # the fixed random numbers of Section 3.3: one draw counter for every iteration
+                (avb, _, _), dt = timed(lambda: m.spvb_step(ns, 7, extrapolate=extrap))
+                t += dt
+                times.append(t)
+                alphas.append(np.array(avb))
+            m.close()
+            dev = [round(float(np.max(np.abs(a / alphas[-1] - 1.0))), 4) for a in alphas]
+            svb[name] = {"time_to_1pct_s": time_to_within(alphas, times), "total_s": times[-1],
+                         "iteration_ms_Ns100": (times[-1] - times[-2]) * 1e3,
+                         "alpha_final": alphas[-1].tolist(), "max_rel_dev_from_final": dev}
+        # MCMC
+        m = Model.from_workload(w, delta=1e-8, seed=32, **precond_options(args))
+        _, t_stats = timed(m.precompute_stats)
+        t = t_stats
+        _, dt = timed(lambda: m.gibbs_sweep(1000, 0, info=False))
+        t += dt
+        times_m, cum = [], []
+        acc = np.zeros(w.K)
+        for j in range(800):
+            _, dt = timed(lambda: m.gibbs_sweep(5, 1000 + 5 * j, info=False))
+            t += dt
+            acc += m.get_state()["alpha"]
+            times_m.append(t)
+            cum.append(acc / (j + 1))
+        m.synchronize()
+        m.close()
+        mcmc_conv = time_to_within(cum, times_m)
+        out.append({"N": N, **svb,
+                    "mcmc": {"time_to_1pct_s": mcmc_conv, "total_s": times_m[-1],
+                             "ms_per_sweep": (times_m[-1] - times_m[0]) / (5 * 799) * 1e3,
+                             "alpha_final": cum[-1].tolist()}})
+    return {"workload": "paper simulation (Appendix D), K5 P1 T351, N = 1e3 / 1e4 / 1e5",
+            "metric": "device seconds until E[alpha] is within 1 % of its final value",
+            "precond": args.precond, "sizes": out}
 
 
 def run_mixed(args, w, flush, stream):
@@ -838,6 +927,9 @@ def main():
     ap.add_argument("--no-precond", action="store_true")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--no-summaries", action="store_true")
+    ap.add_argument("--convergence", action="store_true",
+                    help="also run the paper's simulation study (time to 1 %% convergence of "
+                         "E[alpha] for SVB and MCMC at N = 1e3, 1e4, 1e5; about a minute)")
     ap.add_argument("--precond", choices=["reduced", "ssor", "bj"], default="reduced",
                     help="preconditioner of the headline chain and of its mixed-precision twin "
                          "(the multi-RHS solves use block-Jacobi)")

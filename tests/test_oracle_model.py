@@ -293,3 +293,25 @@ def test_svb_extrapolation_rules():
     # decreasing toward zero: negative prediction falls back to the proposal
     v = gibbs.svb_extrapolate((np.array([3.0]), np.array([2.0])), np.array([1.0]))
     assert v[0] >= 1.0 / 5.0
+
+
+def test_paper_simulation_workloads_have_the_papers_shapes():
+    """Appendix D's simulation: N = 1e3 / 1e4 / 1e5 centred boxes of the 53x63x46 block,
+    K = 5, P = 1, T = 351, voxel means scaled to 100; the UGL-prior rows are centred and
+    smoother (smaller neighbour differences) the larger their alpha."""
+    w = synth.paper_simulation(1000, seed=3)
+    assert w.N == 1000 and w.K == 5 and w.P == 1 and w.T == 351
+    assert w.dims == (53, 63, 46) and int(w.mask.sum()) == 1000
+    assert np.allclose(w.Y.mean(axis=0), 100.0)
+    assert np.all(np.abs(w.A_true) <= 0.9)
+    lat = Lattice(w.mask, 6)
+    E = lat.edges()
+    spread = [np.mean((w.W_true[k, E[:, 0]] - w.W_true[k, E[:, 1]]) ** 2) for k in range(4)]
+    assert spread[0] > spread[1] > spread[2] > spread[3]
+    # increments of the periodic UGL field have variance 1/(3 alpha) per direction on average
+    f = synth.periodic_ugl_field((46, 63, 53), 0.5, np.random.default_rng(1))
+    assert abs(f.mean()) < 1e-12
+    d = np.concatenate([np.diff(f, axis=a).ravel() for a in range(3)])
+    assert abs(np.var(d) * 0.5 * 3 - 1.0) < 0.15
+    for N in (10000,):
+        assert int(synth.paper_simulation(N, seed=4).mask.sum()) == N
