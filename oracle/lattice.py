@@ -1,8 +1,15 @@
-"""In-mask voxel graph for the UGL spatial prior (Section 2, after Eq. 5; Section 3.1, Eq. 6-7).
+"""In-mask voxel graph for the UGL spatial prior (Section 2, after Eq. 5; Section 3.1, Eq. 6-7)
+and its weighted form, the WGL prior of the Discussion.
 
 D_w has, for every in-mask voxel, its number of in-mask face neighbours on the diagonal
 and -1 for every adjacent in-mask pair. G_w has one row per adjacent pair (i, j) with +1 in
 column i and -1 in column j, so that D_w = G_w' G_w (Eq. 6-7).
+
+Weighted graph Laplacian (Discussion: D_w = G_w' C G_w for a diagonal edge-weight matrix C
+chosen from the distances between neighbouring voxels; in Algorithm 2 row e of G_w is
+multiplied by sqrt(C_ee)). Here C_ee = weights[d] for an edge along direction d (x, y, z), the
+form that anisotropic voxel sizes call for; weights = (1, 1, 1) is the UGL prior. D() then has
+the weighted degree sum_d c_d on the diagonal and -c_d per adjacent pair.
 
 Conventions (shared with the CUDA library by specification only, not by code):
 * the mask is an (nz, ny, nx) array, x fastest; in-mask voxels are numbered in raster order;
@@ -17,7 +24,10 @@ import scipy.sparse as sp
 
 
 class Lattice:
-    def __init__(self, mask: np.ndarray, neighbourhood: int):
+    def __init__(self, mask: np.ndarray, neighbourhood: int, weights=(1.0, 1.0, 1.0)):
+        self.weights = np.asarray(weights, dtype=np.float64)
+        if self.weights.shape != (3,) or not np.all(self.weights > 0):
+            raise ValueError("weights: three positive edge weights (x, y, z)")
         mask = np.asarray(mask)
         if mask.ndim == 2:
             mask = mask[None]
@@ -71,6 +81,14 @@ class Lattice:
         order = np.lexsort((e[:, 2], self.lin[e[:, 0]]))
         return e[order]
 
+    def edge_weights(self):
+        """C_ee for the edges in edges() order."""
+        return self.weights[self.edges()[:, 2]]
+
+    def Gw(self):
+        """C^(1/2) G_w: row e of G_w times sqrt(C_ee) (the form Algorithm 2 uses)."""
+        return (sp.diags(np.sqrt(self.edge_weights())) @ self.G()).tocsr()
+
     def G(self):
         """G_w (Eq. 7): one row per edge, +1 at the lower endpoint i, -1 at j."""
         e = self.edges()
@@ -81,14 +99,15 @@ class Lattice:
         return sp.csr_matrix((v, (r, c)), shape=(m, self.N))
 
     def D(self):
-        """D_w, the unweighted graph Laplacian (Section 2), built from adjacency lookups:
-        degree on the diagonal, -1 per adjacent in-mask pair. Built independently of G()."""
+        """D_w, the graph Laplacian (Section 2; weighted as in the Discussion), built from
+        adjacency lookups: weighted degree on the diagonal, -c_d per adjacent in-mask pair along
+        direction d. Built independently of G()."""
         x, y, z = self.coords()
         offs = [(1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0)]
         if self.neighbourhood == 6:
             offs += [(0, 0, 1), (0, 0, -1)]
-        rows, cols = [], []
-        for dx, dy, dz in offs:
+        rows, cols, vals = [], [], []
+        for idx, (dx, dy, dz) in enumerate(offs):
             xx, yy, zz = x + dx, y + dy, z + dz
             ok = (xx >= 0) & (xx < self.nx) & (yy >= 0) & (yy < self.ny) & (zz >= 0) & (zz < self.nz)
             lin = zz * self.nx * self.ny + yy * self.nx + xx
@@ -97,9 +116,10 @@ class Lattice:
             keep = nb >= 0
             rows.append(np.flatnonzero(keep))
             cols.append(nb[keep])
+            vals.append(np.full(int(keep.sum()), self.weights[idx // 2]))
         rows = np.concatenate(rows)
         cols = np.concatenate(cols)
-        adj = sp.csr_matrix((np.ones(len(rows)), (rows, cols)), shape=(self.N, self.N))
+        adj = sp.csr_matrix((np.concatenate(vals), (rows, cols)), shape=(self.N, self.N))
         deg = np.asarray(adj.sum(axis=1)).ravel()
         return (sp.diags(deg) - adj).tocsr()
 

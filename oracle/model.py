@@ -201,7 +201,7 @@ def perturbation(lat: Lattice, blocks, scale, seed, counter, tag, stream=0):
     sites_e = lat.lin[E[:, 0]] * 4 + E[:, 2]
     z1 = philox.normals(seed, sites_e, K, counter, tag, stream)
     z2 = philox.normals(seed, lat.lin * 4 + 3, K, counter, tag, stream)
-    G = lat.G()
+    G = lat.Gw()
     part1 = np.concatenate([np.sqrt(scale[k]) * (G.T @ z1[:, k]) for k in range(K)])
     Lz = np.stack([np.linalg.cholesky(blocks[n]) @ z2[n] for n in range(N)])  # (N, K)
     part2 = kmajor(Lz)
@@ -212,7 +212,7 @@ def perturbation_matrix(lat: Lattice, blocks, scale):
     """The linear map (z1, z2) -> perturbation as an explicit matrix (for the covariance pin:
     its Gram matrix must equal B~ exactly, which is why Algorithm 2 samples correctly)."""
     N, K, _ = blocks.shape
-    G = lat.G()
+    G = lat.Gw()
     part1 = sp.block_diag([sp.csr_matrix(np.sqrt(scale[k]) * G.T) for k in range(K)], format="csr")
     H = H_perm(N, K)
     L = blkdiag([np.linalg.cholesky(blocks[n]) for n in range(N)])
@@ -230,10 +230,11 @@ def lambda_params(rss, T, P, u1, u2):
 
 
 def quad_forms_edges(lat: Lattice, V):
-    """Q_k = V_k D V_k' as the sum over edges of squared differences (D = G'G, Eq. 6-7)."""
+    """Q_k = V_k D V_k' as the weighted sum over edges of squared differences
+    (D = G'CG, Eq. 6-7 and the Discussion's WGL form)."""
     E = lat.edges()
     diff = V[:, E[:, 0]] - V[:, E[:, 1]]
-    return (diff * diff).sum(axis=1)
+    return (lat.weights[E[:, 2]][None, :] * diff * diff).sum(axis=1)
 
 
 def quad_forms_laplacian(lat: Lattice, V):

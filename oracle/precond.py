@@ -94,16 +94,16 @@ def ssor_apply_sweeps(lat: Lattice, blocks, scale, v_nk, omega=1.0):
     col = colours(lat)
     diag = blocks + lat.degree()[:, None, None] * np.diag(scale)[None]
     nbrs = [[] for _ in range(N)]
-    for i, j, _ in lat.edges():
-        nbrs[i].append(j)
-        nbrs[j].append(i)
+    for i, j, d in lat.edges():
+        nbrs[i].append((j, lat.weights[d]))
+        nbrs[j].append((i, lat.weights[d]))
     v = np.asarray(v_nk, dtype=float)
     z = np.zeros((N, D))
     order = [n for n in range(N) if col[n] == 0] + [n for n in range(N) if col[n] == 1]
 
     def relax(n):
-        # off-diagonal coupling of voxels n, m in component k is -scale_k
-        r = v[n] + sum(scale * z[m] for m in nbrs[n])
+        # off-diagonal coupling of voxels n, m in component k is -scale_k c_e (edge weight)
+        r = v[n] + sum(scale * c * z[m] for m, c in nbrs[n])
         z[n] = (1.0 - omega) * z[n] + omega * np.linalg.solve(diag[n], r)
 
     for n in order:

@@ -315,3 +315,39 @@ def test_paper_simulation_workloads_have_the_papers_shapes():
     assert abs(np.var(d) * 0.5 * 3 - 1.0) < 0.15
     for N in (10000,):
         assert int(synth.paper_simulation(N, seed=4).mask.sum()) == N
+
+
+WGL_WEIGHTS = (2.0, 0.5, 3.25)
+
+
+def test_weighted_laplacian_equals_scaled_incidence_gram():
+    """WGL (Discussion): D_w built from weighted adjacency equals G' C G, with C the edge
+    weights of each edge's direction; equal weights c scale the UGL Laplacian by c; the
+    perturbation uses C^(1/2) G; the edge quadratic forms carry the weights."""
+    for nb in (6, 4):
+        w, _ = tiny(dims=(4, 3, 3) if nb == 6 else (5, 4, 1), K=2, P=1, T=30, nb=nb)
+        lat = Lattice(w.mask, nb, weights=WGL_WEIGHTS)
+        G = lat.G()
+        C = sp.diags(lat.edge_weights())
+        assert np.array_equal((G.T @ C @ G).toarray(), lat.D().toarray())
+        assert np.allclose((lat.Gw().T @ lat.Gw()).toarray(), lat.D().toarray(), rtol=0, atol=1e-14)
+        ugl = Lattice(w.mask, nb)
+        eq = Lattice(w.mask, nb, weights=(1.5, 1.5, 1.5))
+        assert np.array_equal(eq.D().toarray(), 1.5 * ugl.D().toarray())
+        V = np.random.default_rng(2).standard_normal((3, lat.N))
+        assert np.allclose(model.quad_forms_edges(lat, V), model.quad_forms_laplacian(lat, V),
+                           rtol=1e-13, atol=0)
+
+
+@pytest.mark.parametrize("nb", [6, 4])
+def test_weighted_perturbation_covariance_is_precision(nb):
+    """Algorithm 2 under the WGL prior: M M' = B~ with the weighted Laplacian, so the draw is
+    exact; and the weighted precision is SPD."""
+    w, _ = tiny(dims=(3, 3, 2) if nb == 6 else (4, 3, 1), K=2, P=1, T=30, nb=nb)
+    lat = Lattice(w.mask, nb, weights=WGL_WEIGHTS)
+    s = random_state(w, np.random.default_rng(6))
+    Bd, _ = model.w_blocks_direct(w.Y, w.X, s["A"], s["lam"])
+    M = model.perturbation_matrix(lat, Bd, s["alpha"]).toarray()
+    B = model.precision(lat, Bd, s["alpha"]).toarray()
+    assert np.max(np.abs(M @ M.T - B)) <= 1e-12 * np.max(np.abs(B))
+    assert np.linalg.eigvalsh(B).min() > 0

@@ -99,3 +99,14 @@ def test_ssor_omega1_spectrum_is_one_and_the_reduced_spectrum():
     evs = np.linalg.eigvals(np.linalg.solve(Db, S.toarray())).real
     want = np.sort(np.concatenate([np.ones(nr), evs]))
     assert np.allclose(ev, want, rtol=0, atol=1e-10)
+
+
+@pytest.mark.parametrize("omega", [0.8, 1.0])
+def test_weighted_factored_form_equals_sor_sweeps(omega):
+    """Under the WGL prior (edge weights per direction) the SSOR operator in factored form
+    still equals one forward and one backward SOR sweep voxel by voxel."""
+    lat, blocks, scale, v = small_problem(13, D=2, neighbourhood=6)
+    lat = Lattice(lat.mask, 6, weights=(2.0, 0.5, 3.25))
+    a = precond.ssor_apply(lat, blocks, scale, v, omega)
+    b = precond.ssor_apply_sweeps(lat, blocks, scale, v, omega)
+    assert np.allclose(a, b, rtol=1e-12, atol=1e-12)
