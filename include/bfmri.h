@@ -122,6 +122,12 @@ typedef struct {
                                 results as direct launches. Ignored while profile or
                                 debug_skip_block is set; if capture is unavailable the handle
                                 falls back to direct launches. Default 0. */
+  double edge_weight[3];     /* weighted graph-Laplacian (WGL) prior (Discussion): the prior
+                                precision of W_k is alpha_k G_w' C G_w (and that of A_p is
+                                beta_p G_w' C G_w) with C the weight of each edge's direction
+                                x, y, z, e.g. from anisotropic voxel sizes; Algorithm 2 scales
+                                each edge's noise by sqrt(C). All > 0; default 1, 1, 1 (the
+                                UGL prior of Section 2). */
 } bfmri_options;
 
 #define BFMRI_PCG_AUTO      0

@@ -46,7 +46,7 @@ class bfmri_options(C.Structure):
                 ("alloc_ctx", C.c_void_p), ("barrier_timeout_s", C.c_double),
                 ("debug_skip_block", C.c_int), ("profile", C.c_int), ("pcg_variant", C.c_int),
                 ("sm_budget", C.c_int), ("ssor_omega", C.c_double),
-                ("use_graph", C.c_int)]
+                ("use_graph", C.c_int), ("edge_weight", C.c_double * 3)]
 
 
 class bfmri_solve_info(C.Structure):

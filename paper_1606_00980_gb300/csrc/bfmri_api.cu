@@ -219,6 +219,7 @@ Geometry geom(const bfmri_handle* h) {
   g.stride[0] = h->stride[0];
   g.stride[1] = h->stride[1];
   g.stride[2] = h->stride[2];
+  for (int d = 0; d < 3; ++d) g.cw[d] = h->opt.edge_weight[d];
   return g;
 }
 
@@ -323,6 +324,7 @@ bfmri_status run_pcg(bfmri_handle* h, int D, const double* scale, double* x, int
   a.N = h->N;
   a.ld = h->ld;
   a.ndir = h->ndir;
+  for (int d = 0; d < 3; ++d) a.cw[d] = h->opt.edge_weight[d];
   a.nbr = h->d_nbr;
   a.blocks = h->d_blocks;
   a.mfac = h->opt.precond != BFMRI_PRECOND_NONE ? h->d_mfac : nullptr;
@@ -611,6 +613,7 @@ MrhsArgs mrhs_args(bfmri_handle* h, int D, int S, const double* scale, int max_i
   m.max_iter = max_iter;
   m.max_restarts = 4;
   m.sm_cap = h->opt.sm_budget;
+  for (int d = 0; d < 3; ++d) m.cw[d] = h->opt.edge_weight[d];
   return m;
 }
 
@@ -659,6 +662,7 @@ void bfmri_default_options(bfmri_options* o) {
   o->precond = BFMRI_PRECOND_BLOCK_JACOBI;
   o->ssor_omega = 1.0;
   o->use_graph = 0;
+  o->edge_weight[0] = o->edge_weight[1] = o->edge_weight[2] = 1.0;
   o->precision = BFMRI_PREC_FP64;
   o->ar_prior = BFMRI_AR_SPATIAL;
   o->y_layout = BFMRI_Y_MASKED;
@@ -721,6 +725,9 @@ bfmri_status bfmri_create(const bfmri_lattice* lat, const uint8_t* mask, const d
     return fail(nullptr, BFMRI_ERR_INVALID_ARG, "ssor_omega must be in (0, 2)");
   if (o.precision != BFMRI_PREC_FP64 && o.precision != BFMRI_PREC_MIXED)
     return fail(nullptr, BFMRI_ERR_INVALID_ARG, "unknown precision mode");
+  for (int d = 0; d < 3; ++d)
+    if (!(o.edge_weight[d] > 0.0) || !std::isfinite(o.edge_weight[d]))
+      return fail(nullptr, BFMRI_ERR_INVALID_ARG, "edge_weight must be positive and finite");
   if (o.precision == BFMRI_PREC_MIXED && !(o.inner_tol > 0.0 && o.inner_tol < 1.0))
     return fail(nullptr, BFMRI_ERR_INVALID_ARG, "inner_tol must be in (0, 1)");
   if (!all_finite(X, (size_t)T * K)) return fail(nullptr, BFMRI_ERR_INVALID_ARG, "X has non-finite values");
@@ -1609,6 +1616,7 @@ bfmri_status bfmri_logdet_probe(bfmri_handle* h, int which, int n_probes, int la
   pa.b = h->mr_b;
   pa.x = h->mr_x;
   pa.rng = rng_of(h, counter, TAG_PROBE);
+  for (int d = 0; d < 3; ++d) pa.cw[d] = h->opt.edge_weight[d];
   cudaError_t e = launch_probe(D, pa, 0, nullptr, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "probe rhs");
   MrhsArgs m = mrhs_args(h, D, n_probes, scale, lanczos_steps, true);
@@ -1977,6 +1985,7 @@ bfmri_status bfmri_apply_preconditioner(bfmri_handle* h, int which, const double
   p.N = h->N;
   p.ld = h->ld;
   p.ndir = h->ndir;
+  for (int d = 0; d < 3; ++d) p.cw[d] = h->opt.edge_weight[d];
   p.nbr = h->d_nbr;
   p.mfac = h->opt.precond != BFMRI_PRECOND_NONE ? h->d_mfac : nullptr;
   p.scale = which == 0 ? h->d_alpha : h->d_beta;

@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(VOX_THREADS) k_assemble_w(AssembleArgs a) {
 #pragma unroll
   for (int k = 0; k < K; ++k) a.rhs[k * ld + n] = rhs[k];
   if (a.precond) {
-    const double deg = (double)degree(a.g, n);
+    const double deg = degree(a.g, n);
 #pragma unroll
     for (int k = 0; k < K; ++k) B[tri(k, k)] += a.scale[k] * deg;
     ok = chol_packed_invdiag<K>(B) && ok;
@@ -304,7 +304,7 @@ __global__ void __launch_bounds__(VOX_THREADS) k_assemble_a(AssembleArgs a) {
     for (int i = 0; i < PM; ++i)
       if (i < P) a.rhs[i * ld + n] = rhs[i];
     if (a.precond) {
-      const double deg = a.spatial ? (double)degree(a.g, n) : 0.0;
+      const double deg = a.spatial ? degree(a.g, n) : 0.0;
 #pragma unroll
       for (int i = 0; i < PM; ++i)
         if (i < P) J[tri(i, i)] += a.scale[i] * deg;
@@ -326,9 +326,9 @@ __global__ void __launch_bounds__(VOX_THREADS) k_assemble_a(AssembleArgs a) {
 template <int D>
 __global__ void __launch_bounds__(VOX_THREADS) k_edge_noise(Geometry g, const double* scale, Rng rng,
                                                             double* E) {
-  // sqrt(scale_k) once per CTA
-  __shared__ double sq[D];
-  if (threadIdx.x < D) sq[threadIdx.x] = sqrt(scale[threadIdx.x]);
+  // sqrt(scale_k c_d) once per CTA (c_d: the edge weight of direction d)
+  __shared__ double sq[3][D];
+  if (threadIdx.x < 3 * D) sq[threadIdx.x / D][threadIdx.x % D] = sqrt(scale[threadIdx.x % D] * g.cw[threadIdx.x / D]);
   __syncthreads();
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= g.N) return;
@@ -338,7 +338,7 @@ __global__ void __launch_bounds__(VOX_THREADS) k_edge_noise(Geometry g, const do
     const bool has = __ldg(g.nbr + (size_t)(2 * d + 1) * g.ld + n) >= 0;
     if (has) site_normals<D>(rng, lin * 4u + (uint32_t)d, z);
 #pragma unroll
-    for (int k = 0; k < D; ++k) E[((size_t)d * D + k) * g.ld + n] = has ? sq[k] * z[k] : 0.0;
+    for (int k = 0; k < D; ++k) E[((size_t)d * D + k) * g.ld + n] = has ? sq[d][k] * z[k] : 0.0;
   }
 }
 
@@ -398,10 +398,11 @@ __global__ void __launch_bounds__(HYPER_THREADS) k_quadform(HyperArgs a) {
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       if (m[d] >= 0) {
+        const double c = a.g.cw[d];
 #pragma unroll
         for (int k = 0; k < D; ++k) {
           const double df = v[k] - vn[d][k];
-          acc[k] += df * df;
+          acc[k] += c * df * df;
         }
       }
     }
@@ -456,17 +457,18 @@ __global__ void k_apply(ApplyArgs a) {
   double sum[D];
 #pragma unroll
   for (int k = 0; k < D; ++k) sum[k] = 0.0;
-  int deg = 0;
+  double deg = 0.0;
   for (int d = 0; d < a.g.ndir; ++d) {
     const int m = a.g.nbr[(size_t)d * ld + n];
     if (m >= 0) {
-      ++deg;
+      const double c = a.g.cw[d >> 1];
+      deg += c;
 #pragma unroll
-      for (int k = 0; k < D; ++k) sum[k] += a.x[(size_t)k * ld + m];
+      for (int k = 0; k < D; ++k) sum[k] += c * a.x[(size_t)k * ld + m];
     }
   }
 #pragma unroll
-  for (int k = 0; k < D; ++k) a.y[(size_t)k * ld + n] = y[k] + a.scale[k] * ((double)deg * xn[k] - sum[k]);
+  for (int k = 0; k < D; ++k) a.y[(size_t)k * ld + n] = y[k] + a.scale[k] * (deg * xn[k] - sum[k]);
 }
 
 // ---------------------------------------------------------------------------------------

@@ -43,7 +43,7 @@ __device__ __forceinline__ void block_apply(const MrhsArgs& a, const T* B, const
   T sum[D];
 #pragma unroll
   for (int k = 0; k < D; ++k) sum[k] = T(0);
-  int deg = 0;
+  T deg = T(0);
   constexpr int H = sizeof(T) == 4 ? 6 : 3;   // directions per round of loads
 #pragma unroll
   for (int d0 = 0; d0 < 6; d0 += H) {
@@ -57,14 +57,15 @@ __device__ __forceinline__ void block_apply(const MrhsArgs& a, const T* B, const
 #pragma unroll
     for (int h = 0; h < H; ++h) {
       if (nb[d0 + h] >= 0) {
-        ++deg;
+        const T c = (T)a.cw[(d0 + h) >> 1];   // edge weight of the slot's direction
+        deg += c;
 #pragma unroll
-        for (int k = 0; k < D; ++k) sum[k] += nv[h][k];
+        for (int k = 0; k < D; ++k) sum[k] += c * nv[h][k];
       }
     }
   }
 #pragma unroll
-  for (int k = 0; k < D; ++k) out[k] += sc[k] * ((T)deg * v[k] - sum[k]);
+  for (int k = 0; k < D; ++k) out[k] += sc[k] * (deg * v[k] - sum[k]);
 }
 
 // Compensated (Kahan) accumulation in the storage type: per-thread partial sums stay
@@ -380,7 +381,7 @@ __global__ void __launch_bounds__(MRHS_THREADS, (sizeof(T) == 4 || D <= 4) ? 2 :
           for (int d = 0; d < 6; ++d) {
             if (nb[d] >= 0) {
 #pragma unroll
-              for (int k = 0; k < D; ++k) sum[k] += Uu[(size_t)k * ld + nb[d]];
+              for (int k = 0; k < D; ++k) sum[k] += (T)a.cw[d >> 1] * Uu[(size_t)k * ld + nb[d]];
             }
           }
           T t[D], z[D];
@@ -424,7 +425,7 @@ __global__ void __launch_bounds__(MRHS_THREADS, (sizeof(T) == 4 || D <= 4) ? 2 :
     for (int d = 0; d < 6; ++d)
       if (nb[d] >= 0) {
 #pragma unroll
-        for (int k = 0; k < D; ++k) out[k] += v[d][k];
+        for (int k = 0; k < D; ++k) out[k] += (T)a.cw[d >> 1] * v[d][k];
       }
   };
   // red voxels of the selected right-hand sides: U = Dg^-1 (scale .* sum of the neighbours' U)
@@ -1041,17 +1042,18 @@ __global__ void k_probe_traces(ProbeArgs a, double* part) {
       yn[k] = (double)y[(size_t)k * a.ld + n];
       sum[k] = 0.0;
     }
-    int deg = 0;
+    double deg = 0.0;
     for (int d = 0; d < a.ndir; ++d) {
       const int m = a.nbr[(size_t)d * a.ld + n];
       if (m >= 0) {
-        ++deg;
+        const double cd = a.cw[d >> 1];
+        deg += cd;
 #pragma unroll
-        for (int k = 0; k < D; ++k) sum[k] += (double)y[(size_t)k * a.ld + m];
+        for (int k = 0; k < D; ++k) sum[k] += cd * (double)y[(size_t)k * a.ld + m];
       }
     }
 #pragma unroll
-    for (int k = 0; k < D; ++k) c[k] = t[k] * ((double)deg * yn[k] - sum[k]);
+    for (int k = 0; k < D; ++k) c[k] = t[k] * (deg * yn[k] - sum[k]);
   }
 #pragma unroll
   for (int k = 0; k < D; ++k) sh[threadIdx.x][k] = c[k];

@@ -37,10 +37,11 @@ __device__ __forceinline__ double ldx(const double* p) { return __ldcg(p); }
 
 __device__ __forceinline__ float ldx(const float* p) { return __ldcg(p); }
 
-// out = B v + s .* (deg v - sum_m V[m])  (B packed, entry e at Bp[e * bs]); element type T.
+// out = B v + s .* (deg v - sum_m c_m V[m])  (B packed, entry e at Bp[e * bs]; c: the edge
+// weight of each neighbour slot, deg their sum over the in-mask neighbours); element type T.
 template <int D, typename T>
 __device__ __forceinline__ void amul(const T* __restrict__ Bp, int bs, const T* s,
-                                     const int* nb, int ndir, T degT, const T* v,
+                                     const int* nb, const T* cw6, T degT, const T* v,
                                      const T* V, size_t ld, T* out) {
 #pragma unroll
   for (int i = 0; i < D; ++i) {
@@ -54,22 +55,29 @@ __device__ __forceinline__ void amul(const T* __restrict__ Bp, int bs, const T* 
   for (int k = 0; k < D; ++k) sum[k] = T(0);
 #pragma unroll
   for (int d = 0; d < 6; ++d) {
-    if (d < ndir && nb[d] >= 0) {
+    if (nb[d] >= 0) {
 #pragma unroll
-      for (int k = 0; k < D; ++k) sum[k] += ldx(V + (size_t)k * ld + nb[d]);
+      for (int k = 0; k < D; ++k) sum[k] += cw6[d] * ldx(V + (size_t)k * ld + nb[d]);
     }
   }
 #pragma unroll
   for (int k = 0; k < D; ++k) out[k] += s[k] * (degT * v[k] - sum[k]);
 }
 
-// number of in-mask neighbours, in the element type (converted once per voxel)
+// weighted number of in-mask neighbours (slots past the neighbourhood hold -1)
 template <typename T>
-__device__ __forceinline__ T degree_of(const int* nb, int ndir) {
-  int deg = 0;
+__device__ __forceinline__ T degree_of(const int* nb, const T* cw6) {
+  T deg = T(0);
 #pragma unroll
-  for (int d = 0; d < 6; ++d) deg += (d < ndir && nb[d] >= 0) ? 1 : 0;
-  return (T)deg;
+  for (int d = 0; d < 6; ++d) deg += nb[d] >= 0 ? cw6[d] : T(0);
+  return deg;
+}
+
+// the edge weight of each neighbour slot (-x, +x, -y, +y, -z, +z) in element type T
+template <typename T>
+__device__ __forceinline__ void slot_weights(const PcgArgs& a, T* cw6) {
+#pragma unroll
+  for (int d = 0; d < 6; ++d) cw6[d] = (T)a.cw[d >> 1];
 }
 
 // z = (L L')^-1 r with L packed lower (inverted diagonal), entry e at Lp[e * bs].
@@ -189,7 +197,7 @@ __device__ __forceinline__ void ssor_phase(const PcgArgs& a, const T* s, const T
   for (int d = 0; d < 6; ++d) {
     if (nb[d] >= 0) {
 #pragma unroll
-      for (int k = 0; k < D; ++k) sum[k] += ldx(U + (size_t)k * ld + nb[d]);
+      for (int k = 0; k < D; ++k) sum[k] += (T)a.cw[d >> 1] * ldx(U + (size_t)k * ld + nb[d]);
     }
   }
   T t[D], z[D];
@@ -273,7 +281,7 @@ __device__ __forceinline__ bool resident_ssor_phases(const PcgArgs& a, Bar& bar,
       for (int d = 0; d < 6; ++d) {
         if (nb[d] >= 0) {
 #pragma unroll
-          for (int k = 0; k < D; ++k) sum[k] += ldx(U + (size_t)k * a.ld + nb[d]);
+          for (int k = 0; k < D; ++k) sum[k] += (T)a.cw[d >> 1] * ldx(U + (size_t)k * a.ld + nb[d]);
         }
       }
 #pragma unroll
@@ -297,6 +305,14 @@ __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_res(PcgArgs a) {
   extern __shared__ double smem[];
   __shared__ Shared sh;
   grid_barrier_start(a.bar);
+  // per-slot edge weights in shared memory (read as broadcasts; no registers held)
+  __shared__ double cwd[6];
+  __shared__ float cwf[6];
+  if (threadIdx.x == 0) {
+    slot_weights(a, cwd);
+    slot_weights(a, cwf);
+  }
+  __syncthreads();
   constexpr int NT = ntri(D);
   const int bd = blockDim.x, t = threadIdx.x;
   double* shB = smem;
@@ -318,7 +334,7 @@ __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_res(PcgArgs a) {
   int nb[6];
 #pragma unroll
   for (int d = 0; d < 6; ++d) nb[d] = (own && d < a.ndir) ? __ldg(a.nbr + (size_t)d * ld + n) : -1;
-  const double degd = degree_of<double>(nb, a.ndir);
+  const double degd = degree_of<double>(nb, cwd);
   double s[D], x[D], r[D], u[D], w[D], p[D], q[D], bv[D];
 #pragma unroll
   for (int k = 0; k < D; ++k) {
@@ -343,7 +359,7 @@ __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_res(PcgArgs a) {
   // (r, u, w) from the current x, with partials (r'u, w'u, r'r, b'b)
   auto restart = [&](double* tot) -> bool {
     double ax[D];
-    amul<D, double>(Bp, bd, s, nb, a.ndir, degd, x, a.x, ld, ax);
+    amul<D, double>(Bp, bd, s, nb, cwd, degd, x, a.x, ld, ax);
 #pragma unroll
     for (int k = 0; k < D; ++k) r[k] = bv[k] - ax[k];
     // SSOR phase 1 (red voxels only: the black ones are overwritten by phase 2 before
@@ -364,7 +380,7 @@ __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_res(PcgArgs a) {
     }
     if (a.ssor && !ssor_phases()) return false;
     if (!bar()) return false;
-    amul<D, double>(Bp, bd, s, nb, a.ndir, degd, u, a.u, ld, w);
+    amul<D, double>(Bp, bd, s, nb, cwd, degd, u, a.u, ld, w);
     double v[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
     for (int k = 0; k < D; ++k) {
@@ -419,7 +435,7 @@ __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_res(PcgArgs a) {
     }
     if (a.ssor && !ssor_phases()) return;
     if (!bar()) return;
-    amul<D, double>(Bp, bd, s, nb, a.ndir, degd, u, a.u, ld, w);
+    amul<D, double>(Bp, bd, s, nb, cwd, degd, u, a.u, ld, w);
     double v[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
     for (int k = 0; k < D; ++k) {
@@ -490,6 +506,14 @@ __global__ void __launch_bounds__(RB_MAX_THREADS, 1) k_pcg_rb(PcgArgs a) {
   extern __shared__ double smem[];
   __shared__ Shared sh;
   grid_barrier_start(a.bar);
+  // per-slot edge weights in shared memory (read as broadcasts; no registers held)
+  __shared__ double cwd[6];
+  __shared__ float cwf[6];
+  if (threadIdx.x == 0) {
+    slot_weights(a, cwd);
+    slot_weights(a, cwf);
+  }
+  __syncthreads();
   constexpr int NT = ntri(D);
   const int bd = blockDim.x, t = threadIdx.x;
   double* shB = smem;
@@ -512,7 +536,7 @@ __global__ void __launch_bounds__(RB_MAX_THREADS, 1) k_pcg_rb(PcgArgs a) {
   int nb[6];
 #pragma unroll
   for (int d = 0; d < 6; ++d) nb[d] = (own && d < a.ndir) ? __ldg(a.nbr + (size_t)d * ld + n) : -1;
-  const double degd = degree_of<double>(nb, a.ndir);
+  const double degd = degree_of<double>(nb, cwd);
   // b is read from memory where it is needed (start, red recovery, true residual): the
   // black voxels' registers hold b^ instead
   // the prior scale is the same for every voxel: one shared copy instead of D registers
@@ -554,7 +578,7 @@ __global__ void __launch_bounds__(RB_MAX_THREADS, 1) k_pcg_rb(PcgArgs a) {
     for (int d = 0; d < 6; ++d) {
       if (nb[d] >= 0) {
 #pragma unroll
-        for (int k = 0; k < D; ++k) sum[k] += ldx(U + (size_t)k * ld + nb[d]);
+        for (int k = 0; k < D; ++k) sum[k] += cwd[d] * ldx(U + (size_t)k * ld + nb[d]);
       }
     }
 #pragma unroll
@@ -571,7 +595,7 @@ __global__ void __launch_bounds__(RB_MAX_THREADS, 1) k_pcg_rb(PcgArgs a) {
       publish(y);
     }
     if (!bar()) return false;
-    if (black) amul<D, double>(Bp, bd, s, nb, a.ndir, degd, v, U, ld, out);
+    if (black) amul<D, double>(Bp, bd, s, nb, cwd, degd, v, U, ld, out);
     return true;
   };
   // red voxels: x_r from the black voxels' x (one barrier); then every voxel's x is final
@@ -620,7 +644,7 @@ __global__ void __launch_bounds__(RB_MAX_THREADS, 1) k_pcg_rb(PcgArgs a) {
     double ax[D], bv[D], v[4] = {0.0, 0.0, 0.0, 0.0};
     if (own) {
       load_b(bv);
-      amul<D, double>(Bp, bd, s, nb, a.ndir, degd, x, a.x, ld, ax);
+      amul<D, double>(Bp, bd, s, nb, cwd, degd, x, a.x, ld, ax);
 #pragma unroll
       for (int k = 0; k < D; ++k) v[2] += (bv[k] - ax[k]) * (bv[k] - ax[k]);
     }
@@ -643,7 +667,7 @@ __global__ void __launch_bounds__(RB_MAX_THREADS, 1) k_pcg_rb(PcgArgs a) {
     for (int d = 0; d < 6; ++d) {
       if (nb[d] >= 0) {
 #pragma unroll
-        for (int k = 0; k < D; ++k) sum[k] += ldx(U + (size_t)k * ld + nb[d]);
+        for (int k = 0; k < D; ++k) sum[k] += cwd[d] * ldx(U + (size_t)k * ld + nb[d]);
       }
     }
     double bv[D];
@@ -744,6 +768,14 @@ template <int D>
 __global__ void __launch_bounds__(PCG_THREADS) k_pcg_stream(PcgArgs a) {
   __shared__ Shared sh;
   grid_barrier_start(a.bar);
+  // per-slot edge weights in shared memory (read as broadcasts; no registers held)
+  __shared__ double cwd[6];
+  __shared__ float cwf[6];
+  if (threadIdx.x == 0) {
+    slot_weights(a, cwd);
+    slot_weights(a, cwf);
+  }
+  __syncthreads();
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   const int nth = gridDim.x * blockDim.x;
   const size_t ld = a.ld;
@@ -792,7 +824,7 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_stream(PcgArgs a) {
       double xn[D], ax[D], rn[D], un[D];
 #pragma unroll
       for (int k = 0; k < D; ++k) xn[k] = ldx(a.x + (size_t)k * ld + n);
-      amul<D, double>(a.blocks + n, (int)ld, s, nb, a.ndir, degree_of<double>(nb, a.ndir), xn, a.x, ld, ax);
+      amul<D, double>(a.blocks + n, (int)ld, s, nb, cwd, degree_of<double>(nb, cwd), xn, a.x, ld, ax);
 #pragma unroll
       for (int k = 0; k < D; ++k) rn[k] = __ldg(a.b + (size_t)k * ld + n) - ax[k];
       precond(n, rn, un);
@@ -813,7 +845,7 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_stream(PcgArgs a) {
       double un[D], wn[D];
 #pragma unroll
       for (int k = 0; k < D; ++k) un[k] = U[(size_t)k * ld + n];
-      amul<D, double>(a.blocks + n, (int)ld, s, nb, a.ndir, degree_of<double>(nb, a.ndir), un, U, ld, wn);
+      amul<D, double>(a.blocks + n, (int)ld, s, nb, cwd, degree_of<double>(nb, cwd), un, U, ld, wn);
 #pragma unroll
       for (int k = 0; k < D; ++k) {
         const double rk = R[(size_t)k * ld + n], bk = __ldg(a.b + (size_t)k * ld + n);
@@ -889,7 +921,7 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_stream(PcgArgs a) {
         un[k] = U[(size_t)k * ld + n];
         rk[k] = R[(size_t)k * ld + n];
       }
-      amul<D, double>(a.blocks + n, (int)ld, s, nb, a.ndir, degree_of<double>(nb, a.ndir), un, U, ld, wn);
+      amul<D, double>(a.blocks + n, (int)ld, s, nb, cwd, degree_of<double>(nb, cwd), un, U, ld, wn);
 #pragma unroll
       for (int k = 0; k < D; ++k) {
         v[0] += rk[k] * un[k];
@@ -940,6 +972,14 @@ __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_mixed_res(PcgArgs a)
   extern __shared__ double smem[];
   __shared__ Shared sh;
   grid_barrier_start(a.bar);
+  // per-slot edge weights in shared memory (read as broadcasts; no registers held)
+  __shared__ double cwd[6];
+  __shared__ float cwf[6];
+  if (threadIdx.x == 0) {
+    slot_weights(a, cwd);
+    slot_weights(a, cwf);
+  }
+  __syncthreads();
   constexpr int NT = ntri(D);
   const int bd = blockDim.x, t = threadIdx.x;
   double* shB = smem;                                   // [NT][bd] FP64 blocks
@@ -963,7 +1003,7 @@ __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_mixed_res(PcgArgs a)
   int nb[6];
 #pragma unroll
   for (int d = 0; d < 6; ++d) nb[d] = (own && d < a.ndir) ? __ldg(a.nbr + (size_t)d * ld + n) : -1;
-  const double degd = degree_of<double>(nb, a.ndir);
+  const double degd = degree_of<double>(nb, cwd);
   const float degf = (float)degd;
   double s[D], x[D], bv[D];
   float s32[D];
@@ -989,7 +1029,7 @@ __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_mixed_res(PcgArgs a)
     double r64[D];
     {
       double ax[D];
-      amul<D, double>(Bp, bd, s, nb, a.ndir, degd, x, a.x, ld, ax);
+      amul<D, double>(Bp, bd, s, nb, cwd, degd, x, a.x, ld, ax);
       double v[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
       for (int k = 0; k < D; ++k) {
@@ -1043,7 +1083,7 @@ __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_mixed_res(PcgArgs a)
     if (a.ssor && !resident_ssor_phases<D, float>(a, bar, own, is_red, nb, s32, Mp32, bd, n, r, u, a.u32))
       return;
     if (!bar()) return;
-    amul<D, float>(Bp32, bd, s32, nb, a.ndir, degf, u, a.u32, ld, w);
+    amul<D, float>(Bp32, bd, s32, nb, cwf, degf, u, a.u32, ld, w);
     {
       float g = 0.f, dl = 0.f, q2 = 0.f;
 #pragma unroll
@@ -1087,7 +1127,7 @@ __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_mixed_res(PcgArgs a)
       if (a.ssor && !resident_ssor_phases<D, float>(a, bar, own, is_red, nb, s32, Mp32, bd, n, r, u, a.u32))
         return;
       if (!bar()) return;
-      amul<D, float>(Bp32, bd, s32, nb, a.ndir, degf, u, a.u32, ld, w);
+      amul<D, float>(Bp32, bd, s32, nb, cwf, degf, u, a.u32, ld, w);
       float g = 0.f, dl = 0.f, q2 = 0.f;
 #pragma unroll
       for (int k = 0; k < D; ++k) {
@@ -1144,6 +1184,14 @@ __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_mixed_rb(PcgArgs a) 
   extern __shared__ double smem[];
   __shared__ Shared sh;
   grid_barrier_start(a.bar);
+  // per-slot edge weights in shared memory (read as broadcasts; no registers held)
+  __shared__ double cwd[6];
+  __shared__ float cwf[6];
+  if (threadIdx.x == 0) {
+    slot_weights(a, cwd);
+    slot_weights(a, cwf);
+  }
+  __syncthreads();
   constexpr int NT = ntri(D);
   const int bd = blockDim.x, t = threadIdx.x;
   double* shB = smem;                                   // [NT][bd] FP64 blocks
@@ -1167,7 +1215,7 @@ __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_mixed_rb(PcgArgs a) 
   int nb[6];
 #pragma unroll
   for (int d = 0; d < 6; ++d) nb[d] = (own && d < a.ndir) ? __ldg(a.nbr + (size_t)d * ld + n) : -1;
-  const double degd = degree_of<double>(nb, a.ndir);
+  const double degd = degree_of<double>(nb, cwd);
   const float degf = (float)degd;
   double s[D], x[D], bv[D];
   float s32[D];
@@ -1199,7 +1247,7 @@ __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_mixed_rb(PcgArgs a) 
     for (int d = 0; d < 6; ++d) {
       if (nb[d] >= 0) {
 #pragma unroll
-        for (int k = 0; k < D; ++k) sum[k] += ldx(U + (size_t)k * ld + nb[d]);
+        for (int k = 0; k < D; ++k) sum[k] += cwf[d] * ldx(U + (size_t)k * ld + nb[d]);
       }
     }
 #pragma unroll
@@ -1216,7 +1264,7 @@ __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_mixed_rb(PcgArgs a) 
       publish(y);
     }
     if (!bar()) return false;
-    if (black) amul<D, float>(Bp32, bd, s32, nb, a.ndir, degf, v, U, ld, out);
+    if (black) amul<D, float>(Bp32, bd, s32, nb, cwf, degf, v, U, ld, out);
     return true;
   };
   double tot[4];
@@ -1227,7 +1275,7 @@ __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_mixed_rb(PcgArgs a) 
     double r64[D];
     {
       double ax[D];
-      amul<D, double>(Bp, bd, s, nb, a.ndir, degd, x, a.x, ld, ax);
+      amul<D, double>(Bp, bd, s, nb, cwd, degd, x, a.x, ld, ax);
       double v[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
       for (int k = 0; k < D; ++k) {
@@ -1281,7 +1329,7 @@ __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_mixed_rb(PcgArgs a) 
       for (int dd = 0; dd < 6; ++dd) {
         if (nb[dd] >= 0) {
 #pragma unroll
-          for (int k = 0; k < D; ++k) sum[k] += ldx(U + (size_t)k * ld + nb[dd]);
+          for (int k = 0; k < D; ++k) sum[k] += cwf[dd] * ldx(U + (size_t)k * ld + nb[dd]);
         }
       }
 #pragma unroll
@@ -1377,6 +1425,14 @@ template <int D>
 __global__ void __launch_bounds__(PCG_THREADS) k_pcg_mixed_stream(PcgArgs a) {
   __shared__ Shared sh;
   grid_barrier_start(a.bar);
+  // per-slot edge weights in shared memory (read as broadcasts; no registers held)
+  __shared__ double cwd[6];
+  __shared__ float cwf[6];
+  if (threadIdx.x == 0) {
+    slot_weights(a, cwd);
+    slot_weights(a, cwf);
+  }
+  __syncthreads();
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   const int nth = gridDim.x * blockDim.x;
   const size_t ld = a.ld;
@@ -1428,7 +1484,7 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_mixed_stream(PcgArgs a) {
         un[k] = a.u32[(size_t)k * ld + n];
         rk[k] = a.r32[(size_t)k * ld + n];
       }
-      amul<D, float>(a.blocks32 + n, (int)ld, s32, nb, a.ndir, degree_of<float>(nb, a.ndir), un, a.u32, ld, wn);
+      amul<D, float>(a.blocks32 + n, (int)ld, s32, nb, cwf, degree_of<float>(nb, cwf), un, a.u32, ld, wn);
       float g = 0.f, dl = 0.f, q2 = 0.f;
 #pragma unroll
       for (int k = 0; k < D; ++k) {
@@ -1456,7 +1512,7 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_mixed_stream(PcgArgs a) {
         double xn[D], ax[D];
 #pragma unroll
         for (int k = 0; k < D; ++k) xn[k] = ldx(a.x + (size_t)k * ld + n);
-        amul<D, double>(a.blocks + n, (int)ld, s, nb, a.ndir, degree_of<double>(nb, a.ndir), xn, a.x, ld, ax);
+        amul<D, double>(a.blocks + n, (int)ld, s, nb, cwd, degree_of<double>(nb, cwd), xn, a.x, ld, ax);
         float rn[D], un[D];
 #pragma unroll
         for (int k = 0; k < D; ++k) {

@@ -142,12 +142,13 @@ __global__ void __launch_bounds__(SVB_THREADS) k_svb_quad(SvbArgs a, const doubl
     for (int d = 0; d < a.g.ndir / 2; ++d) {
       const int m = __ldg(a.g.nbr + (size_t)(2 * d + 1) * ld + n);
       if (m < 0) continue;
+      const double c = a.g.cw[d];
       for (int j = 0; j < a.S; ++j) {
         const double* v = V + (size_t)j * D * ld;
 #pragma unroll
         for (int k = 0; k < D; ++k) {
           const double df = v[(size_t)k * ld + n] - v[(size_t)k * ld + m];
-          acc[k] += df * df;
+          acc[k] += c * df * df;
         }
       }
     }

@@ -30,6 +30,8 @@ struct Geometry {
   const int* nbr;     // [6][ld]
   const int* lin;     // [ld] lattice-linear index of each voxel
   int stride[3];      // lattice-linear strides of +x, +y, +z
+  double cw[3];       // edge weights of the x, y, z directions (weighted graph Laplacian;
+                      // 1, 1, 1 is the UGL prior); neighbour slot d has weight cw[d / 2]
 };
 
 // ---------------------------------------------------------------------------------------
@@ -44,13 +46,15 @@ __device__ __forceinline__ void add_edge_noise(const Geometry& g, const Rng& rng
   for (int d = 0; d < g.ndir / 2; ++d) {
     if (__ldg(g.nbr + (size_t)(2 * d + 1) * g.ld + n) >= 0) {
       site_normals<D>(rng, (uint32_t)lin * 4u + (uint32_t)d, z);
+      const double c = sqrt(g.cw[d]);
 #pragma unroll
-      for (int k = 0; k < D; ++k) rhs[k] += sq[k] * z[k];
+      for (int k = 0; k < D; ++k) rhs[k] += c * sq[k] * z[k];
     }
     if (__ldg(g.nbr + (size_t)(2 * d) * g.ld + n) >= 0) {
       site_normals<D>(rng, (uint32_t)(lin - g.stride[d]) * 4u + (uint32_t)d, z);
+      const double c = sqrt(g.cw[d]);
 #pragma unroll
-      for (int k = 0; k < D; ++k) rhs[k] -= sq[k] * z[k];
+      for (int k = 0; k < D; ++k) rhs[k] -= c * sq[k] * z[k];
     }
   }
 }
@@ -73,9 +77,10 @@ __device__ __forceinline__ void add_edge_terms(const Geometry& g, const double* 
   }
 }
 
-__device__ __forceinline__ int degree(const Geometry& g, int n) {
-  int deg = 0;
-  for (int d = 0; d < g.ndir; ++d) deg += __ldg(g.nbr + (size_t)d * g.ld + n) >= 0 ? 1 : 0;
+// weighted degree: sum of the edge weights of the in-mask neighbours
+__device__ __forceinline__ double degree(const Geometry& g, int n) {
+  double deg = 0.0;
+  for (int d = 0; d < g.ndir; ++d) deg += __ldg(g.nbr + (size_t)d * g.ld + n) >= 0 ? g.cw[d >> 1] : 0.0;
   return deg;
 }
 

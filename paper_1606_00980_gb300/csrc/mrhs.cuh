@@ -89,6 +89,7 @@ struct MrhsArgs {
   // CG on the red-black reduced system instead (plain solves, FP64): needs mfac, the colour
   // lists and at most one (RHS, chunk) unit per warp (S <= warps of the grid)
   int reduced;
+  double cw[3];          // edge weights of the x, y, z directions (1, 1, 1: UGL prior)
 };
 
 // Probe set-up and post-processing (log-determinant and trace probes).
@@ -106,6 +107,7 @@ struct ProbeArgs {
   void* b;              // [S][D][ld]
   void* x;              // [S][D][ld]
   Rng rng;              // tag in c3's top byte; the probe index is the stream
+  double cw[3];         // edge weights of the x, y, z directions
 };
 // what: 0 = probe right-hand sides b_i = L v_i and x_i = 0; 1 = per-voxel log det of the
 // preconditioner into out[N]; 2 = trace partials into out[grid.x][S][D] (grid.x = ceil(N/128)).

@@ -75,6 +75,7 @@ struct PcgArgs {
   // voxels) with the block factors mfac, equivalent to SSOR with omega = 1; the other
   // variants run that SSOR form instead (ssor = 1, omega = 1 must be set alongside)
   int reduced;
+  double cw[3];          // edge weights of the x, y, z directions (1, 1, 1: UGL prior)
 };
 
 // Launches the cooperative persistent PCG kernel for dimension D (1..12) on `stream`.

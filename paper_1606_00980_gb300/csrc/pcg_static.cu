@@ -152,6 +152,7 @@ bfmri_status bfmri_pcg_solve_static(int N, int D, int neighbourhood, const int* 
   a.N = N;
   a.ld = ld;
   a.ndir = neighbourhood;
+  a.cw[0] = a.cw[1] = a.cw[2] = 1.0;   // the UGL prior
   a.nbr = nbr;
   a.blocks = blocks;
   a.mfac = nullptr;

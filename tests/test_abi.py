@@ -50,6 +50,7 @@ def test_default_options_without_gpu(lib):
     assert (o.q1, o.q2, o.u1, o.u2, o.r1, o.r2) == (10.0, 0.1, 10.0, 0.1, 10000.0, 0.1)
     assert o.delta == 1e-8 and o.precond == bfmri.PRECOND_BLOCK_JACOBI
     assert o.debug_skip_block == -1 and o.inner_tol == 1e-6 and o.ssor_omega == 1.0
+    assert list(o.edge_weight) == [1.0, 1.0, 1.0]
 
 
 def test_create_rejects_bad_arguments_without_touching_the_gpu(lib):
@@ -69,7 +70,8 @@ def test_create_rejects_bad_arguments_without_touching_the_gpu(lib):
                                torch_memory=False)
         assert ei.value.status == -1
     for fields in (dict(precond=2, ssor_omega=2.0), dict(precond=2, ssor_omega=0.0),
-                   dict(precond=4)):
+                   dict(precond=4), dict(edge_weight=(1.0, 0.0, 1.0)),
+                   dict(edge_weight=(1.0, 1.0, float("inf")))):
         o = bfmri.bfmri_default_options()
         for k, v in fields.items():
             setattr(o, k, v)
