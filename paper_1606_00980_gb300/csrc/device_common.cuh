@@ -398,34 +398,14 @@ __device__ __forceinline__ void block_reduce4(const double* v, double* sh, doubl
 // CTA passes before every CTA has read the earlier rows. part0 and part1 hold gridDim.x rows
 // of 4 doubles each. sh needs 4 * 32 + 8 doubles, sh_int 2 ints.
 // ---------------------------------------------------------------------------------------
-__device__ __forceinline__ bool grid_allreduce4(const GridBarrier& b, double* part0, double* part1,
-                                                const double* v, double* sh, int* sh_int, double* out) {
-  double bt[4];
-  block_reduce4(v, sh, bt);
+// Sums the rows of a partial buffer that every CTA wrote before a barrier this CTA has
+// passed, in a fixed order, so every CTA obtains bit-identical totals; every thread receives
+// them in out. sh needs 4 * 32 + 8 doubles.
+__device__ __forceinline__ void allreduce4_collect(const double* part, double* sh, double* out) {
   const int l = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned int nblocks = gridDim.x;
-  if (threadIdx.x == 0) {
-    const unsigned int g0 = g_bar_gen;
-    double* part = (g0 & 1u) ? part1 : part0;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) part[(size_t)blockIdx.x * 4 + i] = bt[i];
-    const unsigned int arrived = atom_add_acq_rel(b.count, 1u);
-    bool ok = true;
-    if (arrived == nblocks - 1) {
-      st_relaxed(b.count, 0u);
-      red_add_release(b.gen, 1u);
-    } else {
-      ok = wait_generation(b, g0);
-    }
-    g_bar_gen = g0 + 1u;
-    sh_int[0] = ok ? 0 : 1;
-    sh_int[1] = (int)(g0 & 1u);
-  }
-  __syncthreads();
-  const bool good = sh_int[0] == 0;
   double* sh_out = sh + 132;
-  const double* part = sh_int[1] ? part1 : part0;
-  if (good && blockDim.x >= 128) {
+  if (blockDim.x >= 128) {
     // warp j < 4 sums value j: lane l over rows l + 32 i (5 rows per lane and round, as a
     // fixed pairwise tree), then a butterfly; the four warps run on different SM sub-partitions
     if (warp < 4) {
@@ -444,7 +424,7 @@ __device__ __forceinline__ bool grid_allreduce4(const GridBarrier& b, double* pa
       for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
       if (l == 0) sh_out[warp] = acc;
     }
-  } else if (good && warp == 0) {
+  } else if (warp == 0) {
     // lane l sums value (l & 3) over rows (l >> 2) + 8 i (20 rows per lane and round)
     const int j = l & 3;
     constexpr int RU = 20;
@@ -471,7 +451,51 @@ __device__ __forceinline__ bool grid_allreduce4(const GridBarrier& b, double* pa
 #pragma unroll
   for (int i = 0; i < 4; ++i) out[i] = sh_out[i];
   __syncthreads();
-  return good;
+}
+
+__device__ __forceinline__ bool grid_allreduce4(const GridBarrier& b, double* part0, double* part1,
+                                                const double* v, double* sh, int* sh_int, double* out) {
+  double bt[4];
+  block_reduce4(v, sh, bt);
+  const unsigned int nblocks = gridDim.x;
+  if (threadIdx.x == 0) {
+    const unsigned int g0 = g_bar_gen;
+    double* part = (g0 & 1u) ? part1 : part0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) part[(size_t)blockIdx.x * 4 + i] = bt[i];
+    const unsigned int arrived = atom_add_acq_rel(b.count, 1u);
+    bool ok = true;
+    if (arrived == nblocks - 1) {
+      st_relaxed(b.count, 0u);
+      red_add_release(b.gen, 1u);
+    } else {
+      ok = wait_generation(b, g0);
+    }
+    g_bar_gen = g0 + 1u;
+    sh_int[0] = ok ? 0 : 1;
+    sh_int[1] = (int)(g0 & 1u);
+  }
+  __syncthreads();
+  const bool good = sh_int[0] == 0;
+  if (!good) return false;
+  allreduce4_collect(sh_int[1] ? part1 : part0, sh, out);
+  return true;
+}
+
+// Split form: the CTA's block totals of v go to the row buffer of the current barrier
+// generation before a plain grid barrier (grid_sync); after that barrier, allreduce4_collect
+// on the returned buffer gives the totals. The collection must finish before the CTA arrives
+// at the following barrier (the buffers alternate with the generation).
+__device__ __forceinline__ const double* allreduce4_post(double* part0, double* part1,
+                                                         const double* v, double* sh) {
+  double bt[4];
+  block_reduce4(v, sh, bt);   // ends with __syncthreads: every thread sees g_bar_gen
+  double* part = (g_bar_gen & 1u) ? part1 : part0;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) part[(size_t)blockIdx.x * 4 + i] = bt[i];
+  }
+  return part;
 }
 
 // ---------------------------------------------------------------------------------------

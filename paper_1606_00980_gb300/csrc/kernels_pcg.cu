@@ -1172,6 +1172,283 @@ __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_mixed_res(PcgArgs a)
 }
 
 // ---------------------------------------------------------------------------------------
+// Pipelined CG (Ghysels & Vanroose 2014, preconditioned form) on the same reduced system:
+// with the extra recurrences q = M^-1 s and z = A q, the two inner products of iteration i
+// are formed from r_i, u_i, w_i before its matrix product, so their reduction completes at
+// the product's first barrier and the reducing barrier disappears: two grid barriers per
+// iteration instead of three. Per iteration (black voxels; M = Dg_b, A = S):
+//   gamma = r'u, delta = w'u  (posted)            m = M^-1 w  (published)
+//   --- barrier: the partials and m are visible --- red phase of S m; every CTA sums the
+//   partials in a fixed order and forms alpha, beta as Chronopoulos & Gear do
+//   --- barrier ---  n = S m (black phase)
+//   z = n + beta z, q = m + beta q, s = w + beta s, p = u + beta p,
+//   x += alpha p, r -= alpha s, u -= alpha q, w -= alpha z.
+// The stop test reads ||r_i|| one product earlier than the unpipelined form (the same
+// iterates); the stop is confirmed on B~'s true residual as in k_pcg_rb. p, s, q, z live in
+// shared memory (D <= 6 fits next to the blocks, factors and b^).
+// ---------------------------------------------------------------------------------------
+template <int D>
+__global__ void __launch_bounds__(RB_MAX_THREADS, 1) k_pcg_rbp(PcgArgs a) {
+  extern __shared__ double smem[];
+  __shared__ Shared sh;
+  grid_barrier_start(a.bar);
+  __shared__ double cwd[6];
+  if (threadIdx.x == 0) slot_weights(a, cwd);
+  __syncthreads();
+  constexpr int NT = ntri(D);
+  const int bd = blockDim.x, t = threadIdx.x;
+  double* shB = smem;
+  double* shM = smem + NT * bd;
+  double* shH = smem + 2 * NT * bd;   // b^
+  double* shP = shH + D * bd;         // p
+  double* shS = shP + D * bd;         // s = A p
+  double* shQ = shS + D * bd;         // q = M^-1 s
+  double* shZ = shQ + D * bd;         // z = A q
+  int n = blockIdx.x * a.res_per + t;
+  bool own = t < a.res_per && n < a.N;
+  bool is_red = true;
+  colour_sort(a, n, own, is_red);
+  const bool red = own && is_red, black = own && !is_red;
+  const size_t ld = a.ld;
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int j = 0; j <= i; ++j) {
+      const int e = tri(i, j);
+      shB[e * bd + t] = own ? __ldg(a.blocks + (size_t)e * ld + n) : (i == j ? 1.0 : 0.0);
+      shM[e * bd + t] = own ? __ldg(a.mfac + (size_t)e * ld + n) : (i == j ? 1.0 : 0.0);
+    }
+  int nb[6];
+#pragma unroll
+  for (int d = 0; d < 6; ++d) nb[d] = (own && d < a.ndir) ? __ldg(a.nbr + (size_t)d * ld + n) : -1;
+  const double degd = degree_of<double>(nb, cwd);
+  __shared__ double s[RES_MAX_D];
+  if (t < D) s[t] = __ldg(a.scale + t);
+  __syncthreads();
+  double x[D], r[D], u[D], w[D];
+  auto load_b = [&](double* bv) {
+#pragma unroll
+    for (int k = 0; k < D; ++k) bv[k] = own ? __ldg(a.b + (size_t)k * ld + n) : 0.0;
+  };
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    x[k] = own ? a.x[(size_t)k * ld + n] : 0.0;
+    r[k] = u[k] = w[k] = 0.0;
+    shH[k * bd + t] = 0.0;
+  }
+  const double* Bp = shB + t;
+  const double* Mp = shM + t;
+  double* U = a.u;
+  auto bar = [&]() -> bool {
+    if (a.skip_block == (int)blockIdx.x) return false;
+    return grid_sync(a.bar, &sh.flag);
+  };
+  auto publish = [&](const double* v) {
+#pragma unroll
+    for (int k = 0; k < D; ++k) U[(size_t)k * ld + n] = v[k];
+  };
+  auto red_solve = [&](const double* c, double* out) {
+    double sum[D], tv[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) sum[k] = 0.0;
+#pragma unroll
+    for (int d = 0; d < 6; ++d) {
+      if (nb[d] >= 0) {
+#pragma unroll
+        for (int k = 0; k < D; ++k) sum[k] += cwd[d] * ldx(U + (size_t)k * ld + nb[d]);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < D; ++k) tv[k] = (c ? c[k] : 0.0) + s[k] * sum[k];
+    minv<D, double>(Mp, bd, tv, out);
+  };
+  auto apply_S = [&](const double* v, double* out) -> bool {
+    if (black) publish(v);
+    if (!bar()) return false;
+    if (red) {
+      double y[D];
+      red_solve(nullptr, y);
+      publish(y);
+    }
+    if (!bar()) return false;
+    if (black) amul<D, double>(Bp, bd, s, nb, cwd, degd, v, U, ld, out);
+    return true;
+  };
+  auto recover_red = [&]() -> bool {
+    if (black) publish(x);
+    if (!bar()) return false;
+    if (red) {
+      double bv[D];
+      load_b(bv);
+      red_solve(bv, x);
+    }
+    return true;
+  };
+  auto true_residual = [&](double* tot) -> bool {
+    if (own) {
+#pragma unroll
+      for (int k = 0; k < D; ++k) a.x[(size_t)k * ld + n] = x[k];
+    }
+    if (!bar()) return false;
+    double ax[D], bv[D], v[4] = {0.0, 0.0, 0.0, 0.0};
+    if (own) {
+      load_b(bv);
+      amul<D, double>(Bp, bd, s, nb, cwd, degd, x, a.x, ld, ax);
+#pragma unroll
+      for (int k = 0; k < D; ++k) v[2] += (bv[k] - ax[k]) * (bv[k] - ax[k]);
+    }
+    return grid_allreduce4(a.bar, a.part, a.part1, v, sh.red, sh.ints, tot);
+  };
+  // (re)start of the recurrences from the current x_b: r = b^ - S x, u = M^-1 r, w = S u,
+  // p = s = q = z = 0
+  auto restart = [&]() -> bool {
+    double sx[D];
+    if (!apply_S(x, sx)) return false;
+    if (black) {
+#pragma unroll
+      for (int k = 0; k < D; ++k) r[k] = shH[k * bd + t] - sx[k];
+      minv<D, double>(Mp, bd, r, u);
+    }
+    if (!apply_S(u, w)) return false;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      shP[k * bd + t] = 0.0;
+      shS[k * bd + t] = 0.0;
+      shQ[k * bd + t] = 0.0;
+      shZ[k * bd + t] = 0.0;
+    }
+    return true;
+  };
+
+  // b^ = b_b + scale .* sum of the red neighbours' Dg_r^-1 b_r
+  if (red) {
+    double y[D], bv[D];
+    load_b(bv);
+    minv<D, double>(Mp, bd, bv, y);
+    publish(y);
+  }
+  if (!bar()) return;
+  if (black) {
+    double sum[D], bv[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) sum[k] = 0.0;
+#pragma unroll
+    for (int d = 0; d < 6; ++d) {
+      if (nb[d] >= 0) {
+#pragma unroll
+        for (int k = 0; k < D; ++k) sum[k] += cwd[d] * ldx(U + (size_t)k * ld + nb[d]);
+      }
+    }
+    load_b(bv);
+#pragma unroll
+    for (int k = 0; k < D; ++k) shH[k * bd + t] = bv[k] + s[k] * sum[k];
+  }
+  if (!restart()) return;   // (apply_S's first barrier orders the reads of U above)
+  double tot[4];
+  double bb = 0.0, tol2 = 0.0, rel0 = 0.0, rr = 0.0;
+  double alpha = 0.0, beta = 0.0, gam = 0.0, rgam = 0.0, ralpha = 0.0;
+  int it = 0, restarts = 0, status = 0;
+  bool first = true;        // first pass of the solve: the partials carry b'b
+  bool x_final = false;
+  while (true) {
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    if (black) {
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        v[0] += r[k] * u[k];
+        v[1] += w[k] * u[k];
+        v[2] += r[k] * r[k];
+      }
+    }
+    if (first) {
+      double bv[D];
+      load_b(bv);
+#pragma unroll
+      for (int k = 0; k < D; ++k) v[3] += bv[k] * bv[k];
+    }
+    const double* part = allreduce4_post(a.part, a.part1, v, sh.red);
+    double m[D];
+    if (black) {
+      minv<D, double>(Mp, bd, w, m);
+      publish(m);
+    }
+    if (!bar()) return;                 // partials and m are visible everywhere
+    if (red) {
+      double y[D];
+      red_solve(nullptr, y);
+      publish(y);
+    }
+    allreduce4_collect(part, sh.red, tot);   // before the next barrier
+    if (first) {
+      bb = tot[3];
+      tol2 = a.delta * a.delta * bb;
+      rel0 = bb > 0.0 ? sqrt(tot[2] / bb) : 0.0;
+      first = false;
+      if (!(isfinite(tot[0]) && isfinite(tot[1]) && isfinite(bb))) status = 7;
+    }
+    rr = tot[2];
+    if (status == 0 && bb == 0.0) {
+#pragma unroll
+      for (int k = 0; k < D; ++k) x[k] = 0.0;
+      x_final = true;
+    }
+    int code = 0;
+    if (status == 0 && bb != 0.0) {
+      cg_scalar_step(sh, tot[0], tot[1], rr, tol2, it, a.max_iter, alpha, beta, gam, rgam, ralpha);
+      code = sh.code;
+      __syncthreads();
+    }
+    if (!bar()) return;                 // the red phase's y is visible; all partials read
+    if (status != 0 || bb == 0.0) break;
+    if (code == 7) { status = 7; break; }
+    if (code == 3) { status = 3; break; }
+    if (code == 1) {
+      // confirm with the true residual of B~
+      if (!recover_red()) return;
+      if (!true_residual(tot)) return;
+      x_final = true;
+      rr = tot[2];
+      if (rr <= tol2) break;
+      if (it >= a.max_iter) { status = 4; break; }
+      ++restarts;
+      if (!restart()) return;
+      rgam = 0.0;
+      ralpha = 0.0;
+      continue;
+    }
+    if (black) {
+      double nn[D];
+      amul<D, double>(Bp, bd, s, nb, cwd, degd, m, U, ld, nn);   // n = S m
+      const double al = alpha, be = beta;
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        const int o = k * bd + t;
+        const double z = nn[k] + be * shZ[o];
+        const double q = m[k] + be * shQ[o];
+        const double sv = w[k] + be * shS[o];
+        const double p = u[k] + be * shP[o];
+        shZ[o] = z;
+        shQ[o] = q;
+        shS[o] = sv;
+        shP[o] = p;
+        x[k] += al * p;
+        r[k] -= al * sv;
+        u[k] -= al * q;
+        w[k] -= al * z;
+      }
+    }
+    x_final = false;
+    ++it;
+  }
+  if (!x_final && !recover_red()) return;
+  if (own) {
+#pragma unroll
+    for (int k = 0; k < D; ++k) a.x[(size_t)k * ld + n] = x[k];
+  }
+  write_ctrl(a, it, restarts, rr, bb, rel0, status);
+}
+
+// ---------------------------------------------------------------------------------------
 // Mixed precision on the red-black reduced system: the FP64 refinement of k_pcg_mixed_res
 // (true residual r of B~ over every voxel, x += d), each correction d from FP32 CG on the
 // reduced system of B~ d = r: S d_b = r_b + scale .* sum_red nbrs Dg_r^-1 r_r, then
@@ -1656,11 +1933,16 @@ cudaError_t launch_resident(const PcgArgs& a, cudaStream_t stream, int* grid_out
   if (threads > (a.reduced && !a.mixed ? RB_MAX_THREADS : RES_MAX_THREADS)) return cudaSuccess;
   if (a.max_grid > 0 && grid > a.max_grid) return cudaSuccess;
   // FP64: blocks + factor in FP64; mixed: FP64 blocks + FP32 blocks + FP32 factor
+  // the pipelined reduced solver keeps p, s, q, z in shared memory: D <= 6
+  constexpr bool kPipe = D <= 6;
   const size_t shm = a.mixed     ? (size_t)ntri(D) * threads * (sizeof(double) + 2 * sizeof(float))
-                     : a.reduced ? (size_t)(2 * ntri(D) + D) * threads * sizeof(double)
+                     : a.reduced ? (size_t)(2 * ntri(D) + (kPipe ? 5 : 1) * D) * threads * sizeof(double)
                                  : (size_t)2 * ntri(D) * threads * sizeof(double);
+  const void* kred = nullptr;
+  if constexpr (kPipe) kred = (const void*)k_pcg_rbp<D>;
+  else kred = (const void*)k_pcg_rb<D>;
   const void* kern = a.mixed ? (a.reduced ? (const void*)k_pcg_mixed_rb<D> : (const void*)k_pcg_mixed_res<D>)
-                             : (a.reduced ? (const void*)k_pcg_rb<D> : (const void*)k_pcg_res<D>);
+                             : (a.reduced ? kred : (const void*)k_pcg_res<D>);
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm) != cudaSuccess) {
     cudaGetLastError();
     return cudaSuccess;
