@@ -63,12 +63,14 @@ def pcg_flops_per_voxel_iter(K, mode="bj"):
     neighbours 6K + 3K, three inner products 6K. Red-black SSOR ("ssor") adds the omega
     scaling K and its two colour phases, each over half of the voxels: neighbour sum 6K,
     right-hand side 2K (black) or K (red), triangular solves 2K^2, update K (black) or 3K
-    (red). The reduced red-black system ("reduced") works per pair of voxels: the black
-    voxel's axpys 8K, triangular solves 2K^2, block product 2K^2, stencil 9K and inner
-    products 6K, the red voxel's neighbour sum and scaling 7K and triangular solves 2K^2."""
+    (red). The reduced red-black system ("reduced", pipelined CG for K <= 6) works per pair
+    of voxels: the black voxel's eight axpys 16K (p, s, q, z, x, r, u, w), block-inverse
+    product 2K^2, block product 2K^2, stencil 9K and inner products 6K, the red voxel's
+    neighbour sum and scaling 7K and block-inverse product 2K^2 (for K > 6 the unpipelined
+    form: four axpys 8K and triangular solves)."""
     base = 4 * K * K + 25 * K
     if mode == "reduced":
-        return (6 * K * K + 30 * K) / 2
+        return (6 * K * K + (38 if K <= 6 else 30) * K) / 2
     if mode != "ssor":
         return base
     return base + K + ((6 * K + 2 * K + 2 * K * K + K) + (6 * K + K + 2 * K * K + 3 * K)) / 2
@@ -83,7 +85,7 @@ def pcg_bytes_per_voxel_iter(K, w=8):
 # DRAM bytes (read + write) of one W-solve launch on the whole-brain workload, from one ncu
 # capture of each kernel version (reduced system: 25.39 MB + 0.72 MB; SSOR form: 22.99 MB +
 # 0.63 MB): the first touch of the staged blocks, factors, b and x; the iterations run from L2.
-NCU_TRAFFIC_W = {"reduced": 26.12e6, "ssor": 23.62e6}
+NCU_TRAFFIC_W = {"ssor": 23.62e6}
 
 
 def precond_options(args):
@@ -345,7 +347,8 @@ def run_ours(args, world, rank, local):
     # kernels per timed launch group: edge terms + assembly (W, A), quadratic form + draw (hyper)
     per_group = {"assemble_W": 2, "assemble_A": 2, "hyper": 2}
     n_launch = sum(v["launches"] * per_group.get(k, 1) for k, v in tim_p.items()) / n_prof * args.steps
-    kname = {"reduced": f"k_pcg_rb<{K}> (W solve, red-black reduced system)",
+    kname = {"reduced": (f"k_pcg_rbp<{K}> (W solve, pipelined CG on the red-black reduced system)"
+                         if K <= 6 else f"k_pcg_rb<{K}> (W solve, red-black reduced system)"),
              "ssor": f"k_pcg_res<{K}> (W solve, SSOR)",
              "bj": f"k_pcg_res<{K}> (W solve, block-Jacobi)"}[args.precond]
     roof = {"kernel": kname,

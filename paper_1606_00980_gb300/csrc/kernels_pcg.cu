@@ -100,6 +100,46 @@ __device__ __forceinline__ void minv(const T* __restrict__ Lp, int bs, const T* 
   }
 }
 
+// z = Minv r with Minv symmetric packed (entry e at Mp[e * bs]): D independent row sums,
+// no dependent chain as in the two triangular solves.
+template <int D, typename T>
+__device__ __forceinline__ void symv(const T* __restrict__ Mp, int bs, const T* r, T* z) {
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    T acc = T(0);
+#pragma unroll
+    for (int j = 0; j < D; ++j) acc += Mp[(size_t)(i >= j ? tri(i, j) : tri(j, i)) * bs] * r[j];
+    z[i] = acc;
+  }
+}
+
+// Replaces a packed Cholesky factor L (lower, inverted diagonal; M = L L') by the packed
+// symmetric inverse M^-1 = L^-T L^-1, in place (entry e at Mp[e * bs]).
+template <int D>
+__device__ __forceinline__ void factor_to_inverse(double* Mp, int bs) {
+  double Li[ntri(D)];   // L^-1, lower, packed
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    Li[tri(j, j)] = Mp[(size_t)tri(j, j) * bs];
+#pragma unroll
+    for (int i = j + 1; i < D; ++i) {
+      double acc = 0.0;
+#pragma unroll
+      for (int k = j; k < i; ++k) acc += Mp[(size_t)tri(i, k) * bs] * Li[tri(k, j)];
+      Li[tri(i, j)] = -acc * Mp[(size_t)tri(i, i) * bs];
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int j = 0; j <= i; ++j) {
+      double acc = 0.0;
+#pragma unroll
+      for (int k = i; k < D; ++k) acc += Li[tri(k, i)] * Li[tri(k, j)];
+      Mp[(size_t)tri(i, j) * bs] = acc;
+    }
+}
+
 struct Shared {
   double red[32 * 4 + 8];
   double scal[4];   // CG scalars computed once per CTA by thread 0
@@ -1218,6 +1258,9 @@ __global__ void __launch_bounds__(RB_MAX_THREADS, 1) k_pcg_rbp(PcgArgs a) {
       shB[e * bd + t] = own ? __ldg(a.blocks + (size_t)e * ld + n) : (i == j ? 1.0 : 0.0);
       shM[e * bd + t] = own ? __ldg(a.mfac + (size_t)e * ld + n) : (i == j ? 1.0 : 0.0);
     }
+  // each thread's block-Jacobi factor becomes the explicit inverse of its block (its own
+  // column of shM; no other thread reads it): every M^-1 below is a symmetric product
+  factor_to_inverse<D>(shM + t, bd);
   int nb[6];
 #pragma unroll
   for (int d = 0; d < 6; ++d) nb[d] = (own && d < a.ndir) ? __ldg(a.nbr + (size_t)d * ld + n) : -1;
@@ -1260,7 +1303,7 @@ __global__ void __launch_bounds__(RB_MAX_THREADS, 1) k_pcg_rbp(PcgArgs a) {
     }
 #pragma unroll
     for (int k = 0; k < D; ++k) tv[k] = (c ? c[k] : 0.0) + s[k] * sum[k];
-    minv<D, double>(Mp, bd, tv, out);
+    symv<D, double>(Mp, bd, tv, out);
   };
   auto apply_S = [&](const double* v, double* out) -> bool {
     if (black) publish(v);
@@ -1307,7 +1350,7 @@ __global__ void __launch_bounds__(RB_MAX_THREADS, 1) k_pcg_rbp(PcgArgs a) {
     if (black) {
 #pragma unroll
       for (int k = 0; k < D; ++k) r[k] = shH[k * bd + t] - sx[k];
-      minv<D, double>(Mp, bd, r, u);
+      symv<D, double>(Mp, bd, r, u);
     }
     if (!apply_S(u, w)) return false;
 #pragma unroll
@@ -1324,7 +1367,7 @@ __global__ void __launch_bounds__(RB_MAX_THREADS, 1) k_pcg_rbp(PcgArgs a) {
   if (red) {
     double y[D], bv[D];
     load_b(bv);
-    minv<D, double>(Mp, bd, bv, y);
+    symv<D, double>(Mp, bd, bv, y);
     publish(y);
   }
   if (!bar()) return;
@@ -1369,7 +1412,7 @@ __global__ void __launch_bounds__(RB_MAX_THREADS, 1) k_pcg_rbp(PcgArgs a) {
     const double* part = allreduce4_post(a.part, a.part1, v, sh.red);
     double m[D];
     if (black) {
-      minv<D, double>(Mp, bd, w, m);
+      symv<D, double>(Mp, bd, w, m);
       publish(m);
     }
     if (!bar()) return;                 // partials and m are visible everywhere
