@@ -83,9 +83,10 @@ def pcg_bytes_per_voxel_iter(K, w=8):
 
 
 # DRAM bytes (read + write) of one W-solve launch on the whole-brain workload, from one ncu
-# capture of each kernel version (reduced system: 25.39 MB + 0.72 MB; SSOR form: 22.99 MB +
-# 0.63 MB): the first touch of the staged blocks, factors, b and x; the iterations run from L2.
-NCU_TRAFFIC_W = {"ssor": 23.62e6}
+# capture of each kernel version (pipelined reduced system: 25.38 MB + 0.66 MB; SSOR form:
+# 22.99 MB + 0.63 MB): the first touch of the staged blocks, factors, b and x; the iterations
+# run from L2.
+NCU_TRAFFIC_W = {"reduced": 26.04e6, "ssor": 23.62e6}
 
 
 def precond_options(args):
