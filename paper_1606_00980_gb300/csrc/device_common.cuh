@@ -530,12 +530,11 @@ __device__ __forceinline__ double ff_to_double(FF a) { return (double)a.hi + (do
 // (rows alternating with the barrier generation, every CTA summing all rows in a fixed
 // order), with the block and cross-CTA sums done in float-float; totals are returned as
 // doubles. A row holds 4 (hi, lo) pairs, the size of a grid_allreduce4 row.
-__device__ __forceinline__ bool grid_allreduce4_ff(const GridBarrier& b, double* part0, double* part1,
-                                                   const FF* v, double* sh, int* sh_int, double* out) {
+// Block totals of 4 float-float values (every warp, then warp 0 over the warps); lane 0 of
+// warp 0 holds them in c4 on return. shw needs 4 * 2 floats per warp.
+__device__ __forceinline__ void block_reduce4_ff(const FF* v, float* shw, FF* c4) {
   const int l = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nwc = (blockDim.x + 31) >> 5;
-  float* shw = reinterpret_cast<float*>(sh);   // [warp][4][2] floats: 96 floats = 48 doubles
-  double* sh_out = sh + 132;
   FF w4[4];
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
@@ -551,42 +550,26 @@ __device__ __forceinline__ bool grid_allreduce4_ff(const GridBarrier& b, double*
     }
   }
   __syncthreads();
-  const unsigned int nblocks = gridDim.x;
   if (warp == 0) {
-    FF c4[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       c4[i] = l < nwc ? FF{shw[(l * 4 + i) * 2 + 0], shw[(l * 4 + i) * 2 + 1]} : FF{0.f, 0.f};
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) c4[i] = ff_add(c4[i], ff_shfl_xor(c4[i], o));
     }
-    if (l == 0) {
-      const unsigned int g0 = g_bar_gen;
-      float* row = reinterpret_cast<float*>((g0 & 1u) ? part1 : part0) + (size_t)blockIdx.x * 8;
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        row[2 * i + 0] = c4[i].hi;
-        row[2 * i + 1] = c4[i].lo;
-      }
-      const unsigned int arrived = atom_add_acq_rel(b.count, 1u);
-      bool ok = true;
-      if (arrived == nblocks - 1) {
-        st_relaxed(b.count, 0u);
-        red_add_release(b.gen, 1u);
-      } else {
-        ok = wait_generation(b, g0);
-      }
-      g_bar_gen = g0 + 1u;
-      sh_int[0] = ok ? 0 : 1;
-      sh_int[1] = (int)(g0 & 1u);
-    }
   }
-  __syncthreads();
-  const bool good = sh_int[0] == 0;
-  const float* part = reinterpret_cast<const float*>(sh_int[1] ? part1 : part0);
+}
+
+// Sums the float-float rows (8 floats each) that every CTA wrote before a barrier this CTA
+// has passed, in a fixed order; every thread receives the FP64 totals in out.
+__device__ __forceinline__ void allreduce4_ff_collect(const float* part, double* sh, double* out) {
+  const int l = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwc = (blockDim.x + 31) >> 5;
+  const unsigned int nblocks = gridDim.x;
+  double* sh_out = sh + 132;
   // warp j < 4 (warp 0 for all four when the CTA has fewer warps) sums value j over the rows
   const int nsum = nwc >= 4 ? 4 : 1;
-  if (good && warp < nsum) {
+  if (warp < nsum) {
     for (int j = warp; j < 4; j += nsum) {
       FF acc{0.f, 0.f};
       for (unsigned int r = (unsigned int)l; r < nblocks; r += 32u) {
@@ -602,7 +585,57 @@ __device__ __forceinline__ bool grid_allreduce4_ff(const GridBarrier& b, double*
 #pragma unroll
   for (int i = 0; i < 4; ++i) out[i] = sh_out[i];
   __syncthreads();
-  return good;
+}
+
+__device__ __forceinline__ bool grid_allreduce4_ff(const GridBarrier& b, double* part0, double* part1,
+                                                   const FF* v, double* sh, int* sh_int, double* out) {
+  float* shw = reinterpret_cast<float*>(sh);   // [warp][4][2] floats: 96 floats = 48 doubles
+  FF c4[4];
+  block_reduce4_ff(v, shw, c4);
+  const unsigned int nblocks = gridDim.x;
+  if (threadIdx.x == 0) {
+    const unsigned int g0 = g_bar_gen;
+    float* row = reinterpret_cast<float*>((g0 & 1u) ? part1 : part0) + (size_t)blockIdx.x * 8;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      row[2 * i + 0] = c4[i].hi;
+      row[2 * i + 1] = c4[i].lo;
+    }
+    const unsigned int arrived = atom_add_acq_rel(b.count, 1u);
+    bool ok = true;
+    if (arrived == nblocks - 1) {
+      st_relaxed(b.count, 0u);
+      red_add_release(b.gen, 1u);
+    } else {
+      ok = wait_generation(b, g0);
+    }
+    g_bar_gen = g0 + 1u;
+    sh_int[0] = ok ? 0 : 1;
+    sh_int[1] = (int)(g0 & 1u);
+  }
+  __syncthreads();
+  if (sh_int[0] != 0) return false;
+  allreduce4_ff_collect(reinterpret_cast<const float*>(sh_int[1] ? part1 : part0), sh, out);
+  return true;
+}
+
+// Split form (see allreduce4_post): the CTA's float-float totals go to the row buffer of the
+// current barrier generation before a plain grid barrier; collect after it.
+__device__ __forceinline__ const float* allreduce4_ff_post(double* part0, double* part1, const FF* v,
+                                                           double* sh) {
+  float* shw = reinterpret_cast<float*>(sh);
+  FF c4[4];
+  block_reduce4_ff(v, shw, c4);
+  __syncthreads();   // every thread sees g_bar_gen; shw free again
+  float* row = reinterpret_cast<float*>((g_bar_gen & 1u) ? part1 : part0);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      row[(size_t)blockIdx.x * 8 + 2 * i + 0] = c4[i].hi;
+      row[(size_t)blockIdx.x * 8 + 2 * i + 1] = c4[i].lo;
+    }
+  }
+  return row;
 }
 
 }  // namespace bfmri

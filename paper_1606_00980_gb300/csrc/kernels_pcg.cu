@@ -115,15 +115,15 @@ __device__ __forceinline__ void symv(const T* __restrict__ Mp, int bs, const T* 
 
 // Replaces a packed Cholesky factor L (lower, inverted diagonal; M = L L') by the packed
 // symmetric inverse M^-1 = L^-T L^-1, in place (entry e at Mp[e * bs]).
-template <int D>
-__device__ __forceinline__ void factor_to_inverse(double* Mp, int bs) {
-  double Li[ntri(D)];   // L^-1, lower, packed
+template <int D, typename T>
+__device__ __forceinline__ void factor_to_inverse(T* Mp, int bs) {
+  T Li[ntri(D)];   // L^-1, lower, packed
 #pragma unroll
   for (int j = 0; j < D; ++j) {
     Li[tri(j, j)] = Mp[(size_t)tri(j, j) * bs];
 #pragma unroll
     for (int i = j + 1; i < D; ++i) {
-      double acc = 0.0;
+      T acc = T(0);
 #pragma unroll
       for (int k = j; k < i; ++k) acc += Mp[(size_t)tri(i, k) * bs] * Li[tri(k, j)];
       Li[tri(i, j)] = -acc * Mp[(size_t)tri(i, i) * bs];
@@ -133,7 +133,7 @@ __device__ __forceinline__ void factor_to_inverse(double* Mp, int bs) {
   for (int i = 0; i < D; ++i)
 #pragma unroll
     for (int j = 0; j <= i; ++j) {
-      double acc = 0.0;
+      T acc = T(0);
 #pragma unroll
       for (int k = i; k < D; ++k) acc += Li[tri(k, i)] * Li[tri(k, j)];
       Mp[(size_t)tri(i, j) * bs] = acc;
@@ -1260,7 +1260,7 @@ __global__ void __launch_bounds__(RB_MAX_THREADS, 1) k_pcg_rbp(PcgArgs a) {
     }
   // each thread's block-Jacobi factor becomes the explicit inverse of its block (its own
   // column of shM; no other thread reads it): every M^-1 below is a symmetric product
-  factor_to_inverse<D>(shM + t, bd);
+  factor_to_inverse<D, double>(shM + t, bd);
   int nb[6];
 #pragma unroll
   for (int d = 0; d < 6; ++d) nb[d] = (own && d < a.ndir) ? __ldg(a.nbr + (size_t)d * ld + n) : -1;
@@ -1489,6 +1489,243 @@ __global__ void __launch_bounds__(RB_MAX_THREADS, 1) k_pcg_rbp(PcgArgs a) {
     for (int k = 0; k < D; ++k) a.x[(size_t)k * ld + n] = x[k];
   }
   write_ctrl(a, it, restarts, rr, bb, rel0, status);
+}
+
+// ---------------------------------------------------------------------------------------
+// Mixed precision on the red-black reduced system with pipelined inner iterations: the FP64
+// refinement of k_pcg_mixed_rb, and for each correction the FP32 pipelined CG of k_pcg_rbp
+// (float-float partial sums posted before the product's first barrier, collected after it;
+// two barriers per inner iteration) with explicit FP32 block inverses.
+// ---------------------------------------------------------------------------------------
+template <int D>
+__global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_mixed_rbp(PcgArgs a) {
+  extern __shared__ double smem[];
+  __shared__ Shared sh;
+  grid_barrier_start(a.bar);
+  __shared__ double cwd[6];
+  __shared__ float cwf[6];
+  if (threadIdx.x == 0) {
+    slot_weights(a, cwd);
+    slot_weights(a, cwf);
+  }
+  __syncthreads();
+  constexpr int NT = ntri(D);
+  const int bd = blockDim.x, t = threadIdx.x;
+  double* shB = smem;                                   // [NT][bd] FP64 blocks
+  float* shB32 = reinterpret_cast<float*>(smem + NT * bd);   // [NT][bd]
+  float* shM32 = shB32 + NT * bd;                       // [NT][bd] block inverses (FP32)
+  int n = blockIdx.x * a.res_per + t;
+  bool own = t < a.res_per && n < a.N;
+  bool is_red = true;
+  colour_sort(a, n, own, is_red);
+  const bool red = own && is_red, black = own && !is_red;
+  const size_t ld = a.ld;
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int j = 0; j <= i; ++j) {
+      const int e = tri(i, j);
+      shB[e * bd + t] = own ? __ldg(a.blocks + (size_t)e * ld + n) : (i == j ? 1.0 : 0.0);
+      shB32[e * bd + t] = own ? __ldg(a.blocks32 + (size_t)e * ld + n) : (i == j ? 1.f : 0.f);
+      shM32[e * bd + t] = own ? __ldg(a.mfac32 + (size_t)e * ld + n) : (i == j ? 1.f : 0.f);
+    }
+  factor_to_inverse<D, float>(shM32 + t, bd);
+  int nb[6];
+#pragma unroll
+  for (int d = 0; d < 6; ++d) nb[d] = (own && d < a.ndir) ? __ldg(a.nbr + (size_t)d * ld + n) : -1;
+  const double degd = degree_of<double>(nb, cwd);
+  const float degf = (float)degd;
+  double s[D], x[D], bv[D];
+  float s32[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    s[k] = __ldg(a.scale + k);
+    s32[k] = (float)s[k];
+    x[k] = own ? a.x[(size_t)k * ld + n] : 0.0;
+    bv[k] = own ? __ldg(a.b + (size_t)k * ld + n) : 0.0;
+  }
+  const double* Bp = shB + t;
+  const float* Bp32 = shB32 + t;
+  const float* Mp32 = shM32 + t;
+  float* U = a.u32;
+  auto bar = [&]() -> bool {
+    if (a.skip_block == (int)blockIdx.x) return false;
+    return grid_sync(a.bar, &sh.flag);
+  };
+  auto publish = [&](const float* v) {
+#pragma unroll
+    for (int k = 0; k < D; ++k) U[(size_t)k * ld + n] = v[k];
+  };
+  auto red_solve = [&](const float* c, float* out) {
+    float sum[D], tv[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) sum[k] = 0.f;
+#pragma unroll
+    for (int d = 0; d < 6; ++d) {
+      if (nb[d] >= 0) {
+#pragma unroll
+        for (int k = 0; k < D; ++k) sum[k] += cwf[d] * ldx(U + (size_t)k * ld + nb[d]);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < D; ++k) tv[k] = (c ? c[k] : 0.f) + s32[k] * sum[k];
+    symv<D, float>(Mp32, bd, tv, out);
+  };
+  auto apply_S = [&](const float* v, float* out) -> bool {
+    if (black) publish(v);
+    if (!bar()) return false;
+    if (red) {
+      float y[D];
+      red_solve(nullptr, y);
+      publish(y);
+    }
+    if (!bar()) return false;
+    if (black) amul<D, float>(Bp32, bd, s32, nb, cwf, degf, v, U, ld, out);
+    return true;
+  };
+  double tot[4];
+  int outer = 0, inner_total = 0, status = 0;
+  double bb = 0.0, rr = 0.0, rel0 = 0.0, tol2 = 0.0;
+  while (true) {
+    // ---- FP64 true residual (x of every voxel is complete: start value or published) ----
+    double r64[D];
+    {
+      double ax[D];
+      amul<D, double>(Bp, bd, s, nb, cwd, degd, x, a.x, ld, ax);
+      double v[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        r64[k] = bv[k] - ax[k];
+        v[0] += r64[k] * r64[k];
+        v[1] += bv[k] * bv[k];
+      }
+      if (!grid_allreduce4(a.bar, a.part, a.part1, v, sh.red, sh.ints, tot)) return;
+    }
+    rr = tot[0];
+    if (outer == 0) {
+      bb = tot[1];
+      tol2 = a.delta * a.delta * bb;
+      rel0 = bb > 0.0 ? sqrt(rr / bb) : 0.0;
+      if (!(isfinite(rr) && isfinite(bb))) { status = 7; break; }
+      if (bb == 0.0) {
+#pragma unroll
+        for (int k = 0; k < D; ++k) x[k] = 0.0;
+        break;
+      }
+    }
+    if (!isfinite(rr)) { status = 7; break; }
+    if (rr <= tol2) break;
+    if (inner_total >= a.max_iter) { status = 4; break; }
+    ++outer;
+    // ---- FP32 pipelined CG on the reduced system of B~ d = r ----
+    float rc[D], r[D], u[D], w[D], d[D], p[D], sv[D], q[D], z[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      rc[k] = (float)r64[k];
+      r[k] = u[k] = w[k] = d[k] = p[k] = sv[k] = q[k] = z[k] = 0.f;
+    }
+    const double itol2 = fmax(a.inner_tol * a.inner_tol * rr, 0.25 * tol2);
+    if (red) {
+      float y[D];
+      symv<D, float>(Mp32, bd, rc, y);
+      publish(y);
+    }
+    if (!bar()) return;
+    if (black) {
+      float sum[D];
+#pragma unroll
+      for (int k = 0; k < D; ++k) sum[k] = 0.f;
+#pragma unroll
+      for (int dd = 0; dd < 6; ++dd) {
+        if (nb[dd] >= 0) {
+#pragma unroll
+          for (int k = 0; k < D; ++k) sum[k] += cwf[dd] * ldx(U + (size_t)k * ld + nb[dd]);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < D; ++k) r[k] = rc[k] + s32[k] * sum[k];
+      symv<D, float>(Mp32, bd, r, u);
+    }
+    if (!apply_S(u, w)) return;   // its first barrier orders the reads of U above
+    double alpha = 0.0, beta = 0.0, gam = 0.0, rgam = 0.0, ralpha = 0.0;
+    int it = 0;
+    while (true) {
+      float g = 0.f, dl = 0.f, q2 = 0.f;
+      if (black) {
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          g += r[k] * u[k];
+          dl += w[k] * u[k];
+          q2 += r[k] * r[k];
+        }
+      }
+      const FF v[4] = {ff_of(g), ff_of(dl), ff_of(q2), ff_of(0.f)};
+      const float* part = allreduce4_ff_post(a.part, a.part1, v, sh.red);
+      float m[D];
+      if (black) {
+        symv<D, float>(Mp32, bd, w, m);
+        publish(m);
+      }
+      if (!bar()) return;                 // partials and m are visible everywhere
+      if (red) {
+        float y[D];
+        red_solve(nullptr, y);
+        publish(y);
+      }
+      allreduce4_ff_collect(part, sh.red, tot);
+      const bool capped = it >= a.max_inner || inner_total + it >= a.max_iter;
+      cg_scalar_step(sh, tot[0], tot[1], tot[2], itol2, capped ? 1 : 0, 1, alpha, beta, gam, rgam, ralpha);
+      const int code = sh.code;
+      __syncthreads();
+      if (!bar()) return;                 // y visible; every CTA has read the partials
+      if (code == 7) { status = 7; break; }
+      if (code != 0) break;   // inner tolerance, iteration cap, or loss of conjugacy in FP32
+      if (black) {
+        float nn[D];
+        amul<D, float>(Bp32, bd, s32, nb, cwf, degf, m, U, ld, nn);   // n = S m
+        const float fa = (float)alpha, fb = (float)beta;
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          z[k] = nn[k] + fb * z[k];
+          q[k] = m[k] + fb * q[k];
+          sv[k] = w[k] + fb * sv[k];
+          p[k] = u[k] + fb * p[k];
+          d[k] += fa * p[k];
+          r[k] -= fa * sv[k];
+          u[k] -= fa * q[k];
+          w[k] -= fa * z[k];
+        }
+      }
+      ++it;
+    }
+    inner_total += it;
+    if (status != 0) break;
+    // red part of the correction from the red rows, then x += d everywhere
+    if (black) publish(d);
+    if (!bar()) return;
+    if (red) red_solve(rc, d);
+#pragma unroll
+    for (int k = 0; k < D; ++k) x[k] += (double)d[k];
+    if (own) {
+#pragma unroll
+      for (int k = 0; k < D; ++k) a.x[(size_t)k * ld + n] = x[k];
+    }
+    if (!bar()) return;
+  }
+  if (own) {
+#pragma unroll
+    for (int k = 0; k < D; ++k) a.x[(size_t)k * ld + n] = x[k];
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    a.ctrl->iterations = inner_total;
+    a.ctrl->restarts = outer;
+    a.ctrl->rel_res = bb > 0.0 ? sqrt(rr / bb) : 0.0;
+    a.ctrl->rel_res0 = rel0;
+    a.ctrl->status = status;
+    if (status != 0 && a.ctrl->status_any == 0) a.ctrl->status_any = status;
+    a.ctrl->iter_total += inner_total;
+    a.ctrl->solves += 1;
+  }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -1984,7 +2221,7 @@ cudaError_t launch_resident(const PcgArgs& a, cudaStream_t stream, int* grid_out
   const void* kred = nullptr;
   if constexpr (kPipe) kred = (const void*)k_pcg_rbp<D>;
   else kred = (const void*)k_pcg_rb<D>;
-  const void* kern = a.mixed ? (a.reduced ? (const void*)k_pcg_mixed_rb<D> : (const void*)k_pcg_mixed_res<D>)
+  const void* kern = a.mixed ? (a.reduced ? (const void*)k_pcg_mixed_rbp<D> : (const void*)k_pcg_mixed_res<D>)
                              : (a.reduced ? kred : (const void*)k_pcg_res<D>);
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm) != cudaSuccess) {
     cudaGetLastError();
