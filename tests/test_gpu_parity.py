@@ -275,3 +275,26 @@ def test_sweeps_are_bitwise_reproducible():
         m.close()
     for k in outs[0]:
         assert np.array_equal(outs[0][k], outs[1][k])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_reduced_red_black_solver_matches_exact_solve(case, precision):
+    """PRECOND_RB_REDUCED on every parity workload (isolated voxels, holes, 2D slices, P = 0,
+    K = 10): the pipelined reduced-system solvers where they apply (resident, D <= 6), the
+    unpipelined ones for larger blocks, SSOR (omega = 1) in the streaming fallback; W and A
+    draws reach the oracle's exact solve."""
+    from paper_1606_00980_gb300 import bfmri
+    w, lat, st, s = case
+    m = make(w, s, precond=bfmri.PRECOND_RB_REDUCED,
+             precision=bfmri.PREC_FP64 if precision == "fp64" else bfmri.PREC_MIXED)
+    W, info = m.sample_W(counter=3)
+    Bd, bw = model.w_blocks_direct(w.Y, w.X, s["A"], s["lam"], w.eps)
+    ref, _ = gibbs.draw_gmrf(lat, Bd, bw, s["alpha"], SEED, 3, philox.TAG_W)
+    assert info.rel_residual <= 1e-12
+    assert rel(W, ref) <= 1e-8
+    if w.P > 0:
+        A, ia = m.sample_A(counter=4)
+        Ar = gibbs.sample_A(lat, w.Y, w.X, dict(s, W=W), SEED, 4, spatial=True)
+        assert ia.rel_residual <= 1e-12
+        assert rel(A, Ar) <= 1e-8
+    m.close()
