@@ -392,7 +392,8 @@ def run_ours(args, world, rank, local):
                 "config": {"workload": workload_name(args), "N": N, "T": T, "K": K, "P": P,
                            "parallelism": f"replicas{world}", "l2": "flushed between steps (256 MB write)",
                            "pcg_iterations_W_per_sweep": it_w / args.steps,
-                           "pcg_iterations_A_per_sweep": it_a / args.steps},
+                           "pcg_iterations_A_per_sweep": it_a / args.steps,
+                           "pcg_iterations_per_s": (it_w + it_a) / total_s},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                 "voxel_draws_per_s": value * N,
                 "mixed_precision": mixed, "summaries": summ, "convergence": conv,
