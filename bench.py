@@ -822,7 +822,8 @@ def run_batched(args):
 def run_serving(args):
     """Serving workload: a Poisson stream of requests, each a synthetic subject (ellipsoid mask
     of 5k-300k voxels, log-uniform; K in {4,6,8,10}; T in {150,300,600}; AR(1)-AR(3)), each
-    running create + statistics + 8 mixed-precision Gibbs sweeps at delta = 1e-8 with its state
+    running create + statistics + 8 mixed-precision Gibbs sweeps at delta = 1e-8 (the --precond
+    preconditioner) with its state
     resident on the device, admitted into 4 slots under a 64 GB device-memory budget. The
     distinct subjects are a pool of 8 that spans those ranges (generating hundreds of distinct
     subjects on the host would dominate the run); requests draw from it uniformly in log N.
@@ -840,7 +841,7 @@ def run_serving(args):
         w.Y = w.Y.astype(np.float32)
         pool.append(w)
     slots, sm_budget, budget = 4, 38, 64 << 30
-    opts = dict(precision=bfmri.PREC_MIXED, delta=1e-8, inner_tol=1e-6)
+    opts = dict(precision=bfmri.PREC_MIXED, delta=1e-8, inner_tol=1e-6, **precond_options(args))
     # capacity pilot: every pool member alone (service time), then a saturating burst of
     # 4 x the pool through all slots (sustained requests/s)
     srv = bfmri.Server(budget, slots, sm_budget)

@@ -2182,6 +2182,264 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_mixed_stream(PcgArgs a) {
 }
 
 // ---------------------------------------------------------------------------------------
+// Streaming mixed precision on the red-black reduced system (any N): the FP64 refinement of
+// k_pcg_mixed_stream, each correction from FP32 CG on the reduced system of B~ d = r with
+// the vectors in global memory. Black voxels run over the black list, red ones over the red
+// list. r32 holds r~ at the black voxels and the red part of the refinement right-hand side
+// at the red ones; u32 carries u at the black voxels and y = Dg_r^-1 (...) at the red ones;
+// d32 holds the correction at both.
+// ---------------------------------------------------------------------------------------
+template <int D>
+__global__ void __launch_bounds__(PCG_THREADS) k_pcg_mixed_stream_rb(PcgArgs a) {
+  __shared__ Shared sh;
+  grid_barrier_start(a.bar);
+  __shared__ double cwd[6];
+  __shared__ float cwf[6];
+  if (threadIdx.x == 0) {
+    slot_weights(a, cwd);
+    slot_weights(a, cwf);
+  }
+  __syncthreads();
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nth = gridDim.x * blockDim.x;
+  const size_t ld = a.ld;
+  double s[D];
+  float s32[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    s[k] = __ldg(a.scale + k);
+    s32[k] = (float)s[k];
+  }
+  auto bar = [&]() -> bool {
+    if (a.skip_block == (int)blockIdx.x) return false;
+    return grid_sync(a.bar, &sh.flag);
+  };
+  auto load_nb = [&](int n, int* nb) {
+#pragma unroll
+    for (int d = 0; d < 6; ++d) nb[d] = d < a.ndir ? __ldg(a.nbr + (size_t)d * ld + n) : -1;
+  };
+  // out = Dg_n^-1 (c + scale .* sum of the neighbours' V), FP32
+  auto colour_solve = [&](int n, const float* c, const float* V, float* out) {
+    int nb[6];
+    load_nb(n, nb);
+    float sum[D], tv[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) sum[k] = 0.f;
+#pragma unroll
+    for (int d = 0; d < 6; ++d) {
+      if (nb[d] >= 0) {
+#pragma unroll
+        for (int k = 0; k < D; ++k) sum[k] += cwf[d] * ldx(V + (size_t)k * ld + nb[d]);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < D; ++k) tv[k] = (c ? c[k] : 0.f) + s32[k] * sum[k];
+    minv<D, float>(a.mfac32 + n, (int)ld, tv, out);
+  };
+  auto store = [&](float* V, int n, const float* v) {
+#pragma unroll
+    for (int k = 0; k < D; ++k) V[(size_t)k * ld + n] = v[k];
+  };
+  auto load = [&](const float* V, int n, float* v) {
+#pragma unroll
+    for (int k = 0; k < D; ++k) v[k] = V[(size_t)k * ld + n];
+  };
+  // red phase (u32 at the red voxels from u at the black ones), barrier, black product
+  // w = S u with the partials (r'u, w'u, r'r)
+  auto product_partials = [&](double* tot) -> bool {
+    for (int i = tid; i < a.n_red; i += nth) {
+      const int n = __ldg(a.red + i);
+      float y[D];
+      colour_solve(n, nullptr, a.u32, y);
+      store(a.u32, n, y);
+    }
+    if (!bar()) return false;
+    FF v[4] = {ff_of(0.f), ff_of(0.f), ff_of(0.f), ff_of(0.f)};
+    for (int i = tid; i < a.n_black; i += nth) {
+      const int n = __ldg(a.black + i);
+      int nb[6];
+      load_nb(n, nb);
+      float un[D], wn[D], rk[D];
+      load(a.u32, n, un);
+      load(a.r32, n, rk);
+      amul<D, float>(a.blocks32 + n, (int)ld, s32, nb, cwf, degree_of<float>(nb, cwf), un, a.u32, ld, wn);
+      float g = 0.f, dl = 0.f, q2 = 0.f;
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        g += rk[k] * un[k];
+        dl += wn[k] * un[k];
+        q2 += rk[k] * rk[k];
+      }
+      store(a.w32, n, wn);
+      v[0] = ff_add(v[0], ff_of(g));
+      v[1] = ff_add(v[1], ff_of(dl));
+      v[2] = ff_add(v[2], ff_of(q2));
+    }
+    return grid_allreduce4_ff(a.bar, a.part, a.part1, v, sh.red, sh.ints, tot);
+  };
+  double tot[4];
+  int outer = 0, inner_total = 0, status = 0;
+  double bb = 0.0, rr = 0.0, rel0 = 0.0, tol2 = 0.0;
+  while (true) {
+    // ---- FP64 true residual over every voxel; its FP32 copy goes to r32 ----
+    {
+      double v[4] = {0.0, 0.0, 0.0, 0.0};
+      for (int n = tid; n < a.N; n += nth) {
+        int nb[6];
+        load_nb(n, nb);
+        double xn[D], ax[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) xn[k] = ldx(a.x + (size_t)k * ld + n);
+        amul<D, double>(a.blocks + n, (int)ld, s, nb, cwd, degree_of<double>(nb, cwd), xn, a.x, ld, ax);
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          const double bk = __ldg(a.b + (size_t)k * ld + n);
+          const double rk = bk - ax[k];
+          v[0] += rk * rk;
+          v[1] += bk * bk;
+          a.r32[(size_t)k * ld + n] = (float)rk;
+          a.d32[(size_t)k * ld + n] = 0.f;
+        }
+      }
+      if (!grid_allreduce4(a.bar, a.part, a.part1, v, sh.red, sh.ints, tot)) return;
+    }
+    rr = tot[0];
+    if (outer == 0) {
+      bb = tot[1];
+      tol2 = a.delta * a.delta * bb;
+      rel0 = bb > 0.0 ? sqrt(rr / bb) : 0.0;
+      if (!(isfinite(rr) && isfinite(bb))) { status = 7; break; }
+      if (bb == 0.0) {
+        for (int n = tid; n < a.N; n += nth)
+#pragma unroll
+          for (int k = 0; k < D; ++k) a.x[(size_t)k * ld + n] = 0.0;
+        break;
+      }
+    }
+    if (!isfinite(rr)) { status = 7; break; }
+    if (rr <= tol2) break;
+    if (inner_total >= a.max_iter) { status = 4; break; }
+    ++outer;
+    const double itol2 = fmax(a.inner_tol * a.inner_tol * rr, 0.25 * tol2);
+    // reduced right-hand side: y0 = Dg_r^-1 r_r at the red voxels, then at the black ones
+    // r~ = r_b + scale .* sum y0, u = Dg_b^-1 r~, p = s = 0
+    for (int i = tid; i < a.n_red; i += nth) {
+      const int n = __ldg(a.red + i);
+      float rc[D], y[D];
+      load(a.r32, n, rc);
+      minv<D, float>(a.mfac32 + n, (int)ld, rc, y);
+      store(a.u32, n, y);
+    }
+    if (!bar()) return;
+    // (black voxels write u32 only at black voxels and read it only at red ones)
+    for (int i = tid; i < a.n_black; i += nth) {
+      const int n = __ldg(a.black + i);
+      float rc[D], rt[D], un[D], zero[D];
+      load(a.r32, n, rc);
+      int nb[6];
+      load_nb(n, nb);
+      float sum[D];
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        sum[k] = 0.f;
+        zero[k] = 0.f;
+      }
+#pragma unroll
+      for (int d = 0; d < 6; ++d) {
+        if (nb[d] >= 0) {
+#pragma unroll
+          for (int k = 0; k < D; ++k) sum[k] += cwf[d] * ldx(a.u32 + (size_t)k * ld + nb[d]);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < D; ++k) rt[k] = rc[k] + s32[k] * sum[k];
+      minv<D, float>(a.mfac32 + n, (int)ld, rt, un);
+      store(a.r32, n, rt);
+      store(a.u32, n, un);
+      store(a.p32, n, zero);
+      store(a.s32, n, zero);
+    }
+    if (!bar()) return;
+    if (!product_partials(tot)) return;
+    double gam = tot[0], del = tot[1];
+    if (!(del > 0.0) || !isfinite(del)) { status = isfinite(del) ? 3 : 7; break; }
+    double alpha = gam / del, beta = 0.0;
+    double rgam = 0.0, ralpha = 0.0;
+    cg_recips(gam, del, rgam, ralpha);
+    int it = 0;
+    while (true) {
+      const float fa = (float)alpha, fb = (float)beta;
+      for (int i = tid; i < a.n_black; i += nth) {
+        const int n = __ldg(a.black + i);
+        float rn[D], un[D], pk[D], sk[D], dk[D], wk[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          const size_t o = (size_t)k * ld + n;
+          un[k] = a.u32[o];
+          pk[k] = a.p32[o];
+          wk[k] = a.w32[o];
+          sk[k] = a.s32[o];
+          dk[k] = a.d32[o];
+          rn[k] = a.r32[o];
+        }
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          pk[k] = un[k] + fb * pk[k];
+          sk[k] = wk[k] + fb * sk[k];
+          dk[k] += fa * pk[k];
+          rn[k] -= fa * sk[k];
+        }
+        minv<D, float>(a.mfac32 + n, (int)ld, rn, un);
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          const size_t o = (size_t)k * ld + n;
+          a.p32[o] = pk[k];
+          a.s32[o] = sk[k];
+          a.d32[o] = dk[k];
+          a.r32[o] = rn[k];
+          a.u32[o] = un[k];
+        }
+      }
+      if (!bar()) return;
+      if (!product_partials(tot)) return;
+      ++it;
+      const bool capped = it >= a.max_inner || inner_total + it >= a.max_iter;
+      cg_scalar_step(sh, tot[0], tot[1], tot[2], itol2, capped ? 1 : 0, 1, alpha, beta, gam, rgam, ralpha);
+      const int code = sh.code;
+      __syncthreads();
+      if (code == 7) { status = 7; break; }
+      if (code != 0) break;   // inner tolerance, iteration cap, or loss of conjugacy in FP32
+    }
+    inner_total += it;
+    if (status != 0) break;
+    // red part of the correction from the red rows (d32 at the black voxels is final), then
+    // x += d everywhere
+    for (int i = tid; i < a.n_red; i += nth) {
+      const int n = __ldg(a.red + i);
+      float rc[D], dn[D];
+      load(a.r32, n, rc);
+      colour_solve(n, rc, a.d32, dn);
+      store(a.d32, n, dn);
+    }
+    if (!bar()) return;
+    for (int n = tid; n < a.N; n += nth)
+#pragma unroll
+      for (int k = 0; k < D; ++k) a.x[(size_t)k * ld + n] += (double)a.d32[(size_t)k * ld + n];
+    if (!bar()) return;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    a.ctrl->iterations = inner_total;
+    a.ctrl->restarts = outer;
+    a.ctrl->rel_res = bb > 0.0 ? sqrt(rr / bb) : 0.0;
+    a.ctrl->rel_res0 = rel0;
+    a.ctrl->status = status;
+    if (status != 0 && a.ctrl->status_any == 0) a.ctrl->status_any = status;
+    a.ctrl->iter_total += inner_total;
+    a.ctrl->solves += 1;
+  }
+}
+
+// ---------------------------------------------------------------------------------------
 // launch
 // ---------------------------------------------------------------------------------------
 namespace {
@@ -2253,7 +2511,8 @@ static cudaError_t launch_d(const PcgArgs& a, cudaStream_t stream, int* grid_out
     }
   }
   const int nsm = capped_sms(a.sm_cap);
-  const void* kern = a.mixed ? (const void*)k_pcg_mixed_stream<D> : (const void*)k_pcg_stream<D>;
+  const void* kern = a.mixed ? (a.reduced ? (const void*)k_pcg_mixed_stream_rb<D> : (const void*)k_pcg_mixed_stream<D>)
+                             : (const void*)k_pcg_stream<D>;
   int per_sm = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, PCG_THREADS, 0);
   if (e != cudaSuccess) return e;
@@ -2269,10 +2528,12 @@ static cudaError_t launch_d(const PcgArgs& a, cudaStream_t stream, int* grid_out
 
 template <int D>
 static int max_grid_d() {
-  int p1 = 0, p2 = 0;
+  int p1 = 0, p2 = 0, p3 = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p1, k_pcg_stream<D>, PCG_THREADS, 0);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p2, k_pcg_mixed_stream<D>, PCG_THREADS, 0);
-  const int per_sm = p1 > p2 ? p1 : p2;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p3, k_pcg_mixed_stream_rb<D>, PCG_THREADS, 0);
+  int per_sm = p1 > p2 ? p1 : p2;
+  per_sm = per_sm > p3 ? per_sm : p3;
   return num_sms() * (per_sm > 1 ? per_sm : 1);
 }
 
