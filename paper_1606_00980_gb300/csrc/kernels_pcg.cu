@@ -1492,10 +1492,12 @@ __global__ void __launch_bounds__(RB_MAX_THREADS, 1) k_pcg_rbp(PcgArgs a) {
 }
 
 // ---------------------------------------------------------------------------------------
-// Mixed precision on the red-black reduced system with pipelined inner iterations: the FP64
-// refinement of k_pcg_mixed_rb, and for each correction the FP32 pipelined CG of k_pcg_rbp
-// (float-float partial sums posted before the product's first barrier, collected after it;
-// two barriers per inner iteration) with explicit FP32 block inverses.
+// Mixed precision on the red-black reduced system (resident): FP64 iterative refinement of
+// the full system (true residual r of B~ over every voxel, x += d), each correction d from
+// FP32 pipelined CG on the reduced system of B~ d = r,
+//   S d_b = r_b + scale .* sum_red nbrs Dg_r^-1 r_r,  d_r = Dg_r^-1 (r_r + scale .* sum d_b),
+// with float-float partial sums posted before the product's first barrier and collected
+// after it (two barriers per inner iteration, as k_pcg_rbp) and explicit FP32 block inverses.
 // ---------------------------------------------------------------------------------------
 template <int D>
 __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_mixed_rbp(PcgArgs a) {
@@ -1728,252 +1730,6 @@ __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_mixed_rbp(PcgArgs a)
   }
 }
 
-// ---------------------------------------------------------------------------------------
-// Mixed precision on the red-black reduced system: the FP64 refinement of k_pcg_mixed_res
-// (true residual r of B~ over every voxel, x += d), each correction d from FP32 CG on the
-// reduced system of B~ d = r: S d_b = r_b + scale .* sum_red nbrs Dg_r^-1 r_r, then
-// d_r = Dg_r^-1 (r_r + scale .* sum of the black neighbours' d_b). The FP32 iterations take
-// the iterates of SSOR-preconditioned CG with omega = 1 at three barriers each, with
-// float-float cross-thread sums as in the other mixed solvers.
-// ---------------------------------------------------------------------------------------
-template <int D>
-__global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_mixed_rb(PcgArgs a) {
-  extern __shared__ double smem[];
-  __shared__ Shared sh;
-  grid_barrier_start(a.bar);
-  // per-slot edge weights in shared memory (read as broadcasts; no registers held)
-  __shared__ double cwd[6];
-  __shared__ float cwf[6];
-  if (threadIdx.x == 0) {
-    slot_weights(a, cwd);
-    slot_weights(a, cwf);
-  }
-  __syncthreads();
-  constexpr int NT = ntri(D);
-  const int bd = blockDim.x, t = threadIdx.x;
-  double* shB = smem;                                   // [NT][bd] FP64 blocks
-  float* shB32 = reinterpret_cast<float*>(smem + NT * bd);   // [NT][bd]
-  float* shM32 = shB32 + NT * bd;                       // [NT][bd]
-  int n = blockIdx.x * a.res_per + t;
-  bool own = t < a.res_per && n < a.N;
-  bool is_red = true;
-  colour_sort(a, n, own, is_red);
-  const bool red = own && is_red, black = own && !is_red;
-  const size_t ld = a.ld;
-#pragma unroll
-  for (int i = 0; i < D; ++i)
-#pragma unroll
-    for (int j = 0; j <= i; ++j) {
-      const int e = tri(i, j);
-      shB[e * bd + t] = own ? __ldg(a.blocks + (size_t)e * ld + n) : (i == j ? 1.0 : 0.0);
-      shB32[e * bd + t] = own ? __ldg(a.blocks32 + (size_t)e * ld + n) : (i == j ? 1.f : 0.f);
-      shM32[e * bd + t] = own ? __ldg(a.mfac32 + (size_t)e * ld + n) : (i == j ? 1.f : 0.f);
-    }
-  int nb[6];
-#pragma unroll
-  for (int d = 0; d < 6; ++d) nb[d] = (own && d < a.ndir) ? __ldg(a.nbr + (size_t)d * ld + n) : -1;
-  const double degd = degree_of<double>(nb, cwd);
-  const float degf = (float)degd;
-  double s[D], x[D], bv[D];
-  float s32[D];
-#pragma unroll
-  for (int k = 0; k < D; ++k) {
-    s[k] = __ldg(a.scale + k);
-    s32[k] = (float)s[k];
-    x[k] = own ? a.x[(size_t)k * ld + n] : 0.0;
-    bv[k] = own ? __ldg(a.b + (size_t)k * ld + n) : 0.0;
-  }
-  const double* Bp = shB + t;
-  const float* Bp32 = shB32 + t;
-  const float* Mp32 = shM32 + t;
-  float* U = a.u32;
-  auto bar = [&]() -> bool {
-    if (a.skip_block == (int)blockIdx.x) return false;
-    return grid_sync(a.bar, &sh.flag);
-  };
-  auto publish = [&](const float* v) {
-#pragma unroll
-    for (int k = 0; k < D; ++k) U[(size_t)k * ld + n] = v[k];
-  };
-  // red voxel: out = Dg^-1 (c + scale .* sum of the neighbours' U), c = 0 or given
-  auto red_solve = [&](const float* c, float* out) {
-    float sum[D], tv[D];
-#pragma unroll
-    for (int k = 0; k < D; ++k) sum[k] = 0.f;
-#pragma unroll
-    for (int d = 0; d < 6; ++d) {
-      if (nb[d] >= 0) {
-#pragma unroll
-        for (int k = 0; k < D; ++k) sum[k] += cwf[d] * ldx(U + (size_t)k * ld + nb[d]);
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < D; ++k) tv[k] = (c ? c[k] : 0.f) + s32[k] * sum[k];
-    minv<D, float>(Mp32, bd, tv, out);
-  };
-  // out = S v on the black voxels (two barriers)
-  auto apply_S = [&](const float* v, float* out) -> bool {
-    if (black) publish(v);
-    if (!bar()) return false;
-    if (red) {
-      float y[D];
-      red_solve(nullptr, y);
-      publish(y);
-    }
-    if (!bar()) return false;
-    if (black) amul<D, float>(Bp32, bd, s32, nb, cwf, degf, v, U, ld, out);
-    return true;
-  };
-  double tot[4];
-  int outer = 0, inner_total = 0, status = 0;
-  double bb = 0.0, rr = 0.0, rel0 = 0.0, tol2 = 0.0;
-  while (true) {
-    // ---- FP64 true residual (x of every voxel is complete: start value or published) ----
-    double r64[D];
-    {
-      double ax[D];
-      amul<D, double>(Bp, bd, s, nb, cwd, degd, x, a.x, ld, ax);
-      double v[4] = {0.0, 0.0, 0.0, 0.0};
-#pragma unroll
-      for (int k = 0; k < D; ++k) {
-        r64[k] = bv[k] - ax[k];
-        v[0] += r64[k] * r64[k];
-        v[1] += bv[k] * bv[k];
-      }
-      if (!grid_allreduce4(a.bar, a.part, a.part1, v, sh.red, sh.ints, tot)) return;
-    }
-    rr = tot[0];
-    if (outer == 0) {
-      bb = tot[1];
-      tol2 = a.delta * a.delta * bb;
-      rel0 = bb > 0.0 ? sqrt(rr / bb) : 0.0;
-      if (!(isfinite(rr) && isfinite(bb))) { status = 7; break; }
-      if (bb == 0.0) {
-#pragma unroll
-        for (int k = 0; k < D; ++k) x[k] = 0.0;
-        break;
-      }
-    }
-    if (!isfinite(rr)) { status = 7; break; }
-    if (rr <= tol2) break;
-    if (inner_total >= a.max_iter) { status = 4; break; }
-    ++outer;
-    // ---- FP32 inner CG on the reduced system of B~ d = r ----
-    float rc[D], r[D], u[D], w[D], p[D], q[D], d[D];
-#pragma unroll
-    for (int k = 0; k < D; ++k) {
-      rc[k] = (float)r64[k];   // red voxels keep their part of the right-hand side
-      r[k] = 0.f;
-      u[k] = 0.f;
-      w[k] = 0.f;
-      d[k] = 0.f;
-      p[k] = 0.f;
-      q[k] = 0.f;
-    }
-    const double itol2 = fmax(a.inner_tol * a.inner_tol * rr, 0.25 * tol2);
-    // reduced right-hand side on the black voxels (d_b = 0: it is the reduced residual)
-    if (red) {
-      float y[D];
-      minv<D, float>(Mp32, bd, rc, y);
-      publish(y);
-    }
-    if (!bar()) return;
-    if (black) {
-      float sum[D];
-#pragma unroll
-      for (int k = 0; k < D; ++k) sum[k] = 0.f;
-#pragma unroll
-      for (int dd = 0; dd < 6; ++dd) {
-        if (nb[dd] >= 0) {
-#pragma unroll
-          for (int k = 0; k < D; ++k) sum[k] += cwf[dd] * ldx(U + (size_t)k * ld + nb[dd]);
-        }
-      }
-#pragma unroll
-      for (int k = 0; k < D; ++k) r[k] = rc[k] + s32[k] * sum[k];
-      minv<D, float>(Mp32, bd, r, u);
-    }
-    if (!apply_S(u, w)) return;   // its first barrier orders the reads of U above
-    {
-      float g = 0.f, dl = 0.f, q2 = 0.f;
-      if (black) {
-#pragma unroll
-        for (int k = 0; k < D; ++k) {
-          g += r[k] * u[k];
-          dl += w[k] * u[k];
-          q2 += r[k] * r[k];
-        }
-      }
-      const FF v[4] = {ff_of(g), ff_of(dl), ff_of(q2), ff_of(0.f)};
-      if (!grid_allreduce4_ff(a.bar, a.part, a.part1, v, sh.red, sh.ints, tot)) return;
-    }
-    double gam = tot[0], del = tot[1];
-    if (!(del > 0.0) || !isfinite(del)) { status = isfinite(del) ? 3 : 7; break; }
-    double alpha = gam / del, beta = 0.0;
-    double rgam = 0.0, ralpha = 0.0;
-    cg_recips(gam, del, rgam, ralpha);
-    int it = 0;
-    while (true) {
-      if (black) {
-        const float fa = (float)alpha, fb = (float)beta;
-#pragma unroll
-        for (int k = 0; k < D; ++k) {
-          p[k] = u[k] + fb * p[k];
-          q[k] = w[k] + fb * q[k];
-          d[k] += fa * p[k];
-          r[k] -= fa * q[k];
-        }
-        minv<D, float>(Mp32, bd, r, u);
-      }
-      if (!apply_S(u, w)) return;
-      float g = 0.f, dl = 0.f, q2 = 0.f;
-      if (black) {
-#pragma unroll
-        for (int k = 0; k < D; ++k) {
-          g += r[k] * u[k];
-          dl += w[k] * u[k];
-          q2 += r[k] * r[k];
-        }
-      }
-      const FF v[4] = {ff_of(g), ff_of(dl), ff_of(q2), ff_of(0.f)};
-      if (!grid_allreduce4_ff(a.bar, a.part, a.part1, v, sh.red, sh.ints, tot)) return;
-      ++it;
-      const bool capped = it >= a.max_inner || inner_total + it >= a.max_iter;
-      cg_scalar_step(sh, tot[0], tot[1], tot[2], itol2, capped ? 1 : 0, 1, alpha, beta, gam, rgam, ralpha);
-      const int code = sh.code;
-      __syncthreads();
-      if (code == 7) { status = 7; break; }
-      if (code != 0) break;   // inner tolerance, iteration cap, or loss of conjugacy in FP32
-    }
-    inner_total += it;
-    if (status != 0) break;
-    // red part of the correction from the red rows, then x += d everywhere
-    if (black) publish(d);
-    if (!bar()) return;
-    if (red) red_solve(rc, d);
-#pragma unroll
-    for (int k = 0; k < D; ++k) x[k] += (double)d[k];
-    if (own) {
-#pragma unroll
-      for (int k = 0; k < D; ++k) a.x[(size_t)k * ld + n] = x[k];
-    }
-    if (!bar()) return;
-  }
-  if (own) {
-#pragma unroll
-    for (int k = 0; k < D; ++k) a.x[(size_t)k * ld + n] = x[k];
-  }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    a.ctrl->iterations = inner_total;
-    a.ctrl->restarts = outer;
-    a.ctrl->rel_res = bb > 0.0 ? sqrt(rr / bb) : 0.0;
-    a.ctrl->rel_res0 = rel0;
-    a.ctrl->status = status;
-    if (status != 0 && a.ctrl->status_any == 0) a.ctrl->status_any = status;
-    a.ctrl->iter_total += inner_total;
-    a.ctrl->solves += 1;
-  }
-}
 
 // ---------------------------------------------------------------------------------------
 // Mixed precision (streaming): the same refinement with vectors in global memory.

@@ -258,3 +258,21 @@ def test_mixed_reduced_inner_iterations_match_mixed_ssor():
         m.close()
     assert its["reduced"] < its["bj"], its
     assert abs(its["reduced"] - its["ssor"]) <= max(3, its["ssor"] // 5), its
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_reduced_system_with_large_blocks(precision):
+    """K = 8 runs the unpipelined reduced solver (the pipelined one keeps four extra vectors in
+    shared memory and stops at D = 6); mixed precision runs the pipelined FP32 inner solver."""
+    from paper_1606_00980_gb300 import bfmri
+    w = synth.small3d(seed=34, dims=(9, 8, 6), K=8, P=1, T=60)
+    lat = Lattice(w.mask, w.neighbourhood)
+    s = state_for(w, np.random.default_rng(12))
+    m = make(w, s, precond=bfmri.PRECOND_RB_REDUCED,
+             precision=bfmri.PREC_FP64 if precision == "fp64" else bfmri.PREC_MIXED)
+    W, info = m.sample_W(counter=3)
+    Bd, bw = model.w_blocks_direct(w.Y, w.X, s["A"], s["lam"], w.eps)
+    ref, _ = gibbs.draw_gmrf(lat, Bd, bw, s["alpha"], SEED, 3, philox.TAG_W)
+    assert info.rel_residual <= 1e-12
+    assert rel(W, ref) <= 1e-8
+    m.close()
