@@ -63,14 +63,18 @@ def pcg_flops_per_voxel_iter(K, mode="bj"):
     neighbours 6K + 3K, three inner products 6K. Red-black SSOR ("ssor") adds the omega
     scaling K and its two colour phases, each over half of the voxels: neighbour sum 6K,
     right-hand side 2K (black) or K (red), triangular solves 2K^2, update K (black) or 3K
-    (red). The reduced red-black system ("reduced", pipelined CG for K <= 6) works per pair
-    of voxels: the black voxel's eight axpys 16K (p, s, q, z, x, r, u, w), block-inverse
-    product 2K^2, block product 2K^2, stencil 9K and inner products 6K, the red voxel's
-    neighbour sum and scaling 7K and block-inverse product 2K^2 (for K > 6 the unpipelined
-    form: four axpys 8K and triangular solves)."""
+    (red). The reduced red-black system ("reduced", pipelined CG on the split-preconditioned
+    system for K <= 6) works per pair of voxels: the black voxel's six axpys 12K (z, s, p, x,
+    r, w), three triangular products K(K+1) each (L_b r for the residual norm, L_b^-T w,
+    L_b^-1 of the neighbour sum), neighbour sum, scaling and difference 8K, inner products 6K;
+    the red voxel's neighbour sum and scaling 7K and block-inverse product 2K^2. For K > 6 the
+    unpipelined preconditioned form: per pair two block-inverse products and one block
+    product 6K^2 and 30K."""
     base = 4 * K * K + 25 * K
     if mode == "reduced":
-        return (6 * K * K + (38 if K <= 6 else 30) * K) / 2
+        if K <= 6:
+            return (5 * K * K + 36 * K) / 2
+        return (6 * K * K + 30 * K) / 2
     if mode != "ssor":
         return base
     return base + K + ((6 * K + 2 * K + 2 * K * K + K) + (6 * K + K + 2 * K * K + 3 * K)) / 2
@@ -83,10 +87,10 @@ def pcg_bytes_per_voxel_iter(K, w=8):
 
 
 # DRAM bytes (read + write) of one W-solve launch on the whole-brain workload, from one ncu
-# capture of each kernel version (pipelined reduced system: 25.38 MB + 0.66 MB; SSOR form:
-# 22.99 MB + 0.63 MB): the first touch of the staged blocks, factors, b and x; the iterations
-# run from L2.
-NCU_TRAFFIC_W = {"reduced": 26.04e6, "ssor": 23.62e6}
+# capture of each kernel version (pipelined split-preconditioned reduced system: 25.45 MB +
+# 0.64 MB; SSOR form: 22.99 MB + 0.63 MB): the first touch of the staged blocks, factors, b
+# and x; the iterations run from L2.
+NCU_TRAFFIC_W = {"reduced": 26.09e6, "ssor": 23.62e6}
 
 
 def precond_options(args):

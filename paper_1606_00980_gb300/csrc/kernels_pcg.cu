@@ -113,11 +113,10 @@ __device__ __forceinline__ void symv(const T* __restrict__ Mp, int bs, const T* 
   }
 }
 
-// Replaces a packed Cholesky factor L (lower, inverted diagonal; M = L L') by the packed
-// symmetric inverse M^-1 = L^-T L^-1, in place (entry e at Mp[e * bs]).
+// Li = L^-1 (packed lower) of a packed Cholesky factor L (lower, inverted diagonal; entry e
+// at Mp[e * bs]), column by column by forward substitution.
 template <int D, typename T>
-__device__ __forceinline__ void factor_to_inverse(T* Mp, int bs) {
-  T Li[ntri(D)];   // L^-1, lower, packed
+__device__ __forceinline__ void lower_inverse(const T* Mp, int bs, T* Li) {
 #pragma unroll
   for (int j = 0; j < D; ++j) {
     Li[tri(j, j)] = Mp[(size_t)tri(j, j) * bs];
@@ -129,6 +128,32 @@ __device__ __forceinline__ void factor_to_inverse(T* Mp, int bs) {
       Li[tri(i, j)] = -acc * Mp[(size_t)tri(i, i) * bs];
     }
   }
+}
+
+// out = L v (lower = true) or L' v (lower = false) for a packed lower-triangular L (entry e
+// at Lp[e * bs]): rows of independent sums.
+template <int D, typename T, bool lower>
+__device__ __forceinline__ void trmv(const T* __restrict__ Lp, int bs, const T* v, T* out) {
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    T acc = T(0);
+    if constexpr (lower) {
+#pragma unroll
+      for (int j = 0; j <= i; ++j) acc += Lp[(size_t)tri(i, j) * bs] * v[j];
+    } else {
+#pragma unroll
+      for (int j = i; j < D; ++j) acc += Lp[(size_t)tri(j, i) * bs] * v[j];
+    }
+    out[i] = acc;
+  }
+}
+
+// Replaces a packed Cholesky factor L (lower, inverted diagonal; M = L L') by the packed
+// symmetric inverse M^-1 = L^-T L^-1, in place (entry e at Mp[e * bs]).
+template <int D, typename T>
+__device__ __forceinline__ void factor_to_inverse(T* Mp, int bs) {
+  T Li[ntri(D)];   // L^-1, lower, packed
+  lower_inverse<D, T>(Mp, bs, Li);
 #pragma unroll
   for (int i = 0; i < D; ++i)
 #pragma unroll
@@ -1212,20 +1237,27 @@ __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_mixed_res(PcgArgs a)
 }
 
 // ---------------------------------------------------------------------------------------
-// Pipelined CG (Ghysels & Vanroose 2014, preconditioned form) on the same reduced system:
-// with the extra recurrences q = M^-1 s and z = A q, the two inner products of iteration i
-// are formed from r_i, u_i, w_i before its matrix product, so their reduction completes at
-// the product's first barrier and the reducing barrier disappears: two grid barriers per
-// iteration instead of three. Per iteration (black voxels; M = Dg_b, A = S):
-//   gamma = r'u, delta = w'u  (posted)            m = M^-1 w  (published)
-//   --- barrier: the partials and m are visible --- red phase of S m; every CTA sums the
-//   partials in a fixed order and forms alpha, beta as Chronopoulos & Gear do
-//   --- barrier ---  n = S m (black phase)
-//   z = n + beta z, q = m + beta q, s = w + beta s, p = u + beta p,
-//   x += alpha p, r -= alpha s, u -= alpha q, w -= alpha z.
-// The stop test reads ||r_i|| one product earlier than the unpipelined form (the same
-// iterates); the stop is confirmed on B~'s true residual as in k_pcg_rb. p, s, q, z live in
-// shared memory (D <= 6 fits next to the blocks, factors and b^).
+// Pipelined CG (Ghysels & Vanroose 2014) on the same reduced system, split-preconditioned:
+// with Dg_b = L_b L_b' (the block-Jacobi factor of each black voxel), CG runs without a
+// preconditioner on  S^ = L_b^-1 S L_b^-T = I - L_b^-1 L Dg_r^-1 U L_b^-T  in the variable
+// x^ = L_b' x_b. Its iterates are those of CG on S preconditioned by Dg_b (the same Krylov
+// spaces; r = L_b r^), but a product with S^ costs two triangular products at the black voxel
+// and one block product at the red one, where the preconditioned form needs three full block
+// products (M^-1, Dg_r^-1, Dg_b), and the recurrences for u = M^-1 r and q = M^-1 s go away.
+// The two inner products of iteration i come from r^_i and w^_i = S^ r^_i before its product,
+// so their reduction completes at the product's first barrier: two grid barriers per
+// iteration. Per iteration (black voxels):
+//   gamma = r^'r^, delta = w^'r^, rr = |L_b r^|^2 = |r|^2 (posted)   v = L_b^-T w^ (published)
+//   --- barrier: the partials and v are visible --- red phase y = Dg_r^-1 (scale .* sum v);
+//   every CTA sums the partials in a fixed order and forms alpha, beta (Chronopoulos & Gear)
+//   --- barrier ---  n = w^ - L_b^-1 (scale .* sum y)  (= S^ w^)
+//   z = n + beta z, s = w^ + beta s, p = r^ + beta p, x^ += alpha p, r^ -= alpha s,
+//   w^ -= alpha z.
+// The stop test reads the unscaled reduced residual |r| (= the black rows of B~'s residual
+// once the red voxels are recovered) one product earlier than the unpipelined form; the stop
+// is confirmed on B~'s true residual as in k_pcg_rb. p, s, z live in shared memory beside
+// L_b and L_b^-1 (black voxels) or Dg_r^-1 (red voxels); the data blocks are read from global
+// memory by the rare restart and confirmation passes only.
 // ---------------------------------------------------------------------------------------
 template <int D>
 __global__ void __launch_bounds__(RB_MAX_THREADS, 1) k_pcg_rbp(PcgArgs a) {
@@ -1237,38 +1269,54 @@ __global__ void __launch_bounds__(RB_MAX_THREADS, 1) k_pcg_rbp(PcgArgs a) {
   __syncthreads();
   constexpr int NT = ntri(D);
   const int bd = blockDim.x, t = threadIdx.x;
-  double* shB = smem;
-  double* shM = smem + NT * bd;
+  double* shL = smem;                 // black: L_b (true diagonal)
+  double* shM = smem + NT * bd;       // black: L_b^-1; red: Dg_r^-1
   double* shH = smem + 2 * NT * bd;   // b^
   double* shP = shH + D * bd;         // p
-  double* shS = shP + D * bd;         // s = A p
-  double* shQ = shS + D * bd;         // q = M^-1 s
-  double* shZ = shQ + D * bd;         // z = A q
+  double* shS = shP + D * bd;         // s = S^ p
+  double* shZ = shS + D * bd;         // z = S^ s
   int n = blockIdx.x * a.res_per + t;
   bool own = t < a.res_per && n < a.N;
   bool is_red = true;
   colour_sort(a, n, own, is_red);
   const bool red = own && is_red, black = own && !is_red;
   const size_t ld = a.ld;
+  {
+    double Lf[NT];
 #pragma unroll
-  for (int i = 0; i < D; ++i)
+    for (int e = 0; e < NT; ++e) Lf[e] = 0.0;
 #pragma unroll
-    for (int j = 0; j <= i; ++j) {
-      const int e = tri(i, j);
-      shB[e * bd + t] = own ? __ldg(a.blocks + (size_t)e * ld + n) : (i == j ? 1.0 : 0.0);
-      shM[e * bd + t] = own ? __ldg(a.mfac + (size_t)e * ld + n) : (i == j ? 1.0 : 0.0);
+    for (int i = 0; i < D; ++i) Lf[tri(i, i)] = 1.0;
+    if (own) {
+#pragma unroll
+      for (int e = 0; e < NT; ++e) Lf[e] = __ldg(a.mfac + (size_t)e * ld + n);
     }
-  // each thread's block-Jacobi factor becomes the explicit inverse of its block (its own
-  // column of shM; no other thread reads it): every M^-1 below is a symmetric product
-  factor_to_inverse<D, double>(shM + t, bd);
+#pragma unroll
+    for (int e = 0; e < NT; ++e) shM[e * bd + t] = Lf[e];
+    if (black) {
+      // L_b with its true diagonal, and L_b^-1 in place of the factor
+      double Li[NT];
+      lower_inverse<D, double>(shM + t, bd, Li);
+#pragma unroll
+      for (int i = 0; i < D; ++i)
+#pragma unroll
+        for (int j = 0; j <= i; ++j) {
+          const int e = tri(i, j);
+          shL[e * bd + t] = i == j ? 1.0 / Lf[e] : Lf[e];
+          shM[e * bd + t] = Li[e];
+        }
+    } else {
+      // red voxels (and threads without a voxel): the explicit inverse Dg_r^-1
+      factor_to_inverse<D, double>(shM + t, bd);
+    }
+  }
   int nb[6];
 #pragma unroll
   for (int d = 0; d < 6; ++d) nb[d] = (own && d < a.ndir) ? __ldg(a.nbr + (size_t)d * ld + n) : -1;
-  const double degd = degree_of<double>(nb, cwd);
   __shared__ double s[RES_MAX_D];
   if (t < D) s[t] = __ldg(a.scale + t);
   __syncthreads();
-  double x[D], r[D], u[D], w[D];
+  double x[D], r[D], w[D];   // x holds x_b outside the iteration, x^ inside it
   auto load_b = [&](double* bv) {
 #pragma unroll
     for (int k = 0; k < D; ++k) bv[k] = own ? __ldg(a.b + (size_t)k * ld + n) : 0.0;
@@ -1276,11 +1324,12 @@ __global__ void __launch_bounds__(RB_MAX_THREADS, 1) k_pcg_rbp(PcgArgs a) {
 #pragma unroll
   for (int k = 0; k < D; ++k) {
     x[k] = own ? a.x[(size_t)k * ld + n] : 0.0;
-    r[k] = u[k] = w[k] = 0.0;
+    r[k] = w[k] = 0.0;
     shH[k * bd + t] = 0.0;
   }
-  const double* Bp = shB + t;
+  const double* Lp = shL + t;
   const double* Mp = shM + t;
+  const double* Bg = a.blocks + n;     // data block in global memory (own voxels only)
   double* U = a.u;
   auto bar = [&]() -> bool {
     if (a.skip_block == (int)blockIdx.x) return false;
@@ -1290,8 +1339,7 @@ __global__ void __launch_bounds__(RB_MAX_THREADS, 1) k_pcg_rbp(PcgArgs a) {
 #pragma unroll
     for (int k = 0; k < D; ++k) U[(size_t)k * ld + n] = v[k];
   };
-  auto red_solve = [&](const double* c, double* out) {
-    double sum[D], tv[D];
+  auto nsum = [&](double* sum) {
 #pragma unroll
     for (int k = 0; k < D; ++k) sum[k] = 0.0;
 #pragma unroll
@@ -1301,10 +1349,41 @@ __global__ void __launch_bounds__(RB_MAX_THREADS, 1) k_pcg_rbp(PcgArgs a) {
         for (int k = 0; k < D; ++k) sum[k] += cwd[d] * ldx(U + (size_t)k * ld + nb[d]);
       }
     }
+  };
+  auto red_solve = [&](const double* c, double* out) {
+    double sum[D], tv[D];
+    nsum(sum);
 #pragma unroll
     for (int k = 0; k < D; ++k) tv[k] = (c ? c[k] : 0.0) + s[k] * sum[k];
     symv<D, double>(Mp, bd, tv, out);
   };
+  // out = S^ v at the black voxels: v' = L_b^-T v published, red phase, then
+  // out = v - L_b^-1 (scale .* sum of the red neighbours' y)
+  auto apply_Sh = [&](const double* v, double* out) -> bool {
+    if (black) {
+      double vt[D];
+      trmv<D, double, false>(Mp, bd, v, vt);
+      publish(vt);
+    }
+    if (!bar()) return false;
+    if (red) {
+      double y[D];
+      red_solve(nullptr, y);
+      publish(y);
+    }
+    if (!bar()) return false;
+    if (black) {
+      double sum[D], tv[D];
+      nsum(sum);
+#pragma unroll
+      for (int k = 0; k < D; ++k) tv[k] = s[k] * sum[k];
+      trmv<D, double, true>(Mp, bd, tv, out);
+#pragma unroll
+      for (int k = 0; k < D; ++k) out[k] = v[k] - out[k];
+    }
+    return true;
+  };
+  // out = S v at the black voxels in unscaled variables (restarts only)
   auto apply_S = [&](const double* v, double* out) -> bool {
     if (black) publish(v);
     if (!bar()) return false;
@@ -1314,11 +1393,21 @@ __global__ void __launch_bounds__(RB_MAX_THREADS, 1) k_pcg_rbp(PcgArgs a) {
       publish(y);
     }
     if (!bar()) return false;
-    if (black) amul<D, double>(Bp, bd, s, nb, cwd, degd, v, U, ld, out);
+    if (black) {
+      const double degd = degree_of<double>(nb, cwd);
+      amul<D, double>(Bg, (int)ld, s, nb, cwd, degd, v, U, ld, out);
+    }
     return true;
   };
+  // x_b = L_b^-T x^, then the red voxels from their rows
   auto recover_red = [&]() -> bool {
-    if (black) publish(x);
+    if (black) {
+      double xb[D];
+      trmv<D, double, false>(Mp, bd, x, xb);
+#pragma unroll
+      for (int k = 0; k < D; ++k) x[k] = xb[k];
+      publish(x);
+    }
     if (!bar()) return false;
     if (red) {
       double bv[D];
@@ -1336,28 +1425,32 @@ __global__ void __launch_bounds__(RB_MAX_THREADS, 1) k_pcg_rbp(PcgArgs a) {
     double ax[D], bv[D], v[4] = {0.0, 0.0, 0.0, 0.0};
     if (own) {
       load_b(bv);
-      amul<D, double>(Bp, bd, s, nb, cwd, degd, x, a.x, ld, ax);
+      const double degd = degree_of<double>(nb, cwd);
+      amul<D, double>(Bg, (int)ld, s, nb, cwd, degd, x, a.x, ld, ax);
 #pragma unroll
       for (int k = 0; k < D; ++k) v[2] += (bv[k] - ax[k]) * (bv[k] - ax[k]);
     }
     return grid_allreduce4(a.bar, a.part, a.part1, v, sh.red, sh.ints, tot);
   };
-  // (re)start of the recurrences from the current x_b: r = b^ - S x, u = M^-1 r, w = S u,
-  // p = s = q = z = 0
+  // (re)start of the recurrences from the current x_b: r^ = L_b^-1 (b^ - S x_b),
+  // x^ = L_b' x_b, w^ = S^ r^, p = s = z = 0
   auto restart = [&]() -> bool {
     double sx[D];
     if (!apply_S(x, sx)) return false;
     if (black) {
+      double rb[D], xh[D];
 #pragma unroll
-      for (int k = 0; k < D; ++k) r[k] = shH[k * bd + t] - sx[k];
-      symv<D, double>(Mp, bd, r, u);
+      for (int k = 0; k < D; ++k) rb[k] = shH[k * bd + t] - sx[k];
+      trmv<D, double, true>(Mp, bd, rb, r);
+      trmv<D, double, false>(Lp, bd, x, xh);
+#pragma unroll
+      for (int k = 0; k < D; ++k) x[k] = xh[k];
     }
-    if (!apply_S(u, w)) return false;
+    if (!apply_Sh(r, w)) return false;
 #pragma unroll
     for (int k = 0; k < D; ++k) {
       shP[k * bd + t] = 0.0;
       shS[k * bd + t] = 0.0;
-      shQ[k * bd + t] = 0.0;
       shZ[k * bd + t] = 0.0;
     }
     return true;
@@ -1373,15 +1466,7 @@ __global__ void __launch_bounds__(RB_MAX_THREADS, 1) k_pcg_rbp(PcgArgs a) {
   if (!bar()) return;
   if (black) {
     double sum[D], bv[D];
-#pragma unroll
-    for (int k = 0; k < D; ++k) sum[k] = 0.0;
-#pragma unroll
-    for (int d = 0; d < 6; ++d) {
-      if (nb[d] >= 0) {
-#pragma unroll
-        for (int k = 0; k < D; ++k) sum[k] += cwd[d] * ldx(U + (size_t)k * ld + nb[d]);
-      }
-    }
+    nsum(sum);
     load_b(bv);
 #pragma unroll
     for (int k = 0; k < D; ++k) shH[k * bd + t] = bv[k] + s[k] * sum[k];
@@ -1392,15 +1477,17 @@ __global__ void __launch_bounds__(RB_MAX_THREADS, 1) k_pcg_rbp(PcgArgs a) {
   double alpha = 0.0, beta = 0.0, gam = 0.0, rgam = 0.0, ralpha = 0.0;
   int it = 0, restarts = 0, status = 0;
   bool first = true;        // first pass of the solve: the partials carry b'b
-  bool x_final = false;
+  bool x_final = false;     // x holds x_b (and the red voxels are recovered)
   while (true) {
     double v[4] = {0.0, 0.0, 0.0, 0.0};
     if (black) {
+      double lr[D];
+      trmv<D, double, true>(Lp, bd, r, lr);
 #pragma unroll
       for (int k = 0; k < D; ++k) {
-        v[0] += r[k] * u[k];
-        v[1] += w[k] * u[k];
-        v[2] += r[k] * r[k];
+        v[0] += r[k] * r[k];
+        v[1] += w[k] * r[k];
+        v[2] += lr[k] * lr[k];
       }
     }
     if (first) {
@@ -1410,12 +1497,12 @@ __global__ void __launch_bounds__(RB_MAX_THREADS, 1) k_pcg_rbp(PcgArgs a) {
       for (int k = 0; k < D; ++k) v[3] += bv[k] * bv[k];
     }
     const double* part = allreduce4_post(a.part, a.part1, v, sh.red);
-    double m[D];
     if (black) {
-      symv<D, double>(Mp, bd, w, m);
-      publish(m);
+      double vt[D];
+      trmv<D, double, false>(Mp, bd, w, vt);
+      publish(vt);
     }
-    if (!bar()) return;                 // partials and m are visible everywhere
+    if (!bar()) return;                 // partials and v are visible everywhere
     if (red) {
       double y[D];
       red_solve(nullptr, y);
@@ -1455,32 +1542,32 @@ __global__ void __launch_bounds__(RB_MAX_THREADS, 1) k_pcg_rbp(PcgArgs a) {
       if (it >= a.max_iter) { status = 4; break; }
       ++restarts;
       if (!restart()) return;
+      x_final = false;
       rgam = 0.0;
       ralpha = 0.0;
       continue;
     }
     if (black) {
-      double nn[D];
-      amul<D, double>(Bp, bd, s, nb, cwd, degd, m, U, ld, nn);   // n = S m
+      double sum[D], tv[D], nn[D];
+      nsum(sum);
+#pragma unroll
+      for (int k = 0; k < D; ++k) tv[k] = s[k] * sum[k];
+      trmv<D, double, true>(Mp, bd, tv, nn);   // n = w^ - L_b^-1 (scale .* sum y)
       const double al = alpha, be = beta;
 #pragma unroll
       for (int k = 0; k < D; ++k) {
         const int o = k * bd + t;
-        const double z = nn[k] + be * shZ[o];
-        const double q = m[k] + be * shQ[o];
+        const double z = (w[k] - nn[k]) + be * shZ[o];
         const double sv = w[k] + be * shS[o];
-        const double p = u[k] + be * shP[o];
+        const double p = r[k] + be * shP[o];
         shZ[o] = z;
-        shQ[o] = q;
         shS[o] = sv;
         shP[o] = p;
         x[k] += al * p;
         r[k] -= al * sv;
-        u[k] -= al * q;
         w[k] -= al * z;
       }
     }
-    x_final = false;
     ++it;
   }
   if (!x_final && !recover_red()) return;
@@ -2227,10 +2314,10 @@ cudaError_t launch_resident(const PcgArgs& a, cudaStream_t stream, int* grid_out
   if (threads > (a.reduced && !a.mixed ? RB_MAX_THREADS : RES_MAX_THREADS)) return cudaSuccess;
   if (a.max_grid > 0 && grid > a.max_grid) return cudaSuccess;
   // FP64: blocks + factor in FP64; mixed: FP64 blocks + FP32 blocks + FP32 factor
-  // the pipelined reduced solver keeps p, s, q, z in shared memory: D <= 6
+  // the pipelined reduced solver keeps b^, p, s, z in shared memory: D <= 6
   constexpr bool kPipe = D <= 6;
   const size_t shm = a.mixed     ? (size_t)ntri(D) * threads * (sizeof(double) + 2 * sizeof(float))
-                     : a.reduced ? (size_t)(2 * ntri(D) + (kPipe ? 5 : 1) * D) * threads * sizeof(double)
+                     : a.reduced ? (size_t)(2 * ntri(D) + (kPipe ? 4 : 1) * D) * threads * sizeof(double)
                                  : (size_t)2 * ntri(D) * threads * sizeof(double);
   const void* kred = nullptr;
   if constexpr (kPipe) kred = (const void*)k_pcg_rbp<D>;
