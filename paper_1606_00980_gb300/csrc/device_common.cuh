@@ -400,15 +400,19 @@ __device__ __forceinline__ void block_reduce4(const double* v, double* sh, doubl
 // ---------------------------------------------------------------------------------------
 // Sums the rows of a partial buffer that every CTA wrote before a barrier this CTA has
 // passed, in a fixed order, so every CTA obtains bit-identical totals; every thread receives
-// them in out. sh needs 4 * 32 + 8 doubles.
-__device__ __forceinline__ void allreduce4_collect(const double* part, double* sh, double* out) {
+// them in out. sh needs 4 * 32 + 8 doubles. With at least 128 threads, warps w0 .. w0 + 3
+// (w0 + 4 <= the CTA's warps) do the loads, so a caller may hand them to warps that are idle
+// at that point; the summation order, and so the totals, do not depend on w0.
+__device__ __forceinline__ void allreduce4_collect(const double* part, double* sh, double* out,
+                                                   int w0 = 0) {
   const int l = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned int nblocks = gridDim.x;
   double* sh_out = sh + 132;
   if (blockDim.x >= 128) {
-    // warp j < 4 sums value j: lane l over rows l + 32 i (5 rows per lane and round, as a
+    // warp w0 + j sums value j: lane l over rows l + 32 i (5 rows per lane and round, as a
     // fixed pairwise tree), then a butterfly; the four warps run on different SM sub-partitions
-    if (warp < 4) {
+    const int j = warp - w0;
+    if (j >= 0 && j < 4) {
       constexpr int RU = 5;
       double acc = 0.0;
       for (unsigned int r0 = (unsigned int)l; r0 < nblocks; r0 += 32u * RU) {
@@ -416,13 +420,13 @@ __device__ __forceinline__ void allreduce4_collect(const double* part, double* s
 #pragma unroll
         for (int i = 0; i < RU; ++i) {
           const unsigned int r = r0 + 32u * i;
-          buf[i] = r < nblocks ? __ldcg(part + (size_t)r * 4 + warp) : 0.0;
+          buf[i] = r < nblocks ? __ldcg(part + (size_t)r * 4 + j) : 0.0;
         }
         acc += ((buf[0] + buf[1]) + (buf[2] + buf[3])) + buf[4];
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      if (l == 0) sh_out[warp] = acc;
+      if (l == 0) sh_out[j] = acc;
     }
   } else if (warp == 0) {
     // lane l sums value (l & 3) over rows (l >> 2) + 8 i (20 rows per lane and round)
@@ -562,14 +566,18 @@ __device__ __forceinline__ void block_reduce4_ff(const FF* v, float* shw, FF* c4
 
 // Sums the float-float rows (8 floats each) that every CTA wrote before a barrier this CTA
 // has passed, in a fixed order; every thread receives the FP64 totals in out.
-__device__ __forceinline__ void allreduce4_ff_collect(const float* part, double* sh, double* out) {
-  const int l = threadIdx.x & 31, warp = threadIdx.x >> 5;
+// With four warps or more, warps w0 .. w0 + 3 (w0 + 4 <= the CTA's warps) do the loads; the
+// summation order, and so the totals, do not depend on w0.
+__device__ __forceinline__ void allreduce4_ff_collect(const float* part, double* sh, double* out,
+                                                      int w0 = 0) {
+  const int l = threadIdx.x & 31;
   const int nwc = (blockDim.x + 31) >> 5;
   const unsigned int nblocks = gridDim.x;
   double* sh_out = sh + 132;
-  // warp j < 4 (warp 0 for all four when the CTA has fewer warps) sums value j over the rows
+  // warp w0 + j sums value j (warp 0 all four when the CTA has fewer warps) over the rows
   const int nsum = nwc >= 4 ? 4 : 1;
-  if (warp < nsum) {
+  const int warp = nwc >= 4 ? (int)(threadIdx.x >> 5) - w0 : (int)(threadIdx.x >> 5);
+  if (warp >= 0 && warp < nsum) {
     for (int j = warp; j < 4; j += nsum) {
       FF acc{0.f, 0.f};
       for (unsigned int r = (unsigned int)l; r < nblocks; r += 32u) {

@@ -1481,7 +1481,10 @@ __global__ void __launch_bounds__(RB_MAX_THREADS, 1) k_pcg_rbp(PcgArgs a) {
   while (true) {
     double v[4] = {0.0, 0.0, 0.0, 0.0};
     if (black) {
-      double lr[D];
+      // v = L_b^-T w^ first, so that its stores are in flight during the block reduction
+      double vt[D], lr[D];
+      trmv<D, double, false>(Mp, bd, w, vt);
+      publish(vt);
       trmv<D, double, true>(Lp, bd, r, lr);
 #pragma unroll
       for (int k = 0; k < D; ++k) {
@@ -1497,18 +1500,15 @@ __global__ void __launch_bounds__(RB_MAX_THREADS, 1) k_pcg_rbp(PcgArgs a) {
       for (int k = 0; k < D; ++k) v[3] += bv[k] * bv[k];
     }
     const double* part = allreduce4_post(a.part, a.part1, v, sh.red);
-    if (black) {
-      double vt[D];
-      trmv<D, double, false>(Mp, bd, w, vt);
-      publish(vt);
-    }
     if (!bar()) return;                 // partials and v are visible everywhere
     if (red) {
       double y[D];
       red_solve(nullptr, y);
       publish(y);
     }
-    allreduce4_collect(part, sh.red, tot);   // before the next barrier
+    // before the next barrier; the loads run on the last four warps (black voxels or none,
+    // idle in the red phase), beside the red warps' neighbour loads
+    allreduce4_collect(part, sh.red, tot, bd >= 128 ? (bd >> 5) - 4 : 0);
     if (first) {
       bb = tot[3];
       tol2 = a.delta * a.delta * bb;
@@ -1748,20 +1748,22 @@ __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_mixed_rbp(PcgArgs a)
           q2 += r[k] * r[k];
         }
       }
-      const FF v[4] = {ff_of(g), ff_of(dl), ff_of(q2), ff_of(0.f)};
-      const float* part = allreduce4_ff_post(a.part, a.part1, v, sh.red);
+      // m = M^-1 w published before the block reduction, so that its stores are in flight
       float m[D];
       if (black) {
         symv<D, float>(Mp32, bd, w, m);
         publish(m);
       }
+      const FF v[4] = {ff_of(g), ff_of(dl), ff_of(q2), ff_of(0.f)};
+      const float* part = allreduce4_ff_post(a.part, a.part1, v, sh.red);
       if (!bar()) return;                 // partials and m are visible everywhere
       if (red) {
         float y[D];
         red_solve(nullptr, y);
         publish(y);
       }
-      allreduce4_ff_collect(part, sh.red, tot);
+      // the loads run on the last four warps (black voxels or none, idle in the red phase)
+      allreduce4_ff_collect(part, sh.red, tot, bd >= 128 ? (bd >> 5) - 4 : 0);
       const bool capped = it >= a.max_inner || inner_total + it >= a.max_iter;
       cg_scalar_step(sh, tot[0], tot[1], tot[2], itol2, capped ? 1 : 0, 1, alpha, beta, gam, rgam, ralpha);
       const int code = sh.code;
