@@ -1,7 +1,8 @@
 """Pins of the oracle's preconditioners (CPU only): the red-black symmetric SOR operator in
 factored form against the voxel-by-voxel forward/backward SOR sweeps (brute force, tiny
 lattices), its SPD-ness and the SSOR bound 0 < eig(M^-1 B~) <= 1, the reduction to
-block-Jacobi without couplings, and the two-colouring of the lattice."""
+block-Jacobi without couplings, the two-colouring of the lattice, the red-black reduced
+(Schur) system, and CG on its split-preconditioned form against block-Jacobi PCG."""
 import numpy as np
 import pytest
 
@@ -110,3 +111,44 @@ def test_weighted_factored_form_equals_sor_sweeps(omega):
     a = precond.ssor_apply(lat, blocks, scale, v, omega)
     b = precond.ssor_apply_sweeps(lat, blocks, scale, v, omega)
     assert np.allclose(a, b, rtol=1e-12, atol=1e-12)
+
+
+def test_split_preconditioned_cg_has_the_iterates_of_block_jacobi_pcg():
+    """CG without a preconditioner on L_b^-1 S L_b^-T (Dg_b = L_b L_b', the black voxels'
+    diagonal blocks) produces, mapped back by x_b = L_b^-T x^, the iterates of CG on S
+    preconditioned by Dg_b, and its residual maps back by r = L_b r^. So a solver on the
+    split form may stop on |L_b r^| with the iteration counts of the preconditioned one."""
+    lat, blocks, scale, _ = small_problem(17, D=3, neighbourhood=6)
+    rng = np.random.default_rng(4)
+    b = rng.standard_normal((lat.N, 3))
+    S, bhat, _, nr = precond.schur_system(lat, blocks, scale, b)
+    S = S.toarray()
+    _, Dg, _, _ = precond.split(lat, blocks, scale)
+    Db = Dg.toarray()[nr:, nr:]
+    Lb = np.linalg.cholesky(Db)
+    Li = np.linalg.inv(Lb)
+    Sh = Li @ S @ Li.T
+    n = len(bhat)
+    x = np.zeros(n)
+    r = bhat.copy()
+    z = np.linalg.solve(Db, r)
+    p = z.copy()
+    rz = r @ z
+    xh = np.zeros(n)
+    rh = Li @ bhat
+    ph = rh.copy()
+    rr = rh @ rh
+    for _ in range(8):
+        q = S @ p
+        a = rz / (p @ q)
+        x, r = x + a * p, r - a * q
+        z = np.linalg.solve(Db, r)
+        rz2 = r @ z
+        p, rz = z + rz2 / rz * p, rz2
+        qh = Sh @ ph
+        ah = rr / (ph @ qh)
+        xh, rh = xh + ah * ph, rh - ah * qh
+        rr2 = rh @ rh
+        ph, rr = rh + rr2 / rr * ph, rr2
+        assert np.allclose(Li.T @ xh, x, rtol=0, atol=1e-10 * np.abs(x).max())
+        assert np.allclose(Lb @ rh, r, rtol=0, atol=1e-10 * np.abs(bhat).max())
