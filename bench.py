@@ -86,11 +86,12 @@ def pcg_bytes_per_voxel_iter(K, w=8):
     return w * (11 * K + 2 * (K * (K + 1) // 2))
 
 
-# DRAM bytes (read + write) of one W-solve launch on the whole-brain workload, from one ncu
-# capture of each kernel version (pipelined split-preconditioned reduced system: 25.45 MB +
-# 0.64 MB; SSOR form: 22.99 MB + 0.63 MB): the first touch of the staged blocks, factors, b
-# and x; the iterations run from L2.
-NCU_TRAFFIC_W = {"reduced": 26.09e6, "ssor": 23.62e6}
+# DRAM bytes (read + write) of one W-solve launch on the whole-brain workload, from an ncu
+# capture of the current kernel version, or None when the kernel has changed since its last
+# capture. The last captures (pipelined split-preconditioned reduced system: 25.45 MB +
+# 0.64 MB; SSOR form: 22.99 MB + 0.63 MB: the first touch of the staged blocks, factors, b and
+# x, the iterations running from L2) predate the current grid barrier.
+NCU_TRAFFIC_W = {"reduced": None, "ssor": None}
 
 
 def precond_options(args):

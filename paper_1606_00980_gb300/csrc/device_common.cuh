@@ -251,9 +251,13 @@ __device__ __forceinline__ void sym_mul(const T* B, const U* p, U* q) {
 }
 
 // ---------------------------------------------------------------------------------------
-// Bounded grid barrier for cooperative (co-resident) launches. Thread 0 of every CTA arrives
-// with an acquire-release atomic on a counter; the last to arrive resets it and releases a
-// generation word that the others poll with acquire loads. Every wait has a time limit read
+// Bounded grid barrier for cooperative (co-resident) launches. The host zeroes the arrival
+// counter (and the generation word) before every cooperative launch (reset_grid_barrier);
+// during the launch the counter only grows. Thread 0 of every CTA arrives with a release
+// reduction on it, which needs no round trip, and barrier j of the launch (0-based) is passed
+// once the counter reaches (j + 1) x gridDim.x, which thread 0 polls with acquire loads. The
+// generation word is released only by the multi-RHS reducing barrier, whose last CTA to
+// arrive does scalar work before the others may go on. Every wait has a time limit read
 // from %globaltimer: on expiry the CTA records a timeout in *err and returns false, and
 // every CTA leaves at its next barrier. The barrier never traps.
 // ---------------------------------------------------------------------------------------
@@ -292,29 +296,37 @@ __device__ __forceinline__ void red_add_release(unsigned int* p, unsigned int v)
   asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-__device__ __forceinline__ void st_relaxed(unsigned int* p, unsigned int v) {
-  asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+__device__ __forceinline__ void st_release(unsigned int* p, unsigned int v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
 constexpr int ERR_TIMEOUT_CODE = 5;
 constexpr int ERR_NOT_SPD_CODE = 3;
 
-// The barrier generation as thread 0 of this CTA last saw it. grid_barrier_start reads the
-// generation word once when a kernel starts (no CTA can complete a barrier before every CTA
-// has arrived, so all read the same value); every barrier then advances the copy itself, so
-// an arrival is one atomic instead of a dependent load followed by an atomic. Every kernel
-// that uses the barriers below calls grid_barrier_start first.
+// The number of barriers this CTA has passed in the current launch (thread 0's copy). Every
+// kernel that uses the barriers below calls grid_barrier_start first; the counter it pairs
+// with was zeroed by the host before the launch.
 static __shared__ unsigned int g_bar_gen;
 
-__device__ __forceinline__ void grid_barrier_start(const GridBarrier& b) {
-  if (threadIdx.x == 0) g_bar_gen = ld_acquire(b.gen);
+__device__ __forceinline__ void grid_barrier_start(const GridBarrier&) {
+  if (threadIdx.x == 0) g_bar_gen = 0u;
 }
 
-// Polls the generation word until it differs from g0; false on error or time-out.
-__device__ __forceinline__ bool wait_generation(const GridBarrier& b, unsigned int g0) {
+// Zeroes the arrival counter and the generation word; the launchers call it on the launch
+// stream before every cooperative launch that uses the barrier.
+inline cudaError_t reset_grid_barrier(const GridBarrier& b, cudaStream_t stream) {
+  if (b.gen == b.count + 1) return cudaMemsetAsync(b.count, 0, 2 * sizeof(unsigned int), stream);
+  cudaError_t e = cudaMemsetAsync(b.count, 0, sizeof(unsigned int), stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b.gen, 0, sizeof(unsigned int), stream);
+  return e;
+}
+
+// Polls *w until it has reached target (wrap-safe); false on error or time-out.
+__device__ __forceinline__ bool wait_reach(const GridBarrier& b, const unsigned int* w,
+                                           unsigned int target) {
   const unsigned long long t0 = globaltimer_ns();
   unsigned int spins = 0;
-  while (ld_acquire(b.gen) == g0) {
+  while ((int)(ld_acquire(w) - target) < 0) {
     if ((++spins & 255u) == 0u) {
       if (ld_acquire_int(b.err) != 0) return false;
       if (globaltimer_ns() - t0 > b.timeout_ns) {
@@ -326,18 +338,17 @@ __device__ __forceinline__ bool wait_generation(const GridBarrier& b, unsigned i
   return true;
 }
 
+// Arrival of this CTA at barrier g0 of the launch and the wait for all others (thread 0).
+__device__ __forceinline__ bool arrive_and_wait(const GridBarrier& b, unsigned int g0) {
+  red_add_release(b.count, 1u);
+  return wait_reach(b, b.count, (g0 + 1u) * gridDim.x);
+}
+
 __device__ __forceinline__ bool grid_sync(const GridBarrier& b, int* sh_flag) {
   __syncthreads();
   if (threadIdx.x == 0) {
     const unsigned int g0 = g_bar_gen;
-    const unsigned int arrived = atom_add_acq_rel(b.count, 1u);
-    bool ok = true;
-    if (arrived == gridDim.x - 1) {
-      st_relaxed(b.count, 0u);
-      red_add_release(b.gen, 1u);
-    } else {
-      ok = wait_generation(b, g0);
-    }
+    const bool ok = arrive_and_wait(b, g0);
     g_bar_gen = g0 + 1u;
     *sh_flag = ok ? 0 : 1;
   }
@@ -461,20 +472,12 @@ __device__ __forceinline__ bool grid_allreduce4(const GridBarrier& b, double* pa
                                                 const double* v, double* sh, int* sh_int, double* out) {
   double bt[4];
   block_reduce4(v, sh, bt);
-  const unsigned int nblocks = gridDim.x;
   if (threadIdx.x == 0) {
     const unsigned int g0 = g_bar_gen;
     double* part = (g0 & 1u) ? part1 : part0;
 #pragma unroll
     for (int i = 0; i < 4; ++i) part[(size_t)blockIdx.x * 4 + i] = bt[i];
-    const unsigned int arrived = atom_add_acq_rel(b.count, 1u);
-    bool ok = true;
-    if (arrived == nblocks - 1) {
-      st_relaxed(b.count, 0u);
-      red_add_release(b.gen, 1u);
-    } else {
-      ok = wait_generation(b, g0);
-    }
+    const bool ok = arrive_and_wait(b, g0);
     g_bar_gen = g0 + 1u;
     sh_int[0] = ok ? 0 : 1;
     sh_int[1] = (int)(g0 & 1u);
@@ -600,7 +603,6 @@ __device__ __forceinline__ bool grid_allreduce4_ff(const GridBarrier& b, double*
   float* shw = reinterpret_cast<float*>(sh);   // [warp][4][2] floats: 96 floats = 48 doubles
   FF c4[4];
   block_reduce4_ff(v, shw, c4);
-  const unsigned int nblocks = gridDim.x;
   if (threadIdx.x == 0) {
     const unsigned int g0 = g_bar_gen;
     float* row = reinterpret_cast<float*>((g0 & 1u) ? part1 : part0) + (size_t)blockIdx.x * 8;
@@ -609,14 +611,7 @@ __device__ __forceinline__ bool grid_allreduce4_ff(const GridBarrier& b, double*
       row[2 * i + 0] = c4[i].hi;
       row[2 * i + 1] = c4[i].lo;
     }
-    const unsigned int arrived = atom_add_acq_rel(b.count, 1u);
-    bool ok = true;
-    if (arrived == nblocks - 1) {
-      st_relaxed(b.count, 0u);
-      red_add_release(b.gen, 1u);
-    } else {
-      ok = wait_generation(b, g0);
-    }
+    const bool ok = arrive_and_wait(b, g0);
     g_bar_gen = g0 + 1u;
     sh_int[0] = ok ? 0 : 1;
     sh_int[1] = (int)(g0 & 1u);

@@ -257,9 +257,11 @@ __device__ __forceinline__ bool mrhs_reduce(const MrhsArgs& a, const Units& U, i
                                             int* sh_int, int* any_active, int* any_pending) {
   __syncthreads();
   if (threadIdx.x == 0) {
+    // the arrival counter only grows during a launch: the last CTA of barrier g0 is the one
+    // whose arrival takes it to (g0 + 1) x gridDim.x
     const unsigned int g0 = g_bar_gen;
     const unsigned int arrived = atom_add_acq_rel(a.bar.count, 1u);
-    sh_int[0] = (arrived == gridDim.x - 1) ? 1 : 0;
+    sh_int[0] = (arrived == (g0 + 1u) * gridDim.x - 1u) ? 1 : 0;
     sh_int[1] = (int)g0;
     sh_int[2] = 0;
     sh_int[3] = 0;
@@ -289,14 +291,13 @@ __device__ __forceinline__ bool mrhs_reduce(const MrhsArgs& a, const Units& U, i
       a.flags[0] = sh_int[2];
       a.flags[1] = sh_int[3];
       __threadfence();
-      st_relaxed(a.bar.count, 0u);
-      red_add_release(a.bar.gen, 1u);
+      st_release(a.bar.gen, (unsigned int)sh_int[1] + 1u);
       g_bar_gen = (unsigned int)sh_int[1] + 1u;
     }
     __syncthreads();
   } else {
     if (threadIdx.x == 0) {
-      const bool ok = wait_generation(a.bar, (unsigned int)sh_int[1]);
+      const bool ok = wait_reach(a.bar, a.bar.gen, (unsigned int)sh_int[1] + 1u);
       g_bar_gen = (unsigned int)sh_int[1] + 1u;
       sh_int[2] = ok ? __ldcg(a.flags + 0) : 0;
       sh_int[3] = ok ? __ldcg(a.flags + 1) : 0;
@@ -922,6 +923,8 @@ static cudaError_t launch_d(const MrhsArgs& a, cudaStream_t stream, int* units_o
     b.ssor = 1;
     b.omega = 1.0;
   }
+  e = reset_grid_barrier(b.bar, stream);
+  if (e != cudaSuccess) return e;
   void* args[] = {(void*)&b};
   return cudaLaunchCooperativeKernel(kern, dim3((unsigned)grid), dim3(MRHS_THREADS), args, shm, stream);
 }

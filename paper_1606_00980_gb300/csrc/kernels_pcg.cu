@@ -2340,6 +2340,8 @@ cudaError_t launch_resident(const PcgArgs& a, cudaStream_t stream, int* grid_out
   *launched = true;
   PcgArgs b = a;
   b.res_per = per;
+  cudaError_t er = reset_grid_barrier(b.bar, stream);
+  if (er != cudaSuccess) return er;
   void* args[] = {(void*)&b};
   return cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(threads), args, shm, stream);
 }
@@ -2367,6 +2369,8 @@ static cudaError_t launch_d(const PcgArgs& a, cudaStream_t stream, int* grid_out
   if (need < grid) grid = need < 1 ? 1 : need;
   if (a.max_grid > 0 && grid > a.max_grid) grid = a.max_grid;
   if (grid_out) *grid_out = grid;
+  e = reset_grid_barrier(a.bar, stream);
+  if (e != cudaSuccess) return e;
   void* args[] = {(void*)&a};
   return cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(PCG_THREADS), args, 0, stream);
 }
