@@ -24,6 +24,8 @@ gibbs    -- one Gibbs sweep (Section 3.2) and one spatial-VB step (Section 3.3, 
 probes   -- exact log-determinant and trace terms behind the stochastic probes
 precond  -- block-Jacobi and red-black symmetric SOR preconditioners (replacing the
             incomplete Cholesky of Section 3.1), factored form and voxel-by-voxel sweeps
+multigrid -- aggregation multigrid V-cycle (Galerkin coarse operators, symmetric red-black
+            block Gauss-Seidel smoothing) as a further replacement
 summaries -- posterior summaries: chain PPMs and joint PPMs (Eq. MCMCPPM, Eq. MCMCjointPPM),
             SVB sample moments and Gaussian PPMs (Section 3.3), the unnormalised log joint
             posterior (Eq. UnnormalisedJointPosterior)
