@@ -64,12 +64,17 @@ typedef struct {
                                          solves (FP64, and the FP32 inner iterations of mixed),
                                          SVB samples and grouped chains; the log-det / trace
                                          probes always use block-Jacobi */
-#define BFMRI_PRECOND_RB_REDUCED   3  /* the FP64 resident solver runs CG on the red-black
-                                         reduced system (the black voxels' Schur complement
-                                         S = Dg_b - L Dg_r^-1 U, preconditioned by Dg_b),
-                                         which takes the iterates of SSOR with omega = 1 at
-                                         fewer barriers and block solves per iteration;
-                                         every other solver uses SSOR with omega = 1 */
+#define BFMRI_PRECOND_RB_REDUCED   3  /* CG on the red-black reduced system (the black
+                                         voxels' Schur complement S = Dg_b - L Dg_r^-1 U,
+                                         preconditioned by Dg_b; for D <= 6 the FP64
+                                         resident solver runs it in the split form
+                                         L_b^-1 S L_b^-T, Dg_b = L_b L_b'), which takes the
+                                         iterates of SSOR with omega = 1 at fewer barriers
+                                         and block products per iteration. The FP64 and
+                                         mixed resident solvers, the mixed streaming solver
+                                         and the multi-RHS solver (at most one right-hand
+                                         side per warp) run it; the FP64 streaming solver
+                                         and larger batches use SSOR with omega = 1 */
 
 #define BFMRI_PREC_FP64  0  /* FP64 PCG */
 #define BFMRI_PREC_MIXED 1  /* FP32 inner PCG inside an FP64 iterative-refinement loop */
