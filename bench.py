@@ -242,6 +242,16 @@ def cpu_threads():
         return 1
 
 
+def cpu_baseline(args, w):
+    """The oracle on this host's cores: one Gibbs sweep on two central slices of the
+    headline workload, scaled to the whole volume by the voxel ratio."""
+    zc = w.dims[2] // 2
+    t, n_s = oracle_sweep_time(w, zc - 1, zc + 1)
+    return {"value": (n_s / w.N) / t, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
+            "sample": f"one oracle Gibbs sweep on slices z={zc - 1}..{zc} ({n_s} of {w.N} voxels, "
+                      f"{t:.1f} s), scaled to the whole volume by the voxel ratio"}
+
+
 def run_reference(args, world, rank):
     """The FP64 oracle on the host cores: one 1-slice slab of the workload per step; the
     value is scaled to whole-volume W-draws/s by the voxel ratio (optimistic for the oracle:
@@ -367,29 +377,27 @@ def run_ours(args, world, rank, local):
             "iterations_per_launch": iters_per_launch, "avg_launch_ms": dur_s * 1e3,
             "share_of_step": pw["ms"] / total_ms if total_ms > 0 else None}
 
-    # the same chain with the mixed-precision solver (FP32 inner, FP64 refinement, same delta)
-    mixed = run_mixed(args, w, flush, stream) if not args.no_mixed else None
-    # posterior summaries (chain PPMs, moments, log joint) on the same workload
-    summ = run_summaries(args, w) if (rank == 0 and not args.no_summaries) else None
-    conv = run_convergence(args) if (rank == 0 and args.convergence) else None
-
-    # independent chains of the same subject advanced together (one multi-RHS launch per solve)
-    chains = run_chains(args, w, flush, stream, value) if not args.no_chains else None
-    precs = run_precond_compare(args, w) if (rank == 0 and not args.no_precond) else None
-    graphs = run_graph_compare(args, w, flush, stream) if (rank == 0 and not args.no_graph) else None
-    # end to end through the C ABI with host buffers
+    # Auxiliary legs. Each runs inside run_leg: a leg that raises is recorded as
+    # {"error": ...} in the line (and makes the exit status non-zero) instead of taking the
+    # headline, roofline, cpu_baseline and e2e figures down with it. The serving leg, the
+    # only one with several host threads launching at once, runs last.
+    errors = {}
+    main_rank = rank == 0
+    mixed = run_leg(errors, "mixed_precision", run_mixed, args, w, flush, stream) if not args.no_mixed else None
+    summ = run_leg(errors, "summaries", run_summaries, args, w) if (main_rank and not args.no_summaries) else None
+    conv = run_leg(errors, "convergence", run_convergence, args) if (main_rank and args.convergence) else None
+    chains = run_leg(errors, "grouped_chains", run_chains, args, w, flush, stream, value) if not args.no_chains else None
+    precs = run_leg(errors, "preconditioners", run_precond_compare, args, w) if (main_rank and not args.no_precond) else None
+    graphs = run_leg(errors, "captured_sweeps", run_graph_compare, args, w, flush, stream) if (main_rank and not args.no_graph) else None
     del flush
-    e2e = run_e2e(args, w) if rank == 0 else None
-    serving = run_serving(args) if (rank == 0 and not args.no_serving) else None
-    batched = run_batched(args) if (rank == 0 and not args.no_batched) else None
+    # end to end through the C ABI with host buffers
+    e2e = run_leg(errors, "e2e", run_e2e, args, w) if main_rank else None
+    batched = run_leg(errors, "batched_probes", run_batched, args) if (main_rank and not args.no_batched) else None
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        zc = w.dims[2] // 2
-        t, n_s = oracle_sweep_time(w, zc - 1, zc + 1)
-        cpu = {"value": (n_s / N) / t, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
-               "sample": f"one oracle Gibbs sweep on slices z={zc - 1}..{zc} ({n_s} of {N} voxels, "
-                         f"{t:.1f} s), scaled to the whole volume by the voxel ratio"}
-    if rank == 0:
+    if main_rank and world == 1 and not args.no_cpu_baseline:
+        cpu = run_leg(errors, "cpu_baseline", cpu_baseline, args, w)
+    serving = run_leg(errors, "serving", run_serving, args) if (main_rank and not args.no_serving) else None
+    if main_rank:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": total_s / args.steps * 1e3, "higher_is_better": True,
@@ -409,7 +417,22 @@ def run_ours(args, world, rank, local):
                 "kernel_ms_per_step": {k: v["ms"] / n_prof for k, v in tim_p.items() if v["launches"]},
                 "kernel_ms_per_step_note": "the same chain and sweeps rerun with every launch "
                                            "timed; the timed region times only the solver launches"}
+        if errors:
+            line["errors"] = errors
         print(json.dumps(line), flush=True)
+    return 1 if errors else 0
+
+
+def run_leg(errors, name, fn, *a, **kw):
+    """Runs one auxiliary measurement; on an exception records it under errors[name] and
+    returns {"error": ...} so that the JSON line still carries every other figure."""
+    try:
+        return fn(*a, **kw)
+    except Exception as e:           # noqa: BLE001 - recorded in the JSON line, not hidden
+        import traceback
+        traceback.print_exc(file=sys.stderr)
+        errors[name] = f"{type(e).__name__}: {e}"
+        return {"error": errors[name]}
 
 
 def bench_contrasts(K):
@@ -849,36 +872,36 @@ def run_serving(args):
     opts = dict(precision=bfmri.PREC_MIXED, delta=1e-8, inner_tol=1e-6, **precond_options(args))
     # capacity pilot: every pool member alone (service time), then a saturating burst of
     # 4 x the pool through all slots (sustained requests/s)
-    srv = bfmri.Server(budget, slots, sm_budget)
-    pilot = []
-    for i, w in enumerate(pool):
-        t = srv.submit(w, 8, first_counter=0, seed=1000 + i, **opts)
-        r = srv.poll(t)
-        pilot.append(r["end_s"] - r["start_s"])
-    mean_service = float(np.mean(pilot))
-    t0 = time.perf_counter()
-    burst = [srv.submit(pool[i % len(pool)], 8, first_counter=i, seed=2000 + i, **opts)
-             for i in range(4 * len(pool))]
-    for t in burst:
-        srv.poll(t)
-    capacity = 4 * len(pool) / (time.perf_counter() - t0)
-    srv.close()
+    # every server is closed in a finally block: closing waits for the requests in flight,
+    # so an exception never leaves slot kernels running while the process exits
+    with bfmri.Server(budget, slots, sm_budget) as srv:
+        pilot = []
+        for i, w in enumerate(pool):
+            t = srv.submit(w, 8, first_counter=0, seed=1000 + i, **opts)
+            r = srv.poll(t)
+            pilot.append(r["end_s"] - r["start_s"])
+        mean_service = float(np.mean(pilot))
+        t0 = time.perf_counter()
+        burst = [srv.submit(pool[i % len(pool)], 8, first_counter=i, seed=2000 + i, **opts)
+                 for i in range(4 * len(pool))]
+        for t in burst:
+            srv.poll(t)
+        capacity = 4 * len(pool) / (time.perf_counter() - t0)
     rate = 0.8 * capacity                      # offered load 0.8 of the measured capacity
     n_req = args.serving_requests
     arrivals = np.cumsum(rng.exponential(1.0 / rate, n_req))
     picks = rng.integers(0, len(pool), n_req)
-    srv = bfmri.Server(budget, slots, sm_budget)
-    t0 = time.perf_counter()
-    tickets = []
-    for i in range(n_req):
-        delay = arrivals[i] - (time.perf_counter() - t0)
-        if delay > 0:
-            time.sleep(delay)
-        tickets.append(srv.submit(pool[picks[i]], 8, first_counter=17 * i, seed=5000 + i, **opts))
-    results = [srv.poll(t) for t in tickets]
-    makespan = time.perf_counter() - t0
-    st = srv.stats()
-    srv.close()
+    with bfmri.Server(budget, slots, sm_budget) as srv:
+        t0 = time.perf_counter()
+        tickets = []
+        for i in range(n_req):
+            delay = arrivals[i] - (time.perf_counter() - t0)
+            if delay > 0:
+                time.sleep(delay)
+            tickets.append(srv.submit(pool[picks[i]], 8, first_counter=17 * i, seed=5000 + i, **opts))
+        results = [srv.poll(t) for t in tickets]
+        makespan = time.perf_counter() - t0
+        st = srv.stats()
     lat = np.array([r["end_s"] - r["submit_s"] for r in results]) * 1e3
     return {"requests": n_req, "p50_ms": float(np.percentile(lat, 50)),
             "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
@@ -951,16 +974,19 @@ def main():
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     world, rank, local = dist_setup(args)
+    rc = 0
     if args.impl == "reference":
         run_reference(args, world, rank)
     elif args.only_batched:
         if rank == 0:
             print(json.dumps(run_batched(args)), flush=True)
     else:
-        run_ours(args, world, rank, local)
+        rc = run_ours(args, world, rank, local)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+    if rc:
+        sys.exit(rc)
 
 
 if __name__ == "__main__":

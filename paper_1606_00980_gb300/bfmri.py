@@ -10,6 +10,7 @@ owns a handle.
 """
 from __future__ import annotations
 
+import atexit
 import ctypes as C
 import os
 
@@ -277,6 +278,17 @@ class Server:
         _check(self.lib.bfmri_server_create(int(budget_bytes), slots, sm_budget, C.byref(h)))
         self.h = h
         self._keep = {}
+        # the slots' threads read the host arrays in _keep and write W and alpha into them:
+        # a server left open at interpreter exit is drained first (destroy waits for every
+        # admitted and queued request), before those arrays or the CUDA context go away
+        atexit.register(self.close)
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+        return False
 
     def submit(self, w, n_sweeps, first_counter=0, **opt_fields):
         o = bfmri_default_options()
@@ -321,9 +333,10 @@ class Server:
 
     def close(self):
         if self.h:
-            _check(self.lib.bfmri_server_destroy(self.h))
-            self.h = None
+            h, self.h = self.h, None
+            _check(self.lib.bfmri_server_destroy(h))
             self._keep.clear()
+            atexit.unregister(self.close)
 
 
 def bfmri_pcg_solve_static(N, D, neighbourhood, nbr_ptr, ld, blocks_ptr, scale_ptr, b_ptr,

@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -28,6 +29,22 @@ namespace bfmri {
 void set_global_error(const std::string& msg) {
   std::lock_guard<std::mutex> lk(g_err_mu);
   g_create_err = msg;
+}
+}  // namespace bfmri
+
+namespace bfmri {
+cudaError_t raise_smem_limit(const void* kern, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, size_t> limit;   // (kernel, device) -> set limit
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(mu);
+  size_t& cur = limit[{kern, dev}];
+  if (bytes <= cur) return cudaSuccess;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) cur = bytes;
+  return e;
 }
 }  // namespace bfmri
 

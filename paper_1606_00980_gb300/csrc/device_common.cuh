@@ -312,6 +312,13 @@ __device__ __forceinline__ void grid_barrier_start(const GridBarrier&) {
   if (threadIdx.x == 0) g_bar_gen = 0u;
 }
 
+// Raises the dynamic shared-memory limit of kernel `kern` on the current device to at least
+// `bytes` and never lowers it. The limit is a property of the function, shared by every host
+// thread that launches it (the server's slots run launchers concurrently); setting it to each
+// call's own size could lower it between another thread's set and that thread's launch, which
+// then fails. Returns the error of the attribute call, cudaSuccess when no change is needed.
+cudaError_t raise_smem_limit(const void* kern, size_t bytes);
+
 // Zeroes the arrival counter and the generation word; the launchers call it on the launch
 // stream before every cooperative launch that uses the barrier.
 inline cudaError_t reset_grid_barrier(const GridBarrier& b, cudaStream_t stream) {

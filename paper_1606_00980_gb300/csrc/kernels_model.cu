@@ -549,24 +549,19 @@ template <int K>
 static cudaError_t stats_k(const StatsArgs& a, cudaStream_t s) {
   const size_t shm = (size_t)a.T * K * sizeof(double);
   const unsigned gx = (unsigned)((a.N + STATS_THREADS - 1) / STATS_THREADS);
-  if (a.T >= 2 * a.P) {
-    const dim3 grid(gx, 2 * a.P + 1);
-    if (a.y_is_f64) {
-      cudaFuncSetAttribute(k_stats<K, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
-      k_stats<K, double><<<grid, STATS_THREADS, shm, s>>>(a);
-    } else {
-      cudaFuncSetAttribute(k_stats<K, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
-      k_stats<K, float><<<grid, STATS_THREADS, shm, s>>>(a);
-    }
+  const bool lagdiff = a.T >= 2 * a.P;
+  const dim3 grid(gx, lagdiff ? 2 * a.P + 1 : a.P + 1);
+  const void* kern = lagdiff ? (a.y_is_f64 ? (const void*)k_stats<K, double> : (const void*)k_stats<K, float>)
+                             : (a.y_is_f64 ? (const void*)k_stats_direct<K, double>
+                                           : (const void*)k_stats_direct<K, float>);
+  cudaError_t e = raise_smem_limit(kern, shm);
+  if (e != cudaSuccess) return e;
+  if (lagdiff) {
+    if (a.y_is_f64) k_stats<K, double><<<grid, STATS_THREADS, shm, s>>>(a);
+    else k_stats<K, float><<<grid, STATS_THREADS, shm, s>>>(a);
   } else {
-    const dim3 grid(gx, a.P + 1);
-    if (a.y_is_f64) {
-      cudaFuncSetAttribute(k_stats_direct<K, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
-      k_stats_direct<K, double><<<grid, STATS_THREADS, shm, s>>>(a);
-    } else {
-      cudaFuncSetAttribute(k_stats_direct<K, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
-      k_stats_direct<K, float><<<grid, STATS_THREADS, shm, s>>>(a);
-    }
+    if (a.y_is_f64) k_stats_direct<K, double><<<grid, STATS_THREADS, shm, s>>>(a);
+    else k_stats_direct<K, float><<<grid, STATS_THREADS, shm, s>>>(a);
   }
   return cudaGetLastError();
 }
@@ -584,7 +579,8 @@ cudaError_t launch_stats(const StatsArgs& a, cudaStream_t s) {
 template <int K>
 static cudaError_t assemble_w_k(const AssembleArgs& a, cudaStream_t s) {
   const size_t shm = (size_t)n_syy(a.P) * ntri(K) * sizeof(double);
-  cudaFuncSetAttribute(k_assemble_w<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+  cudaError_t e = raise_smem_limit((const void*)k_assemble_w<K>, shm);
+  if (e != cudaSuccess) return e;
   k_assemble_w<K><<<(a.g.N + VOX_THREADS - 1) / VOX_THREADS, VOX_THREADS, shm, s>>>(a);
   return cudaGetLastError();
 }
@@ -592,7 +588,8 @@ static cudaError_t assemble_w_k(const AssembleArgs& a, cudaStream_t s) {
 template <int K>
 static cudaError_t assemble_a_k(const AssembleArgs& a, cudaStream_t s) {
   const size_t shm = quad_weight_doubles(K, a.P) * sizeof(double);
-  cudaFuncSetAttribute(k_assemble_a<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+  cudaError_t e = raise_smem_limit((const void*)k_assemble_a<K>, shm);
+  if (e != cudaSuccess) return e;
   k_assemble_a<K><<<(a.g.N + VOX_THREADS - 1) / VOX_THREADS, VOX_THREADS, shm, s>>>(a);
   return cudaGetLastError();
 }

@@ -900,7 +900,7 @@ static cudaError_t launch_d(const MrhsArgs& a, cudaStream_t stream, int* units_o
   const void* kern = a.f32 ? (const void*)k_mrhs<D, float> : (const void*)k_mrhs<D, double>;
   const size_t shm = a.f32 ? mrhs_stage_bytes<D, float>() : mrhs_stage_bytes<D, double>();
   if (shm > 0) {
-    cudaError_t ea = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    cudaError_t ea = raise_smem_limit(kern, shm);
     if (ea != cudaSuccess) return ea;
   }
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, MRHS_THREADS, shm);

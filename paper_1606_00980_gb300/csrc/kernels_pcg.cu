@@ -2326,7 +2326,7 @@ cudaError_t launch_resident(const PcgArgs& a, cudaStream_t stream, int* grid_out
   else kred = (const void*)k_pcg_rb<D>;
   const void* kern = a.mixed ? (a.reduced ? (const void*)k_pcg_mixed_rbp<D> : (const void*)k_pcg_mixed_res<D>)
                              : (a.reduced ? kred : (const void*)k_pcg_res<D>);
-  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm) != cudaSuccess) {
+  if (raise_smem_limit(kern, shm) != cudaSuccess) {
     cudaGetLastError();
     return cudaSuccess;
   }

@@ -342,7 +342,7 @@ cudaError_t svb_sum_k(const SvbSumArgs& a, cudaStream_t s) {
 template <int K>
 cudaError_t log_joint_k(const LogJointArgs& a, cudaStream_t s) {
   const size_t shm = quad_weight_doubles(K, a.P) * sizeof(double);
-  cudaFuncSetAttribute(k_log_joint_voxels<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+  if (cudaError_t e = raise_smem_limit((const void*)k_log_joint_voxels<K>, shm)) return e;
   const int grid = log_joint_grid(a.g.N);
   k_log_joint_voxels<K><<<grid, LJ_THREADS, shm, s>>>(a);
   k_log_joint_final<<<1, 64, 0, s>>>(a, grid);

@@ -173,14 +173,14 @@ static cudaError_t svb_d(int what, const SvbArgs& a, cudaStream_t s, int* grid_o
   const size_t shm = quad_weight_doubles(D, a.P) * sizeof(double);
   switch (what) {
     case 1:
-      cudaFuncSetAttribute(k_svb_gram<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+      if (cudaError_t e = raise_smem_limit((const void*)k_svb_gram<D>, shm)) return e;
       k_svb_gram<D><<<blocks, SVB_THREADS, shm, s>>>(a);
       break;
     case 2:
       k_svb_rhs<D><<<dim3(blocks, a.S), SVB_THREADS, 0, s>>>(a);
       break;
     case 3:
-      cudaFuncSetAttribute(k_svb_lambda<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+      if (cudaError_t e = raise_smem_limit((const void*)k_svb_lambda<D>, shm)) return e;
       k_svb_lambda<D><<<blocks, SVB_THREADS, shm, s>>>(a);
       break;
     case 4:

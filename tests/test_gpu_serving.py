@@ -73,3 +73,64 @@ def test_admission_respects_the_memory_budget():
             s2.submit(ws[0], 1)
         finally:
             s2.close()
+
+
+def bench_like_pool():
+    """Subjects shaped like the serving benchmark's pool at sizes the oracle solves in
+    seconds: every K appears with two different (T, P), Y is FP32, and with four SMs per slot
+    the larger subjects exceed one CTA per SM, so their W and A systems run the streaming
+    mixed-precision solver on the reduced red-black system while the smaller ones run the
+    resident one."""
+    import numpy as np
+    specs = [(1300, 4, 40, 1), (2600, 4, 80, 2), (1800, 6, 60, 3), (2400, 6, 120, 2),
+             (900, 8, 50, 1), (2200, 8, 90, 3)]
+    out = []
+    for i, (n, K, T, P) in enumerate(specs):
+        w = synth.request_workload(seed=700 + i, N_target=n, K=K, T=T, P=P)
+        w.Y = w.Y.astype(np.float32)
+        out.append(w)
+    return out
+
+
+def test_bench_shaped_mix_matches_alone_and_the_oracle():
+    """Four slots of four SMs, reduced red-black preconditioner, mixed precision at
+    delta = 1e-8 (the serving benchmark's options): every request's W is bit-identical alone
+    and in the mix, and a one-sweep request's W equals the oracle's exact draw of the same
+    perturbed system (Algorithm 2, from the prior-mean start state) to 1e-5 relative L2."""
+    from oracle import gibbs, model, philox
+    from oracle.lattice import Lattice
+    from paper_1606_00980_gb300 import bfmri
+    pool = bench_like_pool()
+    opts = dict(precision=bfmri.PREC_MIXED, delta=1e-8, inner_tol=1e-6,
+                precond=bfmri.PRECOND_RB_REDUCED)
+    reqs = []                      # (pool index, sweeps, first counter, seed)
+    for rep in range(2):
+        for i in range(len(pool)):
+            reqs.append((i, 1 if rep == 0 else 3, 11 * i + rep, 900 + 10 * i + rep))
+    s = bfmri.Server(budget_bytes=8 << 30, slots=4, sm_budget=4)
+    try:
+        tickets = [s.submit(pool[i], n, first_counter=c, seed=sd, **opts) for i, n, c, sd in reqs]
+        mixed = [s.poll(t) for t in tickets]
+        st = s.stats()
+    finally:
+        s.close()
+    assert st["peak_running"] >= 3
+    for (i, n, c, sd), got in zip(reqs, mixed):
+        s1 = bfmri.Server(budget_bytes=8 << 30, slots=1, sm_budget=4)
+        try:
+            alone = s1.poll(s1.submit(pool[i], n, first_counter=c, seed=sd, **opts))
+        finally:
+            s1.close()
+        assert np.array_equal(alone["W"], got["W"]), (i, n)
+        assert np.array_equal(alone["alpha"], got["alpha"]), (i, n)
+        if n != 1:
+            continue
+        w = pool[i]
+        lat = Lattice(w.mask, w.neighbourhood)
+        state = gibbs.default_state(w.K, w.P, w.N)
+        Y = w.Y.astype(np.float64)
+        Bd, bw = model.w_blocks_direct(Y, w.X, state["A"], state["lam"], w.eps)
+        W_ref, _ = gibbs.draw_gmrf(lat, Bd, bw, state["alpha"], seed=sd, counter=c,
+                                   tag=philox.TAG_W)
+        err = np.linalg.norm(got["W"] - W_ref) / np.linalg.norm(W_ref)
+        assert err <= 1e-5, (i, err)
