@@ -182,6 +182,9 @@ const char* bfmri_last_error(const bfmri_handle* h);
 
 /* Number of in-mask voxels N, and the problem sizes. */
 int bfmri_num_voxels(const bfmri_handle* h);
+/* Device bytes the handle holds now and at most so far (its own allocations, each as
+ * requested from the allocator: rounded up to 256 bytes). */
+bfmri_status bfmri_device_bytes(const bfmri_handle* h, size_t* now, size_t* peak);
 bfmri_status bfmri_sizes(const bfmri_handle* h, int* N, int* T, int* K, int* P);
 
 /* Sufficient statistics (Appendix A, Eq. log-like: Y enters only through lagged
@@ -446,7 +449,14 @@ typedef struct {
   size_t device_bytes;      /* the admission estimate */
 } bfmri_result;
 
+/* Admission estimate of one request: every device allocation bfmri_create makes for a handle
+ * of this shape (Y included, although the statistics step releases it), each rounded as the
+ * library rounds it, plus a margin of 1/32 and 2 MiB for the pool's own rounding. 0 for
+ * invalid sizes. */
 size_t bfmri_request_device_bytes(int N, int T, int K, int P, int y_dtype, int precision);
+/* High-water mark of the bytes in use from the server's memory pool
+ * (cudaMemPoolAttrUsedMemHigh); reset != 0 restarts it from the current use. */
+bfmri_status bfmri_server_pool_usage(bfmri_server* s, size_t* used_high, int reset);
 bfmri_status bfmri_server_create(size_t budget_bytes, int max_slots, int sm_budget,
                                  bfmri_server** out);
 /* Errors: INVALID_ARG, OOM (the request alone exceeds the budget). */
@@ -467,8 +477,10 @@ bfmri_status bfmri_server_destroy(bfmri_server* s);
  * another framework's memory pool or arena and may not call cudaMalloc behind its back, a
  * process that must not grow its device footprint after start-up, or a real-time loop where
  * an allocation (and the implicit device synchronisation of cudaMalloc / cudaFree) would
- * stall. bfmri_pcg_solve_static solves B~ x = b with the same FP64 block-Jacobi PCG as
- * bfmri_sample_W, on device arrays the caller owns, and allocates nothing: its scratch (the
+ * stall. bfmri_pcg_solve_static solves B~ x = b with the FP64 block-Jacobi PCG that
+ * bfmri_sample_W runs under its default options (options.precond = BFMRI_PRECOND_BLOCK_JACOBI,
+ * precision FP64; the reduced red-black and mixed-precision solvers are not offered here), on
+ * device arrays the caller owns, and allocates nothing: its scratch (the
  * preconditioner factor, five work vectors, reduction and barrier words) lives in one
  * static device array of bfmri_pcg_static_capacity() bytes (32 MiB) that every GPU which
  * loads the library holds until the process exits.
@@ -477,14 +489,18 @@ bfmri_status bfmri_server_destroy(bfmri_server* s);
  *  neighbourhood 4 or 6: how many of the six neighbour planes are used
  *  nbr           device, int32 [6][ld]: compact index of the -x,+x,-y,+y,-z,+z neighbour of
  *                each voxel, or -1
- *  ld            leading dimension (>= N) of every [rows][ld] device array
+ *  ld            leading dimension of every [rows][ld] device array: >= N and a multiple
+ *                of 32 (the other entry points use N rounded up to 32); anything else is
+ *                rejected with BFMRI_ERR_INVALID_ARG
  *  blocks        device, FP64 [D(D+1)/2][ld]: per-voxel data block, packed lower triangle
  *                (entry (i, j), i >= j, in plane i(i+1)/2 + j)
  *  scale         device, FP64 [D]: prior scale per component (alpha or beta)
  *  b             device, FP64 [D][ld]: right-hand side
  *  x             device, FP64 [D][ld]: start value in, solution out (stop when
  *                ||b - B~ x|| <= delta ||b||, or after max_iter iterations)
- *  cuda_stream   stream for all work (NULL: legacy default stream); the call waits for it
+ *  cuda_stream   stream for all work (NULL: legacy default stream); every call copies its
+ *                status words into host memory and synchronises this stream before it
+ *                returns
  *  info          may be NULL
  * Set-up: the first call on each device looks up the device address of the static array
  * (cudaGetSymbolAddress, with that device current) and caches it; make that first call before

@@ -50,7 +50,7 @@ def lanczos(matvec, z, m):
     """m steps of Lanczos with full reorthogonalisation; returns the (m, m) tridiagonal
     (fewer rows if an invariant subspace is found first)."""
     n = len(z)
-    Q = np.zeros((n, m + 1))
+    Q = np.zeros((n, m + 1), order="F")       # columns contiguous for the reorthogonalisation
     a = np.zeros(m)
     b = np.zeros(m)
     Q[:, 0] = z / np.linalg.norm(z)

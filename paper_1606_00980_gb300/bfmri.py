@@ -143,6 +143,8 @@ SIGNATURES = [
     ("bfmri_server_submit", C.c_int, [C.c_void_p, _P(bfmri_request), _P(C.c_longlong)]),
     ("bfmri_server_poll", C.c_int, [C.c_void_p, C.c_longlong, C.c_int, _P(bfmri_result)]),
     ("bfmri_server_stats", C.c_int, [C.c_void_p, _P(C.c_size_t), _P(C.c_int), _P(C.c_size_t)]),
+    ("bfmri_server_pool_usage", C.c_int, [C.c_void_p, _P(C.c_size_t), C.c_int]),
+    ("bfmri_device_bytes", C.c_int, [_h, _P(C.c_size_t), _P(C.c_size_t)]),
     ("bfmri_server_destroy", C.c_int, [C.c_void_p]),
     ("bfmri_pcg_static_capacity", C.c_size_t, []),
     ("bfmri_pcg_static_bytes", C.c_size_t, [C.c_size_t, C.c_int]),
@@ -331,6 +333,12 @@ class Server:
         _check(self.lib.bfmri_server_stats(self.h, C.byref(pb), C.byref(pr), C.byref(iu)))
         return dict(peak_bytes=pb.value, peak_running=pr.value, in_use=iu.value)
 
+    def pool_usage(self, reset=False):
+        """High-water mark of the bytes in use from the server's memory pool."""
+        v = C.c_size_t()
+        _check(self.lib.bfmri_server_pool_usage(self.h, C.byref(v), 1 if reset else 0))
+        return v.value
+
     def close(self):
         if self.h:
             h, self.h = self.h, None
@@ -415,6 +423,12 @@ class Model:
 
     def _c(self, st):
         _check(st, self.handle)
+
+    def device_bytes(self):
+        """(bytes held now, peak so far) of the handle's own device allocations."""
+        a, b = C.c_size_t(), C.c_size_t()
+        self._c(self.lib.bfmri_device_bytes(self.handle, C.byref(a), C.byref(b)))
+        return a.value, b.value
 
     def precompute_stats(self):
         self._c(self.lib.bfmri_precompute_stats(self.handle))

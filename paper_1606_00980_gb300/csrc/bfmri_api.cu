@@ -46,6 +46,36 @@ cudaError_t raise_smem_limit(const void* kern, size_t bytes) {
   if (e == cudaSuccess) cur = bytes;
   return e;
 }
+
+// Rows of the PCG partial-sum buffer of a handle: the largest streaming cooperative grid of
+// its W (D = K) and A (D = P) solvers.
+int handle_max_grid(int K, int P) {
+  int maxgrid = pcg_max_grid(K);
+  if (P > 0) maxgrid = std::max(maxgrid, pcg_max_grid(P));
+  return maxgrid < 1 ? 1024 : maxgrid;
+}
+
+// Device bytes that bfmri_create allocates for a handle (each allocation rounded up to 256
+// bytes as dalloc does), Y included: the peak of a request that runs create, statistics and
+// Gibbs sweeps (no summaries, probes, grouped chains or SVB samples). Kept in step with
+// bfmri_create's allocation list below.
+size_t handle_device_bytes(int N, int T, int K, int P, size_t y_esz, bool mixed) {
+  const size_t ld = ((size_t)N + 31) & ~size_t(31);
+  const size_t D = std::max(K, P), Pa = std::max(P, 1);
+  const size_t maxgrid = (size_t)handle_max_grid(K, P);
+  auto r = [](size_t b) { return ((b == 0 ? 256 : b) + 255) & ~size_t(255); };
+  size_t b = r(6 * ld * 4) + 3 * r(ld * 4) + r(ld) + r(4);                 // nbr, lin, red, black, colour, ctr
+  b += r((size_t)T * N * y_esz) + r((size_t)T * K * 8);                    // Y, X
+  b += r((size_t)n_stats(K, P) * ld * 8) + r((size_t)(P + 1) * (P + 1) * K * K * 8);
+  b += r((size_t)K * ld * 8) + r(Pa * ld * 8) + r(ld * 8) + r((size_t)K * 8) + r(Pa * 8);
+  b += r((size_t)n_syy(P) * ld * 8) + 2 * r((size_t)ntri((int)D) * ld * 8);
+  b += 7 * r(D * ld * 8);                                                   // rhs, bmean, r, z, q, p0, p1
+  b += r((maxgrid * 8 + 8) * 8) + r((size_t)hyper_grid(N) * D * 8);
+  b += r(8) + r(4) + r(2 * sizeof(PcgCtrl)) + r(16);
+  b += r(3 * D * ld * 8);                                                   // edge terms
+  if (mixed) b += 2 * r((size_t)ntri((int)D) * ld * 4) + 6 * r(D * ld * 4);
+  return b;
+}
 }  // namespace bfmri
 
 struct bfmri_handle {
@@ -56,6 +86,8 @@ struct bfmri_handle {
   cudaStream_t stream = nullptr;
   std::string err = "no error";
   std::vector<void*> allocs;
+  std::vector<size_t> alloc_sizes;    // bytes of allocs[i] as requested from the allocator
+  size_t bytes_now = 0, bytes_peak = 0;
   int* d_nbr = nullptr;
   int* d_lin = nullptr;
   void* d_Y = nullptr;
@@ -170,7 +202,12 @@ void* dalloc(bfmri_handle* h, size_t bytes) {
   } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
     p = nullptr;
   }
-  if (p) h->allocs.push_back(p);
+  if (p) {
+    h->allocs.push_back(p);
+    h->alloc_sizes.push_back(bytes);
+    h->bytes_now += bytes;
+    h->bytes_peak = std::max(h->bytes_peak, h->bytes_now);
+  }
   return p;
 }
 
@@ -178,7 +215,9 @@ void dfree(bfmri_handle* h, void* p) {
   if (!p) return;
   for (size_t i = 0; i < h->allocs.size(); ++i) {
     if (h->allocs[i] == p) {
+      h->bytes_now -= h->alloc_sizes[i];
       h->allocs.erase(h->allocs.begin() + i);
+      h->alloc_sizes.erase(h->alloc_sizes.begin() + i);
       break;
     }
   }
@@ -701,6 +740,13 @@ const char* bfmri_last_error(const bfmri_handle* h) {
 
 int bfmri_num_voxels(const bfmri_handle* h) { return h ? h->N : 0; }
 
+bfmri_status bfmri_device_bytes(const bfmri_handle* h, size_t* now, size_t* peak) {
+  if (!h) return BFMRI_ERR_INVALID_ARG;
+  if (now) *now = h->bytes_now;
+  if (peak) *peak = h->bytes_peak;
+  return BFMRI_OK;
+}
+
 bfmri_status bfmri_sizes(const bfmri_handle* h, int* N, int* T, int* K, int* P) {
   if (!h) return BFMRI_ERR_INVALID_ARG;
   if (N) *N = h->N;
@@ -835,9 +881,7 @@ bfmri_status bfmri_create(const bfmri_lattice* lat, const uint8_t* mask, const d
   auto A = [&](size_t bytes) { return dalloc(h, bytes); };
   const int D = h->D;
   const int Pa = P > 0 ? P : 1;
-  int maxgrid = pcg_max_grid(K);
-  if (P > 0) maxgrid = std::max(maxgrid, pcg_max_grid(P));
-  if (maxgrid < 1) maxgrid = 1024;
+  const int maxgrid = handle_max_grid(K, P);
   h->part_rows = maxgrid;
   h->d_nbr = (int*)A(6 * ld * sizeof(int));
   h->d_lin = (int*)A(ld * sizeof(int));

@@ -110,7 +110,8 @@ bfmri_status bfmri_pcg_solve_static(int N, int D, int neighbourhood, const int* 
                                     bfmri_solve_info* info) {
   if (N < 1 || D < 1 || D > DMAX) return err(BFMRI_ERR_INVALID_ARG, "need N >= 1 and 1 <= D <= 12");
   if (neighbourhood != 4 && neighbourhood != 6) return err(BFMRI_ERR_INVALID_ARG, "neighbourhood must be 4 or 6");
-  if (ld < (size_t)N) return err(BFMRI_ERR_INVALID_ARG, "ld must be >= N");
+  if (ld < (size_t)N || ld % 32 != 0)
+    return err(BFMRI_ERR_INVALID_ARG, "ld must be >= N and a multiple of 32");
   if (!nbr || !blocks || !scale || !b || !x) return err(BFMRI_ERR_INVALID_ARG, "NULL device pointer");
   if (!(delta > 0.0) || max_iter < 1) return err(BFMRI_ERR_INVALID_ARG, "need delta > 0 and max_iter >= 1");
   const size_t need = bfmri_pcg_static_bytes(ld, D);

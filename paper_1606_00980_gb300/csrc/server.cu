@@ -22,7 +22,8 @@
 #include "../../include/bfmri.h"
 
 namespace bfmri {
-void set_global_error(const std::string& msg);  // bfmri_api.cu
+void set_global_error(const std::string& msg);                                        // bfmri_api.cu
+size_t handle_device_bytes(int N, int T, int K, int P, size_t y_esz, bool mixed);      // bfmri_api.cu
 }
 
 namespace {
@@ -37,8 +38,6 @@ struct Job {
   bfmri_result res{};
   bool done = false;
 };
-
-size_t ceil32(size_t n) { return (n + 31) & ~size_t(31); }
 
 // Stream-ordered allocation from the server's pool: neither allocation nor release
 // synchronises the device, so one slot's set-up does not stall the other slots' kernels.
@@ -151,15 +150,24 @@ struct bfmri_server {
 extern "C" {
 
 size_t bfmri_request_device_bytes(int N, int T, int K, int P, int y_dtype, int precision) {
-  const size_t ld = ceil32((size_t)N), D = std::max(K, P), Pa = std::max(P, 1);
-  const size_t nt = D * (D + 1) / 2, syy = (size_t)(P + 1) * (P + 2) / 2;
-  const size_t nstats = syy + (size_t)K * (P + 1) * (P + 1);
-  size_t b = 9 * ld * sizeof(int) + ld;                                  // neighbours, lattice index, colours
-  b += (size_t)T * N * (y_dtype == BFMRI_F64 ? 8 : 4);                   // Y (released after stats)
-  b += (nstats + K + Pa + 1 + syy + 2 * nt + 7 * D) * ld * sizeof(double);
-  if (precision == BFMRI_PREC_MIXED) b += (2 * nt + 6 * D) * ld * sizeof(float);
-  b += (size_t)1 << 20;                                                  // small buffers, padding
-  return b + b / 16;
+  if (N < 1 || T < 1 || K < 1 || P < 0) return 0;
+  // every allocation of the request's handle, Y included (released after the statistics),
+  // plus a margin for the pool's own rounding
+  const size_t b = bfmri::handle_device_bytes(N, T, K, P, y_dtype == BFMRI_F64 ? 8 : 4,
+                                               precision == BFMRI_PREC_MIXED);
+  return b + b / 32 + ((size_t)2 << 20);
+}
+
+bfmri_status bfmri_server_pool_usage(bfmri_server* s, size_t* used_high, int reset) {
+  if (!s || !s->pool) return BFMRI_ERR_INVALID_ARG;
+  uint64_t v = 0;
+  if (cudaMemPoolGetAttribute(s->pool, cudaMemPoolAttrUsedMemHigh, &v) != cudaSuccess) return BFMRI_ERR_CUDA;
+  if (used_high) *used_high = (size_t)v;
+  if (reset) {
+    uint64_t zero = 0;
+    if (cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrUsedMemHigh, &zero) != cudaSuccess) return BFMRI_ERR_CUDA;
+  }
+  return BFMRI_OK;
 }
 
 bfmri_status bfmri_server_create(size_t budget_bytes, int max_slots, int sm_budget, bfmri_server** out) {

@@ -134,3 +134,30 @@ def test_bench_shaped_mix_matches_alone_and_the_oracle():
                                    tag=philox.TAG_W)
         err = np.linalg.norm(got["W"] - W_ref) / np.linalg.norm(W_ref)
         assert err <= 1e-5, (i, err)
+
+
+def test_admission_estimate_covers_every_allocation():
+    """bfmri_request_device_bytes counts every allocation a request makes: for each subject of
+    the bench-shaped pool (FP32 Y, mixed precision) and for FP64 requests, the estimate is at
+    least the handle's own peak and the pool's high-water mark for that request run alone,
+    and not far above them (the margin is 1/32 + 2 MiB)."""
+    from paper_1606_00980_gb300 import bfmri
+    lib = bfmri.load_library()
+    pool = bench_like_pool()
+    for w in pool:
+        for prec in (bfmri.PREC_MIXED, bfmri.PREC_FP64):
+            ydt = bfmri.BFMRI_F32 if w.Y.dtype == np.float32 else bfmri.BFMRI_F64
+            est = lib.bfmri_request_device_bytes(w.N, w.T, w.K, w.P, ydt, prec)
+            m = bfmri.Model.from_workload(w, precision=prec, delta=1e-8,
+                                          precond=bfmri.PRECOND_RB_REDUCED, sm_budget=4)
+            m.precompute_stats()
+            m.gibbs_sweep(2, 0)
+            now, peak = m.device_bytes()
+            m.close()
+            assert peak <= est <= peak * 33 // 32 + (2 << 20) + 4096, (w.N, prec, peak, est)
+            with bfmri.Server(budget_bytes=8 << 30, slots=1, sm_budget=4) as s:
+                s.pool_usage(reset=True)
+                s.poll(s.submit(w, 2, first_counter=0, seed=3, precision=prec, delta=1e-8,
+                                precond=bfmri.PRECOND_RB_REDUCED))
+                high = s.pool_usage()
+            assert high <= est, (w.N, prec, high, est)

@@ -423,3 +423,19 @@ def test_lambda_conditional_matches_normalised_density(P):
         dens /= np.trapezoid(dens, lam)
         ref = stats.gamma.pdf(lam, a=shape, scale=scale[n])
         assert np.max(np.abs(dens - ref)) <= 1e-6 * ref.max()
+
+
+def test_lanczos_probe_terms_equal_dense_ones():
+    """probes.probe_terms_lanczos (sparse, mid-size) reproduces the dense eigendecomposition
+    form exact_probe_terms: per-probe v' log(C) v, the trace terms and both log dets."""
+    from oracle import probes
+    w, lat = tiny(dims=(4, 4, 3), K=3, P=1, T=30, nb=6)
+    s = random_state(w, np.random.default_rng(31))
+    Bd, _ = model.w_blocks_direct(w.Y, w.X, s["A"], s["lam"])
+    V = probes.probe_vectors(lat, 3, 5, seed=9, counter=2)
+    ldm, quad, tr, ldb = probes.exact_probe_terms(lat, Bd, s["alpha"], V)
+    ldm2, quad2, tr2, ldb2 = probes.probe_terms_lanczos(lat, Bd, s["alpha"], V)
+    assert abs(ldm2 - ldm) <= 1e-12 * abs(ldm)
+    assert abs(ldb2 - ldb) <= 1e-10 * abs(ldb)
+    assert np.max(np.abs(quad2 - quad)) <= 1e-10 * np.abs(quad).max()
+    assert np.max(np.abs(tr2 - tr)) <= 1e-10 * np.abs(tr).max()

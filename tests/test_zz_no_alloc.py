@@ -53,27 +53,30 @@ def padded(v, ld):
     return out
 
 
-def test_static_solve_matches_sample_W_twice():
+def compare_twice(w, state_seed):
+    """Hands bfmri_pcg_solve_static the system bfmri_sample_W solves for two draw counters in
+    a row and checks the solutions agree (1e-8 relative L2); neither call may take device
+    memory from PyTorch's allocator, and the second call (its kernels already loaded) may not
+    lower the device's free memory either."""
     import torch
 
     from paper_1606_00980_gb300 import bfmri
     from paper_1606_00980_gb300.bfmri import Model
 
-    w = synth.small3d(seed=21, dims=(12, 10, 7), K=5, P=2, T=50)
     m = Model.from_workload(w, delta=1e-12, seed=SEED)
     m.precompute_stats()
-    rng = np.random.default_rng(2)
+    rng = np.random.default_rng(state_seed)
     m.set_state(W=w.W_true + 0.1 * rng.standard_normal(w.W_true.shape), A=w.A_true,
                 lam=rng.uniform(0.5, 2.0, w.N), alpha=rng.uniform(0.3, 3.0, w.K),
                 beta=rng.uniform(2.0, 9.0, w.P))
     N, D = w.N, w.K
     ld = (N + 31) // 32 * 32
-    assert bfmri.load_library().bfmri_pcg_static_bytes(ld, D) <= \
-        bfmri.load_library().bfmri_pcg_static_capacity()
+    lib = bfmri.load_library()
+    assert lib.bfmri_pcg_static_bytes(ld, D) <= lib.bfmri_pcg_static_capacity()
     dev = torch.device("cuda")
     nbr = torch.from_numpy(neighbour_planes(w.mask, w.neighbourhood, ld)).to(dev)
     stream = torch.cuda.current_stream()
-    for counter in (3, 4):
+    for call, counter in enumerate((3, 4)):
         x0 = m.get_state()["W"]
         blocks, _, bpert = m.build_system(0, counter)
         alpha = m.get_state()["alpha"]
@@ -83,9 +86,15 @@ def test_static_solve_matches_sample_W_twice():
         b = torch.from_numpy(padded(bpert, ld)).to(dev)
         x = torch.from_numpy(padded(x0, ld)).to(dev)
         torch.cuda.synchronize()
+        torch_before = torch.cuda.memory_allocated()
+        free_before = torch.cuda.mem_get_info()[0]
         info = bfmri.bfmri_pcg_solve_static(N, D, w.neighbourhood, nbr.data_ptr(), ld,
                                             Bp.data_ptr(), sc.data_ptr(), b.data_ptr(),
-                                            x.data_ptr(), 1e-12, 2000, stream.cuda_stream)
+                                            x.data_ptr(), 1e-12, 3000, stream.cuda_stream)
+        torch.cuda.synchronize()
+        assert torch.cuda.memory_allocated() == torch_before
+        if call == 1:
+            assert torch.cuda.mem_get_info()[0] >= free_before
         got = x.cpu().numpy()[:, :N]
         assert info.rel_residual <= 1e-12
         err = np.linalg.norm(got - W_ref) / np.linalg.norm(W_ref)
@@ -93,10 +102,31 @@ def test_static_solve_matches_sample_W_twice():
     m.close()
 
 
+def test_static_solve_matches_sample_W_twice():
+    """About 600 voxels: the resident solver (one CTA per SM holds all of them)."""
+    compare_twice(synth.small3d(seed=21, dims=(12, 10, 7), K=5, P=2, T=50), 2)
+
+
+def test_static_solve_matches_sample_W_twice_streaming():
+    """About 65k voxels at D = 6, near the 32 MiB limit: more voxels than the resident solver
+    holds, so the streaming solver runs with its work vectors and partial-sum rows carved out
+    of the static array."""
+    w = synth.request_workload(seed=22, N_target=65000, K=6, T=40, P=1)
+    assert 152 * 384 < w.N
+    compare_twice(w, 3)
+
+
+def test_static_solve_rejects_a_leading_dimension_not_a_multiple_of_32():
+    from paper_1606_00980_gb300 import bfmri
+    with pytest.raises(bfmri.BfmriError) as ei:
+        bfmri.bfmri_pcg_solve_static(100, 3, 6, 1, 101, 1, 1, 1, 1, 1e-8, 10)
+    assert ei.value.status == -1 and "multiple of 32" in str(ei.value)
+
+
 def test_static_solve_rejects_oversized_problems():
     from paper_1606_00980_gb300 import bfmri
     lib = bfmri.load_library()
-    ld = 10_000_000
+    ld = 10_000_000 // 32 * 32
     assert lib.bfmri_pcg_static_bytes(ld, 12) > lib.bfmri_pcg_static_capacity()
     with pytest.raises(bfmri.BfmriError) as ei:
         bfmri.bfmri_pcg_solve_static(ld, 12, 6, 1, ld, 1, 1, 1, 1, 1e-8, 10)
