@@ -242,14 +242,84 @@ def cpu_threads():
         return 1
 
 
+def oracle_draw_time(w):
+    """Seconds for one exact oracle W draw of workload w: the precision B~ factored in
+    nested-dissection order (linalg.factor_nd) and the two solves of Algorithm 2 (the
+    perturbed draw and the conditional mean), from the true A and the prior means of lambda
+    and alpha."""
+    import numpy as np
+
+    from oracle import gibbs, linalg, model, philox
+    from oracle.lattice import Lattice
+    lat = Lattice(w.mask, w.neighbourhood)
+    st = gibbs.default_state(w.K, w.P, w.N)
+    Bd, bw = model.w_blocks_direct(w.Y, w.X, w.A_true, st["lam"], w.eps)
+    t = time.perf_counter()
+    B = model.precision(lat, Bd, st["alpha"])
+    pert, _, _ = model.perturbation(lat, Bd, st["alpha"], 1, 0, philox.TAG_W)
+    x, y, z = lat.coords()
+    f = linalg.factor_nd(B, np.stack([x, y, z], 1), w.K)
+    b = model.kmajor(bw)
+    f.solve(b + pert)
+    f.solve(b)
+    return time.perf_counter() - t
+
+
+ORACLE_DRAW_CASES = {"slice2d": lambda s: s.slice2d(),
+                     "replica3000": lambda s: s.request_workload(seed=5, N_target=3000, K=6, T=60, P=3)}
+
+
+def oracle_child(kind):
+    """Child process of the CPU timings (its BLAS thread count is fixed by the environment
+    the parent sets): prints one JSON object."""
+    from paper_1606_00980_gb300 import synth
+    if kind == "slab":
+        w = synth.wholebrain3d()
+        zc = w.dims[2] // 2
+        t, n_s = oracle_sweep_time(w, zc - 1, zc + 1)
+        print(json.dumps({"t": t, "n": n_s, "N": w.N, "z0": zc - 1, "z1": zc}))
+    else:
+        w = ORACLE_DRAW_CASES[kind](synth)
+        print(json.dumps({"t": oracle_draw_time(w), "n": w.N, "name": w.name}))
+
+
+def oracle_timed(kind, threads):
+    """Runs oracle_child(kind) in a fresh process with `threads` BLAS/OpenMP threads."""
+    env = dict(os.environ)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+        env[v] = str(threads)
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--oracle-child", kind],
+                       env=env, capture_output=True, text=True, timeout=600)
+    if r.returncode != 0:
+        raise RuntimeError(f"oracle timing {kind} failed: {r.stderr[-500:]}")
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
 def cpu_baseline(args, w):
-    """The oracle on this host's cores: one Gibbs sweep on two central slices of the
-    headline workload, scaled to the whole volume by the voxel ratio."""
-    zc = w.dims[2] // 2
-    t, n_s = oracle_sweep_time(w, zc - 1, zc + 1)
-    return {"value": (n_s / w.N) / t, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
-            "sample": f"one oracle Gibbs sweep on slices z={zc - 1}..{zc} ({n_s} of {w.N} voxels, "
-                      f"{t:.1f} s), scaled to the whole volume by the voxel ratio"}
+    """The oracle on this host's cores. The exact oracle is infeasible at the whole-brain size
+    (a sparse factorisation of B~ with 299,568 unknowns: SuperLU ran for 13 minutes on an
+    8-core x86 host without finishing), so the value is one oracle Gibbs sweep on two central
+    slices on one core, scaled to the whole volume by the voxel ratio: an upper bound of the
+    oracle's whole-volume throughput, since its factorisation grows faster than linearly in
+    N. Beside it, the measured per-draw cost (nested-dissection factorisation + two solves) of
+    the 2D slice workload and of a 3,000-voxel replica of the whole-brain model (K = 6,
+    P = 3, T = 60), on one core and on all cores."""
+    cores = os.cpu_count() or 1
+    slab = oracle_timed("slab", 1)
+    per_draw = {}
+    for kind in ORACLE_DRAW_CASES:
+        one = oracle_timed(kind, 1)
+        allc = oracle_timed(kind, cores)
+        per_draw[one["name"]] = {"N": one["n"], "one_core_s": one["t"], "all_cores_s": allc["t"],
+                                 "all_cores": cores}
+    return {"value": (slab["n"] / slab["N"]) / slab["t"], "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one oracle Gibbs sweep on slices z={slab['z0']}..{slab['z1']} ({slab['n']} "
+                      f"of {slab['N']} voxels, {slab['t']:.1f} s on one core), scaled to the whole "
+                      f"volume by the voxel ratio (an upper bound: the exact oracle is infeasible "
+                      f"at this size)",
+            "exact_oracle_whole_brain": "infeasible at this size (299,568 unknowns)",
+            "per_draw_exact": per_draw}
 
 
 def run_reference(args, world, rank):
@@ -970,7 +1040,11 @@ def main():
     ap.add_argument("--only-batched", action="store_true",
                     help="run only the batched-probe measurement (profiling entry point)")
     ap.add_argument("--serving-requests", type=int, default=96)
+    ap.add_argument("--oracle-child", default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
+    if args.oracle_child:
+        oracle_child(args.oracle_child)
+        return
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     world, rank, local = dist_setup(args)

@@ -75,3 +75,62 @@ def slq_quadform(matvec, z, m, f=np.log):
     T = lanczos(matvec, z, m)
     theta, S = np.linalg.eigh(T)
     return float((z @ z) * np.sum(S[0, :] ** 2 * f(theta)))
+
+
+def nested_dissection(coords, leaf=64):
+    """Geometric nested-dissection order of lattice points (recursive plane bisection): the
+    points of a box are split by the median plane across its longest extent; the two halves
+    are ordered first (recursively) and the separating plane last. With face-neighbour
+    couplings only, no point of one half couples to the other, so a Cholesky or LU factor in
+    this order fills in only within the halves and against their separators (George 1973).
+    coords: (n, 3) integer coordinates; returns a permutation of range(n)."""
+    coords = np.asarray(coords)
+    out = []
+
+    def rec(idx):
+        if len(idx) <= leaf:
+            out.extend(idx.tolist())
+            return
+        c = coords[idx]
+        ext = c.max(axis=0) - c.min(axis=0)
+        ax = int(np.argmax(ext))
+        if ext[ax] == 0:
+            out.extend(idx.tolist())
+            return
+        mid = int(np.median(c[:, ax]))
+        if mid == c[:, ax].min():
+            mid += 1
+        left, sep, right = idx[c[:, ax] < mid], idx[c[:, ax] == mid], idx[c[:, ax] > mid]
+        rec(left)
+        rec(right)
+        out.extend(sep.tolist())
+
+    rec(np.arange(len(coords)))
+    return np.array(out, dtype=np.int64)
+
+
+def factor_nd(B, coords, D):
+    """Sparse LU of B~ (k-major unknowns, D per voxel) in nested-dissection order of the
+    voxels, each voxel's D unknowns together, with diagonal pivots (B~ is SPD: its LU with
+    diagonal pivots is its Cholesky factorisation up to the diagonal scaling). Returns an
+    object with .solve(b) in the original order."""
+    N = len(coords)
+    order = nested_dissection(coords)
+    perm = (np.arange(D)[None, :] * N + order[:, None]).reshape(-1)
+    Bp = sp.csc_matrix(B)[perm][:, perm]
+    lu = spla.splu(sp.csc_matrix(Bp), permc_spec="NATURAL", diag_pivot_thresh=0.0,
+                   options=dict(SymmetricMode=True))
+
+    class _Solver:
+        def solve(self, b):
+            b = np.asarray(b, dtype=np.float64)
+            x = np.empty_like(b)
+            x[perm] = lu.solve(b[perm])
+            return x
+
+        def logdet(self):
+            return float(np.sum(np.log(np.abs(lu.U.diagonal()))))
+
+        nnz = lu.L.nnz + lu.U.nnz
+
+    return _Solver()

@@ -439,3 +439,27 @@ def test_lanczos_probe_terms_equal_dense_ones():
     assert abs(ldb2 - ldb) <= 1e-10 * abs(ldb)
     assert np.max(np.abs(quad2 - quad)) <= 1e-10 * np.abs(quad).max()
     assert np.max(np.abs(tr2 - tr)) <= 1e-10 * np.abs(tr).max()
+
+
+def test_nested_dissection_order_and_factor():
+    """linalg.nested_dissection is a permutation whose first split leaves no lattice edge
+    between the two halves (only the separator plane touches both), and factor_nd solves
+    B~ x = b like the dense inverse (6x5x4 block, K = 3) and gives its log det."""
+    w, lat = tiny(dims=(6, 5, 4), K=3, P=1, T=30, nb=6)
+    x, y, z = lat.coords()
+    C = np.stack([x, y, z], 1)
+    order = linalg.nested_dissection(C, leaf=8)
+    assert np.array_equal(np.sort(order), np.arange(w.N))
+    # first level: split across x (the longest extent) at the median plane
+    mid = int(np.median(x))
+    left, right = set(np.flatnonzero(x < mid)), set(np.flatnonzero(x > mid))
+    for i, j, _ in lat.edges():
+        assert not ((i in left and j in right) or (i in right and j in left))
+    s = random_state(w, np.random.default_rng(41))
+    Bd, bw = model.w_blocks_direct(w.Y, w.X, s["A"], s["lam"])
+    B = model.precision(lat, Bd, s["alpha"])
+    f = linalg.factor_nd(B, C, 3)
+    b = model.kmajor(bw)
+    xd = np.linalg.solve(B.toarray(), b)
+    assert np.linalg.norm(f.solve(b) - xd) <= 1e-12 * np.linalg.norm(xd)
+    assert abs(f.logdet() - np.linalg.slogdet(B.toarray())[1]) <= 1e-10 * abs(f.logdet())
