@@ -87,11 +87,10 @@ def pcg_bytes_per_voxel_iter(K, w=8):
 
 
 # DRAM bytes (read + write) of one W-solve launch on the whole-brain workload, from an ncu
-# capture of the current kernel version, or None when the kernel has changed since its last
-# capture. The last captures (pipelined split-preconditioned reduced system: 25.45 MB +
-# 0.64 MB; SSOR form: 22.99 MB + 0.63 MB: the first touch of the staged blocks, factors, b and
-# x, the iterations running from L2) predate the current grid barrier.
-NCU_TRAFFIC_W = {"reduced": None, "ssor": None}
+# capture of the current kernel version (--set full, one launch: 25.45 MB read + 0.60 MB
+# written, the first touch of the blocks, factors, b and x; the iterations run from
+# L2), or None when the kernel has changed since its last capture.
+NCU_TRAFFIC_W = {"reduced": 26.04e6, "ssor": None}
 
 
 def precond_options(args):
