@@ -465,6 +465,7 @@ def run_ours(args, world, rank, local):
     cpu = None
     if main_rank and world == 1 and not args.no_cpu_baseline:
         cpu = run_leg(errors, "cpu_baseline", cpu_baseline, args, w)
+    stats_k = run_leg(errors, "stats_kernels", run_stats_kernels, args) if (main_rank and not args.no_stats) else None
     serving = run_leg(errors, "serving", run_serving, args) if (main_rank and not args.no_serving) else None
     if main_rank:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -482,6 +483,7 @@ def run_ours(args, world, rank, local):
                 "grouped_chains": chains,
                 "preconditioners": precs,
                 "captured_sweeps": graphs, "serving": serving, "batched_probes": batched,
+                "stats_kernels": stats_k,
                 "gpu_launches": int(n_launch),
                 "kernel_ms_per_step": {k: v["ms"] / n_prof for k, v in tim_p.items() if v["launches"]},
                 "kernel_ms_per_step_note": "the same chain and sweeps rerun with every launch "
@@ -916,6 +918,67 @@ def run_batched(args):
                          "bytes_per_voxel_iter_rhs": mrhs_bytes_per_voxel_iter_rhs(w.K, S)}}
 
 
+def stats_case_serving_max(seed=77):
+    """The largest serving request's statistics shape: an ellipsoid of ~300k voxels,
+    T = 600, K = 10, P = 3, FP32 series (random values: the cost does not depend on them)."""
+    import numpy as np
+
+    from paper_1606_00980_gb300 import synth
+    rng = np.random.default_rng(seed)
+    w = synth.request_workload(seed=seed, N_target=20000, K=10, T=600, P=3)
+    a = (3.0 * 300000 / (2.0 * np.pi)) ** (1.0 / 3.0)
+    nx = ny = int(np.ceil(2 * a + 2))
+    nz = int(np.ceil(a + 2))
+    mask = synth.ellipsoid_mask(nx, ny, nz, a, a, a / 2.0)
+    N = int(mask.sum())
+    Y = (100.0 + rng.standard_normal((w.T, N))).astype(np.float32)
+    return (nx, ny, nz, 6), mask, w.X, Y, w.K, w.P
+
+
+def run_stats_kernels(args):
+    """Sufficient statistics of FP32 series (Appendix A's pre-computed lagged products): the
+    FP64 CUDA-core kernel against the tensor-core kernel (exact BF16 digit products), on the
+    whole-brain workload with its series rounded to FP32 and on the largest serving shape
+    (~300k voxels, T = 600, K = 10, P = 3). CUDA events around the statistics launch;
+    the two results are compared element by element. Tensor work: per 128 voxels and 16 time
+    steps, 36 digit-pair MMAs of 128 x N x 16 (N = 8 x (2P + 1) rounded up to 16)."""
+    import numpy as np
+
+    from paper_1606_00980_gb300 import bfmri, synth
+    from paper_1606_00980_gb300.bfmri import Model
+    wb = synth.wholebrain3d()
+    nx, ny, nz = wb.dims
+    cases = {"wholebrain3d_fp32": ((nx, ny, nz, 6), wb.mask, wb.X, wb.Y.astype(np.float32), wb.K, wb.P),
+             "serving_max_N300k_T600_K10_P3": stats_case_serving_max()}
+    out = {}
+    for name, (lat, mask, X, Y, K, P) in cases.items():
+        res, stats = {}, {}
+        for kname, kern in (("fp64_cuda_cores", bfmri.STATS_FP64), ("tensor_cores", bfmri.STATS_TENSOR)):
+            times = []
+            for rep in range(3):
+                m = Model(lat, mask, X, Y, K, P, profile=1, stats_kernel=kern)
+                m.precompute_stats()
+                times.append(m.timing()["stats"]["ms"])
+                if rep == 0:
+                    stats[kname] = m.get_stats()
+                m.close()
+            res[kname] = {"ms": float(np.median(times)), "ms_all": times}
+        N, T = Y.shape[1], Y.shape[0]
+        Tw = T - 2 * P
+        ref = stats["fp64_cuda_cores"]
+        diff = float(np.max(np.abs(stats["tensor_cores"] - ref)) / np.abs(ref).max())
+        nmma = {0: 16, 1: 32, 2: 48, 3: 64}[P] * ((K + 7) // 8)
+        mma_flops = 36.0 * 2 * 128 * nmma * 16 * np.ceil(N / 128) * np.ceil(Tw / 16)
+        t_tc = res["tensor_cores"]["ms"] / 1e3
+        out[name] = {"N": N, "T": T, "K": K, "P": P, **res,
+                     "speedup": res["fp64_cuda_cores"]["ms"] / res["tensor_cores"]["ms"],
+                     "max_rel_diff_vs_fp64_kernel": diff,
+                     "tensor_mma_tflops": mma_flops / t_tc / 1e12,
+                     "fp64_equivalent_tflops": 2.0 * K * (2 * P + 1) * Tw * N / t_tc / 1e12,
+                     "y_read_gbs": 2 * 4.0 * N * T / t_tc / 1e9}
+    return out
+
+
 def run_serving(args):
     """Serving workload: a Poisson stream of requests, each a synthetic subject (ellipsoid mask
     of 5k-300k voxels, log-uniform; K in {4,6,8,10}; T in {150,300,600}; AR(1)-AR(3)), each
@@ -1039,6 +1102,9 @@ def main():
     ap.add_argument("--only-batched", action="store_true",
                     help="run only the batched-probe measurement (profiling entry point)")
     ap.add_argument("--serving-requests", type=int, default=96)
+    ap.add_argument("--no-stats", action="store_true")
+    ap.add_argument("--only-stats", action="store_true",
+                    help="run only the statistics-kernel comparison (profiling entry point)")
     ap.add_argument("--oracle-child", default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.oracle_child:
@@ -1050,6 +1116,9 @@ def main():
     rc = 0
     if args.impl == "reference":
         run_reference(args, world, rank)
+    elif args.only_stats:
+        if rank == 0:
+            print(json.dumps(run_stats_kernels(args)), flush=True)
     elif args.only_batched:
         if rank == 0:
             print(json.dumps(run_batched(args)), flush=True)

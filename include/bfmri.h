@@ -133,7 +133,17 @@ typedef struct {
                                 x, y, z, e.g. from anisotropic voxel sizes; Algorithm 2 scales
                                 each edge's noise by sqrt(C). All > 0; default 1, 1, 1 (the
                                 UGL prior of Section 2). */
+  int stats_kernel;          /* sufficient statistics of FP32 series: BFMRI_STATS_AUTO
+                                (default: the tensor-core kernel where it applies, P <= 3
+                                and K <= 16, else FP64 CUDA cores), BFMRI_STATS_FP64 (always
+                                the FP64 CUDA-core kernel) or BFMRI_STATS_TENSOR (the
+                                tensor-core kernel, INVALID_ARG where it does not apply).
+                                FP64 series always take the FP64 kernel. */
 } bfmri_options;
+
+#define BFMRI_STATS_AUTO   0
+#define BFMRI_STATS_FP64   1
+#define BFMRI_STATS_TENSOR 2
 
 #define BFMRI_PCG_AUTO      0
 #define BFMRI_PCG_STREAMING 1
@@ -192,7 +202,13 @@ bfmri_status bfmri_sizes(const bfmri_handle* h, int* N, int* T, int* K, int* P);
  * p, q in 0..P, summed over t = P+1..T:
  *   Syy[p][q]    = sum_t y_{t-p} y_{t-q}              (p <= q stored)
  *   Sxy[p][q][k] = sum_t y_{t-p} x_{t-q,k}
- * The device copy of Y is released afterwards. Must precede every sampling call. */
+ * The device copy of Y is released afterwards. Must precede every sampling call.
+ * FP32 series (the serving input) take, where options.stats_kernel allows, the tensor-core
+ * kernel: the common-window products sum_s y_s x_{s+d,k} as an exact BF16 digit product
+ * (every FP32 value of Y that is within 2^-24 of its voxel's largest value is represented
+ * exactly; X to 48 bits relative to its column's largest value; the digit levels below
+ * 2^-48 of the leading one are dropped), the rest in FP64. Errors: TIMEOUT if a pipeline
+ * wait of that kernel gave up. */
 bfmri_status bfmri_precompute_stats(bfmri_handle* h);
 
 /* Copies the statistics to the host: out is N x S row-major with S = (P+1)(P+2)/2 + K (P+1)^2,

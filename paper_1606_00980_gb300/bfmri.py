@@ -28,6 +28,7 @@ PREC_FP64, PREC_MIXED = 0, 1
 AR_SPATIAL, AR_INDEPENDENT = 0, 1
 Y_MASKED, Y_LATTICE = 0, 1
 PCG_AUTO, PCG_STREAMING = 0, 1
+STATS_AUTO, STATS_FP64, STATS_TENSOR = 0, 1, 2
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
@@ -47,7 +48,8 @@ class bfmri_options(C.Structure):
                 ("alloc_ctx", C.c_void_p), ("barrier_timeout_s", C.c_double),
                 ("debug_skip_block", C.c_int), ("profile", C.c_int), ("pcg_variant", C.c_int),
                 ("sm_budget", C.c_int), ("ssor_omega", C.c_double),
-                ("use_graph", C.c_int), ("edge_weight", C.c_double * 3)]
+                ("use_graph", C.c_int), ("edge_weight", C.c_double * 3),
+                ("stats_kernel", C.c_int)]
 
 
 class bfmri_solve_info(C.Structure):

@@ -111,6 +111,7 @@ struct bfmri_handle {
   bool stats_ready = false;
   int part_rows = 0;
   std::vector<double> Sxx;
+  std::vector<double> X_host;   // T x K design (digits of the tensor-core statistics)
   int stride[3] = {1, 1, 1};
   int* d_red = nullptr;     // compact indices of the voxels with x + y + z even
   int* d_black = nullptr;   // and of the others (red-black SSOR phases)
@@ -728,6 +729,7 @@ void bfmri_default_options(bfmri_options* o) {
   o->cuda_stream = nullptr;
   o->barrier_timeout_s = 2.0;
   o->debug_skip_block = -1;
+  o->stats_kernel = BFMRI_STATS_AUTO;
 }
 
 const char* bfmri_last_error(const bfmri_handle* h) {
@@ -791,6 +793,9 @@ bfmri_status bfmri_create(const bfmri_lattice* lat, const uint8_t* mask, const d
   for (int d = 0; d < 3; ++d)
     if (!(o.edge_weight[d] > 0.0) || !std::isfinite(o.edge_weight[d]))
       return fail(nullptr, BFMRI_ERR_INVALID_ARG, "edge_weight must be positive and finite");
+  if (o.stats_kernel != BFMRI_STATS_AUTO && o.stats_kernel != BFMRI_STATS_FP64 &&
+      o.stats_kernel != BFMRI_STATS_TENSOR)
+    return fail(nullptr, BFMRI_ERR_INVALID_ARG, "unknown stats_kernel");
   if (o.precision == BFMRI_PREC_MIXED && !(o.inner_tol > 0.0 && o.inner_tol < 1.0))
     return fail(nullptr, BFMRI_ERR_INVALID_ARG, "inner_tol must be in (0, 1)");
   if (!all_finite(X, (size_t)T * K)) return fail(nullptr, BFMRI_ERR_INVALID_ARG, "X has non-finite values");
@@ -866,6 +871,7 @@ bfmri_status bfmri_create(const bfmri_lattice* lat, const uint8_t* mask, const d
     delete h;
     return fail(nullptr, BFMRI_ERR_INVALID_ARG, "Y has non-finite values");
   }
+  h->X_host.assign(X, X + (size_t)T * K);
   // voxel-independent lagged X products Sxx[p][q][i][j] over t = P+1..T (1-based)
   h->Sxx.assign((size_t)(P + 1) * (P + 1) * K * K, 0.0);
   for (int p = 0; p <= P; ++p)
@@ -1001,23 +1007,71 @@ bfmri_status bfmri_destroy(bfmri_handle* h) {
 bfmri_status bfmri_precompute_stats(bfmri_handle* h) {
   if (!h) return BFMRI_ERR_INVALID_ARG;
   if (!h->d_Y) return fail(h, BFMRI_ERR_STATE, "statistics already computed (Y released)");
-  StatsArgs a;
-  a.N = h->N;
-  a.T = h->T;
-  a.K = h->K;
-  a.P = h->P;
-  a.ld = h->ld;
-  a.Y = h->d_Y;
-  a.y_is_f64 = h->y_f64;
-  a.X = h->d_X;
-  a.stats = h->d_stats;
+  int I = 0;
+  const bool tc_ok = !h->y_f64 && stats_tc_supported(h->T, h->K, h->P, &I);
+  if (h->opt.stats_kernel == BFMRI_STATS_TENSOR && !tc_ok)
+    return fail(h, BFMRI_ERR_INVALID_ARG,
+                "tensor-core statistics need FP32 Y, P <= 3, K <= 16 and a design that fits shared memory");
   cudaError_t e;
-  {
-    Timed tm(h, BFMRI_T_STATS);
-    e = launch_stats(a, h->stream);
+  if (tc_ok && h->opt.stats_kernel != BFMRI_STATS_FP64) {
+    std::vector<uint16_t> dig;
+    std::vector<int> exps;
+    int Tpad = 0;
+    stats_tc_digits(h->X_host.data(), h->T, h->K, h->P, I, dig, exps, Tpad);
+    const size_t dig_bytes = (dig.size() * sizeof(uint16_t) + 255) & ~size_t(255);
+    unsigned char* buf = (unsigned char*)dalloc(h, dig_bytes + 256 + exps.size() * sizeof(int));
+    if (!buf) return fail(h, BFMRI_ERR_OOM, "device allocation failed");
+    int* d_err = reinterpret_cast<int*>(buf + dig_bytes);
+    int* d_exp = d_err + 64;
+    e = cudaMemcpyAsync(buf, dig.data(), dig.size() * sizeof(uint16_t), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_exp, exps.data(), exps.size() * sizeof(int), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_err, 0, sizeof(int), h->stream);
+    StatsTcArgs a;
+    a.N = h->N;
+    a.T = h->T;
+    a.K = h->K;
+    a.P = h->P;
+    a.ld = h->ld;
+    a.Y = static_cast<const float*>(h->d_Y);
+    a.X = h->d_X;
+    a.xdig = reinterpret_cast<const uint16_t*>(buf);
+    a.xexp = d_exp;
+    a.stats = h->d_stats;
+    a.I = I;
+    a.Tpad = Tpad;
+    a.groups = (h->K + 7) / 8;
+    a.sm_cap = h->opt.sm_budget;
+    a.err = d_err;
+    if (e == cudaSuccess) {
+      Timed tm(h, BFMRI_T_STATS);
+      e = launch_stats_tc(a, h->stream);
+    }
+    int herr = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    dfree(h, buf);
+    if (e != cudaSuccess) return cuda_fail(h, e, "stats (tensor cores)");
+    if (herr != 0)
+      return fail(h, BFMRI_ERR_TIMEOUT, "tensor-core statistics: a pipeline wait gave up (stage " +
+                                            std::to_string(herr) + ")");
+  } else {
+    StatsArgs a;
+    a.N = h->N;
+    a.T = h->T;
+    a.K = h->K;
+    a.P = h->P;
+    a.ld = h->ld;
+    a.Y = h->d_Y;
+    a.y_is_f64 = h->y_f64;
+    a.X = h->d_X;
+    a.stats = h->d_stats;
+    {
+      Timed tm(h, BFMRI_T_STATS);
+      e = launch_stats(a, h->stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "stats");
+    CU(h, cudaStreamSynchronize(h->stream));
   }
-  if (e != cudaSuccess) return cuda_fail(h, e, "stats");
-  CU(h, cudaStreamSynchronize(h->stream));
   dfree(h, h->d_Y);
   h->d_Y = nullptr;
   h->stats_ready = true;

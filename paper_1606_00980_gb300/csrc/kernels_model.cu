@@ -14,10 +14,6 @@ constexpr int STATS_THREADS = 128;
 constexpr int VOX_THREADS = 128;
 constexpr int HYPER_THREADS = 256;
 
-__device__ __forceinline__ size_t sxy_plane(int p, int q, int k, int K, int P) {
-  return (size_t)(n_syy(P) + (p * (P + 1) + q) * K + k);
-}
-
 }  // namespace
 
 // ---------------------------------------------------------------------------------------

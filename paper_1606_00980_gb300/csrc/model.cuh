@@ -2,6 +2,8 @@
 // A full conditionals with the Algorithm 2 perturbation, and the Gamma full conditionals.
 #pragma once
 
+#include <vector>
+
 #include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -22,6 +24,9 @@ __host__ __device__ inline int syy_index(int p, int q, int P) {
   return p * (P + 1) - p * (p - 1) / 2 + (q - p);
 }
 __host__ __device__ inline int n_stats(int K, int P) { return n_syy(P) + K * (P + 1) * (P + 1); }
+__host__ __device__ inline size_t sxy_plane(int p, int q, int k, int K, int P) {
+  return (size_t)(n_syy(P) + (p * (P + 1) + q) * K + k);
+}
 
 struct Geometry {
   int N;
@@ -179,6 +184,26 @@ struct StatsArgs {
   double* stats;      // [n_stats][ld]
 };
 cudaError_t launch_stats(const StatsArgs& a, cudaStream_t s);
+
+// Statistics of FP32 series on the tensor cores (exact digit products, see
+// kernels_stats_tc.cu): P <= 3, K <= 16.
+struct StatsTcArgs {
+  int N, T, K, P;
+  size_t ld;
+  const float* Y;           // T x N row-major
+  const double* X;          // T x K column-major (terms outside the common window)
+  const uint16_t* xdig;     // [ceil(K/8)][I][Tpad][8] BF16 digits of X
+  const int* xexp;          // [K] column exponents of X
+  double* stats;            // [n_stats][ld]
+  int I, Tpad, groups, sm_cap;
+  int* err;                 // nonzero: a tensor-core pipeline wait gave up
+};
+cudaError_t launch_stats_tc(const StatsTcArgs& a, cudaStream_t s);
+// whether the tensor-core statistics apply (and the number of X digits I that fits)
+bool stats_tc_supported(int T, int K, int P, int* I_out);
+void stats_tc_digits(const double* X, int T, int K, int P, int I, std::vector<uint16_t>& dig,
+                     std::vector<int>& exps, int& Tpad);
+size_t stats_tc_smem_bytes(int T, int K, int P, int I);
 
 // W system: blocks Bd_n = lambda_n X~'X~ + eps I, b_w, block-Jacobi factor of
 // Bd_n + diag(alpha) deg_n, and the perturbed right-hand side of Algorithm 2.
