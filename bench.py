@@ -846,7 +846,12 @@ def run_batched(args):
 
     from paper_1606_00980_gb300 import bfmri, synth
     from paper_1606_00980_gb300.bfmri import Model
-    w = synth.batch3d()
+    if args.batched_lattice == "96x96x60":
+        w = synth.batch3d()
+    else:   # a smaller lattice of the same shape (profiling captures)
+        nx, ny, nz = (int(v) for v in args.batched_lattice.split("x"))
+        w = synth.wholebrain3d(seed=4, K=8, dims=(nx, ny, nz),
+                               axes=(0.476 * nx, 0.476 * ny, 0.4767 * nz), T=300)
     m = Model.from_workload(w, delta=1e-5, precision=bfmri.PREC_MIXED, seed=4242, profile=1)
     m.precompute_stats()
     m.gibbs_sweep(3, 0)
@@ -948,8 +953,11 @@ def run_stats_kernels(args):
     from paper_1606_00980_gb300.bfmri import Model
     wb = synth.wholebrain3d()
     nx, ny, nz = wb.dims
-    cases = {"wholebrain3d_fp32": ((nx, ny, nz, 6), wb.mask, wb.X, wb.Y.astype(np.float32), wb.K, wb.P),
-             "serving_max_N300k_T600_K10_P3": stats_case_serving_max()}
+    cases = {}
+    if args.stats_case in ("all", "wholebrain3d"):
+        cases["wholebrain3d_fp32"] = ((nx, ny, nz, 6), wb.mask, wb.X, wb.Y.astype(np.float32), wb.K, wb.P)
+    if args.stats_case in ("all", "serving_max"):
+        cases["serving_max_N300k_T600_K10_P3"] = stats_case_serving_max()
     out = {}
     for name, (lat, mask, X, Y, K, P) in cases.items():
         res, stats = {}, {}
@@ -1088,6 +1096,8 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--probes", type=int, default=64)
+    ap.add_argument("--batched-lattice", default="96x96x60",
+                    help="lattice of the batched-probe workload (e.g. 64x64x40 for a capture)")
     ap.add_argument("--no-svb", action="store_true")
     ap.add_argument("--no-chains", action="store_true")
     ap.add_argument("--no-precond", action="store_true")
@@ -1103,6 +1113,7 @@ def main():
                     help="run only the batched-probe measurement (profiling entry point)")
     ap.add_argument("--serving-requests", type=int, default=96)
     ap.add_argument("--no-stats", action="store_true")
+    ap.add_argument("--stats-case", default="all", choices=["all", "wholebrain3d", "serving_max"])
     ap.add_argument("--only-stats", action="store_true",
                     help="run only the statistics-kernel comparison (profiling entry point)")
     ap.add_argument("--oracle-child", default=None, help=argparse.SUPPRESS)

@@ -56,6 +56,23 @@ __device__ __forceinline__ void named_sync_converters() { asm volatile("bar.sync
 
 __device__ __forceinline__ uint32_t bf16_of_int(float d) { return __float_as_uint(d) >> 16; }
 
+// Knuth's TwoSum: a + b = s + e exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bp = s - a;
+  e = (a - (s - bp)) + (b - bp);
+}
+
+// (s, c) += a * b with the product split exactly (p + pe, by a fused multiply-add) and the
+// pair renormalised after every term: s + c carries the sum to about 2^-48 of its size.
+__device__ __forceinline__ void ff_add_prod(float a, float b, float& s, float& c) {
+  const float p = a * b;
+  const float pe = fmaf(a, b, -p);
+  float t, e;
+  two_sum(s, p, t, e);
+  two_sum(t, c + (e + pe), s, c);
+}
+
 __host__ __device__ inline size_t align1024(size_t b) { return (b + 1023) & ~size_t(1023); }
 
 }  // namespace
@@ -151,8 +168,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_stats_tc(StatsTcArgs a) {
       float m = 0.f;
       const int mid = P + Tw / 2;
       const int s_lo = h == 0 ? P : mid, s_hi = h == 0 ? mid : T - P;
-      if (valid)
-        for (int s = s_lo; s < s_hi; ++s) m = fmaxf(m, fabsf(__ldg(a.Y + (size_t)s * N + n)));
+      if (valid) {
+        int s = s_lo;
+        for (; s + 8 <= s_hi; s += 8) {
+          float v[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) v[i] = __ldg(a.Y + (size_t)(s + i) * N + n);
+#pragma unroll
+          for (int i = 0; i < 8; ++i) m = fmaxf(m, fabsf(v[i]));
+        }
+        for (; s < s_hi; ++s) m = fmaxf(m, fabsf(__ldg(a.Y + (size_t)s * N + n)));
+      }
       c->ymax[h][row] = m;
       named_sync_converters();
       const float mm = fmaxf(c->ymax[0][row], c->ymax[1][row]);
@@ -234,13 +260,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_stats_tc(StatsTcArgs a) {
               *p1 = make_uint4(w[j][4], w[j][5], w[j][6], w[j][7]);
             }
             if (kg == 0 && valid) {
+              // y'y products of the chunk: exact FP32 product splits summed as float pairs,
+              // then one FP64 addition per lag and chunk
 #pragma unroll
-              for (int t = 0; t < TC_KS; ++t) {
-                if (s0 + t < T - P) {
-                  const double ys = (double)y[t];
+              for (int e = 0; e <= PMAX; ++e) {
+                if (e <= P) {
+                  float hi = 0.f, lo = 0.f;
 #pragma unroll
-                  for (int e = 0; e <= PMAX; ++e)
-                    if (e <= P) syy[e] += ys * (double)y[t + e];
+                  for (int t = 0; t < TC_KS; ++t)
+                    if (s0 + t < T - P) ff_add_prod(y[t], y[t + e], hi, lo);
+                  syy[e] += (double)hi + (double)lo;
                 }
               }
             }
@@ -251,22 +280,26 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_stats_tc(StatsTcArgs a) {
           if (!tc::mbar_wait(&c->accf, wins & 1)) atomicExch(&c->err, 5);
           tc::fence_after_sync();
           const uint32_t lane_base = tbase + ((uint32_t)(32 * (warp & 3)) << 16);
+          // Each level's sum is an integer below 2^24; levels 0..3 and 4..7 combine exactly
+          // in 64-bit integers (sum_l L_l 64^(3-l) < 2^43), and only the two results are
+          // converted: value = 2^-18 hi + 2^-42 lo in units of level 0.
 #pragma unroll
           for (int cc = 0; cc < HALF / 8; ++cc) {
-            double part[8];
+            uint32_t v[TC_LEVELS][8];
 #pragma unroll
-            for (int e = 0; e < 8; ++e) part[e] = 0.0;
+            for (int l = 0; l < TC_LEVELS; ++l)
+              tc::tmem_ld8(lane_base + (uint32_t)(l * NMMA + h * HALF + cc * 8), v[l]);
+            tc::tmem_wait_ld();
 #pragma unroll
-            for (int l = 0; l < TC_LEVELS; ++l) {
-              uint32_t v[8];
-              tc::tmem_ld8(lane_base + (uint32_t)(l * NMMA + h * HALF + cc * 8), v);
-              tc::tmem_wait_ld();
-              const double sc = ldexp(1.0, -6 * l);
+            for (int e = 0; e < 8; ++e) {
+              long long hi = 0, lo = 0;
 #pragma unroll
-              for (int e = 0; e < 8; ++e) part[e] += (double)__uint_as_float(v[e]) * sc;
+              for (int l = 0; l < 4; ++l) {
+                hi = hi * 64 + (long long)__float2int_rz(__uint_as_float(v[l][e]));
+                lo = lo * 64 + (long long)__float2int_rz(__uint_as_float(v[l + 4][e]));
+              }
+              acc[cc * 8 + e] += __ll2double_rn(hi) * 0x1p-18 + __ll2double_rn(lo) * 0x1p-42;
             }
-#pragma unroll
-            for (int e = 0; e < 8; ++e) acc[cc * 8 + e] += part[e];
           }
           tc::fence_before_sync();
           tc::mbar_arrive(&c->acce);

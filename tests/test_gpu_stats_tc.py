@@ -84,7 +84,8 @@ def test_tensor_core_stats_wide_dynamic_range():
 def test_tensor_core_stats_reject_unsupported_shapes():
     from paper_1606_00980_gb300 import bfmri
     from paper_1606_00980_gb300.bfmri import Model
-    w = synth.small3d(seed=6, dims=(6, 5, 4), K=3, P=4, T=40)
+    w = synth.make_workload("p4", (6, 5, 4), np.ones((4, 5, 6), np.uint8), T=40, K=3, P=4,
+                            neighbourhood=6, seed=6, ar_uniform=(0.02, 0.1))
     nx, ny, nz = w.dims
     m = Model((nx, ny, nz, w.neighbourhood), w.mask, w.X, w.Y.astype(np.float32), w.K, w.P,
               stats_kernel=bfmri.STATS_TENSOR)
