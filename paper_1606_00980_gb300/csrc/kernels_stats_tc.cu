@@ -50,6 +50,8 @@ struct TcCtl {
   int err;
   float ymax[2][TC_TILE];
   double syy[TC_TILE][PMAX + 1];
+  double xbl[2 * PMAX][16];   // X rows 0 .. 2P-1 (terms before the common window)
+  double xbr[2 * PMAX][16];   // X rows T-2P .. T-1 (terms after it)
 };
 
 __device__ __forceinline__ void named_sync_converters() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
@@ -128,6 +130,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_stats_tc(StatsTcArgs a) {
   constexpr uint32_t TCOLS = NMMA * TC_LEVELS <= 128 ? 128u : (NMMA * TC_LEVELS <= 256 ? 256u : 512u);
   constexpr uint32_t IDESC = tc::idesc_bf16_f32(TC_TILE, NMMA, false, true);
   constexpr int HALF = NMMA / 2;          // accumulator columns per converter group
+  constexpr int PC = NMMA / 16 - 1;       // the AR order this instance serves (a.P == PC)
   if (tid == 0) {
     for (int b = 0; b < 2; ++b) {
       tc::mbar_init(&c->full[b], 128);
@@ -153,6 +156,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_stats_tc(StatsTcArgs a) {
     }
   }
   if (!tc::mbar_wait(&c->xload, 0)) atomicExch(&c->err, 1);
+  for (int i = tid; i < 2 * P * K; i += blockDim.x) {
+    const int t = i / K, k = i % K;
+    c->xbl[t][k] = __ldg(a.X + t + (size_t)T * k);
+    c->xbr[t][k] = __ldg(a.X + (T - 2 * P + t) + (size_t)T * k);
+  }
+  __syncthreads();
 
   const bool conv = warp < 8;
   const int h = warp >> 2;                  // converter group: 0 or 1
@@ -184,6 +193,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_stats_tc(StatsTcArgs a) {
       const float mm = fmaxf(c->ymax[0][row], c->ymax[1][row]);
       Fv = mm > 0.f ? ilogbf(mm) + 1 : 0;
     }
+    // the series values the terms outside the common window use: y_0 .. y_{2P-1} and
+    // y_{T-P} .. y_{T-1}
+    float ybl[2 * PMAX], ybr[PMAX];
+#pragma unroll
+    for (int t = 0; t < 2 * PMAX; ++t) ybl[t] = (valid && t < 2 * PC) ? __ldg(a.Y + (size_t)t * N + n) : 0.f;
+#pragma unroll
+    for (int i = 0; i < PMAX; ++i) ybr[i] = (valid && i < PC) ? __ldg(a.Y + (size_t)(T - PC + i) * N + n) : 0.f;
     // y * 2^-Fv by one multiplication while 2^-Fv is a normal number, else by ldexpf
     const bool plain_scale = Fv >= -125 && Fv <= 125;
     const float scale = plain_scale ? __int_as_float((127 - Fv) << 23) : 1.f;
@@ -191,9 +207,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_stats_tc(StatsTcArgs a) {
 #pragma unroll
     for (int e = 0; e <= PMAX; ++e) syy[e] = 0.0;
     for (int kg = 0; kg < NG; ++kg) {
-      double acc[HALF];
-#pragma unroll
-      for (int q = 0; q < HALF; ++q) acc[q] = 0.0;
       for (int w0 = 0; w0 < Tw; w0 += TC_WIN) {
         const int span = Tw - w0 < TC_WIN ? Tw - w0 : TC_WIN;
         const int nsteps = (span + TC_KS - 1) / TC_KS;
@@ -283,6 +296,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_stats_tc(StatsTcArgs a) {
           // Each level's sum is an integer below 2^24; levels 0..3 and 4..7 combine exactly
           // in 64-bit integers (sum_l L_l 64^(3-l) < 2^43), and only the two results are
           // converted: value = 2^-18 hi + 2^-42 lo in units of level 0.
+          // Windows before the last keep their partial sums in the output plane of the pair
+          // (p0, p0 - d), p0 = max(d, 0), which the last window reads back and overwrites.
+          const bool first_win = w0 == 0, last_win = w0 + TC_WIN >= Tw;
+          const size_t ld = a.ld;
 #pragma unroll
           for (int cc = 0; cc < HALF / 8; ++cc) {
             uint32_t v[TC_LEVELS][8];
@@ -290,15 +307,44 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_stats_tc(StatsTcArgs a) {
             for (int l = 0; l < TC_LEVELS; ++l)
               tc::tmem_ld8(lane_base + (uint32_t)(l * NMMA + h * HALF + cc * 8), v[l]);
             tc::tmem_wait_ld();
+            const int gsh = (h * HALF + cc * 8) >> 3, d = gsh - PC;
+            if (!valid || gsh > 2 * PC) continue;
+            const int p0 = d > 0 ? d : 0;
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
+              const int k = 8 * kg + e;
+              if (k >= K) continue;
               long long hi = 0, lo = 0;
 #pragma unroll
               for (int l = 0; l < 4; ++l) {
                 hi = hi * 64 + (long long)__float2int_rz(__uint_as_float(v[l][e]));
                 lo = lo * 64 + (long long)__float2int_rz(__uint_as_float(v[l + 4][e]));
               }
-              acc[cc * 8 + e] += __ll2double_rn(hi) * 0x1p-18 + __ll2double_rn(lo) * 0x1p-42;
+              double acc = __ll2double_rn(hi) * 0x1p-18 + __ll2double_rn(lo) * 0x1p-42;
+              double* tmp = a.stats + sxy_plane(p0, p0 - d, k, K, PC) * ld + n;
+              if (!first_win) acc += *tmp;
+              if (!last_win) {
+                *tmp = acc;
+                continue;
+              }
+              // Sxy of the pairs (p, q = p - d): the window sum scaled back, plus the terms
+              // t = P-p .. P-1 before the window (added as p grows) and t = T-P .. T-1-p after it
+              const double C = ldexp(acc, a.xexp[k] + Fv - 12);
+              double after[PC + 1];
+#pragma unroll
+              for (int pp = 0; pp <= PC; ++pp) {
+                double w = 0.0;
+#pragma unroll
+                for (int i = 0; i <= PC - 1 - pp; ++i) w += (double)ybr[i] * c->xbr[PC + i + d][k];
+                after[pp] = w;
+              }
+              double before = 0.0;
+#pragma unroll
+              for (int pp = 0; pp <= PC; ++pp) {
+                if (pp >= 1) before += (double)ybl[PC - pp] * c->xbl[PC - pp + d][k];
+                if (pp >= d && pp - d <= PC)
+                  a.stats[sxy_plane(pp, pp - d, k, K, PC) * ld + n] = C + before + after[pp];
+              }
             }
           }
           tc::fence_before_sync();
@@ -306,26 +352,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_stats_tc(StatsTcArgs a) {
         }
         gstep += nsteps;
         wins += 1;
-      }
-      // Sxy of this k-group: C scaled back, plus the terms outside the common window
-      if (valid) {
-        const size_t ld = a.ld;
-#pragma unroll
-        for (int cl = 0; cl < HALF; ++cl) {
-          const int col = h * HALF + cl, gsh = col >> 3, k = 8 * kg + (col & 7);
-          if (gsh > 2 * P || k >= K) continue;
-          const int d = gsh - P;
-          const double C = ldexp(acc[cl], a.xexp[k] + Fv - 12);
-          const double* xk = a.X + (size_t)T * k;
-          for (int p = d > 0 ? d : 0; p <= P && p - d <= P; ++p) {
-            const int q = p - d;
-            double v = C;
-            for (int t = P - p; t <= P - 1; ++t) v += (double)__ldg(a.Y + (size_t)t * N + n) * __ldg(xk + t + d);
-            for (int t = T - P; t <= T - 1 - p; ++t)
-              v += (double)__ldg(a.Y + (size_t)t * N + n) * __ldg(xk + t + d);
-            a.stats[sxy_plane(p, q, k, K, P) * ld + n] = v;
-          }
-        }
       }
     }
     // Syy: the two groups' window sums, plus the boundary terms
@@ -337,15 +363,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_stats_tc(StatsTcArgs a) {
       named_sync_converters();
       if (h == 0 && valid) {
         const size_t ld = a.ld;
-        auto yv = [&](int t) { return (double)__ldg(a.Y + (size_t)t * N + n); };
-        for (int e = 0; e <= P; ++e) {
+#pragma unroll
+        for (int e = 0; e <= PC; ++e) {
           const double cyy = syy[e] + c->syy[row][e];
-          for (int q = e; q <= P; ++q) {
-            const int p = q - e;
+#pragma unroll
+          for (int q = e; q <= PC; ++q) {
             double v = cyy;
-            for (int t = P - q; t <= P - 1; ++t) v += yv(t) * yv(t + e);
-            for (int t = T - P; t <= T - 1 - q; ++t) v += yv(t) * yv(t + e);
-            a.stats[(size_t)syy_index(p, q, P) * ld + n] = v;
+#pragma unroll
+            for (int j = 1; j <= q; ++j) v += (double)ybl[PC - j] * (double)ybl[PC - j + e];   // t = P - j
+#pragma unroll
+            for (int i = 0; i <= PC - 1 - q; ++i) v += (double)ybr[i] * (double)ybr[i + e];    // t = T - P + i
+            a.stats[(size_t)syy_index(q - e, q, PC) * ld + n] = v;
           }
         }
       }
