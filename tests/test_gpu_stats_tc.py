@@ -44,7 +44,7 @@ CASES = [  # (K, P, T, dims)
     (8, 3, 150, (12, 10, 6)),
     (9, 1, 60, (8, 7, 5)),
     (10, 3, 600, (10, 9, 6)),
-    (12, 2, 700, (9, 7, 5)),
+    (12, 2, 560, (9, 7, 5)),
     (5, 3, 20, (7, 6, 4)),
 ]
 
