@@ -112,13 +112,7 @@ struct bfmri_handle {
   int part_rows = 0;
   std::vector<double> Sxx;
   std::vector<double> X_host;   // T x K design (digits of the tensor-core statistics)
-  std::vector<int> nbr_host;    // [6][ld] neighbour planes (neighbour-CTA lists)
-  std::vector<unsigned char> colour_host;
-  // neighbour-CTA lists of the resident reduced solver for nbf_grid CTAs of nbf_per voxels:
-  // [grid] counts, [grid][NBF_MAX] lists, [grid] flags (device); nbf_ok: every CTA fits
-  int nbf_per = -1, nbf_grid = 0, nbf_cap = 0;
-  bool nbf_ok = false;
-  int* d_nbf = nullptr;
+
   int stride[3] = {1, 1, 1};
   int* d_red = nullptr;     // compact indices of the voxels with x + y + z even
   int* d_black = nullptr;   // and of the others (red-black SSOR phases)
@@ -382,57 +376,6 @@ bfmri_status end_call(bfmri_handle* h, PcgCtrl* ctrl_out /* [2] or null */, int*
   return BFMRI_OK;
 }
 
-// Neighbour-CTA lists for the resident reduced FP64 solver's launch shape (grid CTAs of
-// `per` consecutive voxels): CTA b lists every other CTA owning a red voxel next to one of
-// b's black voxels. Built once per shape; false when the solver does not apply or a CTA has
-// more than NBF_MAX such neighbours (the solver then keeps its grid barrier).
-bool ensure_nbf(bfmri_handle* h, int D, bool allow_build = true) {
-  if (h->opt.precond != BFMRI_PRECOND_RB_REDUCED || h->opt.precision != BFMRI_PREC_FP64 ||
-      h->opt.pcg_variant != BFMRI_PCG_AUTO || D > 6)
-    return false;
-  int dev = 0, nsm = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return false;
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  if (h->opt.sm_budget > 0 && h->opt.sm_budget < nsm) nsm = h->opt.sm_budget;
-  int grid = 0, per = 0;
-  if (!resident_rb_shape(h->N, nsm, &grid, &per)) return false;
-  if (h->nbf_per == per && h->nbf_grid == grid) return h->nbf_ok;
-  if (!allow_build) return false;   // no allocation or copy inside a stream capture
-  h->nbf_per = per;
-  h->nbf_grid = grid;
-  h->nbf_ok = false;
-  std::vector<int> host((size_t)grid * (NBF_MAX + 1), 0);
-  for (int b = 0; b < grid; ++b) {
-    int* cnt = &host[b];
-    int* list = &host[(size_t)grid + (size_t)b * NBF_MAX];
-    const int n1 = std::min(h->N, (b + 1) * per);
-    for (int n = b * per; n < n1; ++n) {
-      if (h->colour_host[n] == 0) continue;   // black voxels only
-      for (int d = 0; d < h->ndir; ++d) {
-        const int m = h->nbr_host[(size_t)d * h->ld + n];
-        if (m < 0) continue;
-        const int o = m / per;
-        if (o == b || std::find(list, list + *cnt, o) != list + *cnt) continue;
-        if (*cnt == NBF_MAX) return false;
-        list[(*cnt)++] = o;
-      }
-    }
-  }
-  if (h->nbf_cap < grid) {
-    if (h->d_nbf) dfree(h, h->d_nbf);
-    h->d_nbf = (int*)dalloc(h, (size_t)grid * (NBF_MAX + 2) * sizeof(int));
-    h->nbf_cap = h->d_nbf ? grid : 0;
-    if (!h->d_nbf) return false;
-  }
-  if (cudaMemcpyAsync(h->d_nbf, host.data(), host.size() * sizeof(int), cudaMemcpyHostToDevice,
-                      h->stream) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  h->nbf_ok = true;
-  return true;
-}
-
 bfmri_status run_pcg(bfmri_handle* h, int D, const double* scale, double* x, int which) {
   PcgArgs a;
   memset(&a, 0, sizeof(a));
@@ -483,12 +426,6 @@ bfmri_status run_pcg(bfmri_handle* h, int D, const double* scale, double* x, int
   a.max_iter = h->opt.max_iter;
   a.skip_block = h->opt.debug_skip_block;
   a.max_grid = h->part_rows;
-  if (ensure_nbf(h, D, !h->capturing)) {
-    a.nbf_cnt = h->d_nbf;
-    a.nbf_list = h->d_nbf + h->nbf_grid;
-    a.nbf_flag = reinterpret_cast<unsigned int*>(h->d_nbf + (size_t)h->nbf_grid * (NBF_MAX + 1));
-    a.nbf_per = h->nbf_per;
-  }
   h->opt.debug_skip_block = -1;  // the hook fires once
   int grid = 0;
   Timed tm(h, which == 0 ? BFMRI_T_PCG_W : BFMRI_T_PCG_A, true, which);
@@ -1024,8 +961,6 @@ bfmri_status bfmri_create(const bfmri_lattice* lat, const uint8_t* mask, const d
   }
   h->n_red = (int)red.size();
   h->n_black = (int)black.size();
-  h->nbr_host = nbr;
-  h->colour_host = colour;
   if (!e) e = cudaMemcpyAsync(h->d_colour, colour.data(), ld, cudaMemcpyHostToDevice, s);
   if (!e && !red.empty()) e = cudaMemcpyAsync(h->d_red, red.data(), red.size() * sizeof(int), cudaMemcpyHostToDevice, s);
   if (!e && !black.empty()) e = cudaMemcpyAsync(h->d_black, black.data(), black.size() * sizeof(int), cudaMemcpyHostToDevice, s);
@@ -1268,7 +1203,6 @@ bfmri_status bfmri_gibbs_sweep(bfmri_handle* h, int n_sweeps, uint64_t first_cou
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaSuccess;
     if (!h->capture_stream) e = cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking);
-    ensure_nbf(h, h->K);   // the solvers' neighbour-CTA lists exist before the capture
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);   // begin_call's resets are done
     if (e == cudaSuccess) e = cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeRelaxed);
     bfmri_status cs = BFMRI_OK;

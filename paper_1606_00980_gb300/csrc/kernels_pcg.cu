@@ -1335,26 +1335,6 @@ __global__ void __launch_bounds__(RB_MAX_THREADS, 1) k_pcg_rbp(PcgArgs a) {
     if (a.skip_block == (int)blockIdx.x) return false;
     return grid_sync(a.bar, &sh.flag);
   };
-  // After the red phase of iteration `gen`: publish this CTA's generation and wait for the
-  // CTAs whose red voxels neighbour this CTA's black voxels (they are also the only readers
-  // of this CTA's black values), instead of a grid barrier.
-  unsigned int red_gen = 0u;
-  auto nbr_sync = [&]() -> bool {
-    ++red_gen;
-    __syncthreads();
-    if (t == 0) {
-      sh.flag = 0;
-      st_release(a.nbf_flag + blockIdx.x, red_gen);
-    }
-    __syncthreads();
-    const int cnt = a.nbf_cnt[blockIdx.x];
-    if (t < cnt) {
-      const unsigned int* f = a.nbf_flag + a.nbf_list[(size_t)blockIdx.x * NBF_MAX + t];
-      if (!wait_reach(a.bar, f, red_gen)) sh.flag = 1;
-    }
-    __syncthreads();
-    return sh.flag == 0;
-  };
   auto publish = [&](const double* v) {
 #pragma unroll
     for (int k = 0; k < D; ++k) U[(size_t)k * ld + n] = v[k];
@@ -1548,12 +1528,7 @@ __global__ void __launch_bounds__(RB_MAX_THREADS, 1) k_pcg_rbp(PcgArgs a) {
       code = sh.code;
       __syncthreads();
     }
-    // the red phase's y is visible (to the black voxels next to it); all partials read
-    if (a.nbf_list != nullptr) {
-      if (!nbr_sync()) return;
-    } else if (!bar()) {
-      return;
-    }
+    if (!bar()) return;                 // the red phase's y is visible; all partials read
     if (status != 0 || bb == 0.0) break;
     if (code == 7) { status = 7; break; }
     if (code == 3) { status = 3; break; }
@@ -2326,24 +2301,6 @@ int capped_sms(int cap) {
   return (cap > 0 && cap < n) ? cap : n;
 }
 
-}  // namespace
-
-bool resident_rb_shape(int N, int nsm, int* grid_out, int* per_out) {
-  int grid = nsm;
-  if ((N + 63) / 64 < grid) grid = (N + 63) / 64;
-  if (grid < 1) grid = 1;
-  const int per = (N + grid - 1) / grid;
-  grid = (N + per - 1) / per;
-  int threads = ((per + 31) / 32) * 32;
-  if (threads < 64) threads = 64;
-  if (threads > RB_MAX_THREADS) return false;
-  *grid_out = grid;
-  *per_out = per;
-  return true;
-}
-
-namespace {
-
 template <int D>
 cudaError_t launch_resident(const PcgArgs& a, cudaStream_t stream, int* grid_out, bool* launched) {
   *launched = false;
@@ -2383,14 +2340,8 @@ cudaError_t launch_resident(const PcgArgs& a, cudaStream_t stream, int* grid_out
   *launched = true;
   PcgArgs b = a;
   b.res_per = per;
-  const bool nbf = kPipe && a.reduced && !a.mixed && a.nbf_list != nullptr && a.nbf_per == per;
-  if (!nbf) b.nbf_list = nullptr;
   cudaError_t er = reset_grid_barrier(b.bar, stream);
   if (er != cudaSuccess) return er;
-  if (nbf) {
-    er = cudaMemsetAsync(b.nbf_flag, 0, (size_t)grid * sizeof(unsigned int), stream);
-    if (er != cudaSuccess) return er;
-  }
   void* args[] = {(void*)&b};
   return cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(threads), args, shm, stream);
 }

@@ -76,21 +76,7 @@ struct PcgArgs {
   // variants run that SSOR form instead (ssor = 1, omega = 1 must be set alongside)
   int reduced;
   double cw[3];          // edge weights of the x, y, z directions (1, 1, 1: UGL prior)
-  // Neighbour-CTA synchronisation of the FP64 resident pipelined reduced solver: after its
-  // red phase, CTA b waits only for the CTAs that own red voxels next to its black voxels
-  // (nbf_cnt[b] entries of nbf_list[b * NBF_MAX ..]) instead of the whole grid. Built by the
-  // host for the launch shape of nbf_per voxels per CTA; null: grid barrier.
-  const int* nbf_cnt;
-  const int* nbf_list;
-  unsigned int* nbf_flag;   // [grid] per-CTA red-phase generation, zeroed before each launch
-  int nbf_per;
 };
-
-constexpr int NBF_MAX = 16;
-
-// Launch shape (grid, voxels per CTA) of the resident reduced FP64 solver for N voxels on at
-// most nsm SMs; false when that solver does not apply.
-bool resident_rb_shape(int N, int nsm, int* grid, int* per);
 
 // Launches the cooperative persistent PCG kernel for dimension D (1..12) on `stream`.
 // grid_out (may be null) receives the grid size used.
