@@ -856,7 +856,10 @@ def run_batched(args):
     m.precompute_stats()
     m.gibbs_sweep(3, 0)
     S = args.probes
-    m.logdet_probe(0, S, 3000, counter=1)            # warm-up (workspace allocation)
+    # warm-up (workspace allocation; the autotuner times the right-hand-side tiles 1, 2, 4
+    # on this first call of the shape and keeps the fastest)
+    m.logdet_probe(0, S, 3000, counter=1)
+    tile, tile_ms = m.probe_tuning()
     m.reset_timing()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -911,13 +914,21 @@ def run_batched(args):
     bytes_ = iters * w.N * mrhs_bytes_per_voxel_iter_rhs(w.K, S)
     hbm_peak, hbm_src, _ = peaks()
     gbs = bytes_ / solve_s / 1e9
+    # the minimum of the two-pass fused PCG form (11 vector passes; this solver's
+    # Chronopoulos-Gear form moves 13)
+    bytes11 = iters * w.N * (4 * 11 * w.K + 4 * 2 * (w.K * (w.K + 1) // 2) / S)
+    gbs11 = bytes11 / solve_s / 1e9
     return {"workload": f"batch3d_96x96x60_ellipsoid_N{w.N}_K{w.K}_T{w.T}_AR3",
             "probes": S, "logdet": res["logdet"], "stderr": res["stderr"],
             "probe_iterations_mean": float(res["iterations"].mean()),
             "probe_iterations_max": int(res["iterations"].max()),
             "solve_ms": solve_s * 1e3, "call_ms": wall * 1e3, "svb_iteration": svb,
+            "autotune": {"rhs_tile": tile, "candidate_ms": {"1": tile_ms[0], "2": tile_ms[1],
+                                                            "4": tile_ms[2]}},
+            "hbm_11_vector_passes": {"achieved_gbs": gbs11, "frac": gbs11 / hbm_peak},
             "chains": None if args.no_svb else run_batched_chains(args, w),
-            "roofline": {"kernel": f"k_mrhs<{w.K}, float>", "bound": "hbm", "achieved": gbs,
+            "roofline": {"kernel": (f"k_mrhs_tile<{w.K}, {tile}>" if tile > 1 else f"k_mrhs<{w.K}, float>"),
+                         "bound": "hbm", "achieved": gbs,
                          "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
                          "traffic": None, "peak_source": f"{hbm_src} (MEASURED_PEAKS.json)",
                          "bytes_per_voxel_iter_rhs": mrhs_bytes_per_voxel_iter_rhs(w.K, S)}}

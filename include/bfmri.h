@@ -139,6 +139,11 @@ typedef struct {
                                 the FP64 CUDA-core kernel) or BFMRI_STATS_TENSOR (the
                                 tensor-core kernel, INVALID_ARG where it does not apply).
                                 FP64 series always take the FP64 kernel. */
+  int mrhs_tile;             /* FP32 log-det / trace probe solves: right-hand sides per thread
+                                (1, 2 or 4, interleaved per voxel and component); 0 (default):
+                                the autotuner times 1, 2 and 4 on the first probe call of each
+                                shape (K or P, probe count, N, sm_budget) and keeps the fastest
+                                for the process (bfmri_probe_tuning reports it) */
 } bfmri_options;
 
 #define BFMRI_STATS_AUTO   0
@@ -195,6 +200,9 @@ int bfmri_num_voxels(const bfmri_handle* h);
 /* Device bytes the handle holds now and at most so far (its own allocations, each as
  * requested from the allocator: rounded up to 256 bytes). */
 bfmri_status bfmri_device_bytes(const bfmri_handle* h, size_t* now, size_t* peak);
+/* Right-hand-side tile of the handle's last probe solve, and the autotuner's solve times in
+ * ms for tiles 1, 2 and 4 (ms[3], -1 where not timed: a cached or fixed choice). */
+bfmri_status bfmri_probe_tuning(const bfmri_handle* h, int* tile, double* ms);
 bfmri_status bfmri_sizes(const bfmri_handle* h, int* N, int* T, int* K, int* P);
 
 /* Sufficient statistics (Appendix A, Eq. log-like: Y enters only through lagged

@@ -49,7 +49,7 @@ class bfmri_options(C.Structure):
                 ("debug_skip_block", C.c_int), ("profile", C.c_int), ("pcg_variant", C.c_int),
                 ("sm_budget", C.c_int), ("ssor_omega", C.c_double),
                 ("use_graph", C.c_int), ("edge_weight", C.c_double * 3),
-                ("stats_kernel", C.c_int)]
+                ("stats_kernel", C.c_int), ("mrhs_tile", C.c_int)]
 
 
 class bfmri_solve_info(C.Structure):
@@ -147,6 +147,7 @@ SIGNATURES = [
     ("bfmri_server_stats", C.c_int, [C.c_void_p, _P(C.c_size_t), _P(C.c_int), _P(C.c_size_t)]),
     ("bfmri_server_pool_usage", C.c_int, [C.c_void_p, _P(C.c_size_t), C.c_int]),
     ("bfmri_device_bytes", C.c_int, [_h, _P(C.c_size_t), _P(C.c_size_t)]),
+    ("bfmri_probe_tuning", C.c_int, [_h, _P(C.c_int), _dp]),
     ("bfmri_server_destroy", C.c_int, [C.c_void_p]),
     ("bfmri_pcg_static_capacity", C.c_size_t, []),
     ("bfmri_pcg_static_bytes", C.c_size_t, [C.c_size_t, C.c_int]),
@@ -425,6 +426,13 @@ class Model:
 
     def _c(self, st):
         _check(st, self.handle)
+
+    def probe_tuning(self):
+        """(tile of the last probe solve, autotuner times in ms for tiles 1, 2, 4 or -1)."""
+        t = C.c_int()
+        ms = np.empty(3)
+        self._c(self.lib.bfmri_probe_tuning(self.handle, C.byref(t), _ptr(ms)))
+        return t.value, ms.tolist()
 
     def device_bytes(self):
         """(bytes held now, peak so far) of the handle's own device allocations."""

@@ -9,6 +9,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/bfmri.h"
@@ -112,6 +113,8 @@ struct bfmri_handle {
   int part_rows = 0;
   std::vector<double> Sxx;
   std::vector<double> X_host;   // T x K design (digits of the tensor-core statistics)
+  int probe_tile = 1;           // right-hand-side tile of the last probe solve
+  double probe_tile_ms[3] = {-1.0, -1.0, -1.0};   // autotuner's solve times of tiles 1, 2, 4
 
   int stride[3] = {1, 1, 1};
   int* d_red = nullptr;     // compact indices of the voxels with x + y + z even
@@ -601,8 +604,9 @@ bfmri_status ensure_mrhs(bfmri_handle* h, int D, int S, int hist_len) {
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  // rows of the partial buffer: one per (RHS, chunk) unit, never more than max(warps, S)
-  const int units = std::max(std::max(nsm, 1) * 64, S);
+  // rows of the partial buffer: one per (RHS, chunk) unit, never more than max(warps, S);
+  // right-hand-side tiles of up to 4 multiply the rows per warp by the tile
+  const int units = std::max(std::max(nsm, 1) * 64 * 4, S);
   const size_t out_len = std::max((size_t)h->ld, (size_t)((h->N + 127) / 128 + 1) * S * D);
   if (S <= h->mr_S && D <= h->mr_D && hist_len <= h->mr_hist_len && units <= h->mr_units &&
       out_len <= h->mr_out_len)
@@ -731,6 +735,7 @@ void bfmri_default_options(bfmri_options* o) {
   o->barrier_timeout_s = 2.0;
   o->debug_skip_block = -1;
   o->stats_kernel = BFMRI_STATS_AUTO;
+  o->mrhs_tile = 0;
 }
 
 const char* bfmri_last_error(const bfmri_handle* h) {
@@ -742,6 +747,14 @@ const char* bfmri_last_error(const bfmri_handle* h) {
 }
 
 int bfmri_num_voxels(const bfmri_handle* h) { return h ? h->N : 0; }
+
+bfmri_status bfmri_probe_tuning(const bfmri_handle* h, int* tile, double* ms) {
+  if (!h) return BFMRI_ERR_INVALID_ARG;
+  if (tile) *tile = h->probe_tile;
+  if (ms)
+    for (int c = 0; c < 3; ++c) ms[c] = h->probe_tile_ms[c];
+  return BFMRI_OK;
+}
 
 bfmri_status bfmri_device_bytes(const bfmri_handle* h, size_t* now, size_t* peak) {
   if (!h) return BFMRI_ERR_INVALID_ARG;
@@ -1689,6 +1702,20 @@ bfmri_status bfmri_reset_timing(bfmri_handle* h) {
   return BFMRI_OK;
 }
 
+namespace {
+
+// Autotuner of the FP32 probe solves: the right-hand-side tile (1, 2 or 4 interleaved
+// right-hand sides per thread) is chosen per shape (D, S, N, SM budget) by timing each
+// candidate's solve once, on the first probe call of that shape, and kept for the process.
+struct TileChoice {
+  int tile;
+  double ms[3];
+};
+std::mutex g_tile_mu;
+std::map<std::tuple<int, int, int, int>, TileChoice> g_tile_cache;
+
+}  // namespace
+
 bfmri_status bfmri_logdet_probe(bfmri_handle* h, int which, int n_probes, int lanczos_steps,
                                 uint64_t counter, double* logdet, double* std_err,
                                 double* traces, double* per_probe, int* iterations) {
@@ -1733,14 +1760,69 @@ bfmri_status bfmri_logdet_probe(bfmri_handle* h, int which, int n_probes, int la
   pa.x = h->mr_x;
   pa.rng = rng_of(h, counter, TAG_PROBE);
   for (int d = 0; d < 3; ++d) pa.cw[d] = h->opt.edge_weight[d];
-  cudaError_t e = launch_probe(D, pa, 0, nullptr, h->stream);
-  if (e != cudaSuccess) return cuda_fail(h, e, "probe rhs");
+  pa.tile = 1;
   MrhsArgs m = mrhs_args(h, D, n_probes, scale, lanczos_steps, true);
   if (f32) {
     m.f32 = 1;
     m.blocks = h->d_blocks32;
     m.mfac = pre ? h->d_mfac32 : nullptr;
   }
+  // right-hand-side tile: fixed by options.mrhs_tile, or chosen by the autotuner (FP32)
+  int tile = 1;
+  double tile_ms[3] = {-1.0, -1.0, -1.0};
+  if (f32 && h->opt.mrhs_tile != 1) {
+    if (h->opt.mrhs_tile == 2 || h->opt.mrhs_tile == 4) {
+      tile = n_probes % h->opt.mrhs_tile == 0 ? h->opt.mrhs_tile : 1;
+    } else {
+      const auto key = std::make_tuple(D, n_probes, h->N, h->opt.sm_budget);
+      bool have = false;
+      {
+        std::lock_guard<std::mutex> lk(g_tile_mu);
+        auto it = g_tile_cache.find(key);
+        if (it != g_tile_cache.end()) {
+          tile = it->second.tile;
+          for (int c = 0; c < 3; ++c) tile_ms[c] = it->second.ms[c];
+          have = true;
+        }
+      }
+      if (!have) {
+        const int cand[3] = {1, 2, 4};
+        double best = 0.0;
+        cudaEvent_t e0 = take_event(h), e1 = take_event(h);
+        for (int c = 0; c < 3; ++c) {
+          if (n_probes % cand[c] != 0) continue;
+          pa.tile = m.tile = cand[c];
+          CU(h, launch_probe(D, pa, 0, nullptr, h->stream));
+          CU(h, cudaEventRecord(e0, h->stream));
+          int units = 0;
+          CU(h, launch_mrhs(D, m, h->stream, &units));
+          CU(h, cudaEventRecord(e1, h->stream));
+          CU(h, cudaEventSynchronize(e1));
+          float ms = 0.f;
+          CU(h, cudaEventElapsedTime(&ms, e0, e1));
+          tile_ms[c] = ms;
+          if (tile_ms[c] >= 0.0 && (best == 0.0 || ms < best)) {
+            best = ms;
+            tile = cand[c];
+          }
+        }
+        h->event_pool.push_back(e0);
+        h->event_pool.push_back(e1);
+        RET(end_call(h, nullptr, nullptr));   // errors of the trial solves surface here
+        RET(begin_call(h));
+        std::lock_guard<std::mutex> lk(g_tile_mu);
+        TileChoice tc;
+        tc.tile = tile;
+        for (int c = 0; c < 3; ++c) tc.ms[c] = tile_ms[c];
+        g_tile_cache[key] = tc;
+      }
+    }
+  }
+  h->probe_tile = tile;
+  for (int c = 0; c < 3; ++c) h->probe_tile_ms[c] = tile_ms[c];
+  pa.tile = m.tile = tile;
+  cudaError_t e = launch_probe(D, pa, 0, nullptr, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "probe rhs");
   {
     Timed tm(h, BFMRI_T_OTHER, true, 0);
     int units = 0;

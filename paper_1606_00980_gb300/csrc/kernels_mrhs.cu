@@ -891,12 +891,397 @@ __global__ void __launch_bounds__(MRHS_THREADS, (sizeof(T) == 4 || D <= 4) ? 2 :
   }
 }
 
+// ---------------------------------------------------------------------------------------
+// Right-hand-side tiles (FP32 storage, one shared matrix, block-Jacobi or no preconditioner:
+// the probe solves). The S right-hand sides are stored in groups of R interleaved per voxel
+// and component, element (i, k, n) at [(i / R) D ld R + (k ld + n) R + i % R], so that one
+// thread updates R right-hand sides of one voxel with R-wide loads and stores, and every
+// block, factor and neighbour-index load serves R right-hand sides. Units are (group of R,
+// voxel chunk); each unit writes the partial row (chunk * S + r) of each of its right-hand
+// sides r, so the reducing barrier and the scalar logic are those of k_mrhs.
+// ---------------------------------------------------------------------------------------
+template <int R>
+struct TileVec;
+template <>
+struct TileVec<2> {
+  __device__ __forceinline__ static void ld(const float* p, float* v) {
+    const float2 t = *reinterpret_cast<const float2*>(p);
+    v[0] = t.x;
+    v[1] = t.y;
+  }
+  __device__ __forceinline__ static void st(float* p, const float* v) {
+    *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
+  }
+};
+template <>
+struct TileVec<4> {
+  __device__ __forceinline__ static void ld(const float* p, float* v) {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    v[0] = t.x;
+    v[1] = t.y;
+    v[2] = t.z;
+    v[3] = t.w;
+  }
+  __device__ __forceinline__ static void st(float* p, const float* v) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  }
+};
+
+template <int D, int R>
+__global__ void __launch_bounds__(MRHS_THREADS, 2) k_mrhs_tile(MrhsArgs a) {
+  __shared__ int sh_int[4];
+  __shared__ int sh_flag;
+  using V = TileVec<R>;
+  const size_t ld = a.ld;
+  const int S = a.S, G = S / R;
+  Units U;
+  U.S = S;
+  U.nw = (gridDim.x * blockDim.x) >> 5;
+  U.gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  U.lane = threadIdx.x & 31;
+  U.chunks = U.nw / G > 0 ? U.nw / G : 1;
+  U.units = G * U.chunks;
+  {
+    const int cs = (a.N + U.chunks - 1) / U.chunks;
+    U.csize = ((cs + 31) / 32) * 32;
+  }
+  grid_barrier_start(a.bar);
+  const size_t gs = (size_t)D * ld * R;    // floats per group
+  const float* B = static_cast<const float*>(a.blocks);
+  const float* M = static_cast<const float*>(a.mfac);
+  float sc[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) sc[k] = (float)__ldg(a.scale + k);
+  float cw6[6];
+#pragma unroll
+  for (int d = 0; d < 6; ++d) cw6[d] = (float)a.cw[d >> 1];
+  auto at = [&](void* base, int g, int k, int n) {
+    return static_cast<float*>(base) + (size_t)g * gs + ((size_t)k * ld + n) * R;
+  };
+  auto cat = [&](const void* base, int g, int k, int n) {
+    return static_cast<const float*>(base) + (size_t)g * gs + ((size_t)k * ld + n) * R;
+  };
+  // y = B~ v for the R right-hand sides of group g at voxel n (v: this voxel's values)
+  auto apply = [&](int g, int n, float (*v)[R], const void* Vb, float (*y)[R]) {
+    int nb[6];
+#pragma unroll
+    for (int d = 0; d < 6; ++d) nb[d] = d < a.ndir ? __ldg(a.nbr + (size_t)d * ld + n) : -1;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      float acc[R];
+#pragma unroll
+      for (int q = 0; q < R; ++q) acc[q] = 0.f;
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        const float bij = __ldg(B + (size_t)(i >= j ? tri(i, j) : tri(j, i)) * ld + n);
+#pragma unroll
+        for (int q = 0; q < R; ++q) acc[q] += bij * v[j][q];
+      }
+#pragma unroll
+      for (int q = 0; q < R; ++q) y[i][q] = acc[q];
+    }
+    // + scale .* sum_d c_d (v - v_m) over the in-mask neighbours
+#pragma unroll
+    for (int d = 0; d < 6; ++d) {
+      if (nb[d] >= 0) {
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          float vm[R];
+          V::ld(cat(Vb, g, k, nb[d]), vm);
+#pragma unroll
+          for (int q = 0; q < R; ++q) y[k][q] += sc[k] * cw6[d] * (v[k][q] - vm[q]);
+        }
+      }
+    }
+  };
+  auto precond = [&](int n, float (*r)[R], float (*z)[R]) {
+    if (M == nullptr) {
+#pragma unroll
+      for (int k = 0; k < D; ++k)
+#pragma unroll
+        for (int q = 0; q < R; ++q) z[k][q] = r[k][q];
+      return;
+    }
+    float L[ntri(D)];
+#pragma unroll
+    for (int e = 0; e < ntri(D); ++e) L[e] = __ldg(M + (size_t)e * ld + n);
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      float rq[D], zq[D];
+#pragma unroll
+      for (int k = 0; k < D; ++k) rq[k] = r[k][q];
+      chol_solve_invdiag<D>(L, rq, zq);
+#pragma unroll
+      for (int k = 0; k < D; ++k) z[k][q] = zq[k];
+    }
+  };
+  auto write_rows = [&](int g, int c, KSum<float> (*acc)[4], unsigned cols) {
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      double v4[4] = {acc[q][0].value(), acc[q][1].value(), acc[q][2].value(), acc[q][3].value()};
+      const double v = warp_reduce4(v4);
+      const int u = c * S + g * R + q;
+      if ((U.lane & 7) == 0 && ((cols >> (U.lane >> 3)) & 1u)) a.part[(size_t)u * 4 + (U.lane >> 3)] = v;
+    }
+  };
+  auto state_of = [&](int r) { return __ldcg(&a.st[r].active); };
+  // (re)start: r = b - B~ x, u = M^-1 r, p = s = 0 for the selected right-hand sides, then
+  // w = B~ u and the partials (r'u, w'u, r'r, b'b)
+  auto restart = [&](bool first) -> bool {
+    for (int u = U.gw; u < U.units; u += U.nw) {
+      const int g = u % G, c = u / G;
+      bool sel[R], any = false;
+#pragma unroll
+      for (int q = 0; q < R; ++q) {
+        sel[q] = first || state_of(g * R + q) == 2;
+        any |= sel[q];
+      }
+      if (!any) continue;
+      const int n1 = min(a.N, (c + 1) * U.csize);
+      for (int n = c * U.csize + U.lane; n < n1; n += 32) {
+        float xn[D][R], ax[D][R], rn[D][R], zn[D][R], bn[D][R], zero[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) zero[q] = 0.f;
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          V::ld(cat(a.x, g, k, n), xn[k]);
+          V::ld(cat(a.b, g, k, n), bn[k]);
+        }
+        apply(g, n, xn, a.x, ax);
+#pragma unroll
+        for (int k = 0; k < D; ++k)
+#pragma unroll
+          for (int q = 0; q < R; ++q) rn[k][q] = bn[k][q] - ax[k][q];
+        precond(n, rn, zn);
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          float ro[R], uo[R], po[R], so[R];
+          if (!first) {
+            V::ld(cat(a.r, g, k, n), ro);
+            V::ld(cat(a.u, g, k, n), uo);
+            V::ld(cat(a.p, g, k, n), po);
+            V::ld(cat(a.s, g, k, n), so);
+          }
+#pragma unroll
+          for (int q = 0; q < R; ++q) {
+            ro[q] = sel[q] ? rn[k][q] : ro[q];
+            uo[q] = sel[q] ? zn[k][q] : uo[q];
+            po[q] = sel[q] ? 0.f : po[q];
+            so[q] = sel[q] ? 0.f : so[q];
+          }
+          V::st(at(a.r, g, k, n), ro);
+          V::st(at(a.u, g, k, n), uo);
+          V::st(at(a.p, g, k, n), po);
+          V::st(at(a.s, g, k, n), so);
+        }
+        (void)zero;
+      }
+    }
+    if (!grid_sync(a.bar, &sh_flag)) return false;
+    for (int u = U.gw; u < U.units; u += U.nw) {
+      const int g = u % G, c = u / G;
+      bool sel[R], any = false;
+#pragma unroll
+      for (int q = 0; q < R; ++q) {
+        sel[q] = first || state_of(g * R + q) == 2;
+        any |= sel[q];
+      }
+      KSum<float> acc[R][4];
+      if (any) {
+        const int n1 = min(a.N, (c + 1) * U.csize);
+        for (int n = c * U.csize + U.lane; n < n1; n += 32) {
+          float un[D][R], wn[D][R], rn[D][R], bn[D][R];
+#pragma unroll
+          for (int k = 0; k < D; ++k) {
+            V::ld(cat(a.u, g, k, n), un[k]);
+            V::ld(cat(a.r, g, k, n), rn[k]);
+            V::ld(cat(a.b, g, k, n), bn[k]);
+          }
+          apply(g, n, un, a.u, wn);
+#pragma unroll
+          for (int k = 0; k < D; ++k) {
+            float wo[R];
+            if (!first) V::ld(cat(a.w, g, k, n), wo);
+#pragma unroll
+            for (int q = 0; q < R; ++q) wo[q] = sel[q] ? wn[k][q] : wo[q];
+            V::st(at(a.w, g, k, n), wo);
+          }
+#pragma unroll
+          for (int q = 0; q < R; ++q) {
+            if (!sel[q]) continue;
+            float gg = 0.f, dl = 0.f, rr2 = 0.f, b2 = 0.f;
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+              gg += rn[k][q] * un[k][q];
+              dl += wn[k][q] * un[k][q];
+              rr2 += rn[k][q] * rn[k][q];
+              b2 += bn[k][q] * bn[k][q];
+            }
+            acc[q][0].add(gg);
+            acc[q][1].add(dl);
+            acc[q][2].add(rr2);
+            acc[q][3].add(b2);
+          }
+        }
+      }
+      write_rows(g, c, acc, 0xFu);
+    }
+    return true;
+  };
+
+  int any_active = 0, any_pending = 0;
+  if (!restart(true)) return;
+  if (!mrhs_reduce(a, U, 0, true, sh_int, &any_active, &any_pending)) return;
+  while (any_active || any_pending) {
+    if (any_active) {
+      // local update (p, s, x, r, u) of the active right-hand sides; partials r'u and r'r
+      for (int u = U.gw; u < U.units; u += U.nw) {
+        const int g = u % G, c = u / G;
+        bool act[R], any = false;
+        float al[R], be[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+          act[q] = state_of(g * R + q) == 1;
+          any |= act[q];
+          al[q] = act[q] ? (float)__ldcg(&a.st[g * R + q].alpha) : 0.f;
+          be[q] = act[q] ? (float)__ldcg(&a.st[g * R + q].beta) : 0.f;
+        }
+        KSum<float> acc[R][4];
+        if (any) {
+          const int n1 = min(a.N, (c + 1) * U.csize);
+          for (int n = c * U.csize + U.lane; n < n1; n += 32) {
+            float rn[D][R], zn[D][R];
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+              float uk[R], pk[R], wk[R], sk[R], xk[R];
+              V::ld(cat(a.u, g, k, n), uk);
+              V::ld(cat(a.p, g, k, n), pk);
+              V::ld(cat(a.w, g, k, n), wk);
+              V::ld(cat(a.s, g, k, n), sk);
+              V::ld(cat(a.x, g, k, n), xk);
+              V::ld(cat(a.r, g, k, n), rn[k]);
+#pragma unroll
+              for (int q = 0; q < R; ++q) {
+                if (act[q]) {
+                  pk[q] = uk[q] + be[q] * pk[q];
+                  sk[q] = wk[q] + be[q] * sk[q];
+                  xk[q] += al[q] * pk[q];
+                  rn[k][q] -= al[q] * sk[q];
+                }
+              }
+              V::st(at(a.p, g, k, n), pk);
+              V::st(at(a.s, g, k, n), sk);
+              V::st(at(a.x, g, k, n), xk);
+            }
+            // z = M^-1 r; for a right-hand side that does not move, r is unchanged and the
+            // same arithmetic reproduces its u exactly
+            precond(n, rn, zn);
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+              V::st(at(a.r, g, k, n), rn[k]);
+              V::st(at(a.u, g, k, n), zn[k]);
+            }
+#pragma unroll
+            for (int q = 0; q < R; ++q) {
+              if (!act[q]) continue;
+              float gg = 0.f, rr2 = 0.f;
+#pragma unroll
+              for (int k = 0; k < D; ++k) {
+                gg += rn[k][q] * zn[k][q];
+                rr2 += rn[k][q] * rn[k][q];
+              }
+              acc[q][0].add(gg);
+              acc[q][2].add(rr2);
+            }
+          }
+        }
+        write_rows(g, c, acc, 0x5u);
+      }
+      if (!grid_sync(a.bar, &sh_flag)) return;
+      // w = B~ u and w'u (column 1)
+      for (int u = U.gw; u < U.units; u += U.nw) {
+        const int g = u % G, c = u / G;
+        bool act[R], any = false;
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+          act[q] = state_of(g * R + q) == 1;
+          any |= act[q];
+        }
+        KSum<float> acc[R][4];
+        if (any) {
+          const int n1 = min(a.N, (c + 1) * U.csize);
+          for (int n = c * U.csize + U.lane; n < n1; n += 32) {
+            float un[D][R], wn[D][R];
+#pragma unroll
+            for (int k = 0; k < D; ++k) V::ld(cat(a.u, g, k, n), un[k]);
+            apply(g, n, un, a.u, wn);
+            float wo[D][R];
+            bool all = true;
+#pragma unroll
+            for (int q = 0; q < R; ++q) all &= act[q];
+            if (!all) {
+#pragma unroll
+              for (int k = 0; k < D; ++k) V::ld(cat(a.w, g, k, n), wo[k]);
+            }
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+#pragma unroll
+              for (int q = 0; q < R; ++q) wo[k][q] = act[q] ? wn[k][q] : wo[k][q];
+              V::st(at(a.w, g, k, n), wo[k]);
+            }
+#pragma unroll
+            for (int q = 0; q < R; ++q) {
+              if (!act[q]) continue;
+              float dl = 0.f;
+#pragma unroll
+              for (int k = 0; k < D; ++k) dl += wn[k][q] * un[k][q];
+              acc[q][1].add(dl);
+            }
+          }
+        }
+        write_rows(g, c, acc, 0x2u);
+      }
+      if (!mrhs_reduce(a, U, 1, false, sh_int, &any_active, &any_pending)) return;
+    } else {
+      if (!restart(false)) return;
+      if (!mrhs_reduce(a, U, 0, false, sh_int, &any_active, &any_pending)) return;
+    }
+  }
+}
+
+template <int D, int R>
+static cudaError_t launch_tile(const MrhsArgs& a, int nsm, cudaStream_t stream, int* units_out) {
+  const void* kern = (const void*)k_mrhs_tile<D, R>;
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, MRHS_THREADS, 0);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  const int G = a.S / R;
+  const long long want_warps = (long long)G * ((a.N + 31) / 32);
+  long long grid = (want_warps * 32 + MRHS_THREADS - 1) / MRHS_THREADS;
+  if (grid > (long long)nsm * per_sm) grid = (long long)nsm * per_sm;
+  if (grid < 1) grid = 1;
+  const int nw = (int)grid * (MRHS_THREADS / 32);
+  const int chunks = nw / G > 0 ? nw / G : 1;
+  if (units_out) *units_out = G * chunks;
+  e = reset_grid_barrier(a.bar, stream);
+  if (e != cudaSuccess) return e;
+  void* args[] = {(void*)&a};
+  return cudaLaunchCooperativeKernel(kern, dim3((unsigned)grid), dim3(MRHS_THREADS), args, 0, stream);
+}
+
 template <int D>
 static cudaError_t launch_d(const MrhsArgs& a, cudaStream_t stream, int* units_out) {
   int dev = 0, nsm = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   if (a.sm_cap > 0 && a.sm_cap < nsm) nsm = a.sm_cap;
+  if (a.tile > 1) {
+    if (!a.f32 || a.ssor || a.reduced || a.tab != nullptr || a.S % a.tile != 0) return cudaErrorInvalidValue;
+    if (a.tile == 2) return launch_tile<D, 2>(a, nsm, stream, units_out);
+    if (a.tile == 4) return launch_tile<D, 4>(a, nsm, stream, units_out);
+    return cudaErrorInvalidValue;
+  }
   const void* kern = a.f32 ? (const void*)k_mrhs<D, float> : (const void*)k_mrhs<D, double>;
   const size_t shm = a.f32 ? mrhs_stage_bytes<D, float>() : mrhs_stage_bytes<D, double>();
   if (shm > 0) {
@@ -967,6 +1352,13 @@ int mrhs_max_units(int D, int S) {
 // ---------------------------------------------------------------------------------------
 namespace bfmri {
 
+// element (i, k, n) of a probe vector in the layout of ProbeArgs.tile
+__device__ __forceinline__ size_t probe_idx(const ProbeArgs& a, int D, int i, int k, int n) {
+  if (a.tile > 1)
+    return (size_t)(i / a.tile) * ((size_t)D * a.ld * a.tile) + ((size_t)k * a.ld + n) * a.tile + (i % a.tile);
+  return (size_t)i * a.vs + (size_t)k * a.ld + n;
+}
+
 // b_i = L v_i (v_i Rademacher, site lattice-linear * 4 + 3, stream i), x_i = 0.
 template <int D, typename T>
 __global__ void k_probe_rhs(ProbeArgs a) {
@@ -990,8 +1382,8 @@ __global__ void k_probe_rhs(ProbeArgs a) {
   T* x = static_cast<T*>(a.x);
 #pragma unroll
   for (int k = 0; k < D; ++k) {
-    b[(size_t)i * a.vs + (size_t)k * a.ld + n] = (T)bv[k];
-    x[(size_t)i * a.vs + (size_t)k * a.ld + n] = T(0);
+    b[probe_idx(a, D, i, k, n)] = (T)bv[k];
+    x[probe_idx(a, D, i, k, n)] = T(0);
   }
 }
 
@@ -1038,11 +1430,11 @@ __global__ void k_probe_traces(ProbeArgs a, double* part) {
 #pragma unroll
       for (int k = 0; k < D; ++k) t[k] = v[k];
     }
-    const T* y = static_cast<const T*>(a.x) + (size_t)i * a.vs;
+    const T* y = static_cast<const T*>(a.x);
     double yn[D], sum[D];
 #pragma unroll
     for (int k = 0; k < D; ++k) {
-      yn[k] = (double)y[(size_t)k * a.ld + n];
+      yn[k] = (double)y[probe_idx(a, D, i, k, n)];
       sum[k] = 0.0;
     }
     double deg = 0.0;
@@ -1052,7 +1444,7 @@ __global__ void k_probe_traces(ProbeArgs a, double* part) {
         const double cd = a.cw[d >> 1];
         deg += cd;
 #pragma unroll
-        for (int k = 0; k < D; ++k) sum[k] += cd * (double)y[(size_t)k * a.ld + m];
+        for (int k = 0; k < D; ++k) sum[k] += cd * (double)y[probe_idx(a, D, i, k, m)];
       }
     }
 #pragma unroll

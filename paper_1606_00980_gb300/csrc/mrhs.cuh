@@ -90,6 +90,11 @@ struct MrhsArgs {
   // lists and at most one (RHS, chunk) unit per warp (S <= warps of the grid)
   int reduced;
   double cw[3];          // edge weights of the x, y, z directions (1, 1, 1: UGL prior)
+  // right-hand-side tile (FP32, one shared matrix, block-Jacobi or none, no SSOR, no
+  // table): 2 or 4 = the vectors hold groups of `tile` right-hand sides interleaved per voxel
+  // and component (element (i, k, n) at (i / tile) D ld tile + (k ld + n) tile + i % tile)
+  // and k_mrhs_tile runs; 0 or 1 = the [S][D][ld] layout and k_mrhs
+  int tile;
 };
 
 // Probe set-up and post-processing (log-determinant and trace probes).
@@ -108,6 +113,7 @@ struct ProbeArgs {
   void* x;              // [S][D][ld]
   Rng rng;              // tag in c3's top byte; the probe index is the stream
   double cw[3];         // edge weights of the x, y, z directions
+  int tile;             // layout of b and x: 2 or 4 = right-hand-side tiles (MrhsArgs.tile)
 };
 // what: 0 = probe right-hand sides b_i = L v_i and x_i = 0; 1 = per-voxel log det of the
 // preconditioner into out[N]; 2 = trace partials into out[grid.x][S][D] (grid.x = ceil(N/128)).

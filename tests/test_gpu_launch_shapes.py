@@ -123,8 +123,8 @@ def test_gibbs_sweep_at_full_cta_shape(case6):
     m.close()
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_64_probes_at_k8_fill_the_grid(precision):
+@pytest.mark.parametrize("precision,tile", [("fp64", 1), ("fp32", 1), ("fp32", 2), ("fp32", 4)])
+def test_64_probes_at_k8_fill_the_grid(precision, tile):
     """64 Rademacher probes of the K = 8 W system in one multi-RHS launch (the batched
     workload's probe count and K; 1,328 voxels give every one of the 64 right-hand sides 38
     voxel chunks over the full grid, as 250k voxels do). Eight sampled probes are checked
@@ -137,7 +137,7 @@ def test_64_probes_at_k8_fill_the_grid(precision):
     s = dict(W=w.W_true + 0.1 * rng.standard_normal(w.W_true.shape), A=w.A_true,
              lam=rng.uniform(0.5, 2.0, w.N), alpha=rng.uniform(0.3, 3.0, w.K),
              beta=rng.uniform(2.0, 9.0, w.P))
-    extra = dict(precision=bfmri.PREC_MIXED, delta=1e-5) if precision == "fp32" else {}
+    extra = dict(precision=bfmri.PREC_MIXED, delta=1e-5, mrhs_tile=tile) if precision == "fp32" else {}
     m = make(w, s, precond=bfmri.PRECOND_BLOCK_JACOBI, **extra)
     n_probes = 64
     res = m.logdet_probe(0, n_probes, 3000, counter=6)

@@ -83,3 +83,52 @@ def test_logdet_probe_matches_oracle(name, which, variant):
     assert np.all(res["iterations"] > 0)
     assert abs(res["logdet"] - ldb) <= 5 * max(res["stderr"], 1e-9) + 1e-6 * abs(ldb)
     m.close()
+
+
+@pytest.mark.parametrize("tile", [2, 4])
+@pytest.mark.parametrize("which", [0, 1])
+def test_tiled_fp32_probes_match_oracle(tile, which):
+    """FP32 probe solves with 2 or 4 right-hand sides interleaved per thread (the tile the
+    autotuner chooses among): per-probe quadrature within 1e-4 of the exact value, traces
+    within 1e-3, and the tile reported back."""
+    from paper_1606_00980_gb300 import bfmri
+    w = CASES["small3d_K3_P2"]()
+    lat = Lattice(w.mask, w.neighbourhood)
+    rng = np.random.default_rng(4)
+    s = dict(W=w.W_true + 0.1 * rng.standard_normal(w.W_true.shape), A=w.A_true,
+             lam=rng.uniform(0.5, 2.0, w.N), alpha=rng.uniform(0.3, 3.0, w.K),
+             beta=rng.uniform(2.0, 9.0, w.P))
+    m = make(w, s, precond=bfmri.PRECOND_BLOCK_JACOBI, precision=bfmri.PREC_MIXED, delta=1e-5,
+             mrhs_tile=tile)
+    n_probes = 12
+    res = m.logdet_probe(which, n_probes, 2000, counter=6)
+    assert m.probe_tuning()[0] == tile
+    m.close()
+    D = w.K if which == 0 else w.P
+    if which == 0:
+        Bd, _ = model.w_blocks_direct(w.Y, w.X, s["A"], s["lam"], w.eps)
+        scale = s["alpha"]
+    else:
+        Bd, _ = model.a_blocks_direct(w.Y, w.X, s["W"], s["lam"], w.P)
+        scale = s["beta"]
+    V = probes.probe_vectors(lat, D, n_probes, SEED, 6)
+    ldm, quad, tr, ldb = probes.exact_probe_terms(lat, Bd, scale, V)
+    assert np.max(np.abs(res["per_probe"] - quad) / np.abs(quad)) <= 1e-4
+    assert np.allclose(res["traces"], tr.mean(axis=0), rtol=1e-3, atol=1e-3 * np.abs(tr).mean())
+
+
+def test_autotuner_times_every_tile_and_keeps_the_fastest():
+    from paper_1606_00980_gb300 import bfmri
+    w = synth.small3d(seed=33, dims=(9, 8, 7), K=4, P=1, T=40)
+    rng = np.random.default_rng(5)
+    s = dict(W=w.W_true, A=w.A_true, lam=rng.uniform(0.5, 2.0, w.N),
+             alpha=rng.uniform(0.3, 3.0, w.K), beta=rng.uniform(2.0, 9.0, w.P))
+    m = make(w, s, precond=bfmri.PRECOND_BLOCK_JACOBI, precision=bfmri.PREC_MIXED, delta=1e-5)
+    r1 = m.logdet_probe(0, 8, 2000, counter=3)
+    tile, ms = m.probe_tuning()
+    assert all(t > 0 for t in ms) and tile in (1, 2, 4)
+    assert ms[(1, 2, 4).index(tile)] == min(ms)
+    r2 = m.logdet_probe(0, 8, 2000, counter=3)          # cached: same tile, no new timing
+    assert m.probe_tuning()[0] == tile
+    assert np.array_equal(r1["per_probe"], r2["per_probe"])
+    m.close()
