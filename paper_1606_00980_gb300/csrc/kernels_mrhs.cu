@@ -927,8 +927,10 @@ struct TileVec<4> {
   }
 };
 
+// Two CTAs per SM for tiles of 2 (128 registers); one for tiles of 4, whose R-wide
+// vectors of D components need the whole register file of the CTA.
 template <int D, int R>
-__global__ void __launch_bounds__(MRHS_THREADS, 2) k_mrhs_tile(MrhsArgs a) {
+__global__ void __launch_bounds__(MRHS_THREADS, R >= 4 ? 1 : 2) k_mrhs_tile(MrhsArgs a) {
   __shared__ int sh_int[4];
   __shared__ int sh_flag;
   using V = TileVec<R>;
