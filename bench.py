@@ -466,7 +466,7 @@ def run_ours(args, world, rank, local):
     if main_rank and world == 1 and not args.no_cpu_baseline:
         cpu = run_leg(errors, "cpu_baseline", cpu_baseline, args, w)
     stats_k = run_leg(errors, "stats_kernels", run_stats_kernels, args) if (main_rank and not args.no_stats) else None
-    serving = run_leg(errors, "serving", run_serving, args) if (main_rank and not args.no_serving) else None
+    serving = run_leg(errors, "serving", run_serving, args, value * N) if (main_rank and not args.no_serving) else None
     if main_rank:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup,
@@ -998,7 +998,7 @@ def run_stats_kernels(args):
     return out
 
 
-def run_serving(args):
+def run_serving(args, fp64_single_voxel_draws=None):
     """Serving workload: a Poisson stream of requests, each a synthetic subject (ellipsoid mask
     of 5k-300k voxels, log-uniform; K in {4,6,8,10}; T in {150,300,600}; AR(1)-AR(3)), each
     running create + statistics + 8 mixed-precision Gibbs sweeps at delta = 1e-8 (the --precond
@@ -1068,7 +1068,10 @@ def run_serving(args):
             "peak_in_flight": st["peak_running"], "peak_bytes": st["peak_bytes"],
             "pool_N": [int(w.N) for w in pool], "pool_K": [int(w.K) for w in pool],
             "pool_T": [int(w.T) for w in pool], "pool_P": [int(w.P) for w in pool],
-            "work_per_request": "create + stats + 8 mixed-precision Gibbs sweeps (delta 1e-8)"}
+            "work_per_request": "create + stats + 8 mixed-precision Gibbs sweeps (delta 1e-8)",
+            "fp64_single_chain_voxel_draws_per_s": fp64_single_voxel_draws,
+            "capacity_vs_fp64_single_chain": (8 * capacity * float(np.mean([w.N for w in pool]))
+                                              / fp64_single_voxel_draws) if fp64_single_voxel_draws else None}
 
 
 def run_e2e(args, w):
