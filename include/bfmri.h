@@ -76,6 +76,18 @@ typedef struct {
                                          side per warp) run it; the FP64 streaming solver
                                          and larger batches use SSOR with omega = 1 */
 
+#define BFMRI_PRECOND_MULTIGRID    4  /* aggregation multigrid V-cycle (a replacement of
+                                         Section 3.1's incomplete Cholesky): levels of 2x2x2
+                                         aggregates (2x2 in-slice for the 4-neighbour
+                                         prior), at most 3, Galerkin coarse operators (summed
+                                         blocks, coarse Laplacian of the summed fine edge
+                                         weights), red-black block Gauss-Seidel smoothing
+                                         (red, black before the coarse correction; black, red
+                                         after), two symmetric red-black steps on the
+                                         coarsest level; single FP64 W and A solves (the
+                                         multi-RHS and mixed-precision solves use
+                                         block-Jacobi) */
+
 #define BFMRI_PREC_FP64  0  /* FP64 PCG */
 #define BFMRI_PREC_MIXED 1  /* FP32 inner PCG inside an FP64 iterative-refinement loop */
 

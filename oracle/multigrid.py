@@ -16,7 +16,8 @@ definitions (aggregation multigrid with Galerkin coarse operators):
   the coarse correction, one backward sweep black then red after it). Every coarse coupling
   joins face-adjacent aggregates, so the parity of the coarse coordinates two-colours every
   level;
-* coarsest level: exact sparse solve.
+* coarsest level: exact sparse solve, or a fixed number of symmetric red-black block
+  Gauss-Seidel steps from zero (the form the GPU runs: it keeps the cycle SPD).
 
 The V-cycle with pre- and post-smoothing mirrored and an exact coarsest solve is a symmetric
 positive definite preconditioner M, with the eigenvalues of M^-1 A in (0, 1]. With a single
@@ -85,8 +86,9 @@ def prolongation(agg, n_coarse, K):
     return sp.kron(sp.identity(K, format="csr"), P1, format="csr")
 
 
-def hierarchy(lat: Lattice, blocks, scale, n_min=64, max_levels=10):
-    """Levels from the fine B~ down to at most n_min voxels (Galerkin coarse operators)."""
+def hierarchy(lat: Lattice, blocks, scale, n_min=64, max_levels=10, min_coarse=0):
+    """Levels from the fine B~ down to at most n_min voxels (Galerkin coarse operators); a
+    coarser level is only added while it has at least min_coarse voxels."""
     N, K, _ = blocks.shape
     x, y, z = lat.coords()
     coords = np.stack([x, y, z], axis=1).astype(np.int64)
@@ -95,7 +97,7 @@ def hierarchy(lat: Lattice, blocks, scale, n_min=64, max_levels=10):
     while levels[-1].n > n_min and len(levels) < max_levels:
         fine = levels[-1]
         cc, agg = aggregate(fine.coords, two_d)
-        if len(cc) == fine.n:
+        if len(cc) == fine.n or len(cc) < min_coarse:
             break
         fine.P = prolongation(agg, len(cc), K)
         Ac = (fine.P.T @ fine.A @ fine.P).tocsr()
@@ -119,14 +121,20 @@ def block_gs(level: Level, b, x, colours):
     return x
 
 
-def vcycle(levels, b, l=0):
-    """z = M^-1 b for the V-cycle preconditioner starting at level l (regressor-major)."""
+def vcycle(levels, b, l=0, coarse_steps=None):
+    """z = M^-1 b for the V-cycle preconditioner starting at level l (regressor-major).
+    The coarsest level is solved exactly (coarse_steps None) or approximated by that many
+    symmetric red-black block Gauss-Seidel steps from zero (half-sweeps red, black, red,
+    ..., red: 2 coarse_steps + 1 of them), which keeps the cycle symmetric positive
+    definite."""
     L = levels[l]
     if l == len(levels) - 1:
-        return L.lu.solve(b)
+        if coarse_steps is None:
+            return L.lu.solve(b)
+        return block_gs(L, b, np.zeros_like(b), (0,) + (1, 0) * coarse_steps)
     x = block_gs(L, b, np.zeros_like(b), (0, 1))          # red, then black
     r = b - L.A @ x
-    x = x + L.P @ vcycle(levels, L.P.T @ r, l + 1)
+    x = x + L.P @ vcycle(levels, L.P.T @ r, l + 1, coarse_steps)
     return block_gs(L, b, x, (1, 0))                      # black, then red
 
 

@@ -23,7 +23,7 @@ BFMRI_OK = 0
 STATUS_NAMES = {0: "OK", -1: "INVALID_ARG", -2: "OOM", -3: "NOT_SPD", -4: "NOT_CONVERGED",
                 -5: "TIMEOUT", -6: "CUDA", -7: "INTERNAL", -8: "STATE"}
 BFMRI_F32, BFMRI_F64 = 0, 1
-PRECOND_NONE, PRECOND_BLOCK_JACOBI, PRECOND_SSOR, PRECOND_RB_REDUCED = 0, 1, 2, 3
+PRECOND_NONE, PRECOND_BLOCK_JACOBI, PRECOND_SSOR, PRECOND_RB_REDUCED, PRECOND_MULTIGRID = 0, 1, 2, 3, 4
 PREC_FP64, PREC_MIXED = 0, 1
 AR_SPATIAL, AR_INDEPENDENT = 0, 1
 Y_MASKED, Y_LATTICE = 0, 1

@@ -14,6 +14,7 @@
 
 #include "../../include/bfmri.h"
 #include "model.cuh"
+#include "mg.cuh"
 #include "mrhs.cuh"
 #include "pcg.cuh"
 #include "summary.cuh"
@@ -113,6 +114,13 @@ struct bfmri_handle {
   int part_rows = 0;
   std::vector<double> Sxx;
   std::vector<double> X_host;   // T x K design (digits of the tensor-core statistics)
+  std::vector<int> lin_host;    // lattice-linear index of every voxel (multigrid hierarchy)
+  // multigrid hierarchy (BFMRI_PRECOND_MULTIGRID), built on the first multigrid solve:
+  // levels 1..mg_L-1 plus level 0's slot weights and aggregate map
+  int mg_L = 0;
+  MgLevel mg_lv[MG_MAX_LEVELS];
+  double* mg_wgt0 = nullptr;
+  int* mg_agg0 = nullptr;
   int probe_tile = 1;           // right-hand-side tile of the last probe solve
   double probe_tile_ms[3] = {-1.0, -1.0, -1.0};   // autotuner's solve times of tiles 1, 2, 4
 
@@ -379,7 +387,203 @@ bfmri_status end_call(bfmri_handle* h, PcgCtrl* ctrl_out /* [2] or null */, int*
   return BFMRI_OK;
 }
 
+// Multigrid hierarchy of the handle's lattice: level l + 1 aggregates 2 x 2 x 2 voxels of
+// level l (2 x 2 in-slice for the 4-neighbour prior), at most 3 levels, stopping when a
+// coarsening no longer shrinks the level or leaves fewer than 64 voxels. Each level keeps
+// its voxels in raster order of its coordinates, the neighbour slots with the summed weights
+// of the fine edges joining two aggregates, the children of every voxel, its colour lists,
+// and work planes for D = max(K, P).
+bfmri_status ensure_mg(bfmri_handle* h) {
+  if (h->mg_L > 0) return BFMRI_OK;
+  const bool two_d = h->ndir == 4;
+  const int Dm = h->D;
+  struct Geo {
+    int N = 0, nx = 0, ny = 0, nz = 0;
+    std::vector<int> x, y, z, nbr;   // nbr [6][N]
+    std::vector<double> w;            // [6][N]
+  };
+  std::vector<Geo> geo(1);
+  Geo& g0 = geo[0];
+  g0.N = h->N;
+  g0.nx = h->nx;
+  g0.ny = h->ny;
+  g0.nz = h->nz;
+  for (int n = 0; n < h->N; ++n) {
+    const int l = h->lin_host[n];
+    g0.x.push_back(l % h->nx);
+    g0.y.push_back((l / h->nx) % h->ny);
+    g0.z.push_back(l / (h->nx * h->ny));
+  }
+  auto neighbours = [&](Geo& g, const std::vector<double>* wdir) {
+    std::vector<int> index((size_t)g.nx * g.ny * g.nz, -1);
+    for (int n = 0; n < g.N; ++n) index[((size_t)g.z[n] * g.ny + g.y[n]) * g.nx + g.x[n]] = n;
+    g.nbr.assign((size_t)6 * g.N, -1);
+    if (wdir) g.w.assign((size_t)6 * g.N, 0.0);
+    const int dx[6] = {-1, 1, 0, 0, 0, 0}, dy[6] = {0, 0, -1, 1, 0, 0}, dz[6] = {0, 0, 0, 0, -1, 1};
+    for (int n = 0; n < g.N; ++n)
+      for (int d = 0; d < h->ndir; ++d) {
+        const int xx = g.x[n] + dx[d], yy = g.y[n] + dy[d], zz = g.z[n] + dz[d];
+        if (xx < 0 || yy < 0 || zz < 0 || xx >= g.nx || yy >= g.ny || zz >= g.nz) continue;
+        const int m = index[((size_t)zz * g.ny + yy) * g.nx + xx];
+        g.nbr[(size_t)d * g.N + n] = m;
+        if (wdir && m >= 0) g.w[(size_t)d * g.N + n] = (*wdir)[d];
+      }
+  };
+  std::vector<double> wdir(6);
+  for (int d = 0; d < 6; ++d) wdir[d] = h->opt.edge_weight[d >> 1];
+  neighbours(g0, &wdir);
+  std::vector<std::vector<int>> aggs, children;   // per coarsening
+  while (geo.size() < 3) {
+    const Geo& f = geo.back();
+    Geo c;
+    c.nx = (f.nx + 1) / 2;
+    c.ny = (f.ny + 1) / 2;
+    c.nz = two_d ? f.nz : (f.nz + 1) / 2;
+    std::vector<int> slot((size_t)c.nx * c.ny * c.nz, -1), agg(f.N);
+    for (int n = 0; n < f.N; ++n) {
+      const int cx = f.x[n] / 2, cy = f.y[n] / 2, cz = two_d ? f.z[n] : f.z[n] / 2;
+      slot[((size_t)cz * c.ny + cy) * c.nx + cx] = 0;
+    }
+    for (size_t q = 0; q < slot.size(); ++q)
+      if (slot[q] == 0) {
+        slot[q] = c.N++;
+        c.x.push_back((int)(q % c.nx));
+        c.y.push_back((int)((q / c.nx) % c.ny));
+        c.z.push_back((int)(q / ((size_t)c.nx * c.ny)));
+      }
+    if (c.N == f.N || c.N < 64) break;
+    std::vector<int> ch((size_t)8 * c.N, -1), cnt(c.N, 0);
+    for (int n = 0; n < f.N; ++n) {
+      const int cx = f.x[n] / 2, cy = f.y[n] / 2, cz = two_d ? f.z[n] : f.z[n] / 2;
+      const int a = slot[((size_t)cz * c.ny + cy) * c.nx + cx];
+      agg[n] = a;
+      ch[(size_t)(cnt[a]++) * c.N + a] = n;
+    }
+    neighbours(c, nullptr);
+    c.w.assign((size_t)6 * c.N, 0.0);
+    for (int n = 0; n < f.N; ++n)
+      for (int d = 0; d < 6; ++d) {
+        const int m = f.nbr[(size_t)d * f.N + n];
+        if (m >= 0 && agg[n] != agg[m]) c.w[(size_t)d * c.N + agg[n]] += f.w[(size_t)d * f.N + n];
+      }
+    aggs.push_back(agg);
+    children.push_back(ch);
+    geo.push_back(c);
+  }
+  const int L = (int)geo.size();
+  auto dcopy = [&](const void* src, size_t bytes) -> void* {
+    void* p = dalloc(h, bytes);
+    if (p && bytes && cudaMemcpyAsync(p, src, bytes, cudaMemcpyHostToDevice, h->stream) != cudaSuccess) return nullptr;
+    return p;
+  };
+  // planes [rows][ld] from host [rows][N]
+  auto planes_i = [&](const std::vector<int>& v, int rows, int N, size_t ld) -> int* {
+    std::vector<int> pad((size_t)rows * ld, -1);
+    for (int r = 0; r < rows; ++r) std::copy(v.begin() + (size_t)r * N, v.begin() + (size_t)(r + 1) * N, pad.begin() + (size_t)r * ld);
+    return (int*)dcopy(pad.data(), pad.size() * sizeof(int));
+  };
+  auto planes_d = [&](const std::vector<double>& v, int rows, int N, size_t ld) -> double* {
+    std::vector<double> pad((size_t)rows * ld, 0.0);
+    for (int r = 0; r < rows; ++r) std::copy(v.begin() + (size_t)r * N, v.begin() + (size_t)(r + 1) * N, pad.begin() + (size_t)r * ld);
+    return (double*)dcopy(pad.data(), pad.size() * sizeof(double));
+  };
+  // level 0: the handle's planes, lists, blocks and factor; its slot weights and aggregates
+  h->mg_wgt0 = planes_d(g0.w, 6, g0.N, h->ld);
+  if (L > 1) h->mg_agg0 = planes_i(aggs[0], 1, g0.N, h->ld);
+  if (!h->mg_wgt0 || (L > 1 && !h->mg_agg0)) return fail(h, BFMRI_ERR_OOM, "multigrid allocation failed");
+  for (int l = 1; l < L; ++l) {
+    const Geo& g = geo[l];
+    MgLevel& v = h->mg_lv[l];
+    memset(&v, 0, sizeof(v));
+    v.N = g.N;
+    v.ld = ((size_t)g.N + 31) & ~size_t(31);
+    v.nbr = planes_i(g.nbr, 6, g.N, v.ld);
+    v.wgt = planes_d(g.w, 6, g.N, v.ld);
+    v.child = planes_i(children[l - 1], 8, g.N, v.ld);
+    if (l + 1 < L) v.agg = planes_i(aggs[l], 1, g.N, v.ld);
+    std::vector<unsigned char> col(v.ld, 0);
+    std::vector<int> red, black;
+    for (int n = 0; n < g.N; ++n) {
+      col[n] = (unsigned char)((g.x[n] + g.y[n] + g.z[n]) & 1);
+      (col[n] ? black : red).push_back(n);
+    }
+    v.colour = (const unsigned char*)dcopy(col.data(), col.size());
+    v.red = (const int*)dcopy(red.data(), std::max<size_t>(red.size(), 1) * sizeof(int));
+    v.black = (const int*)dcopy(black.data(), std::max<size_t>(black.size(), 1) * sizeof(int));
+    v.n_red = (int)red.size();
+    v.n_black = (int)black.size();
+    v.blocks = (const double*)dalloc(h, (size_t)ntri(Dm) * v.ld * sizeof(double));
+    v.fac = (double*)dalloc(h, (size_t)ntri(Dm) * v.ld * sizeof(double));
+    v.b = (double*)dalloc(h, (size_t)Dm * v.ld * sizeof(double));
+    v.x = (double*)dalloc(h, (size_t)Dm * v.ld * sizeof(double));
+    v.r = (double*)dalloc(h, (size_t)Dm * v.ld * sizeof(double));
+    if (!v.nbr || !v.wgt || !v.child || (l + 1 < L && !v.agg) || !v.colour || !v.red || !v.black ||
+        !v.blocks || !v.fac || !v.b || !v.x || !v.r)
+      return fail(h, BFMRI_ERR_OOM, "multigrid allocation failed");
+  }
+  CU(h, cudaStreamSynchronize(h->stream));   // the host staging vectors go out of scope
+  h->mg_L = L;
+  return BFMRI_OK;
+}
+
+// Arguments of a multigrid solve of the system currently assembled in d_blocks / d_mfac
+// (level 0's Gauss-Seidel factor is the block-Jacobi factor of blocks + diag(scale) deg).
+MgArgs mg_args(bfmri_handle* h, const double* scale, double* x, int which) {
+  MgArgs m;
+  memset(&m, 0, sizeof(m));
+  m.L = h->mg_L;
+  m.coarse_steps = 2;
+  MgLevel& z = m.lv[0];
+  z.N = h->N;
+  z.ld = h->ld;
+  z.nbr = h->d_nbr;
+  z.wgt = h->mg_wgt0;
+  z.agg = h->mg_agg0;
+  z.colour = h->d_colour;
+  z.red = h->d_red;
+  z.n_red = h->n_red;
+  z.black = h->d_black;
+  z.n_black = h->n_black;
+  z.blocks = h->d_blocks;
+  z.fac = h->d_mfac;
+  z.b = h->d_r;
+  z.x = h->d_z;
+  z.r = h->d_p1;
+  for (int l = 1; l < h->mg_L; ++l) m.lv[l] = h->mg_lv[l];
+  m.scale = scale;
+  m.b = h->d_rhs;
+  m.x = x;
+  m.r = h->d_r;
+  m.z = h->d_z;
+  m.p = h->d_p0;
+  m.q = h->d_q;
+  m.part = h->d_part;
+  m.part1 = h->d_part + (size_t)h->part_rows * 4;
+  m.max_grid = h->part_rows;
+  m.bar.count = h->d_bar;
+  m.bar.gen = h->d_bar + 1;
+  m.bar.err = h->d_err;
+  m.bar.timeout_ns = (unsigned long long)(h->opt.barrier_timeout_s * 1e9);
+  m.ctrl = h->d_ctrl + which;
+  m.delta = h->opt.delta;
+  m.max_iter = h->opt.max_iter;
+  m.bad_voxel = h->d_flags;
+  return m;
+}
+
+bfmri_status run_pcg_mg(bfmri_handle* h, int D, const double* scale, double* x, int which) {
+  RET(ensure_mg(h));
+  MgArgs m = mg_args(h, scale, x, which);
+  Timed tm(h, which == 0 ? BFMRI_T_PCG_W : BFMRI_T_PCG_A, true, which);
+  cudaError_t e = launch_mg_setup(D, m, h->stream);
+  int grid = 0;
+  if (e == cudaSuccess) e = launch_pcg_mg(D, m, h->stream, &grid);
+  if (e != cudaSuccess) return cuda_fail(h, e, "multigrid PCG");
+  return BFMRI_OK;
+}
+
 bfmri_status run_pcg(bfmri_handle* h, int D, const double* scale, double* x, int which) {
+  if (h->opt.precond == BFMRI_PRECOND_MULTIGRID) return run_pcg_mg(h, D, scale, x, which);
   PcgArgs a;
   memset(&a, 0, sizeof(a));
   a.N = h->N;
@@ -798,7 +1002,8 @@ bfmri_status bfmri_create(const bfmri_lattice* lat, const uint8_t* mask, const d
   if (o.pcg_variant != BFMRI_PCG_AUTO && o.pcg_variant != BFMRI_PCG_STREAMING)
     return fail(nullptr, BFMRI_ERR_INVALID_ARG, "unknown pcg_variant");
   if (o.precond != BFMRI_PRECOND_NONE && o.precond != BFMRI_PRECOND_BLOCK_JACOBI &&
-      o.precond != BFMRI_PRECOND_SSOR && o.precond != BFMRI_PRECOND_RB_REDUCED)
+      o.precond != BFMRI_PRECOND_SSOR && o.precond != BFMRI_PRECOND_RB_REDUCED &&
+      o.precond != BFMRI_PRECOND_MULTIGRID)
     return fail(nullptr, BFMRI_ERR_INVALID_ARG, "unknown preconditioner");
   if (o.precond == BFMRI_PRECOND_SSOR && !(o.ssor_omega > 0.0 && o.ssor_omega < 2.0))
     return fail(nullptr, BFMRI_ERR_INVALID_ARG, "ssor_omega must be in (0, 2)");
@@ -886,6 +1091,7 @@ bfmri_status bfmri_create(const bfmri_lattice* lat, const uint8_t* mask, const d
     return fail(nullptr, BFMRI_ERR_INVALID_ARG, "Y has non-finite values");
   }
   h->X_host.assign(X, X + (size_t)T * K);
+  h->lin_host = lin;
   // voxel-independent lagged X products Sxx[p][q][i][j] over t = P+1..T (1-based)
   h->Sxx.assign((size_t)(P + 1) * (P + 1) * K * K, 0.0);
   for (int p = 0; p <= P; ++p)
@@ -2202,7 +2408,15 @@ bfmri_status bfmri_apply_preconditioner(bfmri_handle* h, int which, const double
   p.black = h->d_black;
   p.n_black = h->n_black;
   p.colour = h->d_colour;
-  e = launch_precond_apply(D, p, h->stream);
+  if (h->opt.precond == BFMRI_PRECOND_MULTIGRID) {
+    RET(ensure_mg(h));
+    MgArgs m = mg_args(h, p.scale, h->d_W, which);
+    m.apply_only = 1;
+    e = launch_mg_setup(D, m, h->stream);
+    if (e == cudaSuccess) e = launch_pcg_mg(D, m, h->stream, nullptr);
+  } else {
+    e = launch_precond_apply(D, p, h->stream);
+  }
   if (e != cudaSuccess) return cuda_fail(h, e, "preconditioner apply");
   RET(end_call(h, nullptr, nullptr));
   return to_host(h, y, h->d_z, D);

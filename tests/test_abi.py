@@ -70,7 +70,7 @@ def test_create_rejects_bad_arguments_without_touching_the_gpu(lib):
                                torch_memory=False)
         assert ei.value.status == -1
     for fields in (dict(precond=2, ssor_omega=2.0), dict(precond=2, ssor_omega=0.0),
-                   dict(precond=4), dict(edge_weight=(1.0, 0.0, 1.0)),
+                   dict(precond=5), dict(edge_weight=(1.0, 0.0, 1.0)),
                    dict(edge_weight=(1.0, 1.0, float("inf")))):
         o = bfmri.bfmri_default_options()
         for k, v in fields.items():
