@@ -457,6 +457,7 @@ def run_ours(args, world, rank, local):
     conv = run_leg(errors, "convergence", run_convergence, args) if (main_rank and args.convergence) else None
     chains = run_leg(errors, "grouped_chains", run_chains, args, w, flush, stream, value) if not args.no_chains else None
     precs = run_leg(errors, "preconditioners", run_precond_compare, args, w) if (main_rank and not args.no_precond) else None
+    mgc = run_leg(errors, "multigrid_chain", run_multigrid_chain, args, w) if (main_rank and not args.no_precond) else None
     graphs = run_leg(errors, "captured_sweeps", run_graph_compare, args, w, flush, stream) if (main_rank and not args.no_graph) else None
     del flush
     # end to end through the C ABI with host buffers
@@ -481,7 +482,7 @@ def run_ours(args, world, rank, local):
                 "voxel_draws_per_s": value * N,
                 "mixed_precision": mixed, "summaries": summ, "convergence": conv,
                 "grouped_chains": chains,
-                "preconditioners": precs,
+                "preconditioners": precs, "multigrid_chain": mgc,
                 "captured_sweeps": graphs, "serving": serving, "batched_probes": batched,
                 "stats_kernels": stats_k,
                 "gpu_launches": int(n_launch),
@@ -758,7 +759,8 @@ def run_precond_compare(args, w, n_draws=10):
              ("mixed_ssor_omega1.0_resident", dict(precond=bfmri.PRECOND_SSOR, ssor_omega=1.0,
                                                    precision=bfmri.PREC_MIXED)),
              ("mixed_rb_reduced_resident", dict(precond=bfmri.PRECOND_RB_REDUCED,
-                                                precision=bfmri.PREC_MIXED))]
+                                                precision=bfmri.PREC_MIXED)),
+             ("multigrid", dict(precond=bfmri.PRECOND_MULTIGRID))]
     out = {}
     for name, opts in cases:
         m = Model.from_workload(w, delta=1e-8, seed=2024, profile=1, **opts)
@@ -776,6 +778,41 @@ def run_precond_compare(args, w, n_draws=10):
                      "W_solve_ms_per_draw": t["pcg_W"]["ms"] / n_draws,
                      "A_iterations_per_draw": t["pcg_A"]["pcg_iterations"] / n_draws,
                      "A_solve_ms_per_draw": t["pcg_A"]["ms"] / n_draws}
+    return out
+
+
+def run_multigrid_chain(args, w, sweeps=200, windows=((5, 25), (25, 50), (50, 100), (100, 200))):
+    """The headline chain (same seed, delta 1e-8, FP64) with the reduced red-black solver and
+    with the multigrid V-cycle preconditioner, 200 sweeps each: per window of sweeps, W and A
+    PCG iterations and solve time per draw (CUDA events around every solver launch). The
+    chains' states differ (different rounding), the windows compare like with like."""
+    import torch
+
+    from paper_1606_00980_gb300 import bfmri
+    from paper_1606_00980_gb300.bfmri import Model
+    out = {}
+    for name, pc in (("rb_reduced", bfmri.PRECOND_RB_REDUCED), ("multigrid", bfmri.PRECOND_MULTIGRID)):
+        m = Model.from_workload(w, delta=1e-8, seed=2024, profile=2, precond=pc)
+        m.precompute_stats()
+        rows = {}
+        done = 0
+        for (a, b) in windows:
+            if done < a:
+                m.gibbs_sweep(a - done, done, info=False)
+                m.synchronize()
+            m.reset_timing()
+            m.gibbs_sweep(b - a, a, info=False)
+            m.synchronize()
+            torch.cuda.synchronize()
+            t = m.timing()
+            n = b - a
+            rows[f"{a}-{b}"] = {"W_iterations": t["pcg_W"]["pcg_iterations"] / n,
+                                "W_ms": t["pcg_W"]["ms"] / n,
+                                "A_iterations": t["pcg_A"]["pcg_iterations"] / n,
+                                "A_ms": t["pcg_A"]["ms"] / n}
+            done = b
+        m.close()
+        out[name] = rows
     return out
 
 
@@ -1127,6 +1164,8 @@ def main():
                     help="run only the batched-probe measurement (profiling entry point)")
     ap.add_argument("--serving-requests", type=int, default=96)
     ap.add_argument("--no-stats", action="store_true")
+    ap.add_argument("--only-multigrid", action="store_true",
+                    help="run only the multigrid-vs-reduced chain comparison")
     ap.add_argument("--stats-case", default="all", choices=["all", "wholebrain3d", "serving_max"])
     ap.add_argument("--only-stats", action="store_true",
                     help="run only the statistics-kernel comparison (profiling entry point)")
@@ -1141,6 +1180,10 @@ def main():
     rc = 0
     if args.impl == "reference":
         run_reference(args, world, rank)
+    elif args.only_multigrid:
+        if rank == 0:
+            from paper_1606_00980_gb300 import synth
+            print(json.dumps(run_multigrid_chain(args, synth.wholebrain3d())), flush=True)
     elif args.only_stats:
         if rank == 0:
             print(json.dumps(run_stats_kernels(args)), flush=True)
