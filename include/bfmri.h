@@ -439,8 +439,9 @@ bfmri_status bfmri_reset_timing(bfmri_handle* h);
 bfmri_status bfmri_apply_precision(bfmri_handle* h, int which, const double* x, double* y);
 /*  bfmri_apply_preconditioner: y = M^-1 x (dim x N row-major) with M the solver's
  *    preconditioner for the current state's system: block-Jacobi (blocks B_n + diag(scale)
- *    deg_n), identity, or red-black SSOR over those blocks (Section 3.1 uses an incomplete
- *    Cholesky factor instead). */
+ *    deg_n), identity, red-black SSOR over those blocks, or one multigrid V-cycle
+ *    (BFMRI_PRECOND_MULTIGRID; the first call builds the hierarchy). Section 3.1 uses an
+ *    incomplete Cholesky factor instead. */
 bfmri_status bfmri_apply_preconditioner(bfmri_handle* h, int which, const double* x, double* y);
 bfmri_status bfmri_build_system(bfmri_handle* h, int which, uint64_t counter, double* blocks,
                                 double* b_mean, double* b_pert);
@@ -488,7 +489,10 @@ typedef struct {
 /* Admission estimate of one request: every device allocation bfmri_create makes for a handle
  * of this shape (Y included, although the statistics step releases it), each rounded as the
  * library rounds it, plus a margin of 1/32 and 2 MiB for the pool's own rounding. 0 for
- * invalid sizes. */
+ * invalid sizes. A request with precond = BFMRI_PRECOND_MULTIGRID also builds the
+ * multigrid hierarchy of its mask on its first solve; bfmri_server_submit adds those bytes
+ * (from the mask) and 1/32 of them to this estimate, and reports the sum in
+ * bfmri_result.device_bytes. */
 size_t bfmri_request_device_bytes(int N, int T, int K, int P, int y_dtype, int precision);
 /* High-water mark of the bytes in use from the server's memory pool
  * (cudaMemPoolAttrUsedMemHigh); reset != 0 restarts it from the current use. */

@@ -78,6 +78,122 @@ size_t handle_device_bytes(int N, int T, int K, int P, size_t y_esz, bool mixed)
   if (mixed) b += 2 * r((size_t)ntri((int)D) * ld * 4) + 6 * r(D * ld * 4);
   return b;
 }
+
+// Host geometry of the multigrid hierarchy of a lattice. Level l + 1 aggregates 2 x 2 x 2
+// voxels of level l (2 x 2 in-slice for the 4-neighbour prior); there are at most
+// MG_BUILD_LEVELS levels, and a coarsening is kept only while it shrinks the level and leaves
+// at least 64 voxels. Each level holds its voxels in raster order of their coordinates and
+// their neighbour slots; level 0's slot weights are the prior's per-direction weights, a
+// coarse slot's weight is the sum of the weights of the fine edges joining the two aggregates
+// (the Galerkin coarse graph of piecewise-constant prolongation).
+constexpr int MG_BUILD_LEVELS = 3;
+
+struct MgGeo {
+  int N = 0, nx = 0, ny = 0, nz = 0;
+  std::vector<int> x, y, z, nbr;   // nbr [6][N]: neighbour per slot (-x,+x,-y,+y,-z,+z) or -1
+  std::vector<double> w;            // [6][N] slot weights (0 where there is no neighbour)
+  std::vector<int> agg;             // [N] aggregate on the next level (all but the coarsest)
+  std::vector<int> child;           // [8][N] voxels of the previous level (levels >= 1), -1 padding
+  std::vector<int> red, black;      // voxels of even / odd coordinate sum
+};
+
+std::vector<MgGeo> mg_geometry(int nx, int ny, int nz, int ndir, const int* lin, int N, const double* cw) {
+  const bool two_d = ndir == 4;
+  std::vector<MgGeo> geo(1);
+  geo.reserve(MG_BUILD_LEVELS);
+  {
+    MgGeo& g = geo[0];
+    g.N = N;
+    g.nx = nx;
+    g.ny = ny;
+    g.nz = nz;
+    for (int n = 0; n < N; ++n) {
+      g.x.push_back(lin[n] % nx);
+      g.y.push_back((lin[n] / nx) % ny);
+      g.z.push_back(lin[n] / (nx * ny));
+    }
+  }
+  auto neighbours = [&](MgGeo& g) {
+    std::vector<int> index((size_t)g.nx * g.ny * g.nz, -1);
+    for (int n = 0; n < g.N; ++n) index[((size_t)g.z[n] * g.ny + g.y[n]) * g.nx + g.x[n]] = n;
+    g.nbr.assign((size_t)6 * g.N, -1);
+    g.w.assign((size_t)6 * g.N, 0.0);
+    const int dx[6] = {-1, 1, 0, 0, 0, 0}, dy[6] = {0, 0, -1, 1, 0, 0}, dz[6] = {0, 0, 0, 0, -1, 1};
+    for (int n = 0; n < g.N; ++n)
+      for (int d = 0; d < ndir; ++d) {
+        const int xx = g.x[n] + dx[d], yy = g.y[n] + dy[d], zz = g.z[n] + dz[d];
+        if (xx < 0 || yy < 0 || zz < 0 || xx >= g.nx || yy >= g.ny || zz >= g.nz) continue;
+        g.nbr[(size_t)d * g.N + n] = index[((size_t)zz * g.ny + yy) * g.nx + xx];
+      }
+    for (int n = 0; n < g.N; ++n) ((g.x[n] + g.y[n] + g.z[n]) & 1 ? g.black : g.red).push_back(n);
+  };
+  neighbours(geo[0]);
+  for (int d = 0; d < 6; ++d)
+    for (int n = 0; n < N; ++n)
+      if (geo[0].nbr[(size_t)d * N + n] >= 0) geo[0].w[(size_t)d * N + n] = cw[d >> 1];
+  while ((int)geo.size() < MG_BUILD_LEVELS) {
+    MgGeo& f = geo.back();
+    MgGeo c;
+    c.nx = (f.nx + 1) / 2;
+    c.ny = (f.ny + 1) / 2;
+    c.nz = two_d ? f.nz : (f.nz + 1) / 2;
+    std::vector<int> slot((size_t)c.nx * c.ny * c.nz, -1);
+    auto cell = [&](int n) {
+      return ((size_t)(two_d ? f.z[n] : f.z[n] / 2) * c.ny + f.y[n] / 2) * c.nx + f.x[n] / 2;
+    };
+    for (int n = 0; n < f.N; ++n) slot[cell(n)] = 0;
+    for (size_t q = 0; q < slot.size(); ++q)
+      if (slot[q] == 0) {
+        slot[q] = c.N++;
+        c.x.push_back((int)(q % c.nx));
+        c.y.push_back((int)((q / c.nx) % c.ny));
+        c.z.push_back((int)(q / ((size_t)c.nx * c.ny)));
+      }
+    if (c.N == f.N || c.N < 64) break;
+    f.agg.assign(f.N, 0);
+    c.child.assign((size_t)8 * c.N, -1);
+    std::vector<int> cnt(c.N, 0);
+    for (int n = 0; n < f.N; ++n) {
+      const int a = slot[cell(n)];
+      f.agg[n] = a;
+      c.child[(size_t)(cnt[a]++) * c.N + a] = n;
+    }
+    neighbours(c);
+    for (int n = 0; n < f.N; ++n)
+      for (int d = 0; d < 6; ++d) {
+        const int m = f.nbr[(size_t)d * f.N + n];
+        if (m >= 0 && f.agg[n] != f.agg[m]) c.w[(size_t)d * c.N + f.agg[n]] += f.w[(size_t)d * f.N + n];
+      }
+    geo.push_back(std::move(c));   // capacity was reserved: f stays valid until here
+  }
+  return geo;
+}
+
+// Device bytes that ensure_mg allocates for a hierarchy (each allocation rounded up to 256
+// bytes as dalloc does) for work planes of D components.
+size_t mg_device_bytes(const std::vector<MgGeo>& geo, size_t ld0, int D) {
+  auto r = [](size_t b) { return ((b == 0 ? 256 : b) + 255) & ~size_t(255); };
+  const int L = (int)geo.size();
+  size_t b = r(6 * ld0 * 8) + (L > 1 ? r(ld0 * 4) : 0);             // level 0: slot weights, aggregates
+  for (int l = 1; l < L; ++l) {
+    const size_t ld = ((size_t)geo[l].N + 31) & ~size_t(31);
+    b += r(6 * ld * 4) + r(6 * ld * 8) + r(8 * ld * 4) + (l + 1 < L ? r(ld * 4) : 0);
+    b += r(ld) + r(geo[l].red.size() * 4) + r(geo[l].black.size() * 4);
+    b += 2 * r((size_t)ntri(D) * ld * 8) + 3 * r((size_t)D * ld * 8);
+  }
+  return b;
+}
+
+// The multigrid bytes of a request on a masked lattice (serving admission).
+size_t mg_request_bytes(const bfmri_lattice& lat, const uint8_t* mask, int D) {
+  std::vector<int> lin;
+  const long long nsite = (long long)lat.nx * lat.ny * lat.nz;
+  for (long long l = 0; l < nsite; ++l)
+    if (mask[l]) lin.push_back((int)l);
+  const double ones[3] = {1.0, 1.0, 1.0};
+  const auto geo = mg_geometry(lat.nx, lat.ny, lat.nz, lat.neighbourhood, lin.data(), (int)lin.size(), ones);
+  return mg_device_bytes(geo, ((size_t)lin.size() + 31) & ~size_t(31), D);
+}
 }  // namespace bfmri
 
 struct bfmri_handle {
@@ -387,89 +503,15 @@ bfmri_status end_call(bfmri_handle* h, PcgCtrl* ctrl_out /* [2] or null */, int*
   return BFMRI_OK;
 }
 
-// Multigrid hierarchy of the handle's lattice: level l + 1 aggregates 2 x 2 x 2 voxels of
-// level l (2 x 2 in-slice for the 4-neighbour prior), at most 3 levels, stopping when a
-// coarsening no longer shrinks the level or leaves fewer than 64 voxels. Each level keeps
-// its voxels in raster order of its coordinates, the neighbour slots with the summed weights
-// of the fine edges joining two aggregates, the children of every voxel, its colour lists,
-// and work planes for D = max(K, P).
+// Multigrid hierarchy of the handle's lattice on the device (mg_geometry): per level its
+// neighbour slots and weights, the children of every voxel, its aggregates on the next level,
+// its colour lists, and blocks, factor and work planes for D = max(K, P). Level 0 uses the
+// handle's own planes, lists, blocks and factor.
 bfmri_status ensure_mg(bfmri_handle* h) {
   if (h->mg_L > 0) return BFMRI_OK;
-  const bool two_d = h->ndir == 4;
   const int Dm = h->D;
-  struct Geo {
-    int N = 0, nx = 0, ny = 0, nz = 0;
-    std::vector<int> x, y, z, nbr;   // nbr [6][N]
-    std::vector<double> w;            // [6][N]
-  };
-  std::vector<Geo> geo(1);
-  Geo& g0 = geo[0];
-  g0.N = h->N;
-  g0.nx = h->nx;
-  g0.ny = h->ny;
-  g0.nz = h->nz;
-  for (int n = 0; n < h->N; ++n) {
-    const int l = h->lin_host[n];
-    g0.x.push_back(l % h->nx);
-    g0.y.push_back((l / h->nx) % h->ny);
-    g0.z.push_back(l / (h->nx * h->ny));
-  }
-  auto neighbours = [&](Geo& g, const std::vector<double>* wdir) {
-    std::vector<int> index((size_t)g.nx * g.ny * g.nz, -1);
-    for (int n = 0; n < g.N; ++n) index[((size_t)g.z[n] * g.ny + g.y[n]) * g.nx + g.x[n]] = n;
-    g.nbr.assign((size_t)6 * g.N, -1);
-    if (wdir) g.w.assign((size_t)6 * g.N, 0.0);
-    const int dx[6] = {-1, 1, 0, 0, 0, 0}, dy[6] = {0, 0, -1, 1, 0, 0}, dz[6] = {0, 0, 0, 0, -1, 1};
-    for (int n = 0; n < g.N; ++n)
-      for (int d = 0; d < h->ndir; ++d) {
-        const int xx = g.x[n] + dx[d], yy = g.y[n] + dy[d], zz = g.z[n] + dz[d];
-        if (xx < 0 || yy < 0 || zz < 0 || xx >= g.nx || yy >= g.ny || zz >= g.nz) continue;
-        const int m = index[((size_t)zz * g.ny + yy) * g.nx + xx];
-        g.nbr[(size_t)d * g.N + n] = m;
-        if (wdir && m >= 0) g.w[(size_t)d * g.N + n] = (*wdir)[d];
-      }
-  };
-  std::vector<double> wdir(6);
-  for (int d = 0; d < 6; ++d) wdir[d] = h->opt.edge_weight[d >> 1];
-  neighbours(g0, &wdir);
-  std::vector<std::vector<int>> aggs, children;   // per coarsening
-  while (geo.size() < 3) {
-    const Geo& f = geo.back();
-    Geo c;
-    c.nx = (f.nx + 1) / 2;
-    c.ny = (f.ny + 1) / 2;
-    c.nz = two_d ? f.nz : (f.nz + 1) / 2;
-    std::vector<int> slot((size_t)c.nx * c.ny * c.nz, -1), agg(f.N);
-    for (int n = 0; n < f.N; ++n) {
-      const int cx = f.x[n] / 2, cy = f.y[n] / 2, cz = two_d ? f.z[n] : f.z[n] / 2;
-      slot[((size_t)cz * c.ny + cy) * c.nx + cx] = 0;
-    }
-    for (size_t q = 0; q < slot.size(); ++q)
-      if (slot[q] == 0) {
-        slot[q] = c.N++;
-        c.x.push_back((int)(q % c.nx));
-        c.y.push_back((int)((q / c.nx) % c.ny));
-        c.z.push_back((int)(q / ((size_t)c.nx * c.ny)));
-      }
-    if (c.N == f.N || c.N < 64) break;
-    std::vector<int> ch((size_t)8 * c.N, -1), cnt(c.N, 0);
-    for (int n = 0; n < f.N; ++n) {
-      const int cx = f.x[n] / 2, cy = f.y[n] / 2, cz = two_d ? f.z[n] : f.z[n] / 2;
-      const int a = slot[((size_t)cz * c.ny + cy) * c.nx + cx];
-      agg[n] = a;
-      ch[(size_t)(cnt[a]++) * c.N + a] = n;
-    }
-    neighbours(c, nullptr);
-    c.w.assign((size_t)6 * c.N, 0.0);
-    for (int n = 0; n < f.N; ++n)
-      for (int d = 0; d < 6; ++d) {
-        const int m = f.nbr[(size_t)d * f.N + n];
-        if (m >= 0 && agg[n] != agg[m]) c.w[(size_t)d * c.N + agg[n]] += f.w[(size_t)d * f.N + n];
-      }
-    aggs.push_back(agg);
-    children.push_back(ch);
-    geo.push_back(c);
-  }
+  const std::vector<MgGeo> geo =
+      mg_geometry(h->nx, h->ny, h->nz, h->ndir, h->lin_host.data(), h->N, h->opt.edge_weight);
   const int L = (int)geo.size();
   auto dcopy = [&](const void* src, size_t bytes) -> void* {
     void* p = dalloc(h, bytes);
@@ -487,31 +529,26 @@ bfmri_status ensure_mg(bfmri_handle* h) {
     for (int r = 0; r < rows; ++r) std::copy(v.begin() + (size_t)r * N, v.begin() + (size_t)(r + 1) * N, pad.begin() + (size_t)r * ld);
     return (double*)dcopy(pad.data(), pad.size() * sizeof(double));
   };
-  // level 0: the handle's planes, lists, blocks and factor; its slot weights and aggregates
-  h->mg_wgt0 = planes_d(g0.w, 6, g0.N, h->ld);
-  if (L > 1) h->mg_agg0 = planes_i(aggs[0], 1, g0.N, h->ld);
+  h->mg_wgt0 = planes_d(geo[0].w, 6, geo[0].N, h->ld);
+  if (L > 1) h->mg_agg0 = planes_i(geo[0].agg, 1, geo[0].N, h->ld);
   if (!h->mg_wgt0 || (L > 1 && !h->mg_agg0)) return fail(h, BFMRI_ERR_OOM, "multigrid allocation failed");
   for (int l = 1; l < L; ++l) {
-    const Geo& g = geo[l];
+    const MgGeo& g = geo[l];
     MgLevel& v = h->mg_lv[l];
     memset(&v, 0, sizeof(v));
     v.N = g.N;
     v.ld = ((size_t)g.N + 31) & ~size_t(31);
     v.nbr = planes_i(g.nbr, 6, g.N, v.ld);
     v.wgt = planes_d(g.w, 6, g.N, v.ld);
-    v.child = planes_i(children[l - 1], 8, g.N, v.ld);
-    if (l + 1 < L) v.agg = planes_i(aggs[l], 1, g.N, v.ld);
+    v.child = planes_i(g.child, 8, g.N, v.ld);
+    if (l + 1 < L) v.agg = planes_i(g.agg, 1, g.N, v.ld);
     std::vector<unsigned char> col(v.ld, 0);
-    std::vector<int> red, black;
-    for (int n = 0; n < g.N; ++n) {
-      col[n] = (unsigned char)((g.x[n] + g.y[n] + g.z[n]) & 1);
-      (col[n] ? black : red).push_back(n);
-    }
+    for (int n : g.black) col[n] = 1;
     v.colour = (const unsigned char*)dcopy(col.data(), col.size());
-    v.red = (const int*)dcopy(red.data(), std::max<size_t>(red.size(), 1) * sizeof(int));
-    v.black = (const int*)dcopy(black.data(), std::max<size_t>(black.size(), 1) * sizeof(int));
-    v.n_red = (int)red.size();
-    v.n_black = (int)black.size();
+    v.red = (const int*)dcopy(g.red.data(), g.red.size() * sizeof(int));
+    v.black = (const int*)dcopy(g.black.data(), g.black.size() * sizeof(int));
+    v.n_red = (int)g.red.size();
+    v.n_black = (int)g.black.size();
     v.blocks = (const double*)dalloc(h, (size_t)ntri(Dm) * v.ld * sizeof(double));
     v.fac = (double*)dalloc(h, (size_t)ntri(Dm) * v.ld * sizeof(double));
     v.b = (double*)dalloc(h, (size_t)Dm * v.ld * sizeof(double));
@@ -560,6 +597,7 @@ MgArgs mg_args(bfmri_handle* h, const double* scale, double* x, int which) {
   m.part = h->d_part;
   m.part1 = h->d_part + (size_t)h->part_rows * 4;
   m.max_grid = h->part_rows;
+  m.sm_cap = h->opt.sm_budget;
   m.bar.count = h->d_bar;
   m.bar.gen = h->d_bar + 1;
   m.bar.err = h->d_err;

@@ -370,6 +370,7 @@ cudaError_t pcg_mg_d(const MgArgs& a, cudaStream_t stream, int* grid_out) {
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_mg<D>, PCG_THREADS, 0);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  if (a.sm_cap > 0 && a.sm_cap < nsm) nsm = a.sm_cap;
   int grid = nsm * per_sm;
   const int need = (a.lv[0].N + PCG_THREADS - 1) / PCG_THREADS;
   if (need < grid) grid = need < 1 ? 1 : need;

@@ -54,6 +54,7 @@ struct MgArgs {
   double* part;          // [grid][4] reduction rows (even barrier generations)
   double* part1;         // [grid][4] (odd generations)
   int max_grid;
+  int sm_cap;            // most SMs the grid may span (0 = all)
   GridBarrier bar;
   PcgCtrl* ctrl;
   double delta;

@@ -24,6 +24,7 @@
 namespace bfmri {
 void set_global_error(const std::string& msg);                                        // bfmri_api.cu
 size_t handle_device_bytes(int N, int T, int K, int P, size_t y_esz, bool mixed);      // bfmri_api.cu
+size_t mg_request_bytes(const bfmri_lattice& lat, const uint8_t* mask, int D);         // bfmri_api.cu
 }
 
 namespace {
@@ -228,6 +229,11 @@ bfmri_status bfmri_server_submit(bfmri_server* s, const bfmri_request* req, long
   j->req = *req;
   j->N = N;
   j->bytes = bfmri_request_device_bytes(N, req->T, req->K, req->P, req->y_dtype, req->opt.precision);
+  if (req->opt.precond == BFMRI_PRECOND_MULTIGRID && N > 0) {
+    // the hierarchy a multigrid request builds on its first solve, with the same margin
+    const size_t mg = bfmri::mg_request_bytes(req->lat, req->mask, std::max(req->K, req->P));
+    j->bytes += mg + mg / 32;
+  }
   std::lock_guard<std::mutex> lk(s->mu);
   if (j->bytes > s->budget) {
     delete j;

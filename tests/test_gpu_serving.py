@@ -161,3 +161,25 @@ def test_admission_estimate_covers_every_allocation():
                                 precond=bfmri.PRECOND_RB_REDUCED))
                 high = s.pool_usage()
             assert high <= est, (w.N, prec, high, est)
+
+
+def test_multigrid_request_estimate_covers_the_hierarchy():
+    """A multigrid request builds its hierarchy on the first solve; the server's estimate for
+    it (bfmri_result.device_bytes) adds those bytes, so it stays at least the handle's own
+    peak and the pool's high-water mark for that request run alone."""
+    from paper_1606_00980_gb300 import bfmri
+    for w in bench_like_pool()[:3]:
+        m = bfmri.Model.from_workload(w, precision=bfmri.PREC_FP64, delta=1e-8,
+                                      precond=bfmri.PRECOND_MULTIGRID, sm_budget=4)
+        m.precompute_stats()
+        m.gibbs_sweep(2, 0)
+        _, peak = m.device_bytes()
+        m.close()
+        with bfmri.Server(budget_bytes=8 << 30, slots=1, sm_budget=4) as s:
+            s.pool_usage(reset=True)
+            res = s.poll(s.submit(w, 2, first_counter=0, seed=3, precision=bfmri.PREC_FP64,
+                                  delta=1e-8, precond=bfmri.PRECOND_MULTIGRID))
+            high = s.pool_usage()
+        est = res["device_bytes"]
+        assert peak <= est <= peak * 33 // 32 + (2 << 20) + 8192, (w.N, peak, est)
+        assert high <= est, (w.N, high, est)
