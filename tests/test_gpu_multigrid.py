@@ -4,12 +4,14 @@ The GPU builds at most three levels of 2x2x2 aggregates (2x2 in-slice for the 4-
 prior), adding a coarser level only while it keeps at least 64 voxels, and takes two
 symmetric red-black Gauss-Seidel steps on the coarsest level; the oracle's hierarchy with the
 same rule (max_levels = 3, min_coarse = 64, coarse_steps = 2) is the reference. One
-application of the cycle matches the oracle's to 1e-12; W and A draws with the multigrid
+application of the cycle matches the oracle's, on the oracle's own blocks, within the bound
+that the blocks' assembly error allows (block_bounds); W and A draws with the multigrid
 PCG reach the oracle's exact solve of the same perturbed system to 1e-8 (delta = 1e-12).
 """
 import numpy as np
 import pytest
 
+from block_bounds import apply_tolerance
 from oracle import gibbs, model, multigrid
 from oracle.lattice import Lattice
 from paper_1606_00980_gb300 import synth
@@ -72,12 +74,15 @@ def test_vcycle_apply_matches_oracle(case, which):
     if which == 0:
         Bd, _ = model.w_blocks_direct(w.Y, w.X, s["A"], s["lam"], w.eps)
         scale = s["alpha"]
+        entry_err = 1e-12 * np.abs(Bd).max()
     else:
         Bd, _ = model.a_blocks_direct(w.Y, w.X, s["W"], s["lam"], w.P)
         scale = s["beta"]
+        st = model.sufficient_stats(w.Y, w.X, w.P)
+        entry_err = 1e-12 * (s["lam"] * st["Syy"][:, 0, 0]).max()
     levels = multigrid.hierarchy(lat, Bd, scale, n_min=0, max_levels=3, min_coarse=64)
     ref = multigrid.vcycle(levels, model.kmajor(x.T), coarse_steps=2).reshape(D, w.N)
-    assert rel(y, ref) <= 1e-12
+    assert rel(y, ref) <= apply_tolerance(Bd, entry_err)
 
 
 def test_draws_with_multigrid_reach_the_exact_solve(case):
