@@ -790,6 +790,7 @@ def run_multigrid_chain(args, w, sweeps=200, windows=((5, 25), (25, 50), (50, 10
 
     from paper_1606_00980_gb300 import bfmri
     from paper_1606_00980_gb300.bfmri import Model
+    windows = tuple((a, b) for a, b in windows if b <= sweeps) or ((min(2, sweeps - 1), sweeps),)
     out = {}
     for name, pc in (("rb_reduced", bfmri.PRECOND_RB_REDUCED), ("multigrid", bfmri.PRECOND_MULTIGRID)):
         m = Model.from_workload(w, delta=1e-8, seed=2024, profile=2, precond=pc)
@@ -1166,6 +1167,8 @@ def main():
     ap.add_argument("--no-stats", action="store_true")
     ap.add_argument("--only-multigrid", action="store_true",
                     help="run only the multigrid-vs-reduced chain comparison")
+    ap.add_argument("--multigrid-sweeps", type=int, default=200,
+                    help="sweeps of each chain of the multigrid comparison (profiling: a few)")
     ap.add_argument("--stats-case", default="all", choices=["all", "wholebrain3d", "serving_max"])
     ap.add_argument("--only-stats", action="store_true",
                     help="run only the statistics-kernel comparison (profiling entry point)")
@@ -1183,7 +1186,8 @@ def main():
     elif args.only_multigrid:
         if rank == 0:
             from paper_1606_00980_gb300 import synth
-            print(json.dumps(run_multigrid_chain(args, synth.wholebrain3d())), flush=True)
+            print(json.dumps(run_multigrid_chain(args, synth.wholebrain3d(),
+                                                 sweeps=max(args.multigrid_sweeps, 2))), flush=True)
     elif args.only_stats:
         if rank == 0:
             print(json.dumps(run_stats_kernels(args)), flush=True)

@@ -543,8 +543,8 @@ bfmri_status bfmri_server_destroy(bfmri_server* s);
  *                returns
  *  info          may be NULL
  * Set-up: the first call on each device looks up the device address of the static array
- * (cudaGetSymbolAddress, with that device current) and caches it; make that first call before
- * any stream capture on the device. Every call reuses the same array and clears what must
+ * (cudaGetSymbolAddress, with that device current) and caches it for later calls. Every call
+ * reuses the same array and clears what must
  * start at zero, so calls that overlap on the GPU (other streams or threads, same device)
  * race and must be serialised by the caller. Problems whose scratch need
  * (bfmri_pcg_static_bytes(ld, D)) exceeds the capacity are rejected with
