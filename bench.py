@@ -87,17 +87,19 @@ def pcg_bytes_per_voxel_iter(K, w=8):
 
 
 # DRAM bytes (read + write) of one W-solve launch on the whole-brain workload, from an ncu
-# capture of the current kernel version (--set full, one launch: 25.45 MB read + 0.60 MB
-# written, the first touch of the blocks, factors, b and x; the iterations run from
-# L2), or None when the kernel has changed since its last capture.
-NCU_TRAFFIC_W = {"reduced": 26.04e6, "ssor": None}
+# capture of the current kernel version (--set full, one launch), or None when the kernel has
+# changed since its last capture. "reduced": the lane-pair kernel k_pcg_rbp2<6> (the default
+# at K = 6: 25.37 MB read + 0.56 MB written); "reduced_one_lane": k_pcg_rbp<6> (--pcg-lanes 1:
+# 25.45 MB read + 0.60 MB written). Both are the first touch of the blocks, factors, b and x;
+# the iterations run from L2.
+NCU_TRAFFIC_W = {"reduced": 25.92e6, "reduced_one_lane": 26.04e6, "ssor": None}
 
 
 def precond_options(args):
     """Options of the headline FP64 chain's preconditioner (--precond)."""
     from paper_1606_00980_gb300 import bfmri
     if args.precond == "reduced":
-        return {"precond": bfmri.PRECOND_RB_REDUCED}
+        return {"precond": bfmri.PRECOND_RB_REDUCED, "pcg_lanes": args.pcg_lanes}
     if args.precond == "ssor":
         return {"precond": bfmri.PRECOND_SSOR, "ssor_omega": 1.0}
     return {"precond": bfmri.PRECOND_BLOCK_JACOBI}
@@ -432,14 +434,18 @@ def run_ours(args, world, rank, local):
     # kernels per timed launch group: edge terms + assembly (W, A), quadratic form + draw (hyper)
     per_group = {"assemble_W": 2, "assemble_A": 2, "hyper": 2}
     n_launch = sum(v["launches"] * per_group.get(k, 1) for k, v in tim_p.items()) / n_prof * args.steps
-    kname = {"reduced": (f"k_pcg_rbp<{K}> (W solve, pipelined CG on the red-black reduced system)"
+    pairs = args.pcg_lanes == 2 or (args.pcg_lanes == 0 and K == 6)
+    kname = {"reduced": ((f"k_pcg_rbp2<{K}> (W solve, pipelined CG on the red-black reduced system, "
+                          "lane pairs)" if pairs else
+                          f"k_pcg_rbp<{K}> (W solve, pipelined CG on the red-black reduced system)")
                          if K <= 6 else f"k_pcg_rb<{K}> (W solve, red-black reduced system)"),
              "ssor": f"k_pcg_res<{K}> (W solve, SSOR)",
              "bj": f"k_pcg_res<{K}> (W solve, block-Jacobi)"}[args.precond]
     roof = {"kernel": kname,
             "bound": "alu", "achieved": achieved_tf,
             "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved_tf / FP64_PEAK_TFLOPS,
-            "traffic": NCU_TRAFFIC_W.get(args.precond),
+            "traffic": NCU_TRAFFIC_W.get("reduced_one_lane" if args.precond == "reduced" and not pairs
+                                         else args.precond),
             "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2070 MHz",
             "hbm_view": {"achieved_gbs": achieved_gbs, "peak_gbs": hbm_peak,
                          "frac": achieved_gbs / hbm_peak, "peak_source": f"{hbm_src} (MEASURED_PEAKS.json)"},
@@ -1167,6 +1173,9 @@ def main():
     ap.add_argument("--no-stats", action="store_true")
     ap.add_argument("--only-multigrid", action="store_true",
                     help="run only the multigrid-vs-reduced chain comparison")
+    ap.add_argument("--pcg-lanes", type=int, default=0, choices=[0, 1, 2],
+                    help="lanes per voxel of the resident reduced solver (0: the library's "
+                         "default, lane pairs; 1: one lane per voxel)")
     ap.add_argument("--multigrid-sweeps", type=int, default=200,
                     help="sweeps of each chain of the multigrid comparison (profiling: a few)")
     ap.add_argument("--stats-case", default="all", choices=["all", "wholebrain3d", "serving_max"])

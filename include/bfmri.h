@@ -156,6 +156,13 @@ typedef struct {
                                 the autotuner times 1, 2 and 4 on the first probe call of each
                                 shape (K or P, probe count, N, sm_budget) and keeps the fastest
                                 for the process (bfmri_probe_tuning reports it) */
+  int pcg_lanes;             /* lanes of the register-resident FP64 solver on the red-black
+                                reduced system (BFMRI_PRECOND_RB_REDUCED, K or P <= 6):
+                                2 = lane pairs, each pair holding one red and one black voxel
+                                and each lane half of their components (block products by
+                                rows, neighbour sums and updates by components); 1 = one lane
+                                per voxel; 0 (default) = lane pairs for 6 x 6 blocks, one lane
+                                otherwise. Same iterates up to rounding. */
 } bfmri_options;
 
 #define BFMRI_STATS_AUTO   0

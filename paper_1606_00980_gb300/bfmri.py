@@ -49,7 +49,8 @@ class bfmri_options(C.Structure):
                 ("debug_skip_block", C.c_int), ("profile", C.c_int), ("pcg_variant", C.c_int),
                 ("sm_budget", C.c_int), ("ssor_omega", C.c_double),
                 ("use_graph", C.c_int), ("edge_weight", C.c_double * 3),
-                ("stats_kernel", C.c_int), ("mrhs_tile", C.c_int)]
+                ("stats_kernel", C.c_int), ("mrhs_tile", C.c_int),
+                ("pcg_lanes", C.c_int)]
 
 
 class bfmri_solve_info(C.Structure):

@@ -231,6 +231,8 @@ struct bfmri_handle {
   std::vector<double> Sxx;
   std::vector<double> X_host;   // T x K design (digits of the tensor-core statistics)
   std::vector<int> lin_host;    // lattice-linear index of every voxel (multigrid hierarchy)
+  std::vector<unsigned char> colour_host;   // 0 red, 1 black per voxel
+  std::map<int, int> pair_slots;            // voxels per CTA -> lane pairs of k_pcg_rbp2
   // multigrid hierarchy (BFMRI_PRECOND_MULTIGRID), built on the first multigrid solve:
   // levels 1..mg_L-1 plus level 0's slot weights and aggregate map
   int mg_L = 0;
@@ -491,6 +493,8 @@ bfmri_status end_call(bfmri_handle* h, PcgCtrl* ctrl_out /* [2] or null */, int*
   if (exhausted) *exhausted = flags[1];
   if (err == ERR_TIMEOUT_CODE)
     return fail(h, BFMRI_ERR_TIMEOUT, "device grid barrier wait exceeded its time limit");
+  if (err == ERR_LAYOUT_CODE)
+    return fail(h, BFMRI_ERR_INTERNAL, "solver launch layout does not match the voxel colours");
   if (flags[0] != 0x7f7f7f7f)
     return fail(h, BFMRI_ERR_NOT_SPD,
                 "per-voxel block not positive definite at voxel " + std::to_string(flags[0]));
@@ -649,6 +653,27 @@ bfmri_status run_pcg(bfmri_handle* h, int D, const double* scale, double* x, int
   a.ssor = uses_ssor(h->opt);
   a.omega = ssor_omega_of(h->opt);
   a.reduced = h->opt.precond == BFMRI_PRECOND_RB_REDUCED;
+  // lane pairs by default only for 6 x 6 blocks: measured on the whole-brain workload they
+  // take the W solve (K = 6) from 0.414 to 0.404 ms per sweep, but the A solve (P = 3) from
+  // 0.364 to 0.432 ms, where the second lane holds one component and the gathers and padded
+  // triangular rows cost more than the extra warps save
+  a.lanes = (h->opt.pcg_lanes == 2 || (h->opt.pcg_lanes == 0 && D >= 6)) ? 2 : 1;
+  if (a.reduced && a.lanes == 2 && D <= 6) {
+    // lane pairs of the resident solver: the most red, or black, voxels of any CTA
+    const int per = resident_voxels_per_cta(h->N, h->opt.sm_budget);
+    auto it = h->pair_slots.find(per);
+    if (it == h->pair_slots.end()) {
+      int slots = 0;
+      for (int b0 = 0; b0 < h->N; b0 += per) {
+        int nr = 0, nb = 0;
+        for (int n = b0; n < std::min(h->N, b0 + per); ++n) (h->colour_host[n] ? nb : nr) += 1;
+        slots = std::max(slots, std::max(nr, nb));
+      }
+      it = h->pair_slots.emplace(per, slots).first;
+    }
+    a.pair_per = per;
+    a.pair_slots = it->second;
+  }
   a.red = h->d_red;
   a.n_red = h->n_red;
   a.black = h->d_black;
@@ -978,6 +1003,7 @@ void bfmri_default_options(bfmri_options* o) {
   o->debug_skip_block = -1;
   o->stats_kernel = BFMRI_STATS_AUTO;
   o->mrhs_tile = 0;
+  o->pcg_lanes = 0;
 }
 
 const char* bfmri_last_error(const bfmri_handle* h) {
@@ -1050,6 +1076,7 @@ bfmri_status bfmri_create(const bfmri_lattice* lat, const uint8_t* mask, const d
   for (int d = 0; d < 3; ++d)
     if (!(o.edge_weight[d] > 0.0) || !std::isfinite(o.edge_weight[d]))
       return fail(nullptr, BFMRI_ERR_INVALID_ARG, "edge_weight must be positive and finite");
+  if (o.pcg_lanes < 0 || o.pcg_lanes > 2) return fail(nullptr, BFMRI_ERR_INVALID_ARG, "pcg_lanes must be 0, 1 or 2");
   if (o.stats_kernel != BFMRI_STATS_AUTO && o.stats_kernel != BFMRI_STATS_FP64 &&
       o.stats_kernel != BFMRI_STATS_TENSOR)
     return fail(nullptr, BFMRI_ERR_INVALID_ARG, "unknown stats_kernel");
@@ -1218,6 +1245,7 @@ bfmri_status bfmri_create(const bfmri_lattice* lat, const uint8_t* mask, const d
   }
   h->n_red = (int)red.size();
   h->n_black = (int)black.size();
+  h->colour_host.assign(colour.begin(), colour.begin() + N);
   if (!e) e = cudaMemcpyAsync(h->d_colour, colour.data(), ld, cudaMemcpyHostToDevice, s);
   if (!e && !red.empty()) e = cudaMemcpyAsync(h->d_red, red.data(), red.size() * sizeof(int), cudaMemcpyHostToDevice, s);
   if (!e && !black.empty()) e = cudaMemcpyAsync(h->d_black, black.data(), black.size() * sizeof(int), cudaMemcpyHostToDevice, s);

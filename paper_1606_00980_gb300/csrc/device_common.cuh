@@ -302,6 +302,7 @@ __device__ __forceinline__ void st_release(unsigned int* p, unsigned int v) {
 
 constexpr int ERR_TIMEOUT_CODE = 5;
 constexpr int ERR_NOT_SPD_CODE = 3;
+constexpr int ERR_LAYOUT_CODE = 11;   // a kernel found its launch layout inconsistent with its data
 
 // The number of barriers this CTA has passed in the current launch (thread 0's copy). Every
 // kernel that uses the barriers below calls grid_barrier_start first; the counter it pairs

@@ -21,6 +21,8 @@
 // All reductions are fixed-order, so a solve is bit-reproducible: FP64 sums (grid_allreduce4)
 // for the FP64 solves and the outer residuals of the mixed solves, float-float sums
 // (grid_allreduce4_ff) for the FP32 inner iterations of the mixed solves.
+#include <algorithm>
+
 #include "pcg.cuh"
 
 namespace bfmri {
@@ -1579,6 +1581,488 @@ __global__ void __launch_bounds__(RB_MAX_THREADS, 1) k_pcg_rbp(PcgArgs a) {
 }
 
 // ---------------------------------------------------------------------------------------
+// The pipelined reduced solver on lane pairs (k_pcg_rbp2): the iteration of k_pcg_rbp, with
+// the CTA's red and black voxels paired up. Lanes 2q and 2q + 1 of the CTA hold red voxel q
+// and black voxel q of the CTA together, and lane h of the pair owns the components
+// k = 2j + h of both. In k_pcg_rbp one thread holds one voxel, so only the threads of one
+// colour work in each phase and half the warps idle; here every lane works in every phase,
+// on half of a voxel of the phase's colour, so each phase has twice the independent FP64
+// chains in flight with the same number of threads. Products with a block (triangular or
+// symmetric) are split by rows: both lanes gather the whole input vector (one __shfl_xor per
+// component) and form their own rows; neighbour sums, vector updates and inner-product
+// partials are split by components. Both lanes of a pair take the same branches, and every
+// gather runs where the whole warp takes part.
+// ---------------------------------------------------------------------------------------
+namespace {
+
+constexpr int RB2_MAX_THREADS = 384;   // two lanes per slot; 12 warps leave 168 registers
+
+// full[D] from this lane's components (2j + h) and its partner's; every lane of the warp
+// must call it together
+template <int D>
+__device__ __forceinline__ void gather2(const double* half, int h, double* full) {
+#pragma unroll
+  for (int j = 0; j < (D + 1) / 2; ++j) {
+    const double other = __shfl_xor_sync(0xffffffffu, half[j], 1);
+    full[2 * j] = h ? other : half[j];
+    if (2 * j + 1 < D) full[2 * j + 1] = h ? half[j] : other;
+  }
+}
+
+// rows k = 2j + h of L v for L packed lower (entry e at Mp[e * bs]); 0 for k >= D
+template <int D>
+__device__ __forceinline__ void lower_rows(const double* Mp, size_t bs, int h, const double* v, double* out) {
+#pragma unroll
+  for (int j = 0; j < (D + 1) / 2; ++j) {
+    const int k = 2 * j + h;
+    const int row = k < D ? k * (k + 1) / 2 : 0;
+    double acc = 0.0;
+#pragma unroll
+    for (int m = 0; m <= 2 * j; ++m) acc += Mp[(size_t)(row + m) * bs] * v[m];
+    if (2 * j + 1 < D) {
+      const double c = h ? Mp[(size_t)tri(2 * j + 1, 2 * j + 1) * bs] : 0.0;
+      acc += c * v[2 * j + 1];
+    }
+    out[j] = k < D ? acc : 0.0;
+  }
+}
+
+// rows k = 2j + h of L' v for L packed lower; 0 for k >= D
+template <int D>
+__device__ __forceinline__ void upper_rows(const double* Mp, size_t bs, int h, const double* v, double* out) {
+#pragma unroll
+  for (int j = 0; j < (D + 1) / 2; ++j) {
+    const int k = 2 * j + h;
+    double acc = h ? 0.0 : Mp[(size_t)tri(2 * j, 2 * j) * bs] * v[2 * j];
+#pragma unroll
+    for (int m = 2 * j + 1; m < D; ++m) acc += Mp[(size_t)(m * (m + 1) / 2 + k) * bs] * v[m];
+    out[j] = k < D ? acc : 0.0;
+  }
+}
+
+// rows k = 2j + h of S v for S packed symmetric; 0 for k >= D
+template <int D>
+__device__ __forceinline__ void sym_rows(const double* Mp, size_t bs, int h, const double* v, double* out) {
+#pragma unroll
+  for (int j = 0; j < (D + 1) / 2; ++j) {
+    const int k = 2 * j + h;
+    const int kk = k < D ? k : 0;
+    double acc = 0.0;
+#pragma unroll
+    for (int m = 0; m < D; ++m) {
+      const int e = kk >= m ? kk * (kk + 1) / 2 + m : m * (m + 1) / 2 + kk;
+      acc += Mp[(size_t)e * bs] * v[m];
+    }
+    out[j] = k < D ? acc : 0.0;
+  }
+}
+
+}  // namespace
+
+template <int D>
+__global__ void __launch_bounds__(RB2_MAX_THREADS, 1) k_pcg_rbp2(PcgArgs a) {
+  extern __shared__ double smem[];
+  __shared__ Shared sh;
+  __shared__ int sh_red[RB2_MAX_THREADS / 2], sh_black[RB2_MAX_THREADS / 2];
+  __shared__ int sh_cnt[2 * (RB2_MAX_THREADS / 32)];
+  __shared__ double cwd[6];
+  __shared__ double s[RES_MAX_D];
+  grid_barrier_start(a.bar);
+  constexpr int NT = ntri(D), J = (D + 1) / 2;
+  const int t = threadIdx.x, h = t & 1, q = t >> 1;
+  const int ns = a.pair_slots;   // lane pairs of a CTA: the stride of the shared planes
+  if (t == 0) slot_weights(a, cwd);
+  if (t < D) s[t] = __ldg(a.scale + t);
+  // the CTA's voxels blockIdx.x * res_per + (0 .. res_per - 1), split into a red and a black
+  // list (every CTA has at most ns of each colour; the host checked it)
+  int nred = 0, nblack = 0;
+  {
+    const int n0 = blockIdx.x * a.res_per + t;
+    const bool mine = t < a.res_per && n0 < a.N;
+    const bool blk = mine && a.colour[n0] != 0, rd = mine && !blk;
+    const int lane = t & 31, warp = t >> 5, nw = (blockDim.x + 31) >> 5;
+    const unsigned mr = __ballot_sync(0xffffffffu, rd), mb = __ballot_sync(0xffffffffu, blk);
+    if (lane == 0) {
+      sh_cnt[2 * warp] = __popc(mr);
+      sh_cnt[2 * warp + 1] = __popc(mb);
+    }
+    __syncthreads();
+    int red_before = 0, black_before = 0;
+    for (int w = 0; w < nw; ++w) {
+      if (w < warp) {
+        red_before += sh_cnt[2 * w];
+        black_before += sh_cnt[2 * w + 1];
+      }
+      nred += sh_cnt[2 * w];
+      nblack += sh_cnt[2 * w + 1];
+    }
+    const unsigned below = (1u << lane) - 1u;
+    if (rd && red_before + __popc(mr & below) < ns) sh_red[red_before + __popc(mr & below)] = n0;
+    if (blk && black_before + __popc(mb & below) < ns) sh_black[black_before + __popc(mb & below)] = n0;
+    __syncthreads();
+  }
+  const int expect = min(a.res_per, a.N - (int)blockIdx.x * a.res_per);
+  if (nred > ns || nblack > ns || 2 * ns > (int)blockDim.x || nred + nblack != expect) {
+    // the launcher sized the pairs from the colours; a mismatch stops the solve with an error
+    // (the other CTAs leave at their next barrier, which polls the error word)
+    if (t == 0) atomicCAS(a.bar.err, 0, ERR_LAYOUT_CODE);
+    return;
+  }
+  const bool hr = q < nred && q < ns, hb = q < nblack && q < ns;   // this pair's red / black voxel
+  const int nr = hr ? sh_red[q] : 0, nbv = hb ? sh_black[q] : 0;
+  const size_t ld = a.ld;
+  double* shR = smem;                 // red slot: Dg_r^-1 (symmetric)
+  double* shL = smem + NT * ns;       // black slot: L_b (true diagonal)
+  double* shM = smem + 2 * NT * ns;   // black slot: L_b^-1
+  double* shH = smem + 3 * NT * ns;   // b^
+  double* shP = shH + D * ns;         // p
+  double* shS = shP + D * ns;         // s = S^ p
+  double* shZ = shS + D * ns;         // z = S^ s
+  if (q < ns) {
+    // lane 0 of the pair prepares the red slot, lane 1 the black one
+    const bool mine = h == 0 ? hr : hb;
+    const int nn = h == 0 ? nr : nbv;
+    double Lf[NT];
+#pragma unroll
+    for (int e = 0; e < NT; ++e) Lf[e] = 0.0;
+#pragma unroll
+    for (int i = 0; i < D; ++i) Lf[tri(i, i)] = 1.0;
+    if (mine) {
+#pragma unroll
+      for (int e = 0; e < NT; ++e) Lf[e] = __ldg(a.mfac + (size_t)e * ld + nn);
+    }
+    if (h == 0) {
+#pragma unroll
+      for (int e = 0; e < NT; ++e) shR[e * ns + q] = Lf[e];
+      factor_to_inverse<D, double>(shR + q, ns);
+    } else {
+#pragma unroll
+      for (int e = 0; e < NT; ++e) shM[e * ns + q] = Lf[e];
+      double Li[NT];
+      lower_inverse<D, double>(shM + q, ns, Li);
+#pragma unroll
+      for (int i = 0; i < D; ++i)
+#pragma unroll
+        for (int j = 0; j <= i; ++j) {
+          const int e = tri(i, j);
+          shL[e * ns + q] = i == j ? 1.0 / Lf[e] : Lf[e];
+          shM[e * ns + q] = Li[e];
+        }
+    }
+  }
+  int nbr_r[6], nbr_b[6];
+#pragma unroll
+  for (int d = 0; d < 6; ++d) {
+    nbr_r[d] = (hr && d < a.ndir) ? __ldg(a.nbr + (size_t)d * ld + nr) : -1;
+    nbr_b[d] = (hb && d < a.ndir) ? __ldg(a.nbr + (size_t)d * ld + nbv) : -1;
+  }
+  __syncthreads();
+  // component 2j + h exists (only the last one of lane 1 may not, for odd D)
+  auto valid = [&](int j) -> bool { return 2 * j + 1 < D || h == 0; };
+  auto sidx = [&](int j) -> int { return (2 * j + h) * ns + q; };
+  // the black voxel's components; x holds x_b outside the iteration, x^ inside it
+  double x[J], r[J], w[J], xr[J];   // xr: the red voxel's components of x (final pass)
+#pragma unroll
+  for (int j = 0; j < J; ++j) {
+    x[j] = (hb && valid(j)) ? a.x[(size_t)(2 * j + h) * ld + nbv] : 0.0;
+    r[j] = w[j] = xr[j] = 0.0;
+  }
+  // lanes past the last pair (padding to whole warps) compute on slot 0 and store nothing
+  const int qs = q < ns ? q : 0;
+  const double* Rp = shR + qs;
+  const double* Lp = shL + qs;
+  const double* Mp = shM + qs;
+  double* U = a.u;
+  auto bar = [&]() -> bool {
+    if (a.skip_block == (int)blockIdx.x) return false;
+    return grid_sync(a.bar, &sh.flag);
+  };
+  auto scale_of = [&](int j) -> double { return valid(j) ? s[2 * j + h] : 0.0; };
+  auto publish = [&](int n, const double* v) {
+#pragma unroll
+    for (int j = 0; j < J; ++j)
+      if (valid(j)) U[(size_t)(2 * j + h) * ld + n] = v[j];
+  };
+  auto load_b = [&](bool has, int n, double* bv) {
+#pragma unroll
+    for (int j = 0; j < J; ++j) bv[j] = (has && valid(j)) ? __ldg(a.b + (size_t)(2 * j + h) * ld + n) : 0.0;
+  };
+  // this lane's components of the weighted neighbour sum of V over the slots nb
+  auto nsum = [&](const int* nb, const double* V, double* sum) {
+#pragma unroll
+    for (int j = 0; j < J; ++j) sum[j] = 0.0;
+#pragma unroll
+    for (int d = 0; d < 6; ++d) {
+      if (nb[d] >= 0) {
+#pragma unroll
+        for (int j = 0; j < J; ++j)
+          if (valid(j)) sum[j] += cwd[d] * ldx(V + (size_t)(2 * j + h) * ld + nb[d]);
+      }
+    }
+  };
+  // the red voxel: out = Dg_r^-1 (c + scale .* sum of the black neighbours' U); every lane
+  // calls it
+  auto red_solve = [&](const double* c, double* out) {
+    double sum[J], tv[J], tf[D];
+    nsum(nbr_r, U, sum);
+#pragma unroll
+    for (int j = 0; j < J; ++j) tv[j] = (c ? c[j] : 0.0) + scale_of(j) * sum[j];
+    gather2<D>(tv, h, tf);
+    sym_rows<D>(Rp, ns, h, tf, out);
+  };
+  // this lane's rows of B~ v at voxel n (data block from global memory), V the published v
+  // of every voxel; vf the whole v of voxel n, vh this lane's components
+  auto amul_rows = [&](int n, const int* nb, const double* vf, const double* vh, const double* V,
+                       double* out) {
+    double bv[J], sum[J];
+    sym_rows<D>(a.blocks + n, ld, h, vf, bv);
+    nsum(nb, V, sum);
+    const double degd = degree_of<double>(nb, cwd);
+#pragma unroll
+    for (int j = 0; j < J; ++j) out[j] = valid(j) ? bv[j] + scale_of(j) * (degd * vh[j] - sum[j]) : 0.0;
+  };
+  // red phase of a product: y = Dg_r^-1 (scale .* sum of the black neighbours' U), published
+  auto red_phase = [&]() {
+    double y[J];
+    red_solve(nullptr, y);
+    if (hr) publish(nr, y);
+  };
+  // out = S^ v at the black voxels (see k_pcg_rbp)
+  auto apply_Sh = [&](const double* v, double* out) -> bool {
+    double vf[D], vt[J];
+    gather2<D>(v, h, vf);
+    upper_rows<D>(Mp, ns, h, vf, vt);
+    if (hb) publish(nbv, vt);
+    if (!bar()) return false;
+    red_phase();
+    if (!bar()) return false;
+    double sum[J], tv[J], tf[D], nn[J];
+    nsum(nbr_b, U, sum);
+#pragma unroll
+    for (int j = 0; j < J; ++j) tv[j] = scale_of(j) * sum[j];
+    gather2<D>(tv, h, tf);
+    lower_rows<D>(Mp, ns, h, tf, nn);
+    if (hb) {
+#pragma unroll
+      for (int j = 0; j < J; ++j) out[j] = v[j] - nn[j];
+    }
+    return true;
+  };
+  // out = S v at the black voxels in unscaled variables (restarts only)
+  auto apply_S = [&](const double* v, double* out) -> bool {
+    if (hb) publish(nbv, v);
+    if (!bar()) return false;
+    red_phase();
+    if (!bar()) return false;
+    double vf[D];
+    gather2<D>(v, h, vf);
+    if (hb) amul_rows(nbv, nbr_b, vf, v, U, out);
+    return true;
+  };
+  // x_b = L_b^-T x^, then the red voxels from their rows
+  auto recover_red = [&]() -> bool {
+    double xf[D], xb[J];
+    gather2<D>(x, h, xf);
+    upper_rows<D>(Mp, ns, h, xf, xb);
+    if (hb) {
+#pragma unroll
+      for (int j = 0; j < J; ++j) x[j] = xb[j];
+      publish(nbv, x);
+    }
+    if (!bar()) return false;
+    double bv[J];
+    load_b(hr, nr, bv);
+    red_solve(bv, xr);
+    return true;
+  };
+  auto true_residual = [&](double* tot) -> bool {
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+      if (!valid(j)) continue;
+      if (hb) a.x[(size_t)(2 * j + h) * ld + nbv] = x[j];
+      if (hr) a.x[(size_t)(2 * j + h) * ld + nr] = xr[j];
+    }
+    if (!bar()) return false;
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    double xf[D], bv[J], ax[J];
+    gather2<D>(x, h, xf);
+    if (hb) {
+      load_b(true, nbv, bv);
+      amul_rows(nbv, nbr_b, xf, x, a.x, ax);
+#pragma unroll
+      for (int j = 0; j < J; ++j) v[2] += (bv[j] - ax[j]) * (bv[j] - ax[j]);
+    }
+    gather2<D>(xr, h, xf);
+    if (hr) {
+      load_b(true, nr, bv);
+      amul_rows(nr, nbr_r, xf, xr, a.x, ax);
+#pragma unroll
+      for (int j = 0; j < J; ++j) v[2] += (bv[j] - ax[j]) * (bv[j] - ax[j]);
+    }
+    return grid_allreduce4(a.bar, a.part, a.part1, v, sh.red, sh.ints, tot);
+  };
+  // (re)start from the current x_b: r^ = L_b^-1 (b^ - S x_b), x^ = L_b' x_b, w^ = S^ r^,
+  // p = s = z = 0
+  auto restart = [&]() -> bool {
+    double sx[J];
+#pragma unroll
+    for (int j = 0; j < J; ++j) sx[j] = 0.0;
+    if (!apply_S(x, sx)) return false;
+    double rb[J], rbf[D], xf[D], rh[J], xh[J];
+#pragma unroll
+    for (int j = 0; j < J; ++j) rb[j] = (hb && valid(j)) ? shH[sidx(j)] - sx[j] : 0.0;
+    gather2<D>(rb, h, rbf);
+    gather2<D>(x, h, xf);
+    lower_rows<D>(Mp, ns, h, rbf, rh);
+    upper_rows<D>(Lp, ns, h, xf, xh);
+    if (hb) {
+#pragma unroll
+      for (int j = 0; j < J; ++j) {
+        r[j] = rh[j];
+        x[j] = xh[j];
+      }
+    }
+    if (!apply_Sh(r, w)) return false;
+    if (hb) {
+#pragma unroll
+      for (int j = 0; j < J; ++j)
+        if (valid(j)) shP[sidx(j)] = shS[sidx(j)] = shZ[sidx(j)] = 0.0;
+    }
+    return true;
+  };
+
+  // b^ = b_b + scale .* sum of the red neighbours' Dg_r^-1 b_r
+  {
+    double bv[J], bf[D], y[J];
+    load_b(hr, nr, bv);
+    gather2<D>(bv, h, bf);
+    sym_rows<D>(Rp, ns, h, bf, y);
+    if (hr) publish(nr, y);
+  }
+  if (!bar()) return;
+  if (hb) {
+    double sum[J], bv[J];
+    nsum(nbr_b, U, sum);
+    load_b(true, nbv, bv);
+#pragma unroll
+    for (int j = 0; j < J; ++j)
+      if (valid(j)) shH[sidx(j)] = bv[j] + s[2 * j + h] * sum[j];
+  }
+  if (!restart()) return;   // (apply_S's first barrier orders the reads of U above)
+  double tot[4];
+  double bb = 0.0, tol2 = 0.0, rel0 = 0.0, rr = 0.0;
+  double alpha = 0.0, beta = 0.0, gam = 0.0, rgam = 0.0, ralpha = 0.0;
+  int it = 0, restarts = 0, status = 0;
+  bool first = true;        // first pass of the solve: the partials carry b'b
+  bool x_final = false;     // x holds x_b (and the red voxels are recovered)
+  while (true) {
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    {
+      // v = L_b^-T w^ first, so that its stores are in flight during the block reduction
+      double wf[D], rf[D], vt[J], lr[J];
+      gather2<D>(w, h, wf);
+      gather2<D>(r, h, rf);
+      upper_rows<D>(Mp, ns, h, wf, vt);
+      if (hb) publish(nbv, vt);
+      lower_rows<D>(Lp, ns, h, rf, lr);
+      if (hb) {
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+          v[0] += r[j] * r[j];
+          v[1] += w[j] * r[j];
+          v[2] += lr[j] * lr[j];
+        }
+      }
+    }
+    if (first) {
+      double bv[J];
+      load_b(hb, nbv, bv);
+#pragma unroll
+      for (int j = 0; j < J; ++j) v[3] += bv[j] * bv[j];
+      load_b(hr, nr, bv);
+#pragma unroll
+      for (int j = 0; j < J; ++j) v[3] += bv[j] * bv[j];
+    }
+    const double* part = allreduce4_post(a.part, a.part1, v, sh.red);
+    if (!bar()) return;                 // partials and v are visible everywhere
+    red_phase();
+    allreduce4_collect(part, sh.red, tot, 0);
+    if (first) {
+      bb = tot[3];
+      tol2 = a.delta * a.delta * bb;
+      rel0 = bb > 0.0 ? sqrt(tot[2] / bb) : 0.0;
+      first = false;
+      if (!(isfinite(tot[0]) && isfinite(tot[1]) && isfinite(bb))) status = 7;
+    }
+    rr = tot[2];
+    if (status == 0 && bb == 0.0) {
+#pragma unroll
+      for (int j = 0; j < J; ++j) x[j] = xr[j] = 0.0;
+      x_final = true;
+    }
+    int code = 0;
+    if (status == 0 && bb != 0.0) {
+      cg_scalar_step(sh, tot[0], tot[1], rr, tol2, it, a.max_iter, alpha, beta, gam, rgam, ralpha);
+      code = sh.code;
+      __syncthreads();
+    }
+    if (!bar()) return;                 // the red phase's y is visible; all partials read
+    if (status != 0 || bb == 0.0) break;
+    if (code == 7) { status = 7; break; }
+    if (code == 3) { status = 3; break; }
+    if (code == 1) {
+      // confirm with the true residual of B~
+      if (!recover_red()) return;
+      if (!true_residual(tot)) return;
+      x_final = true;
+      rr = tot[2];
+      if (rr <= tol2) break;
+      if (it >= a.max_iter) { status = 4; break; }
+      ++restarts;
+      if (!restart()) return;
+      x_final = false;
+      rgam = 0.0;
+      ralpha = 0.0;
+      continue;
+    }
+    {
+      double sum[J], tv[J], tf[D], nn[J];
+      nsum(nbr_b, U, sum);
+#pragma unroll
+      for (int j = 0; j < J; ++j) tv[j] = scale_of(j) * sum[j];
+      gather2<D>(tv, h, tf);
+      lower_rows<D>(Mp, ns, h, tf, nn);   // n = w^ - L_b^-1 (scale .* sum y)
+      if (hb) {
+        const double al = alpha, be = beta;
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+          if (!valid(j)) continue;
+          const int o = sidx(j);
+          const double z = (w[j] - nn[j]) + be * shZ[o];
+          const double sv = w[j] + be * shS[o];
+          const double p = r[j] + be * shP[o];
+          shZ[o] = z;
+          shS[o] = sv;
+          shP[o] = p;
+          x[j] += al * p;
+          r[j] -= al * sv;
+          w[j] -= al * z;
+        }
+      }
+    }
+    ++it;
+  }
+  if (!x_final && !recover_red()) return;
+#pragma unroll
+  for (int j = 0; j < J; ++j) {
+    if (!valid(j)) continue;
+    if (hb) a.x[(size_t)(2 * j + h) * ld + nbv] = x[j];
+    if (hr) a.x[(size_t)(2 * j + h) * ld + nr] = xr[j];
+  }
+  write_ctrl(a, it, restarts, rr, bb, rel0, status);
+}
+
+// ---------------------------------------------------------------------------------------
 // Mixed precision on the red-black reduced system (resident): FP64 iterative refinement of
 // the full system (true residual r of B~ over every voxel, x += d), each correction d from
 // FP32 pipelined CG on the reduced system of B~ d = r,
@@ -2301,16 +2785,24 @@ int capped_sms(int cap) {
   return (cap > 0 && cap < n) ? cap : n;
 }
 
+}  // namespace
+
+int resident_voxels_per_cta(int N, int sm_cap) {
+  int grid = capped_sms(sm_cap);
+  if ((N + 63) / 64 < grid) grid = (N + 63) / 64;
+  if (grid < 1) grid = 1;
+  return (N + grid - 1) / grid;
+}
+
+namespace {
+
 template <int D>
 cudaError_t launch_resident(const PcgArgs& a, cudaStream_t stream, int* grid_out, bool* launched) {
   *launched = false;
   const int nsm = capped_sms(a.sm_cap);
   // spread the voxels evenly over the SMs: CTA b owns voxels [b per, (b + 1) per)
-  int grid = nsm;
-  if ((a.N + 63) / 64 < grid) grid = (a.N + 63) / 64;
-  if (grid < 1) grid = 1;
-  const int per = (a.N + grid - 1) / grid;
-  grid = (a.N + per - 1) / per;
+  const int per = resident_voxels_per_cta(a.N, a.sm_cap);
+  const int grid = (a.N + per - 1) / per;
   int threads = ((per + 31) / 32) * 32;
   if (threads < 64) threads = 64;
   if (threads > (a.reduced && !a.mixed ? RB_MAX_THREADS : RES_MAX_THREADS)) return cudaSuccess;
@@ -2318,11 +2810,17 @@ cudaError_t launch_resident(const PcgArgs& a, cudaStream_t stream, int* grid_out
   // FP64: blocks + factor in FP64; mixed: FP64 blocks + FP32 blocks + FP32 factor
   // the pipelined reduced solver keeps b^, p, s, z in shared memory: D <= 6
   constexpr bool kPipe = D <= 6;
-  const size_t shm = a.mixed     ? (size_t)ntri(D) * threads * (sizeof(double) + 2 * sizeof(float))
+  // lane pairs (k_pcg_rbp2): one red and one black voxel per pair of lanes; the host sized
+  // the pairs for this voxels-per-CTA count
+  const bool pair = kPipe && a.reduced && !a.mixed && a.lanes != 1 && a.pair_slots > 0 &&
+                    a.pair_per == per && 2 * a.pair_slots <= RB2_MAX_THREADS;
+  if (pair) threads = std::max(64, ((2 * a.pair_slots + 31) / 32) * 32);
+  const size_t shm = a.mixed ? (size_t)ntri(D) * threads * (sizeof(double) + 2 * sizeof(float))
+                     : pair  ? (size_t)(3 * ntri(D) + 4 * D) * a.pair_slots * sizeof(double)
                      : a.reduced ? (size_t)(2 * ntri(D) + (kPipe ? 4 : 1) * D) * threads * sizeof(double)
                                  : (size_t)2 * ntri(D) * threads * sizeof(double);
   const void* kred = nullptr;
-  if constexpr (kPipe) kred = (const void*)k_pcg_rbp<D>;
+  if constexpr (kPipe) kred = pair ? (const void*)k_pcg_rbp2<D> : (const void*)k_pcg_rbp<D>;
   else kred = (const void*)k_pcg_rb<D>;
   const void* kern = a.mixed ? (a.reduced ? (const void*)k_pcg_mixed_rbp<D> : (const void*)k_pcg_mixed_res<D>)
                              : (a.reduced ? kred : (const void*)k_pcg_res<D>);

@@ -76,7 +76,15 @@ struct PcgArgs {
   // variants run that SSOR form instead (ssor = 1, omega = 1 must be set alongside)
   int reduced;
   double cw[3];          // edge weights of the x, y, z directions (1, 1, 1: UGL prior)
+  int lanes;             // FP64 resident reduced solver (D <= 6): 1 = one lane per voxel
+                         // (k_pcg_rbp), otherwise lane pairs (k_pcg_rbp2) when pair_slots is set
+  int pair_per;          // the voxels per CTA that pair_slots was computed for
+  int pair_slots;        // lane pairs per CTA: the most red, or black, voxels of any CTA
 };
+
+// Voxels per CTA of the resident solvers for N voxels on at most sm_cap SMs (0 = all): the
+// grid spreads the voxels evenly, CTA b owning voxels [b per, (b + 1) per).
+int resident_voxels_per_cta(int N, int sm_cap);
 
 // Launches the cooperative persistent PCG kernel for dimension D (1..12) on `stream`.
 // grid_out (may be null) receives the grid size used.

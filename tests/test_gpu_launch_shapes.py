@@ -91,6 +91,30 @@ def test_reduced_solver_draws_at_full_cta_shape(case6, sm, precision, delta, tol
     m.close()
 
 
+@pytest.mark.parametrize("lanes", [1, 2])
+def test_one_lane_and_lane_pairs_at_full_cta_shape(case6, lanes):
+    """The resident FP64 reduced solver with one lane per voxel (k_pcg_rbp) and with lane
+    pairs (k_pcg_rbp2: one red and one black voxel per pair of lanes, each lane half of each
+    voxel's components) at the headline CTA shape: W (D = 6) and A (D = 3, an odd D, where the
+    second lane of a pair holds one component) against the oracle, and the same iteration
+    count both ways."""
+    from paper_1606_00980_gb300 import bfmri
+    lat, s, W_ref = case6
+    m = make(W6, s, precond=bfmri.PRECOND_RB_REDUCED, sm_budget=8, pcg_lanes=lanes)
+    W, info = m.sample_W(counter=3)
+    assert info.rel_residual <= 1e-12
+    assert rel(W, W_ref) <= 1e-8
+    A, ia = m.sample_A(counter=4)
+    A_ref = gibbs.sample_A(lat, W6.Y, W6.X, dict(s, W=W), SEED, 4, spatial=True)
+    assert ia.rel_residual <= 1e-12
+    assert rel(A, A_ref) <= 1e-8
+    m.close()
+    other = make(W6, s, precond=bfmri.PRECOND_RB_REDUCED, sm_budget=8, pcg_lanes=3 - lanes)
+    _, info2 = other.sample_W(counter=3)
+    other.close()
+    assert abs(info2.iterations - info.iterations) <= 1
+
+
 @pytest.mark.parametrize("precond", ["bj", "ssor"])
 def test_block_jacobi_and_ssor_at_full_cta_shape(case6, precond):
     """The resident block-Jacobi and SSOR solver (k_pcg_res) with 352-thread CTAs."""

@@ -277,15 +277,15 @@ def test_sweeps_are_bitwise_reproducible():
         assert np.array_equal(outs[0][k], outs[1][k])
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_reduced_red_black_solver_matches_exact_solve(case, precision):
+@pytest.mark.parametrize("precision,lanes", [("fp64", 2), ("fp64", 1), ("mixed", 0)])
+def test_reduced_red_black_solver_matches_exact_solve(case, precision, lanes):
     """PRECOND_RB_REDUCED on every parity workload (isolated voxels, holes, 2D slices, P = 0,
-    K = 10): the pipelined reduced-system solvers where they apply (resident, D <= 6), the
-    unpipelined ones for larger blocks, SSOR (omega = 1) in the streaming fallback; W and A
-    draws reach the oracle's exact solve."""
+    K = 10): the pipelined reduced-system solvers where they apply (resident, D <= 6; FP64
+    with lane pairs or one lane per voxel), the unpipelined ones for larger blocks, SSOR
+    (omega = 1) in the streaming fallback; W and A draws reach the oracle's exact solve."""
     from paper_1606_00980_gb300 import bfmri
     w, lat, st, s = case
-    m = make(w, s, precond=bfmri.PRECOND_RB_REDUCED,
+    m = make(w, s, precond=bfmri.PRECOND_RB_REDUCED, pcg_lanes=lanes,
              precision=bfmri.PREC_FP64 if precision == "fp64" else bfmri.PREC_MIXED)
     W, info = m.sample_W(counter=3)
     Bd, bw = model.w_blocks_direct(w.Y, w.X, s["A"], s["lam"], w.eps)
