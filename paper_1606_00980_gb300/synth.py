@@ -279,9 +279,17 @@ def periodic_ugl_field(shape_zyx, prec, rng):
     return np.real(np.fft.ifftn(np.fft.fftn(white) * filt))
 
 
-def paper_simulation(N=1000, seed=11, T=351):
+def paper_simulation(N=1000, seed=11, T=351, prior_rows=None):
     """The paper's simulated dataset of N voxels (1e3, 1e4 or 1e5): a centred box of the
-    53 x 63 x 46 block, analysed on that block's lattice."""
+    53 x 63 x 46 block, analysed on that block's lattice.
+
+    The four task rows of W (alpha = 1e-4, 5e-4, 2e-3, 1e-2) and the AR row (beta = 10) are
+    fields on the whole block drawn from the UGL prior. prior_rows, if given, is a callable
+    (block_xyz, alphas, beta, seed) -> (W_rows [4][nx*ny*nz], A_row [nx*ny*nz]) in raster
+    order that draws them (the benchmark passes the library's PCG from a zero start with no
+    data term, as the paper's simulation does); without it they are periodic spectral draws
+    (periodic_ugl_field), which need no solver. The AR row is clipped to [-0.9, 0.9] so that
+    every voxel's AR(1) noise is stationary."""
     if N not in PAPER_SIM_BOXES:
         raise ValueError(f"N must be one of {sorted(PAPER_SIM_BOXES)}")
     rng = np.random.default_rng(seed)
@@ -294,10 +302,17 @@ def paper_simulation(N=1000, seed=11, T=351):
     K, P = 5, 1
     X = make_design(T, K - 1, rng)
     W = np.zeros((K, N))
-    for k, a in enumerate(PAPER_SIM_ALPHA):
-        W[k] = periodic_ugl_field((nz, ny, nx), a, rng).reshape(-1)[inside]
+    if prior_rows is None:
+        for k, a in enumerate(PAPER_SIM_ALPHA):
+            W[k] = periodic_ugl_field((nz, ny, nx), a, rng).reshape(-1)[inside]
+        a_row = periodic_ugl_field((nz, ny, nx), 10.0, rng).reshape(-1)
+    else:
+        w_rows, a_row = prior_rows((nx, ny, nz), PAPER_SIM_ALPHA, 10.0, seed)
+        for k in range(len(PAPER_SIM_ALPHA)):
+            W[k] = np.asarray(w_rows[k]).reshape(-1)[inside]
+        a_row = np.asarray(a_row).reshape(-1)
     W[K - 1] = rng.normal(900.0, 130.0, N)
-    A = np.clip(periodic_ugl_field((nz, ny, nx), 10.0, rng).reshape(-1)[inside], -0.9, 0.9)[None, :]
+    A = np.clip(a_row[inside], -0.9, 0.9)[None, :]
     lam = np.full(N, 0.01)
     E = simulate_ar_noise(A, lam, T, rng)
     Y = X @ W + E
@@ -305,4 +320,5 @@ def paper_simulation(N=1000, seed=11, T=351):
     return Workload(name=f"paper_sim_N{N}_K5_P1_T{T}", dims=(nx, ny, nz), neighbourhood=6,
                     mask=mask, X=X, Y=np.ascontiguousarray(Y), P=P, W_true=W, A_true=A,
                     lambda_true=lam, eps=0.0, delta=1e-8,
-                    meta={"seed": seed, "N": N, "box": (bx, by, bz), "block": (nx, ny, nz)})
+                    meta={"seed": seed, "N": N, "box": (bx, by, bz), "block": (nx, ny, nz),
+                          "prior_rows": "spectral" if prior_rows is None else "caller"})
