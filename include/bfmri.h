@@ -298,15 +298,37 @@ bfmri_status bfmri_synchronize(bfmri_handle* h, bfmri_sweep_info* info);
  * AR prior. Chain c's draws follow the same equations, random numbers and stop rule
  * (relative residual <= delta, confirmed by the true residual) as bfmri_gibbs_sweep on
  * hs[c]; they agree with it to the solver tolerance, not bitwise.
- * Requirements: 1 <= n <= 64; all handles on one lattice and mask, with equal K, P, AR
- * prior, delta, max_iter and preconditioner (and ssor_omega under SSOR), FP64 precision,
- * statistics precomputed, on the current device.
+ * The chains may be different subjects on different lattices and masks (uneven masks): every
+ * right-hand side of the launch then carries its own lattice, and the launch's work units
+ * are shared out in proportion to the chains' voxels.
+ * Requirements: 1 <= n <= 64; equal K, P, AR prior, delta, max_iter and preconditioner (and
+ * ssor_omega under SSOR), FP64 precision, statistics precomputed, on the current device.
  * All work runs on hs[0]'s stream; the call returns when it has finished.
  * info: [n] per-chain results (may be NULL). hs and info are host arrays the caller owns.
  * Errors: INVALID_ARG (mismatched or bad handles), STATE, NOT_SPD, NOT_CONVERGED, TIMEOUT,
  * CUDA; on error the states of all n chains are unspecified. */
 bfmri_status bfmri_gibbs_sweep_group(bfmri_handle* const* hs, int n, int n_sweeps,
                                      uint64_t first_counter, bfmri_sweep_info* info);
+
+/* One Gibbs sweep of the chains hs[0..n-1] (as bfmri_gibbs_sweep_group with n_sweeps = 1,
+ * draw counter `counter`) whose W step solves, in the same cooperative launch as the n
+ * chains' W systems (one matrix per chain), n_probes log-determinant probes of the W
+ * precision B~ of probe_handle at its current state (one matrix, n_probes right-hand sides;
+ * as bfmri_logdet_probe with which = 0, probe draws from probe_counter, lanczos_steps CG
+ * coefficients recorded per probe). probe_handle may be one of the chains (then the probes
+ * see the system of that chain's W draw in this sweep) or another handle with the chains' K
+ * (FP64), on any lattice. The Lanczos quadrature needs plain block-Jacobi PCG, so this launch
+ * solves every right-hand side with block-Jacobi, whatever the chains' preconditioner; the
+ * chains' A systems use their own. Outputs as bfmri_logdet_probe: logdet, std_err (may be
+ * NULL), per_probe [n_probes] (may be NULL); info [n] per chain (may be NULL).
+ * Requirements: those of bfmri_gibbs_sweep_group; 1 <= n_probes <= 127; with different
+ * lattices among the chains and probe_handle, n + n_probes <= 128.
+ * Errors: those of bfmri_gibbs_sweep_group and bfmri_logdet_probe. */
+bfmri_status bfmri_gibbs_sweep_group_probes(bfmri_handle* const* hs, int n, uint64_t counter,
+                                            bfmri_handle* probe_handle, int n_probes,
+                                            int lanczos_steps, uint64_t probe_counter,
+                                            double* logdet, double* std_err, double* per_probe,
+                                            bfmri_sweep_info* info);
 
 /* Log-determinant and trace probes of the W (which = 0) or A (which = 1) full-conditional
  * precision B~ at the current state. The paper leaves the log-determinant to future work

@@ -121,6 +121,8 @@ SIGNATURES = [
     ("bfmri_sample_beta", C.c_int, [_h, C.c_uint64, _dp]),
     ("bfmri_gibbs_sweep", C.c_int, [_h, C.c_int, C.c_uint64, _P(bfmri_sweep_info)]),
     ("bfmri_gibbs_sweep_group", C.c_int, [_P(_h), C.c_int, C.c_int, C.c_uint64, _P(bfmri_sweep_info)]),
+    ("bfmri_gibbs_sweep_group_probes", C.c_int, [_P(_h), C.c_int, C.c_uint64, _h, C.c_int, C.c_int,
+                                                 C.c_uint64, _dp, _dp, _dp, _P(bfmri_sweep_info)]),
     ("bfmri_synchronize", C.c_int, [_h, _P(bfmri_sweep_info)]),
     ("bfmri_summary_begin", C.c_int, [_h, C.c_int, _P(C.c_double), _P(C.c_double), _P(C.c_int), C.c_int]),
     ("bfmri_summary_add", C.c_int, [_h]),
@@ -373,8 +375,8 @@ def unpack_cov(packed, K):
 
 
 def gibbs_sweep_group(models, n_sweeps, first_counter=0):
-    """Advances the chains of `models` (Model objects on one lattice and mask) together by
-    n_sweeps Gibbs sweeps, their W and A systems solved as one multi-RHS launch per step
+    """Advances the chains of `models` (Model objects, on one lattice or on several) together
+    by n_sweeps Gibbs sweeps, their W and A systems solved as one multi-RHS launch per step
     (bfmri_gibbs_sweep_group); returns one bfmri_sweep_info per chain."""
     lib = load_library()
     n = len(models)
@@ -384,6 +386,26 @@ def gibbs_sweep_group(models, n_sweeps, first_counter=0):
     if st != BFMRI_OK:
         _check(st, models[0].handle)
     return list(infos)
+
+
+def gibbs_sweep_group_probes(models, counter, probe_model, n_probes, lanczos_steps,
+                             probe_counter=0):
+    """One sweep of the chains of `models` (which may be subjects on different lattices)
+    whose W systems share one multi-RHS launch with n_probes log-det probes of probe_model's
+    W system (bfmri_gibbs_sweep_group_probes); returns (infos, logdet, std_err, per_probe)."""
+    import numpy as np
+    lib = load_library()
+    n = len(models)
+    hs = (_h * n)(*[m.handle for m in models])
+    infos = (bfmri_sweep_info * n)()
+    ld, se = C.c_double(), C.c_double()
+    per = np.empty(n_probes)
+    st = lib.bfmri_gibbs_sweep_group_probes(hs, n, counter, probe_model.handle, n_probes,
+                                            lanczos_steps, probe_counter, C.byref(ld),
+                                            C.byref(se), _ptr(per), infos)
+    if st != BFMRI_OK:
+        _check(st, models[0].handle)
+    return list(infos), ld.value, se.value, per
 
 
 def lanczos_log_quadrature(cg_alpha, cg_beta):

@@ -233,6 +233,7 @@ struct bfmri_handle {
   std::vector<int> lin_host;    // lattice-linear index of every voxel (multigrid hierarchy)
   std::vector<unsigned char> colour_host;   // 0 red, 1 black per voxel
   std::map<int, int> pair_slots;            // voxels per CTA -> lane pairs of k_pcg_rbp2
+  double* d_ldm = nullptr;                  // log det M of a probe set riding with a group sweep
   // multigrid hierarchy (BFMRI_PRECOND_MULTIGRID), built on the first multigrid solve:
   // levels 1..mg_L-1 plus level 0's slot weights and aggregate map
   int mg_L = 0;
@@ -866,17 +867,20 @@ bfmri_status resolve_timing(bfmri_handle* h) {
 }
 
 // Multi-RHS buffers for S right-hand sides of dimension D and hist_len recorded iterations.
-bfmri_status ensure_mrhs(bfmri_handle* h, int D, int S, int hist_len) {
-  const size_t vs = (size_t)D * h->ld;
+bfmri_status ensure_mrhs(bfmri_handle* h, int D, int S, int hist_len, size_t ld_max = 0, int N_max = 0) {
+  // a group of chains on different lattices sizes the workspace for the largest of them
+  const size_t ldw = std::max(h->ld, ld_max);
+  const int Nw = std::max(h->N, N_max);
+  const size_t vs = (size_t)D * ldw;
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   // rows of the partial buffer: one per (RHS, chunk) unit, never more than max(warps, S);
   // right-hand-side tiles of up to 4 multiply the rows per warp by the tile
   const int units = std::max(std::max(nsm, 1) * 64 * 4, S);
-  const size_t out_len = std::max((size_t)h->ld, (size_t)((h->N + 127) / 128 + 1) * S * D);
+  const size_t out_len = std::max(ldw, (size_t)((Nw + 127) / 128 + 1) * S * D);
   if (S <= h->mr_S && D <= h->mr_D && hist_len <= h->mr_hist_len && units <= h->mr_units &&
-      out_len <= h->mr_out_len)
+      out_len <= h->mr_out_len && vs <= h->mr_vs)
     return BFMRI_OK;
   double** vecs[] = {&h->mr_b, &h->mr_x, &h->mr_r, &h->mr_u, &h->mr_w, &h->mr_p, &h->mr_s};
   for (double** v : vecs) {
@@ -889,6 +893,7 @@ bfmri_status ensure_mrhs(bfmri_handle* h, int D, int S, int hist_len) {
   dfree(h, h->mr_st);
   dfree(h, h->mr_flags);
   h->mr_S = h->mr_D = h->mr_hist_len = h->mr_units = 0;
+  h->mr_vs = 0;
   for (double** v : vecs) {
     *v = (double*)dalloc(h, (size_t)S * vs * sizeof(double));
     if (!*v) return fail(h, BFMRI_ERR_OOM, "multi-RHS workspace allocation failed");
@@ -1566,8 +1571,47 @@ bfmri_status bfmri_synchronize(bfmri_handle* h, bfmri_sweep_info* info) {
   return st;
 }
 
-bfmri_status bfmri_gibbs_sweep_group(bfmri_handle* const* hs, int n, int n_sweeps,
-                                     uint64_t first_counter, bfmri_sweep_info* info) {
+namespace {
+
+// Table entry of one right-hand side of a grouped launch, with handle h's lattice.
+MrhsRhsPtrs rhs_entry(const bfmri_handle* h, const void* blocks, const void* mfac,
+                      const double* scale, const void* b, void* x) {
+  MrhsRhsPtrs t{};
+  t.blocks = blocks;
+  t.mfac = mfac;
+  t.scale = scale;
+  t.b = b;
+  t.x = x;
+  t.N = h->N;
+  t.ndir = h->ndir;
+  t.ld = h->ld;
+  t.nbr = h->d_nbr;
+  t.red = h->d_red;
+  t.black = h->d_black;
+  t.n_red = h->n_red;
+  t.n_black = h->n_black;
+  for (int d = 0; d < 3; ++d) t.cw[d] = h->opt.edge_weight[d];
+  return t;
+}
+
+bool same_lattice(const bfmri_handle* a, const bfmri_handle* b) {
+  return a->nx == b->nx && a->ny == b->ny && a->nz == b->nz && a->ndir == b->ndir && a->N == b->N &&
+         a->ld == b->ld && a->mask_hash == b->mask_hash;
+}
+
+// Log-det probes of one handle's W system that ride along with the W launch of a group sweep.
+struct GroupProbes {
+  bfmri_handle* ph;
+  int n;          // probes
+  int steps;      // Lanczos steps recorded per probe
+  uint64_t counter;
+  double* logdet;
+  double* std_err;
+  double* per_probe;
+};
+
+bfmri_status group_sweep(bfmri_handle* const* hs, int n, int n_sweeps, uint64_t first_counter,
+                         bfmri_sweep_info* info, const GroupProbes* gp) {
   if (!hs || n < 1 || n > 64 || n_sweeps < 0) {
     set_global_error("bfmri_gibbs_sweep_group: need 1 <= n <= 64 handles and n_sweeps >= 0");
     return BFMRI_ERR_INVALID_ARG;
@@ -1581,12 +1625,15 @@ bfmri_status bfmri_gibbs_sweep_group(bfmri_handle* const* hs, int n, int n_sweep
       if (hs[d] == hs[c]) return fail(hs[0], BFMRI_ERR_INVALID_ARG, "a handle appears twice in the group");
   }
   bfmri_handle* h0 = hs[0];
+  bool uneven = false;
+  size_t ld_max = 0;
+  int N_max = 0;
   for (int c = 0; c < n; ++c) {
     RET(require_stats(hs[c]));
     const bfmri_handle* h = hs[c];
-    if (h->nx != h0->nx || h->ny != h0->ny || h->nz != h0->nz || h->ndir != h0->ndir ||
-        h->N != h0->N || h->ld != h0->ld || h->mask_hash != h0->mask_hash)
-      return fail(h0, BFMRI_ERR_INVALID_ARG, "grouped chains must share one lattice and mask");
+    if (!same_lattice(h, h0)) uneven = true;
+    ld_max = std::max(ld_max, h->ld);
+    N_max = std::max(N_max, h->N);
     if (h->K != h0->K || h->P != h0->P || h->opt.ar_prior != h0->opt.ar_prior ||
         h->opt.delta != h0->opt.delta || h->opt.max_iter != h0->opt.max_iter ||
         h->opt.precond != h0->opt.precond ||
@@ -1596,43 +1643,108 @@ bfmri_status bfmri_gibbs_sweep_group(bfmri_handle* const* hs, int n, int n_sweep
     if (h->opt.precision != BFMRI_PREC_FP64)
       return fail(h0, BFMRI_ERR_INVALID_ARG, "grouped chains solve in FP64 precision only");
   }
+  const int np = gp ? gp->n : 0;
+  bool ph_in_group = false;
+  if (gp) {
+    bfmri_handle* ph = gp->ph;
+    if (!ph || np < 1 || gp->steps < 1 || n_sweeps != 1)
+      return fail(h0, BFMRI_ERR_INVALID_ARG, "probes ride along with exactly one sweep: need a handle, n_probes >= 1, lanczos_steps >= 1");
+    RET(require_stats(ph));
+    if (ph->K != h0->K || ph->opt.precision != BFMRI_PREC_FP64)
+      return fail(h0, BFMRI_ERR_INVALID_ARG, "the probe handle must have the chains' K and FP64 precision");
+    for (int c = 0; c < n; ++c) ph_in_group = ph_in_group || hs[c] == ph;
+    if (!same_lattice(ph, h0)) uneven = true;
+    ld_max = std::max(ld_max, ph->ld);
+    N_max = std::max(N_max, ph->N);
+  }
+  const int Sw = n + np;   // right-hand sides of the W launch that carries the probes
+  if (uneven && Sw > MRHS_UNEVEN_MAX_S)
+    return fail(h0, BFMRI_ERR_INVALID_ARG, "at most 128 right-hand sides in one launch over different lattices");
   if (info)
     for (int c = 0; c < n; ++c) info[c] = bfmri_sweep_info{};
   if (n_sweeps == 0) return BFMRI_OK;
   const int K = h0->K, P = h0->P;
   const bool spatial_A = P > 0 && h0->opt.ar_prior == BFMRI_AR_SPATIAL;
-  RET(ensure_mrhs(h0, std::max(K, P), n, 0));
-  if (h0->g_cap < n) {
+  RET(ensure_mrhs(h0, std::max(K, P), Sw, gp ? gp->steps : 0, ld_max, N_max));
+  const int tab_len = Sw + n;   // W launch (chains, then probes), A launch
+  if (gp && !h0->d_ldm) {
+    h0->d_ldm = (double*)dalloc(h0, sizeof(double));
+    if (!h0->d_ldm) return fail(h0, BFMRI_ERR_OOM, "probe scratch allocation failed");
+  }
+  if (h0->g_cap < tab_len) {
     dfree(h0, h0->d_gtab);
     dfree(h0, h0->d_gtally);
     h0->g_cap = 0;
-    h0->d_gtab = (MrhsRhsPtrs*)dalloc(h0, 2 * (size_t)n * sizeof(MrhsRhsPtrs));
-    h0->d_gtally = (MrhsTally*)dalloc(h0, 2 * (size_t)n * sizeof(MrhsTally));
+    h0->d_gtab = (MrhsRhsPtrs*)dalloc(h0, (size_t)tab_len * sizeof(MrhsRhsPtrs));
+    h0->d_gtally = (MrhsTally*)dalloc(h0, (size_t)tab_len * sizeof(MrhsTally));
     if (!h0->d_gtab || !h0->d_gtally) return fail(h0, BFMRI_ERR_OOM, "group table allocation failed");
-    h0->g_cap = n;
+    h0->g_cap = tab_len;
   }
   // voxel blocks and their factors (block-Jacobi, and SSOR's block diagonal)
   const bool pre = h0->opt.precond != BFMRI_PRECOND_NONE;
-  std::vector<MrhsRhsPtrs> tab(2 * (size_t)n);
+  const size_t vs = h0->mr_vs;
+  std::vector<MrhsRhsPtrs> tab((size_t)tab_len);
   for (int c = 0; c < n; ++c) {
     bfmri_handle* h = hs[c];
-    tab[c] = MrhsRhsPtrs{h->d_blocks, pre ? h->d_mfac : nullptr, h->d_alpha, h->d_rhs, h->d_W};
-    tab[n + c] = MrhsRhsPtrs{h->d_blocks, pre ? h->d_mfac : nullptr, h->d_beta, h->d_rhs, h->d_A};
+    tab[c] = rhs_entry(h, h->d_blocks, pre ? h->d_mfac : nullptr, h->d_alpha, h->d_rhs, h->d_W);
+    tab[Sw + c] = rhs_entry(h, h->d_blocks, pre ? h->d_mfac : nullptr, h->d_beta, h->d_rhs, h->d_A);
+  }
+  if (gp) {
+    // probe i: b_i = L v_i with v_i Rademacher (k_probe_rhs) and x_i = 0 in the workspace,
+    // preconditioned by the probe handle's block-Jacobi factor, on which log det M is built
+    bfmri_handle* ph = gp->ph;
+    const bool ppre = ph->opt.precond != BFMRI_PRECOND_NONE;
+    for (int i = 0; i < np; ++i)
+      tab[n + i] = rhs_entry(ph, ph->d_blocks, ppre ? ph->d_mfac : nullptr, ph->d_alpha,
+                             h0->mr_b + (size_t)(n + i) * vs, h0->mr_x + (size_t)(n + i) * vs);
   }
   cudaStream_t st0 = h0->stream;
   CU(h0, cudaMemcpyAsync(h0->d_gtab, tab.data(), tab.size() * sizeof(MrhsRhsPtrs), cudaMemcpyHostToDevice, st0));
-  CU(h0, cudaMemsetAsync(h0->d_gtally, 0, 2 * (size_t)n * sizeof(MrhsTally), st0));
-  // every chain's work goes to the first handle's stream for the duration of the call
-  std::vector<cudaStream_t> saved((size_t)n);
-  for (int c = 0; c < n; ++c) {
-    saved[c] = hs[c]->stream;
-    hs[c]->stream = st0;
+  CU(h0, cudaMemsetAsync(h0->d_gtally, 0, (size_t)tab_len * sizeof(MrhsTally), st0));
+  // every chain's work (and the probe handle's) goes to the first handle's stream for the
+  // duration of the call
+  std::vector<bfmri_handle*> all(hs, hs + n);
+  if (gp && !ph_in_group) all.push_back(gp->ph);
+  std::vector<cudaStream_t> saved(all.size());
+  for (size_t c = 0; c < all.size(); ++c) {
+    saved[c] = all[c]->stream;
+    all[c]->stream = st0;
   }
-  auto solve = [&](int D, int which) -> bfmri_status {
-    MrhsArgs m = mrhs_args(h0, D, n, nullptr, h0->opt.max_iter, false);
+  ProbeArgs pa{};
+  if (gp) {
+    bfmri_handle* ph = gp->ph;
+    pa.N = ph->N;
+    pa.ld = ph->ld;
+    pa.ndir = ph->ndir;
+    pa.f32 = 0;
+    pa.nbr = ph->d_nbr;
+    pa.lin = ph->d_lin;
+    pa.mfac = nullptr;
+    pa.mfac64 = ph->opt.precond != BFMRI_PRECOND_NONE ? ph->d_mfac : nullptr;
+    pa.S = np;
+    pa.vs = vs;
+    pa.b = h0->mr_b + (size_t)n * vs;
+    pa.x = h0->mr_x + (size_t)n * vs;
+    pa.rng = rng_of(ph, gp->counter, TAG_PROBE);
+    for (int d = 0; d < 3; ++d) pa.cw[d] = ph->opt.edge_weight[d];
+    pa.tile = 1;
+  }
+  auto solve = [&](int D, int which, bool probes) -> bfmri_status {
+    const int S = probes ? Sw : n;
+    MrhsArgs m = mrhs_args(h0, D, S, nullptr, h0->opt.max_iter, false);
     mrhs_ssor(h0, m);
-    m.tab = h0->d_gtab + (size_t)which * n;
-    m.tally = h0->d_gtally + (size_t)which * n;
+    if (probes) {
+      // the probes' Lanczos quadrature needs plain block-Jacobi PCG: the whole launch uses it
+      m.ssor = 0;
+      m.reduced = 0;
+      m.hist = h0->mr_hist;
+      m.hist_len = gp->steps;
+      m.max_iter = std::max(h0->opt.max_iter, gp->steps);
+    }
+    m.N = N_max;
+    m.uneven = uneven ? 1 : 0;
+    m.tab = h0->d_gtab + (which == 0 ? 0 : (size_t)Sw);
+    m.tally = h0->d_gtally + (which == 0 ? 0 : (size_t)Sw);
     m.blocks = nullptr;
     m.mfac = nullptr;
     m.b = nullptr;
@@ -1643,13 +1755,37 @@ bfmri_status bfmri_gibbs_sweep_group(bfmri_handle* const* hs, int n, int n_sweep
     return BFMRI_OK;
   };
   bfmri_status st = BFMRI_OK;
-  for (int c = 0; c < n && st == BFMRI_OK; ++c) st = begin_call(hs[c]);
+  for (size_t c = 0; c < all.size() && st == BFMRI_OK; ++c) st = begin_call(all[c]);
   for (int sw = 0; sw < n_sweeps && st == BFMRI_OK; ++sw) {
     const uint64_t cnt = first_counter + (uint64_t)sw;
     for (int c = 0; c < n && st == BFMRI_OK; ++c) st = assemble_W(hs[c], cnt);
-    if (st == BFMRI_OK) st = solve(K, 0);
+    const bool probes = gp != nullptr && sw == 0;
+    if (probes && st == BFMRI_OK) {
+      bfmri_handle* ph = gp->ph;
+      if (!ph_in_group) {
+        // the probe handle's W system at its current state, without perturbation
+        AssembleArgs aa = assemble_args(ph, ph->d_alpha, 0, TAG_W);
+        aa.perturb = 0;
+        aa.blocks32 = nullptr;
+        aa.mfac32 = nullptr;
+        const cudaError_t e = launch_assemble_w(aa, st0);
+        if (e != cudaSuccess) st = cuda_fail(h0, e, "assemble (probes)");
+      }
+      if (st == BFMRI_OK) {
+        const cudaError_t e = launch_probe(K, pa, 0, nullptr, st0);
+        if (e != cudaSuccess) st = cuda_fail(h0, e, "probe right-hand sides");
+      }
+    }
+    if (st == BFMRI_OK) st = solve(K, 0, probes);
+    if (probes && st == BFMRI_OK && pa.mfac64) {
+      // log det M from the probe handle's block-Jacobi factor, before a chain's A step
+      // reuses the factor's storage: per-voxel terms, summed in a fixed order
+      cudaError_t e = launch_probe(K, pa, 1, h0->mr_out, st0);
+      if (e == cudaSuccess) e = launch_sum_columns(h0->mr_out, gp->ph->N, 1, h0->d_ldm, st0);
+      if (e != cudaSuccess) st = cuda_fail(h0, e, "logdet M");
+    }
     for (int c = 0; c < n && st == BFMRI_OK; ++c) st = assemble_A(hs[c], cnt);
-    if (st == BFMRI_OK && spatial_A) st = solve(P, 1);
+    if (st == BFMRI_OK && spatial_A) st = solve(P, 1, false);
     for (int c = 0; c < n && st == BFMRI_OK; ++c) {
       bfmri_handle* h = hs[c];
       st = enqueue_lambda(h, cnt);
@@ -1660,32 +1796,90 @@ bfmri_status bfmri_gibbs_sweep_group(bfmri_handle* const* hs, int n, int n_sweep
   }
   for (int c = 0; c < n; ++c)
     if (hs[c]->sum.open) hs[c]->sum.n += n_sweeps;
-  std::vector<int> exhausted((size_t)n, 0);
-  for (int c = 0; c < n; ++c) {
-    const bfmri_status sc = end_call(hs[c], nullptr, &exhausted[c]);
+  std::vector<int> exhausted(all.size(), 0);
+  for (size_t c = 0; c < all.size(); ++c) {
+    const bfmri_status sc = end_call(all[c], nullptr, &exhausted[c]);
     if (st == BFMRI_OK) st = sc;
   }
-  for (int c = 0; c < n; ++c) hs[c]->stream = saved[c];
+  for (size_t c = 0; c < all.size(); ++c) all[c]->stream = saved[c];
   if (st != BFMRI_OK) return st;
-  std::vector<MrhsTally> tally(2 * (size_t)n);
+  std::vector<MrhsTally> tally((size_t)tab_len);
   CU(h0, cudaMemcpy(tally.data(), h0->d_gtally, tally.size() * sizeof(MrhsTally), cudaMemcpyDeviceToHost));
   for (int c = 0; c < n; ++c) {
     if (info) {
       info[c].sweeps = n_sweeps;
       info[c].pcg_iterations_W = tally[c].iters;
-      info[c].pcg_iterations_A = spatial_A ? tally[n + c].iters : 0;
+      info[c].pcg_iterations_A = spatial_A ? tally[Sw + c].iters : 0;
       info[c].last_rel_residual_W = tally[c].rel_res;
       info[c].gamma_exhausted = exhausted[c];
     }
     for (int w = 0; w < (spatial_A ? 2 : 1); ++w) {
-      const int code = tally[(size_t)w * n + c].status_any;
+      const int code = tally[(size_t)(w ? Sw : 0) + c].status_any;
       const std::string who = "chain " + std::to_string(c) + (w ? " (A)" : " (W)");
       if (code == 4) return fail(h0, BFMRI_ERR_NOT_CONVERGED, "PCG reached max_iter in " + who);
       if (code == 3) return fail(h0, BFMRI_ERR_NOT_SPD, "PCG breakdown (p'Bp <= 0) in " + who);
       if (code == 7) return fail(h0, BFMRI_ERR_INVALID_ARG, "non-finite value in PCG of " + who);
     }
   }
+  if (!gp) return BFMRI_OK;
+  // the probes: states and CG coefficients of right-hand sides n .. n + np - 1
+  bfmri_handle* ph = gp->ph;
+  std::vector<RhsState> pst((size_t)np);
+  CU(h0, cudaMemcpy(pst.data(), h0->mr_st + n, (size_t)np * sizeof(RhsState), cudaMemcpyDeviceToHost));
+  for (int i = 0; i < np; ++i) {
+    if (pst[i].status == 3) return fail(h0, BFMRI_ERR_NOT_SPD, "probe solve breakdown");
+    if (pst[i].status == 7) return fail(h0, BFMRI_ERR_INVALID_ARG, "non-finite value in probe solve");
+    if (pst[i].status == 4) return fail(h0, BFMRI_ERR_NOT_CONVERGED, "probe solve reached max_iter");
+  }
+  std::vector<double> hist((size_t)gp->steps * Sw * 2);
+  CU(h0, cudaMemcpy(hist.data(), h0->mr_hist, hist.size() * sizeof(double), cudaMemcpyDeviceToHost));
+  double ldm = 0.0;
+  if (pa.mfac64) CU(h0, cudaMemcpy(&ldm, h0->d_ldm, sizeof(double), cudaMemcpyDeviceToHost));
+  const double vnorm2 = (double)K * ph->N;
+  std::vector<double> est((size_t)np, 0.0);
+  for (int i = 0; i < np; ++i) {
+    const int mi = std::min(pst[i].iters, gp->steps);
+    if (mi < 1) continue;
+    std::vector<double> al(mi), be(mi);
+    for (int j = 0; j < mi; ++j) {
+      al[j] = hist[((size_t)j * Sw + n + i) * 2 + 0];
+      be[j] = hist[((size_t)j * Sw + n + i) * 2 + 1];
+    }
+    double q = 0.0;
+    const bfmri_status qs = bfmri_lanczos_log_quadrature(mi, al.data(), be.data(), &q);
+    if (qs != BFMRI_OK) return fail(h0, qs, "Lanczos quadrature failed");
+    est[i] = vnorm2 * q;
+  }
+  double mean = 0.0;
+  for (double v : est) mean += v;
+  mean /= np;
+  double var = 0.0;
+  for (double v : est) var += (v - mean) * (v - mean);
+  if (gp->logdet) *gp->logdet = ldm + mean;
+  if (gp->std_err) *gp->std_err = np > 1 ? std::sqrt(var / (np - 1) / np) : 0.0;
+  if (gp->per_probe)
+    for (int i = 0; i < np; ++i) gp->per_probe[i] = est[i];
   return BFMRI_OK;
+}
+
+}  // namespace
+
+bfmri_status bfmri_gibbs_sweep_group(bfmri_handle* const* hs, int n, int n_sweeps,
+                                     uint64_t first_counter, bfmri_sweep_info* info) {
+  return group_sweep(hs, n, n_sweeps, first_counter, info, nullptr);
+}
+
+bfmri_status bfmri_gibbs_sweep_group_probes(bfmri_handle* const* hs, int n, uint64_t counter,
+                                            bfmri_handle* probe_handle, int n_probes,
+                                            int lanczos_steps, uint64_t probe_counter,
+                                            double* logdet, double* std_err, double* per_probe,
+                                            bfmri_sweep_info* info) {
+  if (n_probes < 1 || n_probes > 127) {
+    set_global_error("bfmri_gibbs_sweep_group_probes: need 1 <= n_probes <= 127");
+    return BFMRI_ERR_INVALID_ARG;
+  }
+  GroupProbes gp{probe_handle, n_probes, lanczos_steps, probe_counter, logdet, std_err, per_probe};
+  return group_sweep(hs, n, 1, counter, info, &gp);
 }
 
 namespace {

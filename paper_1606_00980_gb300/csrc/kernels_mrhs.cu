@@ -26,18 +26,137 @@ constexpr int MRHS_THREADS = 256;
 // Neighbour values go through L1: lanes of a warp share the lines of their +-x and +-y
 // neighbours. They were written by other CTAs before the last grid barrier, whose gpu-scope
 // acquire orders these loads after those writes.
+struct Units {
+  int S, chunks, units, csize, gw, nw, lane;
+  const int* first = nullptr;   // uneven masks: right-hand side r owns units first[r] .. first[r + 1] - 1
+};
+
+__device__ __forceinline__ Units units_of(const MrhsArgs& a) {
+  Units u;
+  u.S = a.S;
+  u.nw = (gridDim.x * blockDim.x) >> 5;
+  u.gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  u.lane = threadIdx.x & 31;
+  u.chunks = u.nw / a.S;
+  if (u.chunks < 1) u.chunks = 1;
+  u.units = a.S * u.chunks;
+  int cs = (a.N + u.chunks - 1) / u.chunks;
+  u.csize = ((cs + 31) / 32) * 32;
+  u.first = nullptr;
+  return u;
+}
+
+// Work units: without uneven masks every right-hand side has U.chunks units and unit
+// c S + r is chunk c of right-hand side r; with them right-hand side r has the units
+// first[r] .. first[r + 1] - 1, as many as its share of the voxels. Unit u writes partial
+// row u either way.
+__device__ __forceinline__ int unit_count(const Units& U, int r) {
+  return U.first ? U.first[r + 1] - U.first[r] : U.chunks;
+}
+__device__ __forceinline__ int unit_row(const Units& U, int r, int c) {
+  return U.first ? U.first[r] + c : c * U.S + r;
+}
+__device__ __forceinline__ int unit_rhs_of(const Units& U, int u) {
+  if (!U.first) return u % U.S;
+  int lo = 0, hi = U.S - 1;   // the last r with first[r] <= u
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (U.first[mid] <= u) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+__device__ __forceinline__ int unit_chunk_of(const Units& U, int u) {
+  return U.first ? u - U.first[unit_rhs_of(U, u)] : u / U.S;
+}
+
+// Operator, scales, b and x of right-hand side r, and the lattice it lives on (its own with
+// uneven masks, else the launch's): voxels, plane stride, neighbour planes, colour lists, edge
+// weights, and its voxel chunks (nch chunks of cs voxels).
 template <int D, typename T>
-__device__ __forceinline__ void block_apply(const MrhsArgs& a, const T* B, const T* sc, int n, const T* v,
-                                            const T* V, T* out) {
-  const size_t ld = a.ld;
+struct RhsOp {
+  const T* B;
+  const T* M;
+  const T* b;
+  T* x;
+  T sc[D];
+  int N, ndir, n_red, n_black, nch, cs;
+  size_t ld;
+  const int* nbr;
+  const int* red;
+  const int* black;
+  T cw[3];
+};
+
+template <int D, typename T>
+__device__ __forceinline__ RhsOp<D, T> rhs_op(const MrhsArgs& a, const Units& U, int r) {
+  RhsOp<D, T> o;
+  const double* scale;
+  if (a.tab != nullptr) {
+    const MrhsRhsPtrs& t = a.tab[r];
+    o.B = static_cast<const T*>(t.blocks);
+    o.M = static_cast<const T*>(t.mfac);
+    o.b = static_cast<const T*>(t.b);
+    o.x = static_cast<T*>(t.x);
+    scale = t.scale;
+  } else {
+    o.B = static_cast<const T*>(a.blocks);
+    o.M = static_cast<const T*>(a.mfac);
+    o.b = static_cast<const T*>(a.b) + (size_t)r * a.vs;
+    o.x = static_cast<T*>(a.x) + (size_t)r * a.vs;
+    scale = a.scale;
+  }
+#pragma unroll
+  for (int k = 0; k < D; ++k) o.sc[k] = (T)__ldg(scale + k);
+  if (a.uneven) {
+    const MrhsRhsPtrs& t = a.tab[r];
+    o.N = t.N;
+    o.ndir = t.ndir;
+    o.ld = t.ld;
+    o.nbr = t.nbr;
+    o.red = t.red;
+    o.black = t.black;
+    o.n_red = t.n_red;
+    o.n_black = t.n_black;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) o.cw[d] = (T)t.cw[d];
+  } else {
+    o.N = a.N;
+    o.ndir = a.ndir;
+    o.ld = a.ld;
+    o.nbr = a.nbr;
+    o.red = a.red;
+    o.black = a.black;
+    o.n_red = a.n_red;
+    o.n_black = a.n_black;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) o.cw[d] = (T)a.cw[d];
+  }
+  o.nch = unit_count(U, r);
+  const int cs = (o.N + o.nch - 1) / o.nch;
+  o.cs = ((cs + 31) / 32) * 32;
+  return o;
+}
+
+// out = B v + s .* (deg v - sum of the neighbours' V), for voxel n of right-hand side op.
+// All neighbour indices are loaded first and then all neighbour values, so that one group of
+// loads is in flight instead of a chain of dependent index -> value round trips (an absent
+// neighbour reads the voxel's own value, which is masked out). FP64 solves take the six
+// directions in two halves to bound the registers held.
+// Neighbour values go through L1: lanes of a warp share the lines of their +-x and +-y
+// neighbours. They were written by other CTAs before the last grid barrier, whose gpu-scope
+// acquire orders these loads after those writes.
+template <int D, typename T>
+__device__ __forceinline__ void block_apply(const RhsOp<D, T>& op, int n, const T* v, const T* V, T* out) {
+  const size_t ld = op.ld;
   int nb[6];
 #pragma unroll
-  for (int d = 0; d < 6; ++d) nb[d] = d < a.ndir ? __ldg(a.nbr + (size_t)d * ld + n) : -1;
+  for (int d = 0; d < 6; ++d) nb[d] = d < op.ndir ? __ldg(op.nbr + (size_t)d * ld + n) : -1;
 #pragma unroll
   for (int i = 0; i < D; ++i) {
     T acc = T(0);
 #pragma unroll
-    for (int j = 0; j < D; ++j) acc += __ldg(B + (size_t)(i >= j ? tri(i, j) : tri(j, i)) * ld + n) * v[j];
+    for (int j = 0; j < D; ++j) acc += __ldg(op.B + (size_t)(i >= j ? tri(i, j) : tri(j, i)) * ld + n) * v[j];
     out[i] = acc;
   }
   T sum[D];
@@ -57,7 +176,7 @@ __device__ __forceinline__ void block_apply(const MrhsArgs& a, const T* B, const
 #pragma unroll
     for (int h = 0; h < H; ++h) {
       if (nb[d0 + h] >= 0) {
-        const T c = (T)a.cw[(d0 + h) >> 1];   // edge weight of the slot's direction
+        const T c = op.cw[(d0 + h) >> 1];   // edge weight of the slot's direction
         deg += c;
 #pragma unroll
         for (int k = 0; k < D; ++k) sum[k] += c * nv[h][k];
@@ -65,7 +184,7 @@ __device__ __forceinline__ void block_apply(const MrhsArgs& a, const T* B, const
     }
   }
 #pragma unroll
-  for (int k = 0; k < D; ++k) out[k] += sc[k] * (deg * v[k] - sum[k]);
+  for (int k = 0; k < D; ++k) out[k] += op.sc[k] * (deg * v[k] - sum[k]);
 }
 
 // Compensated (Kahan) accumulation in the storage type: per-thread partial sums stay
@@ -92,67 +211,16 @@ struct KSum<double> {
 };
 
 template <int D, typename T>
-__device__ __forceinline__ void precond_apply(const MrhsArgs& a, const T* M, int n, const T* r, T* z) {
-  if (M == nullptr) {
+__device__ __forceinline__ void precond_apply(const RhsOp<D, T>& op, int n, const T* r, T* z) {
+  if (op.M == nullptr) {
 #pragma unroll
     for (int k = 0; k < D; ++k) z[k] = r[k];
     return;
   }
   T L[ntri(D)];
 #pragma unroll
-  for (int e = 0; e < ntri(D); ++e) L[e] = __ldg(M + (size_t)e * a.ld + n);
+  for (int e = 0; e < ntri(D); ++e) L[e] = __ldg(op.M + (size_t)e * op.ld + n);
   chol_solve_invdiag<D>(L, r, z);
-}
-
-// Operator, scales, b and x of right-hand side r.
-template <int D, typename T>
-struct RhsOp {
-  const T* B;
-  const T* M;
-  const T* b;
-  T* x;
-  T sc[D];
-};
-
-template <int D, typename T>
-__device__ __forceinline__ RhsOp<D, T> rhs_op(const MrhsArgs& a, int r) {
-  RhsOp<D, T> o;
-  const double* scale;
-  if (a.tab != nullptr) {
-    const MrhsRhsPtrs t = a.tab[r];
-    o.B = static_cast<const T*>(t.blocks);
-    o.M = static_cast<const T*>(t.mfac);
-    o.b = static_cast<const T*>(t.b);
-    o.x = static_cast<T*>(t.x);
-    scale = t.scale;
-  } else {
-    o.B = static_cast<const T*>(a.blocks);
-    o.M = static_cast<const T*>(a.mfac);
-    o.b = static_cast<const T*>(a.b) + (size_t)r * a.vs;
-    o.x = static_cast<T*>(a.x) + (size_t)r * a.vs;
-    scale = a.scale;
-  }
-#pragma unroll
-  for (int k = 0; k < D; ++k) o.sc[k] = (T)__ldg(scale + k);
-  return o;
-}
-
-struct Units {
-  int S, chunks, units, csize, gw, nw, lane;
-};
-
-__device__ __forceinline__ Units units_of(const MrhsArgs& a) {
-  Units u;
-  u.S = a.S;
-  u.nw = (gridDim.x * blockDim.x) >> 5;
-  u.gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  u.lane = threadIdx.x & 31;
-  u.chunks = u.nw / a.S;
-  if (u.chunks < 1) u.chunks = 1;
-  u.units = a.S * u.chunks;
-  int cs = (a.N + u.chunks - 1) / u.chunks;
-  u.csize = ((cs + 31) / 32) * 32;
-  return u;
 }
 
 // RHS state written by whichever CTA completed an earlier reduction: read through L2.
@@ -271,9 +339,11 @@ __device__ __forceinline__ bool mrhs_reduce(const MrhsArgs& a, const Units& U, i
     const int warp = threadIdx.x >> 5, nwc = blockDim.x >> 5, lane = threadIdx.x & 31;
     for (int r = warp; r < a.S; r += nwc) {
       double acc[4] = {0.0, 0.0, 0.0, 0.0};
-      for (int c = lane; c < U.chunks; c += 32) {
+      const int nc = unit_count(U, r);
+      for (int c = lane; c < nc; c += 32) {
+        const size_t row = (size_t)unit_row(U, r, c);
 #pragma unroll
-        for (int i = 0; i < 4; ++i) acc[i] += __ldcg(a.part + ((size_t)c * a.S + r) * 4 + i);
+        for (int i = 0; i < 4; ++i) acc[i] += __ldcg(a.part + row * 4 + i);
       }
       const double v = warp_reduce4(acc);
       double t[4];
@@ -337,11 +407,29 @@ __global__ void __launch_bounds__(MRHS_THREADS, (sizeof(T) == 4 || D <= 4) ? 2 :
   T* SSv = static_cast<T*>(a.s);
   __shared__ int sh_int[4];
   __shared__ int sh_flag;
-  const Units U = units_of(a);
-  const size_t ld = a.ld;
+  Units U = units_of(a);
   grid_barrier_start(a.bar);
-  auto unit_rhs = [&](int u) { return u % U.S; };
-  auto unit_chunk = [&](int u) { return u / U.S; };
+  __shared__ int sh_first[MRHS_UNEVEN_MAX_S + 1];
+  if (a.uneven) {
+    // every CTA derives the same unit ranges: one unit per right-hand side, and the warps
+    // beyond those shared in proportion to the right-hand sides' voxels
+    if (threadIdx.x == 0) {
+      long long tot = 0;
+      for (int r = 0; r < a.S; ++r) tot += a.tab[r].N;
+      const long long extra = U.nw > a.S ? U.nw - a.S : 0;
+      int acc = 0;
+      for (int r = 0; r < a.S; ++r) {
+        sh_first[r] = acc;
+        acc += 1 + (tot > 0 ? (int)(extra * a.tab[r].N / tot) : 0);
+      }
+      sh_first[a.S] = acc;
+    }
+    __syncthreads();
+    U.first = sh_first;
+    U.units = sh_first[a.S];
+  }
+  auto unit_rhs = [&](int u) { return unit_rhs_of(U, u); };
+  auto unit_chunk = [&](int u) { return unit_chunk_of(U, u); };
   // columns selected by `cols` (bit j = column j) of unit u's partial row
   auto write_partials = [&](int u, double* acc, unsigned cols) {
     const double v = warp_reduce4(acc);
@@ -358,15 +446,15 @@ __global__ void __launch_bounds__(MRHS_THREADS, (sizeof(T) == 4 || D <= 4) ? 2 :
     const T omega = (T)a.omega, c2 = T(2) - omega;
     for (int phase = 2; phase <= 3; ++phase) {
       if (!grid_sync(a.bar, &sh_flag)) return false;
-      const int* list = phase == 2 ? a.black : a.red;
-      const int nl = phase == 2 ? a.n_black : a.n_red;
-      const int ch = U.chunks;
-      int cs = (nl + ch - 1) / ch;
-      cs = ((cs + 31) / 32) * 32;
       for (int u = U.gw; u < U.units; u += U.nw) {
         const int r = unit_rhs(u), c = unit_chunk(u);
         if (!sel(r)) continue;
-        const RhsOp<D, T> op = rhs_op<D, T>(a, r);
+        const RhsOp<D, T> op = rhs_op<D, T>(a, U, r);
+        const size_t ld = op.ld;
+        const int* list = phase == 2 ? op.black : op.red;
+        const int nl = phase == 2 ? op.n_black : op.n_red;
+        int cs = (nl + op.nch - 1) / op.nch;
+        cs = ((cs + 31) / 32) * 32;
         const T* R = Rv + (size_t)r * a.vs;
         T* Uu = UUv + (size_t)r * a.vs;
         const int i1 = min(nl, (c + 1) * cs);
@@ -374,7 +462,7 @@ __global__ void __launch_bounds__(MRHS_THREADS, (sizeof(T) == 4 || D <= 4) ? 2 :
           const int n = __ldg(list + i);
           int nb[6];
 #pragma unroll
-          for (int d = 0; d < 6; ++d) nb[d] = d < a.ndir ? __ldg(a.nbr + (size_t)d * ld + n) : -1;
+          for (int d = 0; d < 6; ++d) nb[d] = d < op.ndir ? __ldg(op.nbr + (size_t)d * ld + n) : -1;
           T sum[D];
 #pragma unroll
           for (int k = 0; k < D; ++k) sum[k] = T(0);
@@ -382,13 +470,13 @@ __global__ void __launch_bounds__(MRHS_THREADS, (sizeof(T) == 4 || D <= 4) ? 2 :
           for (int d = 0; d < 6; ++d) {
             if (nb[d] >= 0) {
 #pragma unroll
-              for (int k = 0; k < D; ++k) sum[k] += (T)a.cw[d >> 1] * Uu[(size_t)k * ld + nb[d]];
+              for (int k = 0; k < D; ++k) sum[k] += op.cw[d >> 1] * Uu[(size_t)k * ld + nb[d]];
             }
           }
           T t[D], z[D];
 #pragma unroll
           for (int k = 0; k < D; ++k) t[k] = phase == 2 ? R[(size_t)k * ld + n] + op.sc[k] * sum[k] : op.sc[k] * sum[k];
-          precond_apply<D, T>(a, op.M, n, t, z);
+          precond_apply<D, T>(op, n, t, z);
 #pragma unroll
           for (int k = 0; k < D; ++k) {
             const size_t o = (size_t)k * ld + n;
@@ -404,17 +492,18 @@ __global__ void __launch_bounds__(MRHS_THREADS, (sizeof(T) == 4 || D <= 4) ? 2 :
   // red voxels' x is recovered from their own rows at every (re)start. u lives at the black
   // voxels of the U planes and y = Dg_r^-1 (scale .* sum of the black neighbours' u) at the
   // red ones; every warp owns at most one unit (the launcher guarantees S <= warps).
-  auto list_chunk = [&](int nl, int c, int& i0, int& i1) {
-    int cs = (nl + U.chunks - 1) / U.chunks;
+  auto list_chunk = [&](const RhsOp<D, T>& op, int nl, int c, int& i0, int& i1) {
+    int cs = (nl + op.nch - 1) / op.nch;
     cs = ((cs + 31) / 32) * 32;
     i0 = c * cs;
     i1 = min(nl, (c + 1) * cs);
   };
   // sum over the in-mask neighbours m of V[m]
-  auto nsum = [&](int n, const T* V, T* out) {
+  auto nsum = [&](const RhsOp<D, T>& op, int n, const T* V, T* out) {
+    const size_t ld = op.ld;
     int nb[6];
 #pragma unroll
-    for (int d = 0; d < 6; ++d) nb[d] = d < a.ndir ? __ldg(a.nbr + (size_t)d * ld + n) : -1;
+    for (int d = 0; d < 6; ++d) nb[d] = d < op.ndir ? __ldg(op.nbr + (size_t)d * ld + n) : -1;
     T v[6][D];
 #pragma unroll
     for (int d = 0; d < 6; ++d)
@@ -426,7 +515,7 @@ __global__ void __launch_bounds__(MRHS_THREADS, (sizeof(T) == 4 || D <= 4) ? 2 :
     for (int d = 0; d < 6; ++d)
       if (nb[d] >= 0) {
 #pragma unroll
-        for (int k = 0; k < D; ++k) out[k] += (T)a.cw[d >> 1] * v[d][k];
+        for (int k = 0; k < D; ++k) out[k] += op.cw[d >> 1] * v[d][k];
       }
   };
   // red voxels of the selected right-hand sides: U = Dg^-1 (scale .* sum of the neighbours' U)
@@ -434,17 +523,18 @@ __global__ void __launch_bounds__(MRHS_THREADS, (sizeof(T) == 4 || D <= 4) ? 2 :
     for (int u = U.gw; u < U.units; u += U.nw) {
       const int r = unit_rhs(u), c = unit_chunk(u);
       if (!sel(r)) continue;
-      const RhsOp<D, T> op = rhs_op<D, T>(a, r);
+      const RhsOp<D, T> op = rhs_op<D, T>(a, U, r);
+        const size_t ld = op.ld;
       T* Uu = UUv + (size_t)r * a.vs;
       int i0, i1;
-      list_chunk(a.n_red, c, i0, i1);
+      list_chunk(op, op.n_red, c, i0, i1);
       for (int i = i0 + U.lane; i < i1; i += 32) {
-        const int n = __ldg(a.red + i);
+        const int n = __ldg(op.red + i);
         T t[D], z[D];
-        nsum(n, Uu, t);
+        nsum(op, n, Uu, t);
 #pragma unroll
         for (int k = 0; k < D; ++k) t[k] *= op.sc[k];
-        precond_apply<D, T>(a, op.M, n, t, z);
+        precond_apply<D, T>(op, n, t, z);
 #pragma unroll
         for (int k = 0; k < D; ++k) Uu[(size_t)k * ld + n] = z[k];
       }
@@ -458,19 +548,20 @@ __global__ void __launch_bounds__(MRHS_THREADS, (sizeof(T) == 4 || D <= 4) ? 2 :
     for (int u = U.gw; u < U.units; u += U.nw) {
       const int r = unit_rhs(u), c = unit_chunk(u);
       if (!sel(r)) continue;
-      const RhsOp<D, T> op = rhs_op<D, T>(a, r);
+      const RhsOp<D, T> op = rhs_op<D, T>(a, U, r);
+        const size_t ld = op.ld;
       int i0, i1;
-      list_chunk(a.n_red, c, i0, i1);
+      list_chunk(op, op.n_red, c, i0, i1);
       for (int i = i0 + U.lane; i < i1; i += 32) {
-        const int n = __ldg(a.red + i);
+        const int n = __ldg(op.red + i);
         T bn[D], t[D], xn[D], ax[D];
 #pragma unroll
         for (int k = 0; k < D; ++k) bn[k] = __ldg(op.b + (size_t)k * ld + n);
-        nsum(n, op.x, t);
+        nsum(op, n, op.x, t);
 #pragma unroll
         for (int k = 0; k < D; ++k) t[k] = bn[k] + op.sc[k] * t[k];
-        precond_apply<D, T>(a, op.M, n, t, xn);
-        block_apply<D, T>(a, op.B, op.sc, n, xn, op.x, ax);
+        precond_apply<D, T>(op, n, t, xn);
+        block_apply<D, T>(op, n, xn, op.x, ax);
         T rr2 = T(0), b2 = T(0);
 #pragma unroll
         for (int k = 0; k < D; ++k) {
@@ -486,23 +577,24 @@ __global__ void __launch_bounds__(MRHS_THREADS, (sizeof(T) == 4 || D <= 4) ? 2 :
     for (int u = U.gw; u < U.units; u += U.nw) {
       const int r = unit_rhs(u), c = unit_chunk(u);
       if (!sel(r)) continue;
-      const RhsOp<D, T> op = rhs_op<D, T>(a, r);
+      const RhsOp<D, T> op = rhs_op<D, T>(a, U, r);
+        const size_t ld = op.ld;
       T *R = Rv + (size_t)r * a.vs, *Uu = UUv + (size_t)r * a.vs;
       T *P = PPv + (size_t)r * a.vs, *Sv = SSv + (size_t)r * a.vs;
       int i0, i1;
-      list_chunk(a.n_black, c, i0, i1);
+      list_chunk(op, op.n_black, c, i0, i1);
       for (int i = i0 + U.lane; i < i1; i += 32) {
-        const int n = __ldg(a.black + i);
+        const int n = __ldg(op.black + i);
         T xn[D], bn[D], ax[D], rn[D], un[D];
 #pragma unroll
         for (int k = 0; k < D; ++k) {
           xn[k] = op.x[(size_t)k * ld + n];
           bn[k] = __ldg(op.b + (size_t)k * ld + n);
         }
-        block_apply<D, T>(a, op.B, op.sc, n, xn, op.x, ax);
+        block_apply<D, T>(op, n, xn, op.x, ax);
 #pragma unroll
         for (int k = 0; k < D; ++k) rn[k] = bn[k] - ax[k];
-        precond_apply<D, T>(a, op.M, n, rn, un);
+        precond_apply<D, T>(op, n, rn, un);
         T g = T(0), rr2 = T(0), b2 = T(0);
 #pragma unroll
         for (int k = 0; k < D; ++k) {
@@ -526,17 +618,18 @@ __global__ void __launch_bounds__(MRHS_THREADS, (sizeof(T) == 4 || D <= 4) ? 2 :
     for (int u = U.gw; u < U.units; u += U.nw) {
       const int r = unit_rhs(u), c = unit_chunk(u);
       if (!sel(r)) continue;
-      const RhsOp<D, T> op = rhs_op<D, T>(a, r);
+      const RhsOp<D, T> op = rhs_op<D, T>(a, U, r);
+        const size_t ld = op.ld;
       const T* Uu = UUv + (size_t)r * a.vs;
       T* Wv = WWv + (size_t)r * a.vs;
       int i0, i1;
-      list_chunk(a.n_black, c, i0, i1);
+      list_chunk(op, op.n_black, c, i0, i1);
       for (int i = i0 + U.lane; i < i1; i += 32) {
-        const int n = __ldg(a.black + i);
+        const int n = __ldg(op.black + i);
         T un[D], wn[D];
 #pragma unroll
         for (int k = 0; k < D; ++k) un[k] = Uu[(size_t)k * ld + n];
-        block_apply<D, T>(a, op.B, op.sc, n, un, Uu, wn);
+        block_apply<D, T>(op, n, un, Uu, wn);
         T dl = T(0);
 #pragma unroll
         for (int k = 0; k < D; ++k) {
@@ -560,14 +653,15 @@ __global__ void __launch_bounds__(MRHS_THREADS, (sizeof(T) == 4 || D <= 4) ? 2 :
       const int r = unit_rhs(u), c = unit_chunk(u);
       if (__ldcg(&a.st[r].active) != 1) continue;
       const T al = (T)__ldcg(&a.st[r].alpha), be = (T)__ldcg(&a.st[r].beta);
-      const RhsOp<D, T> op = rhs_op<D, T>(a, r);
+      const RhsOp<D, T> op = rhs_op<D, T>(a, U, r);
+        const size_t ld = op.ld;
       T *x = op.x, *R = Rv + (size_t)r * a.vs, *Uu = UUv + (size_t)r * a.vs;
       T *P = PPv + (size_t)r * a.vs, *Sv = SSv + (size_t)r * a.vs;
       const T* Wv = WWv + (size_t)r * a.vs;
       int i0, i1;
-      list_chunk(a.n_black, c, i0, i1);
+      list_chunk(op, op.n_black, c, i0, i1);
       for (int i = i0 + U.lane; i < i1; i += 32) {
-        const int n = __ldg(a.black + i);
+        const int n = __ldg(op.black + i);
         T rn[D], un[D], pk[D], sk[D], xk[D], wk[D];
 #pragma unroll
         for (int k = 0; k < D; ++k) {
@@ -586,7 +680,7 @@ __global__ void __launch_bounds__(MRHS_THREADS, (sizeof(T) == 4 || D <= 4) ? 2 :
           xk[k] += al * pk[k];
           rn[k] -= al * sk[k];
         }
-        precond_apply<D, T>(a, op.M, n, rn, un);
+        precond_apply<D, T>(op, n, rn, un);
         T g = T(0), rr2 = T(0);
 #pragma unroll
         for (int k = 0; k < D; ++k) {
@@ -609,17 +703,18 @@ __global__ void __launch_bounds__(MRHS_THREADS, (sizeof(T) == 4 || D <= 4) ? 2 :
     for (int u = U.gw; u < U.units; u += U.nw) {
       const int r = unit_rhs(u), c = unit_chunk(u);
       if (__ldcg(&a.st[r].active) != 1) continue;
-      const RhsOp<D, T> op = rhs_op<D, T>(a, r);
+      const RhsOp<D, T> op = rhs_op<D, T>(a, U, r);
+        const size_t ld = op.ld;
       const T* Uu = UUv + (size_t)r * a.vs;
       T* Wv = WWv + (size_t)r * a.vs;
       int i0, i1;
-      list_chunk(a.n_black, c, i0, i1);
+      list_chunk(op, op.n_black, c, i0, i1);
       for (int i = i0 + U.lane; i < i1; i += 32) {
-        const int n = __ldg(a.black + i);
+        const int n = __ldg(op.black + i);
         T un[D], wn[D];
 #pragma unroll
         for (int k = 0; k < D; ++k) un[k] = Uu[(size_t)k * ld + n];
-        block_apply<D, T>(a, op.B, op.sc, n, un, Uu, wn);
+        block_apply<D, T>(op, n, un, Uu, wn);
         T dl = T(0);
 #pragma unroll
         for (int k = 0; k < D; ++k) {
@@ -640,19 +735,20 @@ __global__ void __launch_bounds__(MRHS_THREADS, (sizeof(T) == 4 || D <= 4) ? 2 :
       const int r = unit_rhs(u), c = unit_chunk(u);
       const int act = first ? 1 : __ldcg(&a.st[r].active);
       if (!first && act != 2) continue;
-      const RhsOp<D, T> op = rhs_op<D, T>(a, r);
+      const RhsOp<D, T> op = rhs_op<D, T>(a, U, r);
+        const size_t ld = op.ld;
       const T* b = op.b;
       T *x = op.x, *R = Rv + (size_t)r * a.vs, *Uu = UUv + (size_t)r * a.vs;
       T *P = PPv + (size_t)r * a.vs, *Sv = SSv + (size_t)r * a.vs;
-      const int n1 = min(a.N, (c + 1) * U.csize);
-      for (int n = c * U.csize + U.lane; n < n1; n += 32) {
+      const int n1 = min(op.N, (c + 1) * op.cs);
+      for (int n = c * op.cs + U.lane; n < n1; n += 32) {
         T xn[D], ax[D], rn[D], un[D];
 #pragma unroll
         for (int k = 0; k < D; ++k) xn[k] = x[(size_t)k * ld + n];
-        block_apply<D, T>(a, op.B, op.sc, n, xn, x, ax);
+        block_apply<D, T>(op, n, xn, x, ax);
 #pragma unroll
         for (int k = 0; k < D; ++k) rn[k] = __ldg(b + (size_t)k * ld + n) - ax[k];
-        precond_apply<D, T>(a, op.M, n, rn, un);
+        precond_apply<D, T>(op, n, rn, un);
         if (a.ssor) {
 #pragma unroll
           for (int k = 0; k < D; ++k) un[k] *= (T)a.omega;   // SSOR phase 1
@@ -674,13 +770,14 @@ __global__ void __launch_bounds__(MRHS_THREADS, (sizeof(T) == 4 || D <= 4) ? 2 :
       const int act = first ? 1 : __ldcg(&a.st[r].active);
       KSum<T> ks[4];
       if (first || act == 2) {
-        const RhsOp<D, T> op = rhs_op<D, T>(a, r);
+        const RhsOp<D, T> op = rhs_op<D, T>(a, U, r);
+        const size_t ld = op.ld;
         const T* b = op.b;
         const T* R = Rv + (size_t)r * a.vs;
         const T* Uu = UUv + (size_t)r * a.vs;
         T* Wv = WWv + (size_t)r * a.vs;
-        const int n1 = min(a.N, (c + 1) * U.csize);
-        for (int n = c * U.csize + U.lane; n < n1; n += 32) {
+        const int n1 = min(op.N, (c + 1) * op.cs);
+        for (int n = c * op.cs + U.lane; n < n1; n += 32) {
           T un[D], wn[D], rk[D], bk[D];
 #pragma unroll
           for (int k = 0; k < D; ++k) {
@@ -688,7 +785,7 @@ __global__ void __launch_bounds__(MRHS_THREADS, (sizeof(T) == 4 || D <= 4) ? 2 :
             rk[k] = R[(size_t)k * ld + n];
             bk[k] = __ldg(b + (size_t)k * ld + n);
           }
-          block_apply<D, T>(a, op.B, op.sc, n, un, Uu, wn);
+          block_apply<D, T>(op, n, un, Uu, wn);
           T g = T(0), dl = T(0), rr2 = T(0), b2 = T(0);
 #pragma unroll
           for (int k = 0; k < D; ++k) {
@@ -740,12 +837,13 @@ __global__ void __launch_bounds__(MRHS_THREADS, (sizeof(T) == 4 || D <= 4) ? 2 :
         if (__ldcg(&a.st[r].active) != 1) continue;
         KSum<T> kg, kr;
         const T al = (T)__ldcg(&a.st[r].alpha), be = (T)__ldcg(&a.st[r].beta);
-        const RhsOp<D, T> op = rhs_op<D, T>(a, r);
+        const RhsOp<D, T> op = rhs_op<D, T>(a, U, r);
+        const size_t ld = op.ld;
         T *x = op.x, *R = Rv + (size_t)r * a.vs, *Uu = UUv + (size_t)r * a.vs;
         T *P = PPv + (size_t)r * a.vs, *Sv = SSv + (size_t)r * a.vs;
         const T* Wv = WWv + (size_t)r * a.vs;
-        const int n0 = c * U.csize;
-        const int n1 = min(a.N, (c + 1) * U.csize);
+        const int n0 = c * op.cs;
+        const int n1 = min(op.N, (c + 1) * op.cs);
         auto update = [&](int n, T* un, T* pk, T* wk, T* sk, T* xk, T* rn) {
 #pragma unroll
           for (int k = 0; k < D; ++k) {
@@ -754,7 +852,7 @@ __global__ void __launch_bounds__(MRHS_THREADS, (sizeof(T) == 4 || D <= 4) ? 2 :
             xk[k] += al * pk[k];
             rn[k] -= al * sk[k];
           }
-          precond_apply<D, T>(a, op.M, n, rn, un);
+          precond_apply<D, T>(op, n, rn, un);
           if (a.ssor) {
 #pragma unroll
             for (int q = 0; q < D; ++q) un[q] *= (T)a.omega;   // SSOR phase 1
@@ -842,16 +940,17 @@ __global__ void __launch_bounds__(MRHS_THREADS, (sizeof(T) == 4 || D <= 4) ? 2 :
         const int r = unit_rhs(u), c = unit_chunk(u);
         if (__ldcg(&a.st[r].active) != 1) continue;
         KSum<T> kd, kg;
-        const RhsOp<D, T> op = rhs_op<D, T>(a, r);
+        const RhsOp<D, T> op = rhs_op<D, T>(a, U, r);
+        const size_t ld = op.ld;
         const T* Uu = UUv + (size_t)r * a.vs;
         const T* R = Rv + (size_t)r * a.vs;
         T* Wv = WWv + (size_t)r * a.vs;
-        const int n1 = min(a.N, (c + 1) * U.csize);
-        for (int n = c * U.csize + U.lane; n < n1; n += 32) {
+        const int n1 = min(op.N, (c + 1) * op.cs);
+        for (int n = c * op.cs + U.lane; n < n1; n += 32) {
           T un[D], wn[D];
 #pragma unroll
           for (int k = 0; k < D; ++k) un[k] = Uu[(size_t)k * ld + n];
-          block_apply<D, T>(a, op.B, op.sc, n, un, Uu, wn);
+          block_apply<D, T>(op, n, un, Uu, wn);
           T dl = T(0), g = T(0);
 #pragma unroll
           for (int k = 0; k < D; ++k) {
@@ -936,7 +1035,7 @@ __global__ void __launch_bounds__(MRHS_THREADS, R >= 4 ? 1 : 2) k_mrhs_tile(Mrhs
   using V = TileVec<R>;
   const size_t ld = a.ld;
   const int S = a.S, G = S / R;
-  Units U;
+  Units U;   // (first stays null: every right-hand side has U.chunks units)
   U.S = S;
   U.nw = (gridDim.x * blockDim.x) >> 5;
   U.gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -1279,11 +1378,13 @@ static cudaError_t launch_d(const MrhsArgs& a, cudaStream_t stream, int* units_o
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   if (a.sm_cap > 0 && a.sm_cap < nsm) nsm = a.sm_cap;
   if (a.tile > 1) {
-    if (!a.f32 || a.ssor || a.reduced || a.tab != nullptr || a.S % a.tile != 0) return cudaErrorInvalidValue;
+    if (!a.f32 || a.ssor || a.reduced || a.tab != nullptr || a.uneven || a.S % a.tile != 0)
+      return cudaErrorInvalidValue;
     if (a.tile == 2) return launch_tile<D, 2>(a, nsm, stream, units_out);
     if (a.tile == 4) return launch_tile<D, 4>(a, nsm, stream, units_out);
     return cudaErrorInvalidValue;
   }
+  if (a.uneven && (a.tab == nullptr || a.S > MRHS_UNEVEN_MAX_S)) return cudaErrorInvalidValue;
   const void* kern = a.f32 ? (const void*)k_mrhs<D, float> : (const void*)k_mrhs<D, double>;
   const size_t shm = a.f32 ? mrhs_stage_bytes<D, float>() : mrhs_stage_bytes<D, double>();
   if (shm > 0) {

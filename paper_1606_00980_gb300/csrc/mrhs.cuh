@@ -27,14 +27,29 @@ struct RhsState {
 
 // Operator and vectors of one right-hand side when the right-hand sides do not share a
 // matrix (independent chains): packed blocks [ntri(D)][ld], block-Jacobi factor (or null),
-// GMRF scales [D], b and x [D][ld].
+// GMRF scales [D], b and x [D][ld]. With MrhsArgs.uneven the right-hand side also brings its
+// own lattice (chains of different subjects, uneven masks): its voxels, neighbour
+// directions, plane stride, neighbour planes [6][ld], red and black voxel lists and edge
+// weights; otherwise those fields are unused and the launch's lattice applies.
 struct MrhsRhsPtrs {
   const void* blocks;
   const void* mfac;
   const double* scale;
   const void* b;
   void* x;
+  int N;
+  int ndir;
+  size_t ld;
+  const int* nbr;
+  const int* red;
+  const int* black;
+  int n_red;
+  int n_black;
+  double cw[3];
 };
+
+// Right-hand sides of one launch with uneven masks (MrhsArgs.uneven) at most.
+constexpr int MRHS_UNEVEN_MAX_S = 128;
 
 // Per right-hand side, accumulated over launches: iterations, solves, the first nonzero
 // status (RhsState codes) and the relative residual of the last solve.
@@ -95,6 +110,10 @@ struct MrhsArgs {
   // and component (element (i, k, n) at (i / tile) D ld tile + (k ld + n) tile + i % tile)
   // and k_mrhs_tile runs; 0 or 1 = the [S][D][ld] layout and k_mrhs
   int tile;
+  // 1: every right-hand side has its own lattice in tab (which must be set), and the work
+  // units are shared out in proportion to the right-hand sides' voxels (S <=
+  // MRHS_UNEVEN_MAX_S; vs >= D ld of every right-hand side; N = the largest N)
+  int uneven;
 };
 
 // Probe set-up and post-processing (log-determinant and trace probes).
