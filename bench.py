@@ -896,6 +896,7 @@ def run_batched_chains(args, w, n_chains=8, sweeps=3):
     torch.cuda.synchronize()
     dt = e0.elapsed_time(e1) / 1e3
     tim = models[0].timing()
+    with_probes = run_chains_with_probes(models, stream)
     for m in models:
         m.close()
     it_w = sum(i.pcg_iterations_W for i in infos)
@@ -914,7 +915,44 @@ def run_batched_chains(args, w, n_chains=8, sweeps=3):
             "W_solve_ms_per_group_sweep": solve_s / sweeps * 1e3,
             "W_solve_hbm": {"achieved_gbs": bytes_w / solve_s / 1e9, "peak_gbs": hbm_peak,
                             "frac": bytes_w / solve_s / 1e9 / hbm_peak},
-            "precond": args.precond, "dtype": "f64", "delta": 1e-8}
+            "precond": args.precond, "dtype": "f64", "delta": 1e-8,
+            "with_probes": with_probes}
+
+
+def run_chains_with_probes(models, stream, n_probes=64):
+    """The grouped chains' W step with n_probes FP64 log-det probes of chain 0's W system in
+    the same cooperative launch (bfmri_gibbs_sweep_group_probes: 8 matrices x 1 right-hand
+    side beside 1 matrix x 64 probes; block-Jacobi for every right-hand side, which the
+    probes' Lanczos quadrature needs), against the same work as two calls (one grouped sweep
+    with the chains' own preconditioner, then bfmri_logdet_probe). CUDA events around each;
+    the first combined call (workspace allocation) is not timed."""
+    import torch
+
+    from paper_1606_00980_gb300.bfmri import gibbs_sweep_group, gibbs_sweep_group_probes
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    gibbs_sweep_group_probes(models, 100, models[0], n_probes, 3000, probe_counter=1)
+    torch.cuda.synchronize()
+    models[0].reset_timing()
+    e0.record(stream)
+    infos, logdet, se, per = gibbs_sweep_group_probes(models, 101, models[0], n_probes, 3000,
+                                                      probe_counter=2)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    combined_ms = e0.elapsed_time(e1)
+    tim = models[0].timing()
+    e0.record(stream)
+    gibbs_sweep_group(models, 1, 102)
+    res = models[0].logdet_probe(0, n_probes, 3000, counter=3)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    separate_ms = e0.elapsed_time(e1)
+    return {"chains": len(models), "probes": n_probes, "right_hand_sides_in_launch": len(models) + n_probes,
+            "combined_sweep_ms": combined_ms, "combined_W_launch_ms": tim["pcg_W"]["ms"],
+            "separate_sweep_and_probe_ms": separate_ms,
+            "pcg_iterations_W_per_chain": sum(i.pcg_iterations_W for i in infos) / len(models),
+            "logdet": logdet, "stderr": se, "logdet_separate_call": res["logdet"],
+            "dtype": "f64"}
 
 
 def run_batched(args):
