@@ -769,6 +769,28 @@ def run_chains(args, w, flush, stream, single_value, n_chains=8):
         it_a += sum(i.pcg_iterations_A for i in infos)
     torch.cuda.synchronize()
     tot = sum(a.elapsed_time(b) for a, b in times) / 1e3
+
+    # the same group in one multi-sweep call, by direct launches and replayed from the CUDA
+    # graph of one group sweep (use_graph on the first chain; captured by the untimed call)
+    def multi(ms):
+        gibbs_sweep_group(ms, 2, 1000)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        gibbs_sweep_group(ms, args.steps, 1002)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / args.steps
+    direct_ms = multi(models)
+    for m in models:
+        m.close()
+    models = []
+    for c in range(n_chains):
+        m = Model.from_workload(w, delta=1e-8, seed=3000 + c, use_graph=1, **precond_options(args))
+        m.precompute_stats()
+        models.append(m)
+    captured_ms = multi(models)
     for m in models:
         m.close()
     value = n_chains * args.steps / tot
@@ -777,6 +799,7 @@ def run_chains(args, w, flush, stream, single_value, n_chains=8):
             "pcg_iterations_W_per_chain_sweep": it_w / (n_chains * args.steps),
             "pcg_iterations_A_per_chain_sweep": it_a / (n_chains * args.steps),
             "vs_single_chain": value / single_value if single_value else None,
+            "multi_sweep_call_ms_per_sweep": {"direct": direct_ms, "captured_graph": captured_ms},
             "precond": args.precond, "delta": 1e-8, "dtype": "f64"}
 
 

@@ -2,6 +2,7 @@
 // host-side orchestration of one Gibbs sweep (Section 3.2) as a fixed sequence of kernel
 // launches on the handle's stream, with no host synchronisation inside a sweep.
 #include <algorithm>
+#include <atomic>
 #include <climits>
 #include <cmath>
 #include <cstdio>
@@ -256,6 +257,14 @@ struct bfmri_handle {
   cudaStream_t capture_stream = nullptr;   // capture cannot run on the legacy default stream
   bool capturing = false;
   bool graph_failed = false;
+  uint64_t uid = 0;                 // distinct for every handle the process creates
+  // captured group sweep (this handle first in the group): the chains' uids and the
+  // workspace it was captured with
+  std::vector<uint64_t> gsweep_uids;
+  const void* gsweep_ws = nullptr;
+  cudaGraph_t gsweep_graph = nullptr;
+  cudaGraphExec_t gsweep_exec = nullptr;
+  bool gsweep_failed = false;
   // asynchronous sweeps (bfmri_gibbs_sweep without info) left their error words and PCG
   // counters unread: they accumulate until the next synchronising call
   bool deferred = false;
@@ -1101,6 +1110,10 @@ bfmri_status bfmri_create(const bfmri_lattice* lat, const uint8_t* mask, const d
 
   bfmri_handle* h = new bfmri_handle();
   h->opt = o;
+  {
+    static std::atomic<uint64_t> next_uid{1};
+    h->uid = next_uid.fetch_add(1);
+  }
   h->mask_hash = 1469598103934665603ull;
   for (int l : lin) {
     for (int byte = 0; byte < 4; ++byte) {
@@ -1287,8 +1300,10 @@ bfmri_status bfmri_destroy(bfmri_handle* h) {
   }
   for (cudaEvent_t e : h->event_pool) cudaEventDestroy(e);
   if (h->sweep_exec) cudaGraphExecDestroy(h->sweep_exec);
+  if (h->gsweep_exec) cudaGraphExecDestroy(h->gsweep_exec);
   if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
   if (h->sweep_graph) cudaGraphDestroy(h->sweep_graph);
+  if (h->gsweep_graph) cudaGraphDestroy(h->gsweep_graph);
   std::vector<void*> all = h->allocs;
   for (void* p : all) dfree(h, p);
   delete h;
@@ -1756,10 +1771,10 @@ bfmri_status group_sweep(bfmri_handle* const* hs, int n, int n_sweeps, uint64_t 
   };
   bfmri_status st = BFMRI_OK;
   for (size_t c = 0; c < all.size() && st == BFMRI_OK; ++c) st = begin_call(all[c]);
-  for (int sw = 0; sw < n_sweeps && st == BFMRI_OK; ++sw) {
-    const uint64_t cnt = first_counter + (uint64_t)sw;
+  // one sweep of every chain, W launch carrying the probes when asked
+  auto one_sweep = [&](uint64_t cnt, bool probes) -> bfmri_status {
+    bfmri_status st = BFMRI_OK;
     for (int c = 0; c < n && st == BFMRI_OK; ++c) st = assemble_W(hs[c], cnt);
-    const bool probes = gp != nullptr && sw == 0;
     if (probes && st == BFMRI_OK) {
       bfmri_handle* ph = gp->ph;
       if (!ph_in_group) {
@@ -1793,6 +1808,69 @@ bfmri_status group_sweep(bfmri_handle* const* hs, int n, int n_sweeps, uint64_t 
       if (st == BFMRI_OK && spatial_A) st = enqueue_hyper(h, cnt, true);
       if (st == BFMRI_OK && h->sum.open) st = enqueue_summary(h);
     }
+    return st;
+  };
+  // CUDA graph of one group sweep (options.use_graph on the first chain): captured once for
+  // this list of chains and workspace, its draws reading each chain's device counter, then
+  // replayed once per sweep; not with probes, per-launch timing, summaries or the test hook
+  bool graph = !gp && h0->opt.use_graph && !h0->gsweep_failed;
+  for (int c = 0; c < n && graph; ++c)
+    graph = !hs[c]->opt.profile && hs[c]->opt.debug_skip_block < 0 && !hs[c]->sum.open;
+  std::vector<uint64_t> uids((size_t)n);
+  for (int c = 0; c < n; ++c) uids[c] = hs[c]->uid;
+  if (graph && st == BFMRI_OK && (!h0->gsweep_exec || h0->gsweep_uids != uids || h0->gsweep_ws != h0->mr_r)) {
+    if (h0->gsweep_exec) cudaGraphExecDestroy(h0->gsweep_exec);
+    if (h0->gsweep_graph) cudaGraphDestroy(h0->gsweep_graph);
+    h0->gsweep_exec = nullptr;
+    h0->gsweep_graph = nullptr;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaSuccess;
+    if (!h0->capture_stream) e = cudaStreamCreateWithFlags(&h0->capture_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st0);   // begin_call's resets and the table are done
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(h0->capture_stream, cudaStreamCaptureModeRelaxed);
+    bfmri_status cs = BFMRI_OK;
+    if (e == cudaSuccess) {
+      const cudaStream_t saved0 = st0;
+      st0 = h0->capture_stream;
+      for (int c = 0; c < n; ++c) {
+        hs[c]->stream = st0;
+        hs[c]->capturing = true;
+      }
+      cs = one_sweep(0, false);
+      for (int c = 0; c < n && cs == BFMRI_OK && e == cudaSuccess; ++c)
+        e = launch_advance_counter(hs[c]->d_sweep_ctr, st0);
+      for (int c = 0; c < n; ++c) {
+        hs[c]->capturing = false;
+        hs[c]->stream = saved0;
+      }
+      st0 = saved0;
+      const cudaError_t ee = cudaStreamEndCapture(h0->capture_stream, &g);
+      if (e == cudaSuccess) e = ee;
+    }
+    if (e == cudaSuccess && cs == BFMRI_OK && g) e = cudaGraphInstantiate(&h0->gsweep_exec, g, 0);
+    if (e != cudaSuccess || cs != BFMRI_OK || !h0->gsweep_exec) {
+      h0->err = std::string("CUDA graph capture unavailable, group sweeps use direct launches: ") +
+                (cs != BFMRI_OK ? h0->err : std::string(cudaGetErrorString(e)));
+      cudaGetLastError();
+      if (g) cudaGraphDestroy(g);
+      h0->gsweep_exec = nullptr;
+      h0->gsweep_failed = true;
+      graph = false;
+    } else {
+      h0->gsweep_graph = g;
+      h0->gsweep_uids = uids;
+      h0->gsweep_ws = h0->mr_r;
+    }
+  }
+  if (graph && st == BFMRI_OK && h0->gsweep_exec) {
+    cudaError_t e = cudaSuccess;
+    for (int c = 0; c < n && e == cudaSuccess; ++c)
+      e = launch_set_counter(hs[c]->d_sweep_ctr, (uint32_t)first_counter, st0);
+    for (int sw = 0; sw < n_sweeps && e == cudaSuccess; ++sw) e = cudaGraphLaunch(h0->gsweep_exec, st0);
+    if (e != cudaSuccess) st = cuda_fail(h0, e, "captured group sweep");
+  } else {
+    for (int sw = 0; sw < n_sweeps && st == BFMRI_OK; ++sw)
+      st = one_sweep(first_counter + (uint64_t)sw, gp != nullptr && sw == 0);
   }
   for (int c = 0; c < n; ++c)
     if (hs[c]->sum.open) hs[c]->sum.n += n_sweeps;
