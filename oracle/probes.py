@@ -68,8 +68,28 @@ def exact_traces(lat: Lattice, blocks, scale):
 
 def block_chol_factors(lat: Lattice, blocks, scale):
     """Per-voxel lower Cholesky factors L_n of the block-Jacobi blocks M_n (N, D, D)."""
-    Mb = precond_blocks(lat, blocks, scale)
-    return np.stack([np.linalg.cholesky(Mb[n]) for n in range(Mb.shape[0])])
+    return np.linalg.cholesky(precond_blocks(lat, blocks, scale))
+
+
+def probe_quadrature_m(lat: Lattice, blocks, scale, v, m):
+    """v' log(C) v by the m-point Gauss quadrature of an m-step Lanczos run on
+    C = L^-1 B~ L^-T (M = L L' the block-Jacobi preconditioner), with sparse operators only,
+    at any size. Preconditioned CG on B~ started from zero with right-hand side L v builds the
+    tridiagonal of this Lanczos run step by step, so with m the iterations of a probe solve
+    this is the value that solve's CG coefficients define."""
+    from . import linalg
+    N, D, _ = blocks.shape
+    Linv = np.linalg.inv(block_chol_factors(lat, blocks, scale))
+    B = model.precision(lat, blocks, scale).tocsr()
+
+    def kmaj_apply(F, x, transpose=False):
+        X = x.reshape(D, N).T
+        Y = np.einsum("nji,nj->ni" if transpose else "nij,nj->ni", F, X)
+        return Y.T.reshape(-1)
+
+    vk = model.kmajor(v)
+    return linalg.slq_quadform(lambda x: kmaj_apply(Linv, B @ kmaj_apply(Linv, x, transpose=True)),
+                               vk, m)
 
 
 def probe_terms_lanczos(lat: Lattice, blocks, scale, V, tol=1e-13, m_max=400):

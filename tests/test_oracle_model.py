@@ -441,6 +441,34 @@ def test_lanczos_probe_terms_equal_dense_ones():
     assert np.max(np.abs(tr2 - tr)) <= 1e-10 * np.abs(tr).max()
 
 
+def test_fixed_step_probe_quadrature():
+    """probes.probe_quadrature_m: with m = the dimension the Gauss quadrature is exact (the
+    dense eigendecomposition's v' log(C) v); with m = 5 it is |v|^2 e1' log(Q' C Q) e1 for
+    an orthonormal basis Q of the Krylov space span{v, C v, ..., C^4 v} whose first column is
+    v / |v|, built here by a QR factorisation of the dense Krylov matrix."""
+    from oracle import probes
+    w, lat = tiny(dims=(4, 4, 3), K=3, P=1, T=30, nb=6)
+    s = random_state(w, np.random.default_rng(32))
+    Bd, _ = model.w_blocks_direct(w.Y, w.X, s["A"], s["lam"])
+    v = probes.probe_vectors(lat, 3, 1, seed=9, counter=3)[0]
+    _, quad, _, _ = probes.exact_probe_terms(lat, Bd, s["alpha"], [v])
+    n = 3 * w.N
+    assert abs(probes.probe_quadrature_m(lat, Bd, s["alpha"], v, n) - quad[0]) <= 1e-9 * abs(quad[0])
+    Ls = probes.block_chol_factors(lat, Bd, s["alpha"])
+    H = model.H_perm(w.N, 3)
+    L = (H.T @ model.blkdiag(Ls) @ H).toarray()
+    B = model.precision(lat, Bd, s["alpha"]).toarray()
+    C = np.linalg.solve(L, np.linalg.solve(L, B).T).T          # L^-1 B L^-T (symmetric)
+    vk = model.kmajor(v)
+    Kry = np.stack([np.linalg.matrix_power(C, j) @ vk for j in range(5)], axis=1)
+    Q, _ = np.linalg.qr(Kry)
+    th, S = np.linalg.eigh(Q.T @ C @ Q)
+    ref = float((vk @ vk) * np.sum(S[0, :] ** 2 * np.log(th)))
+    got = probes.probe_quadrature_m(lat, Bd, s["alpha"], v, 5)
+    assert abs(got - ref) <= 1e-9 * abs(ref)
+    assert abs(got - quad[0]) > 1e-6 * abs(quad[0])           # 5 steps are not yet exact
+
+
 def test_nested_dissection_order_and_factor():
     """linalg.nested_dissection is a permutation whose first split leaves no lattice edge
     between the two halves (only the separator plane touches both), and factor_nd solves
