@@ -136,9 +136,14 @@ typedef struct {
   int use_graph;             /* nonzero: bfmri_gibbs_sweep replays one captured CUDA graph
                                 per sweep (captured at the first call; the draw counter lives
                                 in device memory and the graph advances it), with the same
-                                results as direct launches. Ignored while profile or
-                                debug_skip_block is set; if capture is unavailable the handle
-                                falls back to direct launches. Default 0. */
+                                results as direct launches. On the first handle of a
+                                bfmri_gibbs_sweep_group call it does the same for the group's
+                                sweeps (one graph per list of chains, kept while the chains
+                                and the group's workspace stay the same; not for the sweep of
+                                bfmri_gibbs_sweep_group_probes). Ignored while profile or
+                                debug_skip_block is set, or while a chain summary is open in a
+                                group; if capture is unavailable the handle falls back to
+                                direct launches. Default 0. */
   double edge_weight[3];     /* weighted graph-Laplacian (WGL) prior (Discussion): the prior
                                 precision of W_k is alpha_k G_w' C G_w (and that of A_p is
                                 beta_p G_w' C G_w) with C the weight of each edge's direction
