@@ -83,6 +83,17 @@ def test_create_rejects_bad_arguments_without_touching_the_gpu(lib):
     with pytest.raises(bfmri.BfmriError) as ei:
         bfmri.bfmri_create((4, 3, 2, 6), mask, X, Yn, 2, 1, torch_memory=False)
     assert ei.value.status == -1 and "non-finite" in str(ei.value)
+    # FP32 series, infinities, and a series long enough for the multi-threaded scan (the
+    # offending value in its last block and in the middle)
+    T = 200000
+    XL = np.ones((T, 2))
+    for dt in (np.float64, np.float32):
+        for pos, val in (((3, 5), np.inf), ((T - 1, 23), -np.inf), ((T // 2, 11), np.nan)):
+            YL = np.ones((T if pos[0] >= 20 else 20, 24), dt)
+            YL[pos] = val
+            with pytest.raises(bfmri.BfmriError) as ei:
+                bfmri.bfmri_create((4, 3, 2, 6), mask, XL[:YL.shape[0]], YL, 2, 1, torch_memory=False)
+            assert ei.value.status == -1 and "non-finite" in str(ei.value), (dt, pos)
 
 
 def test_summary_bindings_marshal_without_a_gpu(lib):
