@@ -25,12 +25,13 @@ def default_state(K, P, N, priors=model.PRIORS):
                 beta=np.full(P, priors["r1"] * priors["r2"]))
 
 
-def draw_gmrf(lat: Lattice, blocks, rhs, scale, seed, counter, tag, stream=0):
-    """Algorithm 2 with an exact solve: b = rhs + sum_k sqrt(s_k) G'z1_k + H'L_data H z2,
-    then w = B~^-1 b. Returns (draw as (dim, N), conditional mean as (dim, N))."""
+def draw_gmrf(lat: Lattice, blocks, rhs, scale, seed, counter, tag, stream=0, prior="ugl"):
+    """Algorithm 2 with an exact solve: b = rhs + sum_k sqrt(s_k) G'z1_k + H'L_data H z2
+    (L' z1_k in place of G'z1_k for the L'L prior), then w = B~^-1 b. Returns (draw as
+    (dim, N), conditional mean as (dim, N))."""
     N, K, _ = blocks.shape
-    B = model.precision(lat, blocks, scale)
-    pert, _, _ = model.perturbation(lat, blocks, scale, seed, counter, tag, stream)
+    B = model.precision(lat, blocks, scale, prior)
+    pert, _, _ = model.perturbation(lat, blocks, scale, seed, counter, tag, stream, prior)
     b_mean = model.kmajor(rhs)
     lu = linalg.factor(B)
     x = lu.solve(b_mean + pert)
@@ -38,9 +39,9 @@ def draw_gmrf(lat: Lattice, blocks, rhs, scale, seed, counter, tag, stream=0):
     return x.reshape(K, N), mu.reshape(K, N)
 
 
-def sample_W(lat, Y, X, state, seed, counter, eps=0.0, stream=0):
+def sample_W(lat, Y, X, state, seed, counter, eps=0.0, stream=0, prior="ugl"):
     Bd, bw = model.w_blocks_direct(Y, X, state["A"], state["lam"], eps)
-    return draw_gmrf(lat, Bd, bw, state["alpha"], seed, counter, philox.TAG_W, stream)[0]
+    return draw_gmrf(lat, Bd, bw, state["alpha"], seed, counter, philox.TAG_W, stream, prior)[0]
 
 
 def sample_A(lat, Y, X, state, seed, counter, spatial=True, stream=0):
@@ -59,8 +60,8 @@ def sample_lambda(lat, Y, X, state, seed, counter, priors=model.PRIORS, stream=0
     return lam
 
 
-def sample_alpha(lat, state, seed, counter, priors=model.PRIORS, stream=0):
-    Q = model.quad_forms_edges(lat, state["W"])
+def sample_alpha(lat, state, seed, counter, priors=model.PRIORS, stream=0, prior="ugl"):
+    Q = (model.quad_forms_ltl if prior == "ltl" else model.quad_forms_edges)(lat, state["W"])
     scale, shape = model.alpha_params(Q, lat.N, priors["q1"], priors["q2"])
     a, _ = philox.gamma(seed, np.arange(len(Q)), shape, scale, counter, philox.TAG_ALPHA, stream)
     return a

@@ -174,11 +174,23 @@ def blkdiag(blocks):
     return sp.block_diag([sp.csr_matrix(b) for b in blocks], format="csr")
 
 
-def precision(lat: Lattice, blocks, scale):
-    """B~ = H' blkdiag_n(blocks_n) H + diag(scale) (x) D  in regressor-major order."""
+def prior_precision(lat: Lattice, prior="ugl"):
+    """The spatial precision D_w of Section 2: the (weighted) graph Laplacian L ("ugl", the
+    SPM12 default the paper uses), or L'L ("ltl", the prior of Penny et al. 2005 that the
+    paper mentions as an alternative: a 25-point stencil in 3D, 13-point in 2D)."""
+    L = lat.D()
+    if prior == "ugl":
+        return L
+    if prior == "ltl":
+        return (L.T @ L).tocsr()
+    raise ValueError(prior)
+
+
+def precision(lat: Lattice, blocks, scale, prior="ugl"):
+    """B~ = H' blkdiag_n(blocks_n) H + diag(scale) (x) D_w  in regressor-major order."""
     N, K, _ = blocks.shape
     H = H_perm(N, K)
-    return (H.T @ blkdiag(blocks) @ H + sp.kron(sp.diags(scale), lat.D())).tocsr()
+    return (H.T @ blkdiag(blocks) @ H + sp.kron(sp.diags(scale), prior_precision(lat, prior))).tocsr()
 
 
 def kmajor(v_nk):
@@ -190,29 +202,37 @@ def from_kmajor(v, K):
     return v.reshape(K, -1)
 
 
-def perturbation(lat: Lattice, blocks, scale, seed, counter, tag, stream=0):
+def perturbation(lat: Lattice, blocks, scale, seed, counter, tag, stream=0, prior="ugl"):
     """The random part of Algorithm 2's right-hand side,
         sum_k sqrt(scale_k) (G' z1_k)  +  H' L_data H z2        (regressor-major),
     with L_data the per-voxel lower Cholesky factor of the data block. z1[e, k] is the
     normal of edge e (site = lattice-linear(i) * 4 + d) and z2[n, k] that of voxel n
-    (site = lattice-linear(n) * 4 + 3), lane k (oracle.philox.normals)."""
+    (site = lattice-linear(n) * 4 + 3), lane k (oracle.philox.normals).
+    For the L'L prior the square root of D_w = L'L is L' itself (N x N): z1[n, k] is then one
+    normal per voxel (site = lattice-linear(n) * 4 + 0) and the first term sqrt(scale_k) L' z1_k,
+    whose covariance is scale_k L'L."""
     N, K, _ = blocks.shape
-    E = lat.edges()
-    sites_e = lat.lin[E[:, 0]] * 4 + E[:, 2]
-    z1 = philox.normals(seed, sites_e, K, counter, tag, stream)
     z2 = philox.normals(seed, lat.lin * 4 + 3, K, counter, tag, stream)
-    G = lat.Gw()
-    part1 = np.concatenate([np.sqrt(scale[k]) * (G.T @ z1[:, k]) for k in range(K)])
+    if prior == "ltl":
+        z1 = philox.normals(seed, lat.lin * 4 + 0, K, counter, tag, stream)
+        Lt = lat.D().T.tocsr()
+        part1 = np.concatenate([np.sqrt(scale[k]) * (Lt @ z1[:, k]) for k in range(K)])
+    else:
+        E = lat.edges()
+        sites_e = lat.lin[E[:, 0]] * 4 + E[:, 2]
+        z1 = philox.normals(seed, sites_e, K, counter, tag, stream)
+        G = lat.Gw()
+        part1 = np.concatenate([np.sqrt(scale[k]) * (G.T @ z1[:, k]) for k in range(K)])
     Lz = np.stack([np.linalg.cholesky(blocks[n]) @ z2[n] for n in range(N)])  # (N, K)
     part2 = kmajor(Lz)
     return part1 + part2, z1, z2
 
 
-def perturbation_matrix(lat: Lattice, blocks, scale):
+def perturbation_matrix(lat: Lattice, blocks, scale, prior="ugl"):
     """The linear map (z1, z2) -> perturbation as an explicit matrix (for the covariance pin:
     its Gram matrix must equal B~ exactly, which is why Algorithm 2 samples correctly)."""
     N, K, _ = blocks.shape
-    G = lat.Gw()
+    G = lat.D().T if prior == "ltl" else lat.Gw()
     part1 = sp.block_diag([sp.csr_matrix(np.sqrt(scale[k]) * G.T) for k in range(K)], format="csr")
     H = H_perm(N, K)
     L = blkdiag([np.linalg.cholesky(blocks[n]) for n in range(N)])
@@ -235,6 +255,12 @@ def quad_forms_edges(lat: Lattice, V):
     E = lat.edges()
     diff = V[:, E[:, 0]] - V[:, E[:, 1]]
     return (lat.weights[E[:, 2]][None, :] * diff * diff).sum(axis=1)
+
+
+def quad_forms_ltl(lat: Lattice, V):
+    """Q_k = V_k L'L V_k' = |L V_k'|^2 for the L'L prior."""
+    L = lat.D()
+    return np.array([float(np.sum((L @ V[k]) ** 2)) for k in range(V.shape[0])])
 
 
 def quad_forms_laplacian(lat: Lattice, V):
