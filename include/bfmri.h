@@ -161,6 +161,16 @@ typedef struct {
                                 the autotuner times 1, 2 and 4 on the first probe call of each
                                 shape (K or P, probe count, N, sm_budget) and keeps the fastest
                                 for the process (bfmri_probe_tuning reports it) */
+  int w_prior;               /* spatial prior of W: BFMRI_PRIOR_UGL (default: D_w = L, the
+                                graph Laplacian of Section 2, weighted by edge_weight) or
+                                BFMRI_PRIOR_LTL (D_w = L'L, the alternative Section 2 names:
+                                a 25-point stencil in 3D, 13-point in 2D). With LTL, W is
+                                solved by FP64 streaming PCG with block-Jacobi (blocks plus
+                                diag(alpha) times the diagonal of L'L) or no preconditioner
+                                (precond BLOCK_JACOBI or NONE, precision FP64, else INVALID_ARG
+                                at create); the A prior stays the graph Laplacian; grouped
+                                sweeps, probes, SVB steps and the log joint reject LTL handles
+                                with INVALID_ARG. */
   int pcg_lanes;             /* lanes of the register-resident FP64 solver on the red-black
                                 reduced system (BFMRI_PRECOND_RB_REDUCED, K or P <= 6):
                                 2 = lane pairs, each pair holding one red and one black voxel
@@ -169,6 +179,9 @@ typedef struct {
                                 per voxel; 0 (default) = lane pairs for 6 x 6 blocks, one lane
                                 otherwise. Same iterates up to rounding. */
 } bfmri_options;
+
+#define BFMRI_PRIOR_UGL 0
+#define BFMRI_PRIOR_LTL 1
 
 #define BFMRI_STATS_AUTO   0
 #define BFMRI_STATS_FP64   1

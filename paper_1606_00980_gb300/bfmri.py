@@ -24,6 +24,7 @@ STATUS_NAMES = {0: "OK", -1: "INVALID_ARG", -2: "OOM", -3: "NOT_SPD", -4: "NOT_C
                 -5: "TIMEOUT", -6: "CUDA", -7: "INTERNAL", -8: "STATE"}
 BFMRI_F32, BFMRI_F64 = 0, 1
 PRECOND_NONE, PRECOND_BLOCK_JACOBI, PRECOND_SSOR, PRECOND_RB_REDUCED, PRECOND_MULTIGRID = 0, 1, 2, 3, 4
+PRIOR_UGL, PRIOR_LTL = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
 AR_SPATIAL, AR_INDEPENDENT = 0, 1
 Y_MASKED, Y_LATTICE = 0, 1
@@ -50,7 +51,7 @@ class bfmri_options(C.Structure):
                 ("sm_budget", C.c_int), ("ssor_omega", C.c_double),
                 ("use_graph", C.c_int), ("edge_weight", C.c_double * 3),
                 ("stats_kernel", C.c_int), ("mrhs_tile", C.c_int),
-                ("pcg_lanes", C.c_int)]
+                ("w_prior", C.c_int), ("pcg_lanes", C.c_int)]
 
 
 class bfmri_solve_info(C.Structure):

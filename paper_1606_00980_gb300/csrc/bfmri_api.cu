@@ -236,6 +236,7 @@ struct bfmri_handle {
   std::vector<unsigned char> colour_host;   // 0 red, 1 black per voxel
   std::map<int, int> pair_slots;            // voxels per CTA -> lane pairs of k_pcg_rbp2
   double* d_ldm = nullptr;                  // log det M of a probe set riding with a group sweep
+  double* d_lt = nullptr;                   // [K][ld] L v of the L'L prior's products
   // multigrid hierarchy (BFMRI_PRECOND_MULTIGRID), built on the first multigrid solve:
   // levels 1..mg_L-1 plus level 0's slot weights and aggregate map
   int mg_L = 0;
@@ -706,6 +707,11 @@ bfmri_status run_pcg(bfmri_handle* h, int D, const double* scale, double* x, int
   a.ssor = uses_ssor(h->opt);
   a.omega = ssor_omega_of(h->opt);
   a.reduced = h->opt.precond == BFMRI_PRECOND_RB_REDUCED;
+  if (which == 0 && h->opt.w_prior == BFMRI_PRIOR_LTL) {
+    a.ltl = 1;
+    a.t = h->d_lt;
+    a.allow_resident = 0;
+  }
   // lane pairs by default only for 6 x 6 blocks: measured on the whole-brain workload they
   // take the W solve (K = 6) from 0.414 to 0.404 ms per sweep, but the A solve (P = 3) from
   // 0.364 to 0.432 ms, where the second lane holds one component and the gathers and padded
@@ -781,6 +787,8 @@ AssembleArgs assemble_args(bfmri_handle* h, const double* scale, uint64_t counte
   a.rhs = h->d_rhs;
   a.G = h->d_G;
   a.bad_voxel = h->d_flags;
+  a.ltl = tag == TAG_W && h->opt.w_prior == BFMRI_PRIOR_LTL;
+  if (a.ltl) a.edge = h->d_edge;   // the prior terms, from launch_ltl_noise when perturbed
   return a;
 }
 
@@ -791,7 +799,8 @@ bfmri_status assemble_W(bfmri_handle* h, uint64_t counter) {
   cudaError_t e;
   {
     Timed tm(h, BFMRI_T_ASSEMBLE_W);
-    e = launch_edge_noise(a.g, h->K, h->d_alpha, a.rng, h->d_edge, h->stream);
+    e = a.ltl ? launch_ltl_noise(a.g, h->K, h->d_alpha, a.rng, h->d_edge, h->stream)
+              : launch_edge_noise(a.g, h->K, h->d_alpha, a.rng, h->d_edge, h->stream);
     a.edge = h->d_edge;
     if (e == cudaSuccess) e = launch_assemble_w(a, h->stream);
   }
@@ -896,6 +905,7 @@ bfmri_status enqueue_hyper(bfmri_handle* h, uint64_t counter, bool beta) {
   a.Q_out = nullptr;
   a.rng = rng_of(h, counter, beta ? TAG_BETA : TAG_ALPHA);
   a.exhausted = h->d_flags + 1;
+  a.ltl = !beta && h->opt.w_prior == BFMRI_PRIOR_LTL;
   Timed tm(h, BFMRI_T_HYPER);
   cudaError_t e = launch_hyper(a, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "hyper");
@@ -1060,6 +1070,7 @@ void bfmri_default_options(bfmri_options* o) {
   o->debug_skip_block = -1;
   o->stats_kernel = BFMRI_STATS_AUTO;
   o->mrhs_tile = 0;
+  o->w_prior = BFMRI_PRIOR_UGL;
   o->pcg_lanes = 0;
 }
 
@@ -1134,6 +1145,13 @@ bfmri_status bfmri_create(const bfmri_lattice* lat, const uint8_t* mask, const d
     if (!(o.edge_weight[d] > 0.0) || !std::isfinite(o.edge_weight[d]))
       return fail(nullptr, BFMRI_ERR_INVALID_ARG, "edge_weight must be positive and finite");
   if (o.pcg_lanes < 0 || o.pcg_lanes > 2) return fail(nullptr, BFMRI_ERR_INVALID_ARG, "pcg_lanes must be 0, 1 or 2");
+  if (o.w_prior != BFMRI_PRIOR_UGL && o.w_prior != BFMRI_PRIOR_LTL)
+    return fail(nullptr, BFMRI_ERR_INVALID_ARG, "unknown w_prior");
+  if (o.w_prior == BFMRI_PRIOR_LTL &&
+      ((o.precond != BFMRI_PRECOND_NONE && o.precond != BFMRI_PRECOND_BLOCK_JACOBI) ||
+       o.precision != BFMRI_PREC_FP64))
+    return fail(nullptr, BFMRI_ERR_INVALID_ARG,
+                "the L'L prior needs block-Jacobi or no preconditioner and FP64 precision");
   if (o.stats_kernel != BFMRI_STATS_AUTO && o.stats_kernel != BFMRI_STATS_FP64 &&
       o.stats_kernel != BFMRI_STATS_TENSOR)
     return fail(nullptr, BFMRI_ERR_INVALID_ARG, "unknown stats_kernel");
@@ -1261,7 +1279,8 @@ bfmri_status bfmri_create(const bfmri_lattice* lat, const uint8_t* mask, const d
   h->d_ctrl = (PcgCtrl*)A(2 * sizeof(PcgCtrl));
   h->d_flags = (int*)A(4 * sizeof(int));
   h->d_edge = (double*)A((size_t)3 * D * ld * sizeof(double));
-  if (!h->d_edge) {
+  if (o.w_prior == BFMRI_PRIOR_LTL) h->d_lt = (double*)A((size_t)K * ld * sizeof(double));
+  if (!h->d_edge || (o.w_prior == BFMRI_PRIOR_LTL && !h->d_lt)) {
     bfmri_destroy(h);
     return fail(nullptr, BFMRI_ERR_OOM, "device allocation failed");
   }
@@ -1676,6 +1695,11 @@ bfmri_status group_sweep(bfmri_handle* const* hs, int n, int n_sweeps, uint64_t 
       if (hs[d] == hs[c]) return fail(hs[0], BFMRI_ERR_INVALID_ARG, "a handle appears twice in the group");
   }
   bfmri_handle* h0 = hs[0];
+  for (int c = 0; c < n; ++c)
+    if (hs[c]->opt.w_prior != BFMRI_PRIOR_UGL)
+      return fail(h0, BFMRI_ERR_INVALID_ARG, "grouped chains need the graph-Laplacian prior");
+  if (gp && gp->ph && gp->ph->opt.w_prior != BFMRI_PRIOR_UGL)
+    return fail(h0, BFMRI_ERR_INVALID_ARG, "probes need the graph-Laplacian prior");
   bool uneven = false;
   size_t ld_max = 0;
   int N_max = 0;
@@ -2203,6 +2227,8 @@ bfmri_status bfmri_svb_summary(bfmri_handle* h, int n_contrasts, const double* C
 bfmri_status bfmri_log_joint(bfmri_handle* h, double* terms) {
   RET(require_stats(h));
   if (!terms) return fail(h, BFMRI_ERR_INVALID_ARG, "terms is NULL");
+  if (h->opt.w_prior != BFMRI_PRIOR_UGL)
+    return fail(h, BFMRI_ERR_INVALID_ARG, "the log joint needs the graph-Laplacian prior");
   const int K = h->K, P = h->P;
   const int grid = log_joint_grid(h->N);
   if (!h->d_lj) {
@@ -2225,6 +2251,7 @@ bfmri_status bfmri_log_joint(bfmri_handle* h, double* terms) {
     q.out = nullptr;
     q.rng = rng_of(h, 0, TAG_ALPHA);
     q.exhausted = h->d_flags + 1;
+    q.ltl = 0;
     q.D = K;
     q.V = h->d_W;
     q.Q_out = d_Qw;
@@ -2304,6 +2331,8 @@ bfmri_status bfmri_logdet_probe(bfmri_handle* h, int which, int n_probes, int la
     return fail(h, BFMRI_ERR_INVALID_ARG, "bad arguments");
   const int D = which == 0 ? h->K : h->P;
   if (D == 0) return fail(h, BFMRI_ERR_INVALID_ARG, "no AR part (P = 0)");
+  if (which == 0 && h->opt.w_prior != BFMRI_PRIOR_UGL)
+    return fail(h, BFMRI_ERR_INVALID_ARG, "W probes need the graph-Laplacian prior");
   RET(begin_call(h));
   const double* scale = which == 0 ? h->d_alpha : h->d_beta;
   if (which == 1 && h->opt.ar_prior != BFMRI_AR_SPATIAL) {
@@ -2485,6 +2514,8 @@ bfmri_status bfmri_spvb_step(bfmri_handle* h, int n_samples, uint64_t counter, i
                              double* alpha_vb, double* beta_vb, bfmri_svb_info* info) {
   RET(require_stats(h));
   if (n_samples < 1 || n_samples > 4096) return fail(h, BFMRI_ERR_INVALID_ARG, "n_samples must be in [1, 4096]");
+  if (h->opt.w_prior != BFMRI_PRIOR_UGL)
+    return fail(h, BFMRI_ERR_INVALID_ARG, "the SVB step needs the graph-Laplacian prior");
   const int K = h->K, P = h->P, S = n_samples;
   const size_t ld = h->ld;
   const bool spatial = h->opt.ar_prior == BFMRI_AR_SPATIAL;
@@ -2741,6 +2772,7 @@ bfmri_status bfmri_apply_precision(bfmri_handle* h, int which, const double* x, 
   }
   ap.x = h->d_r;
   ap.y = h->d_z;
+  ap.t = (which == 0 && h->opt.w_prior == BFMRI_PRIOR_LTL) ? h->d_lt : nullptr;
   e = launch_apply(ap, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "apply");
   RET(end_call(h, nullptr, nullptr));
@@ -2806,7 +2838,9 @@ bfmri_status bfmri_build_system(bfmri_handle* h, int which, uint64_t counter, do
   AssembleArgs a = assemble_args(h, which == 0 ? h->d_alpha : h->d_beta, counter, which == 0 ? TAG_W : TAG_A);
   a.precond = 0;
   a.bmean = h->d_bmean;
-  cudaError_t e = which == 0 ? launch_assemble_w(a, h->stream) : launch_assemble_a(a, h->stream);
+  cudaError_t e = cudaSuccess;
+  if (a.ltl) e = launch_ltl_noise(a.g, h->K, h->d_alpha, a.rng, h->d_edge, h->stream);
+  if (e == cudaSuccess) e = which == 0 ? launch_assemble_w(a, h->stream) : launch_assemble_a(a, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "assemble");
   RET(end_call(h, nullptr, nullptr));
   if (blocks) {

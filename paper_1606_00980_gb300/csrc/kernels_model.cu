@@ -166,7 +166,10 @@ __global__ void __launch_bounds__(VOX_THREADS) k_assemble_w(AssembleArgs a) {
     lower_mul_diag<K>(L, Ld, z, Lz);
 #pragma unroll
     for (int k = 0; k < K; ++k) rhs[k] += Lz[k];
-    if (a.edge) {
+    if (a.ltl) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) rhs[k] += __ldg(a.edge + (size_t)k * ld + n);
+    } else if (a.edge) {
       add_edge_terms<K>(a.g, a.edge, n, rhs);
     } else {
       double sq[K];
@@ -178,7 +181,7 @@ __global__ void __launch_bounds__(VOX_THREADS) k_assemble_w(AssembleArgs a) {
 #pragma unroll
   for (int k = 0; k < K; ++k) a.rhs[k * ld + n] = rhs[k];
   if (a.precond) {
-    const double deg = degree(a.g, n);
+    const double deg = a.ltl ? ltl_diagonal(a.g, n) : degree(a.g, n);
 #pragma unroll
     for (int k = 0; k < K; ++k) B[tri(k, k)] += a.scale[k] * deg;
     ok = chol_packed_invdiag<K>(B) && ok;
@@ -314,6 +317,88 @@ __global__ void __launch_bounds__(VOX_THREADS) k_assemble_a(AssembleArgs a) {
     }
   }
   if (!ok) atomicMin(a.bad_voxel, n);
+}
+
+// ---------------------------------------------------------------------------------------
+// The L'L prior: t = f .* (L v) for D planes (L the weighted graph Laplacian, symmetric, so
+// L' v = L v), f_k = 1 or sqrt(scale_k); and the per-voxel normals z1 of its perturbation.
+// ---------------------------------------------------------------------------------------
+template <int D>
+__global__ void __launch_bounds__(VOX_THREADS) k_laplacian(Geometry g, const double* v, double* t,
+                                                           const double* scale) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= g.N) return;
+  const size_t ld = g.ld;
+  double sum[D], deg = 0.0;
+#pragma unroll
+  for (int k = 0; k < D; ++k) sum[k] = 0.0;
+  for (int d = 0; d < g.ndir; ++d) {
+    const int m = __ldg(g.nbr + (size_t)d * ld + n);
+    if (m >= 0) {
+      const double c = g.cw[d >> 1];
+      deg += c;
+#pragma unroll
+      for (int k = 0; k < D; ++k) sum[k] += c * v[(size_t)k * ld + m];
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    const double f = scale ? sqrt(__ldg(scale + k)) : 1.0;
+    t[(size_t)k * ld + n] = f * (deg * v[(size_t)k * ld + n] - sum[k]);
+  }
+}
+
+template <int D>
+__global__ void __launch_bounds__(VOX_THREADS) k_voxel_normals(Geometry g, Rng rng, double* Z) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= g.N) return;
+  double z[D];
+  site_normals<D>(rng, (uint32_t)g.lin[n] * 4u + 0u, z);
+#pragma unroll
+  for (int k = 0; k < D; ++k) Z[(size_t)k * g.ld + n] = z[k];
+}
+
+// alpha under the L'L prior: Q_k = sum_n ((L v_k)_n)^2, the same two-level reduction as
+// k_quadform
+template <int D>
+__global__ void __launch_bounds__(HYPER_THREADS) k_quadform_ltl(HyperArgs a) {
+  __shared__ double sh[HYPER_THREADS / 32][D];
+  double acc[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) acc[k] = 0.0;
+  const size_t ld = a.g.ld;
+  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < a.g.N; n += gridDim.x * blockDim.x) {
+    double sum[D], deg = 0.0;
+#pragma unroll
+    for (int k = 0; k < D; ++k) sum[k] = 0.0;
+    for (int d = 0; d < a.g.ndir; ++d) {
+      const int m = __ldg(a.g.nbr + (size_t)d * ld + n);
+      if (m >= 0) {
+        const double c = a.g.cw[d >> 1];
+        deg += c;
+#pragma unroll
+        for (int k = 0; k < D; ++k) sum[k] += c * a.V[(size_t)k * ld + m];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const double l = deg * a.V[(size_t)k * ld + n] - sum[k];
+      acc[k] += l * l;
+    }
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_down_sync(0xffffffffu, acc[k], o);
+    if (lane == 0) sh[warp][k] = acc[k];
+  }
+  __syncthreads();
+  if (threadIdx.x < D) {
+    double s = 0.0;
+    for (int w = 0; w < HYPER_THREADS / 32; ++w) s += sh[w][threadIdx.x];
+    a.part[(size_t)blockIdx.x * D + threadIdx.x] = s;
+  }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -454,17 +539,20 @@ __global__ void k_apply(ApplyArgs a) {
 #pragma unroll
   for (int k = 0; k < D; ++k) sum[k] = 0.0;
   double deg = 0.0;
+  // the prior part: scale .* (L x), or scale .* (L (L x)) with t = L x under the L'L prior
+  const double* V = a.t ? a.t : a.x;
   for (int d = 0; d < a.g.ndir; ++d) {
     const int m = a.g.nbr[(size_t)d * ld + n];
     if (m >= 0) {
       const double c = a.g.cw[d >> 1];
       deg += c;
 #pragma unroll
-      for (int k = 0; k < D; ++k) sum[k] += c * a.x[(size_t)k * ld + m];
+      for (int k = 0; k < D; ++k) sum[k] += c * V[(size_t)k * ld + m];
     }
   }
 #pragma unroll
-  for (int k = 0; k < D; ++k) a.y[(size_t)k * ld + n] = y[k] + a.scale[k] * (deg * xn[k] - sum[k]);
+  for (int k = 0; k < D; ++k)
+    a.y[(size_t)k * ld + n] = y[k] + a.scale[k] * (deg * V[(size_t)k * ld + n] - sum[k]);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -654,7 +742,8 @@ int hyper_grid(int N) {
 template <int D>
 static cudaError_t hyper_d(const HyperArgs& a, cudaStream_t s) {
   const int grid = hyper_grid(a.g.N);
-  k_quadform<D><<<grid, HYPER_THREADS, 0, s>>>(a);
+  if (a.ltl) k_quadform_ltl<D><<<grid, HYPER_THREADS, 0, s>>>(a);
+  else k_quadform<D><<<grid, HYPER_THREADS, 0, s>>>(a);
   k_hyper_draw<<<1, 32 * D, 0, s>>>(a, grid);
   return cudaGetLastError();
 }
@@ -670,8 +759,31 @@ cudaError_t launch_hyper(const HyperArgs& a, cudaStream_t s) {
 
 template <int D>
 static cudaError_t apply_d(const ApplyArgs& a, cudaStream_t s) {
-  k_apply<D><<<(a.g.N + VOX_THREADS - 1) / VOX_THREADS, VOX_THREADS, 0, s>>>(a);
+  const int grid = (a.g.N + VOX_THREADS - 1) / VOX_THREADS;
+  if (a.t) k_laplacian<D><<<grid, VOX_THREADS, 0, s>>>(a.g, a.x, a.t, nullptr);
+  k_apply<D><<<grid, VOX_THREADS, 0, s>>>(a);
   return cudaGetLastError();
+}
+
+template <int D>
+static cudaError_t ltl_noise_d(const Geometry& g, const double* scale, Rng rng, double* E,
+                               cudaStream_t s) {
+  const int grid = (g.N + VOX_THREADS - 1) / VOX_THREADS;
+  double* Z = E + (size_t)D * g.ld;
+  k_voxel_normals<D><<<grid, VOX_THREADS, 0, s>>>(g, rng, Z);
+  k_laplacian<D><<<grid, VOX_THREADS, 0, s>>>(g, Z, E, scale);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ltl_noise(const Geometry& g, int D, const double* scale, Rng rng, double* E,
+                             cudaStream_t s) {
+  if (g.N <= 0) return cudaSuccess;
+  switch (D) {
+#define CASE(k) case k: return ltl_noise_d<k>(g, scale, rng, E, s);
+    BFMRI_K_CASES(CASE)
+#undef CASE
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t launch_apply(const ApplyArgs& a, cudaStream_t s) {

@@ -1027,6 +1027,222 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_stream(PcgArgs a) {
 
 
 // ---------------------------------------------------------------------------------------
+// The L'L prior (D_w = L'L): the streaming recurrence of k_pcg_stream with a two-pass
+// operator. A product B~ v first forms t = L v over every voxel, then, after a grid barrier,
+// (B~ v)_n = B_n v_n + scale .* (L t)_n: each product costs one more barrier, and its stencil
+// reaches the neighbours' neighbours (25 points in 3D) through t. Block-Jacobi (blocks plus
+// diag(scale) times the diagonal of L'L) or no preconditioner.
+// ---------------------------------------------------------------------------------------
+template <int D>
+__global__ void __launch_bounds__(PCG_THREADS) k_pcg_ltl(PcgArgs a) {
+  __shared__ Shared sh;
+  grid_barrier_start(a.bar);
+  __shared__ double cwd[6];
+  if (threadIdx.x == 0) slot_weights(a, cwd);
+  __syncthreads();
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nth = gridDim.x * blockDim.x;
+  const size_t ld = a.ld;
+  const bool pre = a.mfac != nullptr;
+  double s[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) s[k] = __ldg(a.scale + k);
+  double* R = a.r;
+  double* U = a.u;
+  double* Wv = a.w;
+  double* Pv = a.p;
+  double* Sv = a.s;
+  double* Tv = a.t;
+  auto bar = [&]() -> bool {
+    if (a.skip_block == (int)blockIdx.x) return false;
+    return grid_sync(a.bar, &sh.flag);
+  };
+  // sum_m c_m V[m] over the in-mask neighbours of n, and the weighted degree
+  auto nsum = [&](int n, const double* V, double* sum) -> double {
+    double deg = 0.0;
+#pragma unroll
+    for (int k = 0; k < D; ++k) sum[k] = 0.0;
+#pragma unroll
+    for (int d = 0; d < 6; ++d) {
+      const int m = d < a.ndir ? __ldg(a.nbr + (size_t)d * ld + n) : -1;
+      if (m >= 0) {
+        deg += cwd[d];
+#pragma unroll
+        for (int k = 0; k < D; ++k) sum[k] += cwd[d] * ldx(V + (size_t)k * ld + m);
+      }
+    }
+    return deg;
+  };
+  // pass 1 of a product: t = L V for every voxel (V complete: a barrier precedes)
+  auto lap_pass = [&](const double* V) {
+    for (int n = tid; n < a.N; n += nth) {
+      double sum[D];
+      const double deg = nsum(n, V, sum);
+#pragma unroll
+      for (int k = 0; k < D; ++k) Tv[(size_t)k * ld + n] = deg * ldx(V + (size_t)k * ld + n) - sum[k];
+    }
+  };
+  // pass 2 at voxel n: out = B_n v + scale .* (L t)_n (t complete: a barrier precedes)
+  auto op_at = [&](int n, const double* v, double* out) {
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      double acc = 0.0;
+#pragma unroll
+      for (int j = 0; j < D; ++j) acc += __ldg(a.blocks + (size_t)(i >= j ? tri(i, j) : tri(j, i)) * ld + n) * v[j];
+      out[i] = acc;
+    }
+    double sum[D];
+    const double deg = nsum(n, Tv, sum);
+#pragma unroll
+    for (int k = 0; k < D; ++k) out[k] += s[k] * (deg * ldx(Tv + (size_t)k * ld + n) - sum[k]);
+  };
+  auto precond = [&](int n, const double* rn, double* un) {
+    if (pre) {
+      minv<D, double>(a.mfac + n, (int)ld, rn, un);
+    } else {
+#pragma unroll
+      for (int k = 0; k < D; ++k) un[k] = rn[k];
+    }
+  };
+  // r = b - B~ x, u = M^-1 r (published); then w = B~ u and the partials
+  auto restart = [&](double* tot) -> bool {
+    lap_pass(a.x);
+    if (!bar()) return false;
+    for (int n = tid; n < a.N; n += nth) {
+      double xn[D], ax[D], rn[D], un[D];
+#pragma unroll
+      for (int k = 0; k < D; ++k) xn[k] = ldx(a.x + (size_t)k * ld + n);
+      op_at(n, xn, ax);
+#pragma unroll
+      for (int k = 0; k < D; ++k) rn[k] = __ldg(a.b + (size_t)k * ld + n) - ax[k];
+      precond(n, rn, un);
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        R[(size_t)k * ld + n] = rn[k];
+        U[(size_t)k * ld + n] = un[k];
+        Pv[(size_t)k * ld + n] = 0.0;
+        Sv[(size_t)k * ld + n] = 0.0;
+      }
+    }
+    if (!bar()) return false;
+    lap_pass(U);
+    if (!bar()) return false;
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int n = tid; n < a.N; n += nth) {
+      double un[D], wn[D];
+#pragma unroll
+      for (int k = 0; k < D; ++k) un[k] = U[(size_t)k * ld + n];
+      op_at(n, un, wn);
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        const double rk = R[(size_t)k * ld + n], bk = __ldg(a.b + (size_t)k * ld + n);
+        Wv[(size_t)k * ld + n] = wn[k];
+        v[0] += rk * un[k];
+        v[1] += wn[k] * un[k];
+        v[2] += rk * rk;
+        v[3] += bk * bk;
+      }
+    }
+    return grid_allreduce4(a.bar, a.part, a.part1, v, sh.red, sh.ints, tot);
+  };
+
+  double tot[4];
+  if (!restart(tot)) return;
+  double gam = tot[0], del = tot[1], rr = tot[2];
+  const double bb = tot[3];
+  const double tol2 = a.delta * a.delta * bb;
+  const double rel0 = bb > 0.0 ? sqrt(rr / bb) : 0.0;
+  int it = 0, restarts = 0, status = 0;
+  if (!(isfinite(gam) && isfinite(del) && isfinite(bb))) status = 7;
+  if (status == 0 && bb == 0.0) {
+    for (int n = tid; n < a.N; n += nth)
+#pragma unroll
+      for (int k = 0; k < D; ++k) a.x[(size_t)k * ld + n] = 0.0;
+  }
+  bool done = status != 0 || bb == 0.0 || rr <= tol2;
+  double alpha = (del > 0.0) ? gam / del : 0.0, beta = 0.0;
+  double rgam = 0.0, ralpha = 0.0;
+  cg_recips(gam, del, rgam, ralpha);
+  if (!done && !(del > 0.0)) { status = 3; done = true; }
+  while (!done) {
+    for (int n = tid; n < a.N; n += nth) {
+      double rn[D], un[D], pk[D], sk[D], xk[D], wk[D];
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        const size_t o = (size_t)k * ld + n;
+        un[k] = U[o];
+        pk[k] = Pv[o];
+        wk[k] = Wv[o];
+        sk[k] = Sv[o];
+        xk[k] = a.x[o];
+        rn[k] = R[o];
+      }
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        pk[k] = un[k] + beta * pk[k];
+        sk[k] = wk[k] + beta * sk[k];
+        xk[k] += alpha * pk[k];
+        rn[k] -= alpha * sk[k];
+      }
+      precond(n, rn, un);
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        const size_t o = (size_t)k * ld + n;
+        Pv[o] = pk[k];
+        Sv[o] = sk[k];
+        a.x[o] = xk[k];
+        R[o] = rn[k];
+        U[o] = un[k];
+      }
+    }
+    if (!bar()) return;
+    lap_pass(U);
+    if (!bar()) return;
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int n = tid; n < a.N; n += nth) {
+      double un[D], wn[D], rk[D];
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        un[k] = U[(size_t)k * ld + n];
+        rk[k] = R[(size_t)k * ld + n];
+      }
+      op_at(n, un, wn);
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        v[0] += rk[k] * un[k];
+        v[1] += wn[k] * un[k];
+        v[2] += rk[k] * rk[k];
+        Wv[(size_t)k * ld + n] = wn[k];
+      }
+    }
+    if (!grid_allreduce4(a.bar, a.part, a.part1, v, sh.red, sh.ints, tot)) return;
+    ++it;
+    rr = tot[2];
+    cg_scalar_step(sh, tot[0], tot[1], rr, tol2, it, a.max_iter, alpha, beta, gam, rgam, ralpha);
+    const int code = sh.code;
+    __syncthreads();
+    if (code == 7) { status = 7; break; }
+    if (code == 3) { status = 3; break; }
+    if (code == 1) {
+      // x was last updated before the reducing barrier above, so it is complete
+      if (!restart(tot)) return;
+      gam = tot[0];
+      del = tot[1];
+      rr = tot[2];
+      if (rr <= tol2) break;
+      if (it >= a.max_iter) { status = 4; break; }
+      ++restarts;
+      alpha = del > 0.0 ? gam / del : 0.0;
+      beta = 0.0;
+      cg_recips(gam, del, rgam, ralpha);
+      if (!(del > 0.0)) { status = 3; break; }
+      continue;
+    }
+  }
+  write_ctrl(a, it, restarts, rr, bb, rel0, status);
+}
+
+// ---------------------------------------------------------------------------------------
 // Mixed precision (resident): FP64 iterative refinement around FP32 CG-CG inner solves.
 //   outer: r = b - B~ x (FP64 blocks, FP64 arithmetic), stop when ||r|| <= delta ||b||;
 //   inner: B~ d = r in FP32 (FP32 blocks, preconditioner and vectors) to ||r_in|| <=
@@ -2849,15 +3065,17 @@ cudaError_t launch_resident(const PcgArgs& a, cudaStream_t stream, int* grid_out
 template <int D>
 static cudaError_t launch_d(const PcgArgs& a, cudaStream_t stream, int* grid_out) {
   if constexpr (D <= RES_MAX_D) {
-    if (a.allow_resident) {
+    if (a.allow_resident && !a.ltl) {
       bool launched = false;
       cudaError_t e = launch_resident<D>(a, stream, grid_out, &launched);
       if (launched || e != cudaSuccess) return e;
     }
   }
   const int nsm = capped_sms(a.sm_cap);
-  const void* kern = a.mixed ? (a.reduced ? (const void*)k_pcg_mixed_stream_rb<D> : (const void*)k_pcg_mixed_stream<D>)
-                             : (const void*)k_pcg_stream<D>;
+  if (a.ltl && (a.mixed || a.ssor || a.reduced || a.t == nullptr)) return cudaErrorInvalidValue;
+  const void* kern = a.ltl ? (const void*)k_pcg_ltl<D>
+                     : a.mixed ? (a.reduced ? (const void*)k_pcg_mixed_stream_rb<D> : (const void*)k_pcg_mixed_stream<D>)
+                               : (const void*)k_pcg_stream<D>;
   int per_sm = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, PCG_THREADS, 0);
   if (e != cudaSuccess) return e;
@@ -2875,12 +3093,14 @@ static cudaError_t launch_d(const PcgArgs& a, cudaStream_t stream, int* grid_out
 
 template <int D>
 static int max_grid_d() {
-  int p1 = 0, p2 = 0, p3 = 0;
+  int p1 = 0, p2 = 0, p3 = 0, p4 = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p1, k_pcg_stream<D>, PCG_THREADS, 0);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p2, k_pcg_mixed_stream<D>, PCG_THREADS, 0);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p3, k_pcg_mixed_stream_rb<D>, PCG_THREADS, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p4, k_pcg_ltl<D>, PCG_THREADS, 0);
   int per_sm = p1 > p2 ? p1 : p2;
   per_sm = per_sm > p3 ? per_sm : p3;
+  per_sm = per_sm > p4 ? per_sm : p4;
   return num_sms() * (per_sm > 1 ? per_sm : 1);
 }
 

@@ -89,6 +89,20 @@ __device__ __forceinline__ double degree(const Geometry& g, int n) {
   return deg;
 }
 
+// diagonal of L'L at voxel n (L the weighted graph Laplacian): deg_n^2 + sum of the squared
+// weights of the voxel's edges (column n of L holds deg_n and -c at each neighbour)
+__device__ __forceinline__ double ltl_diagonal(const Geometry& g, int n) {
+  double deg = 0.0, c2 = 0.0;
+  for (int d = 0; d < g.ndir; ++d) {
+    if (__ldg(g.nbr + (size_t)d * g.ld + n) >= 0) {
+      const double c = g.cw[d >> 1];
+      deg += c;
+      c2 += c * c;
+    }
+  }
+  return deg * deg + c2;
+}
+
 // Quadratic-form weights of the lagged X products for the lag pairs p <= q, filled by the
 // whole CTA (the caller synchronises before use): Q[syy_index(p, q)][tri(i, j)] is
 // Sxx[p][q][i][i] on the diagonal and Sxx[p][q][i][j] + Sxx[p][q][j][i] below it, so that
@@ -236,7 +250,10 @@ struct AssembleArgs {
   const double* Cmom;   // W system: [n_syy(P)][ld] E[c_p c_q] over A samples, replaces c c'
   const double* Gin;    // A system: [n_syy(P)][ld] lagged residual Gram averaged over W samples
   double* ldata;        // [ntri(D)][ld] Cholesky factor of the data block (or null)
-  const double* edge;   // [3][D][ld] pre-generated edge terms (launch_edge_noise), or null
+  const double* edge;   // [3][D][ld] pre-generated edge terms (launch_edge_noise), or null;
+                        // with ltl, [D][ld] prior terms of the perturbation (launch_ltl_noise)
+  int ltl;              // W system under the L'L prior: D_w = L'L in the preconditioner's
+                        // diagonal; the perturbation's prior part is read from edge (required)
 };
 
 // E[d][k][n] = sqrt(scale_k) z1_k for the edge from voxel n in direction +d (zero when absent):
@@ -247,6 +264,10 @@ cudaError_t launch_advance_counter(uint32_t* p, cudaStream_t s);
 cudaError_t launch_edge_noise(const Geometry& g, int D, const double* scale, Rng rng, double* E,
                               cudaStream_t s);
 cudaError_t launch_assemble_w(const AssembleArgs& a, cudaStream_t s);
+// The L'L prior's part of the perturbation: E[k][n] = sqrt(scale_k) (L z1_k)_n with z1_k one
+// normal per voxel (site lattice-linear * 4 + 0, lane k); uses E[D .. 2D) as scratch.
+cudaError_t launch_ltl_noise(const Geometry& g, int D, const double* scale, Rng rng, double* E,
+                             cudaStream_t s);
 cudaError_t launch_assemble_a(const AssembleArgs& a, cudaStream_t s);
 
 // lambda_n ~ Ga(1/(1/u1 + RSS_n/2), (T-P)/2 + u2) from the Gram of launch_assemble_a.
@@ -273,6 +294,7 @@ struct HyperArgs {
   double* Q_out;        // [D] (may be null)
   Rng rng;
   int* exhausted;
+  int ltl;              // quadratic forms |L v_k|^2 of the L'L prior instead of the edge sums
 };
 cudaError_t launch_hyper(const HyperArgs& a, cudaStream_t s);
 int hyper_grid(int N);
@@ -285,6 +307,7 @@ struct ApplyArgs {
   const double* scale;
   const double* x;
   double* y;
+  double* t;            // [D][ld] scratch for L x under the L'L prior, or null (graph Laplacian)
 };
 cudaError_t launch_apply(const ApplyArgs& a, cudaStream_t s);
 

@@ -80,6 +80,10 @@ struct PcgArgs {
                          // (k_pcg_rbp), otherwise lane pairs (k_pcg_rbp2) when pair_slots is set
   int pair_per;          // the voxels per CTA that pair_slots was computed for
   int pair_slots;        // lane pairs per CTA: the most red, or black, voxels of any CTA
+  // the L'L prior (D_w = L'L, L the weighted graph Laplacian): k_pcg_ltl, block-Jacobi or no
+  // preconditioner, FP64 streaming; t is a [D][ld] plane for L v
+  int ltl;
+  double* t;
 };
 
 // Voxels per CTA of the resident solvers for N voxels on at most sm_cap SMs (0 = all): the

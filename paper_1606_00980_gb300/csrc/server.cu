@@ -229,6 +229,11 @@ bfmri_status bfmri_server_submit(bfmri_server* s, const bfmri_request* req, long
   j->req = *req;
   j->N = N;
   j->bytes = bfmri_request_device_bytes(N, req->T, req->K, req->P, req->y_dtype, req->opt.precision);
+  if (req->opt.w_prior == BFMRI_PRIOR_LTL && N > 0) {
+    // the L'L prior's plane for L v ([K][ld] doubles), with the same margin
+    const size_t lt = (((size_t)req->K * (((size_t)N + 31) & ~size_t(31)) * 8 + 255) & ~size_t(255));
+    j->bytes += lt + lt / 32;
+  }
   if (req->opt.precond == BFMRI_PRECOND_MULTIGRID && N > 0) {
     // the hierarchy a multigrid request builds on its first solve, with the same margin
     const size_t mg = bfmri::mg_request_bytes(req->lat, req->mask, std::max(req->K, req->P));
