@@ -805,8 +805,8 @@ def run_chains(args, w, flush, stream, single_value, n_chains=8):
 
 def run_precond_compare(args, w, n_draws=10):
     """W and A solves of the headline workload with each preconditioner (after 3 sweeps from
-    the prior means, same state and random numbers for all): PCG iterations and solve time
-    per draw (CUDA events around every launch)."""
+    the prior means, same state and random numbers for all), and with the L'L prior of W:
+    PCG iterations and solve time per draw (CUDA events around every launch)."""
     import torch
 
     from paper_1606_00980_gb300 import bfmri
@@ -825,7 +825,11 @@ def run_precond_compare(args, w, n_draws=10):
                                                    precision=bfmri.PREC_MIXED)),
              ("mixed_rb_reduced_resident", dict(precond=bfmri.PRECOND_RB_REDUCED,
                                                 precision=bfmri.PREC_MIXED)),
-             ("multigrid", dict(precond=bfmri.PRECOND_MULTIGRID))]
+             ("multigrid", dict(precond=bfmri.PRECOND_MULTIGRID)),
+             # the L'L prior of W (25-point stencil, two-pass streaming PCG): another model,
+             # so its chain state and iteration counts are its own
+             ("ltl_prior_block_jacobi_streaming", dict(precond=bfmri.PRECOND_BLOCK_JACOBI,
+                                                       w_prior=bfmri.PRIOR_LTL))]
     out = {}
     for name, opts in cases:
         m = Model.from_workload(w, delta=1e-8, seed=2024, profile=1, **opts)
