@@ -24,10 +24,21 @@ import scipy.sparse as sp
 
 
 class Lattice:
-    def __init__(self, mask: np.ndarray, neighbourhood: int, weights=(1.0, 1.0, 1.0)):
+    def __init__(self, mask: np.ndarray, neighbourhood: int, weights=(1.0, 1.0, 1.0),
+                 edge_factors=None):
+        """edge_factors: optional per-edge factors of C, shape (3, nz, ny, nx) (or (3, sites)):
+        entry [d, site] multiplies the weight of the edge from that site along +d, so that
+        C_ee = weights[d] * edge_factors[d, lattice-linear(i)] for the edge (i, i + stride(d)),
+        a general diagonal C; None is all ones."""
         self.weights = np.asarray(weights, dtype=np.float64)
         if self.weights.shape != (3,) or not np.all(self.weights > 0):
             raise ValueError("weights: three positive edge weights (x, y, z)")
+        self.edge_factors = None
+        if edge_factors is not None:
+            f = np.asarray(edge_factors, dtype=np.float64).reshape(3, -1)
+            if not np.all(f > 0):
+                raise ValueError("edge_factors must be positive")
+            self.edge_factors = f
         mask = np.asarray(mask)
         if mask.ndim == 2:
             mask = mask[None]
@@ -83,7 +94,11 @@ class Lattice:
 
     def edge_weights(self):
         """C_ee for the edges in edges() order."""
-        return self.weights[self.edges()[:, 2]]
+        e = self.edges()
+        c = self.weights[e[:, 2]]
+        if self.edge_factors is not None:
+            c = c * self.edge_factors[e[:, 2], self.lin[e[:, 0]]]
+        return c
 
     def Gw(self):
         """C^(1/2) G_w: row e of G_w times sqrt(C_ee) (the form Algorithm 2 uses)."""
@@ -116,7 +131,12 @@ class Lattice:
             keep = nb >= 0
             rows.append(np.flatnonzero(keep))
             cols.append(nb[keep])
-            vals.append(np.full(int(keep.sum()), self.weights[idx // 2]))
+            c = np.full(int(keep.sum()), self.weights[idx // 2])
+            if self.edge_factors is not None:
+                # the +d edge of voxel i is stored at i, the -d edge at the neighbour
+                low = self.lin[keep] if idx % 2 == 0 else self.lin[nb[keep]]
+                c = c * self.edge_factors[idx // 2, low]
+            vals.append(c)
         rows = np.concatenate(rows)
         cols = np.concatenate(cols)
         adj = sp.csr_matrix((np.concatenate(vals), (rows, cols)), shape=(self.N, self.N))

@@ -254,7 +254,7 @@ def quad_forms_edges(lat: Lattice, V):
     (D = G'CG, Eq. 6-7 and the Discussion's WGL form)."""
     E = lat.edges()
     diff = V[:, E[:, 0]] - V[:, E[:, 1]]
-    return (lat.weights[E[:, 2]][None, :] * diff * diff).sum(axis=1)
+    return (lat.edge_weights()[None, :] * diff * diff).sum(axis=1)
 
 
 def quad_forms_ltl(lat: Lattice, V):

@@ -145,10 +145,10 @@ def symmetric_gs(level: Level, b):
 
 def coarse_laplacian(coords_c, agg, lat: Lattice):
     """The weighted coarse-graph Laplacian built directly from the fine edges: every fine edge
-    (i, j) along direction d joining two different aggregates adds its weight c_d to the
+    (i, j) joining two different aggregates adds its weight C_ee to the
     coupling of the two aggregates (for the Galerkin pin)."""
     E = lat.edges()
-    w = lat.weights[E[:, 2]]
+    w = lat.edge_weights()
     a, b = agg[E[:, 0]], agg[E[:, 1]]
     keep = a != b
     nc = len(coords_c)

@@ -94,9 +94,9 @@ def ssor_apply_sweeps(lat: Lattice, blocks, scale, v_nk, omega=1.0):
     col = colours(lat)
     diag = blocks + lat.degree()[:, None, None] * np.diag(scale)[None]
     nbrs = [[] for _ in range(N)]
-    for i, j, d in lat.edges():
-        nbrs[i].append((j, lat.weights[d]))
-        nbrs[j].append((i, lat.weights[d]))
+    for (i, j, d), c in zip(lat.edges(), lat.edge_weights()):
+        nbrs[i].append((j, c))
+        nbrs[j].append((i, c))
     v = np.asarray(v_nk, dtype=float)
     z = np.zeros((N, D))
     order = [n for n in range(N) if col[n] == 0] + [n for n in range(N) if col[n] == 1]
