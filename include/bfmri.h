@@ -260,6 +260,23 @@ bfmri_status bfmri_precompute_stats(bfmri_handle* h);
  * per voxel first Syy (p <= q, row-major over p), then Sxy in (p, q, k) order. */
 bfmri_status bfmri_get_stats(bfmri_handle* h, double* out);
 
+/* Per-edge weights of the spatial prior: a general diagonal C in D_w = G_w' C G_w (Eq. 7
+ * with C the edge weights of the WGL prior in the Discussion; here one weight per edge instead
+ * of per direction). factors is host memory, [3][nx*ny*nz] float32, indexed by direction
+ * (x, y, z) and lattice-linear site x + nx (y + ny z): entry [d][site] multiplies
+ * options.edge_weight[d] for the edge from that site to its +d neighbour; entries of
+ * sites outside the mask or of edges leaving it are not read, the z plane is not read with
+ * the 4-neighbourhood. Each factor is rounded to the nearest BF16 (ties to even) and kept on
+ * the device, 2 bytes per voxel and direction; the rounded value is the factor the model
+ * uses everywhere (W and A precisions, the perturbation's sqrt(C) G_w noise of Algorithm 2,
+ * the alpha and beta quadratic forms). The caller keeps ownership of factors. NULL removes
+ * the factors (back to per-direction weights). Needs the graph-Laplacian prior, precision
+ * FP64 and precond BLOCK_JACOBI or NONE (the streaming solver), else INVALID_ARG; factors
+ * must be positive and finite, else INVALID_ARG with nothing changed. With factors set,
+ * grouped sweeps, probes, SVB steps and the log joint reject the handle with INVALID_ARG.
+ * Drops a captured sweep graph. Errors: INVALID_ARG, OOM, CUDA. */
+bfmri_status bfmri_set_edge_factors(bfmri_handle* h, const float* factors);
+
 /* Sets / reads the chain state (any pointer may be NULL to leave that part unchanged / not
  * read). Values are validated: lambda, alpha, beta > 0 and finite. */
 bfmri_status bfmri_set_state(bfmri_handle* h, const double* W, const double* A,

@@ -113,6 +113,7 @@ SIGNATURES = [
     ("bfmri_sizes", C.c_int, [_h, _P(C.c_int), _P(C.c_int), _P(C.c_int), _P(C.c_int)]),
     ("bfmri_precompute_stats", C.c_int, [_h]),
     ("bfmri_get_stats", C.c_int, [_h, _dp]),
+    ("bfmri_set_edge_factors", C.c_int, [_h, _P(C.c_float)]),
     ("bfmri_set_state", C.c_int, [_h, _dp, _dp, _dp, _dp, _dp]),
     ("bfmri_get_state", C.c_int, [_h, _dp, _dp, _dp, _dp, _dp]),
     ("bfmri_sample_W", C.c_int, [_h, C.c_uint64, _dp, _P(bfmri_solve_info)]),
@@ -429,6 +430,7 @@ class Model:
         N, T, Kc, Pc = C.c_int(), C.c_int(), C.c_int(), C.c_int()
         _check(self.lib.bfmri_sizes(self.handle, C.byref(N), C.byref(T), C.byref(Kc), C.byref(Pc)), self.handle)
         self.N, self.T, self.K, self.P = N.value, T.value, Kc.value, Pc.value
+        self.sites = int(np.prod(lattice[:3]))
 
     @classmethod
     def from_workload(cls, w, **opt_fields):
@@ -472,6 +474,17 @@ class Model:
         out = np.empty((self.N, from_s))
         self._c(self.lib.bfmri_get_stats(self.handle, _ptr(out)))
         return out
+
+    def set_edge_factors(self, factors):
+        """Per-edge factors of C, shape (3, nz, ny, nx) (or (3, nx*ny*nz)), entry [d, site]
+        for the +d edge from that site; None removes them. Stored as BF16."""
+        if factors is None:
+            self._c(self.lib.bfmri_set_edge_factors(self.handle, None))
+            return
+        f = np.ascontiguousarray(np.asarray(factors, dtype=np.float32).reshape(3, -1))
+        if f.shape[1] != self.sites:
+            raise ValueError("edge factors: shape (3, nz, ny, nx)")
+        self._c(self.lib.bfmri_set_edge_factors(self.handle, f.ctypes.data_as(_P(C.c_float))))
 
     def set_state(self, W=None, A=None, lam=None, alpha=None, beta=None):
         arrs = [None if v is None else _f64(v) for v in (W, A, lam, alpha, beta)]

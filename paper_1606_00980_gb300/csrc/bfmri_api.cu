@@ -237,6 +237,7 @@ struct bfmri_handle {
   std::map<int, int> pair_slots;            // voxels per CTA -> lane pairs of k_pcg_rbp2
   double* d_ldm = nullptr;                  // log det M of a probe set riding with a group sweep
   double* d_lt = nullptr;                   // [K][ld] L v of the L'L prior's products
+  unsigned short* d_ce = nullptr;           // [3][ld] BF16 per-edge factors of C, or null
   // multigrid hierarchy (BFMRI_PRECOND_MULTIGRID), built on the first multigrid solve:
   // levels 1..mg_L-1 plus level 0's slot weights and aggregate map
   int mg_L = 0;
@@ -419,6 +420,7 @@ Geometry geom(const bfmri_handle* h) {
   g.stride[1] = h->stride[1];
   g.stride[2] = h->stride[2];
   for (int d = 0; d < 3; ++d) g.cw[d] = h->opt.edge_weight[d];
+  g.ce = h->d_ce;
   return g;
 }
 
@@ -710,6 +712,10 @@ bfmri_status run_pcg(bfmri_handle* h, int D, const double* scale, double* x, int
   if (which == 0 && h->opt.w_prior == BFMRI_PRIOR_LTL) {
     a.ltl = 1;
     a.t = h->d_lt;
+    a.allow_resident = 0;
+  }
+  if (h->d_ce) {
+    a.ce = h->d_ce;
     a.allow_resident = 0;
   }
   // lane pairs by default only for 6 x 6 blocks: measured on the whole-brain workload they
@@ -1346,6 +1352,44 @@ bfmri_status bfmri_create(const bfmri_lattice* lat, const uint8_t* mask, const d
   return BFMRI_OK;
 }
 
+namespace {
+bfmri_status drop_sweep_graph(bfmri_handle* h);
+}  // namespace
+
+bfmri_status bfmri_set_edge_factors(bfmri_handle* h, const float* factors) {
+  if (!h) return BFMRI_ERR_INVALID_ARG;
+  if (!factors) {
+    RET(drop_sweep_graph(h));
+    if (h->d_ce) dfree(h, h->d_ce);
+    h->d_ce = nullptr;
+    return BFMRI_OK;
+  }
+  if ((h->opt.precond != BFMRI_PRECOND_NONE && h->opt.precond != BFMRI_PRECOND_BLOCK_JACOBI) ||
+      h->opt.precision != BFMRI_PREC_FP64 || h->opt.w_prior != BFMRI_PRIOR_UGL)
+    return fail(h, BFMRI_ERR_INVALID_ARG,
+                "per-edge factors need block-Jacobi or no preconditioner, FP64 and the graph-Laplacian prior");
+  const size_t nsite = (size_t)h->nx * h->ny * h->nz, ld = h->ld;
+  std::vector<unsigned short> planes(3 * ld, (unsigned short)0x3F80);   // BF16 1.0 in the padding
+  for (int d = 0; d < h->ndir / 2; ++d)   // the z plane is not read with 4 neighbours
+    for (int n = 0; n < h->N; ++n) {
+      const float f = factors[(size_t)d * nsite + (size_t)h->lin_host[n]];
+      if (!(f > 0.0f) || !std::isfinite(f)) return fail(h, BFMRI_ERR_INVALID_ARG, "edge factors must be positive and finite");
+      // round to the nearest BF16, ties to even
+      uint32_t u;
+      memcpy(&u, &f, 4);
+      u += 0x7FFFu + ((u >> 16) & 1u);
+      planes[(size_t)d * ld + n] = (unsigned short)(u >> 16);
+    }
+  RET(drop_sweep_graph(h));
+  if (!h->d_ce) {
+    h->d_ce = (unsigned short*)dalloc(h, planes.size() * sizeof(unsigned short));
+    if (!h->d_ce) return fail(h, BFMRI_ERR_OOM, "edge factor allocation failed");
+  }
+  CU(h, cudaMemcpyAsync(h->d_ce, planes.data(), planes.size() * sizeof(unsigned short), cudaMemcpyHostToDevice, h->stream));
+  CU(h, cudaStreamSynchronize(h->stream));
+  return BFMRI_OK;
+}
+
 bfmri_status bfmri_destroy(bfmri_handle* h) {
   if (!h) return BFMRI_OK;
   cudaStreamSynchronize(h->stream);
@@ -1696,10 +1740,10 @@ bfmri_status group_sweep(bfmri_handle* const* hs, int n, int n_sweeps, uint64_t 
   }
   bfmri_handle* h0 = hs[0];
   for (int c = 0; c < n; ++c)
-    if (hs[c]->opt.w_prior != BFMRI_PRIOR_UGL)
-      return fail(h0, BFMRI_ERR_INVALID_ARG, "grouped chains need the graph-Laplacian prior");
-  if (gp && gp->ph && gp->ph->opt.w_prior != BFMRI_PRIOR_UGL)
-    return fail(h0, BFMRI_ERR_INVALID_ARG, "probes need the graph-Laplacian prior");
+    if (hs[c]->opt.w_prior != BFMRI_PRIOR_UGL || hs[c]->d_ce)
+      return fail(h0, BFMRI_ERR_INVALID_ARG, "grouped chains need the graph-Laplacian prior with direction weights");
+  if (gp && gp->ph && (gp->ph->opt.w_prior != BFMRI_PRIOR_UGL || gp->ph->d_ce))
+    return fail(h0, BFMRI_ERR_INVALID_ARG, "probes need the graph-Laplacian prior with direction weights");
   bool uneven = false;
   size_t ld_max = 0;
   int N_max = 0;
@@ -2227,8 +2271,8 @@ bfmri_status bfmri_svb_summary(bfmri_handle* h, int n_contrasts, const double* C
 bfmri_status bfmri_log_joint(bfmri_handle* h, double* terms) {
   RET(require_stats(h));
   if (!terms) return fail(h, BFMRI_ERR_INVALID_ARG, "terms is NULL");
-  if (h->opt.w_prior != BFMRI_PRIOR_UGL)
-    return fail(h, BFMRI_ERR_INVALID_ARG, "the log joint needs the graph-Laplacian prior");
+  if (h->opt.w_prior != BFMRI_PRIOR_UGL || h->d_ce)
+    return fail(h, BFMRI_ERR_INVALID_ARG, "the log joint needs the graph-Laplacian prior with direction weights");
   const int K = h->K, P = h->P;
   const int grid = log_joint_grid(h->N);
   if (!h->d_lj) {
@@ -2331,8 +2375,8 @@ bfmri_status bfmri_logdet_probe(bfmri_handle* h, int which, int n_probes, int la
     return fail(h, BFMRI_ERR_INVALID_ARG, "bad arguments");
   const int D = which == 0 ? h->K : h->P;
   if (D == 0) return fail(h, BFMRI_ERR_INVALID_ARG, "no AR part (P = 0)");
-  if (which == 0 && h->opt.w_prior != BFMRI_PRIOR_UGL)
-    return fail(h, BFMRI_ERR_INVALID_ARG, "W probes need the graph-Laplacian prior");
+  if ((which == 0 && h->opt.w_prior != BFMRI_PRIOR_UGL) || h->d_ce)
+    return fail(h, BFMRI_ERR_INVALID_ARG, "probes need the graph-Laplacian prior with direction weights");
   RET(begin_call(h));
   const double* scale = which == 0 ? h->d_alpha : h->d_beta;
   if (which == 1 && h->opt.ar_prior != BFMRI_AR_SPATIAL) {
@@ -2514,8 +2558,8 @@ bfmri_status bfmri_spvb_step(bfmri_handle* h, int n_samples, uint64_t counter, i
                              double* alpha_vb, double* beta_vb, bfmri_svb_info* info) {
   RET(require_stats(h));
   if (n_samples < 1 || n_samples > 4096) return fail(h, BFMRI_ERR_INVALID_ARG, "n_samples must be in [1, 4096]");
-  if (h->opt.w_prior != BFMRI_PRIOR_UGL)
-    return fail(h, BFMRI_ERR_INVALID_ARG, "the SVB step needs the graph-Laplacian prior");
+  if (h->opt.w_prior != BFMRI_PRIOR_UGL || h->d_ce)
+    return fail(h, BFMRI_ERR_INVALID_ARG, "the SVB step needs the graph-Laplacian prior with direction weights");
   const int K = h->K, P = h->P, S = n_samples;
   const size_t ld = h->ld;
   const bool spatial = h->opt.ar_prior == BFMRI_AR_SPATIAL;

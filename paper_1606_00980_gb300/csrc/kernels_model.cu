@@ -418,8 +418,10 @@ __global__ void __launch_bounds__(VOX_THREADS) k_edge_noise(Geometry g, const do
     double z[D];
     const bool has = __ldg(g.nbr + (size_t)(2 * d + 1) * g.ld + n) >= 0;
     if (has) site_normals<D>(rng, lin * 4u + (uint32_t)d, z);
+    // the edge's own factor of C (stored at its lower voxel n)
+    const double f = g.ce ? sqrt(bf16_value(__ldg(g.ce + (size_t)d * g.ld + n))) : 1.0;
 #pragma unroll
-    for (int k = 0; k < D; ++k) E[((size_t)d * D + k) * g.ld + n] = has ? sq[d][k] * z[k] : 0.0;
+    for (int k = 0; k < D; ++k) E[((size_t)d * D + k) * g.ld + n] = has ? f * sq[d][k] * z[k] : 0.0;
   }
 }
 
@@ -479,7 +481,7 @@ __global__ void __launch_bounds__(HYPER_THREADS) k_quadform(HyperArgs a) {
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       if (m[d] >= 0) {
-        const double c = a.g.cw[d];
+        const double c = slot_weight(a.g, n, 2 * d + 1, m[d]);
 #pragma unroll
         for (int k = 0; k < D; ++k) {
           const double df = v[k] - vn[d][k];
@@ -544,7 +546,7 @@ __global__ void k_apply(ApplyArgs a) {
   for (int d = 0; d < a.g.ndir; ++d) {
     const int m = a.g.nbr[(size_t)d * ld + n];
     if (m >= 0) {
-      const double c = a.g.cw[d >> 1];
+      const double c = slot_weight(a.g, n, d, m);
       deg += c;
 #pragma unroll
       for (int k = 0; k < D; ++k) sum[k] += c * V[(size_t)k * ld + m];

@@ -863,6 +863,16 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_stream(PcgArgs a) {
 #pragma unroll
     for (int d = 0; d < 6; ++d) nb[d] = d < a.ndir ? __ldg(a.nbr + (size_t)d * ld + n) : -1;
   };
+  // edge weights of voxel n's slots: the direction weights, times the per-edge factors when
+  // set (stored at each edge's lower voxel: n for +d, the neighbour for -d)
+  auto weights_at = [&](int n, const int* nb, double* c6) {
+#pragma unroll
+    for (int d = 0; d < 6; ++d) {
+      c6[d] = cwd[d];
+      if (a.ce && nb[d] >= 0)
+        c6[d] *= (double)__uint_as_float((unsigned)__ldg(a.ce + (size_t)(d >> 1) * ld + ((d & 1) ? n : nb[d])) << 16);
+    }
+  };
   auto precond = [&](int n, const double* rn, double* un) {
     if (pre) {
       minv<D, double>(a.mfac + n, (int)ld, rn, un);
@@ -891,7 +901,9 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_stream(PcgArgs a) {
       double xn[D], ax[D], rn[D], un[D];
 #pragma unroll
       for (int k = 0; k < D; ++k) xn[k] = ldx(a.x + (size_t)k * ld + n);
-      amul<D, double>(a.blocks + n, (int)ld, s, nb, cwd, degree_of<double>(nb, cwd), xn, a.x, ld, ax);
+      double c6[6];
+      weights_at(n, nb, c6);
+      amul<D, double>(a.blocks + n, (int)ld, s, nb, c6, degree_of<double>(nb, c6), xn, a.x, ld, ax);
 #pragma unroll
       for (int k = 0; k < D; ++k) rn[k] = __ldg(a.b + (size_t)k * ld + n) - ax[k];
       precond(n, rn, un);
@@ -912,7 +924,9 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_stream(PcgArgs a) {
       double un[D], wn[D];
 #pragma unroll
       for (int k = 0; k < D; ++k) un[k] = U[(size_t)k * ld + n];
-      amul<D, double>(a.blocks + n, (int)ld, s, nb, cwd, degree_of<double>(nb, cwd), un, U, ld, wn);
+      double c6[6];
+      weights_at(n, nb, c6);
+      amul<D, double>(a.blocks + n, (int)ld, s, nb, c6, degree_of<double>(nb, c6), un, U, ld, wn);
 #pragma unroll
       for (int k = 0; k < D; ++k) {
         const double rk = R[(size_t)k * ld + n], bk = __ldg(a.b + (size_t)k * ld + n);
@@ -988,7 +1002,9 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_stream(PcgArgs a) {
         un[k] = U[(size_t)k * ld + n];
         rk[k] = R[(size_t)k * ld + n];
       }
-      amul<D, double>(a.blocks + n, (int)ld, s, nb, cwd, degree_of<double>(nb, cwd), un, U, ld, wn);
+      double c6[6];
+      weights_at(n, nb, c6);
+      amul<D, double>(a.blocks + n, (int)ld, s, nb, c6, degree_of<double>(nb, c6), un, U, ld, wn);
 #pragma unroll
       for (int k = 0; k < D; ++k) {
         v[0] += rk[k] * un[k];
@@ -3065,7 +3081,7 @@ cudaError_t launch_resident(const PcgArgs& a, cudaStream_t stream, int* grid_out
 template <int D>
 static cudaError_t launch_d(const PcgArgs& a, cudaStream_t stream, int* grid_out) {
   if constexpr (D <= RES_MAX_D) {
-    if (a.allow_resident && !a.ltl) {
+    if (a.allow_resident && !a.ltl && !a.ce) {
       bool launched = false;
       cudaError_t e = launch_resident<D>(a, stream, grid_out, &launched);
       if (launched || e != cudaSuccess) return e;
@@ -3073,6 +3089,7 @@ static cudaError_t launch_d(const PcgArgs& a, cudaStream_t stream, int* grid_out
   }
   const int nsm = capped_sms(a.sm_cap);
   if (a.ltl && (a.mixed || a.ssor || a.reduced || a.t == nullptr)) return cudaErrorInvalidValue;
+  if (a.ce && (a.mixed || a.ssor || a.reduced || a.ltl)) return cudaErrorInvalidValue;
   const void* kern = a.ltl ? (const void*)k_pcg_ltl<D>
                      : a.mixed ? (a.reduced ? (const void*)k_pcg_mixed_stream_rb<D> : (const void*)k_pcg_mixed_stream<D>)
                                : (const void*)k_pcg_stream<D>;

@@ -37,7 +37,22 @@ struct Geometry {
   int stride[3];      // lattice-linear strides of +x, +y, +z
   double cw[3];       // edge weights of the x, y, z directions (weighted graph Laplacian;
                       // 1, 1, 1 is the UGL prior); neighbour slot d has weight cw[d / 2]
+  const unsigned short* ce;   // [3][ld] BF16 factors of the edge from each voxel along +x, +y,
+                              // +z (a general diagonal C: C_e = cw[d] * factor), or null (all 1)
 };
+
+// the FP64 value of a BF16 number (its bits are the high half of an FP32)
+__device__ __forceinline__ double bf16_value(unsigned short b) {
+  return (double)__uint_as_float((unsigned)b << 16);
+}
+
+// weight of the edge between voxel n and its in-mask neighbour m in slot d (-x, +x, -y, +y,
+// -z, +z): the edge's factor is stored at its lower voxel, n for +d and m for -d
+__device__ __forceinline__ double slot_weight(const Geometry& g, int n, int d, int m) {
+  double c = g.cw[d >> 1];
+  if (g.ce) c *= bf16_value(__ldg(g.ce + (size_t)(d >> 1) * g.ld + ((d & 1) ? n : m)));
+  return c;
+}
 
 // ---------------------------------------------------------------------------------------
 // Algorithm 2 perturbation for one voxel: rhs += sum_k sqrt(s_k) (G' z1_k)_n over the
@@ -49,15 +64,17 @@ __device__ __forceinline__ void add_edge_noise(const Geometry& g, const Rng& rng
                                                const double* sq, double* rhs) {
   double z[D];
   for (int d = 0; d < g.ndir / 2; ++d) {
-    if (__ldg(g.nbr + (size_t)(2 * d + 1) * g.ld + n) >= 0) {
+    const int mf = __ldg(g.nbr + (size_t)(2 * d + 1) * g.ld + n);
+    if (mf >= 0) {
       site_normals<D>(rng, (uint32_t)lin * 4u + (uint32_t)d, z);
-      const double c = sqrt(g.cw[d]);
+      const double c = sqrt(slot_weight(g, n, 2 * d + 1, mf));
 #pragma unroll
       for (int k = 0; k < D; ++k) rhs[k] += c * sq[k] * z[k];
     }
-    if (__ldg(g.nbr + (size_t)(2 * d) * g.ld + n) >= 0) {
+    const int mb = __ldg(g.nbr + (size_t)(2 * d) * g.ld + n);
+    if (mb >= 0) {
       site_normals<D>(rng, (uint32_t)(lin - g.stride[d]) * 4u + (uint32_t)d, z);
-      const double c = sqrt(g.cw[d]);
+      const double c = sqrt(slot_weight(g, n, 2 * d, mb));
 #pragma unroll
       for (int k = 0; k < D; ++k) rhs[k] -= c * sq[k] * z[k];
     }
@@ -85,7 +102,10 @@ __device__ __forceinline__ void add_edge_terms(const Geometry& g, const double* 
 // weighted degree: sum of the edge weights of the in-mask neighbours
 __device__ __forceinline__ double degree(const Geometry& g, int n) {
   double deg = 0.0;
-  for (int d = 0; d < g.ndir; ++d) deg += __ldg(g.nbr + (size_t)d * g.ld + n) >= 0 ? g.cw[d >> 1] : 0.0;
+  for (int d = 0; d < g.ndir; ++d) {
+    const int m = __ldg(g.nbr + (size_t)d * g.ld + n);
+    if (m >= 0) deg += slot_weight(g, n, d, m);
+  }
   return deg;
 }
 

@@ -84,6 +84,9 @@ struct PcgArgs {
   // preconditioner, FP64 streaming; t is a [D][ld] plane for L v
   int ltl;
   double* t;
+  // per-edge factors of C ([3][ld] BF16 of the edge from each voxel along +x, +y, +z, or
+  // null): the FP64 streaming solver with block-Jacobi or no preconditioner only
+  const unsigned short* ce;
 };
 
 // Voxels per CTA of the resident solvers for N voxels on at most sm_cap SMs (0 = all): the
