@@ -13,6 +13,7 @@ normals and uniforms.
 from __future__ import annotations
 
 import numpy as np
+import scipy.sparse as sp
 
 from . import linalg, model, philox
 from .lattice import Lattice
@@ -60,11 +61,100 @@ def sample_lambda(lat, Y, X, state, seed, counter, priors=model.PRIORS, stream=0
     return lam
 
 
-def sample_alpha(lat, state, seed, counter, priors=model.PRIORS, stream=0, prior="ugl"):
+def sample_alpha(lat, state, seed, counter, priors=model.PRIORS, stream=0, prior="ugl", step=None):
+    """Gamma full conditional of alpha_k (Eq. fullcondTempa); for the anisotropic prior the
+    exchange step (exchange_alpha) with log-normal step size `step` (default 1/sqrt(N))."""
+    if prior == "aniso":
+        return exchange_alpha(lat, state, seed, counter, 1.0 / np.sqrt(lat.N) if step is None else step,
+                              priors, stream)[0]
     Q = (model.quad_forms_ltl if prior == "ltl" else model.quad_forms_edges)(lat, state["W"])
     scale, shape = model.alpha_params(Q, lat.N, priors["q1"], priors["q2"])
     a, _ = philox.gamma(seed, np.arange(len(Q)), shape, scale, counter, philox.TAG_ALPHA, stream)
     return a
+
+
+# ----------------------------------------------------------------------------------------
+# Anisotropic prior (Discussion): W_k has prior precision sum_d alpha_{d,k} L_d with
+# alpha_{x,k}, alpha_{y,k}, alpha_{z,k} random. The paper leaves its inference open because
+# the prior's determinant no longer factors out of the alpha's. The step below is the
+# exchange algorithm of Murray, Ghahramani & MacKay (UAI 2006), which needs no determinant:
+# for each k,
+#   1. propose theta'_d = theta_d exp(step eps_d) (eps_d standard normal, d in the lattice's
+#      directions; the z weight of a 4-neighbourhood lattice stays as it is);
+#   2. draw an auxiliary field w' exactly from the prior at theta' (the GMRF draw of
+#      Algorithm 2 with no data term: L(theta') w' = sum_d sqrt(theta'_d) G_d' C_d^(1/2) z);
+#   3. accept theta' with probability min(1, a),
+#        log a = sum_d [ -(theta'_d - theta_d)(Q_d(w) - Q_d(w')) / 2
+#                        + q2 (log theta'_d - log theta_d) - (theta'_d - theta_d) / q1 ],
+#      Q_d the direction-d edge sums: the likelihood ratio of (w, w') swapped between the two
+#      parameter values, with the normalising constants cancelling, times the Ga(q1, q2) prior
+#      ratio and the log-normal proposal's ratio theta'_d / theta_d.
+# The intrinsic prior is improper along the constants of each connected part of the graph;
+# w' is drawn on the complement (where it is a proper Gaussian) and Q_d does not see the
+# constants.
+# ----------------------------------------------------------------------------------------
+
+def null_projector(lat: Lattice):
+    """J = sum_c 1_c 1_c' / |c| over the connected parts of the voxel graph (the null space of
+    every L(theta) with theta > 0)."""
+    from scipy.sparse.csgraph import connected_components
+    E = lat.edges()
+    adj = sp.csr_matrix((np.ones(len(E)), (E[:, 0], E[:, 1])), shape=(lat.N, lat.N))
+    nc, lab = connected_components(adj, directed=False)
+    ind = sp.csr_matrix((np.ones(lat.N), (np.arange(lat.N), lab)), shape=(lat.N, nc))
+    sizes = np.bincount(lab, minlength=nc).astype(np.float64)
+    return (ind @ sp.diags(1.0 / sizes) @ ind.T).tocsr()
+
+
+def aux_solve(lat: Lattice, theta_k, z_k, J=None, Ls=None):
+    """L(theta_k)^+ sum_d sqrt(theta_k[d]) G_d' C_d^(1/2) z_k for one k (z_k: one value per
+    edge in edges() order). The right-hand side is orthogonal to the range of J, so
+    (L + J) x = b gives x = L^+ b."""
+    E = lat.edges()
+    J = null_projector(lat) if J is None else J
+    Ls = model.direction_laplacians(lat) if Ls is None else Ls
+    theta_k = np.asarray(theta_k, dtype=np.float64)
+    b = lat.Gw().T @ (np.sqrt(theta_k[E[:, 2]]) * z_k)
+    return linalg.exact_solve(sum(theta_k[d] * Ls[d] for d in range(3)) + J, b)
+
+
+def aux_prior_draw(lat: Lattice, theta, seed, counter, stream=0):
+    """Step 2 for all k: aux_solve with z[e, k] the normal of edge e (site lattice-linear(i) * 4
+    + d, lane k, TAG_ALPHA_AUX). Returns (K, N)."""
+    theta = np.asarray(theta, dtype=np.float64)
+    K = theta.shape[0]
+    E = lat.edges()
+    z = philox.normals(seed, lat.lin[E[:, 0]] * 4 + E[:, 2], K, counter, philox.TAG_ALPHA_AUX, stream)
+    J = null_projector(lat)
+    Ls = model.direction_laplacians(lat)
+    return np.stack([aux_solve(lat, theta[k], z[:, k], J, Ls) for k in range(K)])
+
+
+def exchange_log_ratio(theta, theta_p, Q, Qp, step_eps, nd, priors=model.PRIORS):
+    """log a of step 3 per k (theta, theta_p, Q, Qp: K x 3; step_eps = log theta_p - log theta)."""
+    dt = (theta_p - theta)[:, :nd]
+    return np.sum(-0.5 * dt * (Q - Qp)[:, :nd] + priors["q2"] * step_eps[:, :nd] - dt / priors["q1"], axis=1)
+
+
+def exchange_alpha(lat, state, seed, counter, step, priors=model.PRIORS, stream=0):
+    """One exchange step for every k. state["alpha"] is K x 3. Returns (alpha', accepted (K,),
+    details: proposal, eps, Q, Q', log a, u)."""
+    theta = np.asarray(state["alpha"], dtype=np.float64)
+    K = theta.shape[0]
+    nd = lat.neighbourhood // 2
+    eps = philox.normals(seed, np.arange(K), 3, counter, philox.TAG_ALPHA_PROP, stream)
+    se = step * eps
+    se[:, nd:] = 0.0
+    theta_p = theta * np.exp(se)
+    theta_p[:, nd:] = theta[:, nd:]
+    wp = aux_prior_draw(lat, theta_p, seed, counter, stream)
+    Q = model.quad_forms_dirs(lat, state["W"])
+    Qp = model.quad_forms_dirs(lat, wp)
+    la = exchange_log_ratio(theta, theta_p, Q, Qp, se, nd, priors)
+    u = philox.uniform_open(seed, np.arange(K), 2, counter, philox.TAG_ALPHA_PROP, stream)
+    acc = np.log(u) < la
+    new = np.where(acc[:, None], theta_p, theta)
+    return new, acc, dict(proposal=theta_p, eps=eps, Q=Q, Qp=Qp, log_a=la, u=u, aux=wp)
 
 
 def sample_beta(lat, state, seed, counter, priors=model.PRIORS, stream=0):
@@ -75,14 +165,15 @@ def sample_beta(lat, state, seed, counter, priors=model.PRIORS, stream=0):
 
 
 def gibbs_sweep(lat, Y, X, state, seed, counter, eps=0.0, spatial_ar=True,
-                priors=model.PRIORS, stream=0):
-    """W -> A -> lambda -> alpha -> beta, each conditioned on the newest values."""
+                priors=model.PRIORS, stream=0, prior="ugl", step=None):
+    """W -> A -> lambda -> alpha -> beta, each conditioned on the newest values (prior: the W
+    prior, "ugl", "ltl" or "aniso"; A keeps the graph Laplacian)."""
     s = {k: np.array(v, copy=True) for k, v in state.items()}
-    s["W"] = sample_W(lat, Y, X, s, seed, counter, eps, stream)
+    s["W"] = sample_W(lat, Y, X, s, seed, counter, eps, stream, prior)
     if s["A"].shape[0] > 0:
         s["A"] = sample_A(lat, Y, X, s, seed, counter, spatial_ar, stream)
     s["lam"] = sample_lambda(lat, Y, X, s, seed, counter, priors, stream)
-    s["alpha"] = sample_alpha(lat, s, seed, counter, priors, stream)
+    s["alpha"] = sample_alpha(lat, s, seed, counter, priors, stream, prior, step)
     if s["A"].shape[0] > 0 and spatial_ar:
         s["beta"] = sample_beta(lat, s, seed, counter, priors, stream)
     return s

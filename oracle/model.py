@@ -186,10 +186,32 @@ def prior_precision(lat: Lattice, prior="ugl"):
     raise ValueError(prior)
 
 
+def direction_laplacians(lat: Lattice):
+    """L_d = G_d' C_d G_d for d = x, y, z: the graph Laplacian of the direction-d edges alone,
+    from the incidence matrix with the other directions' rows weighted 0 (sum_d L_d = D_w).
+    The Discussion's anisotropic prior gives W_k the precision sum_d alpha_{d,k} L_d."""
+    G = lat.G()
+    e = lat.edges()
+    c = lat.edge_weights()
+    return [(G.T @ sp.diags(np.where(e[:, 2] == d, c, 0.0)) @ G).tocsr() for d in range(3)]
+
+
+def aniso_prior(lat: Lattice, scale):
+    """blockdiag_k(sum_d scale[k, d] L_d): the anisotropic prior precision of the Discussion
+    (C_k = diag(alpha_x,k I, alpha_y,k I, alpha_z,k I) between G_w' and G_w)."""
+    Ls = direction_laplacians(lat)
+    scale = np.asarray(scale, dtype=np.float64)
+    return sp.block_diag([sum(scale[k, d] * Ls[d] for d in range(3)) for k in range(scale.shape[0])],
+                         format="csr")
+
+
 def precision(lat: Lattice, blocks, scale, prior="ugl"):
-    """B~ = H' blkdiag_n(blocks_n) H + diag(scale) (x) D_w  in regressor-major order."""
+    """B~ = H' blkdiag_n(blocks_n) H + diag(scale) (x) D_w  in regressor-major order; for the
+    anisotropic prior ("aniso") scale is K x 3 and the prior part is aniso_prior()."""
     N, K, _ = blocks.shape
     H = H_perm(N, K)
+    if prior == "aniso":
+        return (H.T @ blkdiag(blocks) @ H + aniso_prior(lat, scale)).tocsr()
     return (H.T @ blkdiag(blocks) @ H + sp.kron(sp.diags(scale), prior_precision(lat, prior))).tocsr()
 
 
@@ -210,7 +232,8 @@ def perturbation(lat: Lattice, blocks, scale, seed, counter, tag, stream=0, prio
     (site = lattice-linear(n) * 4 + 3), lane k (oracle.philox.normals).
     For the L'L prior the square root of D_w = L'L is L' itself (N x N): z1[n, k] is then one
     normal per voxel (site = lattice-linear(n) * 4 + 0) and the first term sqrt(scale_k) L' z1_k,
-    whose covariance is scale_k L'L."""
+    whose covariance is scale_k L'L. For the anisotropic prior (scale K x 3) edge e of
+    direction d carries sqrt(scale[k, d]) on top of sqrt(C_ee): covariance sum_d scale[k, d] L_d."""
     N, K, _ = blocks.shape
     z2 = philox.normals(seed, lat.lin * 4 + 3, K, counter, tag, stream)
     if prior == "ltl":
@@ -222,7 +245,11 @@ def perturbation(lat: Lattice, blocks, scale, seed, counter, tag, stream=0, prio
         sites_e = lat.lin[E[:, 0]] * 4 + E[:, 2]
         z1 = philox.normals(seed, sites_e, K, counter, tag, stream)
         G = lat.Gw()
-        part1 = np.concatenate([np.sqrt(scale[k]) * (G.T @ z1[:, k]) for k in range(K)])
+        if prior == "aniso":
+            sq = np.sqrt(np.asarray(scale, dtype=np.float64)[:, E[:, 2]])   # (K, edges)
+            part1 = np.concatenate([G.T @ (sq[k] * z1[:, k]) for k in range(K)])
+        else:
+            part1 = np.concatenate([np.sqrt(scale[k]) * (G.T @ z1[:, k]) for k in range(K)])
     Lz = np.stack([np.linalg.cholesky(blocks[n]) @ z2[n] for n in range(N)])  # (N, K)
     part2 = kmajor(Lz)
     return part1 + part2, z1, z2
@@ -233,7 +260,12 @@ def perturbation_matrix(lat: Lattice, blocks, scale, prior="ugl"):
     its Gram matrix must equal B~ exactly, which is why Algorithm 2 samples correctly)."""
     N, K, _ = blocks.shape
     G = lat.D().T if prior == "ltl" else lat.Gw()
-    part1 = sp.block_diag([sp.csr_matrix(np.sqrt(scale[k]) * G.T) for k in range(K)], format="csr")
+    if prior == "aniso":
+        d = lat.edges()[:, 2]
+        part1 = sp.block_diag([(G.T @ sp.diags(np.sqrt(np.asarray(scale[k], dtype=np.float64)[d]))).tocsr()
+                               for k in range(K)], format="csr")
+    else:
+        part1 = sp.block_diag([sp.csr_matrix(np.sqrt(scale[k]) * G.T) for k in range(K)], format="csr")
     H = H_perm(N, K)
     L = blkdiag([np.linalg.cholesky(blocks[n]) for n in range(N)])
     part2 = H.T @ L @ H          # z2 indexed regressor-major here
@@ -255,6 +287,15 @@ def quad_forms_edges(lat: Lattice, V):
     E = lat.edges()
     diff = V[:, E[:, 0]] - V[:, E[:, 1]]
     return (lat.edge_weights()[None, :] * diff * diff).sum(axis=1)
+
+
+def quad_forms_dirs(lat: Lattice, V):
+    """Q[k, d] = sum over the direction-d edges of C_e (V_k,i - V_k,j)^2 (K x 3): the
+    statistics of the anisotropic prior's alpha_{d,k}."""
+    E = lat.edges()
+    diff = V[:, E[:, 0]] - V[:, E[:, 1]]
+    q = lat.edge_weights()[None, :] * diff * diff
+    return np.stack([q[:, E[:, 2] == d].sum(axis=1) for d in range(3)], axis=1)
 
 
 def quad_forms_ltl(lat: Lattice, V):

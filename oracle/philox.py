@@ -39,6 +39,8 @@ TAG_LAMBDA = 3   # lambda Gamma draws
 TAG_ALPHA = 4    # alpha Gamma draws
 TAG_BETA = 5     # beta Gamma draws
 TAG_PROBE = 6    # Rademacher probes for traces / log-determinants
+TAG_ALPHA_PROP = 7   # anisotropic prior: proposal normals (sub 0, 1) and acceptance uniform (sub 2)
+TAG_ALPHA_AUX = 8    # anisotropic prior: edge normals of the exchange step's auxiliary draw
 
 
 def philox4x32_10(c0, c1, c2, c3, k0, k1):
@@ -67,6 +69,13 @@ def key_of(seed):
 
 def c3_of(tag, stream):
     return (int(tag) << 24) | (int(stream) & 0xFFFFFF)
+
+
+def uniform_open(seed, sites, sub, counter, tag, stream):
+    """u in (0, 1] per site from words 0 and 1 of the call (site, sub, counter, tag/stream)."""
+    k0, k1 = key_of(seed)
+    w = philox4x32_10(np.asarray(sites, dtype=np.uint64), sub, counter, c3_of(tag, stream), k0, k1)
+    return (u53(w[0], w[1]) + 1.0) * 2.0 ** -53
 
 
 def u53(a, b):
