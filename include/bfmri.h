@@ -178,10 +178,33 @@ typedef struct {
                                 rows, neighbour sums and updates by components); 1 = one lane
                                 per voxel; 0 (default) = lane pairs for 6 x 6 blocks, one lane
                                 otherwise. Same iterates up to rounding. */
+  double aniso_step;         /* BFMRI_PRIOR_ANISO: standard deviation of the log-normal
+                                random-walk proposal of the exchange step (log alpha_{d,k}
+                                moves by aniso_step times a standard normal); <= 0 (default 0)
+                                means 1 / sqrt(N). */
 } bfmri_options;
 
 #define BFMRI_PRIOR_UGL 0
 #define BFMRI_PRIOR_LTL 1
+/* The anisotropic prior the Discussion proposes: the prior precision of W_k is
+ * G_w' C_k G_w with C_k = diag(alpha_x,k I, alpha_y,k I, alpha_z,k I) (times edge_weight),
+ * the alpha_{d,k} random with the Ga(q1, q2) prior of alpha. The paper leaves its inference
+ * open because the prior's determinant no longer factors out of the alphas; the alphas are
+ * updated here by the exchange algorithm (Murray, Ghahramani & MacKay, UAI 2006), which needs
+ * no determinant: per k, a log-normal random-walk proposal theta' (normals from Philox tag 7,
+ * site k, subs 0-1), an auxiliary field w' drawn from the prior at theta' by the Algorithm 2
+ * perturbation without a data term (edge normals from tag 8) and PCG from zero to delta, and
+ * acceptance when log u < log a (u from tag 7, site k, sub 2) with
+ *   log a = sum_d [ -(theta'_d - theta_d)(Q_d(w) - Q_d(w')) / 2
+ *                   + q2 (log theta'_d - log theta_d) - (theta'_d - theta_d) / q1 ],
+ * Q_d the direction-d edge sums. W is solved by FP64 streaming PCG with block-Jacobi (blocks
+ * plus diag_k sum_d alpha_{d,k} deg_d) or no preconditioner: precond BLOCK_JACOBI or NONE and
+ * precision FP64, else INVALID_ARG at create. The A prior stays the graph Laplacian. Grouped
+ * sweeps, probes, SVB steps, the log joint and per-edge factors reject it (INVALID_ARG).
+ * bfmri_set_state's alpha sets alpha_{d,k} = alpha_k for every d; bfmri_get_state's alpha
+ * returns the mean over the lattice's directions; bfmri_sample_alpha runs one exchange step
+ * for every k. */
+#define BFMRI_PRIOR_ANISO 2
 
 #define BFMRI_STATS_AUTO   0
 #define BFMRI_STATS_FP64   1
@@ -276,6 +299,21 @@ bfmri_status bfmri_get_stats(bfmri_handle* h, double* out);
  * grouped sweeps, probes, SVB steps and the log joint reject the handle with INVALID_ARG.
  * Drops a captured sweep graph. Errors: INVALID_ARG, OOM, CUDA. */
 bfmri_status bfmri_set_edge_factors(bfmri_handle* h, const float* factors);
+
+/* Anisotropic prior (BFMRI_PRIOR_ANISO only, else INVALID_ARG): sets / reads alpha_{d,k}.
+ * alpha is host memory, K x 3 row-major (x, y, z per k; the z entry of a 4-neighbourhood
+ * lattice is kept but not used); values must be positive and finite (INVALID_ARG, nothing
+ * changed). accepted (K, may be NULL) receives the exchange steps accepted per k since the
+ * handle was created. */
+bfmri_status bfmri_set_alpha_dirs(bfmri_handle* h, const double* alpha);
+bfmri_status bfmri_get_alpha_dirs(bfmri_handle* h, double* alpha, long long* accepted);
+
+/* Anisotropic prior: the last exchange step's quantities (any pointer may be NULL): Q and
+ * Q_aux (K x 3) the direction edge sums of W and of the auxiliary field, log_a (K) the log
+ * acceptance ratio, w_aux (K x N) the auxiliary field (its constant part along each
+ * connected component is whatever PCG from zero left there; the edge sums ignore it). */
+bfmri_status bfmri_aniso_last_step(bfmri_handle* h, double* Q, double* Q_aux, double* log_a,
+                                   double* w_aux);
 
 /* Sets / reads the chain state (any pointer may be NULL to leave that part unchanged / not
  * read). Values are validated: lambda, alpha, beta > 0 and finite. */

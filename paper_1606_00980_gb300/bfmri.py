@@ -24,7 +24,7 @@ STATUS_NAMES = {0: "OK", -1: "INVALID_ARG", -2: "OOM", -3: "NOT_SPD", -4: "NOT_C
                 -5: "TIMEOUT", -6: "CUDA", -7: "INTERNAL", -8: "STATE"}
 BFMRI_F32, BFMRI_F64 = 0, 1
 PRECOND_NONE, PRECOND_BLOCK_JACOBI, PRECOND_SSOR, PRECOND_RB_REDUCED, PRECOND_MULTIGRID = 0, 1, 2, 3, 4
-PRIOR_UGL, PRIOR_LTL = 0, 1
+PRIOR_UGL, PRIOR_LTL, PRIOR_ANISO = 0, 1, 2
 PREC_FP64, PREC_MIXED = 0, 1
 AR_SPATIAL, AR_INDEPENDENT = 0, 1
 Y_MASKED, Y_LATTICE = 0, 1
@@ -51,7 +51,7 @@ class bfmri_options(C.Structure):
                 ("sm_budget", C.c_int), ("ssor_omega", C.c_double),
                 ("use_graph", C.c_int), ("edge_weight", C.c_double * 3),
                 ("stats_kernel", C.c_int), ("mrhs_tile", C.c_int),
-                ("w_prior", C.c_int), ("pcg_lanes", C.c_int)]
+                ("w_prior", C.c_int), ("pcg_lanes", C.c_int), ("aniso_step", C.c_double)]
 
 
 class bfmri_solve_info(C.Structure):
@@ -114,6 +114,9 @@ SIGNATURES = [
     ("bfmri_precompute_stats", C.c_int, [_h]),
     ("bfmri_get_stats", C.c_int, [_h, _dp]),
     ("bfmri_set_edge_factors", C.c_int, [_h, _P(C.c_float)]),
+    ("bfmri_set_alpha_dirs", C.c_int, [_h, _dp]),
+    ("bfmri_get_alpha_dirs", C.c_int, [_h, _dp, _P(C.c_longlong)]),
+    ("bfmri_aniso_last_step", C.c_int, [_h, _dp, _dp, _dp, _dp]),
     ("bfmri_set_state", C.c_int, [_h, _dp, _dp, _dp, _dp, _dp]),
     ("bfmri_get_state", C.c_int, [_h, _dp, _dp, _dp, _dp, _dp]),
     ("bfmri_sample_W", C.c_int, [_h, C.c_uint64, _dp, _P(bfmri_solve_info)]),
@@ -485,6 +488,28 @@ class Model:
         if f.shape[1] != self.sites:
             raise ValueError("edge factors: shape (3, nz, ny, nx)")
         self._c(self.lib.bfmri_set_edge_factors(self.handle, f.ctypes.data_as(_P(C.c_float))))
+
+    def set_alpha_dirs(self, alpha):
+        """Anisotropic prior: alpha_{d,k} as a K x 3 array (x, y, z per k)."""
+        a = _f64(alpha, (self.K, 3))
+        self._c(self.lib.bfmri_set_alpha_dirs(self.handle, _ptr(a)))
+
+    def get_alpha_dirs(self):
+        """Anisotropic prior: (alpha K x 3, accepted exchange steps per k)."""
+        a = np.empty((self.K, 3))
+        acc = np.zeros(self.K, dtype=np.int64)
+        self._c(self.lib.bfmri_get_alpha_dirs(self.handle, _ptr(a), acc.ctypes.data_as(_P(C.c_longlong))))
+        return a, acc
+
+    def aniso_last_step(self):
+        """Anisotropic prior: dict of the last exchange step's Q, Q_aux (K x 3), log_a (K) and
+        the auxiliary field w_aux (K x N)."""
+        Q = np.empty((self.K, 3))
+        Qa = np.empty((self.K, 3))
+        la = np.empty(self.K)
+        wa = np.empty((self.K, self.N))
+        self._c(self.lib.bfmri_aniso_last_step(self.handle, _ptr(Q), _ptr(Qa), _ptr(la), _ptr(wa)))
+        return dict(Q=Q, Q_aux=Qa, log_a=la, w_aux=wa)
 
     def set_state(self, W=None, A=None, lam=None, alpha=None, beta=None):
         arrs = [None if v is None else _f64(v) for v in (W, A, lam, alpha, beta)]

@@ -226,7 +226,7 @@ struct bfmri_handle {
   double* d_edge = nullptr;   // [3][D][ld] perturbation edge terms
   unsigned int* d_bar = nullptr;
   int* d_err = nullptr;
-  PcgCtrl* d_ctrl = nullptr;  // [0] W solves, [1] A solves
+  PcgCtrl* d_ctrl = nullptr;  // [0] W solves, [1] A solves, [2] auxiliary solves (exchange step)
   int* d_flags = nullptr;     // [0] bad voxel (min index), [1] Gamma draws out of attempts
   bool stats_ready = false;
   int part_rows = 0;
@@ -238,6 +238,11 @@ struct bfmri_handle {
   double* d_ldm = nullptr;                  // log det M of a probe set riding with a group sweep
   double* d_lt = nullptr;                   // [K][ld] L v of the L'L prior's products
   unsigned short* d_ce = nullptr;           // [3][ld] BF16 per-edge factors of C, or null
+  // anisotropic prior: alpha_{d,k} and the exchange step's proposal ([3][K] each), the
+  // auxiliary field [K][ld], direction edge sums of W and of the field [2][3][K], log a [K]
+  // and accepted steps [K]
+  double *d_alpha3 = nullptr, *d_prop3 = nullptr, *d_waux = nullptr, *d_qdir = nullptr, *d_loga = nullptr;
+  long long* d_acc = nullptr;
   // multigrid hierarchy (BFMRI_PRECOND_MULTIGRID), built on the first multigrid solve:
   // levels 1..mg_L-1 plus level 0's slot weights and aggregate map
   int mg_L = 0;
@@ -523,7 +528,7 @@ bfmri_status begin_call(bfmri_handle* h) {
   if (h->deferred) return BFMRI_OK;
   CU(h, cudaMemsetAsync(h->d_bar, 0, 2 * sizeof(unsigned int), h->stream));
   CU(h, cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream));
-  CU(h, cudaMemsetAsync(h->d_ctrl, 0, 2 * sizeof(PcgCtrl), h->stream));
+  CU(h, cudaMemsetAsync(h->d_ctrl, 0, 3 * sizeof(PcgCtrl), h->stream));
   CU(h, cudaMemsetAsync(h->d_flags, 0x7f, sizeof(int), h->stream));
   CU(h, cudaMemsetAsync(h->d_flags + 1, 0, 3 * sizeof(int), h->stream));
   return BFMRI_OK;
@@ -533,7 +538,7 @@ bfmri_status begin_call(bfmri_handle* h) {
 bfmri_status end_call(bfmri_handle* h, PcgCtrl* ctrl_out /* [2] or null */, int* exhausted) {
   h->deferred = false;
   CU(h, cudaStreamSynchronize(h->stream));
-  PcgCtrl ctrl[2];
+  PcgCtrl ctrl[3];
   int flags[4], err = 0;
   CU(h, cudaMemcpy(ctrl, h->d_ctrl, sizeof(ctrl), cudaMemcpyDeviceToHost));
   CU(h, cudaMemcpy(flags, h->d_flags, sizeof(flags), cudaMemcpyDeviceToHost));
@@ -545,6 +550,7 @@ bfmri_status end_call(bfmri_handle* h, PcgCtrl* ctrl_out /* [2] or null */, int*
   if (h->opt.profile) {
     h->timing.pcg_iterations[BFMRI_T_PCG_W] += ctrl[0].iter_total;
     h->timing.pcg_iterations[BFMRI_T_PCG_A] += ctrl[1].iter_total;
+    h->timing.pcg_iterations[BFMRI_T_HYPER] += ctrl[2].iter_total;
   }
   if (exhausted) *exhausted = flags[1];
   if (err == ERR_TIMEOUT_CODE)
@@ -554,7 +560,7 @@ bfmri_status end_call(bfmri_handle* h, PcgCtrl* ctrl_out /* [2] or null */, int*
   if (flags[0] != 0x7f7f7f7f)
     return fail(h, BFMRI_ERR_NOT_SPD,
                 "per-voxel block not positive definite at voxel " + std::to_string(flags[0]));
-  for (int i = 0; i < 2; ++i) {
+  for (int i = 0; i < 3; ++i) {
     const int st = ctrl[i].status_any;
     if (st == 4) return fail(h, BFMRI_ERR_NOT_CONVERGED, "PCG reached max_iter");
     if (st == 3) return fail(h, BFMRI_ERR_NOT_SPD, "PCG breakdown (p'Bp <= 0)");
@@ -718,6 +724,11 @@ bfmri_status run_pcg(bfmri_handle* h, int D, const double* scale, double* x, int
     a.ce = h->d_ce;
     a.allow_resident = 0;
   }
+  if (h->opt.w_prior == BFMRI_PRIOR_ANISO && which != 1) {
+    // the W system (alpha_{d,k}) or the exchange step's auxiliary system (the proposal)
+    a.scale3 = which == 0 ? h->d_alpha3 : h->d_prop3;
+    a.allow_resident = 0;
+  }
   // lane pairs by default only for 6 x 6 blocks: measured on the whole-brain workload they
   // take the W solve (K = 6) from 0.414 to 0.404 ms per sweep, but the A solve (P = 3) from
   // 0.364 to 0.432 ms, where the second lane holds one component and the gathers and padded
@@ -763,7 +774,7 @@ bfmri_status run_pcg(bfmri_handle* h, int D, const double* scale, double* x, int
   a.max_grid = h->part_rows;
   h->opt.debug_skip_block = -1;  // the hook fires once
   int grid = 0;
-  Timed tm(h, which == 0 ? BFMRI_T_PCG_W : BFMRI_T_PCG_A, true, which);
+  Timed tm(h, which == 0 ? BFMRI_T_PCG_W : which == 1 ? BFMRI_T_PCG_A : BFMRI_T_HYPER, true, which);
   cudaError_t e = launch_pcg(D, a, h->stream, &grid);
   if (e != cudaSuccess) return cuda_fail(h, e, "launch_pcg");
   return BFMRI_OK;
@@ -795,6 +806,7 @@ AssembleArgs assemble_args(bfmri_handle* h, const double* scale, uint64_t counte
   a.bad_voxel = h->d_flags;
   a.ltl = tag == TAG_W && h->opt.w_prior == BFMRI_PRIOR_LTL;
   if (a.ltl) a.edge = h->d_edge;   // the prior terms, from launch_ltl_noise when perturbed
+  if (tag == TAG_W && h->opt.w_prior == BFMRI_PRIOR_ANISO) a.scale3 = h->d_alpha3;
   return a;
 }
 
@@ -806,7 +818,7 @@ bfmri_status assemble_W(bfmri_handle* h, uint64_t counter) {
   {
     Timed tm(h, BFMRI_T_ASSEMBLE_W);
     e = a.ltl ? launch_ltl_noise(a.g, h->K, h->d_alpha, a.rng, h->d_edge, h->stream)
-              : launch_edge_noise(a.g, h->K, h->d_alpha, a.rng, h->d_edge, h->stream);
+              : launch_edge_noise(a.g, h->K, h->d_alpha, a.rng, h->d_edge, h->stream, a.scale3);
     a.edge = h->d_edge;
     if (e == cudaSuccess) e = launch_assemble_w(a, h->stream);
   }
@@ -899,7 +911,74 @@ bfmri_status enqueue_summary(bfmri_handle* h) {
   return BFMRI_OK;
 }
 
+// Anisotropic prior: alpha_k as the mean of alpha_{d,k} over the lattice's directions.
+bfmri_status alpha_dir_mean(bfmri_handle* h, double* alpha) {
+  std::vector<double> a3(3 * (size_t)h->K);
+  CU(h, cudaMemcpyAsync(a3.data(), h->d_alpha3, a3.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CU(h, cudaStreamSynchronize(h->stream));
+  const int nd = h->ndir / 2;
+  for (int k = 0; k < h->K; ++k) {
+    double m = 0.0;
+    for (int d = 0; d < nd; ++d) m += a3[(size_t)d * h->K + k];
+    alpha[k] = m / nd;
+  }
+  return BFMRI_OK;
+}
+
+// The anisotropic prior's alpha step: one exchange step for every k (proposal, auxiliary
+// prior draw into d_waux through the W system's buffers, direction edge sums, acceptance).
+bfmri_status enqueue_aniso(bfmri_handle* h, uint64_t counter) {
+  const int K = h->K;
+  AnisoArgs s;
+  s.K = K;
+  s.nd = h->ndir / 2;
+  s.step = h->opt.aniso_step > 0.0 ? h->opt.aniso_step : 1.0 / sqrt((double)h->N);
+  s.q1 = h->opt.q1;
+  s.q2 = h->opt.q2;
+  s.alpha3 = h->d_alpha3;
+  s.prop3 = h->d_prop3;
+  s.Q = h->d_qdir;
+  s.Qp = h->d_qdir + 3 * K;
+  s.log_a = h->d_loga;
+  s.accepted = h->d_acc;
+  s.rng = rng_of(h, counter, TAG_ALPHA_PROP);
+  const Geometry g = geom(h);
+  cudaError_t e;
+  {
+    Timed tm(h, BFMRI_T_HYPER);
+    e = launch_aniso_propose(s, h->stream);
+    if (e == cudaSuccess)
+      e = launch_edge_noise(g, K, h->d_alpha, rng_of(h, counter, TAG_ALPHA_AUX), h->d_edge, h->stream, h->d_prop3);
+    if (e == cudaSuccess)
+      e = launch_aux_system(g, K, h->d_prop3, h->d_edge, h->d_blocks, h->d_mfac, h->d_rhs, h->d_waux, h->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(h, e, "exchange step (proposal)");
+  RET(run_pcg(h, K, h->d_alpha, h->d_waux, 2));
+  {
+    Timed tm(h, BFMRI_T_HYPER);
+    HyperArgs q;
+    q.g = g;
+    q.D = K;
+    q.part = h->d_hpart;
+    q.out = nullptr;
+    q.rng = s.rng;
+    q.exhausted = h->d_flags + 1;
+    q.ltl = 0;
+    q.dirs = 1;
+    q.V = h->d_W;
+    q.Q_out = h->d_qdir;
+    e = launch_hyper(q, h->stream);
+    q.V = h->d_waux;
+    q.Q_out = h->d_qdir + 3 * K;
+    if (e == cudaSuccess) e = launch_hyper(q, h->stream);
+    if (e == cudaSuccess) e = launch_aniso_accept(s, h->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(h, e, "exchange step (acceptance)");
+  return BFMRI_OK;
+}
+
 bfmri_status enqueue_hyper(bfmri_handle* h, uint64_t counter, bool beta) {
+  if (!beta && h->opt.w_prior == BFMRI_PRIOR_ANISO) return enqueue_aniso(h, counter);
   HyperArgs a;
   a.g = geom(h);
   a.D = beta ? h->P : h->K;
@@ -1078,6 +1157,7 @@ void bfmri_default_options(bfmri_options* o) {
   o->mrhs_tile = 0;
   o->w_prior = BFMRI_PRIOR_UGL;
   o->pcg_lanes = 0;
+  o->aniso_step = 0.0;
 }
 
 const char* bfmri_last_error(const bfmri_handle* h) {
@@ -1151,8 +1231,13 @@ bfmri_status bfmri_create(const bfmri_lattice* lat, const uint8_t* mask, const d
     if (!(o.edge_weight[d] > 0.0) || !std::isfinite(o.edge_weight[d]))
       return fail(nullptr, BFMRI_ERR_INVALID_ARG, "edge_weight must be positive and finite");
   if (o.pcg_lanes < 0 || o.pcg_lanes > 2) return fail(nullptr, BFMRI_ERR_INVALID_ARG, "pcg_lanes must be 0, 1 or 2");
-  if (o.w_prior != BFMRI_PRIOR_UGL && o.w_prior != BFMRI_PRIOR_LTL)
+  if (o.w_prior != BFMRI_PRIOR_UGL && o.w_prior != BFMRI_PRIOR_LTL && o.w_prior != BFMRI_PRIOR_ANISO)
     return fail(nullptr, BFMRI_ERR_INVALID_ARG, "unknown w_prior");
+  if (o.w_prior == BFMRI_PRIOR_ANISO &&
+      ((o.precond != BFMRI_PRECOND_NONE && o.precond != BFMRI_PRECOND_BLOCK_JACOBI) ||
+       o.precision != BFMRI_PREC_FP64 || !std::isfinite(o.aniso_step)))
+    return fail(nullptr, BFMRI_ERR_INVALID_ARG,
+                "the anisotropic prior needs block-Jacobi or no preconditioner, FP64 precision and a finite aniso_step");
   if (o.w_prior == BFMRI_PRIOR_LTL &&
       ((o.precond != BFMRI_PRECOND_NONE && o.precond != BFMRI_PRECOND_BLOCK_JACOBI) ||
        o.precision != BFMRI_PREC_FP64))
@@ -1279,14 +1364,25 @@ bfmri_status bfmri_create(const bfmri_lattice* lat, const uint8_t* mask, const d
   h->d_p0 = (double*)A((size_t)D * ld * sizeof(double));
   h->d_p1 = (double*)A((size_t)D * ld * sizeof(double));
   h->d_part = (double*)A(((size_t)maxgrid * 8 + 8) * sizeof(double));
-  h->d_hpart = (double*)A((size_t)hyper_grid(N) * D * sizeof(double));
+  // the anisotropic prior's direction edge sums keep three partials per component
+  h->d_hpart = (double*)A((size_t)hyper_grid(N) * D * (o.w_prior == BFMRI_PRIOR_ANISO ? 3 : 1) * sizeof(double));
   h->d_bar = (unsigned int*)A(2 * sizeof(unsigned int));
   h->d_err = (int*)A(sizeof(int));
-  h->d_ctrl = (PcgCtrl*)A(2 * sizeof(PcgCtrl));
+  h->d_ctrl = (PcgCtrl*)A(3 * sizeof(PcgCtrl));
   h->d_flags = (int*)A(4 * sizeof(int));
   h->d_edge = (double*)A((size_t)3 * D * ld * sizeof(double));
   if (o.w_prior == BFMRI_PRIOR_LTL) h->d_lt = (double*)A((size_t)K * ld * sizeof(double));
-  if (!h->d_edge || (o.w_prior == BFMRI_PRIOR_LTL && !h->d_lt)) {
+  if (o.w_prior == BFMRI_PRIOR_ANISO) {
+    h->d_alpha3 = (double*)A(3 * (size_t)K * sizeof(double));
+    h->d_prop3 = (double*)A(3 * (size_t)K * sizeof(double));
+    h->d_waux = (double*)A((size_t)K * ld * sizeof(double));
+    h->d_qdir = (double*)A(6 * (size_t)K * sizeof(double));
+    h->d_loga = (double*)A((size_t)K * sizeof(double));
+    h->d_acc = (long long*)A((size_t)K * sizeof(long long));
+  }
+  if (!h->d_edge || (o.w_prior == BFMRI_PRIOR_LTL && !h->d_lt) ||
+      (o.w_prior == BFMRI_PRIOR_ANISO &&
+       (!h->d_alpha3 || !h->d_prop3 || !h->d_waux || !h->d_qdir || !h->d_loga || !h->d_acc))) {
     bfmri_destroy(h);
     return fail(nullptr, BFMRI_ERR_OOM, "device allocation failed");
   }
@@ -1341,7 +1437,15 @@ bfmri_status bfmri_create(const bfmri_lattice* lat, const uint8_t* mask, const d
   if (!e) e = cudaMemcpyAsync(h->d_lam, lam0.data(), ld * sizeof(double), cudaMemcpyHostToDevice, s);
   if (!e) e = cudaMemcpyAsync(h->d_alpha, al0.data(), K * sizeof(double), cudaMemcpyHostToDevice, s);
   if (!e) e = cudaMemcpyAsync(h->d_beta, be0.data(), Pa * sizeof(double), cudaMemcpyHostToDevice, s);
-  if (!e) e = cudaMemsetAsync(h->d_ctrl, 0, 2 * sizeof(PcgCtrl), s);
+  if (!e) e = cudaMemsetAsync(h->d_ctrl, 0, 3 * sizeof(PcgCtrl), s);
+  if (!e && h->d_alpha3) {
+    std::vector<double> a3(3 * (size_t)K, o.q1 * o.q2);
+    e = cudaMemcpyAsync(h->d_alpha3, a3.data(), a3.size() * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (!e) e = cudaMemsetAsync(h->d_acc, 0, K * sizeof(long long), s);
+    if (!e) e = cudaMemsetAsync(h->d_qdir, 0, 6 * (size_t)K * sizeof(double), s);
+    if (!e) e = cudaMemsetAsync(h->d_loga, 0, K * sizeof(double), s);
+    if (!e) e = cudaMemsetAsync(h->d_waux, 0, (size_t)K * ld * sizeof(double), s);
+  }
   if (!e) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
     std::string msg = std::string("bfmri_create: ") + cudaGetErrorString(e);
@@ -1387,6 +1491,50 @@ bfmri_status bfmri_set_edge_factors(bfmri_handle* h, const float* factors) {
   }
   CU(h, cudaMemcpyAsync(h->d_ce, planes.data(), planes.size() * sizeof(unsigned short), cudaMemcpyHostToDevice, h->stream));
   CU(h, cudaStreamSynchronize(h->stream));
+  return BFMRI_OK;
+}
+
+bfmri_status bfmri_set_alpha_dirs(bfmri_handle* h, const double* alpha) {
+  if (!h) return BFMRI_ERR_INVALID_ARG;
+  if (!h->d_alpha3) return fail(h, BFMRI_ERR_INVALID_ARG, "alpha per direction needs the anisotropic prior");
+  if (!alpha || !all_positive(alpha, 3 * (size_t)h->K))
+    return fail(h, BFMRI_ERR_INVALID_ARG, "alpha per direction must be positive and finite");
+  std::vector<double> a3(3 * (size_t)h->K);
+  for (int k = 0; k < h->K; ++k)
+    for (int d = 0; d < 3; ++d) a3[(size_t)d * h->K + k] = alpha[(size_t)k * 3 + d];
+  CU(h, cudaMemcpyAsync(h->d_alpha3, a3.data(), a3.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  CU(h, cudaStreamSynchronize(h->stream));
+  return BFMRI_OK;
+}
+
+bfmri_status bfmri_get_alpha_dirs(bfmri_handle* h, double* alpha, long long* accepted) {
+  if (!h) return BFMRI_ERR_INVALID_ARG;
+  if (!h->d_alpha3) return fail(h, BFMRI_ERR_INVALID_ARG, "alpha per direction needs the anisotropic prior");
+  std::vector<double> a3(3 * (size_t)h->K);
+  CU(h, cudaMemcpyAsync(a3.data(), h->d_alpha3, a3.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  if (accepted)
+    CU(h, cudaMemcpyAsync(accepted, h->d_acc, h->K * sizeof(long long), cudaMemcpyDeviceToHost, h->stream));
+  CU(h, cudaStreamSynchronize(h->stream));
+  if (alpha)
+    for (int k = 0; k < h->K; ++k)
+      for (int d = 0; d < 3; ++d) alpha[(size_t)k * 3 + d] = a3[(size_t)d * h->K + k];
+  return BFMRI_OK;
+}
+
+bfmri_status bfmri_aniso_last_step(bfmri_handle* h, double* Q, double* Q_aux, double* log_a, double* w_aux) {
+  if (!h) return BFMRI_ERR_INVALID_ARG;
+  if (!h->d_alpha3) return fail(h, BFMRI_ERR_INVALID_ARG, "the exchange step needs the anisotropic prior");
+  const int K = h->K;
+  std::vector<double> q(6 * (size_t)K);
+  CU(h, cudaMemcpyAsync(q.data(), h->d_qdir, q.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  if (log_a) CU(h, cudaMemcpyAsync(log_a, h->d_loga, K * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CU(h, cudaStreamSynchronize(h->stream));
+  for (int k = 0; k < K; ++k)
+    for (int d = 0; d < 3; ++d) {
+      if (Q) Q[(size_t)k * 3 + d] = q[(size_t)d * K + k];
+      if (Q_aux) Q_aux[(size_t)k * 3 + d] = q[(size_t)(3 + d) * K + k];
+    }
+  if (w_aux) RET(to_host(h, w_aux, h->d_waux, K));
   return BFMRI_OK;
 }
 
@@ -1509,6 +1657,14 @@ bfmri_status bfmri_set_state(bfmri_handle* h, const double* W, const double* A,
   if (A) RET(to_dev(h, h->d_A, A, h->P));
   if (lambda) RET(to_dev(h, h->d_lam, lambda, 1));
   if (alpha) CU(h, cudaMemcpyAsync(h->d_alpha, alpha, h->K * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  if (alpha && h->d_alpha3) {
+    // anisotropic prior: alpha_{d,k} = alpha_k for every direction
+    std::vector<double> a3(3 * (size_t)h->K);
+    for (int d = 0; d < 3; ++d)
+      for (int k = 0; k < h->K; ++k) a3[(size_t)d * h->K + k] = alpha[k];
+    CU(h, cudaMemcpyAsync(h->d_alpha3, a3.data(), a3.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    CU(h, cudaStreamSynchronize(h->stream));
+  }
   if (beta && h->P > 0)
     CU(h, cudaMemcpyAsync(h->d_beta, beta, h->P * sizeof(double), cudaMemcpyHostToDevice, h->stream));
   CU(h, cudaStreamSynchronize(h->stream));
@@ -1521,7 +1677,11 @@ bfmri_status bfmri_get_state(bfmri_handle* h, double* W, double* A, double* lamb
   if (W) RET(to_host(h, W, h->d_W, h->K));
   if (A) RET(to_host(h, A, h->d_A, h->P));
   if (lambda) RET(to_host(h, lambda, h->d_lam, 1));
-  if (alpha) CU(h, cudaMemcpyAsync(alpha, h->d_alpha, h->K * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  if (alpha && h->d_alpha3) {
+    RET(alpha_dir_mean(h, alpha));
+  } else if (alpha) {
+    CU(h, cudaMemcpyAsync(alpha, h->d_alpha, h->K * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  }
   if (beta && h->P > 0)
     CU(h, cudaMemcpyAsync(beta, h->d_beta, h->P * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   CU(h, cudaStreamSynchronize(h->stream));
@@ -1566,7 +1726,9 @@ bfmri_status bfmri_sample_alpha(bfmri_handle* h, uint64_t counter, double* alpha
   RET(begin_call(h));
   RET(enqueue_hyper(h, counter, false));
   RET(end_call(h, nullptr, nullptr));
-  if (alpha_out) {
+  if (alpha_out && h->d_alpha3) {
+    RET(alpha_dir_mean(h, alpha_out));
+  } else if (alpha_out) {
     CU(h, cudaMemcpy(alpha_out, h->d_alpha, h->K * sizeof(double), cudaMemcpyDeviceToHost));
   }
   return BFMRI_OK;
@@ -2817,6 +2979,7 @@ bfmri_status bfmri_apply_precision(bfmri_handle* h, int which, const double* x, 
   ap.x = h->d_r;
   ap.y = h->d_z;
   ap.t = (which == 0 && h->opt.w_prior == BFMRI_PRIOR_LTL) ? h->d_lt : nullptr;
+  ap.scale3 = (which == 0 && h->opt.w_prior == BFMRI_PRIOR_ANISO) ? h->d_alpha3 : nullptr;
   e = launch_apply(ap, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "apply");
   RET(end_call(h, nullptr, nullptr));
@@ -2884,6 +3047,10 @@ bfmri_status bfmri_build_system(bfmri_handle* h, int which, uint64_t counter, do
   a.bmean = h->d_bmean;
   cudaError_t e = cudaSuccess;
   if (a.ltl) e = launch_ltl_noise(a.g, h->K, h->d_alpha, a.rng, h->d_edge, h->stream);
+  if (a.scale3) {
+    e = launch_edge_noise(a.g, h->K, h->d_alpha, a.rng, h->d_edge, h->stream, a.scale3);
+    a.edge = h->d_edge;
+  }
   if (e == cudaSuccess) e = which == 0 ? launch_assemble_w(a, h->stream) : launch_assemble_a(a, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "assemble");
   RET(end_call(h, nullptr, nullptr));

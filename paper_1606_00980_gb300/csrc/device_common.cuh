@@ -12,7 +12,9 @@ namespace bfmri {
 //   x = site (lattice-linear voxel * 4 + slot; slot 0..2 edge +x/+y/+z, 3 the voxel),
 //   y = sub (normal pair index / Gamma attempt), z = draw counter, w = tag << 24 | stream.
 // ---------------------------------------------------------------------------------------
-enum : uint32_t { TAG_W = 1, TAG_A = 2, TAG_LAMBDA = 3, TAG_ALPHA = 4, TAG_BETA = 5, TAG_PROBE = 6 };
+enum : uint32_t { TAG_W = 1, TAG_A = 2, TAG_LAMBDA = 3, TAG_ALPHA = 4, TAG_BETA = 5, TAG_PROBE = 6,
+                  TAG_ALPHA_PROP = 7,   // anisotropic prior: proposal normals, acceptance uniform
+                  TAG_ALPHA_AUX = 8 };  // anisotropic prior: the auxiliary draw's edge normals
 
 __device__ __forceinline__ uint4 philox(uint4 c, uint32_t k0, uint32_t k1) {
 #pragma unroll

@@ -181,9 +181,18 @@ __global__ void __launch_bounds__(VOX_THREADS) k_assemble_w(AssembleArgs a) {
 #pragma unroll
   for (int k = 0; k < K; ++k) a.rhs[k * ld + n] = rhs[k];
   if (a.precond) {
-    const double deg = a.ltl ? ltl_diagonal(a.g, n) : degree(a.g, n);
+    if (a.scale3) {
+      double dd[3];
+      for (int d = 0; d < 3; ++d) dd[d] = d < a.g.ndir / 2 ? degree_dir(a.g, n, d) : 0.0;
 #pragma unroll
-    for (int k = 0; k < K; ++k) B[tri(k, k)] += a.scale[k] * deg;
+      for (int k = 0; k < K; ++k)
+        B[tri(k, k)] += __ldg(a.scale3 + k) * dd[0] + __ldg(a.scale3 + K + k) * dd[1] +
+                        __ldg(a.scale3 + 2 * K + k) * dd[2];
+    } else {
+      const double deg = a.ltl ? ltl_diagonal(a.g, n) : degree(a.g, n);
+#pragma unroll
+      for (int k = 0; k < K; ++k) B[tri(k, k)] += a.scale[k] * deg;
+    }
     ok = chol_packed_invdiag<K>(B) && ok;
     store_packed<K>(a.mfac, ld, n, B);
     if (a.mfac32) {
@@ -406,10 +415,13 @@ __global__ void __launch_bounds__(HYPER_THREADS) k_quadform_ltl(HyperArgs a) {
 // ---------------------------------------------------------------------------------------
 template <int D>
 __global__ void __launch_bounds__(VOX_THREADS) k_edge_noise(Geometry g, const double* scale, Rng rng,
-                                                            double* E) {
-  // sqrt(scale_k c_d) once per CTA (c_d: the edge weight of direction d)
+                                                            double* E, const double* scale3) {
+  // sqrt(scale_k c_d) once per CTA (c_d: the edge weight of direction d; scale3[d][k] in
+  // place of scale_k under the anisotropic prior)
   __shared__ double sq[3][D];
-  if (threadIdx.x < 3 * D) sq[threadIdx.x / D][threadIdx.x % D] = sqrt(scale[threadIdx.x % D] * g.cw[threadIdx.x / D]);
+  if (threadIdx.x < 3 * D)
+    sq[threadIdx.x / D][threadIdx.x % D] =
+        sqrt((scale3 ? scale3[threadIdx.x] : scale[threadIdx.x % D]) * g.cw[threadIdx.x / D]);
   __syncthreads();
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= g.N) return;
@@ -524,6 +536,130 @@ __global__ void k_hyper_draw(HyperArgs a, int nblocks) {
   if (ex) atomicAdd(a.exhausted, 1);
 }
 
+// Per-direction edge sums Q[d][k] = sum over the direction-d edges of C_e (v_i - v_j)^2, with
+// the partials of CTA b at part[(b * 3 + d) * D + k].
+template <int D>
+__global__ void __launch_bounds__(HYPER_THREADS) k_quadform_dirs(HyperArgs a) {
+  __shared__ double sh[HYPER_THREADS / 32][3][D];
+  double acc[3][D];
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+#pragma unroll
+    for (int k = 0; k < D; ++k) acc[d][k] = 0.0;
+  const size_t ld = a.g.ld;
+  const int nfwd = a.g.ndir / 2;
+  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < a.g.N; n += gridDim.x * blockDim.x) {
+    double v[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) v[k] = a.V[(size_t)k * ld + n];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const int m = d < nfwd ? __ldg(a.g.nbr + (size_t)(2 * d + 1) * ld + n) : -1;
+      if (m >= 0) {
+        const double c = slot_weight(a.g, n, 2 * d + 1, m);
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          const double df = v[k] - a.V[(size_t)k * ld + m];
+          acc[d][k] += c * df * df;
+        }
+      }
+    }
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc[d][k] += __shfl_down_sync(0xffffffffu, acc[d][k], o);
+      if (lane == 0) sh[warp][d][k] = acc[d][k];
+    }
+  __syncthreads();
+  for (int j = threadIdx.x; j < 3 * D; j += blockDim.x) {
+    double s = 0.0;
+    for (int w = 0; w < HYPER_THREADS / 32; ++w) s += sh[w][j / D][j % D];
+    a.part[(size_t)blockIdx.x * 3 * D + j] = s;
+  }
+}
+
+// Q_out[j] for j = d D + k: each warp adds the CTA partials of its j's in a fixed order.
+__global__ void k_quad_dirs_sum(HyperArgs a, int nblocks) {
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int j = threadIdx.x >> 5; j < 3 * a.D; j += nw) {
+    double Q = 0.0;
+    for (int b = lane; b < nblocks; b += 32) Q += a.part[(size_t)b * 3 * a.D + j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) Q += __shfl_xor_sync(0xffffffffu, Q, o);
+    if (lane == 0) a.Q_out[j] = Q;
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Anisotropic prior: the exchange step's proposal and acceptance, one thread per k.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ void aniso_eps(const AnisoArgs& a, int k, double* eps) {
+  site_normals<3>(a.rng, (uint32_t)k, eps);
+}
+
+__global__ void k_aniso_propose(AnisoArgs a) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= a.K) return;
+  double eps[3];
+  aniso_eps(a, k, eps);
+  for (int d = 0; d < 3; ++d) {
+    const double t = a.alpha3[d * a.K + k];
+    a.prop3[d * a.K + k] = d < a.nd ? t * exp(a.step * eps[d]) : t;
+  }
+}
+
+__global__ void k_aniso_accept(AnisoArgs a) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= a.K) return;
+  double eps[3];
+  aniso_eps(a, k, eps);
+  double la = 0.0;
+  for (int d = 0; d < a.nd; ++d) {
+    const int j = d * a.K + k;
+    const double dt = a.prop3[j] - a.alpha3[j];
+    la += -0.5 * dt * (a.Q[j] - a.Qp[j]) + a.q2 * (a.step * eps[d]) - dt / a.q1;
+  }
+  const uint4 w = a.rng.call((uint32_t)k, 2u);
+  const double u = (u53(w.x, w.y) + 1.0) * 0x1.0p-53;
+  a.log_a[k] = la;
+  if (log(u) < la) {
+    for (int d = 0; d < a.nd; ++d) a.alpha3[d * a.K + k] = a.prop3[d * a.K + k];
+    a.accepted[k] += 1;
+  }
+}
+
+template <int D>
+__global__ void __launch_bounds__(VOX_THREADS) k_aux_system(Geometry g, const double* prop3, const double* E,
+                                                            double* blocks, double* mfac, double* rhs,
+                                                            double* x) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= g.N) return;
+  const size_t ld = g.ld;
+  double dd[3];
+  for (int d = 0; d < 3; ++d) dd[d] = d < g.ndir / 2 ? degree_dir(g, n, d) : 0.0;
+  double r[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) r[k] = 0.0;
+  add_edge_terms<D>(g, E, n, r);
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+#pragma unroll
+    for (int j = 0; j <= i; ++j) {
+      blocks[(size_t)tri(i, j) * ld + n] = 0.0;
+      mfac[(size_t)tri(i, j) * ld + n] = 0.0;
+    }
+    const double m = __ldg(prop3 + i) * dd[0] + __ldg(prop3 + D + i) * dd[1] + __ldg(prop3 + 2 * D + i) * dd[2];
+    // inverted diagonal of the Cholesky factor of diag(m)
+    mfac[(size_t)tri(i, i) * ld + n] = m > 0.0 ? 1.0 / sqrt(m) : 1.0;
+    rhs[(size_t)i * ld + n] = r[i];
+    x[(size_t)i * ld + n] = 0.0;
+  }
+}
+
 // ---------------------------------------------------------------------------------------
 // y = B~ x for inspection.
 // ---------------------------------------------------------------------------------------
@@ -547,10 +683,22 @@ __global__ void k_apply(ApplyArgs a) {
     const int m = a.g.nbr[(size_t)d * ld + n];
     if (m >= 0) {
       const double c = slot_weight(a.g, n, d, m);
-      deg += c;
+      if (a.scale3) {
+        // anisotropic prior: sum over the slots of scale3[d][k] c (x_n - x_m)
 #pragma unroll
-      for (int k = 0; k < D; ++k) sum[k] += c * V[(size_t)k * ld + m];
+        for (int k = 0; k < D; ++k)
+          sum[k] += a.scale3[(d >> 1) * D + k] * c * (V[(size_t)k * ld + n] - V[(size_t)k * ld + m]);
+      } else {
+        deg += c;
+#pragma unroll
+        for (int k = 0; k < D; ++k) sum[k] += c * V[(size_t)k * ld + m];
+      }
     }
+  }
+  if (a.scale3) {
+#pragma unroll
+    for (int k = 0; k < D; ++k) a.y[(size_t)k * ld + n] = y[k] + sum[k];
+    return;
   }
 #pragma unroll
   for (int k = 0; k < D; ++k)
@@ -720,16 +868,17 @@ cudaError_t launch_lambda(const LambdaArgs& a, cudaStream_t s) {
 }
 
 template <int D>
-static cudaError_t edge_d(const Geometry& g, const double* scale, Rng rng, double* E, cudaStream_t s) {
-  k_edge_noise<D><<<(g.N + VOX_THREADS - 1) / VOX_THREADS, VOX_THREADS, 0, s>>>(g, scale, rng, E);
+static cudaError_t edge_d(const Geometry& g, const double* scale, Rng rng, double* E, cudaStream_t s,
+                          const double* scale3) {
+  k_edge_noise<D><<<(g.N + VOX_THREADS - 1) / VOX_THREADS, VOX_THREADS, 0, s>>>(g, scale, rng, E, scale3);
   return cudaGetLastError();
 }
 
 cudaError_t launch_edge_noise(const Geometry& g, int D, const double* scale, Rng rng, double* E,
-                              cudaStream_t s) {
+                              cudaStream_t s, const double* scale3) {
   if (g.N <= 0) return cudaSuccess;
   switch (D) {
-#define CASE(k) case k: return edge_d<k>(g, scale, rng, E, s);
+#define CASE(k) case k: return edge_d<k>(g, scale, rng, E, s, scale3);
     BFMRI_K_CASES(CASE)
 #undef CASE
     default: return cudaErrorInvalidValue;
@@ -744,6 +893,11 @@ int hyper_grid(int N) {
 template <int D>
 static cudaError_t hyper_d(const HyperArgs& a, cudaStream_t s) {
   const int grid = hyper_grid(a.g.N);
+  if (a.dirs) {
+    k_quadform_dirs<D><<<grid, HYPER_THREADS, 0, s>>>(a);
+    k_quad_dirs_sum<<<1, 32 * (3 * D < 32 ? 3 * D : 32), 0, s>>>(a, grid);
+    return cudaGetLastError();
+  }
   if (a.ltl) k_quadform_ltl<D><<<grid, HYPER_THREADS, 0, s>>>(a);
   else k_quadform<D><<<grid, HYPER_THREADS, 0, s>>>(a);
   k_hyper_draw<<<1, 32 * D, 0, s>>>(a, grid);
@@ -782,6 +936,37 @@ cudaError_t launch_ltl_noise(const Geometry& g, int D, const double* scale, Rng 
   if (g.N <= 0) return cudaSuccess;
   switch (D) {
 #define CASE(k) case k: return ltl_noise_d<k>(g, scale, rng, E, s);
+    BFMRI_K_CASES(CASE)
+#undef CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_aniso_propose(const AnisoArgs& a, cudaStream_t s) {
+  if (a.K <= 0) return cudaSuccess;
+  k_aniso_propose<<<1, 32, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_aniso_accept(const AnisoArgs& a, cudaStream_t s) {
+  if (a.K <= 0) return cudaSuccess;
+  k_aniso_accept<<<1, 32, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int D>
+static cudaError_t aux_d(const Geometry& g, const double* prop3, const double* E, double* blocks,
+                         double* mfac, double* rhs, double* x, cudaStream_t s) {
+  k_aux_system<D><<<(g.N + VOX_THREADS - 1) / VOX_THREADS, VOX_THREADS, 0, s>>>(g, prop3, E, blocks, mfac,
+                                                                                rhs, x);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_aux_system(const Geometry& g, int D, const double* prop3, const double* E,
+                              double* blocks, double* mfac, double* rhs, double* x, cudaStream_t s) {
+  if (g.N <= 0) return cudaSuccess;
+  switch (D) {
+#define CASE(k) case k: return aux_d<k>(g, prop3, E, blocks, mfac, rhs, x, s);
     BFMRI_K_CASES(CASE)
 #undef CASE
     default: return cudaErrorInvalidValue;

@@ -66,6 +66,28 @@ __device__ __forceinline__ void amul(const T* __restrict__ Bp, int bs, const T* 
   for (int k = 0; k < D; ++k) out[k] += s[k] * (degT * v[k] - sum[k]);
 }
 
+// out = B v + sum over the neighbour slots d of s3[d / 2][k] c_d (v_k - V_k[m_d]): the
+// anisotropic prior, one scale per direction and component (FP64 streaming solver).
+template <int D>
+__device__ __forceinline__ void amul_dir(const double* __restrict__ Bp, int bs, const double (*s3)[DMAX],
+                                         const int* nb, const double* cw6, const double* v,
+                                         const double* V, size_t ld, double* out) {
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    double acc = 0.0;
+#pragma unroll
+    for (int j = 0; j < D; ++j) acc += Bp[(size_t)(i >= j ? tri(i, j) : tri(j, i)) * bs] * v[j];
+    out[i] = acc;
+  }
+#pragma unroll
+  for (int d = 0; d < 6; ++d) {
+    if (nb[d] >= 0) {
+#pragma unroll
+      for (int k = 0; k < D; ++k) out[k] += s3[d >> 1][k] * cw6[d] * (v[k] - ldx(V + (size_t)k * ld + nb[d]));
+    }
+  }
+}
+
 // weighted number of in-mask neighbours (slots past the neighbourhood hold -1)
 template <typename T>
 __device__ __forceinline__ T degree_of(const int* nb, const T* cw6) {
@@ -838,10 +860,13 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_stream(PcgArgs a) {
   // per-slot edge weights in shared memory (read as broadcasts; no registers held)
   __shared__ double cwd[6];
   __shared__ float cwf[6];
+  // anisotropic prior: scale3[d][k] per direction and component
+  __shared__ double s3[3][DMAX];
   if (threadIdx.x == 0) {
     slot_weights(a, cwd);
     slot_weights(a, cwf);
   }
+  if (a.scale3 && threadIdx.x < 3 * D) s3[threadIdx.x / D][threadIdx.x % D] = a.scale3[threadIdx.x];
   __syncthreads();
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   const int nth = gridDim.x * blockDim.x;
@@ -849,7 +874,7 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_stream(PcgArgs a) {
   const bool pre = a.mfac != nullptr;
   double s[D];
 #pragma unroll
-  for (int k = 0; k < D; ++k) s[k] = __ldg(a.scale + k);
+  for (int k = 0; k < D; ++k) s[k] = a.scale3 ? 0.0 : __ldg(a.scale + k);
   double* R = a.r;
   double* U = a.u;
   double* Wv = a.w;
@@ -872,6 +897,12 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_stream(PcgArgs a) {
       if (a.ce && nb[d] >= 0)
         c6[d] *= (double)__uint_as_float((unsigned)__ldg(a.ce + (size_t)(d >> 1) * ld + ((d & 1) ? n : nb[d])) << 16);
     }
+  };
+  // (B~ v)_n with v_n = vn and the vector V for the neighbours
+  auto product = [&](int n, const int* nb, const double* c6, const double* vn, const double* V,
+                     double* out) {
+    if (a.scale3) amul_dir<D>(a.blocks + n, (int)ld, s3, nb, c6, vn, V, ld, out);
+    else amul<D, double>(a.blocks + n, (int)ld, s, nb, c6, degree_of<double>(nb, c6), vn, V, ld, out);
   };
   auto precond = [&](int n, const double* rn, double* un) {
     if (pre) {
@@ -903,7 +934,7 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_stream(PcgArgs a) {
       for (int k = 0; k < D; ++k) xn[k] = ldx(a.x + (size_t)k * ld + n);
       double c6[6];
       weights_at(n, nb, c6);
-      amul<D, double>(a.blocks + n, (int)ld, s, nb, c6, degree_of<double>(nb, c6), xn, a.x, ld, ax);
+      product(n, nb, c6, xn, a.x, ax);
 #pragma unroll
       for (int k = 0; k < D; ++k) rn[k] = __ldg(a.b + (size_t)k * ld + n) - ax[k];
       precond(n, rn, un);
@@ -926,7 +957,7 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_stream(PcgArgs a) {
       for (int k = 0; k < D; ++k) un[k] = U[(size_t)k * ld + n];
       double c6[6];
       weights_at(n, nb, c6);
-      amul<D, double>(a.blocks + n, (int)ld, s, nb, c6, degree_of<double>(nb, c6), un, U, ld, wn);
+      product(n, nb, c6, un, U, wn);
 #pragma unroll
       for (int k = 0; k < D; ++k) {
         const double rk = R[(size_t)k * ld + n], bk = __ldg(a.b + (size_t)k * ld + n);
@@ -1004,7 +1035,7 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg_stream(PcgArgs a) {
       }
       double c6[6];
       weights_at(n, nb, c6);
-      amul<D, double>(a.blocks + n, (int)ld, s, nb, c6, degree_of<double>(nb, c6), un, U, ld, wn);
+      product(n, nb, c6, un, U, wn);
 #pragma unroll
       for (int k = 0; k < D; ++k) {
         v[0] += rk[k] * un[k];
@@ -3081,7 +3112,7 @@ cudaError_t launch_resident(const PcgArgs& a, cudaStream_t stream, int* grid_out
 template <int D>
 static cudaError_t launch_d(const PcgArgs& a, cudaStream_t stream, int* grid_out) {
   if constexpr (D <= RES_MAX_D) {
-    if (a.allow_resident && !a.ltl && !a.ce) {
+    if (a.allow_resident && !a.ltl && !a.ce && !a.scale3) {
       bool launched = false;
       cudaError_t e = launch_resident<D>(a, stream, grid_out, &launched);
       if (launched || e != cudaSuccess) return e;
@@ -3090,6 +3121,7 @@ static cudaError_t launch_d(const PcgArgs& a, cudaStream_t stream, int* grid_out
   const int nsm = capped_sms(a.sm_cap);
   if (a.ltl && (a.mixed || a.ssor || a.reduced || a.t == nullptr)) return cudaErrorInvalidValue;
   if (a.ce && (a.mixed || a.ssor || a.reduced || a.ltl)) return cudaErrorInvalidValue;
+  if (a.scale3 && (a.mixed || a.ssor || a.reduced || a.ltl || D > DMAX)) return cudaErrorInvalidValue;
   const void* kern = a.ltl ? (const void*)k_pcg_ltl<D>
                      : a.mixed ? (a.reduced ? (const void*)k_pcg_mixed_stream_rb<D> : (const void*)k_pcg_mixed_stream<D>)
                                : (const void*)k_pcg_stream<D>;

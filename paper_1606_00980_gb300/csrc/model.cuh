@@ -109,6 +109,16 @@ __device__ __forceinline__ double degree(const Geometry& g, int n) {
   return deg;
 }
 
+// weighted degree along one direction (slots 2d and 2d + 1)
+__device__ __forceinline__ double degree_dir(const Geometry& g, int n, int d) {
+  double deg = 0.0;
+  for (int s = 2 * d; s <= 2 * d + 1; ++s) {
+    const int m = __ldg(g.nbr + (size_t)s * g.ld + n);
+    if (m >= 0) deg += slot_weight(g, n, s, m);
+  }
+  return deg;
+}
+
 // diagonal of L'L at voxel n (L the weighted graph Laplacian): deg_n^2 + sum of the squared
 // weights of the voxel's edges (column n of L holds deg_n and -c at each neighbour)
 __device__ __forceinline__ double ltl_diagonal(const Geometry& g, int n) {
@@ -274,6 +284,8 @@ struct AssembleArgs {
                         // with ltl, [D][ld] prior terms of the perturbation (launch_ltl_noise)
   int ltl;              // W system under the L'L prior: D_w = L'L in the preconditioner's
                         // diagonal; the perturbation's prior part is read from edge (required)
+  const double* scale3 = nullptr;  // W system under the anisotropic prior: [3][K] alpha_{d,k}, the
+                        // preconditioner's diagonal sum_d alpha_{d,k} deg_d (edge required)
 };
 
 // E[d][k][n] = sqrt(scale_k) z1_k for the edge from voxel n in direction +d (zero when absent):
@@ -281,8 +293,9 @@ struct AssembleArgs {
 // Device draw counter of captured sweeps: set it, or advance it by one (one-thread kernels).
 cudaError_t launch_set_counter(uint32_t* p, uint32_t v, cudaStream_t s);
 cudaError_t launch_advance_counter(uint32_t* p, cudaStream_t s);
+// With scale3 ([3][D], the anisotropic prior) the edge of direction d carries sqrt(scale3[d][k]).
 cudaError_t launch_edge_noise(const Geometry& g, int D, const double* scale, Rng rng, double* E,
-                              cudaStream_t s);
+                              cudaStream_t s, const double* scale3 = nullptr);
 cudaError_t launch_assemble_w(const AssembleArgs& a, cudaStream_t s);
 // The L'L prior's part of the perturbation: E[k][n] = sqrt(scale_k) (L z1_k)_n with z1_k one
 // normal per voxel (site lattice-linear * 4 + 0, lane k); uses E[D .. 2D) as scratch.
@@ -315,6 +328,8 @@ struct HyperArgs {
   Rng rng;
   int* exhausted;
   int ltl;              // quadratic forms |L v_k|^2 of the L'L prior instead of the edge sums
+  int dirs = 0;         // per-direction edge sums Q_out[d][k] (3 x D; part holds grid x 3D),
+                        // no draw
 };
 cudaError_t launch_hyper(const HyperArgs& a, cudaStream_t s);
 int hyper_grid(int N);
@@ -328,7 +343,35 @@ struct ApplyArgs {
   const double* x;
   double* y;
   double* t;            // [D][ld] scratch for L x under the L'L prior, or null (graph Laplacian)
+  const double* scale3 = nullptr;  // [3][D] per-direction scales of the anisotropic prior, or null
 };
 cudaError_t launch_apply(const ApplyArgs& a, cudaStream_t s);
+
+// ---------------------------------------------------------------------------------------
+// Anisotropic prior (alpha_{d,k} per direction d and regressor k): the exchange step
+// (Murray, Ghahramani & MacKay 2006) for the alphas.
+// ---------------------------------------------------------------------------------------
+struct AnisoArgs {
+  int K;
+  int nd;               // directions of the lattice (2 or 3)
+  double step;          // log-normal random-walk step
+  double q1, q2;        // Ga(scale q1, shape q2) prior of every alpha_{d,k}
+  double* alpha3;       // [3][K] current values (updated on acceptance)
+  double* prop3;        // [3][K] proposal
+  const double* Q;      // [3][K] direction edge sums of W
+  const double* Qp;     // [3][K] direction edge sums of the auxiliary field
+  double* log_a;        // [K] log acceptance ratio of the last step
+  long long* accepted;  // [K] accepted proposals (cumulative)
+  Rng rng;              // tag TAG_ALPHA_PROP: normals (sub 0, 1), uniform (sub 2)
+};
+// prop3 = alpha3 exp(step eps) in the lattice's directions (the others copied)
+cudaError_t launch_aniso_propose(const AnisoArgs& a, cudaStream_t s);
+// log a from Q, Qp; alpha3 = prop3 where log u < log a
+cudaError_t launch_aniso_accept(const AnisoArgs& a, cudaStream_t s);
+// The auxiliary system L(prop3) x = sum_d sqrt(prop3_d) G_d' C_d^(1/2) z: blocks = 0, Jacobi
+// factor diag(sum_d prop3[d][k] deg_d) (1 where a voxel has no neighbour), rhs = the edge
+// terms E (launch_edge_noise with scale3 = prop3), x = 0.
+cudaError_t launch_aux_system(const Geometry& g, int D, const double* prop3, const double* E,
+                              double* blocks, double* mfac, double* rhs, double* x, cudaStream_t s);
 
 }  // namespace bfmri

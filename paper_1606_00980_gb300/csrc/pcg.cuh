@@ -87,6 +87,9 @@ struct PcgArgs {
   // per-edge factors of C ([3][ld] BF16 of the edge from each voxel along +x, +y, +z, or
   // null): the FP64 streaming solver with block-Jacobi or no preconditioner only
   const unsigned short* ce;
+  // anisotropic prior ([3][D] scale of direction d and component k, or null): the FP64
+  // streaming solver with block-Jacobi or no preconditioner only; scale is then unused
+  const double* scale3 = nullptr;
 };
 
 // Voxels per CTA of the resident solvers for N voxels on at most sm_cap SMs (0 = all): the

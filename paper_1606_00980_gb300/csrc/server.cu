@@ -234,6 +234,15 @@ bfmri_status bfmri_server_submit(bfmri_server* s, const bfmri_request* req, long
     const size_t lt = (((size_t)req->K * (((size_t)N + 31) & ~size_t(31)) * 8 + 255) & ~size_t(255));
     j->bytes += lt + lt / 32;
   }
+  if (req->opt.w_prior == BFMRI_PRIOR_ANISO && N > 0) {
+    // the exchange step's auxiliary field ([K][ld] doubles), its small per-k arrays and the
+    // direction edge sums' partials (three per component), with the same margin
+    const size_t ldr = ((size_t)N + 31) & ~size_t(31);
+    auto r256 = [](size_t b) { return (b + 255) & ~size_t(255); };
+    const size_t hp = (size_t)1024 * std::max(req->K, req->P) * 8;   // at most 1024 partial rows
+    const size_t an = r256((size_t)req->K * ldr * 8) + 6 * r256(6 * (size_t)req->K * 8) + r256(3 * hp);
+    j->bytes += an + an / 32;
+  }
   if (req->opt.precond == BFMRI_PRECOND_MULTIGRID && N > 0) {
     // the hierarchy a multigrid request builds on its first solve, with the same margin
     const size_t mg = bfmri::mg_request_bytes(req->lat, req->mask, std::max(req->K, req->P));
