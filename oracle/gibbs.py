@@ -63,10 +63,11 @@ def sample_lambda(lat, Y, X, state, seed, counter, priors=model.PRIORS, stream=0
 
 def sample_alpha(lat, state, seed, counter, priors=model.PRIORS, stream=0, prior="ugl", step=None):
     """Gamma full conditional of alpha_k (Eq. fullcondTempa); for the anisotropic prior the
-    exchange step (exchange_alpha) with log-normal step size `step` (default 1/sqrt(N))."""
+    ray move and the exchange step (aniso_alpha_step) with log-normal step size `step`
+    (default 1/sqrt(N))."""
     if prior == "aniso":
-        return exchange_alpha(lat, state, seed, counter, 1.0 / np.sqrt(lat.N) if step is None else step,
-                              priors, stream)[0]
+        return aniso_alpha_step(lat, state, seed, counter, 1.0 / np.sqrt(lat.N) if step is None else step,
+                                priors, stream)[0]
     Q = (model.quad_forms_ltl if prior == "ltl" else model.quad_forms_edges)(lat, state["W"])
     scale, shape = model.alpha_params(Q, lat.N, priors["q1"], priors["q2"])
     a, _ = philox.gamma(seed, np.arange(len(Q)), shape, scale, counter, philox.TAG_ALPHA, stream)
@@ -92,6 +93,12 @@ def sample_alpha(lat, state, seed, counter, priors=model.PRIORS, stream=0, prior
 # The intrinsic prior is improper along the constants of each connected part of the graph;
 # w' is drawn on the complement (where it is a proper Gaussian) and Q_d does not see the
 # constants.
+# Before the exchange step, the common scale of alpha_{.,k} gets an exact draw: the move
+# alpha -> lam alpha with lam from the posterior restricted to that ray (generalised Gibbs
+# with the multiplicative group, Liu & Sabatti, JASA 2000: density pi(lam alpha) lam^(nd - 1)
+# in lam). As pdet L(lam alpha) = lam^(N - c) pdet L(alpha) (c connected parts), this is
+#   lam ~ Ga(shape nd q2 + (N - c)/2, rate sum_d alpha_d (1/q1 + Q_d / 2)),
+# so the slow random walk only has to move the ratios between the directions.
 # ----------------------------------------------------------------------------------------
 
 def null_projector(lat: Lattice):
@@ -128,6 +135,45 @@ def aux_prior_draw(lat: Lattice, theta, seed, counter, stream=0):
     J = null_projector(lat)
     Ls = model.direction_laplacians(lat)
     return np.stack([aux_solve(lat, theta[k], z[:, k], J, Ls) for k in range(K)])
+
+
+def n_parts(lat: Lattice):
+    """Number of connected parts of the voxel graph."""
+    from scipy.sparse.csgraph import connected_components
+    E = lat.edges()
+    adj = sp.csr_matrix((np.ones(len(E)), (E[:, 0], E[:, 1])), shape=(lat.N, lat.N))
+    return connected_components(adj, directed=False)[0]
+
+
+def scale_move_params(theta, Q, N, nparts, nd, priors=model.PRIORS):
+    """(shape, rate) of lam per k for the ray move (theta, Q: K x 3)."""
+    theta = np.asarray(theta, dtype=np.float64)
+    shape = nd * priors["q2"] + 0.5 * (N - nparts)
+    rate = np.sum(theta[:, :nd] * (1.0 / priors["q1"] + 0.5 * np.asarray(Q)[:, :nd]), axis=1)
+    return shape, rate
+
+
+def scale_move_alpha(lat, state, seed, counter, priors=model.PRIORS, stream=0):
+    """The ray move for every k: returns (alpha' (K x 3), lam (K,)); lam from Philox tag
+    TAG_ALPHA (site k), the Gamma generator of the graph-Laplacian alpha step."""
+    theta = np.asarray(state["alpha"], dtype=np.float64)
+    nd = lat.neighbourhood // 2
+    Q = model.quad_forms_dirs(lat, state["W"])
+    shape, rate = scale_move_params(theta, Q, lat.N, n_parts(lat), nd, priors)
+    lam, _ = philox.gamma(seed, np.arange(theta.shape[0]), shape, 1.0 / rate, counter,
+                          philox.TAG_ALPHA, stream)
+    out = theta.copy()
+    out[:, :nd] *= lam[:, None]
+    return out, lam
+
+
+def aniso_alpha_step(lat, state, seed, counter, step, priors=model.PRIORS, stream=0):
+    """The anisotropic prior's alpha update: the ray move, then the exchange step from its
+    result. Returns (alpha', accepted, details incl. lam and the scaled alphas)."""
+    scaled, lam = scale_move_alpha(lat, state, seed, counter, priors, stream)
+    new, acc, d = exchange_alpha(lat, dict(state, alpha=scaled), seed, counter, step, priors, stream)
+    d.update(lam=lam, scaled=scaled)
+    return new, acc, d
 
 
 def exchange_log_ratio(theta, theta_p, Q, Qp, step_eps, nd, priors=model.PRIORS):

@@ -13,9 +13,13 @@ its exchange step (Murray, Ghahramani & MacKay 2006; the paper leaves this infer
   along the constants of any connected part;
 * log a equals the log of the density ratio the exchange algorithm accepts with, evaluated
   from brute-force quadratic forms and scipy's Gamma and log-normal densities;
-* a chain of exchange steps on a 20-voxel lattice reaches the posterior mean of log alpha
-  that a grid integration with the exact pseudo-determinant gives (this is what catches a
-  dropped proposal Jacobian or an auxiliary draw that ignores the proposal).
+* the ray move's Gamma density differs from the posterior along the ray, pi(lam alpha)
+  lam^(nd - 1) with the exact pseudo-determinant from numpy's eigenvalues, by a constant in lam
+  (on a connected lattice and on one of two parts);
+* chains of exchange steps, alone and after the ray move, on a 20-voxel lattice reach the
+  posterior mean of log alpha that a grid integration with the exact pseudo-determinant
+  gives (this is what catches a dropped proposal Jacobian or an auxiliary draw that ignores
+  the proposal).
 """
 import numpy as np
 import pytest
@@ -163,6 +167,48 @@ def test_exchange_step_uses_its_random_numbers():
     assert np.array_equal(new[acc], d["proposal"][acc]) and np.array_equal(new[~acc], st["alpha"][~acc])
 
 
+@pytest.mark.parametrize("two_parts", [False, True])
+def test_ray_move_is_the_posterior_along_the_ray(two_parts):
+    stats = pytest.importorskip("scipy.stats")
+    if two_parts:
+        mask = np.zeros((2, 4, 6), np.uint8)
+        mask[:, :3, :3] = 1
+        mask[:, 0:2, 5] = 1
+        lat = Lattice(mask, 6, weights=W3)
+    else:
+        lat = lattice((5, 4, 3), 6)
+    nd, c = 3, gibbs.n_parts(lat)
+    assert c == (2 if two_parts else 1)
+    rng = np.random.default_rng(10)
+    theta = rng.uniform(0.3, 3.0, 3)
+    w = rng.standard_normal(lat.N)
+    Q = pair_sums(lat, w)
+    Ls = [L.toarray() for L in model.direction_laplacians(lat)]
+    pr = model.PRIORS
+    shape, rate = gibbs.scale_move_params(theta[None], Q[None], lat.N, c, nd)
+    diffs = []
+    for lam in (0.3, 0.8, 1.0, 2.5, 7.0):
+        t = lam * theta
+        ev = np.linalg.eigvalsh(sum(t[d] * Ls[d] for d in range(3)))[c:]
+        logpi = (stats.gamma.logpdf(t, a=pr["q2"], scale=pr["q1"]).sum() + 0.5 * np.sum(np.log(ev))
+                 - 0.5 * t @ Q)
+        diffs.append(logpi + (nd - 1) * np.log(lam) - stats.gamma.logpdf(lam, a=shape, scale=1.0 / rate[0]))
+    assert np.ptp(diffs) <= 1e-9 * max(1.0, np.abs(diffs).max())
+
+
+def test_ray_move_uses_its_random_numbers():
+    lat = lattice((5, 4, 1), 4, hole=False)
+    rng = np.random.default_rng(11)
+    K = 3
+    st = dict(W=rng.standard_normal((K, lat.N)), alpha=rng.uniform(0.5, 2.0, (K, 3)))
+    out, lam = gibbs.scale_move_alpha(lat, st, 5, 2)
+    shape, rate = gibbs.scale_move_params(st["alpha"], model.quad_forms_dirs(lat, st["W"]), lat.N, 1, 2)
+    ref, _ = philox.gamma(5, np.arange(K), shape, 1.0 / rate, 2, philox.TAG_ALPHA, 0)
+    assert np.array_equal(lam, ref)
+    assert np.array_equal(out[:, :2], st["alpha"][:, :2] * lam[:, None])
+    assert np.array_equal(out[:, 2], st["alpha"][:, 2])
+
+
 def exact_posterior_mean_log(lat, w, priors, grid=160):
     """E[log alpha_x], E[log alpha_y] under p(alpha | w) for a connected 2D lattice and one
     field w: Ga(q1, q2) priors times pdet(L(alpha))^(1/2) exp(-Q(alpha) / 2), on a grid."""
@@ -183,7 +229,8 @@ def exact_posterior_mean_log(lat, w, priors, grid=160):
     return np.array([np.sum(p * LX), np.sum(p * LY)])
 
 
-def test_exchange_chain_reaches_the_exact_posterior():
+@pytest.mark.parametrize("kernel", ["exchange", "ray_then_exchange"])
+def test_exchange_chain_reaches_the_exact_posterior(kernel):
     pytest.importorskip("scipy.stats")
     lat = Lattice(np.ones((1, 4, 5), np.uint8), 4)
     rng = np.random.default_rng(1)
@@ -193,7 +240,8 @@ def test_exchange_chain_reaches_the_exact_posterior():
     st = dict(W=np.repeat(w[None], K, axis=0), alpha=np.ones((K, 3)))
     trace = []
     for c in range(steps):
-        st["alpha"], _, _ = gibbs.exchange_alpha(lat, st, 11, c, 0.6)
+        step = gibbs.exchange_alpha if kernel == "exchange" else gibbs.aniso_alpha_step
+        st["alpha"], _, _ = step(lat, st, 11, c, 0.6)
         trace.append(np.log(st["alpha"][:, :2]))
     x = np.array(trace)[burn:]
     nb = 10
