@@ -464,6 +464,7 @@ def run_ours(args, world, rank, local):
     chains = run_leg(errors, "grouped_chains", run_chains, args, w, flush, stream, value) if not args.no_chains else None
     precs = run_leg(errors, "preconditioners", run_precond_compare, args, w) if (main_rank and not args.no_precond) else None
     mgc = run_leg(errors, "multigrid_chain", run_multigrid_chain, args, w) if (main_rank and not args.no_precond) else None
+    priors = run_leg(errors, "prior_variants", run_prior_variants, args, w) if (main_rank and not args.no_priors) else None
     graphs = run_leg(errors, "captured_sweeps", run_graph_compare, args, w, flush, stream) if (main_rank and not args.no_graph) else None
     del flush
     # end to end through the C ABI with host buffers
@@ -488,7 +489,7 @@ def run_ours(args, world, rank, local):
                 "voxel_draws_per_s": value * N,
                 "mixed_precision": mixed, "summaries": summ, "convergence": conv,
                 "grouped_chains": chains,
-                "preconditioners": precs, "multigrid_chain": mgc,
+                "preconditioners": precs, "multigrid_chain": mgc, "prior_variants": priors,
                 "captured_sweeps": graphs, "serving": serving, "batched_probes": batched,
                 "stats_kernels": stats_k,
                 "gpu_launches": int(n_launch),
@@ -847,6 +848,57 @@ def run_precond_compare(args, w, n_draws=10):
                      "W_solve_ms_per_draw": t["pcg_W"]["ms"] / n_draws,
                      "A_iterations_per_draw": t["pcg_A"]["pcg_iterations"] / n_draws,
                      "A_solve_ms_per_draw": t["pcg_A"]["ms"] / n_draws}
+    return out
+
+
+def run_prior_variants(args, w, sweeps=20, warm=3):
+    """Whole Gibbs sweeps of the headline workload under each prior of W on the FP64
+    streaming solver with block-Jacobi (delta 1e-8, seed 2024, from the prior means): the
+    graph Laplacian (the baseline of this comparison), per-edge BF16 factors (k / 16 drawn
+    uniformly from 8..24), the anisotropic prior with its exchange step for the alphas, and
+    the L'L prior; and the anisotropic prior once more with the register-resident
+    block-Jacobi kernel (the default where the voxels fit). Per sweep: milliseconds (CUDA events around every launch), W PCG
+    iterations, and for the anisotropic prior the exchange step's time (auxiliary solve
+    included), auxiliary PCG iterations and acceptance rate."""
+    import numpy as np
+    import torch
+
+    from paper_1606_00980_gb300 import bfmri
+    from paper_1606_00980_gb300.bfmri import Model
+    nx, ny, nz = w.dims
+    fac = np.random.default_rng(99).integers(8, 25, size=(3, nz, ny, nx)) / 16.0
+    cases = [("graph_laplacian", {}, None), ("per_edge_factors", {}, fac),
+             ("anisotropic", dict(w_prior=bfmri.PRIOR_ANISO), None),
+             ("anisotropic_resident", dict(w_prior=bfmri.PRIOR_ANISO, pcg_variant=bfmri.PCG_AUTO), None),
+             ("ltl", dict(w_prior=bfmri.PRIOR_LTL), None)]
+    out = {}
+    for name, opts, f in cases:
+        opts = dict(dict(pcg_variant=bfmri.PCG_STREAMING), **opts)
+        m = Model.from_workload(w, delta=1e-8, seed=2024, profile=1, precond=bfmri.PRECOND_BLOCK_JACOBI,
+                                **opts)
+        if f is not None:
+            m.set_edge_factors(f)
+        m.precompute_stats()
+        m.gibbs_sweep(warm, 0, info=False)
+        m.synchronize()
+        acc0 = m.get_alpha_dirs()[1] if name.startswith("anisotropic") else None
+        m.reset_timing()
+        m.gibbs_sweep(sweeps, warm, info=False)
+        m.synchronize()
+        torch.cuda.synchronize()
+        t = m.timing()
+        row = {"ms_per_sweep": sum(v["ms"] for v in t.values()) / sweeps,
+               "W_solve_ms_per_sweep": t["pcg_W"]["ms"] / sweeps,
+               "W_iterations_per_sweep": t["pcg_W"]["pcg_iterations"] / sweeps,
+               "hyper_ms_per_sweep": t["hyper"]["ms"] / sweeps}
+        if name.startswith("anisotropic"):
+            a3, acc = m.get_alpha_dirs()
+            row.update({"exchange_aux_iterations_per_sweep": t["hyper"]["pcg_iterations"] / sweeps,
+                        "acceptance_rate": float(np.mean(acc - acc0)) / sweeps,
+                        "alpha_dirs_mean": a3.mean(axis=0).tolist(),
+                        "aniso_step": 1.0 / np.sqrt(w.N)})
+        m.close()
+        out[name] = row
     return out
 
 
@@ -1269,6 +1321,7 @@ def main():
     ap.add_argument("--no-svb", action="store_true")
     ap.add_argument("--no-chains", action="store_true")
     ap.add_argument("--no-precond", action="store_true")
+    ap.add_argument("--no-priors", action="store_true")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--no-summaries", action="store_true")
     ap.add_argument("--no-convergence", action="store_true",

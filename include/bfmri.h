@@ -190,20 +190,26 @@ typedef struct {
  * G_w' C_k G_w with C_k = diag(alpha_x,k I, alpha_y,k I, alpha_z,k I) (times edge_weight),
  * the alpha_{d,k} random with the Ga(q1, q2) prior of alpha. The paper leaves its inference
  * open because the prior's determinant no longer factors out of the alphas; the alphas are
- * updated here by the exchange algorithm (Murray, Ghahramani & MacKay, UAI 2006), which needs
- * no determinant: per k, a log-normal random-walk proposal theta' (normals from Philox tag 7,
+ * updated here in two moves per k. First the common scale, exactly: alpha -> lam alpha with
+ *   lam ~ Ga(shape nd q2 + (N - c)/2, rate sum_d alpha_d (1/q1 + Q_d(w)/2))
+ * (the posterior along that ray; nd directions, c connected parts of the voxel graph, the
+ * Gamma generator of alpha with Philox tag 4, site k). Then the exchange algorithm (Murray,
+ * Ghahramani & MacKay, UAI 2006), which needs no determinant, for the ratios between the
+ * directions: a log-normal random-walk proposal theta' (normals from Philox tag 7,
  * site k, subs 0-1), an auxiliary field w' drawn from the prior at theta' by the Algorithm 2
  * perturbation without a data term (edge normals from tag 8) and PCG from zero to delta, and
  * acceptance when log u < log a (u from tag 7, site k, sub 2) with
  *   log a = sum_d [ -(theta'_d - theta_d)(Q_d(w) - Q_d(w')) / 2
  *                   + q2 (log theta'_d - log theta_d) - (theta'_d - theta_d) / q1 ],
- * Q_d the direction-d edge sums. W is solved by FP64 streaming PCG with block-Jacobi (blocks
- * plus diag_k sum_d alpha_{d,k} deg_d) or no preconditioner: precond BLOCK_JACOBI or NONE and
+ * Q_d the direction-d edge sums. W and the auxiliary field are solved by FP64 PCG (the
+ * register-resident kernel where the voxels fit and pcg_variant is AUTO, else the streaming
+ * one) with block-Jacobi (blocks plus diag_k sum_d alpha_{d,k} deg_d; for the auxiliary
+ * field, Jacobi on sum_d theta'_d deg_d) or no preconditioner: precond BLOCK_JACOBI or NONE and
  * precision FP64, else INVALID_ARG at create. The A prior stays the graph Laplacian. Grouped
  * sweeps, probes, SVB steps, the log joint and per-edge factors reject it (INVALID_ARG).
  * bfmri_set_state's alpha sets alpha_{d,k} = alpha_k for every d; bfmri_get_state's alpha
- * returns the mean over the lattice's directions; bfmri_sample_alpha runs one exchange step
- * for every k. */
+ * returns the mean over the lattice's directions; bfmri_sample_alpha runs the ray move and
+ * one exchange step for every k (the sweep's alpha step). */
 #define BFMRI_PRIOR_ANISO 2
 
 #define BFMRI_STATS_AUTO   0
@@ -308,12 +314,13 @@ bfmri_status bfmri_set_edge_factors(bfmri_handle* h, const float* factors);
 bfmri_status bfmri_set_alpha_dirs(bfmri_handle* h, const double* alpha);
 bfmri_status bfmri_get_alpha_dirs(bfmri_handle* h, double* alpha, long long* accepted);
 
-/* Anisotropic prior: the last exchange step's quantities (any pointer may be NULL): Q and
+/* Anisotropic prior: the last alpha step's quantities (any pointer may be NULL): Q and
  * Q_aux (K x 3) the direction edge sums of W and of the auxiliary field, log_a (K) the log
- * acceptance ratio, w_aux (K x N) the auxiliary field (its constant part along each
- * connected component is whatever PCG from zero left there; the edge sums ignore it). */
+ * acceptance ratio, lam (K) the ray move's factor, w_aux (K x N) the auxiliary field (its
+ * constant part along each connected component is whatever PCG from zero left there; the
+ * edge sums ignore it). */
 bfmri_status bfmri_aniso_last_step(bfmri_handle* h, double* Q, double* Q_aux, double* log_a,
-                                   double* w_aux);
+                                   double* lam, double* w_aux);
 
 /* Sets / reads the chain state (any pointer may be NULL to leave that part unchanged / not
  * read). Values are validated: lambda, alpha, beta > 0 and finite. */

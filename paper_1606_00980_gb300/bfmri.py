@@ -116,7 +116,7 @@ SIGNATURES = [
     ("bfmri_set_edge_factors", C.c_int, [_h, _P(C.c_float)]),
     ("bfmri_set_alpha_dirs", C.c_int, [_h, _dp]),
     ("bfmri_get_alpha_dirs", C.c_int, [_h, _dp, _P(C.c_longlong)]),
-    ("bfmri_aniso_last_step", C.c_int, [_h, _dp, _dp, _dp, _dp]),
+    ("bfmri_aniso_last_step", C.c_int, [_h, _dp, _dp, _dp, _dp, _dp]),
     ("bfmri_set_state", C.c_int, [_h, _dp, _dp, _dp, _dp, _dp]),
     ("bfmri_get_state", C.c_int, [_h, _dp, _dp, _dp, _dp, _dp]),
     ("bfmri_sample_W", C.c_int, [_h, C.c_uint64, _dp, _P(bfmri_solve_info)]),
@@ -502,14 +502,15 @@ class Model:
         return a, acc
 
     def aniso_last_step(self):
-        """Anisotropic prior: dict of the last exchange step's Q, Q_aux (K x 3), log_a (K) and
-        the auxiliary field w_aux (K x N)."""
+        """Anisotropic prior: dict of the last alpha step's Q, Q_aux (K x 3), log_a, lam (K)
+        and the auxiliary field w_aux (K x N)."""
         Q = np.empty((self.K, 3))
         Qa = np.empty((self.K, 3))
         la = np.empty(self.K)
+        lam = np.empty(self.K)
         wa = np.empty((self.K, self.N))
-        self._c(self.lib.bfmri_aniso_last_step(self.handle, _ptr(Q), _ptr(Qa), _ptr(la), _ptr(wa)))
-        return dict(Q=Q, Q_aux=Qa, log_a=la, w_aux=wa)
+        self._c(self.lib.bfmri_aniso_last_step(self.handle, _ptr(Q), _ptr(Qa), _ptr(la), _ptr(lam), _ptr(wa)))
+        return dict(Q=Q, Q_aux=Qa, log_a=la, lam=lam, w_aux=wa)
 
     def set_state(self, W=None, A=None, lam=None, alpha=None, beta=None):
         arrs = [None if v is None else _f64(v) for v in (W, A, lam, alpha, beta)]

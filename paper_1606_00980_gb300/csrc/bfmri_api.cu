@@ -242,7 +242,9 @@ struct bfmri_handle {
   // auxiliary field [K][ld], direction edge sums of W and of the field [2][3][K], log a [K]
   // and accepted steps [K]
   double *d_alpha3 = nullptr, *d_prop3 = nullptr, *d_waux = nullptr, *d_qdir = nullptr, *d_loga = nullptr;
+  double* d_alam = nullptr;                 // [K] lam of the last ray move
   long long* d_acc = nullptr;
+  int aniso_parts = 1;                      // connected parts of the voxel graph
   // multigrid hierarchy (BFMRI_PRECOND_MULTIGRID), built on the first multigrid solve:
   // levels 1..mg_L-1 plus level 0's slot weights and aggregate map
   int mg_L = 0;
@@ -725,9 +727,9 @@ bfmri_status run_pcg(bfmri_handle* h, int D, const double* scale, double* x, int
     a.allow_resident = 0;
   }
   if (h->opt.w_prior == BFMRI_PRIOR_ANISO && which != 1) {
-    // the W system (alpha_{d,k}) or the exchange step's auxiliary system (the proposal)
+    // the W system (alpha_{d,k}) or the exchange step's auxiliary system (the proposal):
+    // the block-Jacobi resident kernel where the voxels fit, else the streaming one
     a.scale3 = which == 0 ? h->d_alpha3 : h->d_prop3;
-    a.allow_resident = 0;
   }
   // lane pairs by default only for 6 x 6 blocks: measured on the whole-brain workload they
   // take the W solve (K = 6) from 0.414 to 0.404 ms per sweep, but the A solve (P = 3) from
@@ -925,8 +927,9 @@ bfmri_status alpha_dir_mean(bfmri_handle* h, double* alpha) {
   return BFMRI_OK;
 }
 
-// The anisotropic prior's alpha step: one exchange step for every k (proposal, auxiliary
-// prior draw into d_waux through the W system's buffers, direction edge sums, acceptance).
+// The anisotropic prior's alpha step for every k: the direction edge sums of W, the exact ray
+// move alpha -> lam alpha, then one exchange step (proposal, auxiliary prior draw into d_waux
+// through the W system's buffers, the field's edge sums, acceptance).
 bfmri_status enqueue_aniso(bfmri_handle* h, uint64_t counter) {
   const int K = h->K;
   AnisoArgs s;
@@ -942,11 +945,30 @@ bfmri_status enqueue_aniso(bfmri_handle* h, uint64_t counter) {
   s.log_a = h->d_loga;
   s.accepted = h->d_acc;
   s.rng = rng_of(h, counter, TAG_ALPHA_PROP);
+  s.N = h->N;
+  s.parts = h->aniso_parts;
+  s.lam = h->d_alam;
+  s.rng_scale = rng_of(h, counter, TAG_ALPHA);
+  s.exhausted = h->d_flags + 1;
   const Geometry g = geom(h);
+  HyperArgs q;
+  q.g = g;
+  q.D = K;
+  q.part = h->d_hpart;
+  q.out = nullptr;
+  q.rng = s.rng;
+  q.exhausted = h->d_flags + 1;
+  q.ltl = 0;
+  q.dirs = 1;
   cudaError_t e;
   {
     Timed tm(h, BFMRI_T_HYPER);
-    e = launch_aniso_propose(s, h->stream);
+    // direction edge sums of W, the ray move, then the exchange step's proposal
+    q.V = h->d_W;
+    q.Q_out = h->d_qdir;
+    e = launch_hyper(q, h->stream);
+    if (e == cudaSuccess) e = launch_aniso_scale(s, h->stream);
+    if (e == cudaSuccess) e = launch_aniso_propose(s, h->stream);
     if (e == cudaSuccess)
       e = launch_edge_noise(g, K, h->d_alpha, rng_of(h, counter, TAG_ALPHA_AUX), h->d_edge, h->stream, h->d_prop3);
     if (e == cudaSuccess)
@@ -956,21 +978,9 @@ bfmri_status enqueue_aniso(bfmri_handle* h, uint64_t counter) {
   RET(run_pcg(h, K, h->d_alpha, h->d_waux, 2));
   {
     Timed tm(h, BFMRI_T_HYPER);
-    HyperArgs q;
-    q.g = g;
-    q.D = K;
-    q.part = h->d_hpart;
-    q.out = nullptr;
-    q.rng = s.rng;
-    q.exhausted = h->d_flags + 1;
-    q.ltl = 0;
-    q.dirs = 1;
-    q.V = h->d_W;
-    q.Q_out = h->d_qdir;
-    e = launch_hyper(q, h->stream);
     q.V = h->d_waux;
     q.Q_out = h->d_qdir + 3 * K;
-    if (e == cudaSuccess) e = launch_hyper(q, h->stream);
+    e = launch_hyper(q, h->stream);
     if (e == cudaSuccess) e = launch_aniso_accept(s, h->stream);
   }
   if (e != cudaSuccess) return cuda_fail(h, e, "exchange step (acceptance)");
@@ -1320,6 +1330,29 @@ bfmri_status bfmri_create(const bfmri_lattice* lat, const uint8_t* mask, const d
   }
   h->X_host.assign(X, X + (size_t)T * K);
   h->lin_host = lin;
+  if (o.w_prior == BFMRI_PRIOR_ANISO) {
+    // connected parts of the voxel graph (the ray move's pseudo-determinant exponent N - parts)
+    std::vector<int> part(N, -1), stack;
+    int parts = 0;
+    for (int s0 = 0; s0 < N; ++s0) {
+      if (part[s0] >= 0) continue;
+      part[s0] = parts;
+      stack.assign(1, s0);
+      while (!stack.empty()) {
+        const int n = stack.back();
+        stack.pop_back();
+        for (int d = 0; d < h->ndir; ++d) {
+          const int m = nbr[(size_t)d * ld + n];
+          if (m >= 0 && part[m] < 0) {
+            part[m] = parts;
+            stack.push_back(m);
+          }
+        }
+      }
+      ++parts;
+    }
+    h->aniso_parts = parts;
+  }
   // voxel-independent lagged X products Sxx[p][q][i][j] over t = P+1..T (1-based)
   h->Sxx.assign((size_t)(P + 1) * (P + 1) * K * K, 0.0);
   for (int p = 0; p <= P; ++p)
@@ -1378,11 +1411,12 @@ bfmri_status bfmri_create(const bfmri_lattice* lat, const uint8_t* mask, const d
     h->d_waux = (double*)A((size_t)K * ld * sizeof(double));
     h->d_qdir = (double*)A(6 * (size_t)K * sizeof(double));
     h->d_loga = (double*)A((size_t)K * sizeof(double));
+    h->d_alam = (double*)A((size_t)K * sizeof(double));
     h->d_acc = (long long*)A((size_t)K * sizeof(long long));
   }
   if (!h->d_edge || (o.w_prior == BFMRI_PRIOR_LTL && !h->d_lt) ||
       (o.w_prior == BFMRI_PRIOR_ANISO &&
-       (!h->d_alpha3 || !h->d_prop3 || !h->d_waux || !h->d_qdir || !h->d_loga || !h->d_acc))) {
+       (!h->d_alpha3 || !h->d_prop3 || !h->d_waux || !h->d_qdir || !h->d_loga || !h->d_alam || !h->d_acc))) {
     bfmri_destroy(h);
     return fail(nullptr, BFMRI_ERR_OOM, "device allocation failed");
   }
@@ -1444,6 +1478,7 @@ bfmri_status bfmri_create(const bfmri_lattice* lat, const uint8_t* mask, const d
     if (!e) e = cudaMemsetAsync(h->d_acc, 0, K * sizeof(long long), s);
     if (!e) e = cudaMemsetAsync(h->d_qdir, 0, 6 * (size_t)K * sizeof(double), s);
     if (!e) e = cudaMemsetAsync(h->d_loga, 0, K * sizeof(double), s);
+    if (!e) e = cudaMemsetAsync(h->d_alam, 0, K * sizeof(double), s);
     if (!e) e = cudaMemsetAsync(h->d_waux, 0, (size_t)K * ld * sizeof(double), s);
   }
   if (!e) e = cudaStreamSynchronize(s);
@@ -1521,13 +1556,15 @@ bfmri_status bfmri_get_alpha_dirs(bfmri_handle* h, double* alpha, long long* acc
   return BFMRI_OK;
 }
 
-bfmri_status bfmri_aniso_last_step(bfmri_handle* h, double* Q, double* Q_aux, double* log_a, double* w_aux) {
+bfmri_status bfmri_aniso_last_step(bfmri_handle* h, double* Q, double* Q_aux, double* log_a, double* lam,
+                                   double* w_aux) {
   if (!h) return BFMRI_ERR_INVALID_ARG;
   if (!h->d_alpha3) return fail(h, BFMRI_ERR_INVALID_ARG, "the exchange step needs the anisotropic prior");
   const int K = h->K;
   std::vector<double> q(6 * (size_t)K);
   CU(h, cudaMemcpyAsync(q.data(), h->d_qdir, q.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   if (log_a) CU(h, cudaMemcpyAsync(log_a, h->d_loga, K * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  if (lam) CU(h, cudaMemcpyAsync(lam, h->d_alam, K * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   CU(h, cudaStreamSynchronize(h->stream));
   for (int k = 0; k < K; ++k)
     for (int d = 0; d < 3; ++d) {

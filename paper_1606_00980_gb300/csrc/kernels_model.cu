@@ -601,6 +601,19 @@ __device__ __forceinline__ void aniso_eps(const AnisoArgs& a, int k, double* eps
   site_normals<3>(a.rng, (uint32_t)k, eps);
 }
 
+__global__ void k_aniso_scale(AnisoArgs a) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= a.K) return;
+  double rate = 0.0;
+  for (int d = 0; d < a.nd; ++d) rate += a.alpha3[d * a.K + k] * (1.0 / a.q1 + 0.5 * a.Q[d * a.K + k]);
+  const double shape = a.nd * a.q2 + 0.5 * (double)(a.N - a.parts);
+  int ex = 0;
+  const double lam = gamma_draw(a.rng_scale, (uint32_t)k, shape, 1.0 / rate, &ex);
+  if (ex) atomicAdd(a.exhausted, 1);
+  a.lam[k] = lam;
+  for (int d = 0; d < a.nd; ++d) a.alpha3[d * a.K + k] *= lam;
+}
+
 __global__ void k_aniso_propose(AnisoArgs a) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= a.K) return;
@@ -940,6 +953,12 @@ cudaError_t launch_ltl_noise(const Geometry& g, int D, const double* scale, Rng 
 #undef CASE
     default: return cudaErrorInvalidValue;
   }
+}
+
+cudaError_t launch_aniso_scale(const AnisoArgs& a, cudaStream_t s) {
+  if (a.K <= 0) return cudaSuccess;
+  k_aniso_scale<<<1, 32, 0, s>>>(a);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_aniso_propose(const AnisoArgs& a, cudaStream_t s) {

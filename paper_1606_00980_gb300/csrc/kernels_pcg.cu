@@ -389,7 +389,9 @@ __device__ __forceinline__ bool resident_ssor_phases(const PcgArgs& a, Bar& bar,
 // ---------------------------------------------------------------------------------------
 // Resident variant.
 // ---------------------------------------------------------------------------------------
-template <int D>
+// ANISO: the anisotropic prior (a.scale3, per-direction scales in shared memory; no SSOR), a
+// separate instantiation so that the graph-Laplacian kernels keep their register allocation.
+template <int D, bool ANISO>
 __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_res(PcgArgs a) {
   extern __shared__ double smem[];
   __shared__ Shared sh;
@@ -397,9 +399,13 @@ __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_res(PcgArgs a) {
   // per-slot edge weights in shared memory (read as broadcasts; no registers held)
   __shared__ double cwd[6];
   __shared__ float cwf[6];
+  __shared__ double s3[ANISO ? 3 : 1][ANISO ? DMAX : 1];
   if (threadIdx.x == 0) {
     slot_weights(a, cwd);
     slot_weights(a, cwf);
+  }
+  if constexpr (ANISO) {
+    if (threadIdx.x < 3 * D) s3[threadIdx.x / D][threadIdx.x % D] = a.scale3[threadIdx.x];
   }
   __syncthreads();
   constexpr int NT = ntri(D);
@@ -427,7 +433,7 @@ __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_res(PcgArgs a) {
   double s[D], x[D], r[D], u[D], w[D], p[D], q[D], bv[D];
 #pragma unroll
   for (int k = 0; k < D; ++k) {
-    s[k] = __ldg(a.scale + k);
+    s[k] = ANISO ? 0.0 : __ldg(a.scale + k);
     x[k] = own ? a.x[(size_t)k * ld + n] : 0.0;
     bv[k] = own ? __ldg(a.b + (size_t)k * ld + n) : 0.0;
     p[k] = 0.0;
@@ -439,6 +445,11 @@ __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_res(PcgArgs a) {
     if (a.skip_block == (int)blockIdx.x) return false;
     return grid_sync(a.bar, &sh.flag);
   };
+  // (B~ v)_n with v_n = vn and the vector V for the neighbours
+  auto product = [&](const double* vn, const double* V, double* out) {
+    if constexpr (ANISO) amul_dir<D>(Bp, bd, s3, nb, cwd, vn, V, ld, out);
+    else amul<D, double>(Bp, bd, s, nb, cwd, degd, vn, V, ld, out);
+  };
   const double omega = a.omega;
   // SSOR phase 1 is the block-Jacobi step scaled by omega (u published by the caller);
   // phases 2 (black voxels) and 3 (red voxels) follow, each after a barrier
@@ -448,7 +459,7 @@ __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_res(PcgArgs a) {
   // (r, u, w) from the current x, with partials (r'u, w'u, r'r, b'b)
   auto restart = [&](double* tot) -> bool {
     double ax[D];
-    amul<D, double>(Bp, bd, s, nb, cwd, degd, x, a.x, ld, ax);
+    product(x, a.x, ax);
 #pragma unroll
     for (int k = 0; k < D; ++k) r[k] = bv[k] - ax[k];
     // SSOR phase 1 (red voxels only: the black ones are overwritten by phase 2 before
@@ -469,7 +480,7 @@ __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_res(PcgArgs a) {
     }
     if (a.ssor && !ssor_phases()) return false;
     if (!bar()) return false;
-    amul<D, double>(Bp, bd, s, nb, cwd, degd, u, a.u, ld, w);
+    product(u, a.u, w);
     double v[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
     for (int k = 0; k < D; ++k) {
@@ -524,7 +535,7 @@ __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_res(PcgArgs a) {
     }
     if (a.ssor && !ssor_phases()) return;
     if (!bar()) return;
-    amul<D, double>(Bp, bd, s, nb, cwd, degd, u, a.u, ld, w);
+    product(u, a.u, w);
     double v[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
     for (int k = 0; k < D; ++k) {
@@ -3086,7 +3097,8 @@ cudaError_t launch_resident(const PcgArgs& a, cudaStream_t stream, int* grid_out
   if constexpr (kPipe) kred = pair ? (const void*)k_pcg_rbp2<D> : (const void*)k_pcg_rbp<D>;
   else kred = (const void*)k_pcg_rb<D>;
   const void* kern = a.mixed ? (a.reduced ? (const void*)k_pcg_mixed_rbp<D> : (const void*)k_pcg_mixed_res<D>)
-                             : (a.reduced ? kred : (const void*)k_pcg_res<D>);
+                             : (a.reduced ? kred
+                                : a.scale3 ? (const void*)k_pcg_res<D, true> : (const void*)k_pcg_res<D, false>);
   if (raise_smem_limit(kern, shm) != cudaSuccess) {
     cudaGetLastError();
     return cudaSuccess;
@@ -3112,7 +3124,8 @@ cudaError_t launch_resident(const PcgArgs& a, cudaStream_t stream, int* grid_out
 template <int D>
 static cudaError_t launch_d(const PcgArgs& a, cudaStream_t stream, int* grid_out) {
   if constexpr (D <= RES_MAX_D) {
-    if (a.allow_resident && !a.ltl && !a.ce && !a.scale3) {
+    // the anisotropic prior: the block-Jacobi resident kernel only
+    if (a.allow_resident && !a.ltl && !a.ce && (!a.scale3 || (!a.reduced && !a.mixed && !a.ssor))) {
       bool launched = false;
       cudaError_t e = launch_resident<D>(a, stream, grid_out, &launched);
       if (launched || e != cudaSuccess) return e;

@@ -363,7 +363,15 @@ struct AnisoArgs {
   double* log_a;        // [K] log acceptance ratio of the last step
   long long* accepted;  // [K] accepted proposals (cumulative)
   Rng rng;              // tag TAG_ALPHA_PROP: normals (sub 0, 1), uniform (sub 2)
+  // the ray move alpha -> lam alpha before the exchange step
+  int N, parts;         // voxels and connected parts of the voxel graph
+  double* lam;          // [K] the last lam
+  Rng rng_scale;        // tag TAG_ALPHA: the Gamma draw of lam (site k)
+  int* exhausted;       // Gamma attempts exhausted (counted)
 };
+// lam_k ~ Ga(shape nd q2 + (N - parts)/2, rate sum_d alpha_d (1/q1 + Q_d/2)); alpha3 *= lam_k
+// in the lattice's directions (Q: the direction edge sums of W)
+cudaError_t launch_aniso_scale(const AnisoArgs& a, cudaStream_t s);
 // prop3 = alpha3 exp(step eps) in the lattice's directions (the others copied)
 cudaError_t launch_aniso_propose(const AnisoArgs& a, cudaStream_t s);
 // log a from Q, Qp; alpha3 = prop3 where log u < log a
