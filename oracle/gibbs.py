@@ -113,15 +113,20 @@ def null_projector(lat: Lattice):
     return (ind @ sp.diags(1.0 / sizes) @ ind.T).tocsr()
 
 
-def aux_solve(lat: Lattice, theta_k, z_k, J=None, Ls=None):
-    """L(theta_k)^+ sum_d sqrt(theta_k[d]) G_d' C_d^(1/2) z_k for one k (z_k: one value per
-    edge in edges() order). The right-hand side is orthogonal to the range of J, so
-    (L + J) x = b gives x = L^+ b."""
+def aux_rhs(lat: Lattice, theta_k, z_k):
+    """sum_d sqrt(theta_k[d]) G_d' C_d^(1/2) z_k for one k (z_k: one value per edge in edges()
+    order): Algorithm 2's prior term, the auxiliary draw's right-hand side."""
     E = lat.edges()
+    return lat.Gw().T @ (np.sqrt(np.asarray(theta_k, dtype=np.float64)[E[:, 2]]) * z_k)
+
+
+def aux_solve(lat: Lattice, theta_k, z_k, J=None, Ls=None):
+    """L(theta_k)^+ aux_rhs(theta_k, z_k) for one k. The right-hand side is orthogonal to the
+    range of J, so (L + J) x = b gives x = L^+ b."""
     J = null_projector(lat) if J is None else J
     Ls = model.direction_laplacians(lat) if Ls is None else Ls
     theta_k = np.asarray(theta_k, dtype=np.float64)
-    b = lat.Gw().T @ (np.sqrt(theta_k[E[:, 2]]) * z_k)
+    b = aux_rhs(lat, theta_k, z_k)
     return linalg.exact_solve(sum(theta_k[d] * Ls[d] for d in range(3)) + J, b)
 
 

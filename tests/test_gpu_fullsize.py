@@ -125,3 +125,70 @@ def test_batched_probes_in_the_bench_configuration():
         v = philox.rademacher(4242, lat.lin * 4 + 3, w.K, 2, philox.TAG_PROBE, i)
         q = probes.probe_quadrature_m(lat, Bd, s["alpha"], v, int(res["iterations"][i]))
         assert abs(res["per_probe"][i] - q) <= 1e-3 * abs(q), (i, res["per_probe"][i], q)
+
+
+def test_wholebrain_anisotropic_prior_steps(wholebrain):
+    """The anisotropic prior on the whole-brain workload in the configuration the bench's
+    prior_variants leg times (block-Jacobi, the register-resident kernel, delta 1e-8): the W
+    draw's residual in the oracle's anisotropic system; for the alpha step the direction edge
+    sums of W (1e-12), lam against the oracle's Gamma draw from those sums (1e-10), the
+    proposal, the auxiliary field's residual in the oracle's L(theta') system (delta), its
+    edge sums (1e-12), log a from the oracle's formula (1e-9 of its terms' size) and the
+    decision wherever |log u - log a| exceeds that."""
+    from paper_1606_00980_gb300 import bfmri
+    from paper_1606_00980_gb300.bfmri import Model
+    w, lat, s = wholebrain
+    theta = np.random.default_rng(14).uniform(0.5, 3.0, (w.K, 3))
+    nx, ny, nz = w.dims
+    m = Model((nx, ny, nz, w.neighbourhood), w.mask, w.X, w.Y, w.K, w.P, eps=w.eps, delta=1e-8,
+              seed=SEED, precond=bfmri.PRECOND_BLOCK_JACOBI, w_prior=bfmri.PRIOR_ANISO)
+    m.precompute_stats()
+    m.set_state(W=s["W"], A=s["A"], lam=s["lam"], beta=s["beta"])
+    m.set_alpha_dirs(theta)
+    W, iw = m.sample_W(counter=5)
+    m.set_state(W=s["W"])
+    m.sample_alpha(counter=6)
+    a3, _ = m.get_alpha_dirs()
+    ls = m.aniso_last_step()
+    m.close()
+    assert iw.rel_residual <= 1e-8
+    Bd, bw = model.w_blocks_direct(w.Y, w.X, s["A"], s["lam"], w.eps)
+    pert, _, _ = model.perturbation(lat, Bd, theta, SEED, 5, philox.TAG_W, 0, "aniso")
+    b = model.kmajor(bw) + pert
+    r = model.precision(lat, Bd, theta, "aniso") @ W.reshape(-1) - b
+    nb = np.linalg.norm(b)
+    e = 1e-12 * np.abs(Bd).max()
+    assert np.linalg.norm(r) / nb <= 1e-8 + (w.K * e * np.linalg.norm(W) + 1e-12 * nb) / nb
+    # the alpha step from (W, theta)
+    Q = model.quad_forms_dirs(lat, s["W"])
+    assert rel_max(ls["Q"], Q) <= 1e-12
+    shape, rate = gibbs.scale_move_params(theta, Q, w.N, gibbs.n_parts(lat), 3)
+    lam, _ = philox.gamma(SEED, np.arange(w.K), shape, 1.0 / rate, 6, philox.TAG_ALPHA, 0)
+    assert np.max(np.abs(ls["lam"] / lam - 1)) <= 1e-10
+    scaled = theta * ls["lam"][:, None]
+    step = 1.0 / np.sqrt(w.N)
+    eps = philox.normals(SEED, np.arange(w.K), 3, 6, philox.TAG_ALPHA_PROP, 0)
+    prop = scaled * np.exp(step * eps)
+    E = lat.edges()
+    z = philox.normals(SEED, lat.lin[E[:, 0]] * 4 + E[:, 2], w.K, 6, philox.TAG_ALPHA_AUX, 0)
+    Ls = model.direction_laplacians(lat)
+    for k in range(w.K):
+        bk = gibbs.aux_rhs(lat, prop[k], z[:, k])
+        rk = sum(prop[k, d] * (Ls[d] @ ls["w_aux"][k]) for d in range(3)) - bk
+        # delta, plus the proposal's difference from the GPU's (a common factor within lam's
+        # 1e-10, which moves the residual by 1.5e-10 of |b|)
+        assert np.linalg.norm(rk) <= (1e-8 + 1e-9) * np.linalg.norm(bk), k
+    Qp = model.quad_forms_dirs(lat, ls["w_aux"])
+    assert rel_max(ls["Q_aux"], Qp) <= 1e-12
+    la = gibbs.exchange_log_ratio(scaled, prop, Q, Qp, step * eps, 3)
+    size = np.sum(np.abs(0.5 * (prop - scaled) * (Q + Qp)), axis=1) + 1.0
+    assert np.all(np.abs(ls["log_a"] - la) <= 1e-9 * size)
+    u = philox.uniform_open(SEED, np.arange(w.K), 2, 6, philox.TAG_ALPHA_PROP, 0)
+    for k in range(w.K):
+        if abs(np.log(u[k]) - la[k]) > 1e-9 * size[k]:
+            ref = prop[k] if np.log(u[k]) < la[k] else scaled[k]
+            assert np.allclose(a3[k], ref, rtol=1e-10, atol=0), k
+
+
+def rel_max(a, b):
+    return np.max(np.abs(np.asarray(a) - b)) / np.max(np.abs(b))
