@@ -857,7 +857,7 @@ def run_prior_variants(args, w, sweeps=20, warm=3):
     graph Laplacian (the baseline of this comparison), per-edge BF16 factors (k / 16 drawn
     uniformly from 8..24), the anisotropic prior with its exchange step for the alphas, and
     the L'L prior; and the anisotropic prior once more with the register-resident
-    block-Jacobi kernel (the default where the voxels fit). Per sweep: milliseconds (CUDA events around every launch), W PCG
+    block-Jacobi kernel and with the resident reduced red-black solver. Per sweep: milliseconds (CUDA events around every launch), W PCG
     iterations, and for the anisotropic prior the exchange step's time (auxiliary solve
     included), auxiliary PCG iterations and acceptance rate."""
     import numpy as np
@@ -870,12 +870,14 @@ def run_prior_variants(args, w, sweeps=20, warm=3):
     cases = [("graph_laplacian", {}, None), ("per_edge_factors", {}, fac),
              ("anisotropic", dict(w_prior=bfmri.PRIOR_ANISO), None),
              ("anisotropic_resident", dict(w_prior=bfmri.PRIOR_ANISO, pcg_variant=bfmri.PCG_AUTO), None),
+             ("anisotropic_reduced", dict(w_prior=bfmri.PRIOR_ANISO, pcg_variant=bfmri.PCG_AUTO,
+                                          precond=bfmri.PRECOND_RB_REDUCED), None),
              ("ltl", dict(w_prior=bfmri.PRIOR_LTL), None)]
     out = {}
     for name, opts, f in cases:
         opts = dict(dict(pcg_variant=bfmri.PCG_STREAMING), **opts)
-        m = Model.from_workload(w, delta=1e-8, seed=2024, profile=1, precond=bfmri.PRECOND_BLOCK_JACOBI,
-                                **opts)
+        opts = dict(dict(precond=bfmri.PRECOND_BLOCK_JACOBI), **opts)
+        m = Model.from_workload(w, delta=1e-8, seed=2024, profile=1, **opts)
         if f is not None:
             m.set_edge_factors(f)
         m.precompute_stats()

@@ -202,10 +202,13 @@ typedef struct {
  *   log a = sum_d [ -(theta'_d - theta_d)(Q_d(w) - Q_d(w')) / 2
  *                   + q2 (log theta'_d - log theta_d) - (theta'_d - theta_d) / q1 ],
  * Q_d the direction-d edge sums. W and the auxiliary field are solved by FP64 PCG (the
- * register-resident kernel where the voxels fit and pcg_variant is AUTO, else the streaming
+ * register-resident kernels where the voxels fit and pcg_variant is AUTO, else the streaming
  * one) with block-Jacobi (blocks plus diag_k sum_d alpha_{d,k} deg_d; for the auxiliary
- * field, Jacobi on sum_d theta'_d deg_d) or no preconditioner: precond BLOCK_JACOBI or NONE and
- * precision FP64, else INVALID_ARG at create. The A prior stays the graph Laplacian. Grouped
+ * field, Jacobi on sum_d theta'_d deg_d), with CG on the red-black reduced system built on
+ * those blocks (precond RB_REDUCED, K <= 6, where the voxels fit the resident kernel; else
+ * block-Jacobi streaming on the same blocks), or with no preconditioner; other precond values
+ * or a precision other than FP64 are INVALID_ARG at create; bfmri_apply_preconditioner
+ * rejects W under RB_REDUCED. The A prior stays the graph Laplacian. Grouped
  * sweeps, probes, SVB steps, the log joint and per-edge factors reject it (INVALID_ARG).
  * bfmri_set_state's alpha sets alpha_{d,k} = alpha_k for every d; bfmri_get_state's alpha
  * returns the mean over the lattice's directions; bfmri_sample_alpha runs the ray move and

@@ -1244,10 +1244,12 @@ bfmri_status bfmri_create(const bfmri_lattice* lat, const uint8_t* mask, const d
   if (o.w_prior != BFMRI_PRIOR_UGL && o.w_prior != BFMRI_PRIOR_LTL && o.w_prior != BFMRI_PRIOR_ANISO)
     return fail(nullptr, BFMRI_ERR_INVALID_ARG, "unknown w_prior");
   if (o.w_prior == BFMRI_PRIOR_ANISO &&
-      ((o.precond != BFMRI_PRECOND_NONE && o.precond != BFMRI_PRECOND_BLOCK_JACOBI) ||
+      ((o.precond != BFMRI_PRECOND_NONE && o.precond != BFMRI_PRECOND_BLOCK_JACOBI &&
+        o.precond != BFMRI_PRECOND_RB_REDUCED) ||
        o.precision != BFMRI_PREC_FP64 || !std::isfinite(o.aniso_step)))
     return fail(nullptr, BFMRI_ERR_INVALID_ARG,
-                "the anisotropic prior needs block-Jacobi or no preconditioner, FP64 precision and a finite aniso_step");
+                "the anisotropic prior needs the reduced red-black, block-Jacobi or no preconditioner, "
+                "FP64 precision and a finite aniso_step");
   if (o.w_prior == BFMRI_PRIOR_LTL &&
       ((o.precond != BFMRI_PRECOND_NONE && o.precond != BFMRI_PRECOND_BLOCK_JACOBI) ||
        o.precision != BFMRI_PREC_FP64))
@@ -3028,6 +3030,9 @@ bfmri_status bfmri_apply_preconditioner(bfmri_handle* h, int which, const double
   if (!x || !y || (which != 0 && which != 1)) return fail(h, BFMRI_ERR_INVALID_ARG, "bad arguments");
   const int D = which == 0 ? h->K : h->P;
   if (D == 0) return BFMRI_OK;
+  if (which == 0 && h->opt.w_prior == BFMRI_PRIOR_ANISO && uses_ssor(h->opt))
+    return fail(h, BFMRI_ERR_INVALID_ARG,
+                "the anisotropic prior's reduced system has no separate preconditioner to inspect");
   RET(begin_call(h));
   AssembleArgs a = assemble_args(h, which == 0 ? h->d_alpha : h->d_beta, 0, which == 0 ? TAG_W : TAG_A);
   a.perturb = 0;

@@ -1535,7 +1535,9 @@ __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_mixed_res(PcgArgs a)
 // L_b and L_b^-1 (black voxels) or Dg_r^-1 (red voxels); the data blocks are read from global
 // memory by the rare restart and confirmation passes only.
 // ---------------------------------------------------------------------------------------
-template <int D>
+// ANISO: the anisotropic prior (a.scale3): the prior scales move into the neighbour sums
+// (s = 1), a separate instantiation so that the graph-Laplacian kernel keeps its registers.
+template <int D, bool ANISO>
 __global__ void __launch_bounds__(RB_MAX_THREADS, 1) k_pcg_rbp(PcgArgs a) {
   extern __shared__ double smem[];
   __shared__ Shared sh;
@@ -1590,7 +1592,11 @@ __global__ void __launch_bounds__(RB_MAX_THREADS, 1) k_pcg_rbp(PcgArgs a) {
 #pragma unroll
   for (int d = 0; d < 6; ++d) nb[d] = (own && d < a.ndir) ? __ldg(a.nbr + (size_t)d * ld + n) : -1;
   __shared__ double s[RES_MAX_D];
-  if (t < D) s[t] = __ldg(a.scale + t);
+  __shared__ double s3[ANISO ? 3 : 1][ANISO ? DMAX : 1];
+  if (t < D) s[t] = ANISO ? 1.0 : __ldg(a.scale + t);
+  if constexpr (ANISO) {
+    if (t < 3 * D) s3[t / D][t % D] = a.scale3[t];
+  }
   __syncthreads();
   double x[D], r[D], w[D];   // x holds x_b outside the iteration, x^ inside it
   auto load_b = [&](double* bv) {
@@ -1622,7 +1628,10 @@ __global__ void __launch_bounds__(RB_MAX_THREADS, 1) k_pcg_rbp(PcgArgs a) {
     for (int d = 0; d < 6; ++d) {
       if (nb[d] >= 0) {
 #pragma unroll
-        for (int k = 0; k < D; ++k) sum[k] += cwd[d] * ldx(U + (size_t)k * ld + nb[d]);
+        for (int k = 0; k < D; ++k) {
+          if constexpr (ANISO) sum[k] += s3[d >> 1][k] * cwd[d] * ldx(U + (size_t)k * ld + nb[d]);
+          else sum[k] += cwd[d] * ldx(U + (size_t)k * ld + nb[d]);
+        }
       }
     }
   };
@@ -1670,8 +1679,12 @@ __global__ void __launch_bounds__(RB_MAX_THREADS, 1) k_pcg_rbp(PcgArgs a) {
     }
     if (!bar()) return false;
     if (black) {
-      const double degd = degree_of<double>(nb, cwd);
-      amul<D, double>(Bg, (int)ld, s, nb, cwd, degd, v, U, ld, out);
+      if constexpr (ANISO) {
+        amul_dir<D>(Bg, (int)ld, s3, nb, cwd, v, U, ld, out);
+      } else {
+        const double degd = degree_of<double>(nb, cwd);
+        amul<D, double>(Bg, (int)ld, s, nb, cwd, degd, v, U, ld, out);
+      }
     }
     return true;
   };
@@ -1701,8 +1714,12 @@ __global__ void __launch_bounds__(RB_MAX_THREADS, 1) k_pcg_rbp(PcgArgs a) {
     double ax[D], bv[D], v[4] = {0.0, 0.0, 0.0, 0.0};
     if (own) {
       load_b(bv);
-      const double degd = degree_of<double>(nb, cwd);
-      amul<D, double>(Bg, (int)ld, s, nb, cwd, degd, x, a.x, ld, ax);
+      if constexpr (ANISO) {
+        amul_dir<D>(Bg, (int)ld, s3, nb, cwd, x, a.x, ld, ax);
+      } else {
+        const double degd = degree_of<double>(nb, cwd);
+        amul<D, double>(Bg, (int)ld, s, nb, cwd, degd, x, a.x, ld, ax);
+      }
 #pragma unroll
       for (int k = 0; k < D; ++k) v[2] += (bv[k] - ax[k]) * (bv[k] - ax[k]);
     }
@@ -3087,14 +3104,18 @@ cudaError_t launch_resident(const PcgArgs& a, cudaStream_t stream, int* grid_out
   // lane pairs (k_pcg_rbp2): one red and one black voxel per pair of lanes; the host sized
   // the pairs for this voxels-per-CTA count
   const bool pair = kPipe && a.reduced && !a.mixed && a.lanes != 1 && a.pair_slots > 0 &&
-                    a.pair_per == per && 2 * a.pair_slots <= RB2_MAX_THREADS;
+                    a.pair_per == per && 2 * a.pair_slots <= RB2_MAX_THREADS && !a.scale3;
+  // the anisotropic prior's reduced system: the pipelined one-lane kernel (D <= 6) only
+  if (a.scale3 && a.reduced && !kPipe) return cudaSuccess;
   if (pair) threads = std::max(64, ((2 * a.pair_slots + 31) / 32) * 32);
   const size_t shm = a.mixed ? (size_t)ntri(D) * threads * (sizeof(double) + 2 * sizeof(float))
                      : pair  ? (size_t)(3 * ntri(D) + 4 * D) * a.pair_slots * sizeof(double)
                      : a.reduced ? (size_t)(2 * ntri(D) + (kPipe ? 4 : 1) * D) * threads * sizeof(double)
                                  : (size_t)2 * ntri(D) * threads * sizeof(double);
   const void* kred = nullptr;
-  if constexpr (kPipe) kred = pair ? (const void*)k_pcg_rbp2<D> : (const void*)k_pcg_rbp<D>;
+  if constexpr (kPipe)
+    kred = pair ? (const void*)k_pcg_rbp2<D>
+                : a.scale3 ? (const void*)k_pcg_rbp<D, true> : (const void*)k_pcg_rbp<D, false>;
   else kred = (const void*)k_pcg_rb<D>;
   const void* kern = a.mixed ? (a.reduced ? (const void*)k_pcg_mixed_rbp<D> : (const void*)k_pcg_mixed_res<D>)
                              : (a.reduced ? kred
@@ -3124,8 +3145,8 @@ cudaError_t launch_resident(const PcgArgs& a, cudaStream_t stream, int* grid_out
 template <int D>
 static cudaError_t launch_d(const PcgArgs& a, cudaStream_t stream, int* grid_out) {
   if constexpr (D <= RES_MAX_D) {
-    // the anisotropic prior: the block-Jacobi resident kernel only
-    if (a.allow_resident && !a.ltl && !a.ce && (!a.scale3 || (!a.reduced && !a.mixed && !a.ssor))) {
+    // the anisotropic prior: the block-Jacobi or the reduced resident kernel
+    if (a.allow_resident && !a.ltl && !a.ce && (!a.scale3 || (!a.mixed && (a.reduced || !a.ssor)))) {
       bool launched = false;
       cudaError_t e = launch_resident<D>(a, stream, grid_out, &launched);
       if (launched || e != cudaSuccess) return e;
@@ -3134,7 +3155,16 @@ static cudaError_t launch_d(const PcgArgs& a, cudaStream_t stream, int* grid_out
   const int nsm = capped_sms(a.sm_cap);
   if (a.ltl && (a.mixed || a.ssor || a.reduced || a.t == nullptr)) return cudaErrorInvalidValue;
   if (a.ce && (a.mixed || a.ssor || a.reduced || a.ltl)) return cudaErrorInvalidValue;
-  if (a.scale3 && (a.mixed || a.ssor || a.reduced || a.ltl || D > DMAX)) return cudaErrorInvalidValue;
+  if (a.scale3 && (a.mixed || a.ltl || D > DMAX)) return cudaErrorInvalidValue;
+  if (a.scale3 && (a.ssor || a.reduced)) {
+    // the reduced system did not fit the resident kernel: the streaming solver with the same
+    // block-Jacobi factor (the reduced system's diagonal blocks) instead of SSOR
+    if (a.ssor && !a.reduced) return cudaErrorInvalidValue;
+    PcgArgs b = a;
+    b.reduced = 0;
+    b.ssor = 0;
+    return launch_d<D>(b, stream, grid_out);
+  }
   const void* kern = a.ltl ? (const void*)k_pcg_ltl<D>
                      : a.mixed ? (a.reduced ? (const void*)k_pcg_mixed_stream_rb<D> : (const void*)k_pcg_mixed_stream<D>)
                                : (const void*)k_pcg_stream<D>;

@@ -106,13 +106,15 @@ def test_block_jacobi_apply(case):
 
 
 @pytest.mark.parametrize("variant", ["auto", "streaming"])
-@pytest.mark.parametrize("precond", [0, 1])
+@pytest.mark.parametrize("precond", ["none", "bj", "reduced"])
 def test_w_draw(case, precond, variant):
-    """Both the register-resident block-Jacobi kernel (auto at these sizes) and the streaming
-    kernel, with block-Jacobi and with no preconditioner."""
+    """The register-resident kernels (auto at these sizes: block-Jacobi, or CG on the red-black
+    reduced system) and the streaming kernel (block-Jacobi on the same blocks for both), with
+    and without a preconditioner."""
     from paper_1606_00980_gb300 import bfmri
     w, cw, lat, s = case
-    m = make(w, cw, s, precond=precond,
+    pc = dict(none=bfmri.PRECOND_NONE, bj=bfmri.PRECOND_BLOCK_JACOBI, reduced=bfmri.PRECOND_RB_REDUCED)
+    m = make(w, cw, s, precond=pc[precond],
              pcg_variant=bfmri.PCG_AUTO if variant == "auto" else bfmri.PCG_STREAMING)
     W, info = m.sample_W(counter=3)
     m.close()
@@ -143,11 +145,12 @@ def check_exchange(lat, m, state, counter, got_alpha, steps_seen):
     return new, acc
 
 
-@pytest.mark.parametrize("variant", ["auto", "streaming"])
+@pytest.mark.parametrize("variant", ["auto", "streaming", "reduced"])
 def test_exchange_steps(case, variant):
     from paper_1606_00980_gb300 import bfmri
     w, cw, lat, s = case
-    m = make(w, cw, s, pcg_variant=bfmri.PCG_AUTO if variant == "auto" else bfmri.PCG_STREAMING)
+    m = make(w, cw, s, pcg_variant=bfmri.PCG_STREAMING if variant == "streaming" else bfmri.PCG_AUTO,
+             precond=bfmri.PRECOND_RB_REDUCED if variant == "reduced" else bfmri.PRECOND_BLOCK_JACOBI)
     seen = set()
     cur = dict(s)
     acc_total = np.zeros(w.K, dtype=np.int64)
@@ -215,7 +218,7 @@ def test_options_and_calls_that_do_not_take_the_anisotropic_prior():
     from paper_1606_00980_gb300 import bfmri
     from paper_1606_00980_gb300.bfmri import Model, gibbs_sweep_group
     w, cw = CASES["small3d_K3_P2"]
-    for bad in (dict(precond=bfmri.PRECOND_SSOR), dict(precond=bfmri.PRECOND_RB_REDUCED),
+    for bad in (dict(precond=bfmri.PRECOND_SSOR), dict(precond=bfmri.PRECOND_MULTIGRID),
                 dict(precision=bfmri.PREC_MIXED), dict(precond=1, aniso_step=np.inf)):
         with pytest.raises(bfmri.BfmriError) as ei:
             Model.from_workload(w, w_prior=bfmri.PRIOR_ANISO, **bad)
@@ -241,3 +244,7 @@ def test_options_and_calls_that_do_not_take_the_anisotropic_prior():
         ms[0].spvb_step(4, 1)
     for m in ms:
         m.close()
+    mr = make(w, cw, s, precond=bfmri.PRECOND_RB_REDUCED)
+    with pytest.raises(bfmri.BfmriError):
+        mr.apply_preconditioner(0, np.ones((w.K, w.N)))
+    mr.close()

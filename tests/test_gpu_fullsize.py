@@ -127,9 +127,11 @@ def test_batched_probes_in_the_bench_configuration():
         assert abs(res["per_probe"][i] - q) <= 1e-3 * abs(q), (i, res["per_probe"][i], q)
 
 
-def test_wholebrain_anisotropic_prior_steps(wholebrain):
-    """The anisotropic prior on the whole-brain workload in the configuration the bench's
-    prior_variants leg times (block-Jacobi, the register-resident kernel, delta 1e-8): the W
+@pytest.mark.parametrize("precond", ["bj", "reduced"])
+def test_wholebrain_anisotropic_prior_steps(wholebrain, precond):
+    """The anisotropic prior on the whole-brain workload in the configurations the bench's
+    prior_variants leg times (the register-resident block-Jacobi and reduced red-black
+    kernels, delta 1e-8): the W
     draw's residual in the oracle's anisotropic system; for the alpha step the direction edge
     sums of W (1e-12), lam against the oracle's Gamma draw from those sums (1e-10), the
     proposal, the auxiliary field's residual in the oracle's L(theta') system (delta), its
@@ -141,7 +143,8 @@ def test_wholebrain_anisotropic_prior_steps(wholebrain):
     theta = np.random.default_rng(14).uniform(0.5, 3.0, (w.K, 3))
     nx, ny, nz = w.dims
     m = Model((nx, ny, nz, w.neighbourhood), w.mask, w.X, w.Y, w.K, w.P, eps=w.eps, delta=1e-8,
-              seed=SEED, precond=bfmri.PRECOND_BLOCK_JACOBI, w_prior=bfmri.PRIOR_ANISO)
+              seed=SEED, w_prior=bfmri.PRIOR_ANISO,
+              precond=bfmri.PRECOND_BLOCK_JACOBI if precond == "bj" else bfmri.PRECOND_RB_REDUCED)
     m.precompute_stats()
     m.set_state(W=s["W"], A=s["A"], lam=s["lam"], beta=s["beta"])
     m.set_alpha_dirs(theta)
