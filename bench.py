@@ -437,7 +437,7 @@ def run_ours(args, world, rank, local):
     pairs = args.pcg_lanes == 2 or (args.pcg_lanes == 0 and K == 6)
     kname = {"reduced": ((f"k_pcg_rbp2<{K}> (W solve, pipelined CG on the red-black reduced system, "
                           "lane pairs)" if pairs else
-                          f"k_pcg_rbp<{K}> (W solve, pipelined CG on the red-black reduced system)")
+                          f"k_pcg_rbp<{K}, false> (W solve, pipelined CG on the red-black reduced system)")
                          if K <= 6 else f"k_pcg_rb<{K}> (W solve, red-black reduced system)"),
              "ssor": f"k_pcg_res<{K}> (W solve, SSOR)",
              "bj": f"k_pcg_res<{K}> (W solve, block-Jacobi)"}[args.precond]
