@@ -111,3 +111,46 @@ def test_summary_bindings_marshal_without_a_gpu(lib):
         with pytest.raises(bfmri.BfmriError) as ei:
             call()
         assert ei.value.status == -1
+
+
+def test_prior_options_rejected_without_touching_the_gpu(lib):
+    """The W-prior options are validated on the host at create: an unknown prior, the L'L and
+    anisotropic priors with a solver they do not run on, and a non-finite proposal step."""
+    import numpy as np
+    from paper_1606_00980_gb300 import bfmri
+    mask = np.ones((2, 3, 4), np.uint8)
+    X = np.ones((20, 2))
+    Y = np.ones((20, 24))
+    bad = [dict(w_prior=3), dict(w_prior=-1),
+           dict(w_prior=bfmri.PRIOR_LTL, precond=bfmri.PRECOND_SSOR),
+           dict(w_prior=bfmri.PRIOR_LTL, precond=bfmri.PRECOND_RB_REDUCED),
+           dict(w_prior=bfmri.PRIOR_LTL, precision=bfmri.PREC_MIXED),
+           dict(w_prior=bfmri.PRIOR_ANISO, precond=bfmri.PRECOND_SSOR),
+           dict(w_prior=bfmri.PRIOR_ANISO, precond=bfmri.PRECOND_MULTIGRID),
+           dict(w_prior=bfmri.PRIOR_ANISO, precision=bfmri.PREC_MIXED),
+           dict(w_prior=bfmri.PRIOR_ANISO, aniso_step=float("nan")),
+           dict(w_prior=bfmri.PRIOR_ANISO, aniso_step=float("inf"))]
+    for fields in bad:
+        o = bfmri.bfmri_default_options()
+        for k, v in fields.items():
+            setattr(o, k, v)
+        with pytest.raises(bfmri.BfmriError) as ei:
+            bfmri.bfmri_create((4, 3, 2, 6), mask, X, Y, 2, 1, opts=o, torch_memory=False)
+        assert ei.value.status == -1, fields
+
+
+def test_prior_bindings_marshal_without_a_gpu(lib):
+    """The per-edge factor and anisotropic-prior bindings build their ctypes arguments and
+    reach the library, which rejects the NULL handle with INVALID_ARG before any device call."""
+    import numpy as np
+    from paper_1606_00980_gb300 import bfmri
+    m = object.__new__(bfmri.Model)
+    m.handle, m.lib, m.K, m.N, m.P, m.sites = None, lib, 3, 10, 1, 24
+    calls = [lambda: m.set_edge_factors(np.ones((3, 24))), lambda: m.set_edge_factors(None),
+             lambda: m.set_alpha_dirs(np.ones((3, 3))), m.get_alpha_dirs, m.aniso_last_step]
+    for call in calls:
+        with pytest.raises(bfmri.BfmriError) as ei:
+            call()
+        assert ei.value.status == -1
+    with pytest.raises(ValueError):
+        m.set_edge_factors(np.ones((3, 23)))
