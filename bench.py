@@ -856,8 +856,10 @@ def run_prior_variants(args, w, sweeps=20, warm=3):
     streaming solver with block-Jacobi (delta 1e-8, seed 2024, from the prior means): the
     graph Laplacian (the baseline of this comparison), per-edge BF16 factors (k / 16 drawn
     uniformly from 8..24), the anisotropic prior with its exchange step for the alphas, and
-    the L'L prior; and the anisotropic prior once more with the register-resident
-    block-Jacobi kernel and with the resident reduced red-black solver. Per sweep: milliseconds (CUDA events around every launch), W PCG
+    the L'L prior; the graph Laplacian and the per-edge factors once more with the resident
+    reduced red-black solver (the headline's solver family; one lane per voxel for per-edge
+    factors), and the anisotropic prior with the register-resident block-Jacobi kernel and
+    with the resident reduced red-black solver. Per sweep: milliseconds (CUDA events around every launch), W PCG
     iterations, and for the anisotropic prior the exchange step's time (auxiliary solve
     included), auxiliary PCG iterations and acceptance rate."""
     import numpy as np
@@ -868,6 +870,8 @@ def run_prior_variants(args, w, sweeps=20, warm=3):
     nx, ny, nz = w.dims
     fac = np.random.default_rng(99).integers(8, 25, size=(3, nz, ny, nx)) / 16.0
     cases = [("graph_laplacian", {}, None), ("per_edge_factors", {}, fac),
+             ("graph_laplacian_reduced", dict(pcg_variant=bfmri.PCG_AUTO, precond=bfmri.PRECOND_RB_REDUCED), None),
+             ("per_edge_factors_reduced", dict(pcg_variant=bfmri.PCG_AUTO, precond=bfmri.PRECOND_RB_REDUCED), fac),
              ("anisotropic", dict(w_prior=bfmri.PRIOR_ANISO), None),
              ("anisotropic_resident", dict(w_prior=bfmri.PRIOR_ANISO, pcg_variant=bfmri.PCG_AUTO), None),
              ("anisotropic_reduced", dict(w_prior=bfmri.PRIOR_ANISO, pcg_variant=bfmri.PCG_AUTO,

@@ -303,7 +303,10 @@ bfmri_status bfmri_get_stats(bfmri_handle* h, double* out);
  * uses everywhere (W and A precisions, the perturbation's sqrt(C) G_w noise of Algorithm 2,
  * the alpha and beta quadratic forms). The caller keeps ownership of factors. NULL removes
  * the factors (back to per-direction weights). Needs the graph-Laplacian prior, precision
- * FP64 and precond BLOCK_JACOBI or NONE (the streaming solver), else INVALID_ARG; factors
+ * FP64 and precond RB_REDUCED (CG on the red-black reduced system, K or P <= 6, where the
+ * voxels fit the register-resident kernel; else block-Jacobi streaming on the same blocks),
+ * BLOCK_JACOBI or NONE, else INVALID_ARG; bfmri_apply_preconditioner rejects such a handle
+ * under RB_REDUCED; factors
  * must be positive and finite, else INVALID_ARG with nothing changed. With factors set,
  * grouped sweeps, probes, SVB steps and the log joint reject the handle with INVALID_ARG.
  * Drops a captured sweep graph. Errors: INVALID_ARG, OOM, CUDA. */

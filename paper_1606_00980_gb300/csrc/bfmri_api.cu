@@ -722,10 +722,7 @@ bfmri_status run_pcg(bfmri_handle* h, int D, const double* scale, double* x, int
     a.t = h->d_lt;
     a.allow_resident = 0;
   }
-  if (h->d_ce) {
-    a.ce = h->d_ce;
-    a.allow_resident = 0;
-  }
+  if (h->d_ce) a.ce = h->d_ce;   // block-Jacobi or reduced resident kernels, else streaming
   if (h->opt.w_prior == BFMRI_PRIOR_ANISO && which != 1) {
     // the W system (alpha_{d,k}) or the exchange step's auxiliary system (the proposal):
     // the block-Jacobi resident kernel where the voxels fit, else the streaming one
@@ -1505,10 +1502,12 @@ bfmri_status bfmri_set_edge_factors(bfmri_handle* h, const float* factors) {
     h->d_ce = nullptr;
     return BFMRI_OK;
   }
-  if ((h->opt.precond != BFMRI_PRECOND_NONE && h->opt.precond != BFMRI_PRECOND_BLOCK_JACOBI) ||
+  if ((h->opt.precond != BFMRI_PRECOND_NONE && h->opt.precond != BFMRI_PRECOND_BLOCK_JACOBI &&
+       h->opt.precond != BFMRI_PRECOND_RB_REDUCED) ||
       h->opt.precision != BFMRI_PREC_FP64 || h->opt.w_prior != BFMRI_PRIOR_UGL)
     return fail(h, BFMRI_ERR_INVALID_ARG,
-                "per-edge factors need block-Jacobi or no preconditioner, FP64 and the graph-Laplacian prior");
+                "per-edge factors need the reduced red-black, block-Jacobi or no preconditioner, FP64 "
+                "and the graph-Laplacian prior");
   const size_t nsite = (size_t)h->nx * h->ny * h->nz, ld = h->ld;
   std::vector<unsigned short> planes(3 * ld, (unsigned short)0x3F80);   // BF16 1.0 in the padding
   for (int d = 0; d < h->ndir / 2; ++d)   // the z plane is not read with 4 neighbours
@@ -3033,6 +3032,9 @@ bfmri_status bfmri_apply_preconditioner(bfmri_handle* h, int which, const double
   if (which == 0 && h->opt.w_prior == BFMRI_PRIOR_ANISO && uses_ssor(h->opt))
     return fail(h, BFMRI_ERR_INVALID_ARG,
                 "the anisotropic prior's reduced system has no separate preconditioner to inspect");
+  if (h->d_ce && uses_ssor(h->opt))
+    return fail(h, BFMRI_ERR_INVALID_ARG,
+                "the reduced system with per-edge factors has no separate preconditioner to inspect");
   RET(begin_call(h));
   AssembleArgs a = assemble_args(h, which == 0 ? h->d_alpha : h->d_beta, 0, which == 0 ? TAG_W : TAG_A);
   a.perturb = 0;

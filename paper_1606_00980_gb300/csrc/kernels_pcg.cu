@@ -34,6 +34,11 @@ constexpr int RES_MAX_THREADS = 384;
 // that it may take 184 registers a thread (N <= 152 x 352 voxels on one GB300)
 constexpr int RB_MAX_THREADS = 352;
 constexpr int RES_MAX_D = 8;
+// prior variants of the resident kernels (separate instantiations, so that the graph-Laplacian
+// kernels keep their register allocation): direction weights, the anisotropic prior's
+// per-direction scales (a.scale3), per-edge factors (a.ce, slot weights per voxel in shared
+// memory)
+constexpr int PRIOR_DIR = 0, PRIOR_SCALE3 = 1, PRIOR_EDGE = 2;
 
 __device__ __forceinline__ double ldx(const double* p) { return __ldcg(p); }
 
@@ -389,10 +394,12 @@ __device__ __forceinline__ bool resident_ssor_phases(const PcgArgs& a, Bar& bar,
 // ---------------------------------------------------------------------------------------
 // Resident variant.
 // ---------------------------------------------------------------------------------------
-// ANISO: the anisotropic prior (a.scale3, per-direction scales in shared memory; no SSOR), a
-// separate instantiation so that the graph-Laplacian kernels keep their register allocation.
-template <int D, bool ANISO>
+// PRIOR: PRIOR_SCALE3 (the anisotropic prior's per-direction scales in shared memory) and
+// PRIOR_EDGE (per-edge factors: the voxel's six slot weights in shared memory after the
+// blocks) run without SSOR.
+template <int D, int PRIOR>
 __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_res(PcgArgs a) {
+  constexpr bool ANISO = PRIOR == PRIOR_SCALE3;
   extern __shared__ double smem[];
   __shared__ Shared sh;
   grid_barrier_start(a.bar);
@@ -429,7 +436,29 @@ __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_res(PcgArgs a) {
   int nb[6];
 #pragma unroll
   for (int d = 0; d < 6; ++d) nb[d] = (own && d < a.ndir) ? __ldg(a.nbr + (size_t)d * ld + n) : -1;
-  const double degd = degree_of<double>(nb, cwd);
+  double* shC = smem + 2 * NT * bd;    // PRIOR_EDGE: slot weights [6][bd]
+  if constexpr (PRIOR == PRIOR_EDGE) {
+#pragma unroll
+    for (int d = 0; d < 6; ++d) {
+      double c = cwd[d];
+      // the edge's factor is stored at its lower voxel: n for +d, the neighbour for -d
+      if (nb[d] >= 0)
+        c *= (double)__uint_as_float((unsigned)__ldg(a.ce + (size_t)(d >> 1) * ld + ((d & 1) ? n : nb[d])) << 16);
+      shC[d * bd + t] = c;
+    }
+  }
+  auto edge_weights = [&](double* c6) {
+#pragma unroll
+    for (int d = 0; d < 6; ++d) c6[d] = shC[d * bd + t];
+  };
+  double degd;
+  if constexpr (PRIOR == PRIOR_EDGE) {
+    double c6[6];
+    edge_weights(c6);
+    degd = degree_of<double>(nb, c6);
+  } else {
+    degd = degree_of<double>(nb, cwd);
+  }
   double s[D], x[D], r[D], u[D], w[D], p[D], q[D], bv[D];
 #pragma unroll
   for (int k = 0; k < D; ++k) {
@@ -447,8 +476,15 @@ __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_res(PcgArgs a) {
   };
   // (B~ v)_n with v_n = vn and the vector V for the neighbours
   auto product = [&](const double* vn, const double* V, double* out) {
-    if constexpr (ANISO) amul_dir<D>(Bp, bd, s3, nb, cwd, vn, V, ld, out);
-    else amul<D, double>(Bp, bd, s, nb, cwd, degd, vn, V, ld, out);
+    if constexpr (ANISO) {
+      amul_dir<D>(Bp, bd, s3, nb, cwd, vn, V, ld, out);
+    } else if constexpr (PRIOR == PRIOR_EDGE) {
+      double c6[6];
+      edge_weights(c6);
+      amul<D, double>(Bp, bd, s, nb, c6, degd, vn, V, ld, out);
+    } else {
+      amul<D, double>(Bp, bd, s, nb, cwd, degd, vn, V, ld, out);
+    }
   };
   const double omega = a.omega;
   // SSOR phase 1 is the block-Jacobi step scaled by omega (u published by the caller);
@@ -1535,10 +1571,11 @@ __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_mixed_res(PcgArgs a)
 // L_b and L_b^-1 (black voxels) or Dg_r^-1 (red voxels); the data blocks are read from global
 // memory by the rare restart and confirmation passes only.
 // ---------------------------------------------------------------------------------------
-// ANISO: the anisotropic prior (a.scale3): the prior scales move into the neighbour sums
-// (s = 1), a separate instantiation so that the graph-Laplacian kernel keeps its registers.
-template <int D, bool ANISO>
+// PRIOR_SCALE3: the anisotropic prior's scales move into the neighbour sums (s = 1);
+// PRIOR_EDGE: the voxel's six slot weights (per-edge factors) in shared memory after z.
+template <int D, int PRIOR>
 __global__ void __launch_bounds__(RB_MAX_THREADS, 1) k_pcg_rbp(PcgArgs a) {
+  constexpr bool ANISO = PRIOR == PRIOR_SCALE3;
   extern __shared__ double smem[];
   __shared__ Shared sh;
   grid_barrier_start(a.bar);
@@ -1591,6 +1628,17 @@ __global__ void __launch_bounds__(RB_MAX_THREADS, 1) k_pcg_rbp(PcgArgs a) {
   int nb[6];
 #pragma unroll
   for (int d = 0; d < 6; ++d) nb[d] = (own && d < a.ndir) ? __ldg(a.nbr + (size_t)d * ld + n) : -1;
+  double* shC = shZ + D * bd;         // PRIOR_EDGE: slot weights [6][bd]
+  if constexpr (PRIOR == PRIOR_EDGE) {
+#pragma unroll
+    for (int d = 0; d < 6; ++d) {
+      double c = cwd[d];
+      // the edge's factor is stored at its lower voxel: n for +d, the neighbour for -d
+      if (nb[d] >= 0)
+        c *= (double)__uint_as_float((unsigned)__ldg(a.ce + (size_t)(d >> 1) * ld + ((d & 1) ? n : nb[d])) << 16);
+      shC[d * bd + t] = c;
+    }
+  }
   __shared__ double s[RES_MAX_D];
   __shared__ double s3[ANISO ? 3 : 1][ANISO ? DMAX : 1];
   if (t < D) s[t] = ANISO ? 1.0 : __ldg(a.scale + t);
@@ -1630,6 +1678,7 @@ __global__ void __launch_bounds__(RB_MAX_THREADS, 1) k_pcg_rbp(PcgArgs a) {
 #pragma unroll
         for (int k = 0; k < D; ++k) {
           if constexpr (ANISO) sum[k] += s3[d >> 1][k] * cwd[d] * ldx(U + (size_t)k * ld + nb[d]);
+          else if constexpr (PRIOR == PRIOR_EDGE) sum[k] += shC[d * bd + t] * ldx(U + (size_t)k * ld + nb[d]);
           else sum[k] += cwd[d] * ldx(U + (size_t)k * ld + nb[d]);
         }
       }
@@ -1681,6 +1730,12 @@ __global__ void __launch_bounds__(RB_MAX_THREADS, 1) k_pcg_rbp(PcgArgs a) {
     if (black) {
       if constexpr (ANISO) {
         amul_dir<D>(Bg, (int)ld, s3, nb, cwd, v, U, ld, out);
+      } else if constexpr (PRIOR == PRIOR_EDGE) {
+        double c6[6];
+#pragma unroll
+        for (int d = 0; d < 6; ++d) c6[d] = shC[d * bd + t];
+        const double degd = degree_of<double>(nb, c6);
+        amul<D, double>(Bg, (int)ld, s, nb, c6, degd, v, U, ld, out);
       } else {
         const double degd = degree_of<double>(nb, cwd);
         amul<D, double>(Bg, (int)ld, s, nb, cwd, degd, v, U, ld, out);
@@ -1716,6 +1771,12 @@ __global__ void __launch_bounds__(RB_MAX_THREADS, 1) k_pcg_rbp(PcgArgs a) {
       load_b(bv);
       if constexpr (ANISO) {
         amul_dir<D>(Bg, (int)ld, s3, nb, cwd, x, a.x, ld, ax);
+      } else if constexpr (PRIOR == PRIOR_EDGE) {
+        double c6[6];
+#pragma unroll
+        for (int d = 0; d < 6; ++d) c6[d] = shC[d * bd + t];
+        const double degd = degree_of<double>(nb, c6);
+        amul<D, double>(Bg, (int)ld, s, nb, c6, degd, x, a.x, ld, ax);
       } else {
         const double degd = degree_of<double>(nb, cwd);
         amul<D, double>(Bg, (int)ld, s, nb, cwd, degd, x, a.x, ld, ax);
@@ -3104,22 +3165,29 @@ cudaError_t launch_resident(const PcgArgs& a, cudaStream_t stream, int* grid_out
   // lane pairs (k_pcg_rbp2): one red and one black voxel per pair of lanes; the host sized
   // the pairs for this voxels-per-CTA count
   const bool pair = kPipe && a.reduced && !a.mixed && a.lanes != 1 && a.pair_slots > 0 &&
-                    a.pair_per == per && 2 * a.pair_slots <= RB2_MAX_THREADS && !a.scale3;
+                    a.pair_per == per && 2 * a.pair_slots <= RB2_MAX_THREADS && !a.scale3 && !a.ce;
   // the anisotropic prior's reduced system: the pipelined one-lane kernel (D <= 6) only
   if (a.scale3 && a.reduced && !kPipe) return cudaSuccess;
   if (pair) threads = std::max(64, ((2 * a.pair_slots + 31) / 32) * 32);
+  // per-edge factors: the one-lane FP64 kernels keep six slot weights a voxel after the rest
+  const int prior = a.scale3 ? PRIOR_SCALE3 : a.ce ? PRIOR_EDGE : PRIOR_DIR;
+  if (a.ce && (a.mixed || (a.reduced && !kPipe))) return cudaSuccess;
   const size_t shm = a.mixed ? (size_t)ntri(D) * threads * (sizeof(double) + 2 * sizeof(float))
                      : pair  ? (size_t)(3 * ntri(D) + 4 * D) * a.pair_slots * sizeof(double)
-                     : a.reduced ? (size_t)(2 * ntri(D) + (kPipe ? 4 : 1) * D) * threads * sizeof(double)
-                                 : (size_t)2 * ntri(D) * threads * sizeof(double);
+                     : a.reduced ? (size_t)(2 * ntri(D) + (kPipe ? 4 : 1) * D + (a.ce ? 6 : 0)) * threads * sizeof(double)
+                                 : (size_t)(2 * ntri(D) + (a.ce ? 6 : 0)) * threads * sizeof(double);
   const void* kred = nullptr;
   if constexpr (kPipe)
     kred = pair ? (const void*)k_pcg_rbp2<D>
-                : a.scale3 ? (const void*)k_pcg_rbp<D, true> : (const void*)k_pcg_rbp<D, false>;
+                : prior == PRIOR_SCALE3 ? (const void*)k_pcg_rbp<D, PRIOR_SCALE3>
+                : prior == PRIOR_EDGE   ? (const void*)k_pcg_rbp<D, PRIOR_EDGE>
+                                        : (const void*)k_pcg_rbp<D, PRIOR_DIR>;
   else kred = (const void*)k_pcg_rb<D>;
   const void* kern = a.mixed ? (a.reduced ? (const void*)k_pcg_mixed_rbp<D> : (const void*)k_pcg_mixed_res<D>)
                              : (a.reduced ? kred
-                                : a.scale3 ? (const void*)k_pcg_res<D, true> : (const void*)k_pcg_res<D, false>);
+                                : prior == PRIOR_SCALE3 ? (const void*)k_pcg_res<D, PRIOR_SCALE3>
+                                : prior == PRIOR_EDGE   ? (const void*)k_pcg_res<D, PRIOR_EDGE>
+                                                        : (const void*)k_pcg_res<D, PRIOR_DIR>);
   if (raise_smem_limit(kern, shm) != cudaSuccess) {
     cudaGetLastError();
     return cudaSuccess;
@@ -3145,8 +3213,9 @@ cudaError_t launch_resident(const PcgArgs& a, cudaStream_t stream, int* grid_out
 template <int D>
 static cudaError_t launch_d(const PcgArgs& a, cudaStream_t stream, int* grid_out) {
   if constexpr (D <= RES_MAX_D) {
-    // the anisotropic prior: the block-Jacobi or the reduced resident kernel
-    if (a.allow_resident && !a.ltl && !a.ce && (!a.scale3 || (!a.mixed && (a.reduced || !a.ssor)))) {
+    // the anisotropic prior and per-edge factors: the block-Jacobi or the reduced resident kernel
+    if (a.allow_resident && !a.ltl &&
+        (!(a.scale3 || a.ce) || (!a.mixed && (a.reduced || !a.ssor)))) {
       bool launched = false;
       cudaError_t e = launch_resident<D>(a, stream, grid_out, &launched);
       if (launched || e != cudaSuccess) return e;
@@ -3154,9 +3223,9 @@ static cudaError_t launch_d(const PcgArgs& a, cudaStream_t stream, int* grid_out
   }
   const int nsm = capped_sms(a.sm_cap);
   if (a.ltl && (a.mixed || a.ssor || a.reduced || a.t == nullptr)) return cudaErrorInvalidValue;
-  if (a.ce && (a.mixed || a.ssor || a.reduced || a.ltl)) return cudaErrorInvalidValue;
+  if (a.ce && (a.mixed || a.ltl || a.scale3)) return cudaErrorInvalidValue;
   if (a.scale3 && (a.mixed || a.ltl || D > DMAX)) return cudaErrorInvalidValue;
-  if (a.scale3 && (a.ssor || a.reduced)) {
+  if ((a.scale3 || a.ce) && (a.ssor || a.reduced)) {
     // the reduced system did not fit the resident kernel: the streaming solver with the same
     // block-Jacobi factor (the reduced system's diagonal blocks) instead of SSOR
     if (a.ssor && !a.reduced) return cudaErrorInvalidValue;

@@ -3,7 +3,9 @@
 The Discussion's weighted graph Laplacian puts a diagonal C between G_w' and G_w (Eq. 7);
 with per-direction weights C has three values, here every edge has its own: the handle keeps
 one BF16 factor per voxel and direction (the edge to the +d neighbour, stored at its lower
-site) and multiplies it into the direction weight in the streaming solver's neighbour sums,
+site) and multiplies it into the direction weight in the solvers' neighbour sums (resident
+block-Jacobi and red-black reduced kernels with the voxel's slot weights in shared memory,
+streaming block-Jacobi),
 the block-Jacobi diagonal, the sqrt(C) G_w noise of Algorithm 2 and the alpha / beta edge
 sums. Everything is checked against the oracle's lattice with the same factors (pinned in
 tests/test_oracle_edge_factors.py) at the bars of the graph-Laplacian tests: B~ x 1e-13,
@@ -111,10 +113,17 @@ def test_block_jacobi_apply_uses_the_weighted_degree(case):
     assert rel(got, ref) <= apply_tolerance(Bd, 1e-12 * np.abs(Bd).max())
 
 
-@pytest.mark.parametrize("precond", [0, 1])
-def test_draws_and_precisions(case, precond):
+@pytest.mark.parametrize("variant", ["auto", "streaming"])
+@pytest.mark.parametrize("precond", ["none", "bj", "reduced"])
+def test_draws_and_precisions(case, precond, variant):
+    """The register-resident kernels (auto at these sizes: block-Jacobi, or CG on the red-black
+    reduced system) and the streaming kernel (block-Jacobi on the same blocks for both), with
+    and without a preconditioner."""
+    from paper_1606_00980_gb300 import bfmri
     w, cw, f, lat, s = case
-    m = make(w, cw, f, s, precond=precond)
+    pc = dict(none=bfmri.PRECOND_NONE, bj=bfmri.PRECOND_BLOCK_JACOBI, reduced=bfmri.PRECOND_RB_REDUCED)
+    m = make(w, cw, f, s, precond=pc[precond],
+             pcg_variant=bfmri.PCG_AUTO if variant == "auto" else bfmri.PCG_STREAMING)
     W, iw = m.sample_W(counter=3)
     m.set_state(W=s["W"])
     A, ia = m.sample_A(counter=3)
@@ -129,9 +138,12 @@ def test_draws_and_precisions(case, precond):
     assert np.max(np.abs(beta / gibbs.sample_beta(lat, s, SEED, 4) - 1)) <= 1e-10
 
 
-def test_sweep_step_by_step_and_captured(case):
+@pytest.mark.parametrize("precond", ["bj", "reduced"])
+def test_sweep_step_by_step_and_captured(case, precond):
+    from paper_1606_00980_gb300 import bfmri
     w, cw, f, lat, s = case
-    m = make(w, cw, f, s)
+    pc = bfmri.PRECOND_BLOCK_JACOBI if precond == "bj" else bfmri.PRECOND_RB_REDUCED
+    m = make(w, cw, f, s, precond=pc)
     m.gibbs_sweep(1, first_counter=9)
     g = m.get_state()
     m.close()
@@ -145,7 +157,7 @@ def test_sweep_step_by_step_and_captured(case):
     assert np.max(np.abs(g["beta"] / gibbs.sample_beta(lat, s1, SEED, 9) - 1)) <= 1e-10
     runs = []
     for graph in (0, 1):
-        mm = make(w, cw, f, s, use_graph=graph, delta=1e-10)
+        mm = make(w, cw, f, s, use_graph=graph, delta=1e-10, precond=pc)
         mm.gibbs_sweep(3, first_counter=12)
         runs.append(mm.get_state())
         mm.close()
@@ -179,7 +191,7 @@ def test_options_values_and_calls_that_do_not_take_factors():
     from paper_1606_00980_gb300.bfmri import Model, gibbs_sweep_group
     w, cw = CASES["small3d_K3_P2"]
     f = bf16_factors(w, 98)
-    for bad in (dict(precond=bfmri.PRECOND_SSOR), dict(precond=bfmri.PRECOND_RB_REDUCED),
+    for bad in (dict(precond=bfmri.PRECOND_SSOR), dict(precond=bfmri.PRECOND_MULTIGRID),
                 dict(precision=bfmri.PREC_MIXED), dict(w_prior=bfmri.PRIOR_LTL)):
         m = Model.from_workload(w, **bad)
         with pytest.raises(bfmri.BfmriError) as ei:
@@ -205,3 +217,7 @@ def test_options_values_and_calls_that_do_not_take_factors():
         ms[0].spvb_step(4, 1)
     for m in ms:
         m.close()
+    mr = make(w, cw, f, s, precond=bfmri.PRECOND_RB_REDUCED)
+    with pytest.raises(bfmri.BfmriError):
+        mr.apply_preconditioner(0, np.ones((w.K, w.N)))
+    mr.close()

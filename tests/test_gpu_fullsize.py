@@ -195,3 +195,28 @@ def test_wholebrain_anisotropic_prior_steps(wholebrain, precond):
 
 def rel_max(a, b):
     return np.max(np.abs(np.asarray(a) - b)) / np.max(np.abs(b))
+
+
+def test_wholebrain_per_edge_factors_in_the_reduced_solver(wholebrain):
+    """Per-edge BF16 factors on the whole-brain workload with the resident reduced solver (the
+    bench's prior_variants configuration, delta 1e-8): the W draw's residual in the oracle's
+    system on the lattice with the same factors, and alpha against the oracle's Gamma draw."""
+    from paper_1606_00980_gb300 import bfmri
+    w, _, s = wholebrain
+    nx, ny, nz = w.dims
+    f = np.random.default_rng(15).integers(8, 25, size=(3, nz, ny, nx)) / 16.0
+    lat = Lattice(w.mask, w.neighbourhood, edge_factors=f)
+    m = headline_model(w)
+    m.set_edge_factors(f)
+    m.precompute_stats()
+    m.set_state(W=s["W"], A=s["A"], lam=s["lam"], alpha=s["alpha"], beta=s["beta"])
+    W, iw = m.sample_W(counter=5)
+    m.set_state(W=s["W"])
+    alpha = m.sample_alpha(counter=5)
+    m.close()
+    assert iw.rel_residual <= 1e-8
+    Bd, bw = model.w_blocks_direct(w.Y, w.X, s["A"], s["lam"], w.eps)
+    res, nb = residual_in_oracle_system(lat, Bd, bw, s["alpha"], philox.TAG_W, 5, W)
+    e = 1e-12 * np.abs(Bd).max()
+    assert res <= 1e-8 + (w.K * e * np.linalg.norm(W) + 1e-12 * nb) / nb, res
+    assert np.max(np.abs(alpha / gibbs.sample_alpha(lat, s, SEED, 5) - 1)) <= 1e-10
