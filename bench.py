@@ -877,6 +877,9 @@ def run_prior_variants(args, w, sweeps=20, warm=3):
              ("anisotropic_reduced", dict(w_prior=bfmri.PRIOR_ANISO, pcg_variant=bfmri.PCG_AUTO,
                                           precond=bfmri.PRECOND_RB_REDUCED), None),
              ("ltl", dict(w_prior=bfmri.PRIOR_LTL), None)]
+    if args is not None and getattr(args, "prior_cases", "all") != "all":
+        keep = set(args.prior_cases.split(","))
+        cases = [c for c in cases if c[0] in keep]
     out = {}
     for name, opts, f in cases:
         opts = dict(dict(pcg_variant=bfmri.PCG_STREAMING), **opts)
@@ -1350,6 +1353,12 @@ def main():
     ap.add_argument("--stats-case", default="all", choices=["all", "wholebrain3d", "serving_max"])
     ap.add_argument("--only-stats", action="store_true",
                     help="run only the statistics-kernel comparison (profiling entry point)")
+    ap.add_argument("--only-priors", action="store_true",
+                    help="run only the prior-variant sweeps (profiling entry point)")
+    ap.add_argument("--prior-sweeps", type=int, default=20,
+                    help="timed sweeps per prior variant (profiling: a few)")
+    ap.add_argument("--prior-cases", default="all",
+                    help="comma-separated prior-variant cases to run (default all)")
     ap.add_argument("--oracle-child", default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.oracle_child:
@@ -1372,6 +1381,11 @@ def main():
     elif args.only_batched:
         if rank == 0:
             print(json.dumps(run_batched(args)), flush=True)
+    elif args.only_priors:
+        if rank == 0:
+            from paper_1606_00980_gb300 import synth
+            print(json.dumps(run_prior_variants(args, synth.wholebrain3d(),
+                                                sweeps=max(args.prior_sweeps, 1))), flush=True)
     else:
         rc = run_ours(args, world, rank, local)
     if world > 1:
