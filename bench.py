@@ -858,8 +858,9 @@ def run_prior_variants(args, w, sweeps=20, warm=3):
     uniformly from 8..24), the anisotropic prior with its exchange step for the alphas, and
     the L'L prior; the graph Laplacian and the per-edge factors once more with the resident
     reduced red-black solver (the headline's solver family; one lane per voxel for per-edge
-    factors), and the anisotropic prior with the register-resident block-Jacobi kernel and
-    with the resident reduced red-black solver. Per sweep: milliseconds (CUDA events around every launch), W PCG
+    factors), the anisotropic prior with the register-resident block-Jacobi kernel and with
+    the resident reduced red-black solver, and the L'L prior on the resident block-Jacobi
+    kernel. Per sweep: milliseconds (CUDA events around every launch), W PCG
     iterations, and for the anisotropic prior the exchange step's time (auxiliary solve
     included), auxiliary PCG iterations and acceptance rate."""
     import numpy as np
@@ -876,7 +877,8 @@ def run_prior_variants(args, w, sweeps=20, warm=3):
              ("anisotropic_resident", dict(w_prior=bfmri.PRIOR_ANISO, pcg_variant=bfmri.PCG_AUTO), None),
              ("anisotropic_reduced", dict(w_prior=bfmri.PRIOR_ANISO, pcg_variant=bfmri.PCG_AUTO,
                                           precond=bfmri.PRECOND_RB_REDUCED), None),
-             ("ltl", dict(w_prior=bfmri.PRIOR_LTL), None)]
+             ("ltl", dict(w_prior=bfmri.PRIOR_LTL), None),
+             ("ltl_resident", dict(w_prior=bfmri.PRIOR_LTL, pcg_variant=bfmri.PCG_AUTO), None)]
     if args is not None and getattr(args, "prior_cases", "all") != "all":
         keep = set(args.prior_cases.split(","))
         cases = [c for c in cases if c[0] in keep]

@@ -719,8 +719,7 @@ bfmri_status run_pcg(bfmri_handle* h, int D, const double* scale, double* x, int
   a.reduced = h->opt.precond == BFMRI_PRECOND_RB_REDUCED;
   if (which == 0 && h->opt.w_prior == BFMRI_PRIOR_LTL) {
     a.ltl = 1;
-    a.t = h->d_lt;
-    a.allow_resident = 0;
+    a.t = h->d_lt;   // the block-Jacobi resident kernel where the voxels fit, else k_pcg_ltl
   }
   if (h->d_ce) a.ce = h->d_ce;   // block-Jacobi or reduced resident kernels, else streaming
   if (h->opt.w_prior == BFMRI_PRIOR_ANISO && which != 1) {

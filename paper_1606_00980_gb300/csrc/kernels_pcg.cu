@@ -39,6 +39,9 @@ constexpr int RES_MAX_D = 8;
 // per-direction scales (a.scale3), per-edge factors (a.ce, slot weights per voxel in shared
 // memory)
 constexpr int PRIOR_DIR = 0, PRIOR_SCALE3 = 1, PRIOR_EDGE = 2;
+// the L'L prior (block-Jacobi resident kernel): each product publishes t = L v (a.t) and
+// reads its neighbours after a grid barrier
+constexpr int PRIOR_LTL = 3;
 
 __device__ __forceinline__ double ldx(const double* p) { return __ldcg(p); }
 
@@ -475,16 +478,55 @@ __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_res(PcgArgs a) {
     return grid_sync(a.bar, &sh.flag);
   };
   // (B~ v)_n with v_n = vn and the vector V for the neighbours
-  auto product = [&](const double* vn, const double* V, double* out) {
+  // false when a grid barrier gave up (the L'L prior's product waits for the other CTAs' t)
+  auto product = [&](const double* vn, const double* V, double* out) -> bool {
     if constexpr (ANISO) {
       amul_dir<D>(Bp, bd, s3, nb, cwd, vn, V, ld, out);
     } else if constexpr (PRIOR == PRIOR_EDGE) {
       double c6[6];
       edge_weights(c6);
       amul<D, double>(Bp, bd, s, nb, c6, degd, vn, V, ld, out);
+    } else if constexpr (PRIOR == PRIOR_LTL) {
+      // t = L v at this voxel, published for the neighbours; then B v + s .* (L t)
+      double tn[D], sum[D];
+#pragma unroll
+      for (int k = 0; k < D; ++k) sum[k] = 0.0;
+#pragma unroll
+      for (int d = 0; d < 6; ++d) {
+        if (nb[d] >= 0) {
+#pragma unroll
+          for (int k = 0; k < D; ++k) sum[k] += cwd[d] * ldx(V + (size_t)k * ld + nb[d]);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < D; ++k) tn[k] = degd * vn[k] - sum[k];
+      if (own) {
+#pragma unroll
+        for (int k = 0; k < D; ++k) a.t[(size_t)k * ld + n] = tn[k];
+      }
+      if (!bar()) return false;
+#pragma unroll
+      for (int i = 0; i < D; ++i) {
+        double acc = 0.0;
+#pragma unroll
+        for (int j = 0; j < D; ++j) acc += Bp[(size_t)(i >= j ? tri(i, j) : tri(j, i)) * bd] * vn[j];
+        out[i] = acc;
+      }
+#pragma unroll
+      for (int k = 0; k < D; ++k) sum[k] = 0.0;
+#pragma unroll
+      for (int d = 0; d < 6; ++d) {
+        if (nb[d] >= 0) {
+#pragma unroll
+          for (int k = 0; k < D; ++k) sum[k] += cwd[d] * ldx(a.t + (size_t)k * ld + nb[d]);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < D; ++k) out[k] += s[k] * (degd * tn[k] - sum[k]);
     } else {
       amul<D, double>(Bp, bd, s, nb, cwd, degd, vn, V, ld, out);
     }
+    return true;
   };
   const double omega = a.omega;
   // SSOR phase 1 is the block-Jacobi step scaled by omega (u published by the caller);
@@ -495,7 +537,7 @@ __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_res(PcgArgs a) {
   // (r, u, w) from the current x, with partials (r'u, w'u, r'r, b'b)
   auto restart = [&](double* tot) -> bool {
     double ax[D];
-    product(x, a.x, ax);
+    if (!product(x, a.x, ax)) return false;
 #pragma unroll
     for (int k = 0; k < D; ++k) r[k] = bv[k] - ax[k];
     // SSOR phase 1 (red voxels only: the black ones are overwritten by phase 2 before
@@ -516,7 +558,7 @@ __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_res(PcgArgs a) {
     }
     if (a.ssor && !ssor_phases()) return false;
     if (!bar()) return false;
-    product(u, a.u, w);
+    if (!product(u, a.u, w)) return false;
     double v[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
     for (int k = 0; k < D; ++k) {
@@ -571,7 +613,7 @@ __global__ void __launch_bounds__(RES_MAX_THREADS, 1) k_pcg_res(PcgArgs a) {
     }
     if (a.ssor && !ssor_phases()) return;
     if (!bar()) return;
-    product(u, a.u, w);
+    if (!product(u, a.u, w)) return;
     double v[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
     for (int k = 0; k < D; ++k) {
@@ -3170,7 +3212,8 @@ cudaError_t launch_resident(const PcgArgs& a, cudaStream_t stream, int* grid_out
   if (a.scale3 && a.reduced && !kPipe) return cudaSuccess;
   if (pair) threads = std::max(64, ((2 * a.pair_slots + 31) / 32) * 32);
   // per-edge factors: the one-lane FP64 kernels keep six slot weights a voxel after the rest
-  const int prior = a.scale3 ? PRIOR_SCALE3 : a.ce ? PRIOR_EDGE : PRIOR_DIR;
+  const int prior = a.scale3 ? PRIOR_SCALE3 : a.ce ? PRIOR_EDGE : a.ltl ? PRIOR_LTL : PRIOR_DIR;
+  if (a.ltl && (a.mixed || a.reduced || a.ssor || a.t == nullptr)) return cudaSuccess;
   if (a.ce && (a.mixed || (a.reduced && !kPipe))) return cudaSuccess;
   const size_t shm = a.mixed ? (size_t)ntri(D) * threads * (sizeof(double) + 2 * sizeof(float))
                      : pair  ? (size_t)(3 * ntri(D) + 4 * D) * a.pair_slots * sizeof(double)
@@ -3187,6 +3230,7 @@ cudaError_t launch_resident(const PcgArgs& a, cudaStream_t stream, int* grid_out
                              : (a.reduced ? kred
                                 : prior == PRIOR_SCALE3 ? (const void*)k_pcg_res<D, PRIOR_SCALE3>
                                 : prior == PRIOR_EDGE   ? (const void*)k_pcg_res<D, PRIOR_EDGE>
+                                : prior == PRIOR_LTL    ? (const void*)k_pcg_res<D, PRIOR_LTL>
                                                         : (const void*)k_pcg_res<D, PRIOR_DIR>);
   if (raise_smem_limit(kern, shm) != cudaSuccess) {
     cudaGetLastError();
@@ -3214,7 +3258,8 @@ template <int D>
 static cudaError_t launch_d(const PcgArgs& a, cudaStream_t stream, int* grid_out) {
   if constexpr (D <= RES_MAX_D) {
     // the anisotropic prior and per-edge factors: the block-Jacobi or the reduced resident kernel
-    if (a.allow_resident && !a.ltl &&
+    // the L'L prior: the block-Jacobi resident kernel
+    if (a.allow_resident && (!a.ltl || (!a.mixed && !a.reduced && !a.ssor)) &&
         (!(a.scale3 || a.ce) || (!a.mixed && (a.reduced || !a.ssor)))) {
       bool launched = false;
       cudaError_t e = launch_resident<D>(a, stream, grid_out, &launched);

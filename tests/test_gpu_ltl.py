@@ -88,10 +88,15 @@ def test_block_jacobi_apply(case):
     assert rel(got, ref) <= apply_tolerance(Bd, 1e-12 * np.abs(Bd).max())
 
 
+@pytest.mark.parametrize("variant", ["auto", "streaming"])
 @pytest.mark.parametrize("precond", [0, 1])
-def test_w_draw_and_alpha(case, precond):
+def test_w_draw_and_alpha(case, precond, variant):
+    """The register-resident block-Jacobi kernel (auto at these sizes: t = L v published, a grid
+    barrier, then L t) and the streaming two-pass kernel, with and without block-Jacobi."""
+    from paper_1606_00980_gb300 import bfmri
     w, cw, lat, s = case
-    m = make(w, cw, s, precond=precond)
+    m = make(w, cw, s, precond=precond,
+             pcg_variant=bfmri.PCG_AUTO if variant == "auto" else bfmri.PCG_STREAMING)
     W, info = m.sample_W(counter=3)
     m.set_state(W=s["W"])
     alpha = m.sample_alpha(counter=4)
