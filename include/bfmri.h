@@ -165,7 +165,8 @@ typedef struct {
                                 graph Laplacian of Section 2, weighted by edge_weight) or
                                 BFMRI_PRIOR_LTL (D_w = L'L, the alternative Section 2 names:
                                 a 25-point stencil in 3D, 13-point in 2D). With LTL, W is
-                                solved by FP64 streaming PCG with block-Jacobi (blocks plus
+                                solved by FP64 PCG (register-resident where the voxels fit
+                                and pcg_variant is AUTO, else streaming) with block-Jacobi (blocks plus
                                 diag(alpha) times the diagonal of L'L) or no preconditioner
                                 (precond BLOCK_JACOBI or NONE, precision FP64, else INVALID_ARG
                                 at create); the A prior stays the graph Laplacian; grouped
