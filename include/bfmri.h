@@ -171,7 +171,8 @@ typedef struct {
                                 (precond BLOCK_JACOBI or NONE, precision FP64, else INVALID_ARG
                                 at create); the A prior stays the graph Laplacian; grouped
                                 sweeps, probes, SVB steps and the log joint reject LTL handles
-                                with INVALID_ARG. */
+                                with INVALID_ARG. BFMRI_PRIOR_ANISO: the anisotropic prior
+                                with random alpha per direction (see its #define). */
   int pcg_lanes;             /* lanes of the register-resident FP64 solver on the red-black
                                 reduced system (BFMRI_PRECOND_RB_REDUCED, K or P <= 6):
                                 2 = lane pairs, each pair holding one red and one black voxel
