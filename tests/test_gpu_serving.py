@@ -186,3 +186,30 @@ def test_multigrid_request_estimate_covers_the_hierarchy():
         y_bytes = w.Y.size * w.Y.itemsize
         assert peak <= est <= peak * 33 // 32 + (2 << 20) + y_bytes + 8192, (w.N, peak, est)
         assert high <= est, (w.N, high, est)
+
+
+def test_prior_request_estimates_cover_their_buffers():
+    """Requests with the L'L prior (its [K][ld] plane for L v) and with the anisotropic prior
+    (the exchange step's auxiliary field, its small per-k arrays and the direction partials):
+    the server's estimate (bfmri_result.device_bytes) stays at least the handle's own peak and
+    the pool's high-water mark for the request run alone, and within the usual margin of the
+    peak (1/32 + 2 MiB, plus the 1024-row bound the server takes for the partials)."""
+    from paper_1606_00980_gb300 import bfmri
+    cases = [dict(w_prior=bfmri.PRIOR_LTL, precond=bfmri.PRECOND_BLOCK_JACOBI),
+             dict(w_prior=bfmri.PRIOR_ANISO, precond=bfmri.PRECOND_RB_REDUCED)]
+    for w in bench_like_pool()[:3]:
+        for opts in cases:
+            m = bfmri.Model.from_workload(w, precision=bfmri.PREC_FP64, delta=1e-8, sm_budget=4, **opts)
+            m.precompute_stats()
+            m.gibbs_sweep(2, 0)
+            _, peak = m.device_bytes()
+            m.close()
+            with bfmri.Server(budget_bytes=8 << 30, slots=1, sm_budget=4) as s:
+                s.pool_usage(reset=True)
+                res = s.poll(s.submit(w, 2, first_counter=0, seed=3, precision=bfmri.PREC_FP64,
+                                      delta=1e-8, **opts))
+                high = s.pool_usage()
+            est = res["device_bytes"]
+            slack = 3 * 1024 * max(w.K, w.P) * 8 + 8192
+            assert peak <= est <= peak * 33 // 32 + (2 << 20) + slack, (w.N, opts, peak, est)
+            assert high <= est, (w.N, opts, high, est)
