@@ -2,7 +2,8 @@
 
 The Discussion's second variant gives W_k the prior precision G_w' C_k G_w with
 C_k = diag(alpha_x,k I, alpha_y,k I, alpha_z,k I), the alphas random. W is drawn by the FP64
-streaming solver with one prior scale per direction and component; the alphas by the
+solvers (resident block-Jacobi and red-black reduced kernels, streaming block-Jacobi) with one
+prior scale per direction and component; the alphas by the
 exchange algorithm (Murray, Ghahramani & MacKay 2006): a log-normal proposal, an auxiliary
 field drawn from the prior at the proposal by Algorithm 2's perturbation without a data term
 and PCG from zero, and acceptance from the direction edge sums of W and of the field, after
