@@ -310,7 +310,9 @@ bfmri_status bfmri_get_stats(bfmri_handle* h, double* out);
  * BLOCK_JACOBI or NONE, else INVALID_ARG; bfmri_apply_preconditioner rejects such a handle
  * under RB_REDUCED; factors
  * must be positive and finite, else INVALID_ARG with nothing changed. With factors set,
- * grouped sweeps, probes, SVB steps and the log joint reject the handle with INVALID_ARG.
+ * grouped sweeps, probes and SVB steps reject the handle with INVALID_ARG; the log joint takes
+ * the factors in its edge sums (their pseudo-determinant does not depend on the sampled
+ * parameters and is left out with the other constants).
  * Drops a captured sweep graph. Errors: INVALID_ARG, OOM, CUDA. */
 bfmri_status bfmri_set_edge_factors(bfmri_handle* h, const float* factors);
 

@@ -2470,8 +2470,10 @@ bfmri_status bfmri_svb_summary(bfmri_handle* h, int n_contrasts, const double* C
 bfmri_status bfmri_log_joint(bfmri_handle* h, double* terms) {
   RET(require_stats(h));
   if (!terms) return fail(h, BFMRI_ERR_INVALID_ARG, "terms is NULL");
-  if (h->opt.w_prior != BFMRI_PRIOR_UGL || h->d_ce)
-    return fail(h, BFMRI_ERR_INVALID_ARG, "the log joint needs the graph-Laplacian prior with direction weights");
+  // per-edge factors enter through the edge sums; the pseudo-determinant of G'CG does not
+  // depend on the sampled parameters, so the N/2 log alpha normaliser stands
+  if (h->opt.w_prior != BFMRI_PRIOR_UGL)
+    return fail(h, BFMRI_ERR_INVALID_ARG, "the log joint needs the graph-Laplacian prior");
   const int K = h->K, P = h->P;
   const int grid = log_joint_grid(h->N);
   if (!h->d_lj) {

@@ -221,3 +221,27 @@ def test_options_values_and_calls_that_do_not_take_factors():
     with pytest.raises(bfmri.BfmriError):
         mr.apply_preconditioner(0, np.ones((w.K, w.N)))
     mr.close()
+
+
+def test_log_joint_with_factors_matches_the_oracle():
+    """Eq. UnnormalisedJointPosterior with per-edge factors: the W and A prior terms take the
+    factors in their edge sums (their pseudo-determinant is a constant of the sampled
+    parameters), at the summaries' bar of 1e-10 of the terms' size, from a known state and
+    after two sweeps."""
+    from oracle import summaries
+    w, cw = CASES["small3d_K3_P2"]
+    f = bf16_factors(w, 101)
+    lat = Lattice(w.mask, w.neighbourhood, weights=cw, edge_factors=f)
+    s = state_for(w, np.random.default_rng(102))
+    m = make(w, cw, f, s)
+    for sweep in range(3):
+        if sweep:
+            m.gibbs_sweep(1, sweep)
+        got = m.log_joint()
+        st = m.get_state()
+        ref = summaries.log_joint(lat, w.Y, w.X, st, w.T)
+        scale = sum(abs(ref[k]) for k in ("loglik", "W_prior", "A_prior", "lambda_prior",
+                                           "alpha_prior", "beta_prior"))
+        for key in ref:
+            assert abs(got[key] - ref[key]) <= 1e-10 * scale, (key, got[key], ref[key])
+    m.close()
