@@ -170,9 +170,10 @@ typedef struct {
                                 diag(alpha) times the diagonal of L'L) or no preconditioner
                                 (precond BLOCK_JACOBI or NONE, precision FP64, else INVALID_ARG
                                 at create); the A prior stays the graph Laplacian; grouped
-                                sweeps, probes, SVB steps and the log joint reject LTL handles
-                                with INVALID_ARG. BFMRI_PRIOR_ANISO: the anisotropic prior
-                                with random alpha per direction (see its #define). */
+                                sweeps, probes and SVB steps reject LTL handles with
+                                INVALID_ARG; the log joint takes |L w_k|^2 in its W prior
+                                term. BFMRI_PRIOR_ANISO: the anisotropic prior with random
+                                alpha per direction (see its #define). */
   int pcg_lanes;             /* lanes of the register-resident FP64 solver on the red-black
                                 reduced system (BFMRI_PRECOND_RB_REDUCED, K or P <= 6):
                                 2 = lane pairs, each pair holding one red and one black voxel
@@ -516,8 +517,10 @@ bfmri_status bfmri_svb_summary(bfmri_handle* h, int n_contrasts, const double* C
  * sums over t = P+1..T), [1] log p~(W | alpha) = sum_k N/2 log alpha_k - alpha_k W_k D_w W_k'/2,
  * [2] the same for A and beta (0 under the independent AR prior), [3..5] the Gamma
  * log-priors of lambda, alpha, beta without constants (Ga(scale, shape)), [6] the total.
- * Differences between two states are log posterior ratios. Errors: STATE (statistics not
- * computed), INVALID_ARG, CUDA. */
+ * W_k D_w W_k' is |L W_k'|^2 under the L'L prior and takes per-edge factors in its edge
+ * sums; the anisotropic prior is INVALID_ARG (its normaliser, log pdet sum_d alpha_d L_d,
+ * does not separate from the alphas). Differences between two states are log posterior
+ * ratios. Errors: STATE (statistics not computed), INVALID_ARG, CUDA. */
 bfmri_status bfmri_log_joint(bfmri_handle* h, double* terms);
 
 /* Gauss quadrature value e1' log(T) e1 of the Lanczos tridiagonal T built from m CG

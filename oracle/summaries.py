@@ -108,7 +108,7 @@ def svb_summary(samples, C, gamma):
     return dict(mean=mean, cov=cov, ppm=ppm)
 
 
-def log_joint(lat: Lattice, Y, X, state, T, priors=model.PRIORS, spatial_ar=True):
+def log_joint(lat: Lattice, Y, X, state, T, priors=model.PRIORS, spatial_ar=True, prior="ugl"):
     """Eq. UnnormalisedJointPosterior at state = dict(W, A, lam, alpha, beta).
 
     loglik      = sum_n [(T - P)/2 log lambda_n - lambda_n RSS_n / 2]   (Eq. log-like; RSS
@@ -116,6 +116,8 @@ def log_joint(lat: Lattice, Y, X, state, T, priors=model.PRIORS, spatial_ar=True
     W prior     = sum_k [N/2 log alpha_k - alpha_k W_k D_w W_k' / 2]      (Eq. UnnormalisedWPrior)
     A prior     = sum_p [N/2 log beta_p - beta_p A_p D_a A_p' / 2]        (D_a = D_w)
     lambda, alpha, beta priors: Gamma log densities without their constants.
+    prior = "ltl": D_w = L'L in the W prior (W_k D_w W_k' = |L W_k'|^2); its normaliser scales
+    with alpha_k as that of L, so the N/2 log alpha_k term is the same.
     Returns dict of the six terms and their total."""
     W, A = state["W"], state["A"]
     lam = np.asarray(state["lam"], dtype=np.float64)
@@ -125,7 +127,7 @@ def log_joint(lat: Lattice, Y, X, state, T, priors=model.PRIORS, spatial_ar=True
     rss = model.rss_direct(Y, X, W, A)
     terms = {}
     terms["loglik"] = float(np.sum(0.5 * (T - P) * np.log(lam) - 0.5 * lam * rss))
-    Qw = model.quad_forms_laplacian(lat, W)
+    Qw = model.quad_forms_ltl(lat, W) if prior == "ltl" else model.quad_forms_laplacian(lat, W)
     terms["W_prior"] = float(np.sum(0.5 * N * np.log(alpha) - 0.5 * alpha * Qw))
     sp_a = spatial_ar and P > 0
     if sp_a:

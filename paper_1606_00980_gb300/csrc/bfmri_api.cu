@@ -2470,10 +2470,11 @@ bfmri_status bfmri_svb_summary(bfmri_handle* h, int n_contrasts, const double* C
 bfmri_status bfmri_log_joint(bfmri_handle* h, double* terms) {
   RET(require_stats(h));
   if (!terms) return fail(h, BFMRI_ERR_INVALID_ARG, "terms is NULL");
-  // per-edge factors enter through the edge sums; the pseudo-determinant of G'CG does not
-  // depend on the sampled parameters, so the N/2 log alpha normaliser stands
-  if (h->opt.w_prior != BFMRI_PRIOR_UGL)
-    return fail(h, BFMRI_ERR_INVALID_ARG, "the log joint needs the graph-Laplacian prior");
+  // per-edge factors enter through the edge sums, the L'L prior through |L w_k|^2; neither's
+  // pseudo-determinant depends on the sampled parameters beyond alpha's power, so the N/2
+  // log alpha normaliser stands. The anisotropic prior's does (log pdet sum_d alpha_d L_d).
+  if (h->opt.w_prior == BFMRI_PRIOR_ANISO)
+    return fail(h, BFMRI_ERR_INVALID_ARG, "the log joint needs the graph-Laplacian or the L'L prior");
   const int K = h->K, P = h->P;
   const int grid = log_joint_grid(h->N);
   if (!h->d_lj) {
@@ -2496,12 +2497,13 @@ bfmri_status bfmri_log_joint(bfmri_handle* h, double* terms) {
     q.out = nullptr;
     q.rng = rng_of(h, 0, TAG_ALPHA);
     q.exhausted = h->d_flags + 1;
-    q.ltl = 0;
+    q.ltl = h->opt.w_prior == BFMRI_PRIOR_LTL ? 1 : 0;
     q.D = K;
     q.V = h->d_W;
     q.Q_out = d_Qw;
     cudaError_t e = launch_hyper(q, h->stream);
     if (e == cudaSuccess && spatial) {
+      q.ltl = 0;   // the A prior stays the graph Laplacian
       q.D = P;
       q.V = h->d_A;
       q.Q_out = d_Qa;

@@ -152,3 +152,23 @@ def test_options_and_calls_that_do_not_take_the_ltl_prior():
         ms[0].spvb_step(4, 1)
     for m in ms:
         m.close()
+
+
+def test_log_joint_matches_the_oracle(case):
+    """Eq. UnnormalisedJointPosterior under the L'L prior (W prior term with |L w_k|^2, the A
+    prior the graph Laplacian) at the summaries' bar of 1e-10 of the terms' size, from a known
+    state and after two sweeps."""
+    from oracle import summaries
+    w, cw, lat, s = case
+    m = make(w, cw, s)
+    for sweep in range(3):
+        if sweep:
+            m.gibbs_sweep(1, sweep)
+        got = m.log_joint()
+        st = m.get_state()
+        ref = summaries.log_joint(lat, w.Y, w.X, st, w.T, prior="ltl")
+        scale = sum(abs(ref[k]) for k in ("loglik", "W_prior", "A_prior", "lambda_prior",
+                                           "alpha_prior", "beta_prior"))
+        for key in ref:
+            assert abs(got[key] - ref[key]) <= 1e-10 * scale, (key, got[key], ref[key])
+    m.close()

@@ -137,7 +137,7 @@ def state_of(w, rng):
                 beta=rng.uniform(1.0, 20.0, w.P))
 
 
-def log_joint_scipy(lat, w, s, priors, spatial_ar):
+def log_joint_scipy(lat, w, s, priors, spatial_ar, prior="ugl"):
     """The same density from normalised library densities: AR(P) innovations in the time
     domain with scipy's normal density, scipy's Gamma densities, and the GMRF term summed
     over the lattice edges. Differs from the oracle by a constant only."""
@@ -150,13 +150,21 @@ def log_joint_scipy(lat, w, s, priors, spatial_ar):
             ll += st.norm.logpdf(innov, scale=1.0 / math.sqrt(s["lam"][n]))
     E = lat.edges()
 
-    def gmrf(V, prec):
+    def gmrf(V, prec, ltl=False):
         tot = 0.0
         for k in range(V.shape[0]):
-            q = sum((V[k, i] - V[k, j]) ** 2 for i, j, _ in E)
+            if ltl:
+                # |L v|^2 with (L v)_i = sum over the edges at i of (v_i - v_j)
+                lv = np.zeros(N)
+                for i, j, _ in E:
+                    lv[i] += V[k, i] - V[k, j]
+                    lv[j] += V[k, j] - V[k, i]
+                q = float(lv @ lv)
+            else:
+                q = sum((V[k, i] - V[k, j]) ** 2 for i, j, _ in E)
             tot += 0.5 * N * math.log(prec[k]) - 0.5 * prec[k] * q
         return tot
-    out = ll + gmrf(s["W"], s["alpha"])
+    out = ll + gmrf(s["W"], s["alpha"], prior == "ltl")
     out += st.gamma.logpdf(s["lam"], a=priors["u2"], scale=priors["u1"]).sum()
     out += st.gamma.logpdf(s["alpha"], a=priors["q2"], scale=priors["q1"]).sum()
     if spatial_ar and P > 0:
@@ -165,22 +173,23 @@ def log_joint_scipy(lat, w, s, priors, spatial_ar):
     return out
 
 
+@pytest.mark.parametrize("prior", ["ugl", "ltl"])
 @pytest.mark.parametrize("P,spatial", [(0, True), (2, True), (2, False)])
-def test_log_joint_differences_match_library_densities(P, spatial):
+def test_log_joint_differences_match_library_densities(P, spatial, prior):
     """Ratios of the unnormalised joint posterior (the quantity the paper uses it for) equal
     those of fully normalised scipy densities: any dropped term, sign or factor would show
     up in the difference of two states."""
     w, lat = tiny((3, 3, 2), K=3, P=P, T=25, seed=7 + P)
     rng = np.random.default_rng(11)
     s1, s2 = state_of(w, rng), state_of(w, rng)
-    o1 = summaries.log_joint(lat, w.Y, w.X, s1, w.T, spatial_ar=spatial)
-    o2 = summaries.log_joint(lat, w.Y, w.X, s2, w.T, spatial_ar=spatial)
-    r1 = log_joint_scipy(lat, w, s1, model.PRIORS, spatial)
-    r2 = log_joint_scipy(lat, w, s2, model.PRIORS, spatial)
+    o1 = summaries.log_joint(lat, w.Y, w.X, s1, w.T, spatial_ar=spatial, prior=prior)
+    o2 = summaries.log_joint(lat, w.Y, w.X, s2, w.T, spatial_ar=spatial, prior=prior)
+    r1 = log_joint_scipy(lat, w, s1, model.PRIORS, spatial, prior)
+    r2 = log_joint_scipy(lat, w, s2, model.PRIORS, spatial, prior)
     assert abs((o1["total"] - o2["total"]) - (r1 - r2)) <= 1e-9 * max(1.0, abs(r1 - r2))
     # the parts change with the parameters they name only
     s3 = dict(s1, alpha=s1["alpha"] * 1.5)
-    o3 = summaries.log_joint(lat, w.Y, w.X, s3, w.T, spatial_ar=spatial)
+    o3 = summaries.log_joint(lat, w.Y, w.X, s3, w.T, spatial_ar=spatial, prior=prior)
     for key in ("loglik", "A_prior", "lambda_prior", "beta_prior"):
         assert o3[key] == o1[key]
     assert o3["W_prior"] != o1["W_prior"] and o3["alpha_prior"] != o1["alpha_prior"]
