@@ -31,7 +31,8 @@ summaries -- posterior summaries: chain PPMs and joint PPMs (Eq. MCMCPPM, Eq. MC
             posterior (Eq. UnnormalisedJointPosterior)
 
 Parity status: every function is pinned by a ``-m "not gpu"`` test against a closed form,
-an invariant, an independent library routine or brute force, except the SVB convergence
-heuristics of Appendix C (``gibbs.svb_extrapolate``), which are "parity unpinned": the
-paper prints no iterate values, so only self-consistency is checked.
+an invariant, an independent library routine or brute force. The SVB extrapolation of
+Appendix C (``gibbs.svb_extrapolate``), for which the paper prints no iterate values, is
+pinned branch by branch to values worked by hand from the rule the appendix states; its
+fallback for a non-positive prediction is a reading, not the paper's.
 """

@@ -274,7 +274,8 @@ def svb_hyper_mean(lat, samples, prior1, prior2):
 
 
 def svb_extrapolate(history, proposal):
-    """Appendix C, trick 1 (parity unpinned: the paper prints no iterate values). history
+    """Appendix C, trick 1 (pinned branch by branch to values worked by hand from the rule
+    the appendix states; the paper prints no iterate values). history
     holds the values used at iterations j-2 and j-1, proposal is the VB value at j. Fit a
     parabola through the three points; if its vertex lies after j use the vertex value, else
     step 20 times the last change; keep within a factor 5 of the proposal; fall back to the

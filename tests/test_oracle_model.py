@@ -281,18 +281,27 @@ def test_svb_w_system_is_average_of_sample_systems():
 
 
 def test_svb_extrapolation_rules():
-    """Appendix C trick 1: vertex after j -> vertex value; otherwise a 20x step; clamped to a
-    factor 5 of the VB proposal (self-consistency only: parity unpinned)."""
-    # 1, 1.5, 1.75 at j-2, j-1, j: parabola -x^2/8 + x/8 + 1.75 (x = iteration - j), vertex
-    # at x = 0.5 (after j) with value 1.78125
-    v = gibbs.svb_extrapolate((np.array([1.0]), np.array([1.5])), np.array([1.75]))
-    assert abs(v[0] - 1.78125) < 1e-12
-    # straight line -> no curvature -> 20x step, clamped at 5x
-    v = gibbs.svb_extrapolate((np.array([1.0]), np.array([2.0])), np.array([3.0]))
-    assert v[0] == 15.0
-    # decreasing toward zero: negative prediction falls back to the proposal
-    v = gibbs.svb_extrapolate((np.array([3.0]), np.array([2.0])), np.array([1.0]))
-    assert v[0] >= 1.0 / 5.0
+    """Appendix C trick 1, every branch at values worked by hand from the rule the appendix
+    states: a parabola through the last three values (x = iteration - j); its vertex value
+    when the vertex lies after j, maximum or minimum; otherwise a_{j-1} + 20 (a_j - a_{j-1});
+    then no more than a factor 5 from the VB proposal a_j. A prediction that is not positive
+    falls back to the proposal (the reading taken where the appendix says nothing)."""
+    def ex(a2, a1, a0):
+        return gibbs.svb_extrapolate((np.array([a2]), np.array([a1])), np.array([a0]))[0]
+    # concave, vertex after j: -x^2/8 + x/8 + 1.75, vertex at x = 1/2 with value 57/32
+    assert abs(ex(1.0, 1.5, 1.75) - 1.78125) <= 1e-15
+    # convex, vertex after j: x^2/2 - x/2 + 1, vertex at x = 1/2 with value 7/8
+    assert abs(ex(4.0, 2.0, 1.0) - 0.875) <= 1e-15
+    # convex, vertex before j (x = -2/3): the 20x step 1.5 + 20 (0.1) = 3.5, inside [0.32, 8]
+    assert abs(ex(2.0, 1.5, 1.6) - 3.5) <= 1e-12
+    # a straight line has no vertex: 1.25 + 20 (0.25) = 6.25, inside [0.3, 7.5]
+    assert ex(1.0, 1.25, 1.5) == 6.25
+    # the 20x step limited to 5 a_j: 2 + 20 (1) = 22 -> 15
+    assert ex(1.0, 2.0, 3.0) == 15.0
+    # vertex before j (x = -1): 2.1 + 20 (-0.1) = 0.1 lifted to a_j / 5 = 0.4
+    assert abs(ex(2.0, 2.1, 2.0) - 0.4) <= 1e-15
+    # a negative prediction (2 + 20 (-1) = -18) falls back to the proposal
+    assert ex(3.0, 2.0, 1.0) == 1.0
 
 
 def test_paper_simulation_workloads_have_the_papers_shapes():
