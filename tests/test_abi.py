@@ -51,6 +51,9 @@ def test_default_options_without_gpu(lib):
     assert o.delta == 1e-8 and o.precond == bfmri.PRECOND_BLOCK_JACOBI
     assert o.debug_skip_block == -1 and o.inner_tol == 1e-6 and o.ssor_omega == 1.0
     assert list(o.edge_weight) == [1.0, 1.0, 1.0]
+    # the trailing fields, read back through the same layout (a mismatch shows here first)
+    assert o.w_prior == bfmri.PRIOR_UGL and o.pcg_lanes == 0 and o.aniso_step == 0.0
+    assert o.mrhs_tile == 0 and o.stats_kernel == 0
 
 
 def test_create_rejects_bad_arguments_without_touching_the_gpu(lib):
